@@ -1,0 +1,252 @@
+"""Seeded synthetic inputs: room meshes, sources, receivers, admittances.
+
+This module only produces geometry and random numbers.  It holds none of the
+boundary-element or FMM arithmetic: no normals, areas, quadrature points or
+kernel values are computed here.  Both the CUDA path and the CPU oracle take
+its arrays as plain inputs.
+
+Geometry follows the rooms of Sec. 4 (a shoebox room and an L-shaped room,
+walls meshed with flat triangles).  Every wall is split into a structured grid
+of rectangles and every rectangle into two right triangles.  The vertex order
+of every triangle is counter-clockwise seen from OUTSIDE the room, so the
+right-hand normal points out of the room, as Eq. (sp3) requires.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SOUND_SPEED = 343.0  # m/s, the speed of sound used for the rooms of Sec. 4
+
+
+def wavenumber(freq_hz: float, c: float = SOUND_SPEED) -> float:
+    """k = omega / c (Eq. sp2)."""
+    return 2.0 * math.pi * freq_hz / c
+
+
+def _grid_face(origin, ea, eb, na, nb):
+    """Vertices and triangles of one planar rectangular wall.
+
+    origin, ea, eb: 3-vectors; the wall is origin + s*ea + t*eb, s,t in [0,1].
+    Triangles are ordered so that (ea x eb) is their right-hand normal.
+    """
+    s = np.linspace(0.0, 1.0, na + 1)
+    t = np.linspace(0.0, 1.0, nb + 1)
+    S, T = np.meshgrid(s, t, indexing="ij")
+    verts = (np.asarray(origin, float)[None, None, :]
+             + S[..., None] * np.asarray(ea, float)[None, None, :]
+             + T[..., None] * np.asarray(eb, float)[None, None, :]).reshape(-1, 3)
+    idx = np.arange((na + 1) * (nb + 1)).reshape(na + 1, nb + 1)
+    v00 = idx[:-1, :-1].ravel()
+    v10 = idx[1:, :-1].ravel()
+    v01 = idx[:-1, 1:].ravel()
+    v11 = idx[1:, 1:].ravel()
+    t1 = np.stack([v00, v10, v11], axis=1)
+    t2 = np.stack([v00, v11, v01], axis=1)
+    tris = np.empty((2 * v00.size, 3), dtype=np.int64)
+    tris[0::2] = t1
+    tris[1::2] = t2
+    return verts, tris
+
+
+def _concat(parts):
+    verts, tris, groups = [], [], []
+    off = 0
+    for g, (v, t) in enumerate(parts):
+        verts.append(v)
+        tris.append(t + off)
+        groups.append(np.full(t.shape[0], g, dtype=np.int32))
+        off += v.shape[0]
+    return (np.concatenate(verts).astype(np.float64),
+            np.concatenate(tris).astype(np.int32),
+            np.concatenate(groups))
+
+
+def shoebox_mesh(lx, ly, lz, nx, ny, nz):
+    """Closed shoebox [0,lx]x[0,ly]x[0,lz]; nx,ny,nz rectangles per edge.
+
+    Returns (verts[nv,3] f64, tris[nt,3] i32, wall[nt] i32) with
+    nt = 4*(nx*ny + nx*nz + ny*nz).  Wall ids: 0 x=0, 1 x=lx, 2 y=0, 3 y=ly,
+    4 z=0, 5 z=lz.  Outward normal = (v1-v0) x (v2-v0) direction.
+    """
+    X, Y, Z = np.eye(3)
+    parts = [
+        # x = 0, outward -x: ea x eb must be -x  -> ea = z, eb = y
+        _grid_face([0, 0, 0], Z * lz, Y * ly, nz, ny),
+        # x = lx, outward +x: ea = y, eb = z
+        _grid_face([lx, 0, 0], Y * ly, Z * lz, ny, nz),
+        # y = 0, outward -y: ea = x, eb = z
+        _grid_face([0, 0, 0], X * lx, Z * lz, nx, nz),
+        # y = ly, outward +y: ea = z, eb = x
+        _grid_face([0, ly, 0], Z * lz, X * lx, nz, nx),
+        # z = 0, outward -z: ea = y, eb = x
+        _grid_face([0, 0, 0], Y * ly, X * lx, ny, nx),
+        # z = lz, outward +z: ea = x, eb = y
+        _grid_face([0, 0, lz], X * lx, Y * ly, nx, ny),
+    ]
+    return _concat(parts)
+
+
+def shoebox_counts_for_h(lx, ly, lz, h):
+    """Rectangle counts per edge for leg length at most h."""
+    return tuple(max(1, int(math.ceil(L / h - 1e-9))) for L in (lx, ly, lz))
+
+
+def _rect_wall(origin, ea, eb, ha, hb):
+    na = max(1, int(math.ceil(np.linalg.norm(ea) / ha - 1e-9)))
+    nb = max(1, int(math.ceil(np.linalg.norm(eb) / hb - 1e-9)))
+    return _grid_face(origin, ea, eb, na, nb)
+
+
+def lroom_mesh(h):
+    """L-shaped room: box A=[0,5]x[0,4]x[0,3] joined to B=[5,8]x[0,3]x[0,3].
+
+    The shared 3x3 m face at x=5, y in [0,3] is open.  All walls are meshed
+    with legs <= h.  Wall ids are the part indices below.
+    """
+    X, Y, Z = np.eye(3)
+    parts = [
+        _rect_wall([0, 0, 0], Z * 3, Y * 4, h, h),            # x=0  (-x)
+        _rect_wall([0, 0, 0], X * 8, Z * 3, h, h),            # y=0  (-y), both boxes
+        _rect_wall([0, 4, 0], Z * 3, X * 5, h, h),            # y=4  (+y), box A
+        _rect_wall([5, 3, 0], Z * 3, X * 3, h, h),            # y=3  (+y), box B
+        _rect_wall([5, 3, 0], Y * 1, Z * 3, h, h),            # x=5, y in [3,4] (+x)
+        _rect_wall([8, 0, 0], Y * 3, Z * 3, h, h),            # x=8  (+x)
+        _rect_wall([0, 0, 0], Y * 4, X * 5, h, h),            # z=0 box A (-z)
+        _rect_wall([5, 0, 0], Y * 3, X * 3, h, h),            # z=0 box B (-z)
+        _rect_wall([0, 0, 3], X * 5, Y * 4, h, h),            # z=3 box A (+z)
+        _rect_wall([5, 0, 3], X * 3, Y * 3, h, h),            # z=3 box B (+z)
+    ]
+    return _concat(parts)
+
+
+def lroom_inside(p, margin=0.0):
+    p = np.atleast_2d(p)
+    inA = ((p[:, 0] > margin) & (p[:, 0] < 5 + margin) & (p[:, 1] > margin)
+           & (p[:, 1] < 4 - margin) & (p[:, 2] > margin) & (p[:, 2] < 3 - margin))
+    inB = ((p[:, 0] > 5 - margin) & (p[:, 0] < 8 - margin) & (p[:, 1] > margin)
+           & (p[:, 1] < 3 - margin) & (p[:, 2] > margin) & (p[:, 2] < 3 - margin))
+    return inA | inB
+
+
+def seeded_rng(config_index: int) -> np.random.Generator:
+    """numpy PCG64 seeded with 2103_16073 + config index."""
+    return np.random.Generator(np.random.PCG64(2103_16073 + int(config_index)))
+
+
+def uniform_points_in_box(rng, lo, hi, n, margin, avoid=None, avoid_dist=0.0):
+    lo = np.asarray(lo, float) + margin
+    hi = np.asarray(hi, float) - margin
+    out = []
+    while len(out) < n:
+        p = lo + (hi - lo) * rng.random(3)
+        if avoid is not None and len(avoid):
+            if np.min(np.linalg.norm(np.asarray(avoid) - p, axis=1)) < avoid_dist:
+                continue
+        out.append(p)
+    return np.asarray(out, dtype=np.float64)
+
+
+@dataclass
+class Workload:
+    """One synthetic room problem (geometry + frequency + sources)."""
+    name: str
+    verts: np.ndarray
+    tris: np.ndarray
+    wall: np.ndarray
+    freq_hz: float
+    k: float
+    beta: np.ndarray            # complex admittance per element (beta = 1/zeta)
+    sources: np.ndarray         # [ns,3]
+    receivers: np.ndarray       # [nr,3]
+    room: tuple = ()
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.tris.shape[0])
+
+
+def shoebox_workload(name, lx, ly, lz, counts, freq_hz, beta, source, nrec,
+                     config_index, beta_per_wall=None):
+    verts, tris, wall = shoebox_mesh(lx, ly, lz, *counts)
+    rng = seeded_rng(config_index)
+    if beta_per_wall is not None:
+        b = np.asarray(beta_per_wall, dtype=np.complex128)[wall]
+    else:
+        b = np.full(tris.shape[0], complex(beta), dtype=np.complex128)
+    src = np.atleast_2d(np.asarray(source, dtype=np.float64))
+    rec = uniform_points_in_box(rng, [0, 0, 0], [lx, ly, lz], nrec, 0.25,
+                                avoid=src, avoid_dist=0.1)
+    return Workload(name, verts, tris, wall, float(freq_hz), wavenumber(freq_hz),
+                    b, src, rec, room=(lx, ly, lz))
+
+
+def cfg_small(nrec=64):
+    """Shoebox 3.0x2.4x2.0 m, 125 Hz, 16x16 rectangles per wall -> N=3,072,
+    uniform admittance 0.2, monopole at (0.7,0.6,0.5) m."""
+    return shoebox_workload("shoebox-3.0x2.4x2.0-125Hz-N3072", 3.0, 2.4, 2.0,
+                            (16, 16, 16), 125.0, 0.2, (0.7, 0.6, 0.5), nrec, 0)
+
+
+def cfg_1khz(nrec=64):
+    """Same shoebox at 1 kHz, legs lambda/8 -> 70x56x47 rectangles, N=39,368."""
+    return shoebox_workload("shoebox-3.0x2.4x2.0-1kHz-N39368", 3.0, 2.4, 2.0,
+                            (70, 56, 47), 1000.0, 0.2, (0.7, 0.6, 0.5), nrec, 1)
+
+
+def cfg_1khz_sub(nrec=64):
+    """4k-element sub-instance of the 1 kHz shoebox: 22x18x15 -> N=3,984."""
+    return shoebox_workload("shoebox-3.0x2.4x2.0-1kHz-N3984", 3.0, 2.4, 2.0,
+                            (22, 18, 15), 1000.0, 0.2, (0.7, 0.6, 0.5), nrec, 1)
+
+
+def exterior_source(room, dist=0.5):
+    """A point at least `dist` outside the room's bounding box (for the
+    exterior-source test: its field is regular inside the room)."""
+    lx, ly, lz = room
+    return np.array([lx + dist + 0.13, 0.37 * ly, 0.61 * lz], dtype=np.float64)
+
+
+def sphere_mesh(radius, subdiv):
+    """Icosphere: the icosahedron with every triangle split into 4, `subdiv`
+    times, vertices pushed onto the sphere.  N = 20 * 4**subdiv; normals out."""
+    t = (1.0 + 5 ** 0.5) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t),
+         (0, -1, -t), (0, 1, -t), (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+         (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+         (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    verts = [np.array(p, float) / np.linalg.norm(p) for p in v]
+    faces = list(f)
+    for _ in range(subdiv):
+        cache = {}
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    V = np.asarray(verts) * radius
+    T = np.asarray(faces, dtype=np.int64)
+    # orient every triangle so that its right-hand normal points away from 0
+    cen = V[T].mean(axis=1)
+    nrm = np.cross(V[T[:, 1]] - V[T[:, 0]], V[T[:, 2]] - V[T[:, 0]])
+    flip = np.sum(nrm * cen, axis=1) < 0
+    T[flip] = T[flip][:, [0, 2, 1]]
+    return V.astype(np.float64), T.astype(np.int32), np.zeros(T.shape[0], np.int32)
+
+
+def paper_shoebox_counts(lx=8.0, ly=6.0, lz=3.0, max_edge=0.02):
+    """Rectangle counts for the 8x6x3 m room of Sec. 4 meshed with maximum
+    edge (the hypotenuse) `max_edge`: legs max_edge/sqrt(2)."""
+    return shoebox_counts_for_h(lx, ly, lz, max_edge / math.sqrt(2.0))

@@ -1,0 +1,199 @@
+"""Pins for the oracle's spherical basis, coaxial recursions (Sec. 3.3.1),
+rotations and composed RCR translations."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import sph
+
+
+def _nm(p):
+    n_of = np.repeat(np.arange(p), 2 * np.arange(p) + 1)
+    m_of = np.concatenate([np.arange(-n, n + 1) for n in range(p)])
+    return n_of, m_of
+
+
+def test_ylm_matches_library_with_convention_factor():
+    p = 25
+    rng = np.random.default_rng(0)
+    th = rng.random(40) * np.pi
+    ph = rng.random(40) * 2 * np.pi - np.pi
+    n_of, m_of = _nm(p)
+    Ys = special.sph_harm_y(n_of[:, None], m_of[:, None], th[None], ph[None])
+    eps = np.where(m_of >= 0, (-1.0) ** np.abs(m_of), 1.0)
+    assert np.max(np.abs(eps[:, None] * Ys - sph.ylm(p, th, ph))) < 1e-13
+    # Y_n^{-m} = conj(Y_n^m)
+    Y = sph.ylm(p, th, ph)
+    neg = np.array([sph.idx(n, -m) for n, m in zip(n_of, m_of)])
+    assert np.max(np.abs(Y[neg] - np.conj(Y))) < 1e-15
+
+
+@pytest.mark.parametrize("k", [0.7, 2.0, 9.0])
+def test_green_addition_theorem(k):
+    """G(x,y) = ik sum S_n^m(x-c) R_n^{-m}(y-c) for |x-c| > |y-c|."""
+    rng = np.random.default_rng(1)
+    c = rng.standard_normal(3)
+    p = 45
+    n_of, m_of = _nm(p)
+    neg = np.array([sph.idx(n, -m) for n, m in zip(n_of, m_of)])
+    for _ in range(4):
+        y = c + rng.standard_normal(3) * 0.1
+        x = c + rng.standard_normal(3)
+        x = c + (x - c) / np.linalg.norm(x - c) * 1.3
+        S = sph.singular(p, k, x - c)
+        R = sph.regular(p, k, y - c)
+        G = np.exp(1j * k * np.linalg.norm(x - y)) / (4 * np.pi * np.linalg.norm(x - y))
+        assert abs(1j * k * np.sum(S * R[neg]) - G) < 1e-13 * abs(G)
+
+
+def test_grad_regular_finite_difference():
+    p, k = 10, 3.0
+    rng = np.random.default_rng(2)
+    h = 1e-6
+    for _ in range(5):
+        r = rng.standard_normal(3) * 0.4
+        g = sph.grad_regular(p, k, r)
+        fd = np.stack([(sph.regular(p, k, r + h * e) - sph.regular(p, k, r - h * e)) / (2 * h)
+                       for e in np.eye(3)], -1)
+        assert np.max(np.abs(g - fd)) < 1e-8
+
+
+@pytest.mark.parametrize("ktau", [0.3, 0.9, 3.0, 12.0])
+@pytest.mark.parametrize("kind", ["SR", "RR"])
+@pytest.mark.parametrize("scheme", ["original", "stabilized"])
+def test_coaxial_addition_theorem(ktau, kind, scheme):
+    """F_n^m(r + tau z) = sum_n' (E|F)^m_{n'n} R_n'^m(r): checked column by
+    column against direct evaluation (truncation made negligible by a large
+    row count and |r| = 0.1 tau)."""
+    k = 1.7
+    tau = ktau / k
+    p, big = 10, 36
+    X = sph.coaxial(big, ktau, kind, scheme)
+    r = np.array([0.06, -0.05, 0.055]) * tau
+    F = sph.singular if kind == "SR" else sph.regular
+    lhs = F(p, k, r + np.array([0.0, 0.0, tau]))
+    Rv = sph.regular(big, k, r)
+    n_of, m_of = _nm(p)
+    for q, (n, m) in enumerate(zip(n_of, m_of)):
+        s = sum(X[abs(m), n1, n] * Rv[sph.idx(n1, m)] for n1 in range(abs(m), big))
+        assert abs(s - lhs[q]) <= 1e-11 * max(1.0, abs(lhs[q]))
+
+
+def test_coaxial_projection_quadrature():
+    """(S|R)^m_{n'n}(tau) = int conj(Y_n'^m) S_n^m(a u + tau z) dOmega / j_n'(ka)."""
+    k, tau, a, p = 2.0, 1.5, 0.5, 8
+    X = sph.coaxial(p, k * tau, "SR")
+    nq = 40
+    xg, wg = np.polynomial.legendre.leggauss(nq)
+    phis = 2 * np.pi * np.arange(2 * nq) / (2 * nq)
+    TH, PH = np.meshgrid(np.arccos(xg), phis, indexing="ij")
+    W = (wg[:, None] * np.full(2 * nq, np.pi / nq)).ravel()
+    u = np.stack([np.sin(TH) * np.cos(PH), np.sin(TH) * np.sin(PH), np.cos(TH)], -1).reshape(-1, 3)
+    S = sph.singular(p, k, a * u + np.array([0, 0, tau]))
+    Y = sph.ylm(p, np.arccos(u[:, 2]), np.arctan2(u[:, 1], u[:, 0]))
+    j = special.spherical_jn(np.arange(p), k * a)
+    for n in range(p):
+        for n1 in range(p):
+            for m in range(-min(n, n1), min(n, n1) + 1):
+                proj = np.sum(W * np.conj(Y[sph.idx(n1, m)]) * S[sph.idx(n, m)]) / j[n1]
+                assert abs(proj - X[abs(m), n1, n]) < 1e-9 * max(1.0, abs(proj))
+
+
+def test_printed_shft8_third_formula_fails_corrected_holds():
+    """The third formula of Eq. (shft8) as printed (last coefficient
+    b_{n+1}^{-m-1}) does not reproduce exact coefficients; with b_n^{-m-1}
+    it does (the reading the oracle uses)."""
+    p, ktau = 24, 20.0
+    ref = sph.coaxial(p, ktau, "SR", "original")
+    good = sph.coaxial(p, ktau, "SR", "stabilized")
+    bad = sph.coaxial(p, ktau, "SR", "stabilized", misprint=True)
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(good - ref)) < 1e-13 * scale
+    assert np.max(np.abs(bad - ref)) > 1e-6 * scale
+
+
+def test_stabilized_scheme_stable_where_original_is_not():
+    """Sec. 3.3.1: n-propagation (original step 3) is CFL-unstable for n' > n
+    at large k tau; the stabilized scheme is not.  Reference: the original
+    recursion run in 40-digit arithmetic."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    p, ktau = 100, 300.0
+    ref = sph.coaxial(p, ktau, "SR", "stabilized", mp=mpmath.mp)
+    R = np.vectorize(complex)(ref)
+    scale = np.max(np.abs(R))
+    e_orig = np.max(np.abs(sph.coaxial(p, ktau, "SR", "original") - R)) / scale
+    e_stab = np.max(np.abs(sph.coaxial(p, ktau, "SR", "stabilized") - R)) / scale
+    assert e_stab < 1e-13
+    assert e_orig > 1e3 * e_stab
+
+
+def _random_rotation(rng):
+    q = rng.standard_normal(4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([[a * a + b * b - c * c - d * d, 2 * (b * c - a * d), 2 * (b * d + a * c)],
+                     [2 * (b * c + a * d), a * a - b * b + c * c - d * d, 2 * (c * d - a * b)],
+                     [2 * (b * d - a * c), 2 * (c * d + a * b), a * a - b * b - c * c + d * d]])
+
+
+def test_rotation_blocks_definition_unitarity_composition():
+    rng = np.random.default_rng(4)
+    p = 12
+    Q1, Q2 = _random_rotation(rng), _random_rotation(rng)
+    D1 = sph.rotation_blocks(Q1, p)
+    D2 = sph.rotation_blocks(Q2, p)
+    D12 = sph.rotation_blocks(Q2 @ Q1, p)
+    # pointwise definition: Y_n^m(x) = sum_m' D_{m'm} Y_n^m'(Q x)
+    x = rng.standard_normal((20, 3))
+    x /= np.linalg.norm(x, axis=1)[:, None]
+    qx = x @ Q1.T
+    Y = sph.ylm(p, np.arccos(x[:, 2]), np.arctan2(x[:, 1], x[:, 0]))
+    Yq = sph.ylm(p, np.arccos(qx[:, 2]), np.arctan2(qx[:, 1], qx[:, 0]))
+    for n in range(p):
+        s = slice(n * n, (n + 1) ** 2)
+        assert np.max(np.abs(D1[n].T @ Yq[s] - Y[s])) < 1e-13
+        assert np.max(np.abs(D1[n] @ D1[n].conj().T - np.eye(2 * n + 1))) < 1e-13
+        # first Q1 then Q2: coefficients transform by D(Q2) D(Q1)
+        assert np.max(np.abs(D2[n] @ D1[n] - D12[n])) < 1e-13
+    # rotation about z by a: Y^m(R_z x) = e^{ima} Y^m(x), so D = diag(e^{-ima})
+    a = 0.7
+    Rz = np.array([[math.cos(a), -math.sin(a), 0], [math.sin(a), math.cos(a), 0], [0, 0, 1]])
+    Dz = sph.rotation_blocks(Rz, p)
+    for n in range(p):
+        m = np.arange(-n, n + 1)
+        assert np.max(np.abs(Dz[n] - np.diag(np.exp(-1j * m * a)))) < 1e-13
+
+
+@pytest.mark.parametrize("kind", ["SR", "RR"])
+def test_composed_translation_addition_theorem(kind):
+    """RCR-composed translation reproduces S (or R) about a shifted centre."""
+    rng = np.random.default_rng(6)
+    k = 2.3
+    p_in, p_out = 9, 34
+    for _ in range(3):
+        t = rng.standard_normal(3)
+        t *= 1.2 / np.linalg.norm(t)
+        T = sph.translation(t, k, p_out, p_in, kind)
+        r = rng.standard_normal(3) * 0.05
+        F = sph.singular if kind == "SR" else sph.regular
+        lhs = F(p_in, k, r + t)
+        rhs = T.T @ sph.regular(p_out, k, r)
+        assert np.max(np.abs(lhs - rhs)) < 1e-11 * np.max(np.abs(lhs))
+
+
+def test_multipole_to_multipole_translation():
+    """(S|S) = (R|R): S_n^m(r + t) = sum (R|R)_{n'n}(t) S_n'^m(r), |r| > |t|."""
+    rng = np.random.default_rng(7)
+    k = 1.9
+    t = rng.standard_normal(3)
+    t *= 0.2 / np.linalg.norm(t)
+    p_in, p_out = 8, 40
+    T = sph.translation(t, k, p_out, p_in, "RR")
+    r = rng.standard_normal(3)
+    r *= 2.0 / np.linalg.norm(r)
+    lhs = sph.singular(p_in, k, r + t)
+    rhs = T.T @ sph.singular(p_out, k, r)
+    assert np.max(np.abs(lhs - rhs)) < 1e-10 * np.max(np.abs(lhs))
