@@ -1,0 +1,386 @@
+"""Benchmark: FGMRES time-to-solve at true relative residual 1e-4 and
+matvecs/s of the FMM-accelerated Helmholtz BEM on one GB300.
+
+Workload: shoebox 3.0 x 2.4 x 2.0 m at 1 kHz (kD ~ 81), flat triangles with
+legs lambda/8 (70 x 56 x 47 rectangles per edge) -> N = 39,368 elements,
+uniform admittance 0.2, monopole at (0.7, 0.6, 0.5) m; octree leaves <= 64
+elements; FMM order per level from the excess-bandwidth rule (d0 = 6,
+p_min = 12).  Synthetic seeded input; see the design doc.
+
+A step is one solve A x = b of Eq. (dbem4) with the mixed operator (FP32 near
+field, P2M/L2P and translations, FP64 Arnoldi) right-preconditioned by block
+Jacobi, judged by the true residual of the FP64 FMM operator.  N GPUs (torchrun)
+each solve their own source position: weak scaling, no data-path collective.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import os
+
+# the CPU oracle legs run on one host thread; keep BLAS from spreading
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import json
+import math
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FGMRES time-to-solve @1e-4 & matvecs/s: mixed+learned vs plain FP64, 1 GB300"
+TOL = 1e-4
+RESTART = 40
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    def __init__(self, gpu_index=0):
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        self.cmd = ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                    "-lms", "200"]
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(self.cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self, max_mhz):
+        rows = []
+        try:
+            for ln in open(self.path):
+                parts = [x.strip() for x in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        except Exception:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": max_mhz, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else max_mhz, "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_problem(fb, W, torch, rank):
+    wl = W.cfg_1khz()
+    if rank > 0:   # each rank solves its own seeded source position
+        rng = W.seeded_rng(100 + rank)
+        wl.sources = W.uniform_points_in_box(rng, [0, 0, 0], list(wl.room), 1, 0.25)
+    mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+    fb.fb_mesh_set_admittance(mesh, wl.beta)
+    tree = fb.fb_tree_build(mesh, 64)
+    A32 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 12)
+    A64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, 12)
+    L64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_L, fb.FB_PREC_FP64_FMM, 6.0, 12)
+    pc32 = fb.fb_precond_create(A32, fb.FB_PC_BLOCK_JACOBI)
+    pc64 = fb.fb_precond_create(A64, fb.FB_PC_BLOCK_JACOBI)
+    g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
+    fb.fb_gamma_monopole(mesh, wl.k, wl.sources[0], g)
+    b = torch.empty_like(g)
+    fb.fb_operator_apply(L64, g, b)
+    torch.cuda.synchronize()
+    return dict(wl=wl, mesh=mesh, tree=tree, A32=A32, A64=A64, L64=L64, pc32=pc32, pc64=pc64, b=b)
+
+
+def m2l_algorithmic_flops(fb, P, tree):
+    """Algorithmic M2L flops of one matvec: (10/3) p^3 complex MACs x 8 flops
+    per translation (rotation - coaxial - back-rotation), summed over the
+    V-list pairs of every level."""
+    L, org, side, nb = fb.fb_tree_info(tree)
+    n, L2, p = fb.fb_operator_info(P["A32"])
+    total = 0.0
+    for lev in range(2, L + 1):
+        pairs = fb.fb_tree_export(tree, 4, lev).shape[0]
+        total += pairs * (10.0 / 3.0) * p[lev] ** 3 * 8.0
+    executed = 0.0
+    for lev in range(2, L + 1):
+        pairs = fb.fb_tree_export(tree, 4, lev).shape[0]
+        executed += pairs * 8.0 * float(p[lev]) ** 4
+    return total, executed
+
+
+def run_ours(args):
+    import torch
+    import paper_2103_16073_gb300 as fb
+    from paper_2103_16073_gb300 import workloads as W
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
+    P = build_problem(fb, W, torch, rank)
+    wl = P["wl"]
+    n = wl.n
+    stream = torch.cuda.current_stream()
+
+    def solve_mixed(x):
+        return fb.fb_fgmres_solve(P["A32"], P["b"], x, pc=P["pc32"], tol=TOL, restart=RESTART, maxit=3000,
+                                  max_refine=4, true_op=P["A64"])
+
+    x = torch.zeros_like(P["b"])
+    for _ in range(args.warmup):
+        info = solve_mixed(x)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    pk, pk_kind = peaks()
+    sampler = ClockSampler(local)
+    launches0 = fb.fb_kernel_launches()
+    infos = []
+    with sampler:
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(solve_mixed(x))
+        e1.record(stream)
+        barrier()
+    launches = fb.fb_kernel_launches() - launches0
+    ms_total = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    iters = statistics.mean(i["iters"] for i in infos)
+    relres = max(i["true_relres"] for i in infos)
+    ok = all(i["status"] == 0 for i in infos)
+    clocks = sampler.summary(pk.get("sm_max_mhz"))
+
+    # matvecs/s of the mixed operator and the phase split (device pointers)
+    xv = torch.randn(n, dtype=torch.complex128, device="cuda")
+    yv = torch.empty_like(xv)
+    for _ in range(3):
+        fb.fb_operator_apply(P["A32"], xv, yv)
+    torch.cuda.synchronize()
+    nmv = 50
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(nmv):
+        fb.fb_operator_apply(P["A32"], xv, yv)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    mv_ms = a0.elapsed_time(a1) / nmv
+    phases = [fb.fb_operator_apply_timed(P["A32"], xv, yv) for _ in range(10)]
+    ph = {k: statistics.median(p[k] for p in phases) for k in phases[0]}
+    for _ in range(2):
+        fb.fb_operator_apply(P["A64"], xv, yv)
+    torch.cuda.synchronize()
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    nmv64 = 5
+    b0.record(stream)
+    for _ in range(nmv64):
+        fb.fb_operator_apply(P["A64"], xv, yv)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    mv64_ms = b0.elapsed_time(b1) / nmv64
+    ph64 = fb.fb_operator_apply_timed(P["A64"], xv, yv)
+
+    # plain FP64 path: FP64 FMM + FP64 block Jacobi, one solve
+    x64 = torch.zeros_like(P["b"])
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    info64 = fb.fb_fgmres_solve(P["A64"], P["b"], x64, pc=P["pc64"], tol=TOL, restart=RESTART, maxit=3000)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    t64 = c0.elapsed_time(c1) / 1e3
+
+    # end to end through the public API with host (pinned) buffers
+    bh = torch.empty(n, dtype=torch.complex128, pin_memory=True)
+    bh.copy_(P["b"].cpu())
+    xh = torch.zeros(n, dtype=torch.complex128, pin_memory=True)
+    xn = xh.numpy()
+    e2e_t = []
+    for _ in range(max(1, min(args.steps, 5))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fb.fb_fgmres_solve(P["A32"], bh, xn, pc=P["pc32"], tol=TOL, restart=RESTART, maxit=3000,
+                           max_refine=4, true_op=P["A64"])
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.median(e2e_t)
+
+    # roofline of the dominant kernel (M2L translations, FP32 CUDA-core GEMM)
+    alg_flops, exec_flops = m2l_algorithmic_flops(fb, P, P["tree"])
+    m2l_s = ph["m2l"] / 1e3
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s, FP32 FMA pipes at max clock
+    achieved = alg_flops / m2l_s / 1e12
+    res = {
+        "metric": METRIC,
+        "value": round(ws / (ms_step / 1e3), 4),
+        "unit": "solves/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 3),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": "shoebox 3.0x2.4x2.0 m, 1 kHz, N=39368 flat triangles (lambda/8), "
+                               "beta=0.2, FMM leaf<=64, d0=6 pmin=12, FGMRES(40)+block-Jacobi, tol 1e-4",
+                   "n_elements": n, "frequency_hz": wl.freq_hz, "solver": "FGMRES restart 40",
+                   "precond": "block-Jacobi (leaf self blocks)", "operator": "mixed FP32 FMM, FP64 Arnoldi",
+                   "true_residual": "FP64 FMM", "l2": "working set > L2 (translation matrices alone > 129 MB)",
+                   "parallelism": f"replicas x{ws} (one (f, source) solve per GPU)"},
+        "time_to_solve_s": round(ms_step / 1e3, 5),
+        "iterations": iters,
+        "true_relres": relres,
+        "converged": ok,
+        "matvecs_per_s": round(1e3 / mv_ms, 2),
+        "matvec_ms": round(mv_ms, 4),
+        "phase_ms": {k: round(v, 4) for k, v in ph.items()},
+        "plain_fp64": {"time_to_solve_s": round(t64, 4), "iterations": info64["iters"],
+                       "true_relres": info64["true_relres"], "matvecs_per_s": round(1e3 / mv64_ms, 2),
+                       "phase_ms": {k: round(v, 3) for k, v in ph64.items()}},
+        "speedup_vs_plain_fp64": round(t64 / (ms_step / 1e3), 2),
+        "e2e": {"value": round(1.0 / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": 16 * n,
+                "d2h_bytes_per_step": 16 * n},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_trans<float> (M2L)", "bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
+                     "traffic": None, "peak_kind": "FP32 FMA pipes x max SM clock (152 SMs x 128 lanes x 2)",
+                     "algorithmic_flops_per_launch": alg_flops, "executed_flops_per_launch": exec_flops,
+                     "launch_ms": round(ph["m2l"], 4)},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(wl, iters + res_true_matvecs(infos), budget_s=args.cpu_seconds)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(res))
+
+
+def res_true_matvecs(infos):
+    return int(statistics.mean(i["true_matvecs"] for i in infos))
+
+
+def cpu_baseline(wl, matvecs_per_solve, budget_s=15.0):
+    """The oracle's dense FP64 collocation rows timed on the host: rows of A
+    (Eq. dbem4) assembled on the fly and applied, extrapolated to N rows per
+    matvec and to the GPU solve's matvec count."""
+    from oracle import bem
+    mesh = bem.Mesh(wl.verts, wl.tris)
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal(wl.n) + 1j * rng.standard_normal(wl.n)
+    rows_done = 0
+    t0 = time.perf_counter()
+    chunk = 16
+    while time.perf_counter() - t0 < budget_s:
+        rows = np.arange(rows_done, rows_done + chunk) % wl.n
+        A = bem.system_rows(mesh, wl.k, wl.beta, rows)
+        _ = A @ x
+        rows_done += chunk
+    dt = time.perf_counter() - t0
+    per_row = dt / rows_done
+    per_matvec = per_row * wl.n
+    per_solve = per_matvec * max(1, matvecs_per_solve)
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{rows_done} rows of the dense FP64 matrix-free A (N={wl.n}) in {dt:.1f} s; "
+                      f"extrapolated x N rows x {matvecs_per_solve} matvecs per solve",
+            "matvec_s_extrapolated": per_matvec}
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores: each step a bounded sample of
+    dense matrix-free rows, extrapolated to one solve."""
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2103_16073_gb300 import workloads as W
+    wl = W.cfg_1khz()
+    matvecs = args.ref_matvecs
+    vals = []
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(wl, matvecs, budget_s=budget)
+        if i >= args.warmup:
+            vals.append(cb)
+    v = statistics.mean(c["value"] for c in vals)
+    res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "shoebox 3.0x2.4x2.0 m, 1 kHz, N=39368 flat triangles (lambda/8), "
+                                  "beta=0.2, dense FP64 collocation oracle", "matvecs_per_solve": matvecs},
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                            "sample": vals[-1]["sample"]},
+           "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(res))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-matvecs", type=int, default=60,
+                    help="matvecs per solve used to extrapolate the reference arm")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

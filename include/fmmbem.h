@@ -1,0 +1,261 @@
+/*
+ * fmmbem.h -- C ABI of the GB300 (sm_103a) FMM-accelerated Helmholtz BEM.
+ *
+ * The library computes the matrix-vector product at the heart of the
+ * room-acoustics boundary element method of Gumerov & Duraiswami, "Fast
+ * multipole accelerated boundary element methods for room acoustics", and
+ * solves the direct-BEM system with flexible GMRES on one GPU.
+ *
+ * Problem (Sec. 2): Helmholtz equation (Eq. sp2) in a room bounded by flat
+ * triangles, impedance wall condition (Eq. sp3) with the normal pointing out
+ * of the room, monopole source (Eq. sp6), time factor e^{-i omega t},
+ * G = e^{ikR}/(4 pi R).  With the admittance beta = 1/zeta the direct BEM
+ * (Eq. dbem4) reads
+ *      A psi = L gamma,   A = 1/2 I + M - i k L diag(beta),
+ *      gamma = -(dpsi_in/dn - i k beta psi_in)                 (Eq. sp7)
+ * with the operators L, M (Eq. dbem2) and L' (Eq. ibem3).  Piecewise-constant
+ * collocation at element centroids.
+ *
+ * Conventions of every call:
+ *   - every function returns fb_status (FB_OK == 0); on error
+ *     fb_last_error() returns a message for the calling thread;
+ *   - complex arrays are interleaved (re, im) doubles: element i is
+ *     (a[2i], a[2i+1]);
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default);
+ *     calls enqueue work on it and synchronise it only where documented;
+ *   - host input arrays are copied; the caller keeps ownership of every
+ *     pointer it passes; handles are owned by the library and released by
+ *     the matching *_destroy (NULL is accepted and ignored);
+ *   - `memspace` says where caller arrays live: FB_MEM_HOST (plain or
+ *     pinned host memory; the call copies and synchronises the stream) or
+ *     FB_MEM_DEVICE (device pointers on the current device, no sync);
+ *   - all state of a handle lives on the device that was current when it
+ *     was created; no call is thread-safe on the same handle;
+ *   - no C++ exception crosses this boundary; a CUDA error is reported as
+ *     FB_ERR_CUDA and leaves the handle in an unspecified state (destroy it).
+ */
+#ifndef FMMBEM_H
+#define FMMBEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FB_API __attribute__((visibility("default")))
+#else
+#define FB_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fb_status;
+#define FB_OK 0
+#define FB_ERR_ARG 1       /* invalid argument or unsupported combination  */
+#define FB_ERR_CUDA 2      /* a CUDA runtime call failed                   */
+#define FB_ERR_NOCONV 3    /* FGMRES hit maxit before the tolerance        */
+#define FB_ERR_BREAKDOWN 4 /* FGMRES breakdown (zero Hessenberg pivot)     */
+#define FB_ERR_NAN 5       /* NaN/Inf met in a residual                    */
+#define FB_ERR_TIMEOUT 6   /* a bounded device wait ran out                */
+#define FB_ERR_OOM 7       /* device allocation failed                     */
+#define FB_ERR_STATE 8     /* handle in a state that does not allow this   */
+
+/* Operators (Eqs. dbem2, ibem3, dbem4). */
+#define FB_OP_L 0  /* single layer          L[s](x) = int s G dS_y           */
+#define FB_OP_M 1  /* double layer          M[s](x) = int s dG/dn_y dS_y     */
+#define FB_OP_LP 2 /* adjoint double layer L'[s](x) = int s dG/dn_x dS_y     */
+#define FB_OP_A 3  /* direct-BEM system     A = 1/2 I + M - ik L diag(beta)  */
+
+/* How an operator is applied. */
+#define FB_PREC_FP64_DENSE 0 /* stored dense N x N complex128 matrix        */
+#define FB_PREC_FP64_FMM 1   /* FMM, all arithmetic in FP64                 */
+#define FB_PREC_MIXED_FMM 2  /* FMM: FP32 near field, P2M/L2P and
+                                translations; FP64 setup and I/O            */
+
+#define FB_MEM_HOST 0
+#define FB_MEM_DEVICE 1
+
+#define FB_PC_NONE 0
+#define FB_PC_BLOCK_JACOBI 1 /* inverse of each leaf's self near-field block */
+
+typedef struct fb_mesh fb_mesh;
+typedef struct fb_tree fb_tree;
+typedef struct fb_op fb_op;
+typedef struct fb_precond fb_precond;
+
+/* Version string of the library (static storage). */
+FB_API const char* fb_version(void);
+
+/* Copies the last error message of the calling thread into buf (always
+ * NUL-terminated when len > 0).  Returns the last error code. */
+FB_API fb_status fb_last_error(char* buf, size_t len);
+
+/* ---------------------------------------------------------------- mesh -- */
+
+/* Flat-triangle surface mesh (Sec. 4).  verts: nv x 3 doubles (host), tris:
+ * nt x 3 int32 vertex indices (host), counter-clockwise seen from outside the
+ * room so that (v1-v0) x (v2-v0) is the outward normal (Eq. sp3).  Computes on
+ * the device: centroids (collocation points), unit normals, areas, the
+ * 3-point Gauss points of every element, the longest edge and the near-field
+ * cutoff r_c = 1.5 x longest edge (Sec. 3.3: entries of elements closer than
+ * r_c use closed-form integrals).  Admittance is initialised to 0 (rigid).
+ * Errors: FB_ERR_ARG for nv < 3, nt < 1, an index out of range or a
+ * degenerate (zero-area) triangle. */
+FB_API fb_status fb_mesh_create(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                         void* stream, fb_mesh** out);
+
+/* Per-element complex admittance beta = 1/zeta (Eq. sp4; beta = 0 is the
+ * rigid wall of Eq. sp5), nt interleaved complex values in `memspace`. */
+FB_API fb_status fb_mesh_set_admittance(fb_mesh* mesh, const double* beta, int memspace, void* stream);
+
+/* Element count, near-field cutoff r_c and longest edge. */
+FB_API fb_status fb_mesh_info(const fb_mesh* mesh, int64_t* nt, double* rc, double* max_edge);
+
+/* Copies centroids and unit normals (nt x 3 each, host; either may be NULL). */
+FB_API fb_status fb_mesh_geometry(const fb_mesh* mesh, double* centroids, double* normals);
+
+FB_API void fb_mesh_destroy(fb_mesh* mesh);
+
+/* ---------------------------------------------------------------- tree -- */
+
+/* Uniform octree over the element centroids (Sec. 3.3), built on the device:
+ * root = bounding cube of the vertices (side x (1 + 1e-6)), an element
+ * belongs to the leaf containing its centroid, leaf level = first level >= 2
+ * whose fullest leaf holds <= leaf_max elements, capped at the deepest level
+ * whose box side exceeds r_c (the paper's delta > r_c).  Builds the U-lists
+ * (touching leaves) and V-lists (M2L interaction lists) of every level.
+ * Errors: FB_ERR_ARG if leaf_max < 1 or the mesh allows no level >= 2 with
+ * box side > r_c (use FB_PREC_FP64_DENSE for such meshes). */
+FB_API fb_status fb_tree_build(const fb_mesh* mesh, int leaf_max, void* stream, fb_tree** out);
+
+/* Leaf level, root origin (3 doubles), root side, and box counts per level
+ * (array of leaf_level + 1 int64, may be NULL). */
+FB_API fb_status fb_tree_info(const fb_tree* tree, int* leaf_level, double* origin, double* side,
+                       int64_t* nboxes);
+
+/* Host copies for inspection.  which: 0 = element order (nt int64: sorted
+ * position -> element index), 1 = leaf start offsets (nleaf+1 int64),
+ * 2 = box Morton keys of level `level` (nboxes int64), 3 = U-list as
+ * (target, source) leaf-index pairs (2*count int64), 4 = V-list of `level`
+ * as (target, source) box-index pairs.  *count receives the number of
+ * entries (pairs for 3/4); pass out = NULL to query it. */
+FB_API fb_status fb_tree_export(const fb_tree* tree, int which, int level, int64_t* out, int64_t* count);
+
+FB_API void fb_tree_destroy(fb_tree* tree);
+
+/* ------------------------------------------------------------ operator -- */
+
+/* Operator `kind` (FB_OP_*) at wavenumber k > 0, applied as `precision`
+ * (FB_PREC_*).  FMM precisions need `tree` (built from the same mesh); dense
+ * ignores it (may be NULL).  Truncation per level (the paper defers it to
+ * another reference): p_l = max(pmin, ceil(k r_l + 1.8 d0^(2/3) (k r_l)^(1/3))),
+ * r_l = sqrt(3)/2 x box side.  Setup runs on the device in FP64: near-field
+ * entries (closed-form singular parts, Sec. 3.3), per-leaf P2M/L2P operators,
+ * coaxial coefficients by the recursions of Sec. 3.3.1 (original scheme for
+ * k tau < 1, stabilised scheme otherwise), rotation blocks and the composed
+ * translation matrices.  The admittance of `mesh` at creation time is used.
+ * Errors: FB_ERR_ARG (k <= 0, kind/precision out of range, missing tree,
+ * dense N > 60000), FB_ERR_OOM. */
+FB_API fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k, int kind,
+                             int precision, double d0, int pmin, void* stream, fb_op** out);
+
+/* y = Op x.  x, y: N interleaved complex doubles in `memspace`; they must not
+ * overlap.  Device memspace: enqueued on `stream`, no sync. */
+FB_API fb_status fb_operator_apply(fb_op* op, const double* x, double* y, int memspace, void* stream);
+
+/* N, number of FMM levels used (0 for dense) and p per level (array of
+ * leaf_level + 1 ints, entries below level 2 are 0; may be NULL). */
+FB_API fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p_per_level);
+
+/* Host copies of FP64 setup data for inspection.  which: 0 = near-field
+ * entries of leaf `index` (rows x cols complex, row-major; rows = the leaf's
+ * elements in tree order, cols = the elements of its U-list leaves in
+ * ascending leaf order), 1 = P2M operator of leaf `index` (n_leaf x p_L^2
+ * complex, row per element), 2 = L2P operator of leaf `index` (n_leaf x p_L^2),
+ * 3 = M2L translation matrix of level `level`, offset code `index`
+ * (p_l^2 x p_l^2; offset (dx,dy,dz) in box units, code = (dx+3)*49 +
+ * (dy+3)*7 + (dz+3)), 4 = M2M matrix child->parent at child level `level`,
+ * octant `index` (p_{l-1}^2 x p_l^2), 5 = L2L matrix parent->child at child
+ * level `level`, octant `index` (p_l^2 x p_{l-1}^2), 6 = dense matrix row
+ * `index` (N complex).  *count receives the number of complex values. */
+FB_API fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t index, double* out,
+                             int64_t* count);
+
+FB_API void fb_operator_destroy(fb_op* op);
+
+/* Tracing: y = Op x on device pointers (enqueued on `stream`, then the stream
+ * is synchronised) with CUDA-event times in milliseconds per phase:
+ * phase_ms[0] = zeroing + P2M, [1] = M2M, [2] = M2L, [3] = L2L,
+ * [4] = near field + L2P, [5] = total (dense operators fill only [5]).
+ * phase_ms must hold 6 doubles. */
+FB_API fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* stream,
+                                         double* phase_ms);
+
+/* Tracing: running total of kernel launches issued by the library in this
+ * process (setup and apply); differences bracket a region of interest. */
+FB_API long long fb_kernel_launches(void);
+
+/* ------------------------------------------------------ right-hand side -- */
+
+/* gamma_j = -(dpsi_in/dn - i k beta_j psi_in) at the centroids for a unit
+ * monopole at src (Eq. sp7).  gamma: N complex in memspace. */
+FB_API fb_status fb_gamma_monopole(const fb_mesh* mesh, double k, const double* src, double* gamma,
+                            int memspace, void* stream);
+
+/* ------------------------------------------------------- preconditioner -- */
+
+/* Block-Jacobi right preconditioner for an FMM operator: the inverse of each
+ * leaf's self block of the near-field matrix, factorised in FP64 on the
+ * device (Gauss-Jordan with partial pivoting) and applied in the operator's
+ * precision.  Errors: FB_ERR_ARG for dense operators, FB_ERR_BREAKDOWN for a
+ * singular block. */
+FB_API fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out);
+FB_API void fb_precond_destroy(fb_precond* pc);
+
+/* ---------------------------------------------------------------- solve -- */
+
+typedef struct {
+    double tol;            /* target true relative residual ||b-Ax||/||b||     */
+    int restart;           /* Krylov dimension m (>= 1)                        */
+    int maxit;             /* max total inner iterations                       */
+    int max_refine;        /* max outer refinement sweeps (>= 1)               */
+    double inner_tol;      /* tolerance of each inner FGMRES (<= 0: tol)       */
+    const fb_op* true_op;  /* operator of the true residual (NULL: A itself)   */
+} fb_solver_opts;
+
+typedef struct {
+    int iters;             /* inner FGMRES iterations (= preconditioned matvecs) */
+    int refinements;       /* outer sweeps run                                  */
+    int true_matvecs;      /* applications of true_op                            */
+    double est_relres;     /* last Arnoldi residual estimate                     */
+    double true_relres;    /* ||b - true_op x|| / ||b|| at exit                  */
+    int status;            /* FB_OK, FB_ERR_NOCONV, FB_ERR_BREAKDOWN, FB_ERR_NAN */
+} fb_solve_info;
+
+/* Solves A x = b by flexible GMRES (right preconditioned, restarted, FP64
+ * Arnoldi with classical Gram-Schmidt applied twice, Givens least squares),
+ * wrapped in iterative refinement on the true residual of opts->true_op:
+ *   r = b - T x;  stop if ||r||/||b|| <= tol;  solve A d = r to inner_tol;  x += d.
+ * x0 = 0.  b, x: N complex in memspace.  The host reads one scalar per
+ * Arnoldi step (the residual estimate).  Returns info->status as the status. */
+FB_API fb_status fb_fgmres_solve(fb_op* A, fb_precond* pc, const double* b, double* x,
+                          const fb_solver_opts* opts, fb_solve_info* info, int memspace,
+                          void* stream);
+
+/* ------------------------------------------------------------ receivers -- */
+
+/* Field at interior points by Green's identity (Eq. dbem1):
+ *   psi(r) = psi_in(r) + L[gamma + i k beta psi_sc](r) - M[psi_sc](r)
+ * with the same element rule as the operators (direct sum over elements).
+ * src: 3 doubles on the host, or NULL (no incident field added).
+ * psi_sc, gamma: N complex; rcv: nr x 3 doubles; out: nr complex; these
+ * four in memspace. */
+FB_API fb_status fb_eval_field(const fb_mesh* mesh, double k, const double* psi_sc, const double* gamma,
+                        const double* src, const double* rcv, int64_t nr, double* out,
+                        int memspace, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FMMBEM_H */

@@ -1,0 +1,315 @@
+"""Python binding of libfmmbem (include/fmmbem.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays
+and torch tensors to the plain pointers and sizes of the C ABI and raises
+``FBError`` with the library's message when a call fails.  There is no CPU
+fallback: importing the package builds (if needed) and loads the shared
+library, and fails loudly if that is impossible.
+
+Array conventions: complex vectors are complex128 (interleaved re/im doubles).
+A torch tensor on a CUDA device is passed as a device pointer on the current
+torch stream; numpy arrays (or CPU tensors) are passed as host memory, which
+the library copies in and out.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "FBError", "lib", "FB_OP_L", "FB_OP_M", "FB_OP_LP", "FB_OP_A", "FB_PREC_FP64_DENSE",
+    "FB_PREC_FP64_FMM", "FB_PREC_MIXED_FMM", "FB_PC_NONE", "FB_PC_BLOCK_JACOBI",
+    "fb_version", "fb_mesh_create", "fb_mesh_set_admittance", "fb_mesh_info", "fb_mesh_geometry",
+    "fb_mesh_destroy", "fb_tree_build", "fb_tree_info", "fb_tree_export", "fb_tree_destroy",
+    "fb_operator_create", "fb_operator_apply", "fb_operator_info", "fb_operator_export",
+    "fb_operator_destroy", "fb_gamma_monopole", "fb_precond_create", "fb_precond_destroy",
+    "fb_fgmres_solve", "fb_eval_field", "fb_operator_apply_timed", "fb_kernel_launches",
+    "SolverOpts", "SolveInfo",
+]
+
+FB_OK = 0
+FB_OP_L, FB_OP_M, FB_OP_LP, FB_OP_A = 0, 1, 2, 3
+FB_PREC_FP64_DENSE, FB_PREC_FP64_FMM, FB_PREC_MIXED_FMM = 0, 1, 2
+FB_MEM_HOST, FB_MEM_DEVICE = 0, 1
+FB_PC_NONE, FB_PC_BLOCK_JACOBI = 0, 1
+STATUS_NAMES = {0: "FB_OK", 1: "FB_ERR_ARG", 2: "FB_ERR_CUDA", 3: "FB_ERR_NOCONV",
+                4: "FB_ERR_BREAKDOWN", 5: "FB_ERR_NAN", 6: "FB_ERR_TIMEOUT", 7: "FB_ERR_OOM",
+                8: "FB_ERR_STATE"}
+
+
+class FBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class SolverOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int),
+                ("max_refine", C.c_int), ("inner_tol", C.c_double), ("true_op", C.c_void_p)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("true_matvecs", C.c_int),
+                ("est_relres", C.c_double), ("true_relres", C.c_double), ("status", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def _load():
+    path = _build.build()
+    if not os.path.exists(path):
+        raise ImportError("libfmmbem.so is missing and could not be built")
+    L = C.CDLL(path)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    pvp = C.POINTER(C.c_void_p)
+    sigs = {
+        "fb_version": (C.c_char_p, []),
+        "fb_last_error": (i32, [C.c_char_p, C.c_size_t]),
+        "fb_mesh_create": (i32, [vp, i64, vp, i64, vp, pvp]),
+        "fb_mesh_set_admittance": (i32, [vp, vp, i32, vp]),
+        "fb_mesh_info": (i32, [vp, C.POINTER(i64), C.POINTER(dbl), C.POINTER(dbl)]),
+        "fb_mesh_geometry": (i32, [vp, vp, vp]),
+        "fb_mesh_destroy": (None, [vp]),
+        "fb_tree_build": (i32, [vp, i32, vp, pvp]),
+        "fb_tree_info": (i32, [vp, C.POINTER(i32), vp, C.POINTER(dbl), vp]),
+        "fb_tree_export": (i32, [vp, i32, i32, vp, C.POINTER(i64)]),
+        "fb_tree_destroy": (None, [vp]),
+        "fb_operator_create": (i32, [vp, vp, dbl, i32, i32, dbl, i32, vp, pvp]),
+        "fb_operator_apply": (i32, [vp, vp, vp, i32, vp]),
+        "fb_operator_info": (i32, [vp, C.POINTER(i64), C.POINTER(i32), vp]),
+        "fb_operator_export": (i32, [vp, i32, i32, i64, vp, C.POINTER(i64)]),
+        "fb_operator_destroy": (None, [vp]),
+        "fb_gamma_monopole": (i32, [vp, dbl, vp, vp, i32, vp]),
+        "fb_precond_create": (i32, [vp, i32, vp, pvp]),
+        "fb_precond_destroy": (None, [vp]),
+        "fb_fgmres_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolverOpts), C.POINTER(SolveInfo), i32, vp]),
+        "fb_eval_field": (i32, [vp, dbl, vp, vp, vp, vp, i64, vp, i32, vp]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+def _check(st):
+    if st != FB_OK:
+        buf = C.create_string_buffer(1024)
+        lib.fb_last_error(buf, 1024)
+        raise FBError(st, buf.value.decode(errors="replace"))
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return C.c_void_p(0)
+
+
+def _is_cuda_tensor(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _ptr(a, dtype=None):
+    """(pointer, memspace, keepalive) for a numpy array or torch tensor."""
+    if _is_cuda_tensor(a):
+        if not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return C.c_void_p(a.data_ptr()), FB_MEM_DEVICE, a
+    if hasattr(a, "numpy"):
+        a = a.detach().cpu().numpy()
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return C.c_void_p(arr.ctypes.data), FB_MEM_HOST, arr
+
+
+def _same_space(*ms):
+    if len(set(ms)) != 1:
+        raise ValueError("all vector arguments must be host arrays or all device tensors")
+    return ms[0]
+
+
+def fb_version() -> str:
+    return lib.fb_version().decode()
+
+
+def fb_mesh_create(verts, tris, stream=None):
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    out = C.c_void_p()
+    _check(lib.fb_mesh_create(v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0], _stream(stream),
+                              C.byref(out)))
+    return out
+
+
+def fb_mesh_set_admittance(mesh, beta, stream=None):
+    p, ms, keep = _ptr(beta, np.complex128)
+    _check(lib.fb_mesh_set_admittance(mesh, p, ms, _stream(stream)))
+
+
+def fb_mesh_info(mesh):
+    n, rc, me = C.c_int64(), C.c_double(), C.c_double()
+    _check(lib.fb_mesh_info(mesh, C.byref(n), C.byref(rc), C.byref(me)))
+    return n.value, rc.value, me.value
+
+
+def fb_mesh_geometry(mesh):
+    n = fb_mesh_info(mesh)[0]
+    c = np.empty((n, 3))
+    nn = np.empty((n, 3))
+    _check(lib.fb_mesh_geometry(mesh, c.ctypes.data, nn.ctypes.data))
+    return c, nn
+
+
+def fb_mesh_destroy(mesh):
+    lib.fb_mesh_destroy(mesh)
+
+
+def fb_tree_build(mesh, leaf_max=64, stream=None):
+    out = C.c_void_p()
+    _check(lib.fb_tree_build(mesh, int(leaf_max), _stream(stream), C.byref(out)))
+    return out
+
+
+def fb_tree_info(tree):
+    L = C.c_int()
+    org = np.zeros(3)
+    side = C.c_double()
+    nb = np.zeros(16, np.int64)
+    _check(lib.fb_tree_info(tree, C.byref(L), org.ctypes.data, C.byref(side), nb.ctypes.data))
+    return L.value, org, side.value, nb[:L.value + 1].copy()
+
+
+def fb_tree_export(tree, which, level=0):
+    cnt = C.c_int64()
+    _check(lib.fb_tree_export(tree, which, level, None, C.byref(cnt)))
+    width = 2 if which in (3, 4) else 1
+    out = np.zeros(max(cnt.value * width, 1), np.int64)
+    _check(lib.fb_tree_export(tree, which, level, out.ctypes.data, C.byref(cnt)))
+    out = out[:cnt.value * width]
+    return out.reshape(-1, 2) if width == 2 else out
+
+
+def fb_tree_destroy(tree):
+    lib.fb_tree_destroy(tree)
+
+
+def fb_operator_create(mesh, tree, k, kind, precision, d0=6.0, pmin=12, stream=None):
+    out = C.c_void_p()
+    _check(lib.fb_operator_create(mesh, tree, float(k), int(kind), int(precision), float(d0), int(pmin),
+                                  _stream(stream), C.byref(out)))
+    return out
+
+
+def fb_operator_apply(op, x, y, stream=None):
+    px, mx, kx = _ptr(x, np.complex128)
+    if not _is_cuda_tensor(y) and not isinstance(y, np.ndarray):
+        raise ValueError("y must be a numpy array or a CUDA tensor")
+    py, my, ky = _ptr(y, np.complex128)
+    _check(lib.fb_operator_apply(op, px, py, _same_space(mx, my), _stream(stream)))
+    if my == FB_MEM_HOST and ky is not y:
+        y[...] = ky
+    return y
+
+
+def fb_operator_info(op):
+    n, L = C.c_int64(), C.c_int()
+    p = np.zeros(16, np.int32)
+    _check(lib.fb_operator_info(op, C.byref(n), C.byref(L), p.ctypes.data))
+    return n.value, L.value, p[:L.value + 1].copy()
+
+
+def fb_operator_export(op, which, level=0, index=0):
+    cnt = C.c_int64()
+    _check(lib.fb_operator_export(op, which, level, index, None, C.byref(cnt)))
+    out = np.zeros(max(cnt.value, 1), np.complex128)
+    _check(lib.fb_operator_export(op, which, level, index, out.ctypes.data, C.byref(cnt)))
+    return out[:cnt.value]
+
+
+def fb_operator_destroy(op):
+    lib.fb_operator_destroy(op)
+
+
+def fb_gamma_monopole(mesh, k, src, out, stream=None):
+    s = np.ascontiguousarray(src, dtype=np.float64)
+    po, mo, ko = _ptr(out, np.complex128)
+    _check(lib.fb_gamma_monopole(mesh, float(k), s.ctypes.data, po, mo, _stream(stream)))
+    if mo == FB_MEM_HOST and ko is not out:
+        out[...] = ko
+    return out
+
+
+def fb_precond_create(op, kind=FB_PC_BLOCK_JACOBI, stream=None):
+    out = C.c_void_p()
+    _check(lib.fb_precond_create(op, int(kind), _stream(stream), C.byref(out)))
+    return out if out.value else None
+
+
+def fb_precond_destroy(pc):
+    lib.fb_precond_destroy(pc)
+
+
+def fb_fgmres_solve(A, b, x, pc=None, tol=1e-8, restart=40, maxit=2000, max_refine=3, inner_tol=0.0,
+                    true_op=None, stream=None, raise_on_noconv=False):
+    pb, mb, kb = _ptr(b, np.complex128)
+    if not _is_cuda_tensor(x) and not isinstance(x, np.ndarray):
+        raise ValueError("x must be a numpy array or a CUDA tensor")
+    px, mx, kx = _ptr(x, np.complex128)
+    opts = SolverOpts(float(tol), int(restart), int(maxit), int(max_refine), float(inner_tol),
+                      true_op.value if true_op is not None else None)
+    info = SolveInfo()
+    st = lib.fb_fgmres_solve(A, pc, pb, px, C.byref(opts), C.byref(info), _same_space(mb, mx),
+                             _stream(stream))
+    if st not in (FB_OK, 3, 5) or (raise_on_noconv and st != FB_OK):
+        _check(st)
+    if mx == FB_MEM_HOST and kx is not x:
+        x[...] = kx
+    return info.as_dict()
+
+
+def fb_eval_field(mesh, k, psi_sc, gamma, rcv, out, src=None, stream=None):
+    pp, m1, k1 = _ptr(psi_sc, np.complex128)
+    pg, m2, k2 = _ptr(gamma, np.complex128)
+    pr, m3, k3 = _ptr(rcv, np.float64)
+    po, m4, k4 = _ptr(out, np.complex128)
+    s = None if src is None else np.ascontiguousarray(src, dtype=np.float64)
+    nr = (rcv.shape[0])
+    _check(lib.fb_eval_field(mesh, float(k), pp, pg, None if s is None else s.ctypes.data, pr, nr, po,
+                             _same_space(m1, m2, m3, m4), _stream(stream)))
+    if m4 == FB_MEM_HOST and k4 is not out:
+        out[...] = k4
+    return out
+
+
+lib.fb_operator_apply_timed.restype = C.c_int
+lib.fb_operator_apply_timed.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+lib.fb_kernel_launches.restype = C.c_longlong
+lib.fb_kernel_launches.argtypes = []
+PHASES = ("p2m", "m2m", "m2l", "l2l", "near_l2p", "total")
+
+
+def fb_operator_apply_timed(op, x, y, stream=None):
+    """y = Op x on CUDA tensors; returns per-phase CUDA-event times (ms)."""
+    if not (_is_cuda_tensor(x) and _is_cuda_tensor(y)):
+        raise ValueError("fb_operator_apply_timed needs CUDA tensors")
+    ms = np.zeros(6)
+    _check(lib.fb_operator_apply_timed(op, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                       _stream(stream), ms.ctypes.data))
+    return dict(zip(PHASES, ms.tolist()))
+
+
+def fb_kernel_launches() -> int:
+    return int(lib.fb_kernel_launches())

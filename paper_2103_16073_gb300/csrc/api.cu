@@ -1,0 +1,358 @@
+// C ABI entry points (include/fmmbem.h): argument checks, host/device
+// memory-space handling and dispatch to the CUDA implementation.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "common.cuh"
+
+// implemented in the other translation units
+fb_status fb_mesh_create_impl(const double*, int64_t, const int32_t*, int64_t, cudaStream_t, fb_mesh**);
+void fb_mesh_free(fb_mesh*);
+fb_status fb_gamma_impl(const fb_mesh*, double, const double*, cd*, cudaStream_t);
+fb_status fb_eval_impl(const fb_mesh*, double, const cd*, const cd*, const double*, const double*, int64_t,
+                       cd*, cudaStream_t);
+fb_status fb_tree_build_impl(const fb_mesh*, int, cudaStream_t, fb_tree**);
+void fb_tree_free(fb_tree*);
+fb_status fb_tree_export_impl(const fb_tree*, int, int, int64_t*, int64_t*);
+fb_status fb_fgmres_impl(fb_op*, fb_precond*, const cd*, cd*, const fb_solver_opts*, fb_solve_info*, cudaStream_t);
+fb_status fb_precond_create_impl(fb_op*, int, cudaStream_t, fb_precond**);
+void fb_precond_free(fb_precond*);
+
+static std::atomic<long long> g_launches{0};
+void fb_count_launch(long long n) { g_launches += n; }
+
+static thread_local fb_status g_last_code = FB_OK;
+static thread_local char g_last_msg[1024] = "";
+
+void fb_set_error(fb_status code, const std::string& msg) {
+    g_last_code = code;
+    snprintf(g_last_msg, sizeof(g_last_msg), "%s", msg.c_str());
+}
+fb_status fb_fail(fb_status code, const std::string& msg) {
+    fb_set_error(code, msg);
+    return code;
+}
+
+static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
+
+// Temporary device copy of a caller array for host memspace.
+struct Staged {
+    void* d = nullptr;
+    ~Staged() { if (d) cudaFree(d); }
+};
+static fb_status stage_in(const void* src, size_t bytes, int memspace, Staged& st, const void** dev,
+                          cudaStream_t s) {
+    if (memspace == FB_MEM_DEVICE) {
+        *dev = src;
+        return FB_OK;
+    }
+    if (memspace != FB_MEM_HOST) return fb_fail(FB_ERR_ARG, "memspace must be FB_MEM_HOST or FB_MEM_DEVICE");
+    FB_CUDA(cudaMalloc(&st.d, bytes ? bytes : 1));
+    FB_CUDA(cudaMemcpyAsync(st.d, src, bytes, cudaMemcpyHostToDevice, s));
+    *dev = st.d;
+    return FB_OK;
+}
+static fb_status stage_out_alloc(size_t bytes, int memspace, void* user, Staged& st, void** dev) {
+    if (memspace == FB_MEM_DEVICE) {
+        *dev = user;
+        return FB_OK;
+    }
+    if (memspace != FB_MEM_HOST) return fb_fail(FB_ERR_ARG, "memspace must be FB_MEM_HOST or FB_MEM_DEVICE");
+    FB_CUDA(cudaMalloc(&st.d, bytes ? bytes : 1));
+    *dev = st.d;
+    return FB_OK;
+}
+static fb_status stage_out_finish(size_t bytes, int memspace, void* user, const Staged& st, cudaStream_t s) {
+    if (memspace == FB_MEM_HOST) {
+        FB_CUDA(cudaMemcpyAsync(user, st.d, bytes, cudaMemcpyDeviceToHost, s));
+        FB_CUDA(cudaStreamSynchronize(s));
+    }
+    return FB_OK;
+}
+
+fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s) {
+    if (op->prec == FB_PREC_FP64_DENSE) return fb_dense_apply(op, x, y, s);
+    return fb_fmm_apply(op, x, y, s);
+}
+
+extern "C" {
+
+const char* fb_version(void) { return "fmmbem 0.1 (sm_103a)"; }
+
+fb_status fb_last_error(char* buf, size_t len) {
+    if (buf && len) snprintf(buf, len, "%s", g_last_msg);
+    return g_last_code;
+}
+
+fb_status fb_mesh_create(const double* verts, int64_t nv, const int32_t* tris, int64_t nt, void* stream,
+                         fb_mesh** out) {
+    return fb_mesh_create_impl(verts, nv, tris, nt, as_stream(stream), out);
+}
+
+fb_status fb_mesh_set_admittance(fb_mesh* m, const double* beta, int memspace, void* stream) {
+    if (!m || !beta) return fb_fail(FB_ERR_ARG, "NULL argument");
+    cudaStream_t s = as_stream(stream);
+    size_t bytes = sizeof(cd) * m->n;
+    if (memspace == FB_MEM_DEVICE) {
+        FB_CUDA(cudaMemcpyAsync(m->beta, beta, bytes, cudaMemcpyDeviceToDevice, s));
+    } else if (memspace == FB_MEM_HOST) {
+        FB_CUDA(cudaMemcpyAsync(m->beta, beta, bytes, cudaMemcpyHostToDevice, s));
+        FB_CUDA(cudaStreamSynchronize(s));
+    } else {
+        return fb_fail(FB_ERR_ARG, "bad memspace");
+    }
+    return FB_OK;
+}
+
+fb_status fb_mesh_info(const fb_mesh* m, int64_t* nt, double* rc, double* max_edge) {
+    if (!m) return fb_fail(FB_ERR_ARG, "NULL mesh");
+    if (nt) *nt = m->n;
+    if (rc) *rc = m->rc;
+    if (max_edge) *max_edge = m->max_edge;
+    return FB_OK;
+}
+
+fb_status fb_mesh_geometry(const fb_mesh* m, double* centroids, double* normals) {
+    if (!m) return fb_fail(FB_ERR_ARG, "NULL mesh");
+    int64_t n = m->n;
+    std::string tmp;
+    for (int which = 0; which < 2; ++which) {
+        double* out = which == 0 ? centroids : normals;
+        if (!out) continue;
+        const double* src = m->buf + (which == 0 ? 0 : 3 * n);
+        std::vector<double> h(3 * n);
+        FB_CUDA(cudaMemcpy(h.data(), src, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) out[3 * i + d] = h[d * n + i];
+    }
+    return FB_OK;
+}
+
+void fb_mesh_destroy(fb_mesh* m) { fb_mesh_free(m); }
+
+fb_status fb_tree_build(const fb_mesh* mesh, int leaf_max, void* stream, fb_tree** out) {
+    return fb_tree_build_impl(mesh, leaf_max, as_stream(stream), out);
+}
+
+fb_status fb_tree_info(const fb_tree* t, int* leaf_level, double* origin, double* side, int64_t* nboxes) {
+    if (!t) return fb_fail(FB_ERR_ARG, "NULL tree");
+    if (leaf_level) *leaf_level = t->L;
+    if (origin) for (int d = 0; d < 3; ++d) origin[d] = t->origin[d];
+    if (side) *side = t->side;
+    if (nboxes) for (int l = 0; l <= t->L; ++l) nboxes[l] = t->nbox[l];
+    return FB_OK;
+}
+
+fb_status fb_tree_export(const fb_tree* t, int which, int level, int64_t* out, int64_t* count) {
+    return fb_tree_export_impl(t, which, level, out, count);
+}
+
+void fb_tree_destroy(fb_tree* t) { fb_tree_free(t); }
+
+fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k, int kind, int precision,
+                             double d0, int pmin, void* stream, fb_op** out) {
+    if (!mesh || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (!(k > 0.0)) return fb_fail(FB_ERR_ARG, "k must be > 0");
+    if (kind < FB_OP_L || kind > FB_OP_A) return fb_fail(FB_ERR_ARG, "unknown operator kind");
+    if (precision < FB_PREC_FP64_DENSE || precision > FB_PREC_MIXED_FMM)
+        return fb_fail(FB_ERR_ARG, "unknown precision");
+    if (precision != FB_PREC_FP64_DENSE) {
+        if (!tree) return fb_fail(FB_ERR_ARG, "FMM precision needs a tree");
+        if (tree->mesh != mesh) return fb_fail(FB_ERR_ARG, "tree was built from another mesh");
+        if (!(d0 > 0.0) || pmin < 1) return fb_fail(FB_ERR_ARG, "need d0 > 0 and pmin >= 1");
+    }
+    cudaStream_t s = as_stream(stream);
+    fb_op* op = new fb_op();
+    op->mesh = mesh;
+    op->tree = tree;
+    op->dev = mesh->dev;
+    op->kind = kind;
+    op->prec = precision;
+    op->k = k;
+    op->n = mesh->n;
+    fb_status st = precision == FB_PREC_FP64_DENSE ? fb_dense_create(op, s) : fb_fmm_create(op, d0, pmin, s);
+    if (st == FB_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fb_fail(FB_ERR_CUDA, std::string("operator setup: ") + cudaGetErrorString(e));
+    }
+    if (st != FB_OK) {
+        fb_operator_destroy(op);
+        return st;
+    }
+    *out = op;
+    return FB_OK;
+}
+
+fb_status fb_operator_apply(fb_op* op, const double* x, double* y, int memspace, void* stream) {
+    if (!op || !x || !y) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (x == y) return fb_fail(FB_ERR_ARG, "x and y must not overlap");
+    cudaStream_t s = as_stream(stream);
+    size_t bytes = sizeof(cd) * op->n;
+    Staged sx, sy;
+    const void* dx = nullptr;
+    void* dy = nullptr;
+    FB_CHECK(stage_in(x, bytes, memspace, sx, &dx, s));
+    FB_CHECK(stage_out_alloc(bytes, memspace, y, sy, &dy));
+    FB_CHECK(fb_apply_any(op, (const cd*)dx, (cd*)dy, s));
+    return stage_out_finish(bytes, memspace, y, sy, s);
+}
+
+long long fb_kernel_launches(void) { return g_launches.load(); }
+
+fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* stream, double* phase_ms) {
+    if (!op || !x || !y || !phase_ms) return fb_fail(FB_ERR_ARG, "NULL argument");
+    cudaStream_t s = as_stream(stream);
+    for (int i = 0; i < FB_NPHASE; ++i) phase_ms[i] = 0.0;
+    if (op->prec == FB_PREC_FP64_DENSE) {
+        cudaEvent_t a, b;
+        FB_CUDA(cudaEventCreate(&a));
+        FB_CUDA(cudaEventCreate(&b));
+        cudaEventRecord(a, s);
+        fb_status st = fb_dense_apply(op, (const cd*)x, (cd*)y, s);
+        cudaEventRecord(b, s);
+        cudaEventSynchronize(b);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, a, b);
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        phase_ms[FB_NPHASE - 1] = ms;
+        return st;
+    }
+    PhaseTimer pt;
+    for (int i = 0; i <= FB_NPHASE; ++i) FB_CUDA(cudaEventCreate(&pt.ev[i]));
+    fb_status st = fb_fmm_apply(op, (const cd*)x, (cd*)y, s, &pt);
+    if (st == FB_OK) {
+        FB_CUDA(cudaEventSynchronize(pt.ev[FB_NPHASE - 1]));
+        for (int i = 0; i < FB_NPHASE - 1; ++i) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, pt.ev[i], pt.ev[i + 1]);
+            phase_ms[i] = ms;
+        }
+        float tot = 0;
+        cudaEventElapsedTime(&tot, pt.ev[0], pt.ev[FB_NPHASE - 1]);
+        phase_ms[FB_NPHASE - 1] = tot;
+    }
+    for (int i = 0; i <= FB_NPHASE; ++i) cudaEventDestroy(pt.ev[i]);
+    return st;
+}
+
+fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p) {
+    if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
+    if (n) *n = op->n;
+    if (leaf_level) *leaf_level = op->L;
+    if (p) for (int l = 0; l <= op->L; ++l) p[l] = op->p[l];
+    return FB_OK;
+}
+
+fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t index, double* out, int64_t* count) {
+    if (!op || !count) return fb_fail(FB_ERR_ARG, "NULL argument");
+    const cd* src = nullptr;
+    int64_t cnt = 0;
+    if (which == 6) {
+        if (!op->dense) return fb_fail(FB_ERR_ARG, "not a dense operator");
+        if (index < 0 || index >= op->n) return fb_fail(FB_ERR_ARG, "row out of range");
+        src = op->dense + index * op->n;
+        cnt = op->n;
+    } else {
+        if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "not an FMM operator");
+        const fb_tree* t = op->tree;
+        int L = op->L;
+        int nleaf = t->nbox[L];
+        int PL = op->p[L] * op->p[L];
+        if (which >= 0 && which <= 2) {
+            if (index < 0 || index >= nleaf) return fb_fail(FB_ERR_ARG, "leaf out of range");
+            int r0 = t->h_leaf_start[index], nr = t->h_leaf_start[index + 1] - r0;
+            if (which == 0) {
+                src = op->nf64 + op->h_nf_off[index];
+                cnt = (int64_t)nr * op->h_nf_ncol[index];
+            } else {
+                src = (which == 1 ? op->w64 : op->v64) + (int64_t)r0 * PL;
+                cnt = (int64_t)nr * PL;
+            }
+        } else if (which == 3) {
+            if (level < 2 || level > L || index < 0 || index >= FB_NOFF) return fb_fail(FB_ERR_ARG, "bad level/offset");
+            int64_t off = op->m2l_toff[(size_t)level * FB_NOFF + index];
+            if (off < 0) return fb_fail(FB_ERR_ARG, "offset not used at this level");
+            src = op->T64 + off;
+            cnt = (int64_t)op->p[level] * op->p[level] * op->p[level] * op->p[level];
+        } else if (which == 4 || which == 5) {
+            if (level < 3 || level > L || index < 0 || index > 7) return fb_fail(FB_ERR_ARG, "bad level/octant");
+            int64_t off = which == 4 ? op->m2m_toff[level][index] : op->l2l_toff[level][index];
+            if (off < 0) return fb_fail(FB_ERR_ARG, "octant not used at this level");
+            src = op->T64 + off;
+            cnt = (int64_t)op->p[level] * op->p[level] * op->p[level - 1] * op->p[level - 1];
+        } else {
+            return fb_fail(FB_ERR_ARG, "unknown export");
+        }
+    }
+    *count = cnt;
+    if (out) FB_CUDA(cudaMemcpy(out, src, sizeof(cd) * cnt, cudaMemcpyDeviceToHost));
+    return FB_OK;
+}
+
+void fb_operator_destroy(fb_op* op) {
+    if (!op) return;
+    dfree(op->dense);
+    fb_fmm_destroy(op);
+    dfree(op->io_x);
+    dfree(op->io_y);
+    delete op;
+}
+
+fb_status fb_gamma_monopole(const fb_mesh* m, double k, const double* src, double* gamma, int memspace,
+                            void* stream) {
+    if (!m || !src || !gamma) return fb_fail(FB_ERR_ARG, "NULL argument");
+    cudaStream_t s = as_stream(stream);
+    size_t bytes = sizeof(cd) * m->n;
+    Staged so;
+    void* dg = nullptr;
+    FB_CHECK(stage_out_alloc(bytes, memspace, gamma, so, &dg));
+    FB_CHECK(fb_gamma_impl(m, k, src, (cd*)dg, s));
+    return stage_out_finish(bytes, memspace, gamma, so, s);
+}
+
+fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out) {
+    if (!op || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    return fb_precond_create_impl(op, kind, as_stream(stream), out);
+}
+
+void fb_precond_destroy(fb_precond* pc) { fb_precond_free(pc); }
+
+fb_status fb_fgmres_solve(fb_op* A, fb_precond* pc, const double* b, double* x, const fb_solver_opts* opts,
+                          fb_solve_info* info, int memspace, void* stream) {
+    if (!A || !b || !x || !opts) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (pc && pc->op != A) return fb_fail(FB_ERR_ARG, "preconditioner built for another operator");
+    cudaStream_t s = as_stream(stream);
+    size_t bytes = sizeof(cd) * A->n;
+    Staged sb, sx;
+    const void* db = nullptr;
+    void* dx = nullptr;
+    FB_CHECK(stage_in(b, bytes, memspace, sb, &db, s));
+    FB_CHECK(stage_out_alloc(bytes, memspace, x, sx, &dx));
+    fb_status st = fb_fgmres_impl(A, pc, (const cd*)db, (cd*)dx, opts, info, s);
+    if (st != FB_OK && st != FB_ERR_NOCONV && st != FB_ERR_NAN) return st;
+    fb_status st2 = stage_out_finish(bytes, memspace, x, sx, s);
+    return st != FB_OK ? st : st2;
+}
+
+fb_status fb_eval_field(const fb_mesh* m, double k, const double* psi_sc, const double* gamma, const double* src,
+                        const double* rcv, int64_t nr, double* out, int memspace, void* stream) {
+    if (!m || !psi_sc || !gamma || !rcv || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (nr < 0) return fb_fail(FB_ERR_ARG, "nr < 0");
+    cudaStream_t s = as_stream(stream);
+    size_t nb = sizeof(cd) * m->n;
+    Staged a, b, c, d;
+    const void *dp = nullptr, *dg = nullptr, *dr = nullptr;
+    void* dout = nullptr;
+    FB_CHECK(stage_in(psi_sc, nb, memspace, a, &dp, s));
+    FB_CHECK(stage_in(gamma, nb, memspace, b, &dg, s));
+    FB_CHECK(stage_in(rcv, sizeof(double) * 3 * nr, memspace, c, &dr, s));
+    FB_CHECK(stage_out_alloc(sizeof(cd) * nr, memspace, out, d, &dout));
+    FB_CHECK(fb_eval_impl(m, k, (const cd*)dp, (const cd*)dg, src, (const double*)dr, nr, (cd*)dout, s));
+    return stage_out_finish(sizeof(cd) * nr, memspace, out, d, s);
+}
+
+}  // extern "C"

@@ -1,0 +1,243 @@
+// Internal definitions shared by the CUDA translation units of the library:
+// complex arithmetic, error handling, device-memory helpers and the handle
+// structures behind the opaque types of include/fmmbem.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fmmbem.h"
+
+// ------------------------------------------------------------- complex ----
+template <class R>
+struct __align__(2 * sizeof(R)) cx {
+    R re, im;
+};
+using cd = cx<double>;
+using cf = cx<float>;
+
+template <class R>
+__host__ __device__ __forceinline__ cx<R> mk(R a, R b) { cx<R> z; z.re = a; z.im = b; return z; }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return mk(a.re + b.re, a.im + b.im); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return mk(a.re - b.re, a.im - b.im); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+    return mk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class R>
+__host__ __device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return mk(s * a.re, s * a.im); }
+template <class R>
+__host__ __device__ __forceinline__ cx<R> conjg(cx<R> a) { return mk(a.re, -a.im); }
+template <class R>
+__host__ __device__ __forceinline__ R abs2(cx<R> a) { return a.re * a.re + a.im * a.im; }
+// a += b * c
+template <class R>
+__host__ __device__ __forceinline__ void cmac(cx<R>& a, cx<R> b, cx<R> c) {
+    a.re += b.re * c.re - b.im * c.im;
+    a.im += b.re * c.im + b.im * c.re;
+}
+// a += conj(b) * c
+template <class R>
+__host__ __device__ __forceinline__ void cmacc(cx<R>& a, cx<R> b, cx<R> c) {
+    a.re += b.re * c.re + b.im * c.im;
+    a.im += b.re * c.im - b.im * c.re;
+}
+__host__ __device__ __forceinline__ cf to_f(cd a) { return mk<float>((float)a.re, (float)a.im); }
+__host__ __device__ __forceinline__ cd to_d(cf a) { return mk<double>((double)a.re, (double)a.im); }
+template <class R> __host__ __device__ __forceinline__ cx<R> from_d(cd a);
+template <> __host__ __device__ __forceinline__ cd from_d<double>(cd a) { return a; }
+template <> __host__ __device__ __forceinline__ cf from_d<float>(cd a) { return to_f(a); }
+
+// --------------------------------------------------------- error state ----
+void fb_set_error(fb_status code, const std::string& msg);
+fb_status fb_fail(fb_status code, const std::string& msg);
+
+#define FB_CUDA(call)                                                               \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess) {                                                    \
+            return fb_fail(e_ == cudaErrorMemoryAllocation ? FB_ERR_OOM : FB_ERR_CUDA, \
+                           std::string(#call " failed: ") + cudaGetErrorString(e_));  \
+        }                                                                           \
+    } while (0)
+
+#define FB_CHECK(st)                   \
+    do {                               \
+        fb_status s_ = (st);           \
+        if (s_ != FB_OK) return s_;    \
+    } while (0)
+
+#define FB_LAUNCH_CHECK() FB_CUDA(cudaGetLastError())
+
+inline int div_up(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// A device allocation released by its owner's destroy function.
+template <class T>
+fb_status dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return FB_OK;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fb_fail(FB_ERR_OOM, std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) +
+                                       " bytes failed: " + cudaGetErrorString(e));
+    }
+    return FB_OK;
+}
+template <class T>
+void dfree(T*& p) {
+    if (p) cudaFree((void*)p);
+    p = nullptr;
+}
+
+// --------------------------------------------------------------- mesh ----
+// Element geometry, structure of arrays in FP64 on the device.
+struct Geom {
+    int64_t n;
+    const double *cx, *cy, *cz;     // centroids (collocation points)
+    const double *nx, *ny, *nz;     // unit normals (outward)
+    const double* area;
+    const double *ax, *ay, *az;     // vertex 0
+    const double *bx, *by, *bz;     // vertex 1
+    const double *qx, *qy, *qz;     // vertex 2
+    const double *gx, *gy, *gz;     // 3-point Gauss points: point q of element i at 3i+q
+    const cd* beta;                 // admittance
+};
+
+struct fb_mesh {
+    int dev = 0;
+    int64_t n = 0;
+    double* buf = nullptr;          // 16 n doubles + 9 n Gauss coordinates
+    cd* beta = nullptr;
+    double rc = 0, max_edge = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // bounding box of the vertices
+    Geom g{};
+};
+
+// --------------------------------------------------------------- tree ----
+constexpr int FB_MAXLEV = 12;
+constexpr int FB_NOFF = 343;   // M2L offsets (dx,dy,dz) in [-3,3]^3 -> (dx+3)*49+(dy+3)*7+(dz+3)
+constexpr int FB_ULIST = 27;
+constexpr int FB_VLIST = 189;
+
+struct fb_tree {
+    const fb_mesh* mesh = nullptr;
+    int dev = 0;
+    int L = 0;
+    double origin[3] = {0, 0, 0}, side = 0;
+    int64_t n = 0;
+    int32_t* perm = nullptr;                 // sorted position -> element
+    int32_t* elem_pos = nullptr;             // element -> sorted position
+    int32_t nbox[FB_MAXLEV + 1] = {0};
+    uint32_t* keys[FB_MAXLEV + 1] = {nullptr};   // Morton keys of non-empty boxes, ascending
+    int32_t* parent[FB_MAXLEV + 1] = {nullptr};  // parent box index (level l-1)
+    int32_t* leaf_start = nullptr;           // nleaf + 1
+    std::vector<int32_t> h_leaf_start;       // host copy
+    int32_t* ucnt = nullptr;                 // per leaf
+    int32_t* ulist = nullptr;                // per leaf x 27, ascending
+    int32_t* vcnt[FB_MAXLEV + 1] = {nullptr};
+    int32_t* vlist[FB_MAXLEV + 1] = {nullptr};   // per box x 189, ascending
+    // M2L pairs grouped by (level, offset code): src box, dst box
+    int32_t* m2l_src = nullptr;
+    int32_t* m2l_dst = nullptr;
+    std::vector<int64_t> m2l_group;          // (L+1)*343 + 1 prefix offsets
+    // M2M / L2L pairs per level l (child level), grouped by octant: child, parent
+    int32_t* oct_child[FB_MAXLEV + 1] = {nullptr};
+    int32_t* oct_parent[FB_MAXLEV + 1] = {nullptr};
+    std::vector<int64_t> oct_group[FB_MAXLEV + 1];   // 9 prefix offsets
+    int64_t nlist_u = 0;
+};
+
+// ----------------------------------------------------------- operator ----
+// One translation task: dst[dst_idx[c]] += T * src[src_idx[c]] for a group
+// of column pairs sharing the matrix T (rows x cols, row-major).
+struct TransTask {
+    int64_t t_off;       // offset of T in the matrix buffer (complex entries)
+    int64_t pair_off;    // first pair in the pair arrays
+    int32_t npairs;
+    int32_t rows, cols;
+    int64_t src_base, dst_base;   // offsets (complex entries) of the level arrays
+};
+struct TransTile {
+    int32_t task, row0, col0, pad;
+};
+
+struct TransPlan {
+    std::vector<TransTask> h_tasks;
+    std::vector<TransTile> h_tiles;
+    TransTask* tasks = nullptr;
+    TransTile* tiles = nullptr;
+    const int32_t* src_idx = nullptr;
+    const int32_t* dst_idx = nullptr;
+    int ntiles = 0;
+};
+
+struct fb_op {
+    const fb_mesh* mesh = nullptr;
+    const fb_tree* tree = nullptr;
+    int dev = 0;
+    int kind = 0, prec = 0;
+    double k = 0;
+    int64_t n = 0;
+    // dense
+    cd* dense = nullptr;
+    // FMM
+    int L = 0;
+    int p[FB_MAXLEV + 1] = {0};
+    int64_t lev_off[FB_MAXLEV + 2] = {0};    // offsets of each level in mp/loc (complex entries)
+    int64_t nf_count = 0;
+    int64_t* nf_off = nullptr;               // per leaf, entries offset
+    int32_t* nf_ncol = nullptr;              // per leaf, columns K_t
+    std::vector<int64_t> h_nf_off;
+    std::vector<int32_t> h_nf_ncol;
+    cd* nf64 = nullptr;
+    cf* nf32 = nullptr;
+    cd* w64 = nullptr; cf* w32 = nullptr;    // P2M, [N sorted][P_L]
+    cd* v64 = nullptr; cf* v32 = nullptr;    // L2P, [N sorted][P_L]
+    void* mp = nullptr;                      // multipoles (all levels)
+    void* loc = nullptr;                     // locals (all levels)
+    cd* T64 = nullptr; cf* T32 = nullptr;    // translation matrices
+    int64_t T_count = 0;
+    std::vector<int64_t> m2l_toff;           // (L+1)*343: offset of T or -1
+    int64_t m2m_toff[FB_MAXLEV + 1][8];      // child level l, octant
+    int64_t l2l_toff[FB_MAXLEV + 1][8];
+    TransPlan m2l, m2m[FB_MAXLEV + 1], l2l[FB_MAXLEV + 1];
+    // device vectors for host-memspace calls
+    cd* io_x = nullptr;
+    cd* io_y = nullptr;
+};
+
+struct fb_precond {
+    fb_op* op = nullptr;
+    int kind = 0;
+    int64_t n = 0;
+    int64_t* blk_off = nullptr;    // per leaf, offset of its inverse block
+    cd* inv64 = nullptr;
+    cf* inv32 = nullptr;
+};
+
+// ------------------------------------------------------ launch counting ----
+// Running total of kernel launches issued by the library (tracing aid,
+// reported by fb_kernel_launches()).
+void fb_count_launch(long long n = 1);
+
+// Per-phase CUDA-event timing of one FMM matvec (tracing aid).
+constexpr int FB_NPHASE = 6;   // P2M, M2M, M2L, L2L, near+L2P, total
+struct PhaseTimer {
+    cudaEvent_t ev[FB_NPHASE + 1];
+};
+
+// --------------------------------------------------- internal interface ----
+fb_status fb_dense_create(fb_op* op, cudaStream_t s);
+fb_status fb_dense_apply(const fb_op* op, const cd* x, cd* y, cudaStream_t s);
+fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s);
+fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt = nullptr);
+void fb_fmm_destroy(fb_op* op);
+fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s);
+fb_status fb_precond_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s);
+int fb_order_rule(double k, double delta, double d0, int pmin);

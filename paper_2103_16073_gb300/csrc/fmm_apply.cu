@@ -1,0 +1,235 @@
+// FMM matrix-vector product (Sec. 3.3): P2M -> M2M -> M2L -> L2L -> L2P,
+// plus the stored near field.  Templated on the arithmetic type R (double
+// for the plain FP64 path, float for the mixed path); input and output
+// vectors are complex128 in the caller's element order.
+//
+// Translations use the stacked form: all box pairs of one level that share a
+// translation vector share one p^2 x p^2 matrix, so each (level, offset)
+// group is one complex GEMM  Y = T X  with X gathered from the source boxes
+// and Y scatter-added into the target boxes.
+#include <algorithm>
+
+#include "common.cuh"
+
+// ------------------------------------------------------ gather-GEMM-scatter
+// Tile: 64 output rows x 32 column pairs, K chunks of 16; 256 threads, each
+// 4 rows x 2 columns.  dst[dst_idx] += T * src[src_idx] (atomic adds: the
+// groups of one launch may share targets).
+template <class R>
+__global__ void __launch_bounds__(256) k_trans(const TransTask* __restrict__ tasks,
+                                               const TransTile* __restrict__ tiles,
+                                               const cx<R>* __restrict__ Tbuf,
+                                               const int32_t* __restrict__ src_idx,
+                                               const int32_t* __restrict__ dst_idx,
+                                               const cx<R>* __restrict__ src, cx<R>* __restrict__ dst) {
+    constexpr int BM = 64, BN = 32, BK = 16;
+    __shared__ cx<R> Ts[BK][BM];
+    __shared__ cx<R> Xs[BK][BN];
+    __shared__ int s_src[BN];
+    __shared__ int s_dst[BN];
+    TransTile tl = tiles[blockIdx.x];
+    TransTask tk = tasks[tl.task];
+    int tid = threadIdx.x;
+    int ty = tid >> 4, tx = tid & 15;
+    if (tid < BN) {
+        int c = tl.col0 + tid;
+        s_src[tid] = c < tk.npairs ? src_idx[tk.pair_off + c] : -1;
+        s_dst[tid] = c < tk.npairs ? dst_idx[tk.pair_off + c] : -1;
+    }
+    __syncthreads();
+    const cx<R>* T = Tbuf + tk.t_off;
+    cx<R> acc[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) acc[i][j] = mk<R>(0, 0);
+    for (int k0 = 0; k0 < tk.cols; k0 += BK) {
+#pragma unroll
+        for (int it = 0; it < (BM * BK) / 256; ++it) {
+            int idx = tid + it * 256;
+            int r = idx / BK, kk = idx % BK;
+            int row = tl.row0 + r, k = k0 + kk;
+            Ts[kk][r] = (row < tk.rows && k < tk.cols) ? T[(int64_t)row * tk.cols + k] : mk<R>(0, 0);
+        }
+#pragma unroll
+        for (int it = 0; it < (BN * BK) / 256; ++it) {
+            int idx = tid + it * 256;
+            int c = idx / BK, kk = idx % BK;
+            int k = k0 + kk;
+            int sb = s_src[c];
+            Xs[kk][c] = (sb >= 0 && k < tk.cols) ? src[tk.src_base + (int64_t)sb * tk.cols + k] : mk<R>(0, 0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            cx<R> a[4], b[2];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = Ts[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 2; ++j) b[j] = Xs[kk][tx * 2 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 2; ++j) cmac(acc[i][j], a[i], b[j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        int c = tx * 2 + j;
+        int db = s_dst[c];
+        if (db < 0) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            int row = tl.row0 + ty * 4 + i;
+            if (row >= tk.rows) continue;
+            cx<R>* d = dst + tk.dst_base + (int64_t)db * tk.rows + row;
+            atomicAdd(&d->re, acc[i][j].re);
+            atomicAdd(&d->im, acc[i][j].im);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- P2M ----
+// mp[leaf][r] = sum_{pos in leaf} W[pos][r] x[perm[pos]]
+template <class R>
+__global__ void k_p2m(int P, const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ perm,
+                      const cx<R>* __restrict__ W, const cd* __restrict__ x, cx<R>* __restrict__ mp) {
+    int b = blockIdx.x;
+    int s0 = leaf_start[b], s1 = leaf_start[b + 1];
+    __shared__ cx<R> xs[256];
+    for (int r0 = 0; r0 < P; r0 += blockDim.x) {
+        int r = r0 + threadIdx.x;
+        cx<R> acc = mk<R>(0, 0);
+        for (int c0 = s0; c0 < s1; c0 += 256) {
+            int cn = min(256, s1 - c0);
+            __syncthreads();
+            for (int i = threadIdx.x; i < cn; i += blockDim.x) xs[i] = from_d<R>(x[perm[c0 + i]]);
+            __syncthreads();
+            if (r < P)
+                for (int i = 0; i < cn; ++i) cmac(acc, W[(int64_t)(c0 + i) * P + r], xs[i]);
+        }
+        if (r < P) mp[(int64_t)b * P + r] = acc;
+    }
+}
+
+// ----------------------------------------------------- near field + L2P ----
+// y[perm[pos]] = sum_c A_t[row][c] x[col c] + sum_r V[pos][r] loc[leaf][r]
+template <class R>
+__global__ void k_near_l2p(int P, const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ perm,
+                           const int32_t* __restrict__ ucnt, const int32_t* __restrict__ ulist,
+                           const int64_t* __restrict__ nf_off, const int32_t* __restrict__ nf_ncol,
+                           const cx<R>* __restrict__ A, const cx<R>* __restrict__ V,
+                           const cx<R>* __restrict__ loc, const cd* __restrict__ x, cd* __restrict__ y) {
+    extern __shared__ unsigned char smem_raw[];
+    cx<R>* xs = (cx<R>*)smem_raw;
+    int t = blockIdx.x;
+    int K = nf_ncol[t];
+    cx<R>* ls = xs + K;
+    // gather the x values of the U-list leaves in column order
+    int nu = ucnt[t];
+    int c = 0;
+    for (int i = 0; i < nu; ++i) {
+        int s = ulist[(int64_t)t * FB_ULIST + i];
+        int a0 = leaf_start[s], a1 = leaf_start[s + 1];
+        for (int q = threadIdx.x; q < a1 - a0; q += blockDim.x) xs[c + q] = from_d<R>(x[perm[a0 + q]]);
+        c += a1 - a0;
+    }
+    if (loc)
+        for (int q = threadIdx.x; q < P; q += blockDim.x) ls[q] = loc[(int64_t)t * P + q];
+    __syncthreads();
+    int r0 = leaf_start[t], nr = leaf_start[t + 1] - r0;
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const cx<R>* At = A + nf_off[t];
+    for (int r = warp; r < nr; r += nw) {
+        cx<R> acc = mk<R>(0, 0);
+        const cx<R>* row = At + (int64_t)r * K;
+        for (int q = lane; q < K; q += 32) cmac(acc, row[q], xs[q]);
+        if (loc) {
+            const cx<R>* vr = V + (int64_t)(r0 + r) * P;
+            for (int q = lane; q < P; q += 32) cmac(acc, vr[q], ls[q]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+            acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+        }
+        if (lane == 0) y[perm[r0 + r]] = mk<double>((double)acc.re, (double)acc.im);
+    }
+}
+
+template <class R>
+static fb_status run_plan(const TransPlan& pl, const cx<R>* T, const cx<R>* src, cx<R>* dst, cudaStream_t s) {
+    if (pl.ntiles == 0) return FB_OK;
+    k_trans<R><<<pl.ntiles, 256, 0, s>>>(pl.tasks, pl.tiles, T, pl.src_idx, pl.dst_idx, src, dst);
+    FB_LAUNCH_CHECK();
+    fb_count_launch();
+    return FB_OK;
+}
+
+template <class R>
+static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, const cx<R>* A,
+                             const cx<R>* W, const cx<R>* V, const cx<R>* T, PhaseTimer* pt) {
+    auto mark = [&](int i) { if (pt) cudaEventRecord(pt->ev[i], s); };
+    const fb_tree* t = op->tree;
+    int L = op->L;
+    int pL = op->p[L], PL = pL * pL;
+    cx<R>* mp = (cx<R>*)op->mp;
+    cx<R>* loc = (cx<R>*)op->loc;
+    int64_t cnt = op->lev_off[L + 1];
+    mark(0);
+    FB_CUDA(cudaMemsetAsync(mp, 0, sizeof(cx<R>) * cnt, s));
+    FB_CUDA(cudaMemsetAsync(loc, 0, sizeof(cx<R>) * cnt, s));
+    int nleaf = t->nbox[L];
+    k_p2m<R><<<nleaf, 128, 0, s>>>(PL, t->leaf_start, t->perm, W, x, mp + op->lev_off[L]);
+    FB_LAUNCH_CHECK();
+    fb_count_launch();
+    mark(1);
+    for (int l = L; l >= 3; --l) FB_CHECK(run_plan<R>(op->m2m[l], T, mp, mp, s));
+    mark(2);
+    FB_CHECK(run_plan<R>(op->m2l, T, mp, loc, s));
+    mark(3);
+    for (int l = 3; l <= L; ++l) FB_CHECK(run_plan<R>(op->l2l[l], T, loc, loc, s));
+    mark(4);
+    int maxK = 0;
+    for (int v : op->h_nf_ncol) maxK = std::max(maxK, v);
+    size_t smem = sizeof(cx<R>) * (maxK + PL);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_near_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_near_l2p<R><<<nleaf, 256, smem, s>>>(PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off,
+                                           op->nf_ncol, A, V, loc + op->lev_off[L], x, y);
+    FB_LAUNCH_CHECK();
+    fb_count_launch();
+    mark(5);
+    return FB_OK;
+}
+
+fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt) {
+    if (op->prec == FB_PREC_MIXED_FMM)
+        return fmm_apply_t<float>(op, x, y, s, op->nf32, op->w32, op->v32, op->T32, pt);
+    return fmm_apply_t<double>(op, x, y, s, op->nf64, op->w64, op->v64, op->T64, pt);
+}
+
+static void free_plan(TransPlan& p) {
+    dfree(p.tasks);
+    dfree(p.tiles);
+}
+
+void fb_fmm_destroy(fb_op* op) {
+    dfree(op->nf_off);
+    dfree(op->nf_ncol);
+    dfree(op->nf64);
+    dfree(op->nf32);
+    dfree(op->w64);
+    dfree(op->w32);
+    dfree(op->v64);
+    dfree(op->v32);
+    dfree(op->mp);
+    dfree(op->loc);
+    dfree(op->T64);
+    dfree(op->T32);
+    free_plan(op->m2l);
+    for (int l = 0; l <= FB_MAXLEV; ++l) {
+        free_plan(op->m2m[l]);
+        free_plan(op->l2l[l]);
+    }
+}

@@ -1,0 +1,543 @@
+// Flexible GMRES (Sec. 3.1, Sec. 4: the paper solves Eq. (dbem4) by flexible
+// GMRES, which admits a preconditioner that changes between iterations) and
+// the block-Jacobi preconditioner.  All Krylov vectors, the Hessenberg matrix
+// and the Givens rotations are FP64; the operator may compute in FP32.
+//
+// Arnoldi orthogonalisation: classical Gram-Schmidt applied twice (CGS2),
+// two fused kernels per pass instead of j sequential dot products.
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+// ---------------------------------------------------------- vector ops ----
+constexpr int KB = 256;
+
+__device__ __forceinline__ void block_reduce_add(double v, double* target) {
+    __shared__ double sh[32];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        v = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) atomicAdd(target, v);
+    }
+    __syncthreads();
+}
+
+// h[i] += sum_n conj(V_i[n]) w[n], i = blockIdx.y
+__global__ void k_mdot(const cd* __restrict__ V, int64_t n, const cd* __restrict__ w, cd* h) {
+    int i = blockIdx.y;
+    const cd* v = V + (int64_t)i * n;
+    cd acc = mk(0.0, 0.0);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        cmacc(acc, v[q], w[q]);
+    block_reduce_add(acc.re, &h[i].re);
+    block_reduce_add(acc.im, &h[i].im);
+}
+
+// w -= sum_{i<=j} V_i h[i]
+__global__ void k_gs_update(const cd* __restrict__ V, int64_t n, int j1, const cd* __restrict__ h, cd* w) {
+    __shared__ cd hs[1024];
+    for (int i = threadIdx.x; i < j1; i += blockDim.x) hs[i] = h[i];
+    __syncthreads();
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        cd a = w[q];
+        for (int i = 0; i < j1; ++i) {
+            cd v = V[(int64_t)i * n + q];
+            a.re -= v.re * hs[i].re - v.im * hs[i].im;
+            a.im -= v.re * hs[i].im + v.im * hs[i].re;
+        }
+        w[q] = a;
+    }
+}
+
+__global__ void k_norm2(const cd* __restrict__ w, int64_t n, double* out) {
+    double acc = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        acc += abs2(w[q]);
+    block_reduce_add(acc, out);
+}
+
+__global__ void k_scale(cd* __restrict__ out, const cd* __restrict__ in, int64_t n, const double* s) {
+    double f = *s;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = f * in[q];
+}
+
+// out = a - b
+__global__ void k_sub(cd* out, const cd* a, const cd* b, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = a[q] - b[q];
+}
+__global__ void k_add(cd* out, const cd* a, int64_t n) {
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[q] = out[q] + a[q];
+}
+
+// x += sum_i Z_i y[i]
+__global__ void k_update_x(cd* x, const cd* __restrict__ Z, int64_t n, int j1, const cd* __restrict__ y) {
+    __shared__ cd ys[1024];
+    for (int i = threadIdx.x; i < j1; i += blockDim.x) ys[i] = y[i];
+    __syncthreads();
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        cd a = x[q];
+        for (int i = 0; i < j1; ++i) cmac(a, Z[(int64_t)i * n + q], ys[i]);
+        x[q] = a;
+    }
+}
+
+// Small dense state of one restart cycle (device).
+struct Hess {
+    int m;
+    cd* H;      // (m+1) x m, column-major: H[j*(m+1) + i]
+    cd* cs;     // m (real part used)
+    cd* sn;     // m
+    cd* g;      // m+1
+    cd* h;      // m+1 scratch (CGS pass)
+    cd* y;      // m
+    double* nrm2;
+    double* inv;      // 1 / H[j+1][j]
+    double* est;      // |g[j+1]|
+};
+
+// Starts a cycle: g = (beta, 0, ...), inv = 1/beta (beta = sqrt(nrm2)).
+__global__ void k_cycle_start(Hess hs) {
+    double beta = sqrt(*hs.nrm2);
+    for (int i = 0; i <= hs.m; ++i) hs.g[i] = mk(0.0, 0.0);
+    for (int i = 0; i < (hs.m + 1) * hs.m; ++i) hs.H[i] = mk(0.0, 0.0);
+    hs.g[0] = mk(beta, 0.0);
+    *hs.inv = beta > 0.0 ? 1.0 / beta : 0.0;
+    *hs.est = beta;
+}
+
+// Adds the CGS pass coefficients into column j.
+__global__ void k_accum_h(Hess hs, int j) {
+    int i = threadIdx.x;
+    if (i <= j) hs.H[j * (hs.m + 1) + i] = hs.H[j * (hs.m + 1) + i] + hs.h[i];
+}
+
+// Completes column j: H[j+1][j] = ||w||, previous rotations, new rotation,
+// residual estimate |g[j+1]|, inv = 1/H[j+1][j].
+__global__ void k_arnoldi_close(Hess hs, int j) {
+    int ld = hs.m + 1;
+    cd* col = hs.H + j * ld;
+    double hn = sqrt(*hs.nrm2);
+    col[j + 1] = mk(hn, 0.0);
+    *hs.inv = hn > 0.0 ? 1.0 / hn : 0.0;
+    for (int i = 0; i < j; ++i) {
+        cd c = hs.cs[i], s = hs.sn[i];
+        cd a = col[i], b = col[i + 1];
+        col[i] = c * a + s * b;
+        col[i + 1] = conjg(s) * mk(-a.re, -a.im) + conjg(c) * b;
+    }
+    cd a = col[j], b = col[j + 1];
+    double na = sqrt(abs2(a)), nb = sqrt(abs2(b));
+    double den = sqrt(na * na + nb * nb);
+    cd c, s;
+    if (den == 0.0) { c = mk(1.0, 0.0); s = mk(0.0, 0.0); }
+    else if (na == 0.0) { c = mk(0.0, 0.0); s = mk(1.0, 0.0); }
+    else {
+        c = mk(na / den, 0.0);
+        s = (1.0 / (na * den)) * (a * conjg(b));
+    }
+    hs.cs[j] = c;
+    hs.sn[j] = s;
+    col[j] = c * a + s * b;
+    col[j + 1] = mk(0.0, 0.0);
+    cd gj = hs.g[j];
+    hs.g[j + 1] = conjg(s) * mk(-gj.re, -gj.im);
+    hs.g[j] = c * gj;
+    *hs.est = sqrt(abs2(hs.g[j + 1]));
+}
+
+// Back substitution H y = g for the first j1 columns.
+__global__ void k_backsolve(Hess hs, int j1) {
+    int ld = hs.m + 1;
+    for (int i = j1 - 1; i >= 0; --i) {
+        cd acc = hs.g[i];
+        for (int q = i + 1; q < j1; ++q) acc = acc - hs.H[q * ld + i] * hs.y[q];
+        cd d = hs.H[i * ld + i];
+        double dd = abs2(d);
+        hs.y[i] = (1.0 / dd) * (acc * conjg(d));
+    }
+}
+
+static inline void cnt(long long n = 1) { fb_count_launch(n); }
+
+static int grid_for(int64_t n) { return (int)std::min<int64_t>(div_up(n, KB), 152 * 8); }
+
+static fb_status norm2(const cd* v, int64_t n, double* d_out, cudaStream_t s) {
+    FB_CUDA(cudaMemsetAsync(d_out, 0, sizeof(double), s));
+    k_norm2<<<grid_for(n), KB, 0, s>>>(v, n, d_out);
+    FB_LAUNCH_CHECK();
+    cnt();
+    return FB_OK;
+}
+
+static fb_status read_scalar(const double* d, double* h, cudaStream_t s) {
+    FB_CUDA(cudaMemcpyAsync(h, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FB_CUDA(cudaStreamSynchronize(s));
+    return FB_OK;
+}
+
+struct Work {
+    int64_t n = 0;
+    int m = 0;
+    cd *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *d = nullptr, *tmp = nullptr;
+    cd* small = nullptr;
+    double* scal = nullptr;
+    double* host = nullptr;   // pinned scalar
+    Hess hs{};
+    ~Work() {
+        dfree(V); dfree(Z); dfree(w); dfree(r); dfree(d); dfree(tmp); dfree(small); dfree(scal);
+        if (host) cudaFreeHost(host);
+    }
+};
+
+// Inner restarted FGMRES on A d = rhs from d = 0 until the Arnoldi estimate
+// reaches rel_tol * ||rhs|| or the iteration budget is spent.
+static fb_status fgmres_inner(fb_op* A, fb_precond* pc, Work& W, const cd* rhs, double rhs_norm,
+                              double rel_tol, int budget, int* iters, double* est_rel, int* status,
+                              cudaStream_t s) {
+    int64_t n = W.n;
+    int m = W.m;
+    FB_CUDA(cudaMemsetAsync(W.d, 0, sizeof(cd) * n, s));
+    *status = FB_OK;
+    int it = 0;
+    bool first = true;
+    double est = rhs_norm;
+    while (true) {
+        // r_c = rhs - A d
+        if (first) {
+            FB_CUDA(cudaMemcpyAsync(W.w, rhs, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s));
+        } else {
+            FB_CHECK(fb_apply_any(A, W.d, W.tmp, s));
+            k_sub<<<grid_for(n), KB, 0, s>>>(W.w, rhs, W.tmp, n);
+            cnt();
+        }
+        first = false;
+        FB_CHECK(norm2(W.w, n, W.hs.nrm2, s));
+        k_cycle_start<<<1, 1, 0, s>>>(W.hs);
+        k_scale<<<grid_for(n), KB, 0, s>>>(W.V, W.w, n, W.hs.inv);
+        FB_LAUNCH_CHECK();
+        cnt(2);
+        FB_CHECK(read_scalar(W.hs.est, W.host, s));
+        est = *W.host;
+        if (!std::isfinite(est)) { *status = FB_ERR_NAN; break; }
+        if (est <= rel_tol * rhs_norm || it >= budget) break;
+        int j = 0;
+        bool breakdown = false;
+        for (; j < m && it < budget; ++j) {
+            cd* vj = W.V + (int64_t)j * n;
+            cd* zj = vj;
+            if (pc) {
+                zj = W.Z + (int64_t)j * n;
+                FB_CHECK(fb_precond_apply(pc, vj, zj, s));
+            }
+            FB_CHECK(fb_apply_any(A, zj, W.w, s));
+            for (int pass = 0; pass < 2; ++pass) {
+                FB_CUDA(cudaMemsetAsync(W.hs.h, 0, sizeof(cd) * (j + 1), s));
+                dim3 g(std::min(grid_for(n), 64), j + 1);
+                k_mdot<<<g, KB, 0, s>>>(W.V, n, W.w, W.hs.h);
+                k_gs_update<<<grid_for(n), KB, 0, s>>>(W.V, n, j + 1, W.hs.h, W.w);
+                k_accum_h<<<1, 1024, 0, s>>>(W.hs, j);
+                cnt(3);
+            }
+            FB_CHECK(norm2(W.w, n, W.hs.nrm2, s));
+            k_arnoldi_close<<<1, 1, 0, s>>>(W.hs, j);
+            k_scale<<<grid_for(n), KB, 0, s>>>(W.V + (int64_t)(j + 1) * n, W.w, n, W.hs.inv);
+            FB_LAUNCH_CHECK();
+            cnt(2);
+            // one read per step: nrm2, inv, est are adjacent
+            FB_CUDA(cudaMemcpyAsync(W.host, W.hs.nrm2, sizeof(double) * 3, cudaMemcpyDeviceToHost, s));
+            FB_CUDA(cudaStreamSynchronize(s));
+            est = W.host[2];
+            double hn = W.host[0];
+            ++it;
+            if (!std::isfinite(est)) { *status = FB_ERR_NAN; break; }
+            if (hn == 0.0) { breakdown = true; ++j; break; }
+            if (est <= rel_tol * rhs_norm) { ++j; break; }
+        }
+        if (*status != FB_OK) break;
+        int j1 = j;
+        if (j1 > 0) {
+            k_backsolve<<<1, 1, 0, s>>>(W.hs, j1);
+            k_update_x<<<grid_for(n), KB, 0, s>>>(W.d, pc ? W.Z : W.V, n, j1, W.hs.y);
+            FB_LAUNCH_CHECK();
+            cnt(2);
+        }
+        if (breakdown || est <= rel_tol * rhs_norm || it >= budget) break;
+    }
+    *iters = it;
+    *est_rel = rhs_norm > 0 ? est / rhs_norm : 0.0;
+    return FB_OK;
+}
+
+fb_status fb_fgmres_impl(fb_op* A, fb_precond* pc, const cd* b, cd* x, const fb_solver_opts* o,
+                         fb_solve_info* info, cudaStream_t s) {
+    fb_solver_opts opts = *o;
+    if (opts.restart < 1 || opts.restart > 1000) return fb_fail(FB_ERR_ARG, "restart must be in [1, 1000]");
+    if (opts.maxit < 1) return fb_fail(FB_ERR_ARG, "maxit must be >= 1");
+    if (opts.max_refine < 1) opts.max_refine = 1;
+    fb_op* T = opts.true_op ? const_cast<fb_op*>(opts.true_op) : A;
+    if (T->n != A->n) return fb_fail(FB_ERR_ARG, "true_op size differs");
+    int64_t n = A->n;
+    int m = opts.restart;
+    Work W;
+    W.n = n;
+    W.m = m;
+    FB_CHECK(dalloc(&W.V, (size_t)(m + 1) * n));
+    if (pc) FB_CHECK(dalloc(&W.Z, (size_t)m * n));
+    FB_CHECK(dalloc(&W.w, n));
+    FB_CHECK(dalloc(&W.r, n));
+    FB_CHECK(dalloc(&W.d, n));
+    FB_CHECK(dalloc(&W.tmp, n));
+    size_t nsmall = (size_t)(m + 1) * m + 4 * (m + 1) + 2 * m + 8;
+    FB_CHECK(dalloc(&W.small, nsmall));
+    FB_CHECK(dalloc(&W.scal, 8));
+    FB_CUDA(cudaMallocHost((void**)&W.host, sizeof(double) * 4));
+    cd* sp = W.small;
+    W.hs.m = m;
+    W.hs.H = sp; sp += (size_t)(m + 1) * m;
+    W.hs.cs = sp; sp += m + 1;
+    W.hs.sn = sp; sp += m + 1;
+    W.hs.g = sp; sp += m + 1;
+    W.hs.h = sp; sp += m + 1;
+    W.hs.y = sp;
+    W.hs.nrm2 = W.scal;
+    W.hs.inv = W.scal + 1;
+    W.hs.est = W.scal + 2;
+    double* bnorm2 = W.scal + 3;
+
+    fb_solve_info inf{};
+    FB_CUDA(cudaMemsetAsync(x, 0, sizeof(cd) * n, s));
+    FB_CHECK(norm2(b, n, bnorm2, s));
+    double bn2 = 0;
+    FB_CHECK(read_scalar(bnorm2, &bn2, s));
+    double bn = std::sqrt(bn2);
+    if (bn == 0.0) {
+        inf.status = FB_OK;
+        if (info) *info = inf;
+        return FB_OK;
+    }
+    FB_CUDA(cudaMemcpyAsync(W.r, b, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s));
+    double rn = bn;
+    double inner_floor = opts.inner_tol > 0 ? opts.inner_tol : 0.0;
+    int status = FB_OK;
+    for (int sweep = 0; sweep < opts.max_refine; ++sweep) {
+        if (rn <= opts.tol * bn) break;
+        double rel = std::max(inner_floor, 0.5 * opts.tol * bn / rn);
+        int its = 0, st = FB_OK;
+        double est_rel = 0;
+        FB_CHECK(fgmres_inner(A, pc, W, W.r, rn, rel, opts.maxit - inf.iters, &its, &est_rel, &st, s));
+        inf.iters += its;
+        inf.est_relres = est_rel * rn / bn;
+        inf.refinements = sweep + 1;
+        k_add<<<grid_for(n), KB, 0, s>>>(x, W.d, n);
+        cnt();
+        // true residual r = b - T x
+        FB_CHECK(fb_apply_any(T, x, W.tmp, s));
+        k_sub<<<grid_for(n), KB, 0, s>>>(W.r, b, W.tmp, n);
+        FB_LAUNCH_CHECK();
+        cnt();
+        inf.true_matvecs++;
+        double r2 = 0;
+        FB_CHECK(norm2(W.r, n, W.scal + 4, s));
+        FB_CHECK(read_scalar(W.scal + 4, &r2, s));
+        rn = std::sqrt(r2);
+        if (st != FB_OK) { status = st; break; }
+        if (!std::isfinite(rn)) { status = FB_ERR_NAN; break; }
+        if (inf.iters >= opts.maxit) break;
+    }
+    inf.true_relres = rn / bn;
+    if (status == FB_OK && !(inf.true_relres <= opts.tol)) status = FB_ERR_NOCONV;
+    inf.status = status;
+    if (info) *info = inf;
+    if (status != FB_OK) {
+        fb_set_error(status, status == FB_ERR_NOCONV ? "FGMRES did not reach the tolerance"
+                                                     : "FGMRES stopped on a non-finite residual");
+    }
+    return status;
+}
+
+// ------------------------------------------------------- block Jacobi ----
+// In-place Gauss-Jordan inversion with partial pivoting of each leaf block.
+__global__ void k_bj_extract(const cd* nf, const int64_t* nf_off, const int32_t* nf_ncol,
+                             const int32_t* leaf_start, const int32_t* ucnt, const int32_t* ulist,
+                             const int64_t* blk_off, cd* out) {
+    int t = blockIdx.x;
+    int nr = leaf_start[t + 1] - leaf_start[t];
+    int K = nf_ncol[t];
+    int c0 = 0;
+    for (int i = 0; i < ucnt[t]; ++i) {
+        int sl = ulist[(int64_t)t * FB_ULIST + i];
+        if (sl == t) break;
+        c0 += leaf_start[sl + 1] - leaf_start[sl];
+    }
+    for (int e = threadIdx.x; e < nr * nr; e += blockDim.x) {
+        int r = e / nr, c = e % nr;
+        out[blk_off[t] + e] = nf[nf_off[t] + (int64_t)r * K + c0 + c];
+    }
+}
+
+__global__ void k_bj_invert(const int32_t* leaf_start, const int64_t* blk_off, cd* blocks, int* piv_scr,
+                            int* singular) {
+    int t = blockIdx.x;
+    int n = leaf_start[t + 1] - leaf_start[t];
+    cd* a = blocks + blk_off[t];
+    int* piv = piv_scr + leaf_start[t];
+    extern __shared__ cd fcol[];
+    __shared__ int s_p;
+    __shared__ cd s_inv;
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            int p = k;
+            double best = abs2(a[(int64_t)k * n + k]);
+            for (int i = k + 1; i < n; ++i) {
+                double v = abs2(a[(int64_t)i * n + k]);
+                if (v > best) { best = v; p = i; }
+            }
+            piv[k] = p;
+            s_p = p;
+            if (best == 0.0) { atomicExch(singular, 1); s_inv = mk(0.0, 0.0); }
+            else {
+                cd d = a[(int64_t)p * n + k];
+                s_inv = (1.0 / best) * conjg(d);
+            }
+        }
+        __syncthreads();
+        int p = s_p;
+        if (p != k)
+            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+                cd tmp = a[(int64_t)k * n + j];
+                a[(int64_t)k * n + j] = a[(int64_t)p * n + j];
+                a[(int64_t)p * n + j] = tmp;
+            }
+        __syncthreads();
+        cd inv = s_inv;
+        if (threadIdx.x == 0) a[(int64_t)k * n + k] = mk(1.0, 0.0);
+        __syncthreads();
+        for (int j = threadIdx.x; j < n; j += blockDim.x) a[(int64_t)k * n + j] = inv * a[(int64_t)k * n + j];
+        for (int i = threadIdx.x; i < n; i += blockDim.x) fcol[i] = (i == k) ? mk(0.0, 0.0) : a[(int64_t)i * n + k];
+        __syncthreads();
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            int i = e / n, j = e % n;
+            if (i == k) continue;
+            cd f = fcol[i];
+            if (j == k) a[(int64_t)i * n + j] = mk(0.0, 0.0) - f * a[(int64_t)k * n + j];
+            else a[(int64_t)i * n + j] = a[(int64_t)i * n + j] - f * a[(int64_t)k * n + j];
+        }
+        __syncthreads();
+    }
+    for (int k = n - 1; k >= 0; --k) {
+        int p = piv[k];
+        if (p != k)
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                cd tmp = a[(int64_t)i * n + k];
+                a[(int64_t)i * n + k] = a[(int64_t)i * n + p];
+                a[(int64_t)i * n + p] = tmp;
+            }
+        __syncthreads();
+    }
+}
+
+template <class R>
+__global__ void k_bj_apply(const int32_t* leaf_start, const int32_t* perm, const int64_t* blk_off,
+                           const cx<R>* blocks, const cd* __restrict__ x, cd* __restrict__ y) {
+    int t = blockIdx.x;
+    int r0 = leaf_start[t], n = leaf_start[t + 1] - r0;
+    extern __shared__ unsigned char raw[];
+    cx<R>* xs = (cx<R>*)raw;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) xs[i] = from_d<R>(x[perm[r0 + i]]);
+    __syncthreads();
+    const cx<R>* a = blocks + blk_off[t];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = warp; r < n; r += nw) {
+        cx<R> acc = mk<R>(0, 0);
+        for (int c = lane; c < n; c += 32) cmac(acc, a[(int64_t)r * n + c], xs[c]);
+        for (int o = 16; o > 0; o >>= 1) {
+            acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
+            acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+        }
+        if (lane == 0) y[perm[r0 + r]] = mk<double>((double)acc.re, (double)acc.im);
+    }
+}
+
+__global__ void k_d2f_bj(const cd* a, cf* b, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = to_f(a[i]);
+}
+
+fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond** out) {
+    *out = nullptr;
+    if (kind == FB_PC_NONE) return FB_OK;
+    if (kind != FB_PC_BLOCK_JACOBI) return fb_fail(FB_ERR_ARG, "unknown preconditioner kind");
+    if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "block Jacobi needs an FMM operator");
+    const fb_tree* t = op->tree;
+    int nleaf = t->nbox[t->L];
+    fb_precond* pc = new fb_precond();
+    pc->op = op;
+    pc->kind = kind;
+    pc->n = op->n;
+    std::vector<int64_t> off(nleaf + 1, 0);
+    int maxn = 0;
+    for (int b = 0; b < nleaf; ++b) {
+        int nb = t->h_leaf_start[b + 1] - t->h_leaf_start[b];
+        maxn = std::max(maxn, nb);
+        off[b + 1] = off[b] + (int64_t)nb * nb;
+    }
+    int* piv = nullptr;
+    int* sing = nullptr;
+    auto fail = [&](fb_status st) { dfree(piv); dfree(sing); fb_precond_destroy(pc); return st; };
+    fb_status st;
+    if ((st = dalloc(&pc->blk_off, nleaf + 1)) || (st = dalloc(&pc->inv64, off[nleaf])) ||
+        (st = dalloc(&piv, op->n)) || (st = dalloc(&sing, 1)))
+        return fail(st);
+    FB_CUDA(cudaMemcpyAsync(pc->blk_off, off.data(), sizeof(int64_t) * (nleaf + 1), cudaMemcpyHostToDevice, s));
+    FB_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
+    k_bj_extract<<<nleaf, 256, 0, s>>>(op->nf64, op->nf_off, op->nf_ncol, t->leaf_start, t->ucnt, t->ulist,
+                                       pc->blk_off, pc->inv64);
+    k_bj_invert<<<nleaf, 256, sizeof(cd) * std::max(maxn, 1), s>>>(t->leaf_start, pc->blk_off, pc->inv64, piv, sing);
+    int hs = 0;
+    FB_CUDA(cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FB_CUDA(cudaStreamSynchronize(s));
+    dfree(piv);
+    dfree(sing);
+    if (hs) {
+        fb_precond_destroy(pc);
+        return fb_fail(FB_ERR_BREAKDOWN, "singular leaf block in block-Jacobi setup");
+    }
+    if (op->prec == FB_PREC_MIXED_FMM) {
+        FB_CHECK(dalloc(&pc->inv32, off[nleaf]));
+        k_d2f_bj<<<div_up(off[nleaf], 256), 256, 0, s>>>(pc->inv64, pc->inv32, off[nleaf]);
+        FB_LAUNCH_CHECK();
+    }
+    *out = pc;
+    return FB_OK;
+}
+
+fb_status fb_precond_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s) {
+    const fb_tree* t = pc->op->tree;
+    int nleaf = t->nbox[t->L];
+    int maxn = 0;
+    for (int b = 0; b < nleaf; ++b) maxn = std::max(maxn, t->h_leaf_start[b + 1] - t->h_leaf_start[b]);
+    if (pc->inv32) {
+        k_bj_apply<float><<<nleaf, 128, sizeof(cf) * maxn, s>>>(t->leaf_start, t->perm, pc->blk_off, pc->inv32, x, y);
+    } else {
+        k_bj_apply<double><<<nleaf, 128, sizeof(cd) * maxn, s>>>(t->leaf_start, t->perm, pc->blk_off, pc->inv64, x, y);
+    }
+    FB_LAUNCH_CHECK();
+    fb_count_launch();
+    return FB_OK;
+}
+
+void fb_precond_free(fb_precond* pc) {
+    if (!pc) return;
+    dfree(pc->blk_off);
+    dfree(pc->inv64);
+    dfree(pc->inv32);
+    delete pc;
+}
