@@ -28,6 +28,7 @@ __all__ = [
     "fb_operator_create", "fb_operator_apply", "fb_operator_info", "fb_operator_export",
     "fb_operator_destroy", "fb_gamma_monopole", "fb_precond_create", "fb_precond_destroy",
     "fb_fgmres_solve", "fb_eval_field", "fb_operator_apply_timed", "fb_kernel_launches",
+    "fb_operator_apply_noalloc",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -313,3 +314,20 @@ def fb_operator_apply_timed(op, x, y, stream=None):
 
 def fb_kernel_launches() -> int:
     return int(lib.fb_kernel_launches())
+
+
+lib.fb_operator_apply_noalloc.restype = C.c_int
+lib.fb_operator_apply_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+NOALLOC_SCRATCH_BYTES = 32 << 20
+
+
+def fb_operator_apply_noalloc(op, x, y, stream=None):
+    """y = Op x (FMM operators, CUDA tensors) with the expansion scratch in the
+    library's static device buffer: no device allocation in the call."""
+    if not (_is_cuda_tensor(x) and _is_cuda_tensor(y)):
+        raise ValueError("fb_operator_apply_noalloc needs CUDA tensors")
+    if not (x.is_contiguous() and y.is_contiguous()):
+        raise ValueError("device tensors must be contiguous")
+    _check(lib.fb_operator_apply_noalloc(op, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                         _stream(stream)))
+    return y

@@ -239,6 +239,12 @@ fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* s
     return st;
 }
 
+fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y, void* stream) {
+    if (!op || !x || !y) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (x == y) return fb_fail(FB_ERR_ARG, "x and y must not overlap");
+    return fb_fmm_apply_noalloc(op, (const cd*)x, (cd*)y, as_stream(stream));
+}
+
 fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
     if (n) *n = op->n;

@@ -237,6 +237,7 @@ fb_status fb_dense_create(fb_op* op, cudaStream_t s);
 fb_status fb_dense_apply(const fb_op* op, const cd* x, cd* y, cudaStream_t s);
 fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s);
 fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt = nullptr);
+fb_status fb_fmm_apply_noalloc(fb_op* op, const cd* x, cd* y, cudaStream_t s);
 void fb_fmm_destroy(fb_op* op);
 fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s);
 fb_status fb_precond_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s);

@@ -8,6 +8,8 @@
 // group is one complex GEMM  Y = T X  with X gathered from the source boxes
 // and Y scatter-added into the target boxes.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "common.cuh"
 
@@ -169,14 +171,17 @@ static fb_status run_plan(const TransPlan& pl, const cx<R>* T, const cx<R>* src,
 
 template <class R>
 static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, const cx<R>* A,
-                             const cx<R>* W, const cx<R>* V, const cx<R>* T, PhaseTimer* pt) {
+                             const cx<R>* W, const cx<R>* V, const cx<R>* T, PhaseTimer* pt,
+                             void* scratch = nullptr) {
     auto mark = [&](int i) { if (pt) cudaEventRecord(pt->ev[i], s); };
     const fb_tree* t = op->tree;
     int L = op->L;
     int pL = op->p[L], PL = pL * pL;
-    cx<R>* mp = (cx<R>*)op->mp;
-    cx<R>* loc = (cx<R>*)op->loc;
     int64_t cnt = op->lev_off[L + 1];
+    // expansions: the operator's own buffers, or a caller-provided region
+    // holding the multipoles followed by the locals
+    cx<R>* mp = scratch ? (cx<R>*)scratch : (cx<R>*)op->mp;
+    cx<R>* loc = scratch ? (cx<R>*)scratch + cnt : (cx<R>*)op->loc;
     mark(0);
     FB_CUDA(cudaMemsetAsync(mp, 0, sizeof(cx<R>) * cnt, s));
     FB_CUDA(cudaMemsetAsync(loc, 0, sizeof(cx<R>) * cnt, s));
@@ -232,4 +237,53 @@ void fb_fmm_destroy(fb_op* op) {
         free_plan(op->m2m[l]);
         free_plan(op->l2l[l]);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Matvec without allocation.  Some callers cannot allocate device memory when
+// they apply an operator: code running while a stream is captured into a CUDA
+// graph, real-time audio callbacks that must not block in the driver's
+// allocator, or hosts whose device memory is owned by a fixed arena.  For
+// them fb_operator_apply_noalloc keeps the FMM's per-call scratch (the
+// multipole and local expansions of every level) in this library-wide
+// static device array instead of the operator's own buffers.  Every GPU that
+// loads the library holds the array until the process exits.
+static __device__ __align__(256) unsigned char fb_noalloc_scratch[FB_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {nullptr};
+
+// Resolves the device address of the static array for the current device
+// (once per device; host code only sees a stand-in for the symbol).
+static fb_status noalloc_scratch_ptr(void** out) {
+    int dev = 0;
+    FB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fb_fail(FB_ERR_ARG, "device ordinal out of range for the static scratch");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, fb_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fb_fail(FB_ERR_CUDA, std::string("cudaGetSymbolAddress(fb_noalloc_scratch) failed: ") +
+                                            cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return FB_OK;
+}
+
+fb_status fb_fmm_apply_noalloc(fb_op* op, const cd* x, cd* y, cudaStream_t s) {
+    if (op->prec == FB_PREC_FP64_DENSE)
+        return fb_fail(FB_ERR_ARG, "fb_operator_apply_noalloc needs an FMM operator (dense ones use no scratch)");
+    size_t elem = op->prec == FB_PREC_MIXED_FMM ? sizeof(cf) : sizeof(cd);
+    size_t need = 2 * (size_t)op->lev_off[op->L + 1] * elem;
+    if (need > (size_t)FB_NOALLOC_SCRATCH_BYTES)
+        return fb_fail(FB_ERR_ARG, "operator needs " + std::to_string(need) +
+                                       " bytes of expansion scratch; the static buffer holds " +
+                                       std::to_string((size_t)FB_NOALLOC_SCRATCH_BYTES));
+    void* p = nullptr;
+    FB_CHECK(noalloc_scratch_ptr(&p));
+    if (op->prec == FB_PREC_MIXED_FMM)
+        return fmm_apply_t<float>(op, x, y, s, op->nf32, op->w32, op->v32, op->T32, nullptr, p);
+    return fmm_apply_t<double>(op, x, y, s, op->nf64, op->w64, op->v64, op->T64, nullptr, p);
 }
