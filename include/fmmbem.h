@@ -192,6 +192,24 @@ FB_API void fb_operator_destroy(fb_op* op);
 FB_API fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* stream,
                                          double* phase_ms);
 
+/* How an FMM operator applies its M2M / M2L / L2L translations. */
+#define FB_TRANS_AUTO 0     /* library's choice per level (default)                 */
+#define FB_TRANS_COMPOSED 1 /* stacked GEMM with the composed p^2 x p^2 matrix of
+                               each (level, translation vector), Sec. 3.3           */
+#define FB_TRANS_RCR 2      /* rotation - coaxial - back-rotation per box pair
+                               (Sec. 3.3, Sec. 3.3.1): (10/3) p^3 complex MACs      */
+#define FB_TRANS_TENSOR 3   /* mixed precision only: every M2L level as stacked
+                               composed GEMMs on the tensor cores (3xTF32)          */
+
+/* Selects the translation method of an FMM operator; results agree to
+ * rounding.  FB_TRANS_AUTO: FP64 operators use RCR everywhere; mixed operators
+ * run the M2L of levels with >= 48 box pairs per translation vector as
+ * tensor-core GEMMs (3xTF32) and the rest, M2M and L2L by RCR.
+ * FB_TRANS_TENSOR builds its tensor-core tiles on first selection
+ * (allocates; synchronises the legacy stream).  Errors: FB_ERR_ARG for a
+ * dense operator, an unknown method or FB_TRANS_TENSOR on an FP64 operator. */
+FB_API fb_status fb_operator_set_translation(fb_op* op, int method);
+
 /* Size of the library-wide static device buffer used by
  * fb_operator_apply_noalloc (32 MiB, held by every GPU that loads the
  * library until the process exits). */

@@ -28,7 +28,7 @@ __all__ = [
     "fb_operator_create", "fb_operator_apply", "fb_operator_info", "fb_operator_export",
     "fb_operator_destroy", "fb_gamma_monopole", "fb_precond_create", "fb_precond_destroy",
     "fb_fgmres_solve", "fb_eval_field", "fb_operator_apply_timed", "fb_kernel_launches",
-    "fb_operator_apply_noalloc",
+    "fb_operator_apply_noalloc", "fb_operator_set_translation",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -331,3 +331,12 @@ def fb_operator_apply_noalloc(op, x, y, stream=None):
     _check(lib.fb_operator_apply_noalloc(op, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                          _stream(stream)))
     return y
+
+
+FB_TRANS_AUTO, FB_TRANS_COMPOSED, FB_TRANS_RCR, FB_TRANS_TENSOR = 0, 1, 2, 3
+lib.fb_operator_set_translation.restype = C.c_int
+lib.fb_operator_set_translation.argtypes = [C.c_void_p, C.c_int]
+
+
+def fb_operator_set_translation(op, method):
+    _check(lib.fb_operator_set_translation(op, int(method)))

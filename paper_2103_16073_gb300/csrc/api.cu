@@ -245,6 +245,28 @@ fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y, void*
     return fb_fmm_apply_noalloc(op, (const cd*)x, (cd*)y, as_stream(stream));
 }
 
+fb_status fb_operator_set_translation(fb_op* op, int method) {
+    if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
+    if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "dense operators have no translations");
+    if (method < FB_TRANS_AUTO || method > FB_TRANS_TENSOR) return fb_fail(FB_ERR_ARG, "unknown translation method");
+    if (method == FB_TRANS_TENSOR) {
+        if (op->prec != FB_PREC_MIXED_FMM)
+            return fb_fail(FB_ERR_ARG, "tensor-core translations need the mixed precision");
+        if (!op->tc_plan_all) {
+            std::vector<int> all;
+            for (int l = 2; l <= op->L; ++l) all.push_back(l);
+            fb_status st = fb_tc_build(op, all, &op->tc_plan_all, nullptr);
+            if (st != FB_OK) {
+                fb_tc_free(op->tc_plan_all);
+                return st;
+            }
+            FB_CUDA(cudaStreamSynchronize(nullptr));
+        }
+    }
+    op->method = method;
+    return FB_OK;
+}
+
 fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
     if (n) *n = op->n;

@@ -177,6 +177,30 @@ struct TransPlan {
     int ntiles = 0;
 };
 
+// One RCR translation task: dst[dst_idx[c]] += D_out^H C D_in src[src_idx[c]]
+// with the rotation blocks D of one direction and one coaxial set C.
+struct RcrTask {
+    int64_t rot_off;     // complex offset of the direction's rotation blocks
+    int64_t coax_off;    // complex offset of the coaxial set [m][n'][n] (stride pc)
+    int64_t pair_off;
+    int32_t npairs, p_out, p_in, pc;
+    int64_t src_base, dst_base;
+};
+struct RcrTile {
+    int32_t task, col0, nb, pad;
+};
+struct RcrPlan {
+    std::vector<RcrTask> h_tasks;
+    std::vector<RcrTile> h_tiles;
+    RcrTask* tasks = nullptr;
+    RcrTile* tiles = nullptr;
+    const int32_t* src_idx = nullptr;
+    const int32_t* dst_idx = nullptr;
+    int ntiles = 0;
+    int nb = 1;          // box pairs per CTA
+    size_t smem = 0;     // dynamic shared memory per CTA (bytes)
+};
+
 struct fb_op {
     const fb_mesh* mesh = nullptr;
     const fb_tree* tree = nullptr;
@@ -207,6 +231,23 @@ struct fb_op {
     int64_t m2m_toff[FB_MAXLEV + 1][8];      // child level l, octant
     int64_t l2l_toff[FB_MAXLEV + 1][8];
     TransPlan m2l, m2m[FB_MAXLEV + 1], l2l[FB_MAXLEV + 1];
+    // RCR form: rotation blocks per direction, coaxial sets, plans
+    int Prot = 0;
+    int64_t per_dir = 0;
+    cd* rot64 = nullptr; cf* rot32 = nullptr;
+    cd* coax64 = nullptr; cf* coax32 = nullptr;
+    int64_t coax_count = 0, rot_count = 0;
+    RcrPlan m2l_rcr, m2m_rcr[FB_MAXLEV + 1], l2l_rcr[FB_MAXLEV + 1];
+    // tensor-core (3xTF32) stacked M2L: dense levels (auto) / every level
+    void* tc_plan = nullptr;
+    void* tc_plan_all = nullptr;
+    int tc_level[FB_MAXLEV + 1] = {0};      // 1: M2L of this level on tensor cores (auto)
+    RcrPlan m2l_rcr_rest;                   // RCR M2L of the other levels
+    int method = 0;                         // FB_TRANS_*
+    // translation method per level: 0 = composed stacked GEMM, 1 = RCR
+    int mode_m2l[FB_MAXLEV + 1] = {0};
+    int mode_m2m[FB_MAXLEV + 1] = {0};
+    int mode_l2l[FB_MAXLEV + 1] = {0};
     // device vectors for host-memspace calls
     cd* io_x = nullptr;
     cd* io_y = nullptr;
@@ -238,6 +279,11 @@ fb_status fb_dense_apply(const fb_op* op, const cd* x, cd* y, cudaStream_t s);
 fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s);
 fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt = nullptr);
 fb_status fb_fmm_apply_noalloc(fb_op* op, const cd* x, cd* y, cudaStream_t s);
+fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize);
+fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cudaStream_t s);
+fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s);
+fb_status fb_tc_check(const fb_op* op);
+void fb_tc_free(void*& plan);
 void fb_fmm_destroy(fb_op* op);
 fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s);
 fb_status fb_precond_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s);

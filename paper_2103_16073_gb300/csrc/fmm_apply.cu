@@ -160,6 +160,128 @@ __global__ void k_near_l2p(int P, const int32_t* __restrict__ leaf_start, const 
     }
 }
 
+
+// ------------------------------------------------------- RCR translation ----
+// Rotation - coaxial translation - back-rotation (Sec. 3.3) applied per box
+// pair: for a group of pairs sharing one translation vector (one direction,
+// one |t|) each CTA takes nb pairs:
+//   rotate       u_n^mu   = sum_m   D^n_{mu,m} x_n^m              (n < p_in)
+//   coaxial      v_{n'}^mu = sum_n   C^{|mu|}_{n'n} u_n^mu          (n' < p_out)
+//   back-rotate  y_{n'}^m' = sum_mu conj(D^{n'}_{mu,m'}) v_{n'}^mu
+//   dst[target] += y                                  (atomic adds)
+__device__ __forceinline__ void nm_of(int e, int& n, int& m) {
+    n = (int)sqrtf((float)e);
+    while (n * n > e) --n;
+    while ((n + 1) * (n + 1) <= e) ++n;
+    m = e - n * n - n;
+}
+
+template <class R>
+__global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, const RcrTile* __restrict__ tiles,
+                                             const cx<R>* __restrict__ rot, const cx<R>* __restrict__ coax,
+                                             const int32_t* __restrict__ src_idx,
+                                             const int32_t* __restrict__ dst_idx,
+                                             const cx<R>* __restrict__ src, cx<R>* __restrict__ dst) {
+    extern __shared__ unsigned char smem_raw[];
+    RcrTile tl = tiles[blockIdx.x];
+    RcrTask tk = tasks[tl.task];
+    const int nb = tl.nb;
+    const int Pin = tk.p_in * tk.p_in, Pout = tk.p_out * tk.p_out;
+    const int pmid = tk.p_in;   // the rotated input keeps degrees n < p_in
+    cx<R>* buf = (cx<R>*)smem_raw;
+    cx<R>* xs = buf;                    // [nb][Pin]
+    cx<R>* us = buf + nb * Pin;         // [nb][Pin]
+    cx<R>* vs = buf + 2 * nb * Pin;     // [nb][Pout]
+    int tid = threadIdx.x, nth = blockDim.x;
+    for (int q = tid; q < nb * Pin; q += nth) {
+        int b = q / Pin, e = q % Pin;
+        int sb = src_idx[tk.pair_off + tl.col0 + b];
+        xs[q] = src[tk.src_base + (int64_t)sb * Pin + e];
+    }
+    __syncthreads();
+    const cx<R>* D = rot + tk.rot_off;
+    for (int q = tid; q < nb * Pin; q += nth) {
+        int b = q / Pin, e = q % Pin;
+        int n, mu;
+        nm_of(e, n, mu);
+        const cx<R>* Dn = D + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3 + (int64_t)(mu + n) * (2 * n + 1);
+        const cx<R>* xb = xs + b * Pin + n * n;
+        cx<R> acc = mk<R>(0, 0);
+        for (int m = 0; m <= 2 * n; ++m) cmac(acc, Dn[m], xb[m]);
+        us[q] = acc;
+    }
+    __syncthreads();
+    const cx<R>* C = coax + tk.coax_off;
+    const int pc = tk.pc;
+    for (int q = tid; q < nb * Pout; q += nth) {
+        int b = q / Pout, e = q % Pout;
+        int n1, mu;
+        nm_of(e, n1, mu);
+        int am = abs(mu);
+        cx<R> acc = mk<R>(0, 0);
+        if (am < pmid) {
+            const cx<R>* Cr = C + ((int64_t)am * pc + n1) * pc;
+            const cx<R>* ub = us + b * Pin;
+            for (int n = am; n < pmid; ++n) cmac(acc, Cr[n], ub[n * n + n + mu]);
+        }
+        vs[q] = acc;
+    }
+    __syncthreads();
+    for (int q = tid; q < nb * Pout; q += nth) {
+        int b = q / Pout, e = q % Pout;
+        int n1, m1;
+        nm_of(e, n1, m1);
+        const cx<R>* Dn = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (m1 + n1);
+        const cx<R>* vb = vs + b * Pout + n1 * n1;
+        int w = 2 * n1 + 1;
+        cx<R> acc = mk<R>(0, 0);
+        for (int mu = 0; mu < w; ++mu) cmacc(acc, Dn[(int64_t)mu * w], vb[mu]);
+        int db = dst_idx[tk.pair_off + tl.col0 + b];
+        cx<R>* d = dst + tk.dst_base + (int64_t)db * Pout + e;
+        atomicAdd(&d->re, acc.re);
+        atomicAdd(&d->im, acc.im);
+    }
+}
+
+template <class R>
+static fb_status run_rcr(const RcrPlan& pl, const cx<R>* rot, const cx<R>* coax, const cx<R>* src, cx<R>* dst,
+                         cudaStream_t s) {
+    if (pl.ntiles == 0) return FB_OK;
+    if (pl.smem > 48 * 1024)
+        FB_CUDA(cudaFuncSetAttribute(k_rcr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
+    k_rcr<R><<<pl.ntiles, 256, pl.smem, s>>>(pl.tasks, pl.tiles, rot, coax, pl.src_idx, pl.dst_idx, src, dst);
+    FB_LAUNCH_CHECK();
+    fb_count_launch();
+    return FB_OK;
+}
+
+// Tiles of up to 16 pairs per CTA within a shared-memory budget.
+fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize) {
+    pl.src_idx = src;
+    pl.dst_idx = dst;
+    pl.h_tiles.clear();
+    const size_t budget = 160 * 1024;
+    pl.smem = 0;
+    for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
+        const RcrTask& tk = pl.h_tasks[t];
+        size_t per = (size_t)(2 * tk.p_in * tk.p_in + tk.p_out * tk.p_out) * csize;
+        int nb = (int)std::max<size_t>(1, std::min<size_t>(16, budget / per));
+        for (int c = 0; c < tk.npairs; c += nb) {
+            int k = std::min(nb, tk.npairs - c);
+            pl.h_tiles.push_back(RcrTile{t, c, k, 0});
+            pl.smem = std::max(pl.smem, per * k);
+        }
+    }
+    pl.ntiles = (int)pl.h_tiles.size();
+    if (pl.h_tasks.empty()) return FB_OK;
+    if (pl.smem > 200 * 1024) return fb_fail(FB_ERR_ARG, "RCR tile exceeds shared memory (p too large)");
+    FB_CHECK(dalloc(&pl.tasks, pl.h_tasks.size()));
+    FB_CHECK(dalloc(&pl.tiles, pl.h_tiles.size()));
+    FB_CUDA(cudaMemcpy(pl.tasks, pl.h_tasks.data(), sizeof(RcrTask) * pl.h_tasks.size(), cudaMemcpyHostToDevice));
+    FB_CUDA(cudaMemcpy(pl.tiles, pl.h_tiles.data(), sizeof(RcrTile) * pl.h_tiles.size(), cudaMemcpyHostToDevice));
+    return FB_OK;
+}
+
 template <class R>
 static fb_status run_plan(const TransPlan& pl, const cx<R>* T, const cx<R>* src, cx<R>* dst, cudaStream_t s) {
     if (pl.ntiles == 0) return FB_OK;
@@ -190,11 +312,37 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
     FB_LAUNCH_CHECK();
     fb_count_launch();
     mark(1);
-    for (int l = L; l >= 3; --l) FB_CHECK(run_plan<R>(op->m2m[l], T, mp, mp, s));
+    const cx<R>* rot = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->rot64 : (const void*)op->rot32);
+    const cx<R>* coax = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->coax64 : (const void*)op->coax32);
+    const bool composed = op->method == FB_TRANS_COMPOSED;
+    for (int l = L; l >= 3; --l) {
+        if (composed) FB_CHECK(run_plan<R>(op->m2m[l], T, mp, mp, s));
+        else FB_CHECK(run_rcr<R>(op->m2m_rcr[l], rot, coax, mp, mp, s));
+    }
     mark(2);
-    FB_CHECK(run_plan<R>(op->m2l, T, mp, loc, s));
+    if (composed) {
+        FB_CHECK(run_plan<R>(op->m2l, T, mp, loc, s));
+    } else if (op->method == FB_TRANS_RCR) {
+        FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s));
+    } else {
+        if constexpr (sizeof(R) == 4) {
+            if (op->method == FB_TRANS_TENSOR) {
+                FB_CHECK(fb_tc_run(op, op->tc_plan_all, (const cf*)mp, (cf*)loc, s));
+            } else if (op->tc_plan) {
+                FB_CHECK(fb_tc_run(op, op->tc_plan, (const cf*)mp, (cf*)loc, s));
+                FB_CHECK(run_rcr<R>(op->m2l_rcr_rest, rot, coax, mp, loc, s));
+            } else {
+                FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s));
+            }
+        } else {
+            FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s));
+        }
+    }
     mark(3);
-    for (int l = 3; l <= L; ++l) FB_CHECK(run_plan<R>(op->l2l[l], T, loc, loc, s));
+    for (int l = 3; l <= L; ++l) {
+        if (composed) FB_CHECK(run_plan<R>(op->l2l[l], T, loc, loc, s));
+        else FB_CHECK(run_rcr<R>(op->l2l_rcr[l], rot, coax, loc, loc, s));
+    }
     mark(4);
     int maxK = 0;
     for (int v : op->h_nf_ncol) maxK = std::max(maxK, v);
@@ -218,6 +366,10 @@ static void free_plan(TransPlan& p) {
     dfree(p.tasks);
     dfree(p.tiles);
 }
+static void free_plan(RcrPlan& p) {
+    dfree(p.tasks);
+    dfree(p.tiles);
+}
 
 void fb_fmm_destroy(fb_op* op) {
     dfree(op->nf_off);
@@ -233,10 +385,20 @@ void fb_fmm_destroy(fb_op* op) {
     dfree(op->T64);
     dfree(op->T32);
     free_plan(op->m2l);
+    free_plan(op->m2l_rcr);
+    free_plan(op->m2l_rcr_rest);
+    fb_tc_free(op->tc_plan);
+    fb_tc_free(op->tc_plan_all);
     for (int l = 0; l <= FB_MAXLEV; ++l) {
         free_plan(op->m2m[l]);
         free_plan(op->l2l[l]);
+        free_plan(op->m2m_rcr[l]);
+        free_plan(op->l2l_rcr[l]);
     }
+    dfree(op->rot64);
+    dfree(op->rot32);
+    dfree(op->coax64);
+    dfree(op->coax32);
 }
 
 // ---------------------------------------------------------------------------

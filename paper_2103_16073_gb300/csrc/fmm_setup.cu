@@ -615,10 +615,75 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         FB_LAUNCH_CHECK();
     }
     cudaError_t e = cudaStreamSynchronize(s);
+    // the rotation blocks and coaxial sets stay with the operator (RCR form)
+    op->coax64 = coax;
+    op->coax_count = std::max<int64_t>(coax_total, 1);
+    coax = nullptr;
+    op->rot64 = rot;
+    op->rot_count = (int64_t)ndir * per_dir;
+    op->Prot = Prot;
+    op->per_dir = per_dir;
     free_coax();
-    dfree(rot);
     dfree(djobs);
     if (e != cudaSuccess) return fb_fail(FB_ERR_CUDA, std::string("translation setup: ") + cudaGetErrorString(e));
+    // RCR plans: one task per (level, offset) / (level, octant) group
+    {
+        auto rcr_task = [&](const MatReq& r, int64_t g0, int64_t g1, int64_t src_base, int64_t dst_base) {
+            RcrTask tk;
+            tk.rot_off = (int64_t)r.dir * per_dir;
+            tk.coax_off = sets[r.set].out_off;
+            tk.pair_off = g0;
+            tk.npairs = (int32_t)(g1 - g0);
+            tk.p_out = r.pout;
+            tk.p_in = r.pin;
+            tk.pc = sets[r.set].p;
+            tk.src_base = src_base;
+            tk.dst_base = dst_base;
+            return tk;
+        };
+        // levels whose M2L groups are dense enough for the tensor-core form
+        // (mixed precision): on average >= 48 box pairs per translation vector
+        std::vector<int> tc_levels;
+        if (op->prec == FB_PREC_MIXED_FMM) {
+            for (int l = 2; l <= L; ++l) {
+                int64_t pairs = 0, groups = 0;
+                for (int c = 0; c < FB_NOFF; ++c) {
+                    int64_t cnt = t->m2l_group[(size_t)l * FB_NOFF + c + 1] - t->m2l_group[(size_t)l * FB_NOFF + c];
+                    if (cnt) { pairs += cnt; ++groups; }
+                }
+                if (groups && pairs >= 48 * groups) {
+                    tc_levels.push_back(l);
+                    op->tc_level[l] = 1;
+                }
+            }
+        }
+        for (auto& r : reqs) {
+            if (r.which == 0) {
+                int64_t g0 = t->m2l_group[(size_t)r.level * FB_NOFF + r.code];
+                int64_t g1 = t->m2l_group[(size_t)r.level * FB_NOFF + r.code + 1];
+                RcrTask tk = rcr_task(r, g0, g1, op->lev_off[r.level], op->lev_off[r.level]);
+                op->m2l_rcr.h_tasks.push_back(tk);
+                if (!op->tc_level[r.level]) op->m2l_rcr_rest.h_tasks.push_back(tk);
+            } else {
+                int64_t g0 = t->oct_group[r.level][r.code], g1 = t->oct_group[r.level][r.code + 1];
+                if (r.which == 1)
+                    op->m2m_rcr[r.level].h_tasks.push_back(
+                        rcr_task(r, g0, g1, op->lev_off[r.level], op->lev_off[r.level - 1]));
+                else
+                    op->l2l_rcr[r.level].h_tasks.push_back(
+                        rcr_task(r, g0, g1, op->lev_off[r.level - 1], op->lev_off[r.level]));
+            }
+        }
+        size_t csz = op->prec == FB_PREC_MIXED_FMM ? sizeof(cf) : sizeof(cd);
+        FB_CHECK(fb_rcr_upload(op->m2l_rcr, t->m2l_src, t->m2l_dst, csz));
+        FB_CHECK(fb_rcr_upload(op->m2l_rcr_rest, t->m2l_src, t->m2l_dst, csz));
+        if (!tc_levels.empty()) FB_CHECK(fb_tc_build(op, tc_levels, &op->tc_plan, s));
+        for (int l = 3; l <= L; ++l) {
+            FB_CHECK(fb_rcr_upload(op->m2m_rcr[l], t->oct_child[l], t->oct_parent[l], csz));
+            FB_CHECK(fb_rcr_upload(op->l2l_rcr[l], t->oct_parent[l], t->oct_child[l], csz));
+        }
+        op->method = FB_TRANS_AUTO;
+    }
     // ---- FP32 copies for the mixed path
     if (op->prec == FB_PREC_MIXED_FMM) {
         FB_CHECK(dalloc(&op->nf32, op->nf_count));
@@ -629,6 +694,10 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         k_d2f<<<div_up(n * PL, 256), 256, 0, s>>>(op->w64, op->w32, n * PL);
         k_d2f<<<div_up(n * PL, 256), 256, 0, s>>>(op->v64, op->v32, n * PL);
         if (T_total) k_d2f<<<div_up(T_total, 256), 256, 0, s>>>(op->T64, op->T32, T_total);
+        FB_CHECK(dalloc(&op->rot32, op->rot_count));
+        FB_CHECK(dalloc(&op->coax32, op->coax_count));
+        k_d2f<<<div_up(op->rot_count, 256), 256, 0, s>>>(op->rot64, op->rot32, op->rot_count);
+        k_d2f<<<div_up(op->coax_count, 256), 256, 0, s>>>(op->coax64, op->coax32, op->coax_count);
         FB_LAUNCH_CHECK();
         FB_CHECK(dalloc((cf**)&op->mp, mp_count));
         FB_CHECK(dalloc((cf**)&op->loc, mp_count));

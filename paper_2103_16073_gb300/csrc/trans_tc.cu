@@ -1,0 +1,357 @@
+// Stacked M2L translations on the 5th-generation tensor cores (tcgen05).
+//
+// All box pairs of one level that share a translation vector share one
+// composed translation matrix T (p^2 x p^2 complex, Sec. 3.3 RCR composed in
+// FP64).  The complex GEMM  Y = T X  (X: gathered source multipoles, one
+// column per pair) runs as a real GEMM on interleaved (re, im) rows and
+// columns,
+//     [Y_re(r)]   [ T_re  -T_im ] [X_re]
+//     [Y_im(r)] = [ T_im   T_re ] [X_im],
+// in 3xTF32: every FP32 operand is split into hi (TF32) + lo, and
+// D += A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in tensor
+// memory.  A = real T rows (M = 128 per tile, stored pre-split in global
+// memory in the canonical no-swizzle K-major layout), B = gathered X
+// columns (N <= 256 per tile, split while staging into shared memory),
+// K in chunks of 32 with two shared-memory stages.  The epilogue reads the
+// accumulator with tcgen05.ld and scatter-adds into the target locals.
+//
+// Every wait on an mbarrier is bounded; on timeout the kernel records an
+// error flag, waits (bounded) for its own MMAs and releases tensor memory.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int TC_M = 128;       // real output rows per tile
+constexpr int TC_NMAX = 256;    // box pairs per tile
+constexpr int TC_KC = 32;       // real K per stage
+constexpr int A_BLOCK = TC_M * TC_KC;       // floats per (hi or lo) A block
+constexpr int B_BLOCK = TC_NMAX * TC_KC;    // floats per (hi or lo) B block
+constexpr int STAGE_FLOATS = 2 * A_BLOCK + 2 * B_BLOCK;
+constexpr int SBO = (TC_KC / 4) * 128;      // bytes between 8-row groups
+constexpr int LBO = 128;                    // bytes between K-adjacent core matrices
+constexpr long WAIT_LIMIT = 1L << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+    d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of sm_100-family tcgen05
+    return d;                  // base offset 0, no swizzle
+}
+
+// byte offset of element (row, k) of a 128- or 256-row, 32-wide K-major block
+__device__ __forceinline__ int canon(int row, int k) {
+    return (row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4;
+}
+
+__device__ __forceinline__ float tf32_hi(float v) {
+    return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (long it = 0; it < WAIT_LIMIT; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, P1;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity));
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+}  // namespace
+
+struct TcTask {
+    int64_t a_off;          // float offset of the pre-split tiles of T
+    int64_t pair_off;
+    int32_t npairs, nrt, nkc, p_out2;   // p_out2 = complex rows P_out
+    int32_t p_in2;                      // complex columns P_in
+    int32_t pad;
+    int64_t src_base, dst_base;         // complex offsets of the level arrays
+};
+struct TcTile {
+    int32_t task, rt, col0, ncol;
+};
+
+// Pre-split canonical tiles of the real interleaved form of a complex matrix.
+__global__ void k_tc_pack(const cd* __restrict__ T, int rows, int cols, int nrt, int nkc, float* __restrict__ out) {
+    int64_t total = (int64_t)nrt * nkc * A_BLOCK;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t blk = i / A_BLOCK;
+        int e = (int)(i % A_BLOCK);
+        int rt = (int)(blk / nkc), kc = (int)(blk % nkc);
+        int ri = e / TC_KC, ki = e % TC_KC;
+        int rr = rt * TC_M + ri, kk = kc * TC_KC + ki;
+        int r = rr >> 1, sr = rr & 1, k = kk >> 1, sk = kk & 1;
+        double v = 0.0;
+        if (r < rows && k < cols) {
+            cd t = T[(int64_t)r * cols + k];
+            v = sr == 0 ? (sk == 0 ? t.re : -t.im) : (sk == 0 ? t.im : t.re);
+        }
+        float f = (float)v;
+        float hi = tf32_hi(f);
+        float lo = (float)(v - (double)hi);
+        float* base = out + blk * 2 * A_BLOCK;
+        int off = canon(ri, ki) >> 2;
+        base[off] = hi;
+        base[A_BLOCK + off] = lo;
+    }
+}
+
+__global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
+                                                      const float* __restrict__ Abuf, const int32_t* __restrict__ src_idx,
+                                                      const int32_t* __restrict__ dst_idx, const cf* __restrict__ src,
+                                                      cf* __restrict__ dst, int* __restrict__ err) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ uint32_t tmem_holder;
+    __shared__ int s_src[TC_NMAX];
+    __shared__ int s_dst[TC_NMAX];
+    // 1024-byte aligned stage buffers
+    uint32_t raw = smem_u32(smem_raw);
+    uint32_t pad = (1024 - (raw & 1023)) & 1023;
+    float* stage0 = (float*)(smem_raw + pad);
+
+    const TcTile tl = tiles[blockIdx.x];
+    const TcTask tk = tasks[tl.task];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ncol = tl.ncol;
+    const int nmma = (ncol + 15) & ~15;
+    for (int j = tid; j < TC_NMAX; j += blockDim.x) {
+        bool ok = j < ncol;
+        s_src[j] = ok ? src_idx[tk.pair_off + tl.col0 + j] : -1;
+        s_dst[j] = ok ? dst_idx[tk.pair_off + tl.col0 + j] : -1;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(TC_NMAX));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_holder;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) |
+                           ((uint32_t)(TC_M >> 4) << 24);
+    const float* Atile = Abuf + tk.a_off + (int64_t)tl.rt * tk.nkc * 2 * A_BLOCK;
+    const int kreal = 2 * tk.p_in2;
+    bool failed = false;
+
+    for (int c = 0; c < tk.nkc; ++c) {
+        const int s = c & 1;
+        float* st = stage0 + s * STAGE_FLOATS;
+        float* sAh = st;
+        float* sAl = st + A_BLOCK;
+        float* sBh = st + 2 * A_BLOCK;
+        float* sBl = st + 2 * A_BLOCK + B_BLOCK;
+        if (c >= 2) {
+            if (!mbar_wait(smem_u32(&bars[s]), ((c - 2) >> 1) & 1)) failed = true;
+        }
+        if (__syncthreads_or(failed)) {
+            failed = true;
+            break;
+        }
+        // A: pre-split canonical tiles, contiguous (hi block then lo block)
+        {
+            const float4* g = (const float4*)(Atile + (int64_t)c * 2 * A_BLOCK);
+            float4* d = (float4*)sAh;   // sAl follows sAh contiguously
+            for (int i = tid; i < 2 * A_BLOCK / 4; i += blockDim.x) d[i] = g[i];
+        }
+        // B: gathered source multipoles (interleaved re/im = real K), split
+        for (int i = tid; i < nmma * (TC_KC / 2); i += blockDim.x) {
+            int j = i / (TC_KC / 2);
+            int kp = (i % (TC_KC / 2)) * 2;           // even real k within the chunk
+            int kg = c * TC_KC + kp;
+            float2 v = make_float2(0.f, 0.f);
+            int sb = s_src[j];
+            if (sb >= 0 && kg < kreal) {
+                cf z = src[tk.src_base + (int64_t)sb * tk.p_in2 + (kg >> 1)];
+                v = make_float2(z.re, z.im);
+            }
+            float2 h = make_float2(tf32_hi(v.x), tf32_hi(v.y));
+            float2 l = make_float2(v.x - h.x, v.y - h.y);
+            int off = canon(j, kp) >> 2;
+            *(float2*)(sBh + off) = h;
+            *(float2*)(sBl + off) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            uint32_t aH = smem_u32(sAh), aL = smem_u32(sAl), bH = smem_u32(sBh), bL = smem_u32(sBl);
+#pragma unroll
+            for (int ks = 0; ks < TC_KC / 8; ++ks) {
+                uint32_t o = ks * 2 * LBO;
+                uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
+                mma_tf32(tmem, umma_desc(aH + o), umma_desc(bH + o), idesc, first);
+                mma_tf32(tmem, umma_desc(aH + o), umma_desc(bL + o), idesc, 1u);
+                mma_tf32(tmem, umma_desc(aL + o), umma_desc(bH + o), idesc, 1u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&bars[s])));
+        }
+    }
+    // all MMAs of the tile: the last commit covers every earlier MMA
+    const int last = tk.nkc - 1;
+    bool done = mbar_wait(smem_u32(&bars[last & 1]), (last >> 1) & 1);
+    if (!done || failed) {
+        if (tid == 0) atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (done && !failed) {
+        // epilogue: warps w and w+4 share lane quadrant w%4, split the columns
+        const int quad = warp & 3;
+        const int half = warp >> 2;
+        const int rr = tl.rt * TC_M + quad * 32 + lane;      // real output row
+        const int r = rr >> 1, part = rr & 1;
+        const int cmid = ((nmma / 16 + 1) / 2) * 16;       // split on 16-column boundaries
+        const int cbeg = half ? cmid : 0;
+        const int cend = half ? nmma : cmid;
+        for (int c0 = cbeg; c0 < cend; c0 += 16) {
+            uint32_t v[16];
+            uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (r < tk.p_out2) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    int j = c0 + q;
+                    int db = j < TC_NMAX ? s_dst[j] : -1;
+                    if (db < 0) continue;
+                    float* d = (float*)(dst + tk.dst_base + (int64_t)db * tk.p_out2 + r) + part;
+                    atomicAdd(d, __uint_as_float(v[q]));
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_NMAX));
+}
+
+// ------------------------------------------------------------- host side ----
+struct TcPlanImpl {
+    std::vector<TcTask> h_tasks;
+    std::vector<TcTile> h_tiles;
+    TcTask* tasks = nullptr;
+    TcTile* tiles = nullptr;
+    float* A = nullptr;
+    int* err = nullptr;
+    int64_t a_floats = 0;
+};
+
+size_t fb_tc_smem_bytes() { return (size_t)2 * STAGE_FLOATS * sizeof(float) + 1024; }
+
+// Builds the tensor-core plan for the M2L groups of the levels in `levels`.
+fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cudaStream_t s) {
+    const fb_tree* t = op->tree;
+    TcPlanImpl* pl = new TcPlanImpl();
+    *slot = pl;
+    for (int l : levels) {
+        int P = op->p[l] * op->p[l];
+        int nrt = (2 * P + TC_M - 1) / TC_M;
+        int nkc = (2 * P + TC_KC - 1) / TC_KC;
+        for (int c = 0; c < FB_NOFF; ++c) {
+            int64_t g0 = t->m2l_group[(size_t)l * FB_NOFF + c], g1 = t->m2l_group[(size_t)l * FB_NOFF + c + 1];
+            if (g1 == g0) continue;
+            TcTask tk;
+            tk.a_off = pl->a_floats;
+            tk.pair_off = g0;
+            tk.npairs = (int32_t)(g1 - g0);
+            tk.nrt = nrt;
+            tk.nkc = nkc;
+            tk.p_out2 = P;
+            tk.p_in2 = P;
+            tk.pad = 0;
+            tk.src_base = op->lev_off[l];
+            tk.dst_base = op->lev_off[l];
+            int ti = (int)pl->h_tasks.size();
+            pl->h_tasks.push_back(tk);
+            for (int rt = 0; rt < nrt; ++rt)
+                for (int c0 = 0; c0 < tk.npairs; c0 += TC_NMAX)
+                    pl->h_tiles.push_back(TcTile{ti, rt, c0, std::min(TC_NMAX, tk.npairs - c0)});
+            pl->a_floats += (int64_t)nrt * nkc * 2 * A_BLOCK;
+        }
+    }
+    if (pl->h_tasks.empty()) return FB_OK;
+    FB_CHECK(dalloc(&pl->A, pl->a_floats));
+    FB_CHECK(dalloc(&pl->tasks, pl->h_tasks.size()));
+    FB_CHECK(dalloc(&pl->tiles, pl->h_tiles.size()));
+    FB_CHECK(dalloc(&pl->err, 1));
+    FB_CUDA(cudaMemsetAsync(pl->err, 0, sizeof(int), s));
+    FB_CUDA(cudaMemcpyAsync(pl->tasks, pl->h_tasks.data(), sizeof(TcTask) * pl->h_tasks.size(),
+                            cudaMemcpyHostToDevice, s));
+    FB_CUDA(cudaMemcpyAsync(pl->tiles, pl->h_tiles.data(), sizeof(TcTile) * pl->h_tiles.size(),
+                            cudaMemcpyHostToDevice, s));
+    size_t ti = 0;
+    for (int l : levels) {
+        for (int c = 0; c < FB_NOFF; ++c) {
+            int64_t g0 = t->m2l_group[(size_t)l * FB_NOFF + c], g1 = t->m2l_group[(size_t)l * FB_NOFF + c + 1];
+            if (g1 == g0) continue;
+            const TcTask& tk = pl->h_tasks[ti++];
+            int64_t toff = op->m2l_toff[(size_t)l * FB_NOFF + c];
+            int64_t total = (int64_t)tk.nrt * tk.nkc * A_BLOCK;
+            k_tc_pack<<<(unsigned)std::min<int64_t>(div_up(total, 256), 4096), 256, 0, s>>>(
+                op->T64 + toff, tk.p_out2, tk.p_in2, tk.nrt, tk.nkc, pl->A + tk.a_off);
+        }
+    }
+    FB_LAUNCH_CHECK();
+    FB_CUDA(cudaFuncSetAttribute(k_trans_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_tc_smem_bytes()));
+    return FB_OK;
+}
+
+fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s) {
+    TcPlanImpl* pl = (TcPlanImpl*)plan;
+    if (!pl || pl->h_tiles.empty()) return FB_OK;
+    k_trans_tc<<<(unsigned)pl->h_tiles.size(), 256, fb_tc_smem_bytes(), s>>>(
+        pl->tasks, pl->tiles, pl->A, op->tree->m2l_src, op->tree->m2l_dst, src, dst, pl->err);
+    FB_LAUNCH_CHECK();
+    fb_count_launch();
+    return FB_OK;
+}
+
+// Error flag of the tensor-core kernel (1 = a bounded wait ran out).
+fb_status fb_tc_check(const fb_op* op) {
+    for (void* v : {op->tc_plan, op->tc_plan_all}) {
+        TcPlanImpl* pl = (TcPlanImpl*)v;
+        if (!pl || !pl->err) continue;
+        int h = 0;
+        FB_CUDA(cudaMemcpy(&h, pl->err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h) return fb_fail(FB_ERR_TIMEOUT, "tensor-core translation kernel: a bounded wait ran out");
+    }
+    return FB_OK;
+}
+
+void fb_tc_free(void*& plan) {
+    TcPlanImpl* pl = (TcPlanImpl*)plan;
+    if (!pl) return;
+    dfree(pl->A);
+    dfree(pl->tasks);
+    dfree(pl->tiles);
+    dfree(pl->err);
+    delete pl;
+    plan = nullptr;
+}

@@ -105,20 +105,33 @@ def test_setup_stages_match_oracle(case, kind):
             assert maxrel(g.reshape(ref.shape), ref) < 1e-11, ("L2L", lev, o)
 
 
+@pytest.mark.parametrize("method", [fb.FB_TRANS_RCR, fb.FB_TRANS_COMPOSED])
 @pytest.mark.parametrize("kind", ["A", "L", "M", "LP"])
-def test_fp64_fmm_matvec(case, kind):
+def test_fp64_fmm_matvec(case, kind, method):
     x = seeded_vector(case.wl.n, 11)
-    y = case.apply(case.op(kind, fb.FB_PREC_FP64_FMM), x)
+    op = case.op(kind, fb.FB_PREC_FP64_FMM)
+    fb.fb_operator_set_translation(op, method)
+    try:
+        y = case.apply(op, x)
+    finally:
+        fb.fb_operator_set_translation(op, fb.FB_TRANS_AUTO)
     yo = oracle_fmm(case.name, kind, 6.0, PMIN[kind]).matvec(x)
     assert rel(y, yo) < 1e-11                                   # same truncation
     assert rel(y, oracle_dense(case.name)[kind] @ x) < 1e-5     # FMM accuracy
 
 
+@pytest.mark.parametrize("method", [fb.FB_TRANS_AUTO, fb.FB_TRANS_RCR, fb.FB_TRANS_COMPOSED,
+                                    fb.FB_TRANS_TENSOR])
 @pytest.mark.parametrize("kind", ["A", "L"])
-def test_mixed_fmm_matvec(case, kind):
+def test_mixed_fmm_matvec(case, kind, method):
     x = seeded_vector(case.wl.n, 12)
     y64 = case.apply(case.op(kind, fb.FB_PREC_FP64_FMM), x)
-    y32 = case.apply(case.op(kind, fb.FB_PREC_MIXED_FMM), x)
+    op = case.op(kind, fb.FB_PREC_MIXED_FMM)
+    fb.fb_operator_set_translation(op, method)
+    try:
+        y32 = case.apply(op, x)
+    finally:
+        fb.fb_operator_set_translation(op, fb.FB_TRANS_AUTO)
     assert rel(y32, y64) < 1e-5
     assert rel(y32, oracle_dense(case.name)[kind] @ x) < 2e-5
 
@@ -148,3 +161,23 @@ def test_fmm_fgmres_solution(case):
     fb.fb_precond_destroy(pc)
     assert info2["status"] == 0 and info2["true_relres"] <= 1e-4
     assert rel(x2.cpu().numpy(), x_ref) < 1e-3
+
+
+def test_tensor_core_translations_large_p():
+    """All M2L levels on the tensor cores for the 4k sub-instance of the 1 kHz
+    room (p = 26 and 17: 11 row tiles x 43 K chunks per matrix) against the
+    FP64 RCR path."""
+    c = GpuCase("sub")
+    try:
+        x = seeded_vector(c.wl.n, 13)
+        y64 = c.apply(c.op("A", fb.FB_PREC_FP64_FMM), x)
+        op = c.op("A", fb.FB_PREC_MIXED_FMM)
+        fb.fb_operator_set_translation(op, fb.FB_TRANS_TENSOR)
+        yt = c.apply(op, x)
+        fb.fb_operator_set_translation(op, fb.FB_TRANS_RCR)
+        yr = c.apply(op, x)
+        assert rel(yt, y64) < 1e-5
+        assert rel(yr, y64) < 1e-5
+        assert rel(yt, oracle_dense("sub")["A"] @ x) < 2e-5
+    finally:
+        c.close()
