@@ -126,21 +126,65 @@ def build_problem(fb, W, torch, rank):
     return dict(wl=wl, mesh=mesh, tree=tree, A32=A32, A64=A64, L64=L64, pc32=pc32, pc64=pc64, b=b)
 
 
-def m2l_algorithmic_flops(fb, P, tree):
-    """Algorithmic M2L flops of one matvec: (10/3) p^3 complex MACs x 8 flops
-    per translation (rotation - coaxial - back-rotation), summed over the
-    V-list pairs of every level."""
+def level_counts(fb, op, tree):
+    """(p, tensor-core flag, M2L pairs, boxes) per level."""
     L, org, side, nb = fb.fb_tree_info(tree)
-    n, L2, p = fb.fb_operator_info(P["A32"])
-    total = 0.0
-    for lev in range(2, L + 1):
-        pairs = fb.fb_tree_export(tree, 4, lev).shape[0]
-        total += pairs * (10.0 / 3.0) * p[lev] ** 3 * 8.0
-    executed = 0.0
-    for lev in range(2, L + 1):
-        pairs = fb.fb_tree_export(tree, 4, lev).shape[0]
-        executed += pairs * 8.0 * float(p[lev]) ** 4
-    return total, executed
+    n, L2, p = fb.fb_operator_info(op)
+    tc = fb.fb_operator_export(op, 7).real.astype(int)
+    pairs = [0, 0] + [fb.fb_tree_export(tree, 4, lev).shape[0] for lev in range(2, L + 1)]
+    return L, p, tc, pairs, nb
+
+
+def rcr_flops(p_out, p_in):
+    """Algorithmic flops of one RCR translation: rotations sum (2n+1)^2 for
+    n < p_in and n < p_out, coaxial sum over m of (p_out-|m|)(p_in-|m|),
+    complex MACs x 8 (about (10/3) p^3 x 8 for p_out = p_in)."""
+    rot = sum((2 * n + 1) ** 2 for n in range(p_in)) + sum((2 * n + 1) ** 2 for n in range(p_out))
+    q = min(p_out, p_in)
+    coax = sum((p_out - abs(m)) * (p_in - abs(m)) for m in range(-q + 1, q))
+    return 8.0 * (rot + coax)
+
+
+def roofline(fb, op, tree, phases, pk):
+    """Roofline of the dominant kernel of one mixed matvec (largest phase)."""
+    L, p, tc, pairs, nb = level_counts(fb, op, tree)
+    cand = {k: v for k, v in phases.items() if k != "total"}
+    dom = max(cand, key=cand.get)
+    t = cand[dom] / 1e3
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    if dom == "m2l_tc":
+        alg = sum(pairs[l] * rcr_flops(p[l], p[l]) for l in range(2, L + 1) if tc[l])
+        execd = 0.0
+        for l in range(2, L + 1):
+            if tc[l]:
+                P2 = 2 * p[l] ** 2
+                rows = -(-P2 // 128) * 128
+                kk = -(-P2 // 16) * 16
+                execd += pairs[l] * rows * kk * 2.0 * 3.0
+        # TF32 tensor peak from the measured BF16 peak x nominal TF32/BF16 ratio;
+        # 3 split passes, and one complex MAC (8 algorithmic flops) = 4 real MACs
+        tf32 = float(pk.get("bf16_tflops", 1990.0)) * (1.1 / 2.25)
+        peak = tf32 / 3.0
+        return {"kernel": "k_trans_tc (M2L, tcgen05 3xTF32)", "bound": "tensor",
+                "achieved": round(alg / t / 1e12, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(alg / t / 1e12 / peak, 4), "traffic": None,
+                "peak_kind": "measured BF16 burst x 1.1/2.25 (TF32) / 3 passes, of measured",
+                "algorithmic_flops_per_launch": alg, "executed_tensor_flops_per_launch": execd,
+                "executed_tensor_tflops": round(execd / t / 1e12, 1), "launch_ms": round(cand[dom], 4)}
+    if dom in ("m2l", "m2m", "l2l"):
+        if dom == "m2l":
+            alg = sum(pairs[l] * rcr_flops(p[l], p[l]) for l in range(2, L + 1) if not tc[l])
+        elif dom == "m2m":
+            alg = sum(nb[l] * rcr_flops(p[l - 1], p[l]) for l in range(3, L + 1))
+        else:
+            alg = sum(nb[l] * rcr_flops(p[l], p[l - 1]) for l in range(3, L + 1))
+        return {"kernel": f"k_rcr<float> ({dom.upper()})", "bound": "alu", "achieved": round(alg / t / 1e12, 3),
+                "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(alg / t / 1e12 / fp32_peak, 4),
+                "traffic": None, "peak_kind": "FP32 FMA pipes x max SM clock (152 SMs x 128 lanes x 2), derived",
+                "algorithmic_flops_per_launch": alg, "launch_ms": round(cand[dom], 4)}
+    return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+            "frac": None, "traffic": None, "launch_ms": round(cand[dom], 4)}
 
 
 def run_ours(args):
@@ -253,12 +297,7 @@ def run_ours(args):
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = statistics.median(e2e_t)
 
-    # roofline of the dominant kernel (M2L translations, FP32 CUDA-core GEMM)
-    alg_flops, exec_flops = m2l_algorithmic_flops(fb, P, P["tree"])
-    m2l_s = ph["m2l"] / 1e3
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12     # TFLOP/s, FP32 FMA pipes at max clock
-    achieved = alg_flops / m2l_s / 1e12
+    rf = roofline(fb, P["A32"], P["tree"], ph, pk)
     res = {
         "metric": METRIC,
         "value": round(ws / (ms_step / 1e3), 4),
@@ -292,11 +331,7 @@ def run_ours(args):
         "e2e": {"value": round(1.0 / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 16 * n},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_trans<float> (M2L)", "bound": "alu", "achieved": round(achieved, 3),
-                     "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(achieved / fp32_peak, 4),
-                     "traffic": None, "peak_kind": "FP32 FMA pipes x max SM clock (152 SMs x 128 lanes x 2)",
-                     "algorithmic_flops_per_launch": alg_flops, "executed_flops_per_launch": exec_flops,
-                     "launch_ms": round(ph["m2l"], 4)},
+        "roofline": rf,
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:

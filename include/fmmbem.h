@@ -178,7 +178,9 @@ FB_API fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, 
  * (dy+3)*7 + (dz+3)), 4 = M2M matrix child->parent at child level `level`,
  * octant `index` (p_{l-1}^2 x p_l^2), 5 = L2L matrix parent->child at child
  * level `level`, octant `index` (p_l^2 x p_{l-1}^2), 6 = dense matrix row
- * `index` (N complex).  *count receives the number of complex values. */
+ * `index` (N complex), 7 = per level 1 + 0i if its M2L runs on the tensor
+ * cores under the current translation method, else 0 (leaf_level + 1
+ * values).  *count receives the number of complex values. */
 FB_API fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t index, double* out,
                              int64_t* count);
 
@@ -186,9 +188,10 @@ FB_API void fb_operator_destroy(fb_op* op);
 
 /* Tracing: y = Op x on device pointers (enqueued on `stream`, then the stream
  * is synchronised) with CUDA-event times in milliseconds per phase:
- * phase_ms[0] = zeroing + P2M, [1] = M2M, [2] = M2L, [3] = L2L,
- * [4] = near field + L2P, [5] = total (dense operators fill only [5]).
- * phase_ms must hold 6 doubles. */
+ * phase_ms[0] = zeroing + P2M, [1] = M2M, [2] = M2L on the tensor cores
+ * (0 when none), [3] = rest of M2L, [4] = L2L, [5] = near field + L2P,
+ * [6] = total (dense operators fill only [6]).  phase_ms must hold 7
+ * doubles. */
 FB_API fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* stream,
                                          double* phase_ms);
 

@@ -299,14 +299,14 @@ lib.fb_operator_apply_timed.restype = C.c_int
 lib.fb_operator_apply_timed.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
 lib.fb_kernel_launches.restype = C.c_longlong
 lib.fb_kernel_launches.argtypes = []
-PHASES = ("p2m", "m2m", "m2l", "l2l", "near_l2p", "total")
+PHASES = ("p2m", "m2m", "m2l_tc", "m2l", "l2l", "near_l2p", "total")
 
 
 def fb_operator_apply_timed(op, x, y, stream=None):
     """y = Op x on CUDA tensors; returns per-phase CUDA-event times (ms)."""
     if not (_is_cuda_tensor(x) and _is_cuda_tensor(y)):
         raise ValueError("fb_operator_apply_timed needs CUDA tensors")
-    ms = np.zeros(6)
+    ms = np.zeros(7)
     _check(lib.fb_operator_apply_timed(op, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                        _stream(stream), ms.ctypes.data))
     return dict(zip(PHASES, ms.tolist()))

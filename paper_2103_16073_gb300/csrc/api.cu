@@ -225,6 +225,7 @@ fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* s
     for (int i = 0; i <= FB_NPHASE; ++i) FB_CUDA(cudaEventCreate(&pt.ev[i]));
     fb_status st = fb_fmm_apply(op, (const cd*)x, (cd*)y, s, &pt);
     if (st == FB_OK) {
+        // marks 0..6 bracket the six phases; phase_ms[6] is the total
         FB_CUDA(cudaEventSynchronize(pt.ev[FB_NPHASE - 1]));
         for (int i = 0; i < FB_NPHASE - 1; ++i) {
             float ms = 0;
@@ -249,9 +250,10 @@ fb_status fb_operator_set_translation(fb_op* op, int method) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
     if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "dense operators have no translations");
     if (method < FB_TRANS_AUTO || method > FB_TRANS_TENSOR) return fb_fail(FB_ERR_ARG, "unknown translation method");
+    if (method == FB_TRANS_TENSOR && op->prec != FB_PREC_MIXED_FMM)
+        return fb_fail(FB_ERR_ARG, "tensor-core translations need the mixed precision");
+    if (method == FB_TRANS_COMPOSED || method == FB_TRANS_TENSOR) FB_CHECK(fb_compose_all(op, nullptr));
     if (method == FB_TRANS_TENSOR) {
-        if (op->prec != FB_PREC_MIXED_FMM)
-            return fb_fail(FB_ERR_ARG, "tensor-core translations need the mixed precision");
         if (!op->tc_plan_all) {
             std::vector<int> all;
             for (int l = 2; l <= op->L; ++l) all.push_back(l);
@@ -279,6 +281,18 @@ fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t inde
     if (!op || !count) return fb_fail(FB_ERR_ARG, "NULL argument");
     const cd* src = nullptr;
     int64_t cnt = 0;
+    if (which == 7) {
+        if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "not an FMM operator");
+        *count = op->L + 1;
+        if (out)
+            for (int l = 0; l <= op->L; ++l) {
+                bool tc = op->prec == FB_PREC_MIXED_FMM &&
+                          (op->method == FB_TRANS_TENSOR ? l >= 2 : (op->method == FB_TRANS_AUTO && op->tc_level[l]));
+                out[2 * l] = tc ? 1.0 : 0.0;
+                out[2 * l + 1] = 0.0;
+            }
+        return FB_OK;
+    }
     if (which == 6) {
         if (!op->dense) return fb_fail(FB_ERR_ARG, "not a dense operator");
         if (index < 0 || index >= op->n) return fb_fail(FB_ERR_ARG, "row out of range");
@@ -302,12 +316,14 @@ fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t inde
             }
         } else if (which == 3) {
             if (level < 2 || level > L || index < 0 || index >= FB_NOFF) return fb_fail(FB_ERR_ARG, "bad level/offset");
+            FB_CHECK(fb_compose_all(const_cast<fb_op*>(op), nullptr));
             int64_t off = op->m2l_toff[(size_t)level * FB_NOFF + index];
             if (off < 0) return fb_fail(FB_ERR_ARG, "offset not used at this level");
             src = op->T64 + off;
             cnt = (int64_t)op->p[level] * op->p[level] * op->p[level] * op->p[level];
         } else if (which == 4 || which == 5) {
             if (level < 3 || level > L || index < 0 || index > 7) return fb_fail(FB_ERR_ARG, "bad level/octant");
+            FB_CHECK(fb_compose_all(const_cast<fb_op*>(op), nullptr));
             int64_t off = which == 4 ? op->m2m_toff[level][index] : op->l2l_toff[level][index];
             if (off < 0) return fb_fail(FB_ERR_ARG, "octant not used at this level");
             src = op->T64 + off;

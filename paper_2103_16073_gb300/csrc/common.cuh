@@ -151,6 +151,11 @@ struct fb_tree {
     int32_t* oct_parent[FB_MAXLEV + 1] = {nullptr};
     std::vector<int64_t> oct_group[FB_MAXLEV + 1];   // 9 prefix offsets
     int64_t nlist_u = 0;
+    // rotation blocks of the translation directions (shared by operators)
+    cd* rot64 = nullptr;
+    cf* rot32 = nullptr;
+    int rot_P = 0, rot_ndir = 0;
+    int64_t rot_per_dir = 0;
 };
 
 // ----------------------------------------------------------- operator ----
@@ -201,6 +206,14 @@ struct RcrPlan {
     size_t smem = 0;     // dynamic shared memory per CTA (bytes)
 };
 
+// One composed translation matrix T = D_out^H C D_in to build.
+struct ComposeJob {
+    int64_t t_off;       // output offset (complex entries)
+    int64_t rot_off;     // rotation blocks of the direction
+    int64_t coax_off;    // coaxial set [m][n'][n] with stride pc
+    int p_out, p_in, pc;
+};
+
 struct fb_op {
     const fb_mesh* mesh = nullptr;
     const fb_tree* tree = nullptr;
@@ -244,6 +257,9 @@ struct fb_op {
     int tc_level[FB_MAXLEV + 1] = {0};      // 1: M2L of this level on tensor cores (auto)
     RcrPlan m2l_rcr_rest;                   // RCR M2L of the other levels
     int method = 0;                         // FB_TRANS_*
+    std::vector<ComposeJob> h_jobs;         // composed matrices (built on demand)
+    std::vector<int> h_job_level, h_job_m2l;
+    std::vector<char> job_done;
     // translation method per level: 0 = composed stacked GEMM, 1 = RCR
     int mode_m2l[FB_MAXLEV + 1] = {0};
     int mode_m2m[FB_MAXLEV + 1] = {0};
@@ -268,7 +284,7 @@ struct fb_precond {
 void fb_count_launch(long long n = 1);
 
 // Per-phase CUDA-event timing of one FMM matvec (tracing aid).
-constexpr int FB_NPHASE = 6;   // P2M, M2M, M2L, L2L, near+L2P, total
+constexpr int FB_NPHASE = 7;   // P2M, M2M, M2L tensor part, M2L rest, L2L, near+L2P, total
 struct PhaseTimer {
     cudaEvent_t ev[FB_NPHASE + 1];
 };
@@ -280,6 +296,9 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s);
 fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt = nullptr);
 fb_status fb_fmm_apply_noalloc(fb_op* op, const cd* x, cd* y, cudaStream_t s);
 fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize);
+fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, cudaStream_t s);
+fb_status fb_compose_jobs(fb_op* op, const std::vector<int>& which, cudaStream_t s);
+fb_status fb_compose_all(fb_op* op, cudaStream_t s);
 fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cudaStream_t s);
 fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s);
 fb_status fb_tc_check(const fb_op* op);

@@ -255,12 +255,13 @@ static fb_status run_rcr(const RcrPlan& pl, const cx<R>* rot, const cx<R>* coax,
     return FB_OK;
 }
 
-// Tiles of up to 16 pairs per CTA within a shared-memory budget.
+// Tiles of up to 16 pairs per CTA within a 48 KB shared-memory budget, so
+// that several CTAs share an SM and small levels still spread over many SMs.
 fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize) {
     pl.src_idx = src;
     pl.dst_idx = dst;
     pl.h_tiles.clear();
-    const size_t budget = 160 * 1024;
+    const size_t budget = 48 * 1024;
     pl.smem = 0;
     for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
         const RcrTask& tk = pl.h_tasks[t];
@@ -320,6 +321,9 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
         else FB_CHECK(run_rcr<R>(op->m2m_rcr[l], rot, coax, mp, mp, s));
     }
     mark(2);
+    // phase [2] is the tensor-core part of M2L: empty unless it runs below
+    const bool tc_split = sizeof(R) == 4 && op->method == FB_TRANS_AUTO && op->tc_plan != nullptr;
+    if (!tc_split) mark(3);
     if (composed) {
         FB_CHECK(run_plan<R>(op->m2l, T, mp, loc, s));
     } else if (op->method == FB_TRANS_RCR) {
@@ -330,6 +334,7 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
                 FB_CHECK(fb_tc_run(op, op->tc_plan_all, (const cf*)mp, (cf*)loc, s));
             } else if (op->tc_plan) {
                 FB_CHECK(fb_tc_run(op, op->tc_plan, (const cf*)mp, (cf*)loc, s));
+                mark(3);
                 FB_CHECK(run_rcr<R>(op->m2l_rcr_rest, rot, coax, mp, loc, s));
             } else {
                 FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s));
@@ -338,12 +343,12 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
             FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s));
         }
     }
-    mark(3);
+    mark(4);
     for (int l = 3; l <= L; ++l) {
         if (composed) FB_CHECK(run_plan<R>(op->l2l[l], T, loc, loc, s));
         else FB_CHECK(run_rcr<R>(op->l2l_rcr[l], rot, coax, loc, loc, s));
     }
-    mark(4);
+    mark(5);
     int maxK = 0;
     for (int v : op->h_nf_ncol) maxK = std::max(maxK, v);
     size_t smem = sizeof(cx<R>) * (maxK + PL);
@@ -352,7 +357,7 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
                                            op->nf_ncol, A, V, loc + op->lev_off[L], x, y);
     FB_LAUNCH_CHECK();
     fb_count_launch();
-    mark(5);
+    mark(6);
     return FB_OK;
 }
 
@@ -395,8 +400,8 @@ void fb_fmm_destroy(fb_op* op) {
         free_plan(op->m2m_rcr[l]);
         free_plan(op->l2l_rcr[l]);
     }
-    dfree(op->rot64);
-    dfree(op->rot32);
+    op->rot64 = nullptr;   // owned by the tree
+    op->rot32 = nullptr;
     dfree(op->coax64);
     dfree(op->coax32);
 }

@@ -16,6 +16,11 @@ int fb_order_rule(double k, double delta, double d0, int pmin) {
     return std::max(pmin, (int)p);
 }
 
+__global__ void k_d2f(const cd* a, cf* b, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = to_f(a[i]);
+}
+
 // ------------------------------------------------------------ near field ----
 __global__ void k_near_fill(Geom g, int kind, double k, double rc, const int32_t* __restrict__ perm,
                             const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ ucnt,
@@ -282,12 +287,6 @@ __global__ void k_rot_project(const cd* Yg, const cd* Yr, int ndir, int P, int n
 
 // --------------------------------------------------------- composition ----
 // T[(n',m'),(n,m)] = sum_{|mu| <= min(n',n)} conj(D^{n'}_{mu,m'}) C^{|mu|}_{n',n} D^n_{mu,m}
-struct ComposeJob {
-    int64_t t_off;       // output offset
-    int64_t rot_off;     // rotation blocks of the direction (per_dir layout for Prot)
-    int64_t coax_off;    // coaxial set [m][n'][n] with stride pc
-    int p_out, p_in, pc;
-};
 __global__ void k_compose(const ComposeJob* jobs, const cd* __restrict__ rot, int Prot,
                           const cd* __restrict__ coax, cd* __restrict__ T) {
     ComposeJob jb = jobs[blockIdx.y];
@@ -318,6 +317,42 @@ __global__ void k_compose(const ComposeJob* jobs, const cd* __restrict__ rot, in
     T[jb.t_off + e] = acc;
 }
 
+// Composes the translation matrices of the listed jobs that are not built
+// yet (T = D_out^H C D_in in FP64), plus their FP32 copies when present.
+fb_status fb_compose_jobs(fb_op* op, const std::vector<int>& which, cudaStream_t s) {
+    std::vector<ComposeJob> todo;
+    for (int j : which)
+        if (!op->job_done[j]) todo.push_back(op->h_jobs[j]);
+    if (todo.empty()) return FB_OK;
+    ComposeJob* djobs = nullptr;
+    FB_CHECK(dalloc(&djobs, todo.size()));
+    FB_CUDA(cudaMemcpyAsync(djobs, todo.data(), sizeof(ComposeJob) * todo.size(), cudaMemcpyHostToDevice, s));
+    int64_t maxe = 0;
+    for (auto& jb : todo) maxe = std::max<int64_t>(maxe, (int64_t)jb.p_out * jb.p_out * jb.p_in * jb.p_in);
+    for (size_t j0 = 0; j0 < todo.size(); j0 += 65535) {
+        int nj = (int)std::min<size_t>(65535, todo.size() - j0);
+        dim3 grid(div_up(maxe, 256), nj);
+        k_compose<<<grid, 256, 0, s>>>(djobs + j0, op->rot64, op->Prot, op->coax64, op->T64);
+    }
+    if (op->T32)
+        for (auto& jb : todo) {
+            int64_t cnt = (int64_t)jb.p_out * jb.p_out * jb.p_in * jb.p_in;
+            k_d2f<<<div_up(cnt, 256), 256, 0, s>>>(op->T64 + jb.t_off, op->T32 + jb.t_off, cnt);
+        }
+    FB_LAUNCH_CHECK();
+    cudaError_t e = cudaStreamSynchronize(s);
+    dfree(djobs);
+    if (e != cudaSuccess) return fb_fail(FB_ERR_CUDA, std::string("composition: ") + cudaGetErrorString(e));
+    for (int j : which) op->job_done[j] = 1;
+    return FB_OK;
+}
+
+fb_status fb_compose_all(fb_op* op, cudaStream_t s) {
+    std::vector<int> all(op->h_jobs.size());
+    for (size_t j = 0; j < all.size(); ++j) all[j] = (int)j;
+    return fb_compose_jobs(op, all, s);
+}
+
 // ------------------------------------------------------------ host side ----
 __global__ void k_leaf_of(const int32_t* leaf_start, int nleaf, int32_t* leaf_of) {
     int b = blockIdx.x;
@@ -339,9 +374,57 @@ __global__ void k_box_centers(const uint32_t* keys, int n, int level, double ox,
     c[3 * b + 1] = oy + (y + 0.5) * delta;
     c[3 * b + 2] = oz + (z + 0.5) * delta;
 }
-__global__ void k_d2f(const cd* a, cf* b, int64_t n) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i < n) b[i] = to_f(a[i]);
+
+// Rotation blocks D^n (n < P) of every direction, by projection quadrature
+// (definition of the rotation coefficients, exact for the band limit),
+// cached in the tree and recomputed only when a larger P is needed.
+fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, cudaStream_t s) {
+    int ndir = (int)dirs.size() / 3;
+    if (t->rot64 && t->rot_P >= P && t->rot_ndir == ndir) return FB_OK;
+    dfree(t->rot64);
+    dfree(t->rot32);
+    int Prot = P;
+    int64_t per_dir = (int64_t)Prot * (2 * Prot - 1) * (2 * Prot + 1) / 3;
+    int nq = Prot + 1, nphi = 2 * Prot + 1, npts = nq * nphi;
+    double *glx = nullptr, *glw = nullptr, *ddirs = nullptr, *yscr = nullptr;
+    cd *Yg = nullptr, *Yr = nullptr, *rot = nullptr;
+    const int BATCH = 16;
+    int ystride = Prot * (Prot + 1) / 2 + 8;
+    auto free_tmp = [&]() { dfree(glx); dfree(glw); dfree(ddirs); dfree(yscr); dfree(Yg); dfree(Yr); };
+    fb_status st;
+    if ((st = dalloc(&rot, (size_t)ndir * per_dir)) || (st = dalloc(&glx, nq)) || (st = dalloc(&glw, nq)) ||
+        (st = dalloc(&ddirs, dirs.size())) || (st = dalloc(&yscr, (size_t)BATCH * npts * ystride)) ||
+        (st = dalloc(&Yg, (size_t)npts * Prot * Prot)) || (st = dalloc(&Yr, (size_t)BATCH * npts * Prot * Prot))) {
+        free_tmp();
+        dfree(rot);
+        return st;
+    }
+    FB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, s));
+    k_gauss_legendre<<<div_up(nq, 64), 64, 0, s>>>(nq, glx, glw);
+    // Y_n^m on the unrotated grid
+    k_rot_grid<<<div_up(npts, 128), 128, 0, s>>>(ddirs, 1, 1, Prot, nq, nphi, glx, yscr, ystride, Yg);
+    for (int d0i = 0; d0i < ndir; d0i += BATCH) {
+        int nb = std::min(BATCH, ndir - d0i);
+        k_rot_grid<<<div_up((int64_t)nb * npts, 128), 128, 0, s>>>(ddirs + 3 * d0i, nb, 0, Prot, nq, nphi, glx,
+                                                                   yscr, ystride, Yr);
+        dim3 grid(div_up((2 * Prot - 1) * (2 * Prot - 1), 128), Prot, nb);
+        k_rot_project<<<grid, 128, 0, s>>>(Yg, Yr, nb, Prot, nq, nphi, glw, d0i, rot);
+    }
+    FB_LAUNCH_CHECK();
+    cudaError_t e = cudaStreamSynchronize(s);
+    free_tmp();
+    if (e != cudaSuccess) {
+        dfree(rot);
+        return fb_fail(FB_ERR_CUDA, std::string("rotation setup: ") + cudaGetErrorString(e));
+    }
+    t->rot64 = rot;
+    t->rot_P = Prot;
+    t->rot_per_dir = per_dir;
+    t->rot_ndir = ndir;
+    FB_CHECK(dalloc(&t->rot32, (size_t)ndir * per_dir));
+    k_d2f<<<div_up((int64_t)ndir * per_dir, 256), 256, 0, s>>>(t->rot64, t->rot32, (int64_t)ndir * per_dir);
+    FB_LAUNCH_CHECK();
+    return FB_OK;
 }
 
 static int igcd(int a, int b) {
@@ -545,40 +628,12 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
                                                                   fscr, f_stride, coax);
         FB_LAUNCH_CHECK();
     }
-    // rotation blocks of every direction up to pmax, by projection quadrature
-    int Prot = pmax;
-    int64_t per_dir = (int64_t)Prot * (2 * Prot - 1) * (2 * Prot + 1) / 3;
-    cd* rot = nullptr;
-    {
-        int nq = Prot + 1, nphi = 2 * Prot + 1, npts = nq * nphi;
-        double *glx = nullptr, *glw = nullptr, *ddirs = nullptr, *yscr = nullptr;
-        cd *Yg = nullptr, *Yr = nullptr;
-        const int BATCH = 16;
-        int ystride = Prot * (Prot + 1) / 2 + 8;
-        auto free_rot = [&]() { dfree(glx); dfree(glw); dfree(ddirs); dfree(yscr); dfree(Yg); dfree(Yr); };
-        if ((st = dalloc(&rot, (size_t)ndir * per_dir)) || (st = dalloc(&glx, nq)) || (st = dalloc(&glw, nq)) ||
-            (st = dalloc(&ddirs, dirs.size())) || (st = dalloc(&yscr, (size_t)BATCH * npts * ystride)) ||
-            (st = dalloc(&Yg, (size_t)npts * Prot * Prot)) || (st = dalloc(&Yr, (size_t)BATCH * npts * Prot * Prot))) {
-            free_rot(); free_coax();
-            return st;
-        }
-        FB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, s));
-        k_gauss_legendre<<<div_up(nq, 64), 64, 0, s>>>(nq, glx, glw);
-        // Y_n^m on the unrotated grid
-        k_rot_grid<<<div_up(npts, 128), 128, 0, s>>>(ddirs, 1, 1, Prot, nq, nphi, glx, yscr, ystride, Yg);
-        FB_LAUNCH_CHECK();
-        for (int d0i = 0; d0i < ndir; d0i += BATCH) {
-            int nb = std::min(BATCH, ndir - d0i);
-            k_rot_grid<<<div_up((int64_t)nb * npts, 128), 128, 0, s>>>(ddirs + 3 * d0i, nb, 0, Prot, nq, nphi,
-                                                                       glx, yscr, ystride, Yr);
-            dim3 grid(div_up((2 * Prot - 1) * (2 * Prot - 1), 128), Prot, nb);
-            k_rot_project<<<grid, 128, 0, s>>>(Yg, Yr, nb, Prot, nq, nphi, glw, d0i, rot);
-            FB_LAUNCH_CHECK();
-        }
-        cudaError_t e = cudaStreamSynchronize(s);
-        free_rot();
-        if (e != cudaSuccess) { free_coax(); dfree(rot); return fb_fail(FB_ERR_CUDA, std::string("rotation setup: ") + cudaGetErrorString(e)); }
-    }
+    // rotation blocks of every direction up to pmax (cached in the tree: they
+    // depend only on the directions, not on k or the operator)
+    FB_CHECK(fb_tree_rotations(const_cast<fb_tree*>(t), pmax, dirs, s));
+    int Prot = t->rot_P;
+    int64_t per_dir = t->rot_per_dir;
+    cd* rot = t->rot64;
     // composed translation matrices
     std::vector<ComposeJob> jobs;
     int64_t T_total = 0;
@@ -597,22 +652,9 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         T_total += (int64_t)r.pout * r.pout * r.pin * r.pin;
     }
     op->T_count = T_total;
-    ComposeJob* djobs = nullptr;
-    if ((st = dalloc(&op->T64, std::max<int64_t>(T_total, 1))) || (st = dalloc(&djobs, std::max<size_t>(jobs.size(), 1)))) {
-        free_coax(); dfree(rot); dfree(djobs);
+    if ((st = dalloc(&op->T64, std::max<int64_t>(T_total, 1)))) {
+        free_coax();
         return st;
-    }
-    if (!jobs.empty()) {
-        FB_CUDA(cudaMemcpyAsync(djobs, jobs.data(), sizeof(ComposeJob) * jobs.size(), cudaMemcpyHostToDevice, s));
-        // group launches by max entry count to bound the grid
-        int64_t maxe = 0;
-        for (auto& j : jobs) maxe = std::max<int64_t>(maxe, (int64_t)j.p_out * j.p_out * j.p_in * j.p_in);
-        for (size_t j0 = 0; j0 < jobs.size(); j0 += 65535) {
-            int nj = (int)std::min<size_t>(65535, jobs.size() - j0);
-            dim3 grid(div_up(maxe, 256), nj);
-            k_compose<<<grid, 256, 0, s>>>(djobs + j0, rot, Prot, coax, op->T64);
-        }
-        FB_LAUNCH_CHECK();
     }
     cudaError_t e = cudaStreamSynchronize(s);
     // the rotation blocks and coaxial sets stay with the operator (RCR form)
@@ -620,11 +662,21 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
     op->coax_count = std::max<int64_t>(coax_total, 1);
     coax = nullptr;
     op->rot64 = rot;
+    op->rot32 = t->rot32;
     op->rot_count = (int64_t)ndir * per_dir;
     op->Prot = Prot;
     op->per_dir = per_dir;
     free_coax();
-    dfree(djobs);
+    // composed matrices are built on demand (tensor-core levels below,
+    // everything for the composed method or for inspection)
+    op->h_jobs = jobs;
+    op->h_job_level.clear();
+    op->h_job_m2l.clear();
+    for (auto& r : reqs) {
+        op->h_job_level.push_back(r.level);
+        op->h_job_m2l.push_back(r.which == 0 ? 1 : 0);
+    }
+    op->job_done.assign(jobs.size(), 0);
     if (e != cudaSuccess) return fb_fail(FB_ERR_CUDA, std::string("translation setup: ") + cudaGetErrorString(e));
     // RCR plans: one task per (level, offset) / (level, octant) group
     {
@@ -677,7 +729,13 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         size_t csz = op->prec == FB_PREC_MIXED_FMM ? sizeof(cf) : sizeof(cd);
         FB_CHECK(fb_rcr_upload(op->m2l_rcr, t->m2l_src, t->m2l_dst, csz));
         FB_CHECK(fb_rcr_upload(op->m2l_rcr_rest, t->m2l_src, t->m2l_dst, csz));
-        if (!tc_levels.empty()) FB_CHECK(fb_tc_build(op, tc_levels, &op->tc_plan, s));
+        if (!tc_levels.empty()) {
+            std::vector<int> need;
+            for (size_t j = 0; j < op->h_jobs.size(); ++j)
+                if (op->h_job_m2l[j] && op->tc_level[op->h_job_level[j]]) need.push_back((int)j);
+            FB_CHECK(fb_compose_jobs(op, need, s));
+            FB_CHECK(fb_tc_build(op, tc_levels, &op->tc_plan, s));
+        }
         for (int l = 3; l <= L; ++l) {
             FB_CHECK(fb_rcr_upload(op->m2m_rcr[l], t->oct_child[l], t->oct_parent[l], csz));
             FB_CHECK(fb_rcr_upload(op->l2l_rcr[l], t->oct_parent[l], t->oct_child[l], csz));
@@ -693,10 +751,7 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         k_d2f<<<div_up(op->nf_count, 256), 256, 0, s>>>(op->nf64, op->nf32, op->nf_count);
         k_d2f<<<div_up(n * PL, 256), 256, 0, s>>>(op->w64, op->w32, n * PL);
         k_d2f<<<div_up(n * PL, 256), 256, 0, s>>>(op->v64, op->v32, n * PL);
-        if (T_total) k_d2f<<<div_up(T_total, 256), 256, 0, s>>>(op->T64, op->T32, T_total);
-        FB_CHECK(dalloc(&op->rot32, op->rot_count));
         FB_CHECK(dalloc(&op->coax32, op->coax_count));
-        k_d2f<<<div_up(op->rot_count, 256), 256, 0, s>>>(op->rot64, op->rot32, op->rot_count);
         k_d2f<<<div_up(op->coax_count, 256), 256, 0, s>>>(op->coax64, op->coax32, op->coax_count);
         FB_LAUNCH_CHECK();
         FB_CHECK(dalloc((cf**)&op->mp, mp_count));

@@ -9,14 +9,25 @@
 //     [Y_im(r)] = [ T_im   T_re ] [X_im],
 // in 3xTF32: every FP32 operand is split into hi (TF32) + lo, and
 // D += A_hi B_hi + A_hi B_lo + A_lo B_hi with FP32 accumulation in tensor
-// memory.  A = real T rows (M = 128 per tile, stored pre-split in global
-// memory in the canonical no-swizzle K-major layout), B = gathered X
-// columns (N <= 256 per tile, split while staging into shared memory),
-// K in chunks of 32 with two shared-memory stages.  The epilogue reads the
-// accumulator with tcgen05.ld and scatter-adds into the target locals.
+// memory.
 //
-// Every wait on an mbarrier is bounded; on timeout the kernel records an
-// error flag, waits (bounded) for its own MMAs and releases tensor memory.
+// Operands:  A = real T rows, M = 128 per tile, pre-split and stored in
+// global memory already in the canonical no-swizzle K-major layout, one
+// 16 KB (hi + lo) block per (row tile, K chunk of 16) -> one bulk TMA copy.
+// B = gathered X columns, N <= 256 per tile, from hi/lo planes of the level
+// multipoles written once per matvec by k_tc_split -> 16-byte cp.async
+// pieces into the canonical layout.
+//
+// Pipeline (8 warps, 4 shared-memory stages of 48 KB):
+//   warps 0-5  B producers (cp.async, completion tracked by the stage's
+//              "full" mbarrier), warp 6 lane 0 A producer (bulk copy with
+//              transaction count), warp 7 lane 0 MMA issuer (waits "full",
+//              issues 6 MMAs, commits to the stage's "empty" mbarrier);
+//   epilogue   all warps: tcgen05.ld of the accumulator (warps w and w+4
+//              share lane quadrant w % 4 and split the columns), atomic
+//              scatter-add into the target locals.
+// Every mbarrier wait is bounded; on timeout the kernel records an error
+// flag, drains its own copies and MMAs (bounded) and releases tensor memory.
 #include <algorithm>
 
 #include "common.cuh"
@@ -25,12 +36,14 @@ namespace {
 
 constexpr int TC_M = 128;       // real output rows per tile
 constexpr int TC_NMAX = 256;    // box pairs per tile
-constexpr int TC_KC = 32;       // real K per stage
+constexpr int TC_KC = 16;       // real K per stage
+constexpr int TC_STAGES = 4;
 constexpr int A_BLOCK = TC_M * TC_KC;       // floats per (hi or lo) A block
 constexpr int B_BLOCK = TC_NMAX * TC_KC;    // floats per (hi or lo) B block
 constexpr int STAGE_FLOATS = 2 * A_BLOCK + 2 * B_BLOCK;
 constexpr int SBO = (TC_KC / 4) * 128;      // bytes between 8-row groups
 constexpr int LBO = 128;                    // bytes between K-adjacent core matrices
+constexpr int NPROD = 192;                  // B producer threads (warps 0-5)
 constexpr long WAIT_LIMIT = 1L << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -44,8 +57,8 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
     return d;                  // base offset 0, no swizzle
 }
 
-// byte offset of element (row, k) of a 128- or 256-row, 32-wide K-major block
-__device__ __forceinline__ int canon(int row, int k) {
+// byte offset of element (row, k) of a K-major block of TC_KC columns
+__host__ __device__ __forceinline__ int canon(int row, int k) {
     return (row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4;
 }
 
@@ -80,8 +93,9 @@ struct TcTask {
     int64_t pair_off;
     int32_t npairs, nrt, nkc, p_out2;   // p_out2 = complex rows P_out
     int32_t p_in2;                      // complex columns P_in
-    int32_t pad;
-    int64_t src_base, dst_base;         // complex offsets of the level arrays
+    int32_t stride_f;                   // floats per box vector in the hi/lo planes
+    int64_t plane_base;                 // float offset of the level in the planes
+    int64_t dst_base;                   // complex offset of the target level
 };
 struct TcTile {
     int32_t task, rt, col0, ncol;
@@ -112,16 +126,44 @@ __global__ void k_tc_pack(const cd* __restrict__ T, int rows, int cols, int nrt,
     }
 }
 
+// hi/lo planes of the multipoles of the tensor-core levels: box vectors of
+// 2P floats padded to stride_f (multiple of 4) with zeros.
+struct SplitLevel {
+    int64_t src_base;     // complex offset of the level in the multipoles
+    int64_t plane_base;   // float offset in the planes
+    int32_t nbox, P, stride_f, pad;
+};
+__global__ void k_tc_split(const SplitLevel* __restrict__ lv, int nlev, const cf* __restrict__ mp,
+                           float* __restrict__ hi, float* __restrict__ lo) {
+    int l = blockIdx.y;
+    if (l >= nlev) return;
+    SplitLevel L = lv[l];
+    int64_t total = (int64_t)L.nbox * L.stride_f;
+    const float* src = (const float*)(mp + L.src_base);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t b = i / L.stride_f;
+        int k = (int)(i % L.stride_f);
+        float v = k < 2 * L.P ? src[b * 2 * L.P + k] : 0.f;
+        float h = tf32_hi(v);
+        hi[L.plane_base + i] = h;
+        lo[L.plane_base + i] = v - h;
+    }
+}
+
 __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
                                                       const float* __restrict__ Abuf, const int32_t* __restrict__ src_idx,
-                                                      const int32_t* __restrict__ dst_idx, const cf* __restrict__ src,
-                                                      cf* __restrict__ dst, int* __restrict__ err) {
+                                                      const int32_t* __restrict__ dst_idx,
+                                                      const float* __restrict__ plane_hi,
+                                                      const float* __restrict__ plane_lo, cf* __restrict__ dst,
+                                                      int* __restrict__ err) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
+    __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
+    __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_holder;
     __shared__ int s_src[TC_NMAX];
     __shared__ int s_dst[TC_NMAX];
-    // 1024-byte aligned stage buffers
+    __shared__ int s_fail;
     uint32_t raw = smem_u32(smem_raw);
     uint32_t pad = (1024 - (raw & 1023)) & 1023;
     float* stage0 = (float*)(smem_raw + pad);
@@ -131,6 +173,7 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int ncol = tl.ncol;
     const int nmma = (ncol + 15) & ~15;
+    const int nkc = tk.nkc;
     for (int j = tid; j < TC_NMAX; j += blockDim.x) {
         bool ok = j < ncol;
         s_src[j] = ok ? src_idx[tk.pair_off + tl.col0 + j] : -1;
@@ -142,88 +185,113 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[1])), "r"(1));
+        s_fail = 0;
+        for (int s = 0; s < TC_STAGES; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_bar[s])), "r"(NPROD + 1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty_bar[s])), "r"(1));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done_bar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_holder;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) |
-                           ((uint32_t)(TC_M >> 4) << 24);
-    const float* Atile = Abuf + tk.a_off + (int64_t)tl.rt * tk.nkc * 2 * A_BLOCK;
-    const int kreal = 2 * tk.p_in2;
-    bool failed = false;
 
-    for (int c = 0; c < tk.nkc; ++c) {
-        const int s = c & 1;
-        float* st = stage0 + s * STAGE_FLOATS;
-        float* sAh = st;
-        float* sAl = st + A_BLOCK;
-        float* sBh = st + 2 * A_BLOCK;
-        float* sBl = st + 2 * A_BLOCK + B_BLOCK;
-        if (c >= 2) {
-            if (!mbar_wait(smem_u32(&bars[s]), ((c - 2) >> 1) & 1)) failed = true;
-        }
-        if (__syncthreads_or(failed)) {
-            failed = true;
-            break;
-        }
-        // A: pre-split canonical tiles, contiguous (hi block then lo block)
-        {
-            const float4* g = (const float4*)(Atile + (int64_t)c * 2 * A_BLOCK);
-            float4* d = (float4*)sAh;   // sAl follows sAh contiguously
-            for (int i = tid; i < 2 * A_BLOCK / 4; i += blockDim.x) d[i] = g[i];
-        }
-        // B: gathered source multipoles (interleaved re/im = real K), split
-        for (int i = tid; i < nmma * (TC_KC / 2); i += blockDim.x) {
-            int j = i / (TC_KC / 2);
-            int kp = (i % (TC_KC / 2)) * 2;           // even real k within the chunk
-            int kg = c * TC_KC + kp;
-            float2 v = make_float2(0.f, 0.f);
-            int sb = s_src[j];
-            if (sb >= 0 && kg < kreal) {
-                cf z = src[tk.src_base + (int64_t)sb * tk.p_in2 + (kg >> 1)];
-                v = make_float2(z.re, z.im);
+    if (warp < 6) {
+        // ---------------- B producers: 16-byte cp.async pieces -------------
+        const int npieces = nmma * (TC_KC / 4) * 2;   // columns x K pieces x {hi, lo}
+        for (int c = 0; c < nkc; ++c) {
+            const int s = c % TC_STAGES, u = c / TC_STAGES;
+            if (u > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (u - 1) & 1)) {
+                atomicExch(&s_fail, 1);
+                break;
             }
-            float2 h = make_float2(tf32_hi(v.x), tf32_hi(v.y));
-            float2 l = make_float2(v.x - h.x, v.y - h.y);
-            int off = canon(j, kp) >> 2;
-            *(float2*)(sBh + off) = h;
-            *(float2*)(sBl + off) = l;
+            float* sBh = stage0 + s * STAGE_FLOATS + 2 * A_BLOCK;
+            for (int i = tid; i < npieces; i += NPROD) {
+                int plane = i & 1;
+                int q = (i >> 1) % (TC_KC / 4);
+                int j = (i >> 1) / (TC_KC / 4);
+                int k = c * TC_KC + 4 * q;
+                int sb = s_src[j];
+                const float* pl = plane ? plane_lo : plane_hi;
+                const float* g = pl + tk.plane_base;   // valid address even when nothing is read
+                int bytes = 0;
+                if (sb >= 0 && k < tk.stride_f) {
+                    g = pl + tk.plane_base + (int64_t)sb * tk.stride_f + k;
+                    bytes = 16;
+                }
+                uint32_t d = smem_u32(sBh + plane * B_BLOCK) + canon(j, 4 * q);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g), "r"(bytes));
+            }
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full_bar[s])));
         }
-        asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
-        if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            uint32_t aH = smem_u32(sAh), aL = smem_u32(sAl), bH = smem_u32(sBh), bL = smem_u32(sBl);
+        asm volatile("cp.async.wait_all;");
+    } else if (warp == 6) {
+        // ---------------- A producer: one bulk copy per stage ----------------
+        if (lane == 0) {
+            const float* Atile = Abuf + tk.a_off + (int64_t)tl.rt * nkc * 2 * A_BLOCK;
+            for (int c = 0; c < nkc; ++c) {
+                const int s = c % TC_STAGES, u = c / TC_STAGES;
+                if (u > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (u - 1) & 1)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                uint32_t fb = smem_u32(&full_bar[s]);
+                uint32_t dA = smem_u32(stage0 + s * STAGE_FLOATS);
+                const float* g = Atile + (int64_t)c * 2 * A_BLOCK;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * A_BLOCK * 4));
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dA),
+                    "l"(g), "r"(2 * A_BLOCK * 4), "r"(fb));
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---------------- MMA issuer ----------------------------------------
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) |
+                                   ((uint32_t)(TC_M >> 4) << 24);
+            for (int c = 0; c < nkc; ++c) {
+                const int s = c % TC_STAGES, u = c / TC_STAGES;
+                if (!mbar_wait(smem_u32(&full_bar[s]), u & 1)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                float* st = stage0 + s * STAGE_FLOATS;
+                uint32_t aH = smem_u32(st), aL = smem_u32(st + A_BLOCK);
+                uint32_t bH = smem_u32(st + 2 * A_BLOCK), bL = smem_u32(st + 2 * A_BLOCK + B_BLOCK);
 #pragma unroll
-            for (int ks = 0; ks < TC_KC / 8; ++ks) {
-                uint32_t o = ks * 2 * LBO;
-                uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
-                mma_tf32(tmem, umma_desc(aH + o), umma_desc(bH + o), idesc, first);
-                mma_tf32(tmem, umma_desc(aH + o), umma_desc(bL + o), idesc, 1u);
-                mma_tf32(tmem, umma_desc(aL + o), umma_desc(bH + o), idesc, 1u);
+                for (int ks = 0; ks < TC_KC / 8; ++ks) {
+                    uint32_t o = ks * 2 * LBO;
+                    uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
+                    mma_tf32(tmem, umma_desc(aH + o), umma_desc(bH + o), idesc, first);
+                    mma_tf32(tmem, umma_desc(aH + o), umma_desc(bL + o), idesc, 1u);
+                    mma_tf32(tmem, umma_desc(aL + o), umma_desc(bH + o), idesc, 1u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                    smem_u32(&empty_bar[s])));
             }
+            // completion of every MMA issued above (also on failure)
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&bars[s])));
+                smem_u32(&done_bar)));
         }
+        __syncwarp();
     }
-    // all MMAs of the tile: the last commit covers every earlier MMA
-    const int last = tk.nkc - 1;
-    bool done = mbar_wait(smem_u32(&bars[last & 1]), (last >> 1) & 1);
-    if (!done || failed) {
-        if (tid == 0) atomicExch(err, 1);
-    }
+
+    // ---------------- epilogue ------------------------------------------------
+    bool done = mbar_wait(smem_u32(&done_bar), 0);
+    __syncthreads();
+    const bool ok = done && s_fail == 0;
+    if (!ok && tid == 0) atomicExch(err, 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
-    if (done && !failed) {
-        // epilogue: warps w and w+4 share lane quadrant w%4, split the columns
+    if (ok) {
         const int quad = warp & 3;
         const int half = warp >> 2;
         const int rr = tl.rt * TC_M + quad * 32 + lane;      // real output row
         const int r = rr >> 1, part = rr & 1;
-        const int cmid = ((nmma / 16 + 1) / 2) * 16;       // split on 16-column boundaries
+        const int cmid = ((nmma / 16 + 1) / 2) * 16;        // split on 16-column boundaries
         const int cbeg = half ? cmid : 0;
         const int cend = half ? nmma : cmid;
         for (int c0 = cbeg; c0 < cend; c0 += 16) {
@@ -239,13 +307,17 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
 #pragma unroll
                 for (int q = 0; q < 16; ++q) {
                     int j = c0 + q;
-                    int db = j < TC_NMAX ? s_dst[j] : -1;
+                    int db = s_dst[j];
                     if (db < 0) continue;
                     float* d = (float*)(dst + tk.dst_base + (int64_t)db * tk.p_out2 + r) + part;
                     atomicAdd(d, __uint_as_float(v[q]));
                 }
             }
         }
+    } else if (warp == 6 && lane == 0) {
+        // drain the bulk copies this CTA may still have in flight
+        for (int c = max(0, nkc - TC_STAGES); c < nkc; ++c)
+            mbar_wait(smem_u32(&full_bar[c % TC_STAGES]), (c / TC_STAGES) & 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -256,14 +328,19 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
 struct TcPlanImpl {
     std::vector<TcTask> h_tasks;
     std::vector<TcTile> h_tiles;
+    std::vector<SplitLevel> h_split;
     TcTask* tasks = nullptr;
     TcTile* tiles = nullptr;
+    SplitLevel* split = nullptr;
     float* A = nullptr;
+    float* plane_hi = nullptr;
+    float* plane_lo = nullptr;
     int* err = nullptr;
-    int64_t a_floats = 0;
+    int64_t a_floats = 0, plane_floats = 0;
+    int max_split = 0;
 };
 
-size_t fb_tc_smem_bytes() { return (size_t)2 * STAGE_FLOATS * sizeof(float) + 1024; }
+size_t fb_tc_smem_bytes() { return (size_t)TC_STAGES * STAGE_FLOATS * sizeof(float) + 1024; }
 
 // Builds the tensor-core plan for the M2L groups of the levels in `levels`.
 fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cudaStream_t s) {
@@ -272,8 +349,18 @@ fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cu
     *slot = pl;
     for (int l : levels) {
         int P = op->p[l] * op->p[l];
+        SplitLevel sl;
+        sl.src_base = op->lev_off[l];
+        sl.plane_base = pl->plane_floats;
+        sl.nbox = t->nbox[l];
+        sl.P = P;
+        sl.stride_f = (2 * P + TC_KC - 1) / TC_KC * TC_KC;   // whole K chunks, 16-byte pieces
+        sl.pad = 0;
+        pl->h_split.push_back(sl);
+        pl->plane_floats += (int64_t)sl.nbox * sl.stride_f;
+        pl->max_split = std::max<int>(pl->max_split, (int)std::min<int64_t>((int64_t)sl.nbox * sl.stride_f / 256 + 1, 4096));
         int nrt = (2 * P + TC_M - 1) / TC_M;
-        int nkc = (2 * P + TC_KC - 1) / TC_KC;
+        int nkc = sl.stride_f / TC_KC;
         for (int c = 0; c < FB_NOFF; ++c) {
             int64_t g0 = t->m2l_group[(size_t)l * FB_NOFF + c], g1 = t->m2l_group[(size_t)l * FB_NOFF + c + 1];
             if (g1 == g0) continue;
@@ -285,8 +372,8 @@ fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cu
             tk.nkc = nkc;
             tk.p_out2 = P;
             tk.p_in2 = P;
-            tk.pad = 0;
-            tk.src_base = op->lev_off[l];
+            tk.stride_f = sl.stride_f;
+            tk.plane_base = sl.plane_base;
             tk.dst_base = op->lev_off[l];
             int ti = (int)pl->h_tasks.size();
             pl->h_tasks.push_back(tk);
@@ -298,13 +385,18 @@ fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cu
     }
     if (pl->h_tasks.empty()) return FB_OK;
     FB_CHECK(dalloc(&pl->A, pl->a_floats));
+    FB_CHECK(dalloc(&pl->plane_hi, pl->plane_floats));
+    FB_CHECK(dalloc(&pl->plane_lo, pl->plane_floats));
     FB_CHECK(dalloc(&pl->tasks, pl->h_tasks.size()));
     FB_CHECK(dalloc(&pl->tiles, pl->h_tiles.size()));
+    FB_CHECK(dalloc(&pl->split, pl->h_split.size()));
     FB_CHECK(dalloc(&pl->err, 1));
     FB_CUDA(cudaMemsetAsync(pl->err, 0, sizeof(int), s));
     FB_CUDA(cudaMemcpyAsync(pl->tasks, pl->h_tasks.data(), sizeof(TcTask) * pl->h_tasks.size(),
                             cudaMemcpyHostToDevice, s));
     FB_CUDA(cudaMemcpyAsync(pl->tiles, pl->h_tiles.data(), sizeof(TcTile) * pl->h_tiles.size(),
+                            cudaMemcpyHostToDevice, s));
+    FB_CUDA(cudaMemcpyAsync(pl->split, pl->h_split.data(), sizeof(SplitLevel) * pl->h_split.size(),
                             cudaMemcpyHostToDevice, s));
     size_t ti = 0;
     for (int l : levels) {
@@ -326,10 +418,12 @@ fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cu
 fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s) {
     TcPlanImpl* pl = (TcPlanImpl*)plan;
     if (!pl || pl->h_tiles.empty()) return FB_OK;
+    dim3 sg(pl->max_split, (unsigned)pl->h_split.size());
+    k_tc_split<<<sg, 256, 0, s>>>(pl->split, (int)pl->h_split.size(), src, pl->plane_hi, pl->plane_lo);
     k_trans_tc<<<(unsigned)pl->h_tiles.size(), 256, fb_tc_smem_bytes(), s>>>(
-        pl->tasks, pl->tiles, pl->A, op->tree->m2l_src, op->tree->m2l_dst, src, dst, pl->err);
+        pl->tasks, pl->tiles, pl->A, op->tree->m2l_src, op->tree->m2l_dst, pl->plane_hi, pl->plane_lo, dst, pl->err);
     FB_LAUNCH_CHECK();
-    fb_count_launch();
+    fb_count_launch(2);
     return FB_OK;
 }
 
@@ -349,8 +443,11 @@ void fb_tc_free(void*& plan) {
     TcPlanImpl* pl = (TcPlanImpl*)plan;
     if (!pl) return;
     dfree(pl->A);
+    dfree(pl->plane_hi);
+    dfree(pl->plane_lo);
     dfree(pl->tasks);
     dfree(pl->tiles);
+    dfree(pl->split);
     dfree(pl->err);
     delete pl;
     plan = nullptr;

@@ -424,6 +424,8 @@ void fb_tree_free(fb_tree* t) {
     dfree(t->ulist);
     dfree(t->m2l_src);
     dfree(t->m2l_dst);
+    dfree(t->rot64);
+    dfree(t->rot32);
     delete t;
 }
 
