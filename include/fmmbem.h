@@ -242,6 +242,12 @@ FB_API fb_status fb_operator_set_translation(fb_op* op, int method);
  * the buffer's address cannot be resolved. */
 FB_API fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y, void* stream);
 
+/* Measured FMA throughput of the current device (TFLOP/s, 2 flops per FMA)
+ * for FP32 and FP64 (either pointer may be NULL): the ALU ceilings of the
+ * CUDA-core kernels.  Launches two short kernels per type and synchronises
+ * the stream. */
+FB_API fb_status fb_measure_alu_peaks(double* fp32_tflops, double* fp64_tflops, void* stream);
+
 /* Tracing: running total of kernel launches issued by the library in this
  * process (setup and apply); differences bracket a region of interest. */
 FB_API long long fb_kernel_launches(void);

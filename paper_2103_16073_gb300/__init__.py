@@ -28,7 +28,7 @@ __all__ = [
     "fb_operator_create", "fb_operator_apply", "fb_operator_info", "fb_operator_export",
     "fb_operator_destroy", "fb_gamma_monopole", "fb_precond_create", "fb_precond_destroy",
     "fb_fgmres_solve", "fb_eval_field", "fb_operator_apply_timed", "fb_kernel_launches",
-    "fb_operator_apply_noalloc", "fb_operator_set_translation",
+    "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -340,3 +340,14 @@ lib.fb_operator_set_translation.argtypes = [C.c_void_p, C.c_int]
 
 def fb_operator_set_translation(op, method):
     _check(lib.fb_operator_set_translation(op, int(method)))
+
+
+lib.fb_measure_alu_peaks.restype = C.c_int
+lib.fb_measure_alu_peaks.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+
+
+def fb_measure_alu_peaks(stream=None):
+    """Measured (FP32, FP64) FMA throughput of the current device in TFLOP/s."""
+    a, b = C.c_double(), C.c_double()
+    _check(lib.fb_measure_alu_peaks(C.byref(a), C.byref(b), _stream(stream)))
+    return a.value, b.value

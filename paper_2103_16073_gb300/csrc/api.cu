@@ -19,6 +19,7 @@ fb_status fb_tree_export_impl(const fb_tree*, int, int, int64_t*, int64_t*);
 fb_status fb_fgmres_impl(fb_op*, fb_precond*, const cd*, cd*, const fb_solver_opts*, fb_solve_info*, cudaStream_t);
 fb_status fb_precond_create_impl(fb_op*, int, cudaStream_t, fb_precond**);
 void fb_precond_free(fb_precond*);
+fb_status fb_alu_peaks_impl(double*, double*, cudaStream_t);
 
 static std::atomic<long long> g_launches{0};
 void fb_count_launch(long long n) { g_launches += n; }
@@ -201,6 +202,10 @@ fb_status fb_operator_apply(fb_op* op, const double* x, double* y, int memspace,
 }
 
 long long fb_kernel_launches(void) { return g_launches.load(); }
+
+fb_status fb_measure_alu_peaks(double* fp32_tflops, double* fp64_tflops, void* stream) {
+    return fb_alu_peaks_impl(fp32_tflops, fp64_tflops, as_stream(stream));
+}
 
 fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* stream, double* phase_ms) {
     if (!op || !x || !y || !phase_ms) return fb_fail(FB_ERR_ARG, "NULL argument");

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <deque>
 #include <string>
 #include <vector>
 
@@ -151,11 +152,15 @@ struct fb_tree {
     int32_t* oct_parent[FB_MAXLEV + 1] = {nullptr};
     std::vector<int64_t> oct_group[FB_MAXLEV + 1];   // 9 prefix offsets
     int64_t nlist_u = 0;
-    // rotation blocks of the translation directions (shared by operators)
-    cd* rot64 = nullptr;
-    cf* rot32 = nullptr;
-    int rot_P = 0, rot_ndir = 0;
-    int64_t rot_per_dir = 0;
+    // rotation blocks of the translation directions, one set per degree
+    // bound P, shared by every operator built on this tree
+    struct RotSet {
+        cd* r64 = nullptr;
+        cf* r32 = nullptr;
+        int P = 0, ndir = 0;
+        int64_t per_dir = 0;
+    };
+    std::deque<RotSet> rot_sets;   // deque: references stay valid on push_back
 };
 
 // ----------------------------------------------------------- operator ----
@@ -204,6 +209,15 @@ struct RcrPlan {
     int ntiles = 0;
     int nb = 1;          // box pairs per CTA
     size_t smem = 0;     // dynamic shared memory per CTA (bytes)
+};
+
+// A group of box pairs sharing one composed translation matrix (job) on the
+// tensor cores: sources from level src_level, targets in level dst_level.
+struct TcGroup {
+    int job;
+    int64_t pair_off;
+    int32_t npairs;
+    int src_level, dst_level;
 };
 
 // One composed translation matrix T = D_out^H C D_in to build.
@@ -256,6 +270,11 @@ struct fb_op {
     void* tc_plan_all = nullptr;
     int tc_level[FB_MAXLEV + 1] = {0};      // 1: M2L of this level on tensor cores (auto)
     RcrPlan m2l_rcr_rest;                   // RCR M2L of the other levels
+    void* tc_m2m[FB_MAXLEV + 1] = {nullptr};   // tensor-core M2M / L2L per child level
+    void* tc_l2l[FB_MAXLEV + 1] = {nullptr};
+    std::vector<int> m2l_job;               // (level, offset) -> compose job
+    int m2m_job[FB_MAXLEV + 1][8];
+    int l2l_job[FB_MAXLEV + 1][8];
     int method = 0;                         // FB_TRANS_*
     std::vector<ComposeJob> h_jobs;         // composed matrices (built on demand)
     std::vector<int> h_job_level, h_job_m2l;
@@ -296,10 +315,13 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s);
 fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt = nullptr);
 fb_status fb_fmm_apply_noalloc(fb_op* op, const cd* x, cd* y, cudaStream_t s);
 fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize);
-fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, cudaStream_t s);
+fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, cudaStream_t s,
+                            const fb_tree::RotSet** out);
 fb_status fb_compose_jobs(fb_op* op, const std::vector<int>& which, cudaStream_t s);
 fb_status fb_compose_all(fb_op* op, cudaStream_t s);
 fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cudaStream_t s);
+fb_status fb_tc_build_groups(fb_op* op, const std::vector<TcGroup>& groups, const int32_t* src_idx,
+                             const int32_t* dst_idx, void** slot, cudaStream_t s);
 fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s);
 fb_status fb_tc_check(const fb_op* op);
 void fb_tc_free(void*& plan);

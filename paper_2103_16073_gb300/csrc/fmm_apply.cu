@@ -316,8 +316,10 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
     const cx<R>* rot = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->rot64 : (const void*)op->rot32);
     const cx<R>* coax = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->coax64 : (const void*)op->coax32);
     const bool composed = op->method == FB_TRANS_COMPOSED;
+    const bool auto_tc = sizeof(R) == 4 && op->method == FB_TRANS_AUTO;
     for (int l = L; l >= 3; --l) {
         if (composed) FB_CHECK(run_plan<R>(op->m2m[l], T, mp, mp, s));
+        else if (auto_tc && op->tc_m2m[l]) FB_CHECK(fb_tc_run(op, op->tc_m2m[l], (const cf*)mp, (cf*)mp, s));
         else FB_CHECK(run_rcr<R>(op->m2m_rcr[l], rot, coax, mp, mp, s));
     }
     mark(2);
@@ -346,6 +348,7 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
     mark(4);
     for (int l = 3; l <= L; ++l) {
         if (composed) FB_CHECK(run_plan<R>(op->l2l[l], T, loc, loc, s));
+        else if (auto_tc && op->tc_l2l[l]) FB_CHECK(fb_tc_run(op, op->tc_l2l[l], (const cf*)loc, (cf*)loc, s));
         else FB_CHECK(run_rcr<R>(op->l2l_rcr[l], rot, coax, loc, loc, s));
     }
     mark(5);
@@ -394,6 +397,10 @@ void fb_fmm_destroy(fb_op* op) {
     free_plan(op->m2l_rcr_rest);
     fb_tc_free(op->tc_plan);
     fb_tc_free(op->tc_plan_all);
+    for (int l = 0; l <= FB_MAXLEV; ++l) {
+        fb_tc_free(op->tc_m2m[l]);
+        fb_tc_free(op->tc_l2l[l]);
+    }
     for (int l = 0; l <= FB_MAXLEV; ++l) {
         free_plan(op->m2m[l]);
         free_plan(op->l2l[l]);

@@ -378,11 +378,14 @@ __global__ void k_box_centers(const uint32_t* keys, int n, int level, double ox,
 // Rotation blocks D^n (n < P) of every direction, by projection quadrature
 // (definition of the rotation coefficients, exact for the band limit),
 // cached in the tree and recomputed only when a larger P is needed.
-fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, cudaStream_t s) {
+fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, cudaStream_t s,
+                            const fb_tree::RotSet** out) {
     int ndir = (int)dirs.size() / 3;
-    if (t->rot64 && t->rot_P >= P && t->rot_ndir == ndir) return FB_OK;
-    dfree(t->rot64);
-    dfree(t->rot32);
+    for (const auto& rs : t->rot_sets)
+        if (rs.P == P && rs.ndir == ndir) {
+            *out = &rs;
+            return FB_OK;
+        }
     int Prot = P;
     int64_t per_dir = (int64_t)Prot * (2 * Prot - 1) * (2 * Prot + 1) / 3;
     int nq = Prot + 1, nphi = 2 * Prot + 1, npts = nq * nphi;
@@ -417,13 +420,20 @@ fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, 
         dfree(rot);
         return fb_fail(FB_ERR_CUDA, std::string("rotation setup: ") + cudaGetErrorString(e));
     }
-    t->rot64 = rot;
-    t->rot_P = Prot;
-    t->rot_per_dir = per_dir;
-    t->rot_ndir = ndir;
-    FB_CHECK(dalloc(&t->rot32, (size_t)ndir * per_dir));
-    k_d2f<<<div_up((int64_t)ndir * per_dir, 256), 256, 0, s>>>(t->rot64, t->rot32, (int64_t)ndir * per_dir);
+    fb_tree::RotSet rs;
+    rs.r64 = rot;
+    rs.P = Prot;
+    rs.per_dir = per_dir;
+    rs.ndir = ndir;
+    fb_status st2 = dalloc(&rs.r32, (size_t)ndir * per_dir);
+    if (st2 != FB_OK) {
+        dfree(rs.r64);
+        return st2;
+    }
+    k_d2f<<<div_up((int64_t)ndir * per_dir, 256), 256, 0, s>>>(rs.r64, rs.r32, (int64_t)ndir * per_dir);
     FB_LAUNCH_CHECK();
+    t->rot_sets.push_back(rs);
+    *out = &t->rot_sets.back();
     return FB_OK;
 }
 
@@ -630,10 +640,11 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
     }
     // rotation blocks of every direction up to pmax (cached in the tree: they
     // depend only on the directions, not on k or the operator)
-    FB_CHECK(fb_tree_rotations(const_cast<fb_tree*>(t), pmax, dirs, s));
-    int Prot = t->rot_P;
-    int64_t per_dir = t->rot_per_dir;
-    cd* rot = t->rot64;
+    const fb_tree::RotSet* rset = nullptr;
+    FB_CHECK(fb_tree_rotations(const_cast<fb_tree*>(t), pmax, dirs, s, &rset));
+    int Prot = rset->P;
+    int64_t per_dir = rset->per_dir;
+    cd* rot = rset->r64;
     // composed translation matrices
     std::vector<ComposeJob> jobs;
     int64_t T_total = 0;
@@ -662,7 +673,7 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
     op->coax_count = std::max<int64_t>(coax_total, 1);
     coax = nullptr;
     op->rot64 = rot;
-    op->rot32 = t->rot32;
+    op->rot32 = rset->r32;
     op->rot_count = (int64_t)ndir * per_dir;
     op->Prot = Prot;
     op->per_dir = per_dir;
@@ -677,6 +688,15 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         op->h_job_m2l.push_back(r.which == 0 ? 1 : 0);
     }
     op->job_done.assign(jobs.size(), 0);
+    op->m2l_job.assign((size_t)(L + 1) * FB_NOFF, -1);
+    for (int l = 0; l <= FB_MAXLEV; ++l)
+        for (int o = 0; o < 8; ++o) op->m2m_job[l][o] = op->l2l_job[l][o] = -1;
+    for (size_t j = 0; j < reqs.size(); ++j) {
+        const MatReq& r = reqs[j];
+        if (r.which == 0) op->m2l_job[(size_t)r.level * FB_NOFF + r.code] = (int)j;
+        else if (r.which == 1) op->m2m_job[r.level][r.code] = (int)j;
+        else op->l2l_job[r.level][r.code] = (int)j;
+    }
     if (e != cudaSuccess) return fb_fail(FB_ERR_CUDA, std::string("translation setup: ") + cudaGetErrorString(e));
     // RCR plans: one task per (level, offset) / (level, octant) group
     {
@@ -735,6 +755,25 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
                 if (op->h_job_m2l[j] && op->tc_level[op->h_job_level[j]]) need.push_back((int)j);
             FB_CHECK(fb_compose_jobs(op, need, s));
             FB_CHECK(fb_tc_build(op, tc_levels, &op->tc_plan, s));
+        }
+        // M2M / L2L of child levels with >= 48 boxes per octant on average
+        if (op->prec == FB_PREC_MIXED_FMM) {
+            for (int l = 3; l <= L; ++l) {
+                if (t->nbox[l] < 48 * 8) continue;
+                std::vector<int> need;
+                std::vector<TcGroup> up, down;
+                for (int o = 0; o < 8; ++o) {
+                    int64_t g0 = t->oct_group[l][o], g1 = t->oct_group[l][o + 1];
+                    if (g1 == g0) continue;
+                    need.push_back(op->m2m_job[l][o]);
+                    need.push_back(op->l2l_job[l][o]);
+                    up.push_back(TcGroup{op->m2m_job[l][o], g0, (int32_t)(g1 - g0), l, l - 1});
+                    down.push_back(TcGroup{op->l2l_job[l][o], g0, (int32_t)(g1 - g0), l - 1, l});
+                }
+                FB_CHECK(fb_compose_jobs(op, need, s));
+                FB_CHECK(fb_tc_build_groups(op, up, t->oct_child[l], t->oct_parent[l], &op->tc_m2m[l], s));
+                FB_CHECK(fb_tc_build_groups(op, down, t->oct_parent[l], t->oct_child[l], &op->tc_l2l[l], s));
+            }
         }
         for (int l = 3; l <= L; ++l) {
             FB_CHECK(fb_rcr_upload(op->m2m_rcr[l], t->oct_child[l], t->oct_parent[l], csz));

@@ -336,52 +336,62 @@ struct TcPlanImpl {
     float* plane_hi = nullptr;
     float* plane_lo = nullptr;
     int* err = nullptr;
+    const int32_t* src_idx = nullptr;
+    const int32_t* dst_idx = nullptr;
     int64_t a_floats = 0, plane_floats = 0;
     int max_split = 0;
 };
 
 size_t fb_tc_smem_bytes() { return (size_t)TC_STAGES * STAGE_FLOATS * sizeof(float) + 1024; }
 
-// Builds the tensor-core plan for the M2L groups of the levels in `levels`.
-fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cudaStream_t s) {
+// Builds a tensor-core plan for groups of box pairs; each group shares one
+// composed translation matrix (job) and reads the source expansions of one
+// level (hi/lo planes split once per run).
+fb_status fb_tc_build_groups(fb_op* op, const std::vector<TcGroup>& groups, const int32_t* src_idx,
+                             const int32_t* dst_idx, void** slot, cudaStream_t s) {
     const fb_tree* t = op->tree;
     TcPlanImpl* pl = new TcPlanImpl();
     *slot = pl;
-    for (int l : levels) {
-        int P = op->p[l] * op->p[l];
-        SplitLevel sl;
-        sl.src_base = op->lev_off[l];
-        sl.plane_base = pl->plane_floats;
-        sl.nbox = t->nbox[l];
-        sl.P = P;
-        sl.stride_f = (2 * P + TC_KC - 1) / TC_KC * TC_KC;   // whole K chunks, 16-byte pieces
-        sl.pad = 0;
-        pl->h_split.push_back(sl);
-        pl->plane_floats += (int64_t)sl.nbox * sl.stride_f;
-        pl->max_split = std::max<int>(pl->max_split, (int)std::min<int64_t>((int64_t)sl.nbox * sl.stride_f / 256 + 1, 4096));
-        int nrt = (2 * P + TC_M - 1) / TC_M;
-        int nkc = sl.stride_f / TC_KC;
-        for (int c = 0; c < FB_NOFF; ++c) {
-            int64_t g0 = t->m2l_group[(size_t)l * FB_NOFF + c], g1 = t->m2l_group[(size_t)l * FB_NOFF + c + 1];
-            if (g1 == g0) continue;
-            TcTask tk;
-            tk.a_off = pl->a_floats;
-            tk.pair_off = g0;
-            tk.npairs = (int32_t)(g1 - g0);
-            tk.nrt = nrt;
-            tk.nkc = nkc;
-            tk.p_out2 = P;
-            tk.p_in2 = P;
-            tk.stride_f = sl.stride_f;
-            tk.plane_base = sl.plane_base;
-            tk.dst_base = op->lev_off[l];
-            int ti = (int)pl->h_tasks.size();
-            pl->h_tasks.push_back(tk);
-            for (int rt = 0; rt < nrt; ++rt)
-                for (int c0 = 0; c0 < tk.npairs; c0 += TC_NMAX)
-                    pl->h_tiles.push_back(TcTile{ti, rt, c0, std::min(TC_NMAX, tk.npairs - c0)});
-            pl->a_floats += (int64_t)nrt * nkc * 2 * A_BLOCK;
+    pl->src_idx = src_idx;
+    pl->dst_idx = dst_idx;
+    std::vector<int> split_of(FB_MAXLEV + 1, -1);
+    for (const TcGroup& g : groups) {
+        int ls = g.src_level;
+        if (split_of[ls] < 0) {
+            int Pin = op->p[ls] * op->p[ls];
+            SplitLevel sl;
+            sl.src_base = op->lev_off[ls];
+            sl.plane_base = pl->plane_floats;
+            sl.nbox = t->nbox[ls];
+            sl.P = Pin;
+            sl.stride_f = (2 * Pin + TC_KC - 1) / TC_KC * TC_KC;   // whole K chunks, 16-byte pieces
+            sl.pad = 0;
+            split_of[ls] = (int)pl->h_split.size();
+            pl->h_split.push_back(sl);
+            pl->plane_floats += (int64_t)sl.nbox * sl.stride_f;
+            pl->max_split = std::max<int>(pl->max_split,
+                                          (int)std::min<int64_t>((int64_t)sl.nbox * sl.stride_f / 256 + 1, 4096));
         }
+        const SplitLevel& sl = pl->h_split[split_of[ls]];
+        const ComposeJob& jb = op->h_jobs[g.job];
+        int Pout = jb.p_out * jb.p_out;
+        TcTask tk;
+        tk.a_off = pl->a_floats;
+        tk.pair_off = g.pair_off;
+        tk.npairs = g.npairs;
+        tk.nrt = (2 * Pout + TC_M - 1) / TC_M;
+        tk.nkc = sl.stride_f / TC_KC;
+        tk.p_out2 = Pout;
+        tk.p_in2 = sl.P;
+        tk.stride_f = sl.stride_f;
+        tk.plane_base = sl.plane_base;
+        tk.dst_base = op->lev_off[g.dst_level];
+        int ti = (int)pl->h_tasks.size();
+        pl->h_tasks.push_back(tk);
+        for (int rt = 0; rt < tk.nrt; ++rt)
+            for (int c0 = 0; c0 < tk.npairs; c0 += TC_NMAX)
+                pl->h_tiles.push_back(TcTile{ti, rt, c0, std::min(TC_NMAX, tk.npairs - c0)});
+        pl->a_floats += (int64_t)tk.nrt * tk.nkc * 2 * A_BLOCK;
     }
     if (pl->h_tasks.empty()) return FB_OK;
     FB_CHECK(dalloc(&pl->A, pl->a_floats));
@@ -398,21 +408,30 @@ fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cu
                             cudaMemcpyHostToDevice, s));
     FB_CUDA(cudaMemcpyAsync(pl->split, pl->h_split.data(), sizeof(SplitLevel) * pl->h_split.size(),
                             cudaMemcpyHostToDevice, s));
-    size_t ti = 0;
-    for (int l : levels) {
-        for (int c = 0; c < FB_NOFF; ++c) {
-            int64_t g0 = t->m2l_group[(size_t)l * FB_NOFF + c], g1 = t->m2l_group[(size_t)l * FB_NOFF + c + 1];
-            if (g1 == g0) continue;
-            const TcTask& tk = pl->h_tasks[ti++];
-            int64_t toff = op->m2l_toff[(size_t)l * FB_NOFF + c];
-            int64_t total = (int64_t)tk.nrt * tk.nkc * A_BLOCK;
-            k_tc_pack<<<(unsigned)std::min<int64_t>(div_up(total, 256), 4096), 256, 0, s>>>(
-                op->T64 + toff, tk.p_out2, tk.p_in2, tk.nrt, tk.nkc, pl->A + tk.a_off);
-        }
+    for (size_t i = 0; i < groups.size(); ++i) {
+        const TcTask& tk = pl->h_tasks[i];
+        const ComposeJob& jb = op->h_jobs[groups[i].job];
+        int64_t total = (int64_t)tk.nrt * tk.nkc * A_BLOCK;
+        k_tc_pack<<<(unsigned)std::min<int64_t>(div_up(total, 256), 4096), 256, 0, s>>>(
+            op->T64 + jb.t_off, tk.p_out2, jb.p_in * jb.p_in, tk.nrt, tk.nkc, pl->A + tk.a_off);
     }
     FB_LAUNCH_CHECK();
     FB_CUDA(cudaFuncSetAttribute(k_trans_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_tc_smem_bytes()));
     return FB_OK;
+}
+
+// M2L groups (every non-empty (level, offset) group) of the given levels.
+fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cudaStream_t s) {
+    const fb_tree* t = op->tree;
+    std::vector<TcGroup> groups;
+    for (int l : levels)
+        for (int c = 0; c < FB_NOFF; ++c) {
+            int64_t g0 = t->m2l_group[(size_t)l * FB_NOFF + c], g1 = t->m2l_group[(size_t)l * FB_NOFF + c + 1];
+            if (g1 == g0) continue;
+            int job = op->m2l_job[(size_t)l * FB_NOFF + c];
+            groups.push_back(TcGroup{job, g0, (int32_t)(g1 - g0), l, l});
+        }
+    return fb_tc_build_groups(op, groups, t->m2l_src, t->m2l_dst, slot, s);
 }
 
 fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s) {
@@ -421,7 +440,7 @@ fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t 
     dim3 sg(pl->max_split, (unsigned)pl->h_split.size());
     k_tc_split<<<sg, 256, 0, s>>>(pl->split, (int)pl->h_split.size(), src, pl->plane_hi, pl->plane_lo);
     k_trans_tc<<<(unsigned)pl->h_tiles.size(), 256, fb_tc_smem_bytes(), s>>>(
-        pl->tasks, pl->tiles, pl->A, op->tree->m2l_src, op->tree->m2l_dst, pl->plane_hi, pl->plane_lo, dst, pl->err);
+        pl->tasks, pl->tiles, pl->A, pl->src_idx, pl->dst_idx, pl->plane_hi, pl->plane_lo, dst, pl->err);
     FB_LAUNCH_CHECK();
     fb_count_launch(2);
     return FB_OK;
@@ -429,7 +448,12 @@ fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t 
 
 // Error flag of the tensor-core kernel (1 = a bounded wait ran out).
 fb_status fb_tc_check(const fb_op* op) {
-    for (void* v : {op->tc_plan, op->tc_plan_all}) {
+    std::vector<void*> plans = {op->tc_plan, op->tc_plan_all};
+    for (int l = 0; l <= FB_MAXLEV; ++l) {
+        plans.push_back(op->tc_m2m[l]);
+        plans.push_back(op->tc_l2l[l]);
+    }
+    for (void* v : plans) {
         TcPlanImpl* pl = (TcPlanImpl*)v;
         if (!pl || !pl->err) continue;
         int h = 0;

@@ -424,8 +424,10 @@ void fb_tree_free(fb_tree* t) {
     dfree(t->ulist);
     dfree(t->m2l_src);
     dfree(t->m2l_dst);
-    dfree(t->rot64);
-    dfree(t->rot32);
+    for (auto& rs : t->rot_sets) {
+        dfree(rs.r64);
+        dfree(rs.r32);
+    }
     delete t;
 }
 
