@@ -78,6 +78,7 @@ typedef int fb_status;
 
 #define FB_PC_NONE 0
 #define FB_PC_BLOCK_JACOBI 1 /* inverse of each leaf's self near-field block */
+#define FB_PC_LEARNED 2      /* learned octree network refining block Jacobi */
 
 typedef struct fb_mesh fb_mesh;
 typedef struct fb_tree fb_tree;
@@ -268,6 +269,36 @@ FB_API fb_status fb_gamma_monopole(const fb_mesh* mesh, double k, const double* 
  * singular block. */
 FB_API fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out);
 FB_API void fb_precond_destroy(fb_precond* pc);
+
+/* Learned octree preconditioner (the variable preconditioner that flexible
+ * GMRES admits, Sec. 3.1 / Sec. 4): z = BJ(v) + s N(v / s), where BJ is the
+ * block-Jacobi `base` of the same FMM operator (which must outlive it),
+ * s = rms(v), and N a hierarchical network over the octree (element
+ * encoder, leaf pooling, 3 coarser pooling levels, down-sweep back to the
+ * leaves, element decoder; 64-wide features, SiLU).  Its matrix products run
+ * on the tensor cores in BF16 with FP32 accumulation; parameters, gradients
+ * and Adam moments are FP32.  Parameters start from a deterministic seeded
+ * initialisation with a small output layer (close to block Jacobi).
+ * Errors: FB_ERR_ARG if base is not block Jacobi of op. */
+FB_API fb_status fb_precond_create_learned(fb_op* op, const fb_precond* base, uint64_t seed, void* stream,
+                                           fb_precond** out);
+
+/* Parameters of a learned preconditioner as FP32 host arrays: if host_in is
+ * given they are replaced (*count must equal the parameter count); if
+ * host_out is given they are copied out; *count receives the count. */
+FB_API fb_status fb_learned_params(fb_precond* pc, float* host_out, const float* host_in, int64_t* count);
+
+/* Training objective on a batch of residual/error pairs (R, E: npairs x N
+ * complex, device, element order, pair q at offset q*N):
+ *   loss = mean_q ||z(r_q) - e_q||^2 / ||e_q||^2,  z(r) = BJ(r) + s N(r/s),
+ * and its gradient w.r.t. the parameters (FP32, host, may be NULL). */
+FB_API fb_status fb_learned_loss_and_grad(fb_precond* pc, const double* R, const double* E, int npairs,
+                                          double* loss, float* grad_host, void* stream);
+
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on the batch; *loss (may be
+ * NULL) receives the loss before the step. */
+FB_API fb_status fb_learned_train_step(fb_precond* pc, const double* R, const double* E, int npairs, double lr,
+                                       double* loss, void* stream);
 
 /* ---------------------------------------------------------------- solve -- */
 

@@ -29,6 +29,7 @@ __all__ = [
     "fb_operator_destroy", "fb_gamma_monopole", "fb_precond_create", "fb_precond_destroy",
     "fb_fgmres_solve", "fb_eval_field", "fb_operator_apply_timed", "fb_kernel_launches",
     "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
+    "fb_precond_create_learned", "fb_learned_params", "fb_learned_loss_and_grad", "fb_learned_train_step",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -351,3 +352,57 @@ def fb_measure_alu_peaks(stream=None):
     a, b = C.c_double(), C.c_double()
     _check(lib.fb_measure_alu_peaks(C.byref(a), C.byref(b), _stream(stream)))
     return a.value, b.value
+
+
+FB_PC_LEARNED = 2
+lib.fb_precond_create_learned.restype = C.c_int
+lib.fb_precond_create_learned.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
+lib.fb_learned_params.restype = C.c_int
+lib.fb_learned_params.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64)]
+lib.fb_learned_loss_and_grad.restype = C.c_int
+lib.fb_learned_loss_and_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_double),
+                                         C.c_void_p, C.c_void_p]
+lib.fb_learned_train_step.restype = C.c_int
+lib.fb_learned_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
+                                      C.POINTER(C.c_double), C.c_void_p]
+
+
+def fb_precond_create_learned(op, base, seed=2103_16073, stream=None):
+    out = C.c_void_p()
+    _check(lib.fb_precond_create_learned(op, base, int(seed), _stream(stream), C.byref(out)))
+    return out
+
+
+def fb_learned_params(pc, new=None):
+    """Returns the FP32 parameters; replaces them first if `new` is given."""
+    cnt = C.c_int64(0)
+    if new is not None:
+        arr = np.ascontiguousarray(new, dtype=np.float32)
+        cnt.value = arr.size
+        _check(lib.fb_learned_params(pc, None, arr.ctypes.data, C.byref(cnt)))
+    _check(lib.fb_learned_params(pc, None, None, C.byref(cnt)))
+    out = np.zeros(cnt.value, np.float32)
+    _check(lib.fb_learned_params(pc, out.ctypes.data, None, C.byref(cnt)))
+    return out
+
+
+def fb_learned_loss_and_grad(pc, R, E, stream=None):
+    """R, E: CUDA complex128 tensors [npairs, N].  Returns (loss, grad)."""
+    if not (_is_cuda_tensor(R) and _is_cuda_tensor(E)):
+        raise ValueError("R and E must be CUDA tensors")
+    cnt = C.c_int64(0)
+    _check(lib.fb_learned_params(pc, None, None, C.byref(cnt)))
+    grad = np.zeros(cnt.value, np.float32)
+    loss = C.c_double()
+    _check(lib.fb_learned_loss_and_grad(pc, C.c_void_p(R.data_ptr()), C.c_void_p(E.data_ptr()), R.shape[0],
+                                        C.byref(loss), grad.ctypes.data, _stream(stream)))
+    return loss.value, grad
+
+
+def fb_learned_train_step(pc, R, E, lr, stream=None):
+    if not (_is_cuda_tensor(R) and _is_cuda_tensor(E)):
+        raise ValueError("R and E must be CUDA tensors")
+    loss = C.c_double()
+    _check(lib.fb_learned_train_step(pc, C.c_void_p(R.data_ptr()), C.c_void_p(E.data_ptr()), R.shape[0],
+                                     float(lr), C.byref(loss), _stream(stream)))
+    return loss.value

@@ -370,6 +370,69 @@ fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out)
 
 void fb_precond_destroy(fb_precond* pc) { fb_precond_free(pc); }
 
+fb_status fb_precond_create_learned(fb_op* op, const fb_precond* base, uint64_t seed, void* stream,
+                                    fb_precond** out) {
+    if (!op || !base || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (base->kind != FB_PC_BLOCK_JACOBI || base->op != op)
+        return fb_fail(FB_ERR_ARG, "the base must be a block-Jacobi preconditioner of the same operator");
+    cudaStream_t s = as_stream(stream);
+    fb_precond* pc = new fb_precond();
+    pc->op = op;
+    pc->kind = FB_PC_LEARNED;
+    pc->n = op->n;
+    pc->base = base;
+    fb_status st = fb_learned_alloc(pc->net, op, base, s);
+    if (st == FB_OK) st = fb_learned_init(pc->net, seed, s);
+    if (st != FB_OK) {
+        fb_precond_destroy(pc);
+        return st;
+    }
+    *out = pc;
+    return FB_OK;
+}
+
+static fb_status learned_of(fb_precond* pc) {
+    if (!pc || !pc->net) return fb_fail(FB_ERR_ARG, "not a learned preconditioner");
+    return FB_OK;
+}
+
+fb_status fb_learned_params(fb_precond* pc, float* host_out, const float* host_in, int64_t* count) {
+    FB_CHECK(learned_of(pc));
+    if (!count) return fb_fail(FB_ERR_ARG, "NULL count");
+    int64_t np = fb_learned_nparam(pc->net);
+    if (host_in) {
+        if (*count != np) return fb_fail(FB_ERR_ARG, "parameter count mismatch");
+        FB_CUDA(cudaMemcpy(fb_learned_weights(pc->net), host_in, sizeof(float) * np, cudaMemcpyHostToDevice));
+    }
+    *count = np;
+    if (host_out) FB_CUDA(cudaMemcpy(host_out, fb_learned_weights(pc->net), sizeof(float) * np, cudaMemcpyDeviceToHost));
+    return FB_OK;
+}
+
+fb_status fb_learned_loss_and_grad(fb_precond* pc, const double* R, const double* E, int npairs, double* loss,
+                                   float* grad_host, void* stream) {
+    FB_CHECK(learned_of(pc));
+    if (!R || !E || npairs < 1) return fb_fail(FB_ERR_ARG, "need pairs");
+    cudaStream_t s = as_stream(stream);
+    FB_CHECK(fb_learned_loss_grad(pc->net, (const cd*)R, (const cd*)E, npairs, loss, s));
+    if (grad_host) {
+        FB_CUDA(cudaMemcpyAsync(grad_host, fb_learned_grads(pc->net), sizeof(float) * fb_learned_nparam(pc->net),
+                                cudaMemcpyDeviceToHost, s));
+        FB_CUDA(cudaStreamSynchronize(s));
+    }
+    return FB_OK;
+}
+
+fb_status fb_learned_train_step(fb_precond* pc, const double* R, const double* E, int npairs, double lr,
+                                double* loss, void* stream) {
+    FB_CHECK(learned_of(pc));
+    if (!R || !E || npairs < 1 || !(lr > 0)) return fb_fail(FB_ERR_ARG, "need pairs and lr > 0");
+    cudaStream_t s = as_stream(stream);
+    FB_CHECK(fb_learned_loss_grad(pc->net, (const cd*)R, (const cd*)E, npairs, loss, s));
+    return fb_learned_adam_step(pc->net, lr, s);
+}
+
 fb_status fb_fgmres_solve(fb_op* A, fb_precond* pc, const double* b, double* x, const fb_solver_opts* opts,
                           fb_solve_info* info, int memspace, void* stream) {
     if (!A || !b || !x || !opts) return fb_fail(FB_ERR_ARG, "NULL argument");

@@ -288,6 +288,7 @@ struct fb_op {
     cd* io_y = nullptr;
 };
 
+struct LearnedNet;
 struct fb_precond {
     fb_op* op = nullptr;
     int kind = 0;
@@ -295,6 +296,8 @@ struct fb_precond {
     int64_t* blk_off = nullptr;    // per leaf, offset of its inverse block
     cd* inv64 = nullptr;
     cf* inv32 = nullptr;
+    LearnedNet* net = nullptr;     // learned preconditioner (refines `base`)
+    const fb_precond* base = nullptr;
 };
 
 // ------------------------------------------------------ launch counting ----
@@ -319,6 +322,15 @@ fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, 
                             const fb_tree::RotSet** out);
 fb_status fb_compose_jobs(fb_op* op, const std::vector<int>& which, cudaStream_t s);
 fb_status fb_compose_all(fb_op* op, cudaStream_t s);
+fb_status fb_learned_alloc(LearnedNet*& net, const fb_op* op, const fb_precond* bj, cudaStream_t s);
+void fb_learned_free(LearnedNet*& net);
+fb_status fb_learned_forward(LearnedNet* net, const cd* v, cd* z, cudaStream_t s);
+fb_status fb_learned_loss_grad(LearnedNet* net, const cd* R, const cd* E, int npairs, double* loss, cudaStream_t s);
+fb_status fb_learned_adam_step(LearnedNet* net, double lr, cudaStream_t s);
+fb_status fb_learned_init(LearnedNet* net, uint64_t seed, cudaStream_t s);
+int64_t fb_learned_nparam(const LearnedNet* net);
+float* fb_learned_weights(LearnedNet* net);
+float* fb_learned_grads(LearnedNet* net);
 fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cudaStream_t s);
 fb_status fb_tc_build_groups(fb_op* op, const std::vector<TcGroup>& groups, const int32_t* src_idx,
                              const int32_t* dst_idx, void** slot, cudaStream_t s);

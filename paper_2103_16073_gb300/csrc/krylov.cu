@@ -520,6 +520,7 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
 }
 
 fb_status fb_precond_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s) {
+    if (pc->net) return fb_learned_forward(pc->net, x, y, s);
     const fb_tree* t = pc->op->tree;
     int nleaf = t->nbox[t->L];
     int maxn = 0;
@@ -536,6 +537,7 @@ fb_status fb_precond_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_
 
 void fb_precond_free(fb_precond* pc) {
     if (!pc) return;
+    fb_learned_free(pc->net);
     dfree(pc->blk_off);
     dfree(pc->inv64);
     dfree(pc->inv32);

@@ -1,0 +1,634 @@
+// Learned octree preconditioner: a small hierarchical network over the FMM
+// octree that refines block Jacobi, z = BJ(v) + s * N(v / s), used as the
+// variable right preconditioner that flexible GMRES admits (Sec. 3.1, Sec. 4:
+// FGMRES with a changing preconditioner).  Trained on residual/error pairs
+// (r, e = x* - x) logged from plain block-Jacobi solves, loss
+// ||z(r) - e||^2 / ||e||^2.
+//
+// Network (64-wide features, SiLU, weights W as [in x out], Y = X W + b):
+//   features f_i = (Re v_i, Im v_i, Re u_i, Im u_i)/s, n_i, 1   (u = BJ(v),
+//                  s = rms of v, elements in tree order)
+//   H0 = silu(F W0 + b0)                                  elements
+//   G_L = mean of H0 over each leaf                       leaves
+//   G_l = silu(mean of G_{l+1} over children W_up,k + b)  3 coarser levels
+//   D_{L-3} = G_{L-3};  D_l = silu([G_l, D_{l-1}(parent)] W_dn,k + b)
+//   H1 = silu([H0, D_L(leaf)] W_h + b_h),  O = H1 W_o + b_o (Re, Im)
+//   z_i = u_i + s (O_i0 + i O_i1)
+// All GEMMs run on the tensor cores as BF16 x BF16 -> FP32 (mma.sync
+// m16n8k16) with FP32 activations rounded to BF16 while staging; master
+// weights, gradients and Adam moments are FP32.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int HW = 64;       // feature width
+constexpr int NF = 8;        // element input features
+constexpr int DEPTH = 3;     // coarser levels above the leaves
+
+// ---------------------------------------------------------------- GEMM ----
+// C[M x N] (+)= A[M x K] B[K x N] with arbitrary strides, BF16 operands,
+// FP32 accumulation.  Epilogue: optional bias (per column) and SiLU; writes
+// the pre-activation to Cpre and the activation to C.
+struct GemmArgs {
+    const float* A; int64_t a_m, a_k;
+    const float* B; int64_t b_k, b_n;
+    float* C; int64_t c_m, c_n;
+    float* Cpre;                 // pre-activation (may be null)
+    const float* bias;           // per column (may be null)
+    int M, N, K;
+    int act;                     // 0 none, 1 SiLU
+    int accumulate;              // C += result
+    int kchunk;                  // split-K: K range per blockIdx.z (multiple of 16); 0 = whole K
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ float silu(float x) { return x / (1.f + __expf(-x)); }
+__device__ __forceinline__ float silu_grad(float x) {
+    float sg = 1.f / (1.f + __expf(-x));
+    return sg * (1.f + x * (1.f - sg));
+}
+
+// 128 threads: 4 warps x 16 rows = 64 rows; 64 columns (8 n-tiles of 8).
+__global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
+    __shared__ uint32_t As[64][8 + 1];   // [row][k pair], 16 k per stage
+    __shared__ uint32_t Bs[64][8 + 1];   // [col][k pair]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * 64, n0 = blockIdx.y * 64;
+    float acc[8][4];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
+    const int kb = g.kchunk ? blockIdx.z * g.kchunk : 0;
+    const int ke = g.kchunk ? min(g.K, kb + g.kchunk) : g.K;
+    for (int k0 = kb; k0 < ke; k0 += 16) {
+        for (int i = threadIdx.x; i < 64 * 8; i += blockDim.x) {
+            int r = i >> 3, kp = i & 7;
+            int m = m0 + r, k = k0 + 2 * kp;
+            float x0 = 0.f, x1 = 0.f;
+            if (m < g.M) {
+                if (k < ke) x0 = g.A[m * g.a_m + k * g.a_k];
+                if (k + 1 < ke) x1 = g.A[m * g.a_m + (k + 1) * g.a_k];
+            }
+            As[r][kp] = pack_bf16(x0, x1);
+            int n = n0 + r;
+            float y0 = 0.f, y1 = 0.f;
+            if (n < g.N) {
+                if (k < ke) y0 = g.B[k * g.b_k + n * g.b_n];
+                if (k + 1 < ke) y1 = g.B[(k + 1) * g.b_k + n * g.b_n];
+            }
+            Bs[r][kp] = pack_bf16(y0, y1);
+        }
+        __syncthreads();
+        const int row = warp * 16 + (lane >> 2);
+        const int kq = lane & 3;
+        uint32_t a0 = As[row][kq], a1 = As[row + 8][kq], a2 = As[row][kq + 4], a3 = As[row + 8][kq + 4];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int col = t * 8 + (lane >> 2);
+            uint32_t b0 = Bs[col][kq], b1 = Bs[col][kq + 4];
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+f"(acc[t][0]), "+f"(acc[t][1]), "+f"(acc[t][2]), "+f"(acc[t][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int m = m0 + warp * 16 + (lane >> 2) + (q >> 1) * 8;
+            int n = n0 + t * 8 + (lane & 3) * 2 + (q & 1);
+            if (m >= g.M || n >= g.N) continue;
+            float v = acc[t][q];
+            float* c = g.C + m * g.c_m + n * g.c_n;
+            if (g.kchunk) {              // split-K partial sum (plain accumulation only)
+                atomicAdd(c, v);
+                continue;
+            }
+            if (g.bias) v += g.bias[n];
+            if (g.accumulate) v += *c;
+            if (g.Cpre) g.Cpre[m * g.c_m + n * g.c_n] = v;
+            *c = g.act ? silu(v) : v;
+        }
+}
+
+// --------------------------------------------------------------- helpers ----
+__global__ void k_rms(const cd* v, int64_t n, double* out) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a += abs2(v[i]);
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        a = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (threadIdx.x == 0) atomicAdd(out, a);
+    }
+}
+
+// features in tree order
+__global__ void k_features(Geom g, const int32_t* perm, const cd* v, const cd* u, const double* ssum,
+                           int64_t n, float* F) {
+    int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    double s = sqrt(*ssum / (double)n);
+    double inv = s > 0.0 ? 1.0 / s : 0.0;
+    int64_t e = perm[pos];
+    float* f = F + pos * NF;
+    f[0] = (float)(v[e].re * inv);
+    f[1] = (float)(v[e].im * inv);
+    f[2] = (float)(u[e].re * inv);
+    f[3] = (float)(u[e].im * inv);
+    f[4] = (float)g.nx[e];
+    f[5] = (float)g.ny[e];
+    f[6] = (float)g.nz[e];
+    f[7] = 1.f;
+}
+
+// mean of rows [start[s], start[s+1]) of X (width HW) -> Y[s]
+__global__ void k_segmean(const float* X, const int32_t* start, int nseg, float* Y) {
+    int sgi = blockIdx.x;
+    int c = threadIdx.x;
+    if (sgi >= nseg || c >= HW) return;
+    int a = start[sgi], b = start[sgi + 1];
+    float acc = 0.f;
+    for (int i = a; i < b; ++i) acc += X[(int64_t)i * HW + c];
+    Y[(int64_t)sgi * HW + c] = b > a ? acc / (float)(b - a) : 0.f;
+}
+// backward: dX[i] += dY[seg(i)] / count
+__global__ void k_segmean_back(const float* dY, const int32_t* start, int nseg, float* dX) {
+    int sgi = blockIdx.x;
+    int c = threadIdx.x;
+    if (sgi >= nseg || c >= HW) return;
+    int a = start[sgi], b = start[sgi + 1];
+    if (b <= a) return;
+    float d = dY[(int64_t)sgi * HW + c] / (float)(b - a);
+    for (int i = a; i < b; ++i) dX[(int64_t)i * HW + c] += d;
+}
+
+// C[i] = [X[i], Y[idx[i]]]  (widths HW + HW)
+__global__ void k_concat(const float* X, const float* Y, const int32_t* idx, int64_t rows, float* C) {
+    int64_t i = blockIdx.x;
+    int c = threadIdx.x;
+    if (i >= rows) return;
+    if (c < HW) C[i * 2 * HW + c] = X[i * HW + c];
+    else C[i * 2 * HW + c] = Y[(int64_t)idx[i] * HW + (c - HW)];
+}
+// backward of k_concat: dX[i] += dC[i][:HW], dY[idx[i]] += dC[i][HW:] (atomic)
+__global__ void k_concat_back(const float* dC, const int32_t* idx, int64_t rows, float* dX, float* dY) {
+    int64_t i = blockIdx.x;
+    int c = threadIdx.x;
+    if (i >= rows) return;
+    if (c < HW) dX[i * HW + c] += dC[i * 2 * HW + c];
+    else atomicAdd(&dY[(int64_t)idx[i] * HW + (c - HW)], dC[i * 2 * HW + c]);
+}
+
+__global__ void k_add_f(float* dst, const float* src, int64_t count) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) dst[i] += src[i];
+}
+
+__global__ void k_silu_back(const float* dA, const float* pre, int64_t count, float* dP) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < count) dP[i] = dA[i] * silu_grad(pre[i]);
+}
+
+// column sums (bias gradients): out[c] += sum_r X[r][c]
+__global__ void k_colsum(const float* X, int64_t rows, int cols, float* out) {
+    int c = blockIdx.y;
+    float a = 0.f;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x)
+        a += X[r * cols + c];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&out[c], a);
+}
+
+// z (element order) = u + s (O0 + i O1)
+__global__ void k_output(const int32_t* perm, const cd* u, const float* O, const double* ssum, int64_t n, cd* z) {
+    int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    double s = sqrt(*ssum / (double)n);
+    int64_t e = perm[pos];
+    z[e] = mk(u[e].re + s * (double)O[pos * 2], u[e].im + s * (double)O[pos * 2 + 1]);
+}
+
+// loss pieces: sum |z - e|^2, sum |e|^2; dO = 2 s (z - e) / ||e||^2 (tree order)
+__global__ void k_loss_sums(const cd* z, const cd* e, int64_t n, double* sums) {
+    __shared__ double s0[32], s1[32];
+    double a = 0.0, b = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        cd d = z[i] - e[i];
+        a += abs2(d);
+        b += abs2(e[i]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) { s0[threadIdx.x >> 5] = a; s1[threadIdx.x >> 5] = b; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        a = threadIdx.x < (blockDim.x >> 5) ? s0[threadIdx.x] : 0.0;
+        b = threadIdx.x < (blockDim.x >> 5) ? s1[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (threadIdx.x == 0) { atomicAdd(&sums[0], a); atomicAdd(&sums[1], b); }
+    }
+}
+__global__ void k_loss_grad(const int32_t* perm, const cd* z, const cd* e, const double* ssum, const double* sums,
+                            int64_t n, double scale, float* dO) {
+    int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    double s = sqrt(*ssum / (double)n);
+    int64_t i = perm[pos];
+    double f = scale * 2.0 * s / sums[1];
+    dO[pos * 2] = (float)(f * (z[i].re - e[i].re));
+    dO[pos * 2 + 1] = (float)(f * (z[i].im - e[i].im));
+}
+
+__global__ void k_adam(float* w, const float* gr, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float g = gr[i];
+    float mi = b1 * m[i] + (1.f - b1) * g;
+    float vi = b2 * v[i] + (1.f - b2) * g * g;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host ----
+// Parameter layout (FP32, one flat array):
+//   W0 [8 x 64], b0 [64], Wu[k] [64 x 64], bu[k] [64] (k = 0..2),
+//   Wd[k] [128 x 64], bd[k] [64] (k = 0..2), Wh [128 x 64], bh [64], Wo [64 x 2], bo [2]
+struct LearnedNet {
+    const fb_op* op = nullptr;
+    const fb_precond* bj = nullptr;
+    int L = 0, depth = 0;
+    int64_t n = 0;
+    int64_t nparam = 0;
+    int64_t oW0, ob0, oWu[DEPTH], obu[DEPTH], oWd[DEPTH], obd[DEPTH], oWh, obh, oWo, obo;
+    float *w = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+    int64_t adam_t = 0;
+    // activations (tree order)
+    float *F = nullptr, *pre0 = nullptr, *H0 = nullptr, *E = nullptr, *preh = nullptr, *H1 = nullptr, *O = nullptr;
+    float* G[FB_MAXLEV + 1] = {nullptr};
+    float* Pm[FB_MAXLEV + 1] = {nullptr};
+    float* preu[FB_MAXLEV + 1] = {nullptr};
+    float* D[FB_MAXLEV + 1] = {nullptr};
+    float* Cc[FB_MAXLEV + 1] = {nullptr};
+    float* pred[FB_MAXLEV + 1] = {nullptr};
+    // gradients of activations
+    float *dH0 = nullptr, *dE = nullptr, *dH1 = nullptr, *dO = nullptr, *dtmp = nullptr;
+    float* dG[FB_MAXLEV + 1] = {nullptr};
+    float* dD[FB_MAXLEV + 1] = {nullptr};
+    float* dC[FB_MAXLEV + 1] = {nullptr};
+    float* dPm[FB_MAXLEV + 1] = {nullptr};
+    int32_t* child_start[FB_MAXLEV + 1] = {nullptr};   // children of box b at level l: [cs[b], cs[b+1]) at level l+1
+    int32_t* leaf_of = nullptr;                         // tree position -> leaf
+    cd *u = nullptr, *z = nullptr;
+    double* scal = nullptr;    // [0] sum |v|^2, [1..2] loss sums
+};
+
+static void gemm(cudaStream_t s, const float* A, int64_t am, int64_t ak, const float* B, int64_t bk, int64_t bn,
+                 float* C, int64_t cm, int64_t cn, int M, int N, int K, const float* bias = nullptr,
+                 float* Cpre = nullptr, int act = 0, int accumulate = 0) {
+    if (M <= 0 || N <= 0) return;
+    GemmArgs g{A, am, ak, B, bk, bn, C, cm, cn, Cpre, bias, M, N, K, act, accumulate, 0};
+    dim3 grid(div_up(M, 64), div_up(N, 64));
+    // Long reductions into few output tiles (weight gradients, K = elements
+    // or boxes): split K over blockIdx.z and add the partial sums atomically.
+    const int tiles = (int)(grid.x * grid.y);
+    if (accumulate && !bias && !act && !Cpre && K > 1024 && tiles < 256) {
+        int splits = std::min(div_up(K, 512), std::max(1, 1024 / tiles));
+        g.kchunk = div_up(div_up(K, splits), 16) * 16;
+        grid.z = div_up(K, g.kchunk);
+    }
+    k_gemm_bf16<<<grid, 128, 0, s>>>(g);
+    fb_count_launch();
+}
+
+__global__ void k_child_start(const int32_t* parent, int nchild, int nparent, int32_t* cs) {
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p > nparent) return;
+    // first child whose parent index >= p (children are sorted by parent)
+    int lo = 0, hi = nchild;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (parent[mid] < p) lo = mid + 1; else hi = mid;
+    }
+    cs[p] = lo;
+}
+__global__ void k_leaf_of_pos(const int32_t* leaf_start, int nleaf, int32_t* leaf_of) {
+    int b = blockIdx.x;
+    if (b >= nleaf) return;
+    for (int i = leaf_start[b] + threadIdx.x; i < leaf_start[b + 1]; i += blockDim.x) leaf_of[i] = b;
+}
+
+fb_status fb_learned_alloc(LearnedNet*& net, const fb_op* op, const fb_precond* bj, cudaStream_t s) {
+    const fb_tree* t = op->tree;
+    net = new LearnedNet();
+    net->op = op;
+    net->bj = bj;
+    net->L = t->L;
+    net->depth = std::min(DEPTH, t->L);
+    net->n = op->n;
+    int64_t o = 0;
+    auto take = [&](int64_t c) { int64_t r = o; o += c; return r; };
+    net->oW0 = take(NF * HW);
+    net->ob0 = take(HW);
+    for (int k = 0; k < DEPTH; ++k) { net->oWu[k] = take(HW * HW); net->obu[k] = take(HW); }
+    for (int k = 0; k < DEPTH; ++k) { net->oWd[k] = take(2 * HW * HW); net->obd[k] = take(HW); }
+    net->oWh = take(2 * HW * HW);
+    net->obh = take(HW);
+    net->oWo = take(HW * 2);
+    net->obo = take(2);
+    net->nparam = o;
+    int64_t n = net->n;
+    FB_CHECK(dalloc(&net->w, o));
+    FB_CHECK(dalloc(&net->grad, o));
+    FB_CHECK(dalloc(&net->m1, o));
+    FB_CHECK(dalloc(&net->m2, o));
+    FB_CUDA(cudaMemsetAsync(net->m1, 0, sizeof(float) * o, s));
+    FB_CUDA(cudaMemsetAsync(net->m2, 0, sizeof(float) * o, s));
+    FB_CHECK(dalloc(&net->F, n * NF));
+    FB_CHECK(dalloc(&net->pre0, n * HW));
+    FB_CHECK(dalloc(&net->H0, n * HW));
+    FB_CHECK(dalloc(&net->E, n * 2 * HW));
+    FB_CHECK(dalloc(&net->preh, n * HW));
+    FB_CHECK(dalloc(&net->H1, n * HW));
+    FB_CHECK(dalloc(&net->O, n * 2));
+    FB_CHECK(dalloc(&net->dH0, n * HW));
+    FB_CHECK(dalloc(&net->dE, n * 2 * HW));
+    FB_CHECK(dalloc(&net->dH1, n * HW));
+    FB_CHECK(dalloc(&net->dO, n * 2));
+    FB_CHECK(dalloc(&net->dtmp, n * 2 * HW));
+    int L = net->L;
+    for (int l = L - net->depth; l <= L; ++l) {
+        int64_t nb = t->nbox[l];
+        FB_CHECK(dalloc(&net->G[l], nb * HW));
+        FB_CHECK(dalloc(&net->D[l], nb * HW));
+        FB_CHECK(dalloc(&net->dG[l], nb * HW));
+        FB_CHECK(dalloc(&net->dD[l], nb * HW));
+        if (l < L) {
+            FB_CHECK(dalloc(&net->Pm[l], nb * HW));
+            FB_CHECK(dalloc(&net->preu[l], nb * HW));
+            FB_CHECK(dalloc(&net->dPm[l], nb * HW));
+            FB_CHECK(dalloc(&net->child_start[l], nb + 1));
+            k_child_start<<<div_up(nb + 1, 128), 128, 0, s>>>(t->parent[l + 1], t->nbox[l + 1], (int)nb,
+                                                              net->child_start[l]);
+        }
+        if (l > L - net->depth) {
+            FB_CHECK(dalloc(&net->Cc[l], nb * 2 * HW));
+            FB_CHECK(dalloc(&net->pred[l], nb * HW));
+            FB_CHECK(dalloc(&net->dC[l], nb * 2 * HW));
+        }
+    }
+    FB_CHECK(dalloc(&net->leaf_of, n));
+    k_leaf_of_pos<<<t->nbox[L], 64, 0, s>>>(t->leaf_start, t->nbox[L], net->leaf_of);
+    FB_CHECK(dalloc(&net->u, n));
+    FB_CHECK(dalloc(&net->z, n));
+    FB_CHECK(dalloc(&net->scal, 4));
+    FB_LAUNCH_CHECK();
+    return FB_OK;
+}
+
+void fb_learned_free(LearnedNet*& net) {
+    if (!net) return;
+    float** fl[] = {&net->w, &net->grad, &net->m1, &net->m2, &net->F, &net->pre0, &net->H0, &net->E, &net->preh,
+                    &net->H1, &net->O, &net->dH0, &net->dE, &net->dH1, &net->dO, &net->dtmp};
+    for (auto p : fl) dfree(*p);
+    for (int l = 0; l <= FB_MAXLEV; ++l) {
+        dfree(net->G[l]); dfree(net->Pm[l]); dfree(net->preu[l]); dfree(net->D[l]); dfree(net->Cc[l]);
+        dfree(net->pred[l]); dfree(net->dG[l]); dfree(net->dD[l]); dfree(net->dC[l]); dfree(net->dPm[l]);
+        dfree(net->child_start[l]);
+    }
+    dfree(net->leaf_of);
+    dfree(net->u);
+    dfree(net->z);
+    dfree(net->scal);
+    delete net;
+    net = nullptr;
+}
+
+// Forward: v (element order, device) -> z = BJ(v) + s N(v/s).
+fb_status fb_learned_forward(LearnedNet* net, const cd* v, cd* z, cudaStream_t s) {
+    const fb_tree* t = net->op->tree;
+    const Geom& g = net->op->mesh->g;
+    int L = net->L, Ltop = L - net->depth;
+    int64_t n = net->n;
+    int nleaf = t->nbox[L];
+    FB_CHECK(fb_precond_apply(net->bj, v, net->u, s));
+    FB_CUDA(cudaMemsetAsync(net->scal, 0, sizeof(double), s));
+    k_rms<<<std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(v, n, net->scal);
+    k_features<<<div_up(n, 256), 256, 0, s>>>(g, t->perm, v, net->u, net->scal, n, net->F);
+    fb_count_launch(2);
+    const float* w = net->w;
+    gemm(s, net->F, NF, 1, w + net->oW0, HW, 1, net->H0, HW, 1, (int)n, HW, NF, w + net->ob0, net->pre0, 1);
+    k_segmean<<<nleaf, HW, 0, s>>>(net->H0, t->leaf_start, nleaf, net->G[L]);
+    fb_count_launch();
+    for (int l = L - 1, k = 0; l >= Ltop; --l, ++k) {
+        int nb = t->nbox[l];
+        k_segmean<<<nb, HW, 0, s>>>(net->G[l + 1], net->child_start[l], nb, net->Pm[l]);
+        fb_count_launch();
+        gemm(s, net->Pm[l], HW, 1, w + net->oWu[k], HW, 1, net->G[l], HW, 1, nb, HW, HW, w + net->obu[k],
+             net->preu[l], 1);
+    }
+    FB_CUDA(cudaMemcpyAsync(net->D[Ltop], net->G[Ltop], sizeof(float) * t->nbox[Ltop] * HW,
+                            cudaMemcpyDeviceToDevice, s));
+    for (int l = Ltop + 1, k = 0; l <= L; ++l, ++k) {
+        int nb = t->nbox[l];
+        k_concat<<<nb, 2 * HW, 0, s>>>(net->G[l], net->D[l - 1], t->parent[l], nb, net->Cc[l]);
+        fb_count_launch();
+        gemm(s, net->Cc[l], 2 * HW, 1, w + net->oWd[k], HW, 1, net->D[l], HW, 1, nb, HW, 2 * HW, w + net->obd[k],
+             net->pred[l], 1);
+    }
+    k_concat<<<(unsigned)n, 2 * HW, 0, s>>>(net->H0, net->D[L], net->leaf_of, n, net->E);
+    fb_count_launch();
+    gemm(s, net->E, 2 * HW, 1, w + net->oWh, HW, 1, net->H1, HW, 1, (int)n, HW, 2 * HW, w + net->obh, net->preh, 1);
+    gemm(s, net->H1, HW, 1, w + net->oWo, 2, 1, net->O, 2, 1, (int)n, 2, HW, w + net->obo, nullptr, 0);
+    k_output<<<div_up(n, 256), 256, 0, s>>>(t->perm, net->u, net->O, net->scal, n, z);
+    fb_count_launch();
+    FB_LAUNCH_CHECK();
+    return FB_OK;
+}
+
+// Loss of one pair and accumulation of its gradient (scaled by `scale`)
+// into net->grad.  Returns the loss sums in net->scal[1..2] (device).
+fb_status fb_learned_backward(LearnedNet* net, const cd* r, const cd* e, double scale, cudaStream_t s) {
+    const fb_tree* t = net->op->tree;
+    int L = net->L, Ltop = L - net->depth;
+    int64_t n = net->n;
+    int nleaf = t->nbox[L];
+    FB_CHECK(fb_learned_forward(net, r, net->z, s));
+    FB_CUDA(cudaMemsetAsync(net->scal + 1, 0, 2 * sizeof(double), s));
+    k_loss_sums<<<std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(net->z, e, n, net->scal + 1);
+    k_loss_grad<<<div_up(n, 256), 256, 0, s>>>(t->perm, net->z, e, net->scal, net->scal + 1, n, scale, net->dO);
+    fb_count_launch(2);
+    float* w = net->w;
+    float* gr = net->grad;
+    auto colsum = [&](const float* X, int64_t rows, int cols, float* out) {
+        dim3 grid((unsigned)std::min<int64_t>(div_up(rows, 256), 256), cols);
+        k_colsum<<<grid, 256, 0, s>>>(X, rows, cols, out);
+        fb_count_launch();
+    };
+    // O = H1 Wo + bo
+    gemm(s, net->H1, 1, HW, net->dO, 2, 1, gr + net->oWo, 2, 1, HW, 2, (int)n, nullptr, nullptr, 0, 1);
+    colsum(net->dO, n, 2, gr + net->obo);
+    gemm(s, net->dO, 2, 1, w + net->oWo, 1, 2, net->dH1, HW, 1, (int)n, HW, 2);
+    // H1 = silu(E Wh + bh)
+    k_silu_back<<<div_up(n * HW, 256), 256, 0, s>>>(net->dH1, net->preh, n * HW, net->dtmp);
+    fb_count_launch();
+    gemm(s, net->E, 1, 2 * HW, net->dtmp, HW, 1, gr + net->oWh, HW, 1, 2 * HW, HW, (int)n, nullptr, nullptr, 0, 1);
+    colsum(net->dtmp, n, HW, gr + net->obh);
+    gemm(s, net->dtmp, HW, 1, w + net->oWh, 1, HW, net->dE, 2 * HW, 1, (int)n, 2 * HW, HW);
+    // E = [H0, D_L(leaf)]
+    FB_CUDA(cudaMemsetAsync(net->dH0, 0, sizeof(float) * n * HW, s));
+    for (int l = Ltop; l <= L; ++l) {
+        FB_CUDA(cudaMemsetAsync(net->dD[l], 0, sizeof(float) * t->nbox[l] * HW, s));
+        FB_CUDA(cudaMemsetAsync(net->dG[l], 0, sizeof(float) * t->nbox[l] * HW, s));
+    }
+    k_concat_back<<<(unsigned)n, 2 * HW, 0, s>>>(net->dE, net->leaf_of, n, net->dH0, net->dD[L]);
+    fb_count_launch();
+    // down-sweep backward
+    for (int l = L, k = net->depth - 1; l > Ltop; --l, --k) {
+        int nb = t->nbox[l];
+        k_silu_back<<<div_up((int64_t)nb * HW, 256), 256, 0, s>>>(net->dD[l], net->pred[l], (int64_t)nb * HW, net->dtmp);
+        fb_count_launch();
+        gemm(s, net->Cc[l], 1, 2 * HW, net->dtmp, HW, 1, gr + net->oWd[k], HW, 1, 2 * HW, HW, nb, nullptr, nullptr,
+             0, 1);
+        colsum(net->dtmp, nb, HW, gr + net->obd[k]);
+        gemm(s, net->dtmp, HW, 1, w + net->oWd[k], 1, HW, net->dC[l], 2 * HW, 1, nb, 2 * HW, HW);
+        k_concat_back<<<nb, 2 * HW, 0, s>>>(net->dC[l], t->parent[l], nb, net->dG[l], net->dD[l - 1]);
+        fb_count_launch();
+    }
+    // D_top = G_top: dG_top += dD_top
+    {
+        int64_t cnt = (int64_t)t->nbox[Ltop] * HW;
+        k_add_f<<<div_up(cnt, 256), 256, 0, s>>>(net->dG[Ltop], net->dD[Ltop], cnt);
+        fb_count_launch();
+    }
+    // up-sweep backward (top level first)
+    for (int l = Ltop, k = net->depth - 1; l < L; ++l, --k) {
+        int nb = t->nbox[l];
+        k_silu_back<<<div_up((int64_t)nb * HW, 256), 256, 0, s>>>(net->dG[l], net->preu[l], (int64_t)nb * HW, net->dtmp);
+        fb_count_launch();
+        gemm(s, net->Pm[l], 1, HW, net->dtmp, HW, 1, gr + net->oWu[k], HW, 1, HW, HW, nb, nullptr, nullptr, 0, 1);
+        colsum(net->dtmp, nb, HW, gr + net->obu[k]);
+        gemm(s, net->dtmp, HW, 1, w + net->oWu[k], 1, HW, net->dPm[l], HW, 1, nb, HW, HW);
+        k_segmean_back<<<nb, HW, 0, s>>>(net->dPm[l], net->child_start[l], nb, net->dG[l + 1]);
+        fb_count_launch();
+    }
+    // leaves: G_L = mean(H0)
+    k_segmean_back<<<nleaf, HW, 0, s>>>(net->dG[L], t->leaf_start, nleaf, net->dH0);
+    fb_count_launch();
+    // H0 = silu(F W0 + b0)
+    k_silu_back<<<div_up(n * HW, 256), 256, 0, s>>>(net->dH0, net->pre0, n * HW, net->dtmp);
+    fb_count_launch();
+    gemm(s, net->F, 1, NF, net->dtmp, HW, 1, gr + net->oW0, HW, 1, NF, HW, (int)n, nullptr, nullptr, 0, 1);
+    colsum(net->dtmp, n, HW, gr + net->ob0);
+    FB_LAUNCH_CHECK();
+    return FB_OK;
+}
+
+// Loss and gradient over a batch of pairs (device arrays, element order,
+// pairs stored one after the other).  grad is averaged over the batch.
+fb_status fb_learned_loss_grad(LearnedNet* net, const cd* R, const cd* E, int npairs, double* loss,
+                               cudaStream_t s) {
+    int64_t n = net->n;
+    FB_CUDA(cudaMemsetAsync(net->grad, 0, sizeof(float) * net->nparam, s));
+    double total = 0.0;
+    for (int q = 0; q < npairs; ++q) {
+        FB_CHECK(fb_learned_backward(net, R + (int64_t)q * n, E + (int64_t)q * n, 1.0 / npairs, s));
+        double h[2];
+        FB_CUDA(cudaMemcpyAsync(h, net->scal + 1, sizeof(h), cudaMemcpyDeviceToHost, s));
+        FB_CUDA(cudaStreamSynchronize(s));
+        total += h[1] > 0 ? h[0] / h[1] : 0.0;
+    }
+    if (loss) *loss = total / std::max(npairs, 1);
+    return FB_OK;
+}
+
+fb_status fb_learned_adam_step(LearnedNet* net, double lr, cudaStream_t s) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    net->adam_t++;
+    float c1 = 1.f - powf(b1, (float)net->adam_t), c2 = 1.f - powf(b2, (float)net->adam_t);
+    k_adam<<<div_up(net->nparam, 256), 256, 0, s>>>(net->w, net->grad, net->m1, net->m2, net->nparam, (float)lr, b1,
+                                                    b2, eps, c1, c2);
+    fb_count_launch();
+    FB_LAUNCH_CHECK();
+    return FB_OK;
+}
+
+// Deterministic initialisation: uniform(-a, a), a = sqrt(3 / fan_in) from a
+// counter-based hash of the parameter index and seed; biases zero; the output
+// layer scaled by 1e-2 so the untrained network is close to block Jacobi.
+__global__ void k_init_params(float* w, int64_t n, const int64_t* seg, int nseg, uint64_t seed) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // segments: (offset, count, fan_in, scale_code) quadruples
+    float val = 0.f;
+    for (int k = 0; k < nseg; ++k) {
+        int64_t off = seg[4 * k], cnt = seg[4 * k + 1], fan = seg[4 * k + 2], code = seg[4 * k + 3];
+        if (i >= off && i < off + cnt) {
+            if (fan > 0) {
+                uint64_t x = (uint64_t)i * 0x9E3779B97F4A7C15ULL ^ seed;
+                x ^= x >> 33; x *= 0xff51afd7ed558ccdULL; x ^= x >> 33; x *= 0xc4ceb9fe1a85ec53ULL; x ^= x >> 33;
+                float u01 = (float)((x >> 40) & 0xFFFFFF) / 16777216.0f;
+                float a = sqrtf(3.f / (float)fan) * (code == 1 ? 1e-2f : 1.f);
+                val = (2.f * u01 - 1.f) * a;
+            }
+            break;
+        }
+    }
+    w[i] = val;
+}
+
+fb_status fb_learned_init(LearnedNet* net, uint64_t seed, cudaStream_t s) {
+    std::vector<int64_t> seg;
+    auto add = [&](int64_t off, int64_t cnt, int64_t fan, int64_t code) {
+        seg.push_back(off); seg.push_back(cnt); seg.push_back(fan); seg.push_back(code);
+    };
+    add(net->oW0, NF * HW, NF, 0);
+    add(net->ob0, HW, 0, 0);
+    for (int k = 0; k < DEPTH; ++k) { add(net->oWu[k], HW * HW, HW, 0); add(net->obu[k], HW, 0, 0); }
+    for (int k = 0; k < DEPTH; ++k) { add(net->oWd[k], 2 * HW * HW, 2 * HW, 0); add(net->obd[k], HW, 0, 0); }
+    add(net->oWh, 2 * HW * HW, 2 * HW, 0);
+    add(net->obh, HW, 0, 0);
+    add(net->oWo, HW * 2, HW, 1);
+    add(net->obo, 2, 0, 0);
+    int64_t* dseg = nullptr;
+    FB_CHECK(dalloc(&dseg, seg.size()));
+    FB_CUDA(cudaMemcpyAsync(dseg, seg.data(), sizeof(int64_t) * seg.size(), cudaMemcpyHostToDevice, s));
+    k_init_params<<<div_up(net->nparam, 256), 256, 0, s>>>(net->w, net->nparam, dseg, (int)seg.size() / 4, seed);
+    cudaError_t e = cudaStreamSynchronize(s);
+    dfree(dseg);
+    if (e != cudaSuccess) return fb_fail(FB_ERR_CUDA, cudaGetErrorString(e));
+    net->adam_t = 0;
+    FB_CUDA(cudaMemsetAsync(net->m1, 0, sizeof(float) * net->nparam, s));
+    FB_CUDA(cudaMemsetAsync(net->m2, 0, sizeof(float) * net->nparam, s));
+    return FB_OK;
+}
+
+int64_t fb_learned_nparam(const LearnedNet* net) { return net->nparam; }
+float* fb_learned_weights(LearnedNet* net) { return net->w; }
+float* fb_learned_grads(LearnedNet* net) { return net->grad; }
