@@ -8,9 +8,13 @@ elements; FMM order per level from the excess-bandwidth rule (d0 = 6,
 p_min = 12).  Synthetic seeded input; see the design doc.
 
 A step is one solve A x = b of Eq. (dbem4) with the mixed operator (FP32 near
-field, P2M/L2P and translations, FP64 Arnoldi) right-preconditioned by block
-Jacobi, judged by the true residual of the FP64 FMM operator.  N GPUs (torchrun)
-each solve their own source position: weak scaling, no data-path collective.
+field, P2M/L2P and translations, FP64 Arnoldi) right-preconditioned by the
+learned octree network over block Jacobi (trained before the timed region on
+pairs logged from block-Jacobi solves for other source positions), judged by
+the true residual of the FP64 FMM operator.  The same solve under block Jacobi
+alone and the plain FP64 path (FP64 FMM + FP64 block Jacobi) are timed beside
+it.  N GPUs (torchrun) each solve their own source position: weak scaling, no
+data-path collective.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -126,6 +130,68 @@ def build_problem(fb, W, torch, rank):
     return dict(wl=wl, mesh=mesh, tree=tree, A32=A32, A64=A64, L64=L64, pc32=pc32, pc64=pc64, b=b)
 
 
+def train_learned(fb, W, torch, P, nsrc, steps):
+    """Learned preconditioner for the mixed operator: pairs (r, e) from
+    truncated block-Jacobi solves for `nsrc` seeded source positions other than
+    the benchmarked one, joined by as many white-noise inputs, residual
+    objective, Adam; the parameters kept are those with the fewest FGMRES
+    iterations on one more held-out source (the initial state included).
+    Returns the handle and a summary."""
+    from paper_2103_16073_gb300 import training
+    wl = P["wl"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rng = W.seeded_rng(200)
+    srcs = W.uniform_points_in_box(rng, [0, 0, 0], list(wl.room), nsrc + 1, 0.3, avoid=wl.sources,
+                                   avoid_dist=0.3)
+    rhs = []
+    for src in srcs:
+        g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
+        fb.fb_gamma_monopole(P["mesh"], wl.k, src, g)
+        b = torch.empty_like(g)
+        fb.fb_operator_apply(P["L64"], g, b)
+        rhs.append(b)
+    Rs, Es = [], []
+    for b in rhs[:nsrc]:
+        R, E = training.collect_pairs(P["A32"], P["pc32"], b)
+        Rs.append(R)
+        Es.append(E)
+    R = torch.cat(Rs)
+    E = torch.cat(Es)
+    npairs = int(R.shape[0])
+    R, E = training.augment_noise(R, E, npairs, seed=7)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    pc = fb.fb_precond_create_learned(P["A32"], P["pc32"])
+    fb.fb_learned_set_objective(pc, fb.FB_LOSS_RESIDUAL)
+    bval = rhs[nsrc]
+
+    def validate():
+        x = torch.zeros_like(bval)
+        info = fb.fb_fgmres_solve(P["A32"], bval, x, pc=pc, tol=TOL, restart=RESTART, maxit=3000, max_refine=4)
+        return info["iters"]
+
+    x = torch.zeros_like(bval)
+    bj_val = fb.fb_fgmres_solve(P["A32"], bval, x, pc=P["pc32"], tol=TOL, restart=RESTART, maxit=3000,
+                                max_refine=4)["iters"]
+    res_bj = training.residual_error(P["A32"], P["pc32"], R[:npairs])
+    before = training.evaluate(pc, R, E)
+    hist, vlog = training.train(pc, R, E, steps=steps, lr=1e-3, batch=8, validate=validate, every=10)
+    after = training.evaluate(pc, R, E)
+    res_l = training.residual_error(P["A32"], pc, R[:npairs])
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    info = {"train_sources": nsrc, "pairs": npairs, "noise_inputs": npairs, "objective": "residual",
+            "adam_steps": steps, "batch": 8, "lr": 1e-3,
+            "loss_init": round(before, 5), "loss_selected": round(after, 5),
+            "residual_error_on_pairs": {"block_jacobi": round(res_bj, 4), "learned": round(res_l, 4)},
+            "validation_iterations": {"block_jacobi": bj_val, "selected": min(v for _, v in vlog),
+                                      "log": vlog[:: max(1, len(vlog) // 8)]},
+            "collect_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3)}
+    del R, E, Rs, Es
+    return pc, info
+
+
 def level_counts(fb, op, tree):
     """(p, tensor-core flag, M2L pairs, boxes) per level."""
     L, org, side, nb = fb.fb_tree_info(tree)
@@ -200,9 +266,14 @@ def run_ours(args):
     wl = P["wl"]
     n = wl.n
     stream = torch.cuda.current_stream()
+    learned_info = None
+    if args.precond == "learned":
+        pc_main, learned_info = train_learned(fb, W, torch, P, args.train_sources, args.train_steps)
+    else:
+        pc_main = P["pc32"]
 
-    def solve_mixed(x):
-        return fb.fb_fgmres_solve(P["A32"], P["b"], x, pc=P["pc32"], tol=TOL, restart=RESTART, maxit=3000,
+    def solve_mixed(x, pc=pc_main):
+        return fb.fb_fgmres_solve(P["A32"], P["b"], x, pc=pc, tol=TOL, restart=RESTART, maxit=3000,
                                   max_refine=4, true_op=P["A64"])
 
     x = torch.zeros_like(P["b"])
@@ -271,6 +342,19 @@ def run_ours(args):
     mv64_ms = b0.elapsed_time(b1) / nmv64
     ph64 = fb.fb_operator_apply_timed(P["A64"], xv, yv)
 
+    # the same mixed solve under block Jacobi alone
+    bj_t, bj_infos = [], []
+    for _ in range(3):
+        xb = torch.zeros_like(P["b"])
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        bj_infos.append(solve_mixed(xb, P["pc32"]))
+        d1.record(stream)
+        torch.cuda.synchronize()
+        bj_t.append(d0.elapsed_time(d1) / 1e3)
+    bj_s = statistics.median(bj_t)
+
     # plain FP64 path: FP64 FMM + FP64 block Jacobi, one solve
     x64 = torch.zeros_like(P["b"])
     c0 = torch.cuda.Event(enable_timing=True)
@@ -290,7 +374,7 @@ def run_ours(args):
     for _ in range(max(1, min(args.steps, 5))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        fb.fb_fgmres_solve(P["A32"], bh, xn, pc=P["pc32"], tol=TOL, restart=RESTART, maxit=3000,
+        fb.fb_fgmres_solve(P["A32"], bh, xn, pc=pc_main, tol=TOL, restart=RESTART, maxit=3000,
                            max_refine=4, true_op=P["A64"])
         e2e_t.append(time.perf_counter() - t0)
     e2e_s = statistics.median(e2e_t)
@@ -311,9 +395,11 @@ def run_ours(args):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": "shoebox 3.0x2.4x2.0 m, 1 kHz, N=39368 flat triangles (lambda/8), "
-                               "beta=0.2, FMM leaf<=64, d0=6 pmin=12, FGMRES(40)+block-Jacobi, tol 1e-4",
+                               f"beta=0.2, FMM leaf<=64, d0=6 pmin=12, FGMRES(40)+{args.precond}, tol 1e-4",
                    "n_elements": n, "frequency_hz": wl.freq_hz, "solver": "FGMRES restart 40",
-                   "precond": "block-Jacobi (leaf self blocks)", "operator": "mixed FP32 FMM, FP64 Arnoldi",
+                   "precond": ("learned octree network over block Jacobi (BF16 tensor-core kernels)"
+                               if args.precond == "learned" else "block-Jacobi (leaf self blocks)"),
+                   "operator": "mixed FP32 FMM, FP64 Arnoldi",
                    "true_residual": "FP64 FMM", "l2": "working set > L2 (translation matrices alone > 129 MB)",
                    "parallelism": f"replicas x{ws} (one (f, source) solve per GPU)"},
         "time_to_solve_s": round(ms_step / 1e3, 5),
@@ -323,6 +409,10 @@ def run_ours(args):
         "matvecs_per_s": round(1e3 / mv_ms, 2),
         "matvec_ms": round(mv_ms, 4),
         "phase_ms": {k: round(v, 4) for k, v in ph.items()},
+        "pc_fallbacks": max(i.get("pc_fallbacks", 0) for i in infos),
+        "learned": learned_info,
+        "mixed_block_jacobi": {"time_to_solve_s": round(bj_s, 5), "iterations": bj_infos[-1]["iters"],
+                               "true_relres": bj_infos[-1]["true_relres"]},
         "plain_fp64": {"time_to_solve_s": round(t64, 4), "iterations": info64["iters"],
                        "true_relres": info64["true_relres"], "matvecs_per_s": round(1e3 / mv64_ms, 2),
                        "phase_ms": {k: round(v, 3) for k, v in ph64.items()}},
@@ -408,6 +498,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precond", default="learned", choices=["learned", "bj"])
+    ap.add_argument("--train-sources", type=int, default=4)
+    ap.add_argument("--train-steps", type=int, default=200)
     ap.add_argument("--ref-matvecs", type=int, default=60,
                     help="matvecs per solve used to extrapolate the reference arm")
     args = ap.parse_args()

@@ -270,10 +270,17 @@ FB_API fb_status fb_gamma_monopole(const fb_mesh* mesh, double k, const double* 
 FB_API fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out);
 FB_API void fb_precond_destroy(fb_precond* pc);
 
+/* y = P x for a preconditioner handle (block Jacobi, or a learned network
+ * over its block-Jacobi base).  x, y: N complex in memspace, distinct.
+ * Errors: FB_ERR_ARG for NULL or overlapping arrays. */
+FB_API fb_status fb_precond_apply(const fb_precond* pc, const double* x, double* y, int memspace, void* stream);
+
 /* Learned octree preconditioner (the variable preconditioner that flexible
- * GMRES admits, Sec. 3.1 / Sec. 4): z = BJ(v) + s N(v / s), where BJ is the
- * block-Jacobi `base` of the same FMM operator (which must outlive it),
- * s = rms(v), and N a hierarchical network over the octree (element
+ * GMRES admits, Sec. 3.1 / Sec. 4): z = BJ(v) + s ph N(conj(ph) v / s,
+ * conj(ph) BJ(v) / s), where BJ is the block-Jacobi `base` of the same FMM
+ * operator (which must outlive it), s = rms(v), ph the unit phase of sum v
+ * (so z(a v) = a z(v) for complex a), and N a hierarchical network over the
+ * octree (element
  * encoder, leaf pooling, 3 coarser pooling levels, down-sweep back to the
  * leaves, element decoder; 64-wide features, SiLU).  Its matrix products run
  * on the tensor cores in BF16 with FP32 accumulation; parameters, gradients
@@ -288,9 +295,24 @@ FB_API fb_status fb_precond_create_learned(fb_op* op, const fb_precond* base, ui
  * host_out is given they are copied out; *count receives the count. */
 FB_API fb_status fb_learned_params(fb_precond* pc, float* host_out, const float* host_in, int64_t* count);
 
+/* Training objectives for a pair (r, e) with A e = r:
+ *   FB_LOSS_ERROR:    ||z(r) - e||^2 / ||e||^2
+ *   FB_LOSS_RESIDUAL: ||A z(r) - r||^2 / ||r||^2   (default)
+ * The residual objective is the quantity right-preconditioned GMRES reduces.
+ * Its reverse pass through A uses a matrix-free stand-in for A^H: with one
+ * collocation point per flat element the far-field kernels of M and L' (and
+ * of L and its transpose) are the same function of the centroid pair, so
+ *   A^H ~ I/2 + D conj(L') D^-1 + i k conj(beta) D conj(L) D^-1,  D = diag(area),
+ * applied with single- and adjoint-double-layer FMM operators (mixed
+ * precision, same tree and order rule) that the preconditioner builds on
+ * first use.  The returned gradient is the pull-back through that stand-in. */
+#define FB_LOSS_ERROR 0
+#define FB_LOSS_RESIDUAL 1
+FB_API fb_status fb_learned_set_objective(fb_precond* pc, int objective);
+
 /* Training objective on a batch of residual/error pairs (R, E: npairs x N
  * complex, device, element order, pair q at offset q*N):
- *   loss = mean_q ||z(r_q) - e_q||^2 / ||e_q||^2,  z(r) = BJ(r) + s N(r/s),
+ *   loss = mean_q of the selected objective,  z(r) = BJ(r) + s ph N(...),
  * and its gradient w.r.t. the parameters (FP32, host, may be NULL). */
 FB_API fb_status fb_learned_loss_and_grad(fb_precond* pc, const double* R, const double* E, int npairs,
                                           double* loss, float* grad_host, void* stream);
@@ -318,6 +340,8 @@ typedef struct {
     double est_relres;     /* last Arnoldi residual estimate                     */
     double true_relres;    /* ||b - true_op x|| / ||b|| at exit                  */
     int status;            /* FB_OK, FB_ERR_NOCONV, FB_ERR_BREAKDOWN, FB_ERR_NAN */
+    int pc_fallbacks;      /* refinement sweeps in which a learned preconditioner
+                              was replaced by its block-Jacobi base (see below)  */
 } fb_solve_info;
 
 /* Solves A x = b by flexible GMRES (right preconditioned, restarted, FP64
@@ -325,7 +349,11 @@ typedef struct {
  * wrapped in iterative refinement on the true residual of opts->true_op:
  *   r = b - T x;  stop if ||r||/||b|| <= tol;  solve A d = r to inner_tol;  x += d.
  * x0 = 0.  b, x: N complex in memspace.  The host reads one scalar per
- * Arnoldi step (the residual estimate).  Returns info->status as the status. */
+ * Arnoldi step (the residual estimate).  Returns info->status as the status.
+ * A learned preconditioner (fb_precond_create_learned) falls back to its
+ * block-Jacobi base for the remaining sweeps when a sweep under it produced
+ * a non-finite estimate (its correction is then discarded) or failed to halve
+ * the true residual; info->pc_fallbacks counts such switches. */
 FB_API fb_status fb_fgmres_solve(fb_op* A, fb_precond* pc, const double* b, double* x,
                           const fb_solver_opts* opts, fb_solve_info* info, int memspace,
                           void* stream);

@@ -8,15 +8,21 @@ FP64 here), weights W as [in x out] with Y = X W + b:
     W0[8x64] b0[64] | Wu_k[64x64] bu_k[64] (k=0..2) | Wd_k[128x64] bd_k[64]
     (k=0..2) | Wh[128x64] bh[64] | Wo[64x2] bo[2]
 Forward (elements in tree order, SiLU activations):
-    F = [Re v/s, Im v/s, Re u/s, Im u/s, n_x, n_y, n_z, 1]
+    F = [Re v', Im v', Re u', Im u', n_x, n_y, n_z, 1],  v' = conj(ph) v / s,
+        u' = conj(ph) u / s, s = rms(v), ph = sum(v) / |sum(v)| (1 if zero)
     H0 = silu(F W0 + b0);  G_L = leaf means of H0
     G_l = silu(mean over children of G_{l+1} Wu_k + bu_k),  l = L-1-k
     D_{L-3} = G_{L-3};  D_l = silu([G_l, D_{l-1}[parent]] Wd_k + bd_k),  l = L-2+k
     H1 = silu([H0, D_L[leaf]] Wh + bh);  O = H1 Wo + bo
-    z = u + s (O_0 + i O_1)
-Loss of a pair (r, e): ||z(r) - e||^2 / ||e||^2.  ``loss_grad`` returns the
-loss and the exact FP64 gradient by reverse-mode differentiation written out
-layer by layer.
+    z = u + s ph (O_0 + i O_1)      (so z(a v) = a z(v) for complex a)
+Objectives for a pair (r, e) with A e = r:
+    error:     ||z(r) - e||^2 / ||e||^2
+    residual:  ||A z(r) - r||^2 / ||r||^2   (what right-preconditioned GMRES
+               sees: the residual the correction leaves)
+``loss_grad`` returns the loss and the FP64 gradient by reverse-mode
+differentiation written out layer by layer.  For the residual objective the
+pull-back through A uses the adjoint passed in (the exact A^H gives the exact
+gradient; ``approx_adjoint`` gives the stand-in a matrix-free code can apply).
 """
 from __future__ import annotations
 
@@ -90,9 +96,12 @@ def forward(theta, T, v, u, normals):
     top = L - depth
     s = np.sqrt(np.mean(np.abs(v) ** 2))
     inv = 1.0 / s if s > 0 else 0.0
-    vp, up, nrm = v[T.perm], u[T.perm], normals[T.perm]
-    F = np.column_stack([vp.real * inv, vp.imag * inv, up.real * inv, up.imag * inv, nrm, np.ones(n)])
-    c = {"F": F, "s": s}
+    tot = np.sum(v)
+    ph = tot / abs(tot) if abs(tot) > 0 else 1.0 + 0j
+    rot = np.conj(ph) * inv
+    vp, up, nrm = v[T.perm] * rot, u[T.perm] * rot, normals[T.perm]
+    F = np.column_stack([vp.real, vp.imag, up.real, up.imag, nrm, np.ones(n)])
+    c = {"F": F, "s": s, "ph": ph}
     c["pre0"] = F @ P["W0"] + P["b0"]
     H0 = silu(c["pre0"])
     c["H0"] = H0
@@ -117,23 +126,46 @@ def forward(theta, T, v, u, normals):
     H1 = silu(c["preh"])
     c["H1"] = H1
     O = H1 @ P["Wo"] + P["bo"]
-    zp = up + s * (O[:, 0] + 1j * O[:, 1])
+    zp = u[T.perm] + s * ph * (O[:, 0] + 1j * O[:, 1])
     z = np.empty(n, np.complex128)
     z[T.perm] = zp
     c.update(G=G, D=D, depth=depth, top=top)
     return z, c
 
 
-def loss_grad(theta, T, r, e, u, normals):
-    """(loss, gradient) for one pair; gradient in the flat layout."""
+def approx_adjoint(L, LP, area, beta, k):
+    """Stand-in for A^H, A = I/2 + M - i k L diag(beta), built from the single-
+    and adjoint-double-layer operators.  With one collocation point per flat
+    element the far-field entries satisfy M_ij ~ L'_ji a_j / a_i and
+    L_ij ~ L_ji a_j / a_i (the kernels are the same function of the centroid
+    pair), so with D = diag(area)
+        A^H ~ I/2 + D conj(L') D^-1 + i k conj(beta) D conj(L) D^-1,
+    where conj(X) y = conj(X conj(y))."""
+    def apply(w):
+        y = np.conj(w / area)
+        return 0.5 * w + area * np.conj(LP @ y) + 1j * k * np.conj(beta) * area * np.conj(L @ y)
+    return apply
+
+
+def loss_grad(theta, T, r, e, u, normals, objective="error", A=None, adjoint=None):
+    """(loss, gradient) for one pair; gradient in the flat layout.  The
+    residual objective needs A (matrix) and adjoint (callable w -> ~A^H w)."""
     P = unpack(theta)
     z, c = forward(theta, T, r, u, normals)
     L, top, depth = T.L, c["top"], c["depth"]
-    e2 = np.sum(np.abs(e) ** 2)
-    d = z - e
-    loss = np.sum(np.abs(d) ** 2) / e2
-    dz = 2.0 * d / e2
-    dzp = dz[T.perm]
+    if objective == "error":
+        e2 = np.sum(np.abs(e) ** 2)
+        d = z - e
+        loss = np.sum(np.abs(d) ** 2) / e2
+        dz = 2.0 * d / e2
+    elif objective == "residual":
+        r2 = np.sum(np.abs(r) ** 2)
+        w = A @ z - r
+        loss = np.sum(np.abs(w) ** 2) / r2
+        dz = 2.0 * adjoint(w) / r2
+    else:
+        raise ValueError(objective)
+    dzp = dz[T.perm] * np.conj(c["ph"])
     dO = c["s"] * np.column_stack([dzp.real, dzp.imag])
     g = {}
     g["Wo"] = c["H1"].T @ dO

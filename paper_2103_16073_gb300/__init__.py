@@ -27,9 +27,10 @@ __all__ = [
     "fb_mesh_destroy", "fb_tree_build", "fb_tree_info", "fb_tree_export", "fb_tree_destroy",
     "fb_operator_create", "fb_operator_apply", "fb_operator_info", "fb_operator_export",
     "fb_operator_destroy", "fb_gamma_monopole", "fb_precond_create", "fb_precond_destroy",
-    "fb_fgmres_solve", "fb_eval_field", "fb_operator_apply_timed", "fb_kernel_launches",
+    "fb_precond_apply", "fb_fgmres_solve", "fb_eval_field", "fb_operator_apply_timed", "fb_kernel_launches",
     "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
-    "fb_precond_create_learned", "fb_learned_params", "fb_learned_loss_and_grad", "fb_learned_train_step",
+    "fb_precond_create_learned", "fb_learned_params", "fb_learned_set_objective",
+    "FB_LOSS_ERROR", "FB_LOSS_RESIDUAL", "fb_learned_loss_and_grad", "fb_learned_train_step",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -56,7 +57,8 @@ class SolverOpts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iters", C.c_int), ("refinements", C.c_int), ("true_matvecs", C.c_int),
-                ("est_relres", C.c_double), ("true_relres", C.c_double), ("status", C.c_int)]
+                ("est_relres", C.c_double), ("true_relres", C.c_double), ("status", C.c_int),
+                ("pc_fallbacks", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -89,6 +91,7 @@ def _load():
         "fb_gamma_monopole": (i32, [vp, dbl, vp, vp, i32, vp]),
         "fb_precond_create": (i32, [vp, i32, vp, pvp]),
         "fb_precond_destroy": (None, [vp]),
+        "fb_precond_apply": (i32, [vp, vp, vp, i32, vp]),
         "fb_fgmres_solve": (i32, [vp, vp, vp, vp, C.POINTER(SolverOpts), C.POINTER(SolveInfo), i32, vp]),
         "fb_eval_field": (i32, [vp, dbl, vp, vp, vp, vp, i64, vp, i32, vp]),
     }
@@ -264,6 +267,17 @@ def fb_precond_destroy(pc):
     lib.fb_precond_destroy(pc)
 
 
+def fb_precond_apply(pc, x, y, stream=None):
+    px, mx, kx = _ptr(x, np.complex128)
+    if not _is_cuda_tensor(y) and not isinstance(y, np.ndarray):
+        raise ValueError("y must be a numpy array or a CUDA tensor")
+    py, my, ky = _ptr(y, np.complex128)
+    _check(lib.fb_precond_apply(pc, px, py, _same_space(mx, my), _stream(stream)))
+    if my == FB_MEM_HOST and ky is not y:
+        y[...] = ky
+    return y
+
+
 def fb_fgmres_solve(A, b, x, pc=None, tol=1e-8, restart=40, maxit=2000, max_refine=3, inner_tol=0.0,
                     true_op=None, stream=None, raise_on_noconv=False):
     pb, mb, kb = _ptr(b, np.complex128)
@@ -365,6 +379,15 @@ lib.fb_learned_loss_and_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c
 lib.fb_learned_train_step.restype = C.c_int
 lib.fb_learned_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double,
                                       C.POINTER(C.c_double), C.c_void_p]
+
+
+FB_LOSS_ERROR, FB_LOSS_RESIDUAL = 0, 1
+lib.fb_learned_set_objective.restype = C.c_int
+lib.fb_learned_set_objective.argtypes = [C.c_void_p, C.c_int]
+
+
+def fb_learned_set_objective(pc, objective):
+    _check(lib.fb_learned_set_objective(pc, int(objective)))
 
 
 def fb_precond_create_learned(op, base, seed=2103_16073, stream=None):

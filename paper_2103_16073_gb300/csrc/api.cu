@@ -173,6 +173,8 @@ fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k,
     op->kind = kind;
     op->prec = precision;
     op->k = k;
+    op->d0 = d0;
+    op->pmin = pmin;
     op->n = mesh->n;
     fb_status st = precision == FB_PREC_FP64_DENSE ? fb_dense_create(op, s) : fb_fmm_create(op, d0, pmin, s);
     if (st == FB_OK) {
@@ -202,6 +204,21 @@ fb_status fb_operator_apply(fb_op* op, const double* x, double* y, int memspace,
 }
 
 long long fb_kernel_launches(void) { return g_launches.load(); }
+
+fb_status fb_precond_apply(const fb_precond* pc, const double* x, double* y, int memspace, void* stream) {
+    if (!pc || !x || !y) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (x == y) return fb_fail(FB_ERR_ARG, "x and y must not overlap");
+    cudaStream_t s = as_stream(stream);
+    size_t bytes = sizeof(cd) * pc->n;
+    Staged sx, sy;
+    const void* dx = nullptr;
+    void* dy = nullptr;
+    FB_CHECK(stage_in(x, bytes, memspace, sx, &dx, s));
+    FB_CHECK(stage_out_alloc(bytes, memspace, y, sy, &dy));
+    FB_CHECK(fb_pc_apply(pc, (const cd*)dx, (cd*)dy, s));
+    FB_LAUNCH_CHECK();
+    return stage_out_finish(bytes, memspace, y, sy, s);
+}
 
 fb_status fb_measure_alu_peaks(double* fp32_tflops, double* fp64_tflops, void* stream) {
     return fb_alu_peaks_impl(fp32_tflops, fp64_tflops, as_stream(stream));
@@ -408,6 +425,11 @@ fb_status fb_learned_params(fb_precond* pc, float* host_out, const float* host_i
     *count = np;
     if (host_out) FB_CUDA(cudaMemcpy(host_out, fb_learned_weights(pc->net), sizeof(float) * np, cudaMemcpyDeviceToHost));
     return FB_OK;
+}
+
+fb_status fb_learned_set_objective(fb_precond* pc, int objective) {
+    FB_CHECK(learned_of(pc));
+    return fb_learned_set_objective(pc->net, objective);
 }
 
 fb_status fb_learned_loss_and_grad(fb_precond* pc, const double* R, const double* E, int npairs, double* loss,

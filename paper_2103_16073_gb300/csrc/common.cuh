@@ -234,6 +234,8 @@ struct fb_op {
     int dev = 0;
     int kind = 0, prec = 0;
     double k = 0;
+    double d0 = 0;           // order rule parameters (FMM)
+    int pmin = 0;
     int64_t n = 0;
     // dense
     cd* dense = nullptr;
@@ -328,6 +330,8 @@ fb_status fb_learned_forward(LearnedNet* net, const cd* v, cd* z, cudaStream_t s
 fb_status fb_learned_loss_grad(LearnedNet* net, const cd* R, const cd* E, int npairs, double* loss, cudaStream_t s);
 fb_status fb_learned_adam_step(LearnedNet* net, double lr, cudaStream_t s);
 fb_status fb_learned_init(LearnedNet* net, uint64_t seed, cudaStream_t s);
+fb_status fb_learned_adjoint_ops(LearnedNet* net, cudaStream_t s);
+fb_status fb_learned_set_objective(LearnedNet* net, int objective);
 int64_t fb_learned_nparam(const LearnedNet* net);
 float* fb_learned_weights(LearnedNet* net);
 float* fb_learned_grads(LearnedNet* net);
@@ -339,5 +343,5 @@ fb_status fb_tc_check(const fb_op* op);
 void fb_tc_free(void*& plan);
 void fb_fmm_destroy(fb_op* op);
 fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s);
-fb_status fb_precond_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s);
+fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s);
 int fb_order_rule(double k, double delta, double d0, int pmin);

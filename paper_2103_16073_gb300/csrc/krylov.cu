@@ -235,7 +235,7 @@ static fb_status fgmres_inner(fb_op* A, fb_precond* pc, Work& W, const cd* rhs, 
             cd* zj = vj;
             if (pc) {
                 zj = W.Z + (int64_t)j * n;
-                FB_CHECK(fb_precond_apply(pc, vj, zj, s));
+                FB_CHECK(fb_pc_apply(pc, vj, zj, s));
             }
             FB_CHECK(fb_apply_any(A, zj, W.w, s));
             for (int pass = 0; pass < 2; ++pass) {
@@ -327,15 +327,24 @@ fb_status fb_fgmres_impl(fb_op* A, fb_precond* pc, const cd* b, cd* x, const fb_
     double rn = bn;
     double inner_floor = opts.inner_tol > 0 ? opts.inner_tol : 0.0;
     int status = FB_OK;
+    fb_precond* cur = pc;
     for (int sweep = 0; sweep < opts.max_refine; ++sweep) {
         if (rn <= opts.tol * bn) break;
         double rel = std::max(inner_floor, 0.5 * opts.tol * bn / rn);
         int its = 0, st = FB_OK;
         double est_rel = 0;
-        FB_CHECK(fgmres_inner(A, pc, W, W.r, rn, rel, opts.maxit - inf.iters, &its, &est_rel, &st, s));
+        FB_CHECK(fgmres_inner(A, cur, W, W.r, rn, rel, opts.maxit - inf.iters, &its, &est_rel, &st, s));
         inf.iters += its;
         inf.est_relres = est_rel * rn / bn;
         inf.refinements = sweep + 1;
+        const bool learned = cur && cur->net && cur->base;
+        if (learned && st == FB_ERR_NAN) {
+            // discard the correction and continue under the block-Jacobi base
+            cur = const_cast<fb_precond*>(cur->base);
+            inf.pc_fallbacks++;
+            if (inf.iters >= opts.maxit) break;
+            continue;
+        }
         k_add<<<grid_for(n), KB, 0, s>>>(x, W.d, n);
         cnt();
         // true residual r = b - T x
@@ -347,8 +356,13 @@ fb_status fb_fgmres_impl(fb_op* A, fb_precond* pc, const cd* b, cd* x, const fb_
         double r2 = 0;
         FB_CHECK(norm2(W.r, n, W.scal + 4, s));
         FB_CHECK(read_scalar(W.scal + 4, &r2, s));
+        const double rn_prev = rn;
         rn = std::sqrt(r2);
         if (st != FB_OK) { status = st; break; }
+        if (learned && std::isfinite(rn) && rn > opts.tol * bn && !(rn <= 0.5 * rn_prev)) {
+            cur = const_cast<fb_precond*>(cur->base);
+            inf.pc_fallbacks++;
+        }
         if (!std::isfinite(rn)) { status = FB_ERR_NAN; break; }
         if (inf.iters >= opts.maxit) break;
     }
@@ -519,7 +533,7 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
     return FB_OK;
 }
 
-fb_status fb_precond_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s) {
+fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s) {
     if (pc->net) return fb_learned_forward(pc->net, x, y, s);
     const fb_tree* t = pc->op->tree;
     int nleaf = t->nbox[t->L];

@@ -6,14 +6,16 @@
 // ||z(r) - e||^2 / ||e||^2.
 //
 // Network (64-wide features, SiLU, weights W as [in x out], Y = X W + b):
-//   features f_i = (Re v_i, Im v_i, Re u_i, Im u_i)/s, n_i, 1   (u = BJ(v),
-//                  s = rms of v, elements in tree order)
+//   features f_i = (Re, Im of v_i conj(ph), u_i conj(ph))/s, n_i, 1
+//                  (u = BJ(v), s = rms of v, ph = unit phase of sum_i v_i,
+//                  elements in tree order)
 //   H0 = silu(F W0 + b0)                                  elements
 //   G_L = mean of H0 over each leaf                       leaves
 //   G_l = silu(mean of G_{l+1} over children W_up,k + b)  3 coarser levels
 //   D_{L-3} = G_{L-3};  D_l = silu([G_l, D_{l-1}(parent)] W_dn,k + b)
 //   H1 = silu([H0, D_L(leaf)] W_h + b_h),  O = H1 W_o + b_o (Re, Im)
-//   z_i = u_i + s (O_i0 + i O_i1)
+//   z_i = u_i + s ph (O_i0 + i O_i1)
+// so N(a v) = a N(v) for any complex a, as for a linear preconditioner.
 // All GEMMs run on the tensor cores as BF16 x BF16 -> FP32 (mma.sync
 // m16n8k16) with FP32 activations rounded to BF16 while staging; master
 // weights, gradients and Adam moments are FP32.
@@ -125,34 +127,70 @@ __global__ void __launch_bounds__(128) k_gemm_bf16(GemmArgs g) {
 }
 
 // --------------------------------------------------------------- helpers ----
-__global__ void k_rms(const cd* v, int64_t n, double* out) {
-    __shared__ double sh[32];
-    double a = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        a += abs2(v[i]);
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = a;
+// Input statistics: st[0] += sum |v|^2, st[3..4] += sum v (complex).  The
+// scale s = rms(v) and the phase of sum v normalise the input, so that the
+// network's map is complex-homogeneous: N(a v) = a N(v) for every complex a.
+__global__ void k_stats(const cd* v, int64_t n, double* st) {
+    __shared__ double sh[3][32];
+    double a = 0.0, cr = 0.0, ci = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        cd x = v[i];
+        a += abs2(x);
+        cr += x.re;
+        ci += x.im;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        cr += __shfl_xor_sync(0xffffffffu, cr, o);
+        ci += __shfl_xor_sync(0xffffffffu, ci, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sh[0][threadIdx.x >> 5] = a;
+        sh[1][threadIdx.x >> 5] = cr;
+        sh[2][threadIdx.x >> 5] = ci;
+    }
     __syncthreads();
     if (threadIdx.x < 32) {
-        a = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        if (threadIdx.x == 0) atomicAdd(out, a);
+        bool in = threadIdx.x < (blockDim.x >> 5);
+        a = in ? sh[0][threadIdx.x] : 0.0;
+        cr = in ? sh[1][threadIdx.x] : 0.0;
+        ci = in ? sh[2][threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            cr += __shfl_xor_sync(0xffffffffu, cr, o);
+            ci += __shfl_xor_sync(0xffffffffu, ci, o);
+        }
+        if (threadIdx.x == 0) {
+            atomicAdd(&st[0], a);
+            atomicAdd(&st[3], cr);
+            atomicAdd(&st[4], ci);
+        }
     }
 }
 
-// features in tree order
-__global__ void k_features(Geom g, const int32_t* perm, const cd* v, const cd* u, const double* ssum,
+// unit phase of sum v (1 when the sum vanishes)
+__device__ __forceinline__ cd input_phase(const double* st) {
+    double m = hypot(st[3], st[4]);
+    return m > 0.0 ? mk(st[3] / m, st[4] / m) : mk(1.0, 0.0);
+}
+
+// features in tree order: (v, u) rotated by the conjugate input phase and
+// divided by s
+__global__ void k_features(Geom g, const int32_t* perm, const cd* v, const cd* u, const double* st,
                            int64_t n, float* F) {
     int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (pos >= n) return;
-    double s = sqrt(*ssum / (double)n);
+    double s = sqrt(st[0] / (double)n);
     double inv = s > 0.0 ? 1.0 / s : 0.0;
+    cd ph = input_phase(st);
+    cd rot = mk(ph.re * inv, -ph.im * inv);
     int64_t e = perm[pos];
+    cd vv = v[e] * rot, uu = u[e] * rot;
     float* f = F + pos * NF;
-    f[0] = (float)(v[e].re * inv);
-    f[1] = (float)(v[e].im * inv);
-    f[2] = (float)(u[e].re * inv);
-    f[3] = (float)(u[e].im * inv);
+    f[0] = (float)vv.re;
+    f[1] = (float)vv.im;
+    f[2] = (float)uu.re;
+    f[3] = (float)uu.im;
     f[4] = (float)g.nx[e];
     f[5] = (float)g.ny[e];
     f[6] = (float)g.nz[e];
@@ -217,13 +255,15 @@ __global__ void k_colsum(const float* X, int64_t rows, int cols, float* out) {
     if ((threadIdx.x & 31) == 0) atomicAdd(&out[c], a);
 }
 
-// z (element order) = u + s (O0 + i O1)
-__global__ void k_output(const int32_t* perm, const cd* u, const float* O, const double* ssum, int64_t n, cd* z) {
+// z (element order) = u + s ph (O0 + i O1)
+__global__ void k_output(const int32_t* perm, const cd* u, const float* O, const double* st, int64_t n, cd* z) {
     int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (pos >= n) return;
-    double s = sqrt(*ssum / (double)n);
+    double s = sqrt(st[0] / (double)n);
+    cd ph = input_phase(st);
     int64_t e = perm[pos];
-    z[e] = mk(u[e].re + s * (double)O[pos * 2], u[e].im + s * (double)O[pos * 2 + 1]);
+    cd o = mk(s * (double)O[pos * 2], s * (double)O[pos * 2 + 1]) * ph;
+    z[e] = u[e] + o;
 }
 
 // loss pieces: sum |z - e|^2, sum |e|^2; dO = 2 s (z - e) / ||e||^2 (tree order)
@@ -251,15 +291,48 @@ __global__ void k_loss_sums(const cd* z, const cd* e, int64_t n, double* sums) {
         if (threadIdx.x == 0) { atomicAdd(&sums[0], a); atomicAdd(&sums[1], b); }
     }
 }
-__global__ void k_loss_grad(const int32_t* perm, const cd* z, const cd* e, const double* ssum, const double* sums,
+// dO = 2 s conj(ph) (z - e) / ||e||^2 as (Re, Im), tree order
+__global__ void k_loss_grad(const int32_t* perm, const cd* z, const cd* e, const double* st, const double* sums,
                             int64_t n, double scale, float* dO) {
     int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (pos >= n) return;
-    double s = sqrt(*ssum / (double)n);
+    double s = sqrt(st[0] / (double)n);
+    cd ph = input_phase(st);
     int64_t i = perm[pos];
     double f = scale * 2.0 * s / sums[1];
-    dO[pos * 2] = (float)(f * (z[i].re - e[i].re));
-    dO[pos * 2 + 1] = (float)(f * (z[i].im - e[i].im));
+    cd d = (z[i] - e[i]) * mk(f * ph.re, -f * ph.im);
+    dO[pos * 2] = (float)d.re;
+    dO[pos * 2 + 1] = (float)d.im;
+}
+
+// Residual objective.  yc = conj((A z - r) / area)
+__global__ void k_adj_prep(const cd* az, const cd* r, const double* area, int64_t n, cd* yc) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    cd w = az[i] - r[i];
+    double ia = 1.0 / area[i];
+    yc[i] = mk(w.re * ia, -w.im * ia);
+}
+// g = w/2 + a conj(t1) + i k conj(beta) a conj(t2)  (t1 = L' yc, t2 = L yc),
+// the stand-in adjoint applied to w = A z - r; dO = 2 s conj(ph) g / ||r||^2
+__global__ void k_adj_grad(const int32_t* perm, const cd* az, const cd* r, const cd* t1, const cd* t2,
+                           const double* area, const cd* beta, double k, const double* st, const double* sums,
+                           int64_t n, double scale, float* dO) {
+    int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (pos >= n) return;
+    double s = sqrt(st[0] / (double)n);
+    cd ph = input_phase(st);
+    int64_t i = perm[pos];
+    cd w = az[i] - r[i];
+    double a = area[i];
+    cd c1 = mk(a * t1[i].re, -a * t1[i].im);
+    cd c2 = mk(a * t2[i].re, -a * t2[i].im);
+    cd ikb = mk(k * beta[i].im, k * beta[i].re);      // i k conj(beta)
+    cd g = mk(0.5 * w.re, 0.5 * w.im) + c1 + ikb * c2;
+    double f = scale * 2.0 * s / sums[1];
+    cd d = g * mk(f * ph.re, -f * ph.im);
+    dO[pos * 2] = (float)d.re;
+    dO[pos * 2 + 1] = (float)d.im;
 }
 
 __global__ void k_adam(float* w, const float* gr, float* m, float* v, int64_t n, float lr, float b1, float b2,
@@ -306,7 +379,12 @@ struct LearnedNet {
     int32_t* child_start[FB_MAXLEV + 1] = {nullptr};   // children of box b at level l: [cs[b], cs[b+1]) at level l+1
     int32_t* leaf_of = nullptr;                         // tree position -> leaf
     cd *u = nullptr, *z = nullptr;
-    double* scal = nullptr;    // [0] sum |v|^2, [1..2] loss sums
+    double* scal = nullptr;    // [0] sum |v|^2, [1..2] loss sums, [3..4] sum v
+    // residual objective: single- and adjoint-double-layer operators (mixed
+    // FMM, built on first use) for the stand-in adjoint, and work vectors
+    int objective = FB_LOSS_RESIDUAL;
+    fb_op *opL = nullptr, *opLP = nullptr;
+    cd *az = nullptr, *yc = nullptr, *t1 = nullptr, *t2 = nullptr;
 };
 
 static void gemm(cudaStream_t s, const float* A, int64_t am, int64_t ak, const float* B, int64_t bk, int64_t bn,
@@ -407,7 +485,7 @@ fb_status fb_learned_alloc(LearnedNet*& net, const fb_op* op, const fb_precond* 
     k_leaf_of_pos<<<t->nbox[L], 64, 0, s>>>(t->leaf_start, t->nbox[L], net->leaf_of);
     FB_CHECK(dalloc(&net->u, n));
     FB_CHECK(dalloc(&net->z, n));
-    FB_CHECK(dalloc(&net->scal, 4));
+    FB_CHECK(dalloc(&net->scal, 8));
     FB_LAUNCH_CHECK();
     return FB_OK;
 }
@@ -426,6 +504,9 @@ void fb_learned_free(LearnedNet*& net) {
     dfree(net->u);
     dfree(net->z);
     dfree(net->scal);
+    dfree(net->az); dfree(net->yc); dfree(net->t1); dfree(net->t2);
+    fb_operator_destroy(net->opL);
+    fb_operator_destroy(net->opLP);
     delete net;
     net = nullptr;
 }
@@ -437,9 +518,9 @@ fb_status fb_learned_forward(LearnedNet* net, const cd* v, cd* z, cudaStream_t s
     int L = net->L, Ltop = L - net->depth;
     int64_t n = net->n;
     int nleaf = t->nbox[L];
-    FB_CHECK(fb_precond_apply(net->bj, v, net->u, s));
-    FB_CUDA(cudaMemsetAsync(net->scal, 0, sizeof(double), s));
-    k_rms<<<std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(v, n, net->scal);
+    FB_CHECK(fb_pc_apply(net->bj, v, net->u, s));
+    FB_CUDA(cudaMemsetAsync(net->scal, 0, 8 * sizeof(double), s));
+    k_stats<<<std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(v, n, net->scal);
     k_features<<<div_up(n, 256), 256, 0, s>>>(g, t->perm, v, net->u, net->scal, n, net->F);
     fb_count_launch(2);
     const float* w = net->w;
@@ -481,9 +562,26 @@ fb_status fb_learned_backward(LearnedNet* net, const cd* r, const cd* e, double 
     int nleaf = t->nbox[L];
     FB_CHECK(fb_learned_forward(net, r, net->z, s));
     FB_CUDA(cudaMemsetAsync(net->scal + 1, 0, 2 * sizeof(double), s));
-    k_loss_sums<<<std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(net->z, e, n, net->scal + 1);
-    k_loss_grad<<<div_up(n, 256), 256, 0, s>>>(t->perm, net->z, e, net->scal, net->scal + 1, n, scale, net->dO);
-    fb_count_launch(2);
+    const int red = std::min<int64_t>(div_up(n, 256), 1024);
+    if (net->objective == FB_LOSS_ERROR) {
+        k_loss_sums<<<red, 256, 0, s>>>(net->z, e, n, net->scal + 1);
+        k_loss_grad<<<div_up(n, 256), 256, 0, s>>>(t->perm, net->z, e, net->scal, net->scal + 1, n, scale,
+                                                   net->dO);
+        fb_count_launch(2);
+    } else {
+        FB_CHECK(fb_learned_adjoint_ops(net, s));
+        const fb_op* A = net->op;
+        const Geom& g = A->mesh->g;
+        FB_CHECK(fb_apply_any(const_cast<fb_op*>(A), net->z, net->az, s));
+        k_loss_sums<<<red, 256, 0, s>>>(net->az, r, n, net->scal + 1);   // ||A z - r||^2, ||r||^2
+        k_adj_prep<<<div_up(n, 256), 256, 0, s>>>(net->az, r, g.area, n, net->yc);
+        fb_count_launch(2);
+        FB_CHECK(fb_apply_any(net->opLP, net->yc, net->t1, s));
+        FB_CHECK(fb_apply_any(net->opL, net->yc, net->t2, s));
+        k_adj_grad<<<div_up(n, 256), 256, 0, s>>>(t->perm, net->az, r, net->t1, net->t2, g.area, g.beta, A->k,
+                                                  net->scal, net->scal + 1, n, scale, net->dO);
+        fb_count_launch();
+    }
     float* w = net->w;
     float* gr = net->grad;
     auto colsum = [&](const float* X, int64_t rows, int cols, float* out) {
@@ -547,6 +645,29 @@ fb_status fb_learned_backward(LearnedNet* net, const cd* r, const cd* e, double 
     gemm(s, net->F, 1, NF, net->dtmp, HW, 1, gr + net->oW0, HW, 1, NF, HW, (int)n, nullptr, nullptr, 0, 1);
     colsum(net->dtmp, n, HW, gr + net->ob0);
     FB_LAUNCH_CHECK();
+    return FB_OK;
+}
+
+// Operators of the stand-in adjoint (built once, same tree, k and order rule
+// as the served operator, mixed precision).
+fb_status fb_learned_adjoint_ops(LearnedNet* net, cudaStream_t s) {
+    if (net->opL && net->opLP) return FB_OK;
+    const fb_op* A = net->op;
+    int64_t n = net->n;
+    void* st = (void*)s;
+    FB_CHECK(fb_operator_create(A->mesh, A->tree, A->k, FB_OP_L, FB_PREC_MIXED_FMM, A->d0, A->pmin, st, &net->opL));
+    FB_CHECK(fb_operator_create(A->mesh, A->tree, A->k, FB_OP_LP, FB_PREC_MIXED_FMM, A->d0, A->pmin, st,
+                                &net->opLP));
+    FB_CHECK(dalloc(&net->az, n));
+    FB_CHECK(dalloc(&net->yc, n));
+    FB_CHECK(dalloc(&net->t1, n));
+    FB_CHECK(dalloc(&net->t2, n));
+    return FB_OK;
+}
+
+fb_status fb_learned_set_objective(LearnedNet* net, int objective) {
+    if (objective != FB_LOSS_ERROR && objective != FB_LOSS_RESIDUAL) return fb_fail(FB_ERR_ARG, "unknown objective");
+    net->objective = objective;
     return FB_OK;
 }
 

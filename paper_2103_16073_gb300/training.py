@@ -1,14 +1,22 @@
 """Training driver of the learned octree preconditioner.
 
 Orchestration only: every step runs in the library (FGMRES solves, operator
-applications, the network's forward/backward kernels and Adam).  Pairs
-(r, e) come from the plain method's own solves: FGMRES with block Jacobi is
-stopped after j iterations for several j, giving iterates x_j with
-r_j = b - A x_j and e_j = x* - x_j, where x* is the converged solution, so
-A e_j = r_j holds for the operator A the preconditioner will serve.
+and preconditioner applications, the network's forward/backward kernels and
+Adam).  Pairs (r, e) come from the plain method's own solves: FGMRES with
+block Jacobi is stopped after j iterations for several j, giving iterates x_j
+with r_j = b - A x_j and e_j = x* - x_j, where x* is the converged solution,
+so A e_j = r_j holds for the operator A the preconditioner will serve.
+
+The default objective is the residual one, ||A z(r) - r||^2 / ||r||^2, which
+does not use e; for it the logged residuals can be joined by white-noise
+inputs (``augment_noise``) so that the network does not trade accuracy on
+the directions the Krylov basis also contains for accuracy on the logged
+residuals.  ``train`` can keep the parameters that did best on a validation
+solve (``validate``), the block-Jacobi-like initial state included.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 import paper_2103_16073_gb300 as fb
@@ -32,12 +40,28 @@ def collect_pairs(A, bj, b, iterates=(1, 2, 3, 4, 6, 8, 10, 13, 16), restart=40,
     return R, E
 
 
-def train(pc, R, E, steps=200, lr=1e-3, batch=8, seed=0, log_every=0):
-    """Adam on random mini-batches of the pairs; returns the loss history."""
+def augment_noise(R, E, count, seed=0):
+    """Appends `count` white-noise inputs (for the residual objective only;
+    their E rows are zero and unused)."""
+    g = torch.Generator(device=R.device)
+    g.manual_seed(seed)
+    Nz = torch.randn((count, R.shape[1]), dtype=R.dtype, device=R.device, generator=g)
+    return torch.cat([R, Nz]), torch.cat([E, torch.zeros_like(Nz)])
+
+
+def train(pc, R, E, steps=200, lr=1e-3, batch=8, seed=0, log_every=0, validate=None, every=20):
+    """Adam on random mini-batches of the pairs.  With `validate` (a callable
+    returning a score, lower is better, e.g. FGMRES iterations on a held-out
+    right-hand side) the parameters with the best score, the initial ones
+    included, are restored at the end.  Returns (loss history, validation log)."""
     g = torch.Generator(device="cpu")
     g.manual_seed(seed)
-    hist = []
+    hist, vlog = [], []
     npairs = R.shape[0]
+    best = None
+    if validate is not None:
+        best = (validate(), fb.fb_learned_params(pc))
+        vlog.append((0, best[0]))
     for it in range(steps):
         idx = torch.randperm(npairs, generator=g)[:min(batch, npairs)].to(R.device)
         Rb = R.index_select(0, idx).contiguous()
@@ -46,10 +70,30 @@ def train(pc, R, E, steps=200, lr=1e-3, batch=8, seed=0, log_every=0):
         hist.append(loss)
         if log_every and it % log_every == 0:
             print(f"step {it} loss {loss:.4f}", flush=True)
-    return hist
+        if validate is not None and ((it + 1) % every == 0 or it + 1 == steps):
+            sc = validate()
+            vlog.append((it + 1, sc))
+            if sc < best[0]:
+                best = (sc, fb.fb_learned_params(pc))
+    if best is not None:
+        fb.fb_learned_params(pc, best[1])
+    return hist, vlog
 
 
 def evaluate(pc, R, E):
-    """Mean relative squared error of the preconditioner on the pairs."""
+    """Mean objective of the preconditioner on the pairs."""
     loss, _ = fb.fb_learned_loss_and_grad(pc, R.contiguous(), E.contiguous())
     return loss
+
+
+def residual_error(A, pc, R):
+    """Mean ||A P(r) - r|| / ||r|| over the rows of R: how far A P is from the
+    identity on those inputs (what right-preconditioned GMRES sees)."""
+    z = torch.empty_like(R[0])
+    az = torch.empty_like(z)
+    out = []
+    for q in range(R.shape[0]):
+        fb.fb_precond_apply(pc, R[q], z)
+        fb.fb_operator_apply(A, z, az)
+        out.append(((az - R[q]).norm() / R[q].norm()).item())
+    return float(np.mean(out))

@@ -55,3 +55,66 @@ def test_zero_output_layer_is_block_jacobi():
         theta[o:o + n] = 0.0
     z, _ = learned.forward(theta, T, r, u, nrm)
     assert np.max(np.abs(z - u)) == 0.0
+
+
+def test_complex_homogeneous():
+    """The network's input normalisation (rms scale, phase of sum v) makes the
+    map commute with complex scaling, as a linear preconditioner does."""
+    T, r, e, u, nrm, theta = _setup()
+    z, _ = learned.forward(theta, T, r, u, nrm)
+    for a in (2.5, -1.0, 1j, 0.3 * np.exp(2.1j)):
+        za, _ = learned.forward(theta, T, a * r, a * u, nrm)
+        assert np.max(np.abs(za - a * z)) < 1e-12 * abs(a) * np.max(np.abs(z))
+    # and the map is not linear (the network is not a fixed matrix)
+    r2 = np.roll(r, 7)
+    u2 = np.roll(u, 7)
+    z2, _ = learned.forward(theta, T, r2, u2, nrm)
+    z12, _ = learned.forward(theta, T, r + r2, u + u2, nrm)
+    assert np.max(np.abs(z12 - z - z2)) > 1e-3 * np.max(np.abs(z))
+
+
+def _dense_small():
+    v, t, _ = W.shoebox_mesh(1.0, 0.8, 0.6, 8, 6, 5)
+    mesh = bem.Mesh(v, t)
+    k = 4.0
+    beta = np.full(mesh.n, 0.2 + 0.05j)
+    L, M, LP = bem.dense_operators(mesh, k)
+    return mesh, k, beta, L, LP, bem.system_matrix(L, M, k, beta)
+
+
+def test_residual_objective_exact_adjoint_gradient():
+    """With the exact A^H the residual objective's reverse pass is the exact
+    gradient: central differences agree, and the loss is its definition."""
+    T, r, e, u, nrm, theta = _setup()
+    mesh, k, beta, L, LP, A = _dense_small()
+    assert mesh.n == r.size
+    AH = A.conj().T
+    adj = lambda w: AH @ w
+    loss, g = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, adj)
+    z, _ = learned.forward(theta, T, r, u, nrm)
+    assert abs(loss - np.linalg.norm(A @ z - r) ** 2 / np.linalg.norm(r) ** 2) < 1e-12 * loss
+    rng = np.random.default_rng(3)
+    h = 1e-6
+    for _ in range(4):
+        d = rng.standard_normal(theta.size)
+        lp, _ = learned.loss_grad(theta + h * d, T, r, e, u, nrm, "residual", A, adj)
+        lm, _ = learned.loss_grad(theta - h * d, T, r, e, u, nrm, "residual", A, adj)
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - g @ d) < 1e-6 * max(1.0, abs(fd))
+
+
+def test_approximate_adjoint_is_close():
+    """The matrix-free stand-in for A^H (single- and adjoint-double-layer with
+    area scaling) is within a few percent of the exact adjoint, and its
+    surrogate gradient points downhill (positive inner product with the exact
+    gradient)."""
+    T, r, e, u, nrm, theta = _setup()
+    mesh, k, beta, L, LP, A = _dense_small()
+    adj = learned.approx_adjoint(L, LP, mesh.el.area, beta, k)
+    rng = np.random.default_rng(2)
+    w = rng.standard_normal(mesh.n) + 1j * rng.standard_normal(mesh.n)
+    ex = A.conj().T @ w
+    assert np.linalg.norm(adj(w) - ex) / np.linalg.norm(ex) < 0.1
+    _, g_ex = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, lambda x: A.conj().T @ x)
+    _, g_ap = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, adj)
+    assert g_ap @ g_ex > 0.9 * np.linalg.norm(g_ap) * np.linalg.norm(g_ex)
