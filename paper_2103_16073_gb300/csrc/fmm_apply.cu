@@ -176,12 +176,78 @@ __device__ __forceinline__ void nm_of(int e, int& n, int& m) {
     m = e - n * n - n;
 }
 
+// Each thread owns one coefficient index and computes it for a chunk of W
+// pairs at once, so every rotation / coaxial entry it loads is used W times
+// from registers; the pair operands come from shared memory, where the
+// threads of a warp that share a degree read the same word (broadcast).
+// Full chunks use W = RcrChunk, the remainder of a tile one pair at a time.
+template <class R> struct RcrChunk { static constexpr int value = 8; };
+template <> struct RcrChunk<double> { static constexpr int value = 4; };
+
+template <int W, class R>
+__device__ __forceinline__ void rcr_rotate(const cx<R>* Dn, int n, const cx<R>* xs, int Pin, int b0, int e,
+                                           cx<R>* us) {
+    cx<R> acc[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) acc[j] = mk<R>(0, 0);
+    const cx<R>* xb = xs + b0 * Pin + n * n;
+#pragma unroll 4
+    for (int m = 0; m <= 2 * n; ++m) {
+        cx<R> d = Dn[m];
+#pragma unroll
+        for (int j = 0; j < W; ++j) cmac(acc[j], d, xb[j * Pin + m]);
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) us[(b0 + j) * Pin + e] = acc[j];
+}
+
+template <int W, class R>
+__device__ __forceinline__ void rcr_coax(const cx<R>* Cr, int am, int mu, int pmid, const cx<R>* us, int Pin,
+                                         int Pout, int b0, int e, cx<R>* vs) {
+    cx<R> acc[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) acc[j] = mk<R>(0, 0);
+    const cx<R>* ub = us + b0 * Pin;
+#pragma unroll 4
+    for (int n = am; n < pmid; ++n) {
+        cx<R> c = Cr[n];
+        int o = n * n + n + mu;
+#pragma unroll
+        for (int j = 0; j < W; ++j) cmac(acc[j], c, ub[j * Pin + o]);
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) vs[(b0 + j) * Pout + e] = acc[j];
+}
+
+template <int W, class R>
+__device__ __forceinline__ void rcr_back(const cx<R>* Dn, int n1, const cx<R>* vs, int Pout, int b0, int e,
+                                         const int32_t* dsti, cx<R>* dst) {
+    cx<R> acc[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) acc[j] = mk<R>(0, 0);
+    int w = 2 * n1 + 1;
+    const cx<R>* vb = vs + b0 * Pout + n1 * n1;
+#pragma unroll 4
+    for (int mu = 0; mu < w; ++mu) {
+        cx<R> d = Dn[(int64_t)mu * w];
+#pragma unroll
+        for (int j = 0; j < W; ++j) cmacc(acc[j], d, vb[j * Pout + mu]);
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        cx<R>* d = dst + (int64_t)dsti[b0 + j] * Pout + e;
+        atomicAdd(&d->re, acc[j].re);
+        atomicAdd(&d->im, acc[j].im);
+    }
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, const RcrTile* __restrict__ tiles,
                                              const cx<R>* __restrict__ rot, const cx<R>* __restrict__ coax,
                                              const int32_t* __restrict__ src_idx,
                                              const int32_t* __restrict__ dst_idx,
                                              const cx<R>* __restrict__ src, cx<R>* __restrict__ dst) {
+    constexpr int BCH = RcrChunk<R>::value;
     extern __shared__ unsigned char smem_raw[];
     RcrTile tl = tiles[blockIdx.x];
     RcrTask tk = tasks[tl.task];
@@ -189,9 +255,9 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
     const int Pin = tk.p_in * tk.p_in, Pout = tk.p_out * tk.p_out;
     const int pmid = tk.p_in;   // the rotated input keeps degrees n < p_in
     cx<R>* buf = (cx<R>*)smem_raw;
-    cx<R>* xs = buf;                    // [nb][Pin]
-    cx<R>* us = buf + nb * Pin;         // [nb][Pin]
-    cx<R>* vs = buf + 2 * nb * Pin;     // [nb][Pout]
+    cx<R>* xs = buf;                    // [nb][Pin], later reused for vs
+    cx<R>* us = buf + nb * max(Pin, Pout);   // [nb][Pin]
+    cx<R>* vs = buf;                    // [nb][Pout] (xs is dead after the rotation)
     int tid = threadIdx.x, nth = blockDim.x;
     for (int q = tid; q < nb * Pin; q += nth) {
         int b = q / Pin, e = q % Pin;
@@ -200,47 +266,51 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
     }
     __syncthreads();
     const cx<R>* D = rot + tk.rot_off;
-    for (int q = tid; q < nb * Pin; q += nth) {
-        int b = q / Pin, e = q % Pin;
+    // chunk widths BCH, then 4, 2, 1 for the rest of the tile
+#define RCR_CHUNKS(CALL)                                              \
+    {                                                                 \
+        int b0 = 0;                                                   \
+        for (; b0 + BCH <= nb; b0 += BCH) CALL(BCH);                  \
+        if (BCH > 4 && b0 + 4 <= nb) { CALL(4); b0 += 4; }            \
+        if (b0 + 2 <= nb) { CALL(2); b0 += 2; }                       \
+        if (b0 < nb) CALL(1);                                         \
+    }
+    // rotate: u_n^mu = sum_m D^n_{mu,m} x_n^m
+    for (int e = tid; e < Pin; e += nth) {
         int n, mu;
         nm_of(e, n, mu);
         const cx<R>* Dn = D + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3 + (int64_t)(mu + n) * (2 * n + 1);
-        const cx<R>* xb = xs + b * Pin + n * n;
-        cx<R> acc = mk<R>(0, 0);
-        for (int m = 0; m <= 2 * n; ++m) cmac(acc, Dn[m], xb[m]);
-        us[q] = acc;
+#define RCR_ROT(W) rcr_rotate<(W)>(Dn, n, xs, Pin, b0, e, us)
+        RCR_CHUNKS(RCR_ROT)
+#undef RCR_ROT
     }
     __syncthreads();
+    // coaxial: v_{n'}^mu = sum_n C^{|mu|}_{n'n} u_n^mu
     const cx<R>* C = coax + tk.coax_off;
     const int pc = tk.pc;
-    for (int q = tid; q < nb * Pout; q += nth) {
-        int b = q / Pout, e = q % Pout;
+    for (int e = tid; e < Pout; e += nth) {
         int n1, mu;
         nm_of(e, n1, mu);
         int am = abs(mu);
-        cx<R> acc = mk<R>(0, 0);
-        if (am < pmid) {
-            const cx<R>* Cr = C + ((int64_t)am * pc + n1) * pc;
-            const cx<R>* ub = us + b * Pin;
-            for (int n = am; n < pmid; ++n) cmac(acc, Cr[n], ub[n * n + n + mu]);
-        }
-        vs[q] = acc;
+        const cx<R>* Cr = C + ((int64_t)am * pc + n1) * pc;
+        const int hi = am < pmid ? pmid : am;   // empty sum when |mu| >= p_in
+#define RCR_COAX(W) rcr_coax<(W)>(Cr, am, mu, hi, us, Pin, Pout, b0, e, vs)
+        RCR_CHUNKS(RCR_COAX)
+#undef RCR_COAX
     }
     __syncthreads();
-    for (int q = tid; q < nb * Pout; q += nth) {
-        int b = q / Pout, e = q % Pout;
+    // back-rotate: y_{n'}^{m'} = sum_mu conj(D^{n'}_{mu,m'}) v_{n'}^mu, then scatter-add
+    const int32_t* dsti = dst_idx + tk.pair_off + tl.col0;
+    cx<R>* dbase = dst + tk.dst_base;
+    for (int e = tid; e < Pout; e += nth) {
         int n1, m1;
         nm_of(e, n1, m1);
         const cx<R>* Dn = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (m1 + n1);
-        const cx<R>* vb = vs + b * Pout + n1 * n1;
-        int w = 2 * n1 + 1;
-        cx<R> acc = mk<R>(0, 0);
-        for (int mu = 0; mu < w; ++mu) cmacc(acc, Dn[(int64_t)mu * w], vb[mu]);
-        int db = dst_idx[tk.pair_off + tl.col0 + b];
-        cx<R>* d = dst + tk.dst_base + (int64_t)db * Pout + e;
-        atomicAdd(&d->re, acc.re);
-        atomicAdd(&d->im, acc.im);
+#define RCR_BACK(W) rcr_back<(W)>(Dn, n1, vs, Pout, b0, e, dsti, dbase)
+        RCR_CHUNKS(RCR_BACK)
+#undef RCR_BACK
     }
+#undef RCR_CHUNKS
 }
 
 template <class R>
@@ -255,17 +325,19 @@ static fb_status run_rcr(const RcrPlan& pl, const cx<R>* rot, const cx<R>* coax,
     return FB_OK;
 }
 
-// Tiles of up to 16 pairs per CTA within a 48 KB shared-memory budget, so
-// that several CTAs share an SM and small levels still spread over many SMs.
+// Tiles of up to 16 pairs per CTA within a shared-memory budget: 96 KB for
+// FP32 (two CTAs per SM; the pairs of a tile reuse each rotation / coaxial
+// entry from registers, so larger tiles raise the arithmetic per load) and
+// 48 KB for FP64 (bound by the FP64 pipe, it wants more resident warps).
 fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize) {
     pl.src_idx = src;
     pl.dst_idx = dst;
     pl.h_tiles.clear();
-    const size_t budget = 48 * 1024;
+    const size_t budget = csize == sizeof(cf) ? 96 * 1024 : 48 * 1024;
     pl.smem = 0;
     for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
         const RcrTask& tk = pl.h_tasks[t];
-        size_t per = (size_t)(2 * tk.p_in * tk.p_in + tk.p_out * tk.p_out) * csize;
+        size_t per = (size_t)(tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out)) * csize;
         int nb = (int)std::max<size_t>(1, std::min<size_t>(16, budget / per));
         for (int c = 0; c < tk.npairs; c += nb) {
             int k = std::min(nb, tk.npairs - c);
