@@ -294,11 +294,13 @@ def run_ours(args):
         barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("bench_timed")     # ncu --nvtx-include bench_timed/
         e0.record(stream)
         for _ in range(args.steps):
             infos.append(solve_mixed(x))
         e1.record(stream)
         barrier()
+        torch.cuda.nvtx.range_pop()
     launches = fb.fb_kernel_launches() - launches0
     ms_total = e0.elapsed_time(e1)
     if dist is not None:

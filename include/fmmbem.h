@@ -249,6 +249,17 @@ FB_API fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y
  * the stream. */
 FB_API fb_status fb_measure_alu_peaks(double* fp32_tflops, double* fp64_tflops, void* stream);
 
+/* Operator applied to nrhs right-hand sides at once (Y = Op X; X, Y:
+ * nrhs x N complex, rhs-major, in memspace, distinct).  The FMM kernels take
+ * every right-hand side in one launch (near-field, P2M/L2P and translation
+ * operators read once per matvec; the stacked translation GEMMs are nrhs
+ * times wider), which is how several source positions of one frequency share
+ * a matvec.  1 <= nrhs <= FB_MAX_RHS.  The operator's expansion buffers grow
+ * to nrhs sets on first use.  Errors: FB_ERR_ARG. */
+#define FB_MAX_RHS 64
+FB_API fb_status fb_operator_apply_multi(fb_op* op, const double* x, double* y, int nrhs, int memspace,
+                                         void* stream);
+
 /* Tracing: running total of kernel launches issued by the library in this
  * process (setup and apply); differences bracket a region of interest. */
 FB_API long long fb_kernel_launches(void);
@@ -357,6 +368,19 @@ typedef struct {
 FB_API fb_status fb_fgmres_solve(fb_op* A, fb_precond* pc, const double* b, double* x,
                           const fb_solver_opts* opts, fb_solve_info* info, int memspace,
                           void* stream);
+
+/* nrhs systems A x_r = b_r with one operator (several source positions of
+ * one frequency) solved by flexible GMRES in lockstep: each Arnoldi step
+ * applies the preconditioner and the operator to the nrhs basis vectors in
+ * one batched call (see fb_operator_apply_multi); every system keeps its own
+ * Hessenberg matrix, restart cycles, convergence test and true-residual
+ * refinement as in fb_fgmres_solve (no learned-to-block-Jacobi fallback
+ * here).  b, x: nrhs x N complex, rhs-major, in memspace; info: nrhs entries
+ * (may be NULL).  Returns FB_OK when every system converged, otherwise the
+ * first failing system's status. */
+FB_API fb_status fb_fgmres_solve_multi(fb_op* A, fb_precond* pc, const double* b, double* x, int nrhs,
+                                       const fb_solver_opts* opts, fb_solve_info* info, int memspace,
+                                       void* stream);
 
 /* ------------------------------------------------------------ receivers -- */
 

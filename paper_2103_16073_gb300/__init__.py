@@ -31,6 +31,7 @@ __all__ = [
     "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
     "fb_precond_create_learned", "fb_learned_params", "fb_learned_set_objective",
     "FB_LOSS_ERROR", "FB_LOSS_RESIDUAL", "fb_learned_loss_and_grad", "fb_learned_train_step",
+    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -346,6 +347,48 @@ def fb_operator_apply_noalloc(op, x, y, stream=None):
     _check(lib.fb_operator_apply_noalloc(op, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                          _stream(stream)))
     return y
+
+
+FB_MAX_RHS = 64
+lib.fb_operator_apply_multi.restype = C.c_int
+lib.fb_operator_apply_multi.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+lib.fb_fgmres_solve_multi.restype = C.c_int
+lib.fb_fgmres_solve_multi.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                      C.POINTER(SolverOpts), C.POINTER(SolveInfo), C.c_int, C.c_void_p]
+
+
+def _nrhs(a):
+    if a.ndim != 2:
+        raise ValueError("multi-RHS arrays are [nrhs, N]")
+    return int(a.shape[0])
+
+
+def fb_operator_apply_multi(op, X, Y, stream=None):
+    """Y[r] = Op X[r] for every row r of the [nrhs, N] complex arrays."""
+    R = _nrhs(X)
+    px, mx, kx = _ptr(X, np.complex128)
+    py, my, ky = _ptr(Y, np.complex128)
+    _check(lib.fb_operator_apply_multi(op, px, py, R, _same_space(mx, my), _stream(stream)))
+    if my == FB_MEM_HOST and ky is not Y:
+        Y[...] = ky
+    return Y
+
+
+def fb_fgmres_solve_multi(A, B, X, pc=None, tol=1e-8, restart=40, maxit=2000, max_refine=3, inner_tol=0.0,
+                          true_op=None, stream=None):
+    """Lockstep FGMRES for the rows of B ([nrhs, N]); returns one info dict per row."""
+    R = _nrhs(B)
+    pb, mb, kb = _ptr(B, np.complex128)
+    px, mx, kx = _ptr(X, np.complex128)
+    opts = SolverOpts(float(tol), int(restart), int(maxit), int(max_refine), float(inner_tol),
+                      true_op.value if true_op is not None else None)
+    infos = (SolveInfo * R)()
+    st = lib.fb_fgmres_solve_multi(A, pc, pb, px, R, C.byref(opts), infos, _same_space(mb, mx), _stream(stream))
+    if st not in (FB_OK, 3, 5):
+        _check(st)
+    if mx == FB_MEM_HOST and kx is not X:
+        X[...] = kx
+    return [i.as_dict() for i in infos]
 
 
 FB_TRANS_AUTO, FB_TRANS_COMPOSED, FB_TRANS_RCR, FB_TRANS_TENSOR = 0, 1, 2, 3

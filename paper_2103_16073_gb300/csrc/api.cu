@@ -17,6 +17,8 @@ fb_status fb_tree_build_impl(const fb_mesh*, int, cudaStream_t, fb_tree**);
 void fb_tree_free(fb_tree*);
 fb_status fb_tree_export_impl(const fb_tree*, int, int, int64_t*, int64_t*);
 fb_status fb_fgmres_impl(fb_op*, fb_precond*, const cd*, cd*, const fb_solver_opts*, fb_solve_info*, cudaStream_t);
+fb_status fb_fgmres_multi_impl(fb_op*, fb_precond*, const cd*, cd*, int, const fb_solver_opts*, fb_solve_info*,
+                               cudaStream_t);
 fb_status fb_precond_create_impl(fb_op*, int, cudaStream_t, fb_precond**);
 void fb_precond_free(fb_precond*);
 fb_status fb_alu_peaks_impl(double*, double*, cudaStream_t);
@@ -73,9 +75,12 @@ static fb_status stage_out_finish(size_t bytes, int memspace, void* user, const 
     return FB_OK;
 }
 
-fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s) {
-    if (op->prec == FB_PREC_FP64_DENSE) return fb_dense_apply(op, x, y, s);
-    return fb_fmm_apply(op, x, y, s);
+fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs) {
+    if (op->prec == FB_PREC_FP64_DENSE) {
+        for (int r = 0; r < nrhs; ++r) FB_CHECK(fb_dense_apply(op, x + r * op->n, y + r * op->n, s));
+        return FB_OK;
+    }
+    return fb_fmm_apply(op, x, y, s, nullptr, nrhs);
 }
 
 extern "C" {
@@ -204,6 +209,21 @@ fb_status fb_operator_apply(fb_op* op, const double* x, double* y, int memspace,
 }
 
 long long fb_kernel_launches(void) { return g_launches.load(); }
+
+fb_status fb_operator_apply_multi(fb_op* op, const double* x, double* y, int nrhs, int memspace, void* stream) {
+    if (!op || !x || !y) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (nrhs < 1 || nrhs > FB_MAX_RHS) return fb_fail(FB_ERR_ARG, "nrhs must be in [1, FB_MAX_RHS]");
+    if (x == y) return fb_fail(FB_ERR_ARG, "x and y must not overlap");
+    cudaStream_t s = as_stream(stream);
+    size_t bytes = sizeof(cd) * op->n * nrhs;
+    Staged sx, sy;
+    const void* dx = nullptr;
+    void* dy = nullptr;
+    FB_CHECK(stage_in(x, bytes, memspace, sx, &dx, s));
+    FB_CHECK(stage_out_alloc(bytes, memspace, y, sy, &dy));
+    FB_CHECK(fb_apply_any(op, (const cd*)dx, (cd*)dy, s, nrhs));
+    return stage_out_finish(bytes, memspace, y, sy, s);
+}
 
 fb_status fb_precond_apply(const fb_precond* pc, const double* x, double* y, int memspace, void* stream) {
     if (!pc || !x || !y) return fb_fail(FB_ERR_ARG, "NULL argument");
@@ -467,6 +487,24 @@ fb_status fb_fgmres_solve(fb_op* A, fb_precond* pc, const double* b, double* x, 
     FB_CHECK(stage_in(b, bytes, memspace, sb, &db, s));
     FB_CHECK(stage_out_alloc(bytes, memspace, x, sx, &dx));
     fb_status st = fb_fgmres_impl(A, pc, (const cd*)db, (cd*)dx, opts, info, s);
+    if (st != FB_OK && st != FB_ERR_NOCONV && st != FB_ERR_NAN) return st;
+    fb_status st2 = stage_out_finish(bytes, memspace, x, sx, s);
+    return st != FB_OK ? st : st2;
+}
+
+fb_status fb_fgmres_solve_multi(fb_op* A, fb_precond* pc, const double* b, double* x, int nrhs,
+                                const fb_solver_opts* opts, fb_solve_info* info, int memspace, void* stream) {
+    if (!A || !b || !x || !opts) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (nrhs < 1 || nrhs > FB_MAX_RHS) return fb_fail(FB_ERR_ARG, "nrhs must be in [1, FB_MAX_RHS]");
+    if (pc && pc->op != A) return fb_fail(FB_ERR_ARG, "preconditioner built for another operator");
+    cudaStream_t s = as_stream(stream);
+    size_t bytes = sizeof(cd) * A->n * nrhs;
+    Staged sb, sx;
+    const void* db = nullptr;
+    void* dx = nullptr;
+    FB_CHECK(stage_in(b, bytes, memspace, sb, &db, s));
+    FB_CHECK(stage_out_alloc(bytes, memspace, x, sx, &dx));
+    fb_status st = fb_fgmres_multi_impl(A, pc, (const cd*)db, (cd*)dx, nrhs, opts, info, s);
     if (st != FB_OK && st != FB_ERR_NOCONV && st != FB_ERR_NAN) return st;
     fb_status st2 = stage_out_finish(bytes, memspace, x, sx, s);
     return st != FB_OK ? st : st2;

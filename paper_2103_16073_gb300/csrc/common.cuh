@@ -8,6 +8,7 @@
 
 #include <deque>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "../../include/fmmbem.h"
@@ -154,9 +155,17 @@ struct fb_tree {
     int64_t nlist_u = 0;
     // rotation blocks of the translation directions, one set per degree
     // bound P, shared by every operator built on this tree
+    // Rotation blocks D^n of a set of directions.  D^n_{mu,m} = d^n_{mu,m}
+    // e^{i m phi} with d real (Q = R_y(-theta) R_z(-phi)): d and the phase
+    // table e^{i m phi} (m = -(P-1)..P-1) are kept too, so the RCR kernels
+    // rotate with real multipliers after one phase per coefficient.
     struct RotSet {
         cd* r64 = nullptr;
         cf* r32 = nullptr;
+        double* d64 = nullptr;
+        float* d32 = nullptr;
+        cd* ph64 = nullptr;
+        cf* ph32 = nullptr;
         int P = 0, ndir = 0;
         int64_t per_dir = 0;
     };
@@ -199,6 +208,13 @@ struct RcrTask {
 struct RcrTile {
     int32_t task, col0, nb, pad;
 };
+// Tiles of an RCR plan for a number of right-hand sides: the columns of a
+// task are its (pair, rhs) combinations, pair-major.
+struct RcrTileSet {
+    RcrTile* tiles = nullptr;
+    int ntiles = 0;
+    size_t smem = 0;
+};
 struct RcrPlan {
     std::vector<RcrTask> h_tasks;
     std::vector<RcrTile> h_tiles;
@@ -209,6 +225,8 @@ struct RcrPlan {
     int ntiles = 0;
     int nb = 1;          // box pairs per CTA
     size_t smem = 0;     // dynamic shared memory per CTA (bytes)
+    size_t csize = 0;    // bytes per complex coefficient
+    std::map<int, RcrTileSet> multi;   // tiles for nrhs > 1 (built on first use)
 };
 
 // A group of box pairs sharing one composed translation matrix (job) on the
@@ -252,8 +270,9 @@ struct fb_op {
     cf* nf32 = nullptr;
     cd* w64 = nullptr; cf* w32 = nullptr;    // P2M, [N sorted][P_L]
     cd* v64 = nullptr; cf* v32 = nullptr;    // L2P, [N sorted][P_L]
-    void* mp = nullptr;                      // multipoles (all levels)
-    void* loc = nullptr;                     // locals (all levels)
+    void* mp = nullptr;                      // multipoles (all levels; exp_nrhs sets)
+    void* loc = nullptr;                     // locals (all levels; exp_nrhs sets)
+    int exp_nrhs = 1;                        // right-hand sides the expansion buffers hold
     cd* T64 = nullptr; cf* T32 = nullptr;    // translation matrices
     int64_t T_count = 0;
     std::vector<int64_t> m2l_toff;           // (L+1)*343: offset of T or -1
@@ -264,6 +283,8 @@ struct fb_op {
     int Prot = 0;
     int64_t per_dir = 0;
     cd* rot64 = nullptr; cf* rot32 = nullptr;
+    double* rotd64 = nullptr; float* rotd32 = nullptr;   // real parts d (owned by the tree)
+    cd* rph64 = nullptr; cf* rph32 = nullptr;            // phase tables (owned by the tree)
     cd* coax64 = nullptr; cf* coax32 = nullptr;
     int64_t coax_count = 0, rot_count = 0;
     RcrPlan m2l_rcr, m2m_rcr[FB_MAXLEV + 1], l2l_rcr[FB_MAXLEV + 1];
@@ -317,7 +338,8 @@ struct PhaseTimer {
 fb_status fb_dense_create(fb_op* op, cudaStream_t s);
 fb_status fb_dense_apply(const fb_op* op, const cd* x, cd* y, cudaStream_t s);
 fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s);
-fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt = nullptr);
+fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt = nullptr,
+                       int nrhs = 1);
 fb_status fb_fmm_apply_noalloc(fb_op* op, const cd* x, cd* y, cudaStream_t s);
 fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize);
 fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, cudaStream_t s,
@@ -338,10 +360,11 @@ float* fb_learned_grads(LearnedNet* net);
 fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cudaStream_t s);
 fb_status fb_tc_build_groups(fb_op* op, const std::vector<TcGroup>& groups, const int32_t* src_idx,
                              const int32_t* dst_idx, void** slot, cudaStream_t s);
-fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s);
+fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s, int nrhs = 1,
+                    int64_t rstride = 0);
 fb_status fb_tc_check(const fb_op* op);
 void fb_tc_free(void*& plan);
 void fb_fmm_destroy(fb_op* op);
-fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s);
-fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s);
+fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs = 1);
+fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, int nrhs = 1);
 int fb_order_rule(double k, double delta, double d0, int pmin);

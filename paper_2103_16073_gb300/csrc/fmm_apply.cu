@@ -94,9 +94,13 @@ __global__ void __launch_bounds__(256) k_trans(const TransTask* __restrict__ tas
 
 // ----------------------------------------------------------------- P2M ----
 // mp[leaf][r] = sum_{pos in leaf} W[pos][r] x[perm[pos]]
+// (blockIdx.y = right-hand side: x and mp advance by xstride / mstride)
 template <class R>
 __global__ void k_p2m(int P, const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ perm,
-                      const cx<R>* __restrict__ W, const cd* __restrict__ x, cx<R>* __restrict__ mp) {
+                      const cx<R>* __restrict__ W, const cd* __restrict__ x, cx<R>* __restrict__ mp,
+                      int64_t xstride, int64_t mstride) {
+    x += blockIdx.y * xstride;
+    mp += blockIdx.y * mstride;
     int b = blockIdx.x;
     int s0 = leaf_start[b], s1 = leaf_start[b + 1];
     __shared__ cx<R> xs[256];
@@ -117,46 +121,77 @@ __global__ void k_p2m(int P, const int32_t* __restrict__ leaf_start, const int32
 
 // ----------------------------------------------------- near field + L2P ----
 // y[perm[pos]] = sum_c A_t[row][c] x[col c] + sum_r V[pos][r] loc[leaf][r]
-template <class R>
+// for up to NB right-hand sides per CTA (blockIdx.y selects the chunk): each
+// near-field and L2P entry is read once and applied to every right-hand side
+// of the chunk.  x, y advance by xstride per rhs, loc by lstride.
+template <class R, int NB>
 __global__ void k_near_l2p(int P, const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ ucnt, const int32_t* __restrict__ ulist,
                            const int64_t* __restrict__ nf_off, const int32_t* __restrict__ nf_ncol,
                            const cx<R>* __restrict__ A, const cx<R>* __restrict__ V,
-                           const cx<R>* __restrict__ loc, const cd* __restrict__ x, cd* __restrict__ y) {
+                           const cx<R>* __restrict__ loc, const cd* __restrict__ x, cd* __restrict__ y,
+                           int nrhs, int64_t xstride, int64_t lstride) {
     extern __shared__ unsigned char smem_raw[];
-    cx<R>* xs = (cx<R>*)smem_raw;
+    const int r0 = blockIdx.y * NB;
+    const int nr = min(NB, nrhs - r0);
+    cx<R>* xs = (cx<R>*)smem_raw;       // [nr][K]
     int t = blockIdx.x;
     int K = nf_ncol[t];
-    cx<R>* ls = xs + K;
+    cx<R>* ls = xs + nr * K;            // [nr][P]
     // gather the x values of the U-list leaves in column order
     int nu = ucnt[t];
     int c = 0;
     for (int i = 0; i < nu; ++i) {
         int s = ulist[(int64_t)t * FB_ULIST + i];
         int a0 = leaf_start[s], a1 = leaf_start[s + 1];
-        for (int q = threadIdx.x; q < a1 - a0; q += blockDim.x) xs[c + q] = from_d<R>(x[perm[a0 + q]]);
+        for (int q = threadIdx.x; q < a1 - a0; q += blockDim.x) {
+            int e = perm[a0 + q];
+            for (int j = 0; j < nr; ++j) xs[j * K + c + q] = from_d<R>(x[(r0 + j) * xstride + e]);
+        }
         c += a1 - a0;
     }
     if (loc)
-        for (int q = threadIdx.x; q < P; q += blockDim.x) ls[q] = loc[(int64_t)t * P + q];
+        for (int j = 0; j < nr; ++j)
+            for (int q = threadIdx.x; q < P; q += blockDim.x)
+                ls[j * P + q] = loc[(r0 + j) * lstride + (int64_t)t * P + q];
     __syncthreads();
-    int r0 = leaf_start[t], nr = leaf_start[t + 1] - r0;
+    int rb = leaf_start[t], nrow = leaf_start[t + 1] - rb;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const cx<R>* At = A + nf_off[t];
-    for (int r = warp; r < nr; r += nw) {
-        cx<R> acc = mk<R>(0, 0);
+    for (int r = warp; r < nrow; r += nw) {
+        cx<R> acc[NB];
+#pragma unroll
+        for (int j = 0; j < NB; ++j) acc[j] = mk<R>(0, 0);
         const cx<R>* row = At + (int64_t)r * K;
-        for (int q = lane; q < K; q += 32) cmac(acc, row[q], xs[q]);
+        for (int q = lane; q < K; q += 32) {
+            cx<R> a = row[q];
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+                if (j < nr) cmac(acc[j], a, xs[j * K + q]);
+        }
         if (loc) {
-            const cx<R>* vr = V + (int64_t)(r0 + r) * P;
-            for (int q = lane; q < P; q += 32) cmac(acc, vr[q], ls[q]);
+            const cx<R>* vr = V + (int64_t)(rb + r) * P;
+            for (int q = lane; q < P; q += 32) {
+                cx<R> v = vr[q];
+#pragma unroll
+                for (int j = 0; j < NB; ++j)
+                    if (j < nr) cmac(acc[j], v, ls[j * P + q]);
+            }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            acc.re += __shfl_xor_sync(0xffffffffu, acc.re, o);
-            acc.im += __shfl_xor_sync(0xffffffffu, acc.im, o);
+        for (int j = 0; j < NB; ++j) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                acc[j].re += __shfl_xor_sync(0xffffffffu, acc[j].re, o);
+                acc[j].im += __shfl_xor_sync(0xffffffffu, acc[j].im, o);
+            }
         }
-        if (lane == 0) y[perm[r0 + r]] = mk<double>((double)acc.re, (double)acc.im);
+        if (lane == 0) {
+            int e = perm[rb + r];
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+                if (j < nr) y[(r0 + j) * xstride + e] = mk<double>((double)acc[j].re, (double)acc[j].im);
+        }
     }
 }
 
@@ -184,8 +219,17 @@ __device__ __forceinline__ void nm_of(int e, int& n, int& m) {
 template <class R> struct RcrChunk { static constexpr int value = 8; };
 template <> struct RcrChunk<double> { static constexpr int value = 4; };
 
+// acc += d x for real d
+template <class R>
+__device__ __forceinline__ void rmac(cx<R>& acc, R d, const cx<R>& x) {
+    acc.re = fma(d, x.re, acc.re);
+    acc.im = fma(d, x.im, acc.im);
+}
+
+// rotation with the real factor d of the block (the phase e^{i m phi} has
+// been applied to the input while staging it)
 template <int W, class R>
-__device__ __forceinline__ void rcr_rotate(const cx<R>* Dn, int n, const cx<R>* xs, int Pin, int b0, int e,
+__device__ __forceinline__ void rcr_rotate(const R* dn, int n, const cx<R>* xs, int Pin, int b0, int e,
                                            cx<R>* us) {
     cx<R> acc[W];
 #pragma unroll
@@ -193,9 +237,9 @@ __device__ __forceinline__ void rcr_rotate(const cx<R>* Dn, int n, const cx<R>* 
     const cx<R>* xb = xs + b0 * Pin + n * n;
 #pragma unroll 4
     for (int m = 0; m <= 2 * n; ++m) {
-        cx<R> d = Dn[m];
+        R d = dn[m];
 #pragma unroll
-        for (int j = 0; j < W; ++j) cmac(acc[j], d, xb[j * Pin + m]);
+        for (int j = 0; j < W; ++j) rmac(acc[j], d, xb[j * Pin + m]);
     }
 #pragma unroll
     for (int j = 0; j < W; ++j) us[(b0 + j) * Pin + e] = acc[j];
@@ -219,9 +263,10 @@ __device__ __forceinline__ void rcr_coax(const cx<R>* Cr, int am, int mu, int pm
     for (int j = 0; j < W; ++j) vs[(b0 + j) * Pout + e] = acc[j];
 }
 
+// back-rotation: y^{m'} = e^{-i m' phi} sum_mu d_{mu,m'} v^mu  (phc = e^{-i m' phi})
 template <int W, class R>
-__device__ __forceinline__ void rcr_back(const cx<R>* Dn, int n1, const cx<R>* vs, int Pout, int b0, int e,
-                                         const int32_t* dsti, cx<R>* dst) {
+__device__ __forceinline__ void rcr_back(const R* dn, int n1, cx<R> phc, const cx<R>* vs, int Pout, int b0, int e,
+                                         const int64_t* dsto, cx<R>* dst) {
     cx<R> acc[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) acc[j] = mk<R>(0, 0);
@@ -229,24 +274,27 @@ __device__ __forceinline__ void rcr_back(const cx<R>* Dn, int n1, const cx<R>* v
     const cx<R>* vb = vs + b0 * Pout + n1 * n1;
 #pragma unroll 4
     for (int mu = 0; mu < w; ++mu) {
-        cx<R> d = Dn[(int64_t)mu * w];
+        R d = dn[(int64_t)mu * w];
 #pragma unroll
-        for (int j = 0; j < W; ++j) cmacc(acc[j], d, vb[j * Pout + mu]);
+        for (int j = 0; j < W; ++j) rmac(acc[j], d, vb[j * Pout + mu]);
     }
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-        cx<R>* d = dst + (int64_t)dsti[b0 + j] * Pout + e;
-        atomicAdd(&d->re, acc[j].re);
-        atomicAdd(&d->im, acc[j].im);
+        cx<R> y = acc[j] * phc;
+        cx<R>* d = dst + dsto[b0 + j] + e;
+        atomicAdd(&d->re, y.re);
+        atomicAdd(&d->im, y.im);
     }
 }
 
 template <class R>
 __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, const RcrTile* __restrict__ tiles,
-                                             const cx<R>* __restrict__ rot, const cx<R>* __restrict__ coax,
+                                             const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
+                                             int64_t per_dir, int prot, const cx<R>* __restrict__ coax,
                                              const int32_t* __restrict__ src_idx,
                                              const int32_t* __restrict__ dst_idx,
-                                             const cx<R>* __restrict__ src, cx<R>* __restrict__ dst) {
+                                             const cx<R>* __restrict__ src, cx<R>* __restrict__ dst,
+                                             int nrhs, int64_t rstride) {
     constexpr int BCH = RcrChunk<R>::value;
     extern __shared__ unsigned char smem_raw[];
     RcrTile tl = tiles[blockIdx.x];
@@ -259,13 +307,26 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
     cx<R>* us = buf + nb * max(Pin, Pout);   // [nb][Pin]
     cx<R>* vs = buf;                    // [nb][Pout] (xs is dead after the rotation)
     int tid = threadIdx.x, nth = blockDim.x;
+    // column b of the tile: pair (col0 + b) / nrhs, right-hand side (col0 + b) % nrhs
+    __shared__ int64_t s_dst_off[16];
+    for (int b = tid; b < nb; b += nth) {
+        int col = tl.col0 + b;
+        int pr = col / nrhs, rh = col - pr * nrhs;
+        s_dst_off[b] = rh * rstride + tk.dst_base + (int64_t)dst_idx[tk.pair_off + pr] * Pout;
+    }
+    const int64_t dir = tk.rot_off / per_dir;
+    const cx<R>* ph = rph + dir * (2 * prot - 1) + (prot - 1);   // ph[m] = e^{i m phi}
     for (int q = tid; q < nb * Pin; q += nth) {
         int b = q / Pin, e = q % Pin;
-        int sb = src_idx[tk.pair_off + tl.col0 + b];
-        xs[q] = src[tk.src_base + (int64_t)sb * Pin + e];
+        int col = tl.col0 + b;
+        int pr = col / nrhs, rh = col - pr * nrhs;
+        int sb = src_idx[tk.pair_off + pr];
+        int n, m;
+        nm_of(e, n, m);
+        xs[q] = src[rh * rstride + tk.src_base + (int64_t)sb * Pin + e] * ph[m];
     }
     __syncthreads();
-    const cx<R>* D = rot + tk.rot_off;
+    const R* D = rotd + tk.rot_off;
     // chunk widths BCH, then 4, 2, 1 for the rest of the tile
 #define RCR_CHUNKS(CALL)                                              \
     {                                                                 \
@@ -279,7 +340,7 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
     for (int e = tid; e < Pin; e += nth) {
         int n, mu;
         nm_of(e, n, mu);
-        const cx<R>* Dn = D + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3 + (int64_t)(mu + n) * (2 * n + 1);
+        const R* Dn = D + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3 + (int64_t)(mu + n) * (2 * n + 1);
 #define RCR_ROT(W) rcr_rotate<(W)>(Dn, n, xs, Pin, b0, e, us)
         RCR_CHUNKS(RCR_ROT)
 #undef RCR_ROT
@@ -300,51 +361,96 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
     }
     __syncthreads();
     // back-rotate: y_{n'}^{m'} = sum_mu conj(D^{n'}_{mu,m'}) v_{n'}^mu, then scatter-add
-    const int32_t* dsti = dst_idx + tk.pair_off + tl.col0;
-    cx<R>* dbase = dst + tk.dst_base;
     for (int e = tid; e < Pout; e += nth) {
         int n1, m1;
         nm_of(e, n1, m1);
-        const cx<R>* Dn = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (m1 + n1);
-#define RCR_BACK(W) rcr_back<(W)>(Dn, n1, vs, Pout, b0, e, dsti, dbase)
+        const R* Dn = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (m1 + n1);
+        const cx<R> phc = conjg(ph[m1]);
+#define RCR_BACK(W) rcr_back<(W)>(Dn, n1, phc, vs, Pout, b0, e, s_dst_off, dst)
         RCR_CHUNKS(RCR_BACK)
 #undef RCR_BACK
     }
 #undef RCR_CHUNKS
 }
 
+// Tiles of up to 16 columns per CTA within a shared-memory budget: 96 KB for
+// FP32 (two CTAs per SM; the columns of a tile reuse each rotation / coaxial
+// entry from registers, so larger tiles raise the arithmetic per load) and
+// 48 KB for FP64 (bound by the FP64 pipe, it wants more resident warps).
+static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& tiles, size_t& smem) {
+    const size_t budget = pl.csize == sizeof(cf) ? 96 * 1024 : 48 * 1024;
+    tiles.clear();
+    smem = 0;
+    for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
+        const RcrTask& tk = pl.h_tasks[t];
+        size_t per = (size_t)(tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out)) * pl.csize;
+        int nb = (int)std::max<size_t>(1, std::min<size_t>(16, budget / per));
+        int ncol = tk.npairs * nrhs;
+        for (int c = 0; c < ncol; c += nb) {
+            int k = std::min(nb, ncol - c);
+            tiles.push_back(RcrTile{t, c, k, 0});
+            smem = std::max(smem, per * k);
+        }
+    }
+}
+
+static fb_status rcr_tiles_for(RcrPlan& pl, int nrhs, const RcrTile** tiles, int* ntiles, size_t* smem) {
+    if (nrhs == 1) {
+        *tiles = pl.tiles;
+        *ntiles = pl.ntiles;
+        *smem = pl.smem;
+        return FB_OK;
+    }
+    auto it = pl.multi.find(nrhs);
+    if (it == pl.multi.end()) {
+        std::vector<RcrTile> h;
+        RcrTileSet ts;
+        rcr_make_tiles(pl, nrhs, h, ts.smem);
+        ts.ntiles = (int)h.size();
+        if (!h.empty()) {
+            FB_CHECK(dalloc(&ts.tiles, h.size()));
+            FB_CUDA(cudaMemcpy(ts.tiles, h.data(), sizeof(RcrTile) * h.size(), cudaMemcpyHostToDevice));
+        }
+        it = pl.multi.emplace(nrhs, ts).first;
+    }
+    *tiles = it->second.tiles;
+    *ntiles = it->second.ntiles;
+    *smem = it->second.smem;
+    return FB_OK;
+}
+
+// Rotation data of an operator for the RCR kernels: real factors, phase
+// tables and their strides.
 template <class R>
-static fb_status run_rcr(const RcrPlan& pl, const cx<R>* rot, const cx<R>* coax, const cx<R>* src, cx<R>* dst,
-                         cudaStream_t s) {
-    if (pl.ntiles == 0) return FB_OK;
-    if (pl.smem > 48 * 1024)
-        FB_CUDA(cudaFuncSetAttribute(k_rcr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
-    k_rcr<R><<<pl.ntiles, 256, pl.smem, s>>>(pl.tasks, pl.tiles, rot, coax, pl.src_idx, pl.dst_idx, src, dst);
+struct RotArgs {
+    const R* d;
+    const cx<R>* ph;
+    int64_t per_dir;
+    int prot;
+};
+
+template <class R>
+static fb_status run_rcr(RcrPlan& pl, const RotArgs<R>& rot, const cx<R>* coax, const cx<R>* src, cx<R>* dst,
+                         cudaStream_t s, int nrhs = 1, int64_t rstride = 0) {
+    const RcrTile* tiles = nullptr;
+    int ntiles = 0;
+    size_t smem = 0;
+    FB_CHECK(rcr_tiles_for(pl, nrhs, &tiles, &ntiles, &smem));
+    if (ntiles == 0) return FB_OK;
+    if (smem > 48 * 1024)
+        FB_CUDA(cudaFuncSetAttribute(k_rcr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_rcr<R><<<ntiles, 256, smem, s>>>(pl.tasks, tiles, rot.d, rot.ph, rot.per_dir, rot.prot, coax, pl.src_idx,
+                                       pl.dst_idx, src, dst, nrhs, rstride);
     FB_LAUNCH_CHECK();
     fb_count_launch();
     return FB_OK;
 }
 
-// Tiles of up to 16 pairs per CTA within a shared-memory budget: 96 KB for
-// FP32 (two CTAs per SM; the pairs of a tile reuse each rotation / coaxial
-// entry from registers, so larger tiles raise the arithmetic per load) and
-// 48 KB for FP64 (bound by the FP64 pipe, it wants more resident warps).
 fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize) {
     pl.src_idx = src;
     pl.dst_idx = dst;
-    pl.h_tiles.clear();
-    const size_t budget = csize == sizeof(cf) ? 96 * 1024 : 48 * 1024;
-    pl.smem = 0;
-    for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
-        const RcrTask& tk = pl.h_tasks[t];
-        size_t per = (size_t)(tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out)) * csize;
-        int nb = (int)std::max<size_t>(1, std::min<size_t>(16, budget / per));
-        for (int c = 0; c < tk.npairs; c += nb) {
-            int k = std::min(nb, tk.npairs - c);
-            pl.h_tiles.push_back(RcrTile{t, c, k, 0});
-            pl.smem = std::max(pl.smem, per * k);
-        }
-    }
+    pl.csize = csize;
+    rcr_make_tiles(pl, 1, pl.h_tiles, pl.smem);
     pl.ntiles = (int)pl.h_tiles.size();
     if (pl.h_tasks.empty()) return FB_OK;
     if (pl.smem > 200 * 1024) return fb_fail(FB_ERR_ARG, "RCR tile exceeds shared memory (p too large)");
@@ -364,35 +470,60 @@ static fb_status run_plan(const TransPlan& pl, const cx<R>* T, const cx<R>* src,
     return FB_OK;
 }
 
+// One FMM matvec for nrhs right-hand sides (x, y: nrhs x N, rhs-major).  The
+// expansions of rhs r sit at mp / loc + r * cnt; every kernel handles all
+// right-hand sides in one launch, so the near-field entries, the P2M / L2P
+// operators and every translation operator are read once per matvec.
 template <class R>
 static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, const cx<R>* A,
                              const cx<R>* W, const cx<R>* V, const cx<R>* T, PhaseTimer* pt,
-                             void* scratch = nullptr) {
+                             void* scratch = nullptr, int nrhs = 1) {
     auto mark = [&](int i) { if (pt) cudaEventRecord(pt->ev[i], s); };
     const fb_tree* t = op->tree;
     int L = op->L;
     int pL = op->p[L], PL = pL * pL;
     int64_t cnt = op->lev_off[L + 1];
-    // expansions: the operator's own buffers, or a caller-provided region
-    // holding the multipoles followed by the locals
+    const int64_t n = op->n;
+    const bool composed = op->method == FB_TRANS_COMPOSED;
+    if (composed && nrhs > 1) {   // the composed SIMT path takes one right-hand side at a time
+        for (int r = 0; r < nrhs; ++r)
+            FB_CHECK(fmm_apply_t<R>(op, x + r * n, y + r * n, s, A, W, V, T, r == 0 ? pt : nullptr, scratch, 1));
+        return FB_OK;
+    }
+    // expansions: the operator's own buffers (grown to nrhs sets), or a
+    // caller-provided region holding the multipoles followed by the locals
+    if (!scratch && nrhs > op->exp_nrhs) {
+        cudaStreamSynchronize(s);
+        dfree(op->mp);
+        dfree(op->loc);
+        op->mp = nullptr;
+        op->loc = nullptr;
+        FB_CHECK(dalloc((cx<R>**)&op->mp, cnt * nrhs));
+        FB_CHECK(dalloc((cx<R>**)&op->loc, cnt * nrhs));
+        op->exp_nrhs = nrhs;
+    }
     cx<R>* mp = scratch ? (cx<R>*)scratch : (cx<R>*)op->mp;
-    cx<R>* loc = scratch ? (cx<R>*)scratch + cnt : (cx<R>*)op->loc;
+    cx<R>* loc = scratch ? (cx<R>*)scratch + cnt * nrhs : (cx<R>*)op->loc;
     mark(0);
-    FB_CUDA(cudaMemsetAsync(mp, 0, sizeof(cx<R>) * cnt, s));
-    FB_CUDA(cudaMemsetAsync(loc, 0, sizeof(cx<R>) * cnt, s));
+    FB_CUDA(cudaMemsetAsync(mp, 0, sizeof(cx<R>) * cnt * nrhs, s));
+    FB_CUDA(cudaMemsetAsync(loc, 0, sizeof(cx<R>) * cnt * nrhs, s));
     int nleaf = t->nbox[L];
-    k_p2m<R><<<nleaf, 128, 0, s>>>(PL, t->leaf_start, t->perm, W, x, mp + op->lev_off[L]);
+    k_p2m<R><<<dim3(nleaf, nrhs), 128, 0, s>>>(PL, t->leaf_start, t->perm, W, x, mp + op->lev_off[L], n, cnt);
     FB_LAUNCH_CHECK();
     fb_count_launch();
     mark(1);
-    const cx<R>* rot = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->rot64 : (const void*)op->rot32);
+    RotArgs<R> rot;
+    rot.d = (const R*)(sizeof(R) == 8 ? (const void*)op->rotd64 : (const void*)op->rotd32);
+    rot.ph = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->rph64 : (const void*)op->rph32);
+    rot.per_dir = op->per_dir;
+    rot.prot = op->Prot;
     const cx<R>* coax = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->coax64 : (const void*)op->coax32);
-    const bool composed = op->method == FB_TRANS_COMPOSED;
     const bool auto_tc = sizeof(R) == 4 && op->method == FB_TRANS_AUTO;
     for (int l = L; l >= 3; --l) {
         if (composed) FB_CHECK(run_plan<R>(op->m2m[l], T, mp, mp, s));
-        else if (auto_tc && op->tc_m2m[l]) FB_CHECK(fb_tc_run(op, op->tc_m2m[l], (const cf*)mp, (cf*)mp, s));
-        else FB_CHECK(run_rcr<R>(op->m2m_rcr[l], rot, coax, mp, mp, s));
+        else if (auto_tc && op->tc_m2m[l])
+            FB_CHECK(fb_tc_run(op, op->tc_m2m[l], (const cf*)mp, (cf*)mp, s, nrhs, cnt));
+        else FB_CHECK(run_rcr<R>(op->m2m_rcr[l], rot, coax, mp, mp, s, nrhs, cnt));
     }
     mark(2);
     // phase [2] is the tensor-core part of M2L: empty unless it runs below
@@ -401,45 +532,59 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
     if (composed) {
         FB_CHECK(run_plan<R>(op->m2l, T, mp, loc, s));
     } else if (op->method == FB_TRANS_RCR) {
-        FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s));
+        FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s, nrhs, cnt));
     } else {
         if constexpr (sizeof(R) == 4) {
             if (op->method == FB_TRANS_TENSOR) {
-                FB_CHECK(fb_tc_run(op, op->tc_plan_all, (const cf*)mp, (cf*)loc, s));
+                FB_CHECK(fb_tc_run(op, op->tc_plan_all, (const cf*)mp, (cf*)loc, s, nrhs, cnt));
             } else if (op->tc_plan) {
-                FB_CHECK(fb_tc_run(op, op->tc_plan, (const cf*)mp, (cf*)loc, s));
+                FB_CHECK(fb_tc_run(op, op->tc_plan, (const cf*)mp, (cf*)loc, s, nrhs, cnt));
                 mark(3);
-                FB_CHECK(run_rcr<R>(op->m2l_rcr_rest, rot, coax, mp, loc, s));
+                FB_CHECK(run_rcr<R>(op->m2l_rcr_rest, rot, coax, mp, loc, s, nrhs, cnt));
             } else {
-                FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s));
+                FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s, nrhs, cnt));
             }
         } else {
-            FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s));
+            FB_CHECK(run_rcr<R>(op->m2l_rcr, rot, coax, mp, loc, s, nrhs, cnt));
         }
     }
     mark(4);
     for (int l = 3; l <= L; ++l) {
         if (composed) FB_CHECK(run_plan<R>(op->l2l[l], T, loc, loc, s));
-        else if (auto_tc && op->tc_l2l[l]) FB_CHECK(fb_tc_run(op, op->tc_l2l[l], (const cf*)loc, (cf*)loc, s));
-        else FB_CHECK(run_rcr<R>(op->l2l_rcr[l], rot, coax, loc, loc, s));
+        else if (auto_tc && op->tc_l2l[l])
+            FB_CHECK(fb_tc_run(op, op->tc_l2l[l], (const cf*)loc, (cf*)loc, s, nrhs, cnt));
+        else FB_CHECK(run_rcr<R>(op->l2l_rcr[l], rot, coax, loc, loc, s, nrhs, cnt));
     }
     mark(5);
     int maxK = 0;
     for (int v : op->h_nf_ncol) maxK = std::max(maxK, v);
-    size_t smem = sizeof(cx<R>) * (maxK + PL);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_near_l2p<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_near_l2p<R><<<nleaf, 256, smem, s>>>(PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off,
-                                           op->nf_ncol, A, V, loc + op->lev_off[L], x, y);
+    const cx<R>* locL = loc + op->lev_off[L];
+    if (nrhs == 1) {
+        size_t smem = sizeof(cx<R>) * (maxK + PL);
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_near_l2p<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_near_l2p<R, 1><<<nleaf, 256, smem, s>>>(PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off,
+                                                  op->nf_ncol, A, V, locL, x, y, 1, n, cnt);
+    } else {
+        constexpr int NB = 4;
+        int nr = std::min(nrhs, NB);
+        size_t smem = sizeof(cx<R>) * (size_t)nr * (maxK + PL);
+        if (smem > 227 * 1024) return fb_fail(FB_ERR_ARG, "near-field tile exceeds shared memory");
+        if (smem > 48 * 1024)
+            cudaFuncSetAttribute(k_near_l2p<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_near_l2p<R, NB><<<dim3(nleaf, div_up(nrhs, NB)), 256, smem, s>>>(
+            PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off, op->nf_ncol, A, V, locL, x, y, nrhs, n, cnt);
+    }
     FB_LAUNCH_CHECK();
     fb_count_launch();
     mark(6);
     return FB_OK;
 }
 
-fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt) {
+fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt, int nrhs) {
     if (op->prec == FB_PREC_MIXED_FMM)
-        return fmm_apply_t<float>(op, x, y, s, op->nf32, op->w32, op->v32, op->T32, pt);
-    return fmm_apply_t<double>(op, x, y, s, op->nf64, op->w64, op->v64, op->T64, pt);
+        return fmm_apply_t<float>(op, x, y, s, op->nf32, op->w32, op->v32, op->T32, pt, nullptr, nrhs);
+    return fmm_apply_t<double>(op, x, y, s, op->nf64, op->w64, op->v64, op->T64, pt, nullptr, nrhs);
 }
 
 static void free_plan(TransPlan& p) {
@@ -449,6 +594,8 @@ static void free_plan(TransPlan& p) {
 static void free_plan(RcrPlan& p) {
     dfree(p.tasks);
     dfree(p.tiles);
+    for (auto& kv : p.multi) dfree(kv.second.tiles);
+    p.multi.clear();
 }
 
 void fb_fmm_destroy(fb_op* op) {
@@ -481,6 +628,10 @@ void fb_fmm_destroy(fb_op* op) {
     }
     op->rot64 = nullptr;   // owned by the tree
     op->rot32 = nullptr;
+    op->rotd64 = nullptr;
+    op->rotd32 = nullptr;
+    op->rph64 = nullptr;
+    op->rph32 = nullptr;
     dfree(op->coax64);
     dfree(op->coax32);
 }

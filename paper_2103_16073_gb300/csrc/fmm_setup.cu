@@ -260,6 +260,33 @@ __global__ void k_rot_grid(const double* dirs, int ndir, int identity, int P, in
     ylm_unit(P, u.x / un, u.y / un, u.z / un, scratch + tid * (int64_t)sstride, out + tid * (int64_t)P * P);
 }
 
+// Real factor and phase table of the rotation blocks: with phi the azimuth
+// of the direction (same formula as rotT), d^n_{mu,m} = Re(D^n_{mu,m}
+// e^{-i m phi}) and ph[m + P - 1] = e^{i m phi}.  grid: (entry chunk, n, dir)
+__global__ void k_rot_factor(const cd* rot, const double* dirs, int ndir, int P, double* d64, float* d32,
+                             cd* ph64, cf* ph32) {
+    int n = blockIdx.y, dd = blockIdx.z;
+    int w = 2 * n + 1;
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double phi = atan2(dirs[3 * dd + 1], dirs[3 * dd]);
+    int64_t per_dir = (int64_t)P * (2 * P - 1) * (2 * P + 1) / 3;
+    if (n == 0 && e < 2 * P - 1) {
+        double sp, cp;
+        sincos((double)(e - (P - 1)) * phi, &sp, &cp);
+        ph64[(int64_t)dd * (2 * P - 1) + e] = mk(cp, sp);
+        ph32[(int64_t)dd * (2 * P - 1) + e] = mk((float)cp, (float)sp);
+    }
+    if (e >= w * w) return;
+    int m = e % w - n;
+    double sp, cp;
+    sincos((double)m * phi, &sp, &cp);
+    int64_t o = (int64_t)dd * per_dir + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3 + e;
+    cd D = rot[o];
+    double v = D.re * cp + D.im * sp;    // Re(D e^{-i m phi})
+    d64[o] = v;
+    d32[o] = (float)v;
+}
+
 // D^n_{mu,m} = sum_q W_q conj(Y_n^mu(y_q)) Y_n^m(Q^T y_q) for the batch.
 // grid: (entry chunk, n, dir); out[dir_global][rot_off(n) + (mu+n)(2n+1) + (m+n)]
 __global__ void k_rot_project(const cd* Yg, const cd* Yr, int ndir, int P, int nq, int nphi,
@@ -413,22 +440,29 @@ fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, 
         dim3 grid(div_up((2 * Prot - 1) * (2 * Prot - 1), 128), Prot, nb);
         k_rot_project<<<grid, 128, 0, s>>>(Yg, Yr, nb, Prot, nq, nphi, glw, d0i, rot);
     }
-    FB_LAUNCH_CHECK();
-    cudaError_t e = cudaStreamSynchronize(s);
-    free_tmp();
-    if (e != cudaSuccess) {
-        dfree(rot);
-        return fb_fail(FB_ERR_CUDA, std::string("rotation setup: ") + cudaGetErrorString(e));
-    }
     fb_tree::RotSet rs;
     rs.r64 = rot;
     rs.P = Prot;
     rs.per_dir = per_dir;
     rs.ndir = ndir;
-    fb_status st2 = dalloc(&rs.r32, (size_t)ndir * per_dir);
-    if (st2 != FB_OK) {
-        dfree(rs.r64);
-        return st2;
+    auto free_rs = [&]() { dfree(rs.r64); dfree(rs.r32); dfree(rs.d64); dfree(rs.d32); dfree(rs.ph64); dfree(rs.ph32); };
+    if ((st = dalloc(&rs.r32, (size_t)ndir * per_dir)) || (st = dalloc(&rs.d64, (size_t)ndir * per_dir)) ||
+        (st = dalloc(&rs.d32, (size_t)ndir * per_dir)) || (st = dalloc(&rs.ph64, (size_t)ndir * (2 * Prot - 1))) ||
+        (st = dalloc(&rs.ph32, (size_t)ndir * (2 * Prot - 1)))) {
+        free_tmp();
+        free_rs();
+        return st;
+    }
+    {
+        dim3 grid(div_up(std::max((2 * Prot - 1) * (2 * Prot - 1), 2 * Prot - 1), 128), Prot, ndir);
+        k_rot_factor<<<grid, 128, 0, s>>>(rot, ddirs, ndir, Prot, rs.d64, rs.d32, rs.ph64, rs.ph32);
+    }
+    FB_LAUNCH_CHECK();
+    cudaError_t e = cudaStreamSynchronize(s);
+    free_tmp();
+    if (e != cudaSuccess) {
+        free_rs();
+        return fb_fail(FB_ERR_CUDA, std::string("rotation setup: ") + cudaGetErrorString(e));
     }
     k_d2f<<<div_up((int64_t)ndir * per_dir, 256), 256, 0, s>>>(rs.r64, rs.r32, (int64_t)ndir * per_dir);
     FB_LAUNCH_CHECK();
@@ -674,6 +708,10 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
     coax = nullptr;
     op->rot64 = rot;
     op->rot32 = rset->r32;
+    op->rotd64 = rset->d64;
+    op->rotd32 = rset->d32;
+    op->rph64 = rset->ph64;
+    op->rph32 = rset->ph32;
     op->rot_count = (int64_t)ndir * per_dir;
     op->Prot = Prot;
     op->per_dir = per_dir;

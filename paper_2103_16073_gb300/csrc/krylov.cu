@@ -104,7 +104,7 @@ struct Hess {
 };
 
 // Starts a cycle: g = (beta, 0, ...), inv = 1/beta (beta = sqrt(nrm2)).
-__global__ void k_cycle_start(Hess hs) {
+__device__ void cycle_start(const Hess& hs) {
     double beta = sqrt(*hs.nrm2);
     for (int i = 0; i <= hs.m; ++i) hs.g[i] = mk(0.0, 0.0);
     for (int i = 0; i < (hs.m + 1) * hs.m; ++i) hs.H[i] = mk(0.0, 0.0);
@@ -112,6 +112,7 @@ __global__ void k_cycle_start(Hess hs) {
     *hs.inv = beta > 0.0 ? 1.0 / beta : 0.0;
     *hs.est = beta;
 }
+__global__ void k_cycle_start(Hess hs) { cycle_start(hs); }
 
 // Adds the CGS pass coefficients into column j.
 __global__ void k_accum_h(Hess hs, int j) {
@@ -121,7 +122,7 @@ __global__ void k_accum_h(Hess hs, int j) {
 
 // Completes column j: H[j+1][j] = ||w||, previous rotations, new rotation,
 // residual estimate |g[j+1]|, inv = 1/H[j+1][j].
-__global__ void k_arnoldi_close(Hess hs, int j) {
+__device__ void arnoldi_close(const Hess& hs, int j) {
     int ld = hs.m + 1;
     cd* col = hs.H + j * ld;
     double hn = sqrt(*hs.nrm2);
@@ -152,9 +153,10 @@ __global__ void k_arnoldi_close(Hess hs, int j) {
     hs.g[j] = c * gj;
     *hs.est = sqrt(abs2(hs.g[j + 1]));
 }
+__global__ void k_arnoldi_close(Hess hs, int j) { arnoldi_close(hs, j); }
 
 // Back substitution H y = g for the first j1 columns.
-__global__ void k_backsolve(Hess hs, int j1) {
+__device__ void backsolve(const Hess& hs, int j1) {
     int ld = hs.m + 1;
     for (int i = j1 - 1; i >= 0; --i) {
         cd acc = hs.g[i];
@@ -164,6 +166,7 @@ __global__ void k_backsolve(Hess hs, int j1) {
         hs.y[i] = (1.0 / dd) * (acc * conjg(d));
     }
 }
+__global__ void k_backsolve(Hess hs, int j1) { backsolve(hs, j1); }
 
 static inline void cnt(long long n = 1) { fb_count_launch(n); }
 
@@ -460,7 +463,9 @@ __global__ void k_bj_invert(const int32_t* leaf_start, const int64_t* blk_off, c
 
 template <class R>
 __global__ void k_bj_apply(const int32_t* leaf_start, const int32_t* perm, const int64_t* blk_off,
-                           const cx<R>* blocks, const cd* __restrict__ x, cd* __restrict__ y) {
+                           const cx<R>* blocks, const cd* __restrict__ x, cd* __restrict__ y, int64_t stride) {
+    x += blockIdx.y * stride;   // right-hand side blockIdx.y
+    y += blockIdx.y * stride;
     int t = blockIdx.x;
     int r0 = leaf_start[t], n = leaf_start[t + 1] - r0;
     extern __shared__ unsigned char raw[];
@@ -483,6 +488,368 @@ __global__ void k_bj_apply(const int32_t* leaf_start, const int32_t* perm, const
 __global__ void k_d2f_bj(const cd* a, cf* b, int64_t n) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) b[i] = to_f(a[i]);
+}
+
+// ------------------------------------------------------ batched FGMRES ----
+// nrhs independent systems A x_r = b_r with one operator solved in lockstep:
+// every Arnoldi step applies the preconditioner and the operator to the nrhs
+// current basis vectors in one batched call (fb_pc_apply / fb_apply_any with
+// nrhs), so the operator's data are read once per step for all systems.  Each
+// system keeps its own Hessenberg matrix, Givens rotations, restart cycle,
+// convergence test and true-residual refinement; a system that has converged
+// is masked out of the Krylov updates (its matvec column is still computed
+// until the whole batch finishes).  Layouts: V [(m+1)][R][N], Z [m][R][N],
+// vectors [R][N]; Hessenberg state [R][...].
+namespace {
+
+__global__ void k_bmdot(const cd* __restrict__ V, int64_t n, int R, const cd* __restrict__ w, cd* h, int hstride,
+                        const int* act) {
+    int r = blockIdx.z, i = blockIdx.y;
+    if (!act[r]) return;
+    const cd* v = V + ((int64_t)i * R + r) * n;
+    const cd* wr = w + (int64_t)r * n;
+    cd acc = mk(0.0, 0.0);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        cmacc(acc, v[q], wr[q]);
+    block_reduce_add(acc.re, &h[r * hstride + i].re);
+    block_reduce_add(acc.im, &h[r * hstride + i].im);
+}
+
+__global__ void k_bgs_update(const cd* __restrict__ V, int64_t n, int R, int j1, const cd* __restrict__ h,
+                             int hstride, cd* w, const int* act) {
+    int r = blockIdx.y;
+    if (!act[r]) return;
+    __shared__ cd hs[1024];
+    for (int i = threadIdx.x; i < j1; i += blockDim.x) hs[i] = h[r * hstride + i];
+    __syncthreads();
+    cd* wr = w + (int64_t)r * n;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        cd a = wr[q];
+        for (int i = 0; i < j1; ++i) {
+            cd v = V[((int64_t)i * R + r) * n + q];
+            a.re -= v.re * hs[i].re - v.im * hs[i].im;
+            a.im -= v.re * hs[i].im + v.im * hs[i].re;
+        }
+        wr[q] = a;
+    }
+}
+
+__global__ void k_bnorm2(const cd* __restrict__ w, int64_t n, double* out, int ostride, const int* act) {
+    int r = blockIdx.y;
+    if (act && !act[r]) return;
+    const cd* wr = w + (int64_t)r * n;
+    double acc = 0.0;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        acc += abs2(wr[q]);
+    block_reduce_add(acc, out + r * ostride);
+}
+
+// out_r = f_r in_r with f_r = scal[r * ostride]
+__global__ void k_bscale(cd* __restrict__ out, const cd* __restrict__ in, int64_t n, const double* f, int fstride,
+                         const int* act) {
+    int r = blockIdx.y;
+    if (!act[r]) return;
+    double a = f[r * fstride];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[r * n + q] = a * in[r * n + q];
+}
+
+// out_r = a_r - b_r (masked)
+__global__ void k_bsub(cd* out, const cd* a, const cd* b, int64_t n, const int* act) {
+    int r = blockIdx.y;
+    if (act && !act[r]) return;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[r * n + q] = a[r * n + q] - b[r * n + q];
+}
+__global__ void k_badd(cd* out, const cd* a, int64_t n, const int* act) {
+    int r = blockIdx.y;
+    if (!act[r]) return;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x)
+        out[r * n + q] = out[r * n + q] + a[r * n + q];
+}
+
+// x_r += sum_{i < j1_r} Z_{i,r} y_r[i]
+__global__ void k_bupdate_x(cd* x, const cd* __restrict__ Z, int64_t n, int R, const int* j1, const cd* y,
+                            int ystride) {
+    int r = blockIdx.y;
+    int jr = j1[r];
+    if (jr <= 0) return;
+    __shared__ cd ys[1024];
+    for (int i = threadIdx.x; i < jr; i += blockDim.x) ys[i] = y[r * ystride + i];
+    __syncthreads();
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        cd a = x[r * n + q];
+        for (int i = 0; i < jr; ++i) cmac(a, Z[((int64_t)i * R + r) * n + q], ys[i]);
+        x[r * n + q] = a;
+    }
+}
+
+__global__ void k_bcycle_start(const Hess* hs, const int* act) {
+    int r = blockIdx.x;
+    if (act[r]) cycle_start(hs[r]);
+}
+__global__ void k_baccum_h(const Hess* hs, int j, const int* act) {
+    int r = blockIdx.x, i = threadIdx.x;
+    if (!act[r]) return;
+    const Hess& h = hs[r];
+    if (i <= j) h.H[j * (h.m + 1) + i] = h.H[j * (h.m + 1) + i] + h.h[i];
+}
+__global__ void k_barnoldi_close(const Hess* hs, int j, const int* act) {
+    int r = blockIdx.x;
+    if (act[r]) arnoldi_close(hs[r], j);
+}
+__global__ void k_bbacksolve(const Hess* hs, const int* j1) {
+    int r = blockIdx.x;
+    if (j1[r] > 0) backsolve(hs[r], j1[r]);
+}
+
+}  // namespace
+
+struct BatchWork {
+    int64_t n = 0;
+    int m = 0, R = 0;
+    cd *V = nullptr, *Z = nullptr, *W = nullptr, *Rs = nullptr, *D = nullptr, *T = nullptr;
+    cd* small = nullptr;
+    double* scal = nullptr;     // [R][4]: nrm2, inv, est, spare
+    int* dint = nullptr;        // act [R], j1 [R]
+    Hess* dhs = nullptr;
+    double* host = nullptr;     // pinned [R][4]
+    int* hint = nullptr;        // pinned act [R], j1 [R]
+    ~BatchWork() {
+        dfree(V); dfree(Z); dfree(W); dfree(Rs); dfree(D); dfree(T); dfree(small); dfree(scal); dfree(dint);
+        dfree(dhs);
+        if (host) cudaFreeHost(host);
+        if (hint) cudaFreeHost(hint);
+    }
+};
+
+static fb_status upload_ints(BatchWork& B, cudaStream_t s) {
+    FB_CUDA(cudaMemcpyAsync(B.dint, B.hint, sizeof(int) * 2 * B.R, cudaMemcpyHostToDevice, s));
+    return FB_OK;
+}
+
+// Inner lockstep FGMRES on A d_r = rhs_r (r with in[r]) from d = 0.
+static fb_status bfgmres_inner(fb_op* A, fb_precond* pc, BatchWork& B, const std::vector<char>& in,
+                               const std::vector<double>& rhs_norm, const std::vector<double>& rel_tol,
+                               const std::vector<int>& budget, std::vector<int>& iters, std::vector<double>& est_rel,
+                               std::vector<int>& status, cudaStream_t s) {
+    const int64_t n = B.n;
+    const int m = B.m, R = B.R;
+    const int gx = std::min(grid_for(n), 64);
+    int* act = B.hint;
+    int* j1 = B.hint + R;
+    int* dact = B.dint;
+    int* dj1 = B.dint + R;
+    std::vector<char> fin(R, 1);
+    for (int r = 0; r < R; ++r) {
+        fin[r] = !in[r];
+        iters[r] = 0;
+        est_rel[r] = 0.0;
+        status[r] = FB_OK;
+    }
+    FB_CUDA(cudaMemsetAsync(B.D, 0, sizeof(cd) * n * R, s));
+    std::vector<double> est(R, 0.0);
+    bool first = true;
+    while (true) {
+        for (int r = 0; r < R; ++r) act[r] = !fin[r];
+        FB_CHECK(upload_ints(B, s));
+        if (first) {
+            FB_CUDA(cudaMemcpyAsync(B.W, B.Rs, sizeof(cd) * n * R, cudaMemcpyDeviceToDevice, s));
+        } else {
+            FB_CHECK(fb_apply_any(A, B.D, B.T, s, R));
+            k_bsub<<<dim3(grid_for(n), R), KB, 0, s>>>(B.W, B.Rs, B.T, n, dact);
+            cnt();
+        }
+        first = false;
+        FB_CUDA(cudaMemsetAsync(B.scal, 0, sizeof(double) * 4 * R, s));
+        k_bnorm2<<<dim3(grid_for(n), R), KB, 0, s>>>(B.W, n, B.scal, 4, dact);
+        k_bcycle_start<<<R, 1, 0, s>>>(B.dhs, dact);
+        k_bscale<<<dim3(grid_for(n), R), KB, 0, s>>>(B.V, B.W, n, B.scal + 1, 4, dact);
+        FB_LAUNCH_CHECK();
+        cnt(3);
+        FB_CUDA(cudaMemcpyAsync(B.host, B.scal, sizeof(double) * 4 * R, cudaMemcpyDeviceToHost, s));
+        FB_CUDA(cudaStreamSynchronize(s));
+        bool any = false;
+        for (int r = 0; r < R; ++r) {
+            j1[r] = 0;
+            if (fin[r]) { act[r] = 0; continue; }
+            est[r] = B.host[4 * r + 2];
+            if (!std::isfinite(est[r])) { status[r] = FB_ERR_NAN; fin[r] = 1; act[r] = 0; continue; }
+            if (est[r] <= rel_tol[r] * rhs_norm[r] || iters[r] >= budget[r]) { fin[r] = 1; act[r] = 0; continue; }
+            act[r] = 1;
+            any = true;
+        }
+        FB_CHECK(upload_ints(B, s));
+        if (!any) break;
+        for (int j = 0; j < m; ++j) {
+            cd* Vj = B.V + (int64_t)j * R * n;
+            cd* Zj = Vj;
+            if (pc) {
+                Zj = B.Z + (int64_t)j * R * n;
+                FB_CHECK(fb_pc_apply(pc, Vj, Zj, s, R));
+            }
+            FB_CHECK(fb_apply_any(A, Zj, B.W, s, R));
+            for (int pass = 0; pass < 2; ++pass) {
+                FB_CUDA(cudaMemsetAsync(B.small + (size_t)R * (m + 1) * m, 0, sizeof(cd) * R * (m + 1), s));
+                cd* h = B.small + (size_t)R * (m + 1) * m;    // [R][m+1] CGS scratch (Hess.h)
+                k_bmdot<<<dim3(gx, j + 1, R), KB, 0, s>>>(B.V, n, R, B.W, h, m + 1, dact);
+                k_bgs_update<<<dim3(grid_for(n), R), KB, 0, s>>>(B.V, n, R, j + 1, h, m + 1, B.W, dact);
+                k_baccum_h<<<R, 1024, 0, s>>>(B.dhs, j, dact);
+                cnt(3);
+            }
+            FB_CUDA(cudaMemsetAsync(B.scal, 0, sizeof(double) * 4 * R, s));   // active rows are all rewritten
+            k_bnorm2<<<dim3(grid_for(n), R), KB, 0, s>>>(B.W, n, B.scal, 4, dact);
+            k_barnoldi_close<<<R, 1, 0, s>>>(B.dhs, j, dact);
+            k_bscale<<<dim3(grid_for(n), R), KB, 0, s>>>(B.V + (int64_t)(j + 1) * R * n, B.W, n, B.scal + 1, 4, dact);
+            FB_LAUNCH_CHECK();
+            cnt(3);
+            FB_CUDA(cudaMemcpyAsync(B.host, B.scal, sizeof(double) * 4 * R, cudaMemcpyDeviceToHost, s));
+            FB_CUDA(cudaStreamSynchronize(s));
+            bool changed = false;
+            any = false;
+            for (int r = 0; r < R; ++r) {
+                if (!act[r]) continue;
+                double e = B.host[4 * r + 2], hn = B.host[4 * r];
+                iters[r]++;
+                j1[r] = j + 1;
+                est[r] = e;
+                bool stop = false;
+                if (!std::isfinite(e)) { status[r] = FB_ERR_NAN; fin[r] = 1; stop = true; }
+                else if (hn == 0.0 || e <= rel_tol[r] * rhs_norm[r] || iters[r] >= budget[r]) { fin[r] = 1; stop = true; }
+                if (stop) { act[r] = 0; changed = true; } else any = true;
+            }
+            if (!any) break;
+            if (changed) FB_CHECK(upload_ints(B, s));
+        }
+        // x-update of every system that took steps in this cycle (NaN ones excluded)
+        for (int r = 0; r < R; ++r) if (status[r] != FB_OK) j1[r] = 0;
+        FB_CHECK(upload_ints(B, s));
+        k_bbacksolve<<<R, 1, 0, s>>>(B.dhs, dj1);
+        cd* ys = B.small + (size_t)R * (m + 1) * m + (size_t)R * (m + 1) * 5;   // Hess.y block
+        k_bupdate_x<<<dim3(grid_for(n), R), KB, 0, s>>>(B.D, pc ? B.Z : B.V, n, R, dj1, ys, m + 1);
+        FB_LAUNCH_CHECK();
+        cnt(2);
+        bool all = true;
+        for (int r = 0; r < R; ++r) all = all && fin[r];
+        if (all) break;
+    }
+    for (int r = 0; r < R; ++r) est_rel[r] = rhs_norm[r] > 0 ? est[r] / rhs_norm[r] : 0.0;
+    return FB_OK;
+}
+
+fb_status fb_fgmres_multi_impl(fb_op* A, fb_precond* pc, const cd* b, cd* x, int R, const fb_solver_opts* o,
+                               fb_solve_info* info, cudaStream_t s) {
+    fb_solver_opts opts = *o;
+    if (opts.restart < 1 || opts.restart > 1000) return fb_fail(FB_ERR_ARG, "restart must be in [1, 1000]");
+    if (opts.maxit < 1) return fb_fail(FB_ERR_ARG, "maxit must be >= 1");
+    if (opts.max_refine < 1) opts.max_refine = 1;
+    fb_op* T = opts.true_op ? const_cast<fb_op*>(opts.true_op) : A;
+    if (T->n != A->n) return fb_fail(FB_ERR_ARG, "true_op size differs");
+    const int64_t n = A->n;
+    const int m = opts.restart;
+    BatchWork B;
+    B.n = n;
+    B.m = m;
+    B.R = R;
+    FB_CHECK(dalloc(&B.V, (size_t)(m + 1) * R * n));
+    if (pc) FB_CHECK(dalloc(&B.Z, (size_t)m * R * n));
+    FB_CHECK(dalloc(&B.W, (size_t)R * n));
+    FB_CHECK(dalloc(&B.Rs, (size_t)R * n));
+    FB_CHECK(dalloc(&B.D, (size_t)R * n));
+    FB_CHECK(dalloc(&B.T, (size_t)R * n));
+    // small state: H [R][(m+1) m] | h, cs, sn, g, y, spare [R][m+1] each
+    FB_CHECK(dalloc(&B.small, (size_t)R * (m + 1) * m + (size_t)R * (m + 1) * 6));
+    FB_CHECK(dalloc(&B.scal, (size_t)4 * R));
+    FB_CHECK(dalloc(&B.dint, (size_t)2 * R));
+    FB_CHECK(dalloc(&B.dhs, (size_t)R));
+    FB_CUDA(cudaMallocHost((void**)&B.host, sizeof(double) * 4 * R));
+    FB_CUDA(cudaMallocHost((void**)&B.hint, sizeof(int) * 2 * R));
+    std::vector<Hess> hh(R);
+    cd* H0 = B.small;
+    cd* blk = B.small + (size_t)R * (m + 1) * m;
+    for (int r = 0; r < R; ++r) {
+        Hess& h = hh[r];
+        h.m = m;
+        h.H = H0 + (size_t)r * (m + 1) * m;
+        h.h = blk + (size_t)0 * R * (m + 1) + (size_t)r * (m + 1);
+        h.cs = blk + (size_t)1 * R * (m + 1) + (size_t)r * (m + 1);
+        h.sn = blk + (size_t)2 * R * (m + 1) + (size_t)r * (m + 1);
+        h.g = blk + (size_t)3 * R * (m + 1) + (size_t)r * (m + 1);
+        h.y = blk + (size_t)5 * R * (m + 1) + (size_t)r * (m + 1);
+        h.nrm2 = B.scal + 4 * r;
+        h.inv = B.scal + 4 * r + 1;
+        h.est = B.scal + 4 * r + 2;
+    }
+    FB_CUDA(cudaMemcpyAsync(B.dhs, hh.data(), sizeof(Hess) * R, cudaMemcpyHostToDevice, s));
+
+    std::vector<fb_solve_info> inf(R);
+    for (auto& q : inf) q = fb_solve_info{};
+    FB_CUDA(cudaMemsetAsync(x, 0, sizeof(cd) * n * R, s));
+    // ||b_r||
+    std::vector<double> bn(R), rn(R);
+    FB_CUDA(cudaMemsetAsync(B.scal, 0, sizeof(double) * 4 * R, s));
+    k_bnorm2<<<dim3(grid_for(n), R), KB, 0, s>>>(b, n, B.scal, 4, nullptr);
+    cnt();
+    FB_CUDA(cudaMemcpyAsync(B.host, B.scal, sizeof(double) * 4 * R, cudaMemcpyDeviceToHost, s));
+    FB_CUDA(cudaStreamSynchronize(s));
+    for (int r = 0; r < R; ++r) rn[r] = bn[r] = std::sqrt(B.host[4 * r]);
+    FB_CUDA(cudaMemcpyAsync(B.Rs, b, sizeof(cd) * n * R, cudaMemcpyDeviceToDevice, s));
+    const double inner_floor = opts.inner_tol > 0 ? opts.inner_tol : 0.0;
+    std::vector<char> in(R);
+    std::vector<double> rel(R);
+    std::vector<int> budget(R), its(R), st(R);
+    std::vector<double> estr(R);
+    std::vector<int> status(R, FB_OK);
+    for (int sweep = 0; sweep < opts.max_refine; ++sweep) {
+        bool any = false;
+        for (int r = 0; r < R; ++r) {
+            in[r] = status[r] == FB_OK && bn[r] > 0 && rn[r] > opts.tol * bn[r] && inf[r].iters < opts.maxit;
+            any = any || in[r];
+            rel[r] = in[r] ? std::max(inner_floor, 0.5 * opts.tol * bn[r] / rn[r]) : 0.0;
+            budget[r] = opts.maxit - inf[r].iters;
+        }
+        if (!any) break;
+        FB_CHECK(bfgmres_inner(A, pc, B, in, rn, rel, budget, its, estr, st, s));
+        for (int r = 0; r < R; ++r) {
+            B.hint[r] = in[r] && st[r] == FB_OK;
+            B.hint[R + r] = 0;
+        }
+        FB_CHECK(upload_ints(B, s));
+        k_badd<<<dim3(grid_for(n), R), KB, 0, s>>>(x, B.D, n, B.dint);
+        cnt();
+        // true residuals r = b - T x (all systems, one batched matvec)
+        FB_CHECK(fb_apply_any(T, x, B.T, s, R));
+        k_bsub<<<dim3(grid_for(n), R), KB, 0, s>>>(B.Rs, b, B.T, n, nullptr);
+        FB_CUDA(cudaMemsetAsync(B.scal, 0, sizeof(double) * 4 * R, s));
+        k_bnorm2<<<dim3(grid_for(n), R), KB, 0, s>>>(B.Rs, n, B.scal, 4, nullptr);
+        FB_LAUNCH_CHECK();
+        cnt(2);
+        FB_CUDA(cudaMemcpyAsync(B.host, B.scal, sizeof(double) * 4 * R, cudaMemcpyDeviceToHost, s));
+        FB_CUDA(cudaStreamSynchronize(s));
+        for (int r = 0; r < R; ++r) {
+            if (!in[r]) continue;
+            inf[r].iters += its[r];
+            inf[r].est_relres = estr[r] * rn[r] / bn[r];
+            inf[r].refinements = sweep + 1;
+            inf[r].true_matvecs++;
+            if (st[r] != FB_OK) status[r] = st[r];
+            rn[r] = std::sqrt(B.host[4 * r]);
+            if (!std::isfinite(rn[r])) status[r] = FB_ERR_NAN;
+        }
+    }
+    fb_status worst = FB_OK;
+    for (int r = 0; r < R; ++r) {
+        inf[r].true_relres = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
+        int stt = status[r];
+        if (stt == FB_OK && !(inf[r].true_relres <= opts.tol)) stt = FB_ERR_NOCONV;
+        inf[r].status = stt;
+        if (worst == FB_OK && stt != FB_OK) worst = stt;
+        if (info) info[r] = inf[r];
+    }
+    if (worst != FB_OK)
+        fb_set_error(worst, worst == FB_ERR_NOCONV ? "FGMRES (batched): a system did not reach the tolerance"
+                                                   : "FGMRES (batched): a system stopped on a non-finite residual");
+    return worst;
 }
 
 fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond** out) {
@@ -533,16 +900,21 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
     return FB_OK;
 }
 
-fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s) {
-    if (pc->net) return fb_learned_forward(pc->net, x, y, s);
+fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, int nrhs) {
+    const int64_t n = pc->n;
+    if (pc->net) {
+        for (int r = 0; r < nrhs; ++r) FB_CHECK(fb_learned_forward(pc->net, x + r * n, y + r * n, s));
+        return FB_OK;
+    }
     const fb_tree* t = pc->op->tree;
     int nleaf = t->nbox[t->L];
     int maxn = 0;
     for (int b = 0; b < nleaf; ++b) maxn = std::max(maxn, t->h_leaf_start[b + 1] - t->h_leaf_start[b]);
+    dim3 g(nleaf, nrhs);
     if (pc->inv32) {
-        k_bj_apply<float><<<nleaf, 128, sizeof(cf) * maxn, s>>>(t->leaf_start, t->perm, pc->blk_off, pc->inv32, x, y);
+        k_bj_apply<float><<<g, 128, sizeof(cf) * maxn, s>>>(t->leaf_start, t->perm, pc->blk_off, pc->inv32, x, y, n);
     } else {
-        k_bj_apply<double><<<nleaf, 128, sizeof(cd) * maxn, s>>>(t->leaf_start, t->perm, pc->blk_off, pc->inv64, x, y);
+        k_bj_apply<double><<<g, 128, sizeof(cd) * maxn, s>>>(t->leaf_start, t->perm, pc->blk_off, pc->inv64, x, y, n);
     }
     FB_LAUNCH_CHECK();
     fb_count_launch();

@@ -30,6 +30,8 @@
 // flag, drains its own copies and MMAs (bounded) and releases tensor memory.
 #include <algorithm>
 
+#include <map>
+
 #include "common.cuh"
 
 namespace {
@@ -96,6 +98,8 @@ struct TcTask {
     int32_t stride_f;                   // floats per box vector in the hi/lo planes
     int64_t plane_base;                 // float offset of the level in the planes
     int64_t dst_base;                   // complex offset of the target level
+    int32_t nbox_src;                   // boxes of the source level (planes hold nrhs sets)
+    int32_t pad;
 };
 struct TcTile {
     int32_t task, rt, col0, ncol;
@@ -133,20 +137,24 @@ struct SplitLevel {
     int64_t plane_base;   // float offset in the planes
     int32_t nbox, P, stride_f, pad;
 };
+// With nrhs right-hand sides a level's planes hold nrhs sets of nbox vectors
+// (plane_base scaled by nrhs), set r read from mp + r * rstride.
 __global__ void k_tc_split(const SplitLevel* __restrict__ lv, int nlev, const cf* __restrict__ mp,
-                           float* __restrict__ hi, float* __restrict__ lo) {
+                           float* __restrict__ hi, float* __restrict__ lo, int nrhs, int64_t rstride) {
     int l = blockIdx.y;
     if (l >= nlev) return;
     SplitLevel L = lv[l];
-    int64_t total = (int64_t)L.nbox * L.stride_f;
-    const float* src = (const float*)(mp + L.src_base);
+    int64_t per = (int64_t)L.nbox * L.stride_f;
+    int64_t total = per * nrhs;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t b = i / L.stride_f;
-        int k = (int)(i % L.stride_f);
+        int64_t r = i / per, ib = i - r * per;
+        int64_t b = ib / L.stride_f;
+        int k = (int)(ib % L.stride_f);
+        const float* src = (const float*)(mp + r * rstride + L.src_base);
         float v = k < 2 * L.P ? src[b * 2 * L.P + k] : 0.f;
         float h = tf32_hi(v);
-        hi[L.plane_base + i] = h;
-        lo[L.plane_base + i] = v - h;
+        hi[L.plane_base * nrhs + i] = h;
+        lo[L.plane_base * nrhs + i] = v - h;
     }
 }
 
@@ -155,14 +163,15 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
                                                       const int32_t* __restrict__ dst_idx,
                                                       const float* __restrict__ plane_hi,
                                                       const float* __restrict__ plane_lo, cf* __restrict__ dst,
-                                                      int* __restrict__ err) {
+                                                      int* __restrict__ err, int nrhs, int64_t rstride) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
     __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_holder;
-    __shared__ int s_src[TC_NMAX];
+    __shared__ int s_src[TC_NMAX];       // source vector index in the planes (rhs * nbox + box)
     __shared__ int s_dst[TC_NMAX];
+    __shared__ int s_rhs[TC_NMAX];
     __shared__ int s_fail;
     uint32_t raw = smem_u32(smem_raw);
     uint32_t pad = (1024 - (raw & 1023)) & 1023;
@@ -174,10 +183,14 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
     const int ncol = tl.ncol;
     const int nmma = (ncol + 15) & ~15;
     const int nkc = tk.nkc;
+    // column j: pair (col0 + j) / nrhs, right-hand side (col0 + j) % nrhs
     for (int j = tid; j < TC_NMAX; j += blockDim.x) {
         bool ok = j < ncol;
-        s_src[j] = ok ? src_idx[tk.pair_off + tl.col0 + j] : -1;
-        s_dst[j] = ok ? dst_idx[tk.pair_off + tl.col0 + j] : -1;
+        int col = tl.col0 + j;
+        int pr = col / nrhs, rh = col - pr * nrhs;
+        s_src[j] = ok ? rh * tk.nbox_src + src_idx[tk.pair_off + pr] : -1;
+        s_dst[j] = ok ? dst_idx[tk.pair_off + pr] : -1;
+        s_rhs[j] = ok ? rh : 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
@@ -215,10 +228,11 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
                 int k = c * TC_KC + 4 * q;
                 int sb = s_src[j];
                 const float* pl = plane ? plane_lo : plane_hi;
-                const float* g = pl + tk.plane_base;   // valid address even when nothing is read
+                const int64_t base = tk.plane_base * nrhs;
+                const float* g = pl + base;   // valid address even when nothing is read
                 int bytes = 0;
                 if (sb >= 0 && k < tk.stride_f) {
-                    g = pl + tk.plane_base + (int64_t)sb * tk.stride_f + k;
+                    g = pl + base + (int64_t)sb * tk.stride_f + k;
                     bytes = 16;
                 }
                 uint32_t d = smem_u32(sBh + plane * B_BLOCK) + canon(j, 4 * q);
@@ -309,7 +323,8 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
                     int j = c0 + q;
                     int db = s_dst[j];
                     if (db < 0) continue;
-                    float* d = (float*)(dst + tk.dst_base + (int64_t)db * tk.p_out2 + r) + part;
+                    float* d = (float*)(dst + s_rhs[j] * rstride + tk.dst_base + (int64_t)db * tk.p_out2 + r) +
+                               part;
                     atomicAdd(d, __uint_as_float(v[q]));
                 }
             }
@@ -340,6 +355,8 @@ struct TcPlanImpl {
     const int32_t* dst_idx = nullptr;
     int64_t a_floats = 0, plane_floats = 0;
     int max_split = 0;
+    int plane_nrhs = 1;                     // right-hand sides the planes hold
+    std::map<int, std::pair<TcTile*, int>> multi;   // tiles for nrhs > 1
 };
 
 size_t fb_tc_smem_bytes() { return (size_t)TC_STAGES * STAGE_FLOATS * sizeof(float) + 1024; }
@@ -386,6 +403,8 @@ fb_status fb_tc_build_groups(fb_op* op, const std::vector<TcGroup>& groups, cons
         tk.stride_f = sl.stride_f;
         tk.plane_base = sl.plane_base;
         tk.dst_base = op->lev_off[g.dst_level];
+        tk.nbox_src = sl.nbox;
+        tk.pad = 0;
         int ti = (int)pl->h_tasks.size();
         pl->h_tasks.push_back(tk);
         for (int rt = 0; rt < tk.nrt; ++rt)
@@ -434,13 +453,47 @@ fb_status fb_tc_build(fb_op* op, const std::vector<int>& levels, void** slot, cu
     return fb_tc_build_groups(op, groups, t->m2l_src, t->m2l_dst, slot, s);
 }
 
-fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s) {
+// Runs a plan on nrhs sets of expansions (set r at src/dst + r * rstride).
+// The columns of a task are its (pair, rhs) combinations, so every tile of
+// the translation matrix is loaded once for all right-hand sides.
+fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s, int nrhs, int64_t rstride) {
     TcPlanImpl* pl = (TcPlanImpl*)plan;
     if (!pl || pl->h_tiles.empty()) return FB_OK;
+    const TcTile* tiles = pl->tiles;
+    int ntiles = (int)pl->h_tiles.size();
+    if (nrhs > 1) {
+        if (nrhs > pl->plane_nrhs) {
+            cudaStreamSynchronize(s);
+            dfree(pl->plane_hi);
+            dfree(pl->plane_lo);
+            FB_CHECK(dalloc(&pl->plane_hi, pl->plane_floats * nrhs));
+            FB_CHECK(dalloc(&pl->plane_lo, pl->plane_floats * nrhs));
+            pl->plane_nrhs = nrhs;
+        }
+        auto it = pl->multi.find(nrhs);
+        if (it == pl->multi.end()) {
+            std::vector<TcTile> h;
+            for (int ti = 0; ti < (int)pl->h_tasks.size(); ++ti) {
+                const TcTask& tk = pl->h_tasks[ti];
+                int ncol = tk.npairs * nrhs;
+                for (int rt = 0; rt < tk.nrt; ++rt)
+                    for (int c0 = 0; c0 < ncol; c0 += TC_NMAX)
+                        h.push_back(TcTile{ti, rt, c0, std::min(TC_NMAX, ncol - c0)});
+            }
+            TcTile* d = nullptr;
+            FB_CHECK(dalloc(&d, h.size()));
+            FB_CUDA(cudaMemcpy(d, h.data(), sizeof(TcTile) * h.size(), cudaMemcpyHostToDevice));
+            it = pl->multi.emplace(nrhs, std::make_pair(d, (int)h.size())).first;
+        }
+        tiles = it->second.first;
+        ntiles = it->second.second;
+    }
     dim3 sg(pl->max_split, (unsigned)pl->h_split.size());
-    k_tc_split<<<sg, 256, 0, s>>>(pl->split, (int)pl->h_split.size(), src, pl->plane_hi, pl->plane_lo);
-    k_trans_tc<<<(unsigned)pl->h_tiles.size(), 256, fb_tc_smem_bytes(), s>>>(
-        pl->tasks, pl->tiles, pl->A, pl->src_idx, pl->dst_idx, pl->plane_hi, pl->plane_lo, dst, pl->err);
+    k_tc_split<<<sg, 256, 0, s>>>(pl->split, (int)pl->h_split.size(), src, pl->plane_hi, pl->plane_lo, nrhs,
+                                  rstride);
+    k_trans_tc<<<(unsigned)ntiles, 256, fb_tc_smem_bytes(), s>>>(pl->tasks, tiles, pl->A, pl->src_idx,
+                                                                 pl->dst_idx, pl->plane_hi, pl->plane_lo, dst,
+                                                                 pl->err, nrhs, rstride);
     FB_LAUNCH_CHECK();
     fb_count_launch(2);
     return FB_OK;
@@ -473,6 +526,7 @@ void fb_tc_free(void*& plan) {
     dfree(pl->tiles);
     dfree(pl->split);
     dfree(pl->err);
+    for (auto& kv : pl->multi) dfree(kv.second.first);
     delete pl;
     plan = nullptr;
 }

@@ -427,6 +427,10 @@ void fb_tree_free(fb_tree* t) {
     for (auto& rs : t->rot_sets) {
         dfree(rs.r64);
         dfree(rs.r32);
+        dfree(rs.d64);
+        dfree(rs.d32);
+        dfree(rs.ph64);
+        dfree(rs.ph32);
     }
     delete t;
 }

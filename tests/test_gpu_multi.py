@@ -1,0 +1,83 @@
+"""Several right-hand sides per call: the batched FMM matvec against one
+call per right-hand side (every translation method, mixed and FP64), and the
+lockstep batched FGMRES against single solves (each system meets its own
+true-residual tolerance; solutions and iteration counts agree)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2103_16073_gb300 as fb
+from _cases import rel, seeded_vector, workload
+
+
+@pytest.fixture(scope="module", params=["small", "sub"])
+def setup(request):
+    wl = workload(request.param)
+    mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+    fb.fb_mesh_set_admittance(mesh, wl.beta)
+    tree = fb.fb_tree_build(mesh, 64)
+    ops = {}
+
+    def op(prec):
+        if prec not in ops:
+            ops[prec] = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, prec, 6.0, 12)
+        return ops[prec]
+
+    yield wl, mesh, op
+    for o in ops.values():
+        fb.fb_operator_destroy(o)
+    fb.fb_tree_destroy(tree)
+    fb.fb_mesh_destroy(mesh)
+
+
+METHODS = {"auto": fb.FB_TRANS_AUTO, "rcr": fb.FB_TRANS_RCR, "tensor": fb.FB_TRANS_TENSOR,
+           "composed": fb.FB_TRANS_COMPOSED}
+
+
+@pytest.mark.parametrize("prec,method", [("mixed", "auto"), ("mixed", "rcr"), ("mixed", "tensor"),
+                                         ("mixed", "composed"), ("fp64", "auto")])
+def test_apply_multi_matches_single(setup, prec, method):
+    wl, mesh, op = setup
+    A = op(fb.FB_PREC_MIXED_FMM if prec == "mixed" else fb.FB_PREC_FP64_FMM)
+    fb.fb_operator_set_translation(A, METHODS[method])
+    try:
+        R = 5   # a full chunk of four and a ragged one
+        X = torch.tensor(np.stack([seeded_vector(wl.n, 100 + r) for r in range(R)]), device="cuda")
+        Y = torch.empty_like(X)
+        fb.fb_operator_apply_multi(A, X, Y)
+        y1 = torch.empty_like(X[0])
+        tol = 1e-6 if prec == "mixed" else 1e-13
+        for r in range(R):
+            fb.fb_operator_apply(A, X[r].contiguous(), y1)
+            assert rel(Y[r].cpu().numpy(), y1.cpu().numpy()) < tol, (prec, method, r)
+    finally:
+        fb.fb_operator_set_translation(A, fb.FB_TRANS_AUTO)
+
+
+def test_fgmres_multi_matches_single(setup):
+    wl, mesh, op = setup
+    A = op(fb.FB_PREC_MIXED_FMM)
+    A64 = op(fb.FB_PREC_FP64_FMM)
+    bj = fb.fb_precond_create(A, fb.FB_PC_BLOCK_JACOBI)
+    try:
+        from paper_2103_16073_gb300 import workloads as W
+        rng = W.seeded_rng(60)
+        srcs = W.uniform_points_in_box(rng, [0, 0, 0], list(wl.room), 3, 0.3)
+        B = torch.empty((3, wl.n), dtype=torch.complex128, device="cuda")
+        g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
+        for r, s in enumerate(srcs):
+            fb.fb_gamma_monopole(mesh, wl.k, s, g)
+            fb.fb_operator_apply(A64, g, B[r])
+        X = torch.zeros_like(B)
+        infos = fb.fb_fgmres_solve_multi(A, B, X, pc=bj, tol=1e-6, restart=20, true_op=A64)
+        for r in range(3):
+            x1 = torch.zeros_like(g)
+            i1 = fb.fb_fgmres_solve(A, B[r].contiguous(), x1, pc=bj, tol=1e-6, restart=20, true_op=A64)
+            assert infos[r]["status"] == 0 and infos[r]["true_relres"] <= 1e-6
+            assert abs(infos[r]["iters"] - i1["iters"]) <= 1
+            assert rel(X[r].cpu().numpy(), x1.cpu().numpy()) < 1e-4
+        print("iterations", [i["iters"] for i in infos])
+    finally:
+        fb.fb_precond_destroy(bj)
