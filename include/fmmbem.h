@@ -257,6 +257,18 @@ FB_API fb_status fb_measure_alu_peaks(double* fp32_tflops, double* fp64_tflops, 
  * a matvec.  1 <= nrhs <= FB_MAX_RHS.  The operator's expansion buffers grow
  * to nrhs sets on first use.  Errors: FB_ERR_ARG. */
 #define FB_MAX_RHS 64
+
+/* Autotuner of the translation passes of a mixed-precision FMM operator: for
+ * every level it times on the device (median of 5, nrhs right-hand sides)
+ * the per-pair rotation-coaxial-rotation kernel (Sec. 3.3) against the
+ * stacked tensor-core GEMM of composed matrices, for M2L and for the
+ * M2M/L2L passes into the level, and installs the faster form per level
+ * (translation method FB_TRANS_AUTO).  times: 4*13 doubles or NULL,
+ * times[4l + 0..3] = M2L RCR, M2L tensor, M2M+L2L RCR, M2M+L2L tensor in ms
+ * (-1: not a candidate); choice: 13 ints or NULL, bit 0 = M2L of level l on
+ * the tensor cores, bit 1 = M2M/L2L into level l on the tensor cores.
+ * FP64 operators (RCR only) are left unchanged.  Errors: FB_ERR_ARG. */
+FB_API fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times, int* choice);
 FB_API fb_status fb_operator_apply_multi(fb_op* op, const double* x, double* y, int nrhs, int memspace,
                                          void* stream);
 

@@ -31,7 +31,7 @@ __all__ = [
     "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
     "fb_precond_create_learned", "fb_learned_params", "fb_learned_set_objective",
     "FB_LOSS_ERROR", "FB_LOSS_RESIDUAL", "fb_learned_loss_and_grad", "fb_learned_train_step",
-    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS",
+    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -389,6 +389,29 @@ def fb_fgmres_solve_multi(A, B, X, pc=None, tol=1e-8, restart=40, maxit=2000, ma
     if mx == FB_MEM_HOST and kx is not X:
         X[...] = kx
     return [i.as_dict() for i in infos]
+
+
+lib.fb_operator_autotune.restype = C.c_int
+lib.fb_operator_autotune.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+
+
+def fb_operator_autotune(op, nrhs=1, stream=None):
+    """Times RCR vs tensor-core translations per level and installs the faster
+    form; returns {level: {"m2l_rcr", "m2l_tensor", "m2m_l2l_rcr",
+    "m2m_l2l_tensor" (ms, None if not a candidate), "m2l_on_tensor",
+    "m2m_l2l_on_tensor"}}."""
+    times = np.full(4 * 13, -1.0)
+    choice = np.zeros(13, np.int32)
+    _check(lib.fb_operator_autotune(op, int(nrhs), _stream(stream), times.ctypes.data, choice.ctypes.data))
+    out = {}
+    for l in range(13):
+        t = times[4 * l:4 * l + 4]
+        if np.all(t < 0):
+            continue
+        f = lambda v: None if v < 0 else round(float(v), 4)
+        out[l] = {"m2l_rcr": f(t[0]), "m2l_tensor": f(t[1]), "m2m_l2l_rcr": f(t[2]), "m2m_l2l_tensor": f(t[3]),
+                  "m2l_on_tensor": bool(choice[l] & 1), "m2m_l2l_on_tensor": bool(choice[l] & 2)}
+    return out
 
 
 FB_TRANS_AUTO, FB_TRANS_COMPOSED, FB_TRANS_RCR, FB_TRANS_TENSOR = 0, 1, 2, 3

@@ -311,6 +311,17 @@ fb_status fb_operator_set_translation(fb_op* op, int method) {
     return FB_OK;
 }
 
+fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times, int* choice) {
+    if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
+    if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "dense operators have no translations");
+    if (nrhs < 1 || nrhs > FB_MAX_RHS) return fb_fail(FB_ERR_ARG, "nrhs must be in [1, FB_MAX_RHS]");
+    if (times)
+        for (int i = 0; i < 4 * (FB_MAXLEV + 1); ++i) times[i] = -1.0;
+    if (choice)
+        for (int i = 0; i <= FB_MAXLEV; ++i) choice[i] = 0;
+    return fb_autotune_impl(op, nrhs, as_stream(stream), times, choice);
+}
+
 fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
     if (n) *n = op->n;

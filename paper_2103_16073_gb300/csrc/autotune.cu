@@ -1,0 +1,174 @@
+// Autotuner of the translation passes (mixed precision).  For every level it
+// times, on the device and for a given number of right-hand sides, the
+// per-pair rotation-coaxial-rotation kernel (RCR) against the stacked
+// tensor-core GEMM of composed matrices (3xTF32), for M2L and for the M2M /
+// L2L passes into that level, and keeps the faster form.  The tensor-core
+// candidate of a level is skipped when its composed matrices would exceed a
+// memory cap.  The result replaces the operator's rule-based choice
+// (>= 48 pairs per translation vector); FP64 operators have only the RCR
+// form and are left unchanged.
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    Timer() {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~Timer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+// Median of `reps` timed runs of f (after one untimed run), in ms.
+template <class F>
+fb_status time_ms(F&& f, cudaStream_t s, int reps, double* out) {
+    Timer t;
+    FB_CHECK(f());
+    std::vector<float> v;
+    for (int i = 0; i < reps; ++i) {
+        FB_CUDA(cudaEventRecord(t.a, s));
+        FB_CHECK(f());
+        FB_CUDA(cudaEventRecord(t.b, s));
+        FB_CUDA(cudaEventSynchronize(t.b));
+        float ms = 0.f;
+        FB_CUDA(cudaEventElapsedTime(&ms, t.a, t.b));
+        v.push_back(ms);
+    }
+    std::sort(v.begin(), v.end());
+    *out = v[v.size() / 2];
+    return FB_OK;
+}
+
+void free_rcr(RcrPlan& p) {
+    dfree(p.tasks);
+    dfree(p.tiles);
+    for (auto& kv : p.multi) dfree(kv.second.tiles);
+    p.multi.clear();
+}
+
+}  // namespace
+
+// times[4 * l + {0,1,2,3}] = M2L RCR, M2L tensor, M2M+L2L RCR, M2M+L2L tensor
+// (ms, -1 when not a candidate) for l = 0..L; choice[l] bit 0 = M2L on the
+// tensor cores, bit 1 = M2M/L2L into level l on the tensor cores.
+fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times, int* choice) {
+    if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;
+    const fb_tree* t = op->tree;
+    const int L = op->L;
+    const int64_t cnt = op->lev_off[L + 1];
+    const size_t csz = sizeof(cf);
+    const int reps = 5;
+    const double cap_bytes = 8.0e9;   // composed FP64 + packed TF32 tiles of one level
+    // expansion buffers for nrhs sets (contents do not matter for timing)
+    if (nrhs > op->exp_nrhs) {
+        cudaStreamSynchronize(s);
+        dfree(op->mp);
+        dfree(op->loc);
+        op->mp = op->loc = nullptr;
+        FB_CHECK(dalloc((cf**)&op->mp, cnt * nrhs));
+        FB_CHECK(dalloc((cf**)&op->loc, cnt * nrhs));
+        op->exp_nrhs = nrhs;
+    }
+    cf* mp = (cf*)op->mp;
+    cf* loc = (cf*)op->loc;
+    FB_CUDA(cudaMemsetAsync(mp, 0, sizeof(cf) * cnt * nrhs, s));
+    FB_CUDA(cudaMemsetAsync(loc, 0, sizeof(cf) * cnt * nrhs, s));
+    std::vector<int> tc_m2l;
+    for (int l = 2; l <= L; ++l) {
+        double* tl = times + 4 * l;
+        tl[0] = tl[1] = tl[2] = tl[3] = -1.0;
+        int ch = 0;
+        // ---- M2L of level l
+        RcrPlan pl;
+        for (const RcrTask& tk : op->m2l_rcr.h_tasks)
+            if (tk.src_base == op->lev_off[l]) pl.h_tasks.push_back(tk);
+        if (!pl.h_tasks.empty()) {
+            FB_CHECK(fb_rcr_upload(pl, t->m2l_src, t->m2l_dst, csz));
+            fb_status st = time_ms([&]() { return fb_rcr_run_op(op, pl, mp, loc, s, nrhs, cnt); }, s, reps, &tl[0]);
+            free_rcr(pl);
+            FB_CHECK(st);
+            int64_t p2 = (int64_t)op->p[l] * op->p[l];
+            double bytes = 0;
+            for (int c = 0; c < FB_NOFF; ++c)
+                if (t->m2l_group[(size_t)l * FB_NOFF + c + 1] > t->m2l_group[(size_t)l * FB_NOFF + c])
+                    bytes += (double)p2 * p2 * (16.0 + 2 * 8.0);
+            if (bytes <= cap_bytes) {
+                std::vector<int> need;
+                for (size_t j = 0; j < op->h_jobs.size(); ++j)
+                    if (op->h_job_m2l[j] && op->h_job_level[j] == l) need.push_back((int)j);
+                FB_CHECK(fb_compose_jobs(op, need, s));
+                void* plan = nullptr;
+                fb_status st2 = fb_tc_build(op, {l}, &plan, s);
+                if (st2 == FB_OK)
+                    st2 = time_ms([&]() { return fb_tc_run(op, plan, mp, loc, s, nrhs, cnt); }, s, reps, &tl[1]);
+                cudaStreamSynchronize(s);
+                fb_tc_free(plan);
+                FB_CHECK(st2);
+                if (tl[1] < tl[0]) {
+                    ch |= 1;
+                    tc_m2l.push_back(l);
+                }
+            }
+        }
+        // ---- M2M + L2L between levels l-1 and l
+        if (l >= 3) {
+            double r_ms = 0, r2 = 0;
+            FB_CHECK(time_ms([&]() { return fb_rcr_run_op(op, op->m2m_rcr[l], mp, mp, s, nrhs, cnt); }, s, reps, &r_ms));
+            FB_CHECK(time_ms([&]() { return fb_rcr_run_op(op, op->l2l_rcr[l], loc, loc, s, nrhs, cnt); }, s, reps, &r2));
+            tl[2] = r_ms + r2;
+            std::vector<int> need;
+            std::vector<TcGroup> up, down;
+            for (int o = 0; o < 8; ++o) {
+                int64_t g0 = t->oct_group[l][o], g1 = t->oct_group[l][o + 1];
+                if (g1 == g0) continue;
+                need.push_back(op->m2m_job[l][o]);
+                need.push_back(op->l2l_job[l][o]);
+                up.push_back(TcGroup{op->m2m_job[l][o], g0, (int32_t)(g1 - g0), l, l - 1});
+                down.push_back(TcGroup{op->l2l_job[l][o], g0, (int32_t)(g1 - g0), l - 1, l});
+            }
+            if (!up.empty()) {
+                FB_CHECK(fb_compose_jobs(op, need, s));
+                if (!op->tc_m2m[l])
+                    FB_CHECK(fb_tc_build_groups(op, up, t->oct_child[l], t->oct_parent[l], &op->tc_m2m[l], s));
+                if (!op->tc_l2l[l])
+                    FB_CHECK(fb_tc_build_groups(op, down, t->oct_parent[l], t->oct_child[l], &op->tc_l2l[l], s));
+                double a = 0, b = 0;
+                FB_CHECK(time_ms([&]() { return fb_tc_run(op, op->tc_m2m[l], mp, mp, s, nrhs, cnt); }, s, reps, &a));
+                FB_CHECK(time_ms([&]() { return fb_tc_run(op, op->tc_l2l[l], loc, loc, s, nrhs, cnt); }, s, reps, &b));
+                tl[3] = a + b;
+                if (tl[3] < tl[2]) {
+                    ch |= 2;
+                } else {
+                    cudaStreamSynchronize(s);
+                    fb_tc_free(op->tc_m2m[l]);
+                    fb_tc_free(op->tc_l2l[l]);
+                }
+            }
+        }
+        if (choice) choice[l] = ch;
+    }
+    // ---- install the M2L choice: tensor-core plan of the chosen levels, RCR for the rest
+    FB_CUDA(cudaStreamSynchronize(s));
+    fb_tc_free(op->tc_plan);
+    free_rcr(op->m2l_rcr_rest);
+    op->m2l_rcr_rest.h_tasks.clear();
+    for (int l = 0; l <= FB_MAXLEV; ++l) op->tc_level[l] = 0;
+    for (int l : tc_m2l) op->tc_level[l] = 1;
+    for (const RcrTask& tk : op->m2l_rcr.h_tasks) {
+        bool tc = false;
+        for (int l : tc_m2l) tc = tc || tk.src_base == op->lev_off[l];
+        if (!tc) op->m2l_rcr_rest.h_tasks.push_back(tk);
+    }
+    FB_CHECK(fb_rcr_upload(op->m2l_rcr_rest, t->m2l_src, t->m2l_dst, csz));
+    if (!tc_m2l.empty()) FB_CHECK(fb_tc_build(op, tc_m2l, &op->tc_plan, s));
+    FB_CUDA(cudaStreamSynchronize(s));
+    op->method = FB_TRANS_AUTO;
+    return FB_OK;
+}

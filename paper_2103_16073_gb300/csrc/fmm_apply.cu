@@ -581,6 +581,16 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
     return FB_OK;
 }
 
+// One RCR plan on the operator's expansion buffers (precision of the op).
+fb_status fb_rcr_run_op(fb_op* op, RcrPlan& pl, void* src, void* dst, cudaStream_t s, int nrhs, int64_t rstride) {
+    if (op->prec == FB_PREC_MIXED_FMM) {
+        RotArgs<float> rot{op->rotd32, (const cf*)op->rph32, op->per_dir, op->Prot};
+        return run_rcr<float>(pl, rot, op->coax32, (const cf*)src, (cf*)dst, s, nrhs, rstride);
+    }
+    RotArgs<double> rot{op->rotd64, (const cd*)op->rph64, op->per_dir, op->Prot};
+    return run_rcr<double>(pl, rot, op->coax64, (const cd*)src, (cd*)dst, s, nrhs, rstride);
+}
+
 fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt, int nrhs) {
     if (op->prec == FB_PREC_MIXED_FMM)
         return fmm_apply_t<float>(op, x, y, s, op->nf32, op->w32, op->v32, op->T32, pt, nullptr, nrhs);

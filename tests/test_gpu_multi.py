@@ -81,3 +81,27 @@ def test_fgmres_multi_matches_single(setup):
         print("iterations", [i["iters"] for i in infos])
     finally:
         fb.fb_precond_destroy(bj)
+
+
+def test_autotune_keeps_results(setup):
+    """After the autotuner installs its per-level choice the matvec still
+    agrees with the all-RCR form (single and multi right-hand side)."""
+    wl, mesh, op = setup
+    A = op(fb.FB_PREC_MIXED_FMM)
+    X = torch.tensor(np.stack([seeded_vector(wl.n, 300 + r) for r in range(3)]), device="cuda")
+    fb.fb_operator_set_translation(A, fb.FB_TRANS_RCR)
+    Yref = torch.empty_like(X)
+    fb.fb_operator_apply_multi(A, X, Yref)
+    fb.fb_operator_set_translation(A, fb.FB_TRANS_AUTO)
+    rep = fb.fb_operator_autotune(A, nrhs=3)
+    assert rep and all(v["m2l_rcr"] is not None for l, v in rep.items() if l >= 2)
+    Y = torch.empty_like(X)
+    fb.fb_operator_apply_multi(A, X, Y)
+    y1 = torch.empty_like(X[0])
+    fb.fb_operator_apply(A, X[0].contiguous(), y1)
+    # both are FP32 forms of the same translations (tensor-core composed
+    # matrices vs rotation-coaxial-rotation), equal up to FP32 rounding
+    for r in range(3):
+        assert rel(Y[r].cpu().numpy(), Yref[r].cpu().numpy()) < 1e-5
+    assert rel(y1.cpu().numpy(), Yref[0].cpu().numpy()) < 1e-5
+    print(rep)
