@@ -394,6 +394,48 @@ FB_API fb_status fb_fgmres_solve_multi(fb_op* A, fb_precond* pc, const double* b
                                        const fb_solver_opts* opts, fb_solve_info* info, int memspace,
                                        void* stream);
 
+/* ------------------------------------------------------- batch scheduler -- */
+
+/* One job of a batch: a mesh (admittance set) with its tree at one
+ * wavenumber, and nsrc monopole sources (Eq. sp6).  Outputs: x (device,
+ * nsrc x N complex, the surface field psi_sc of each source, Eq. dbem4),
+ * info (host, nsrc entries, may be NULL), times and status. */
+typedef struct fb_batch_job {
+    const fb_mesh* mesh;
+    const fb_tree* tree;
+    double k;
+    int nsrc;
+    const double* src;        /* host, nsrc x 3                               */
+    double* x;                /* device, nsrc x N complex                     */
+    fb_solve_info* info;      /* host, nsrc entries, or NULL                  */
+    double setup_ms;          /* out: operator + preconditioner (+ tuning)    */
+    double solve_ms;          /* out: right-hand sides + batched solves       */
+    int status;               /* out: FB_OK or the first failure              */
+    int order;                /* out: position in the execution order         */
+} fb_batch_job;
+
+typedef struct fb_batch_opts {
+    double tol;               /* true relative residual (FP64 judge)          */
+    int restart, maxit;       /* FGMRES; <= 0 selects 40 / 3000               */
+    double d0;                /* order rule (<= 0: 6)                         */
+    int pmin;                 /* order rule (<= 0: 12)                        */
+    int autotune;             /* 1: fb_operator_autotune per job              */
+    int max_rhs;              /* sources per batched solve (<= 0: 8)          */
+    int fp64_judge;           /* 1: true residual by the FP64 FMM operator    */
+    int lookahead;            /* 1: build job i+1 while job i solves          */
+} fb_batch_opts;
+
+/* Runs a batch (a frequency sweep with several sources per frequency, as in
+ * the paper's experiments, Sec. 4): jobs in order of decreasing predicted
+ * cost (sources x N x p_leaf^2); per job the mixed FMM operator, block
+ * Jacobi, the FP64 operators (b = L gamma, true residual) and, if asked, the
+ * autotuned translation forms are built once, then the job's sources are
+ * solved max_rhs at a time by fb_fgmres_solve_multi.  With lookahead a host
+ * thread builds the next job on a second stream while the current one
+ * solves.  Operators are released after each job.  Returns FB_OK when every
+ * solve converged, else the first failing status (per-job status set). */
+FB_API fb_status fb_batch_solve(fb_batch_job* jobs, int njobs, const fb_batch_opts* opts);
+
 /* ------------------------------------------------------------ receivers -- */
 
 /* Field at interior points by Green's identity (Eq. dbem1):

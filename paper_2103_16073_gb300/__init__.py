@@ -31,7 +31,7 @@ __all__ = [
     "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
     "fb_precond_create_learned", "fb_learned_params", "fb_learned_set_objective",
     "FB_LOSS_ERROR", "FB_LOSS_RESIDUAL", "fb_learned_loss_and_grad", "fb_learned_train_step",
-    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune",
+    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune", "fb_batch_solve",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -411,6 +411,51 @@ def fb_operator_autotune(op, nrhs=1, stream=None):
         f = lambda v: None if v < 0 else round(float(v), 4)
         out[l] = {"m2l_rcr": f(t[0]), "m2l_tensor": f(t[1]), "m2m_l2l_rcr": f(t[2]), "m2m_l2l_tensor": f(t[3]),
                   "m2l_on_tensor": bool(choice[l] & 1), "m2m_l2l_on_tensor": bool(choice[l] & 2)}
+    return out
+
+
+class BatchJob(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("tree", C.c_void_p), ("k", C.c_double), ("nsrc", C.c_int),
+                ("src", C.c_void_p), ("x", C.c_void_p), ("info", C.POINTER(SolveInfo)),
+                ("setup_ms", C.c_double), ("solve_ms", C.c_double), ("status", C.c_int), ("order", C.c_int)]
+
+
+class BatchOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("d0", C.c_double),
+                ("pmin", C.c_int), ("autotune", C.c_int), ("max_rhs", C.c_int), ("fp64_judge", C.c_int),
+                ("lookahead", C.c_int)]
+
+
+lib.fb_batch_solve.restype = C.c_int
+lib.fb_batch_solve.argtypes = [C.POINTER(BatchJob), C.c_int, C.POINTER(BatchOpts)]
+
+
+def fb_batch_solve(jobs, tol=1e-4, restart=40, maxit=3000, d0=6.0, pmin=12, autotune=True, max_rhs=8,
+                   fp64_judge=True, lookahead=True):
+    """jobs: list of dicts {mesh, tree, k, src [nsrc,3], x (CUDA complex128 [nsrc,N])}.
+    Returns one dict per job: {status, setup_ms, solve_ms, order, infos}."""
+    arr = (BatchJob * len(jobs))()
+    keep = []
+    for i, j in enumerate(jobs):
+        src = np.ascontiguousarray(j["src"], dtype=np.float64).reshape(-1, 3)
+        x = j["x"]
+        if not _is_cuda_tensor(x) or not x.is_contiguous() or x.shape[0] != src.shape[0]:
+            raise ValueError("x must be a contiguous CUDA tensor [nsrc, N]")
+        infos = (SolveInfo * src.shape[0])()
+        keep += [src, infos]
+        arr[i] = BatchJob(j["mesh"].value if hasattr(j["mesh"], "value") else j["mesh"],
+                          j["tree"].value if hasattr(j["tree"], "value") else j["tree"], float(j["k"]),
+                          src.shape[0], src.ctypes.data, x.data_ptr(), infos, 0.0, 0.0, 0, -1)
+    o = BatchOpts(float(tol), int(restart), int(maxit), float(d0), int(pmin), int(bool(autotune)), int(max_rhs),
+                  int(bool(fp64_judge)), int(bool(lookahead)))
+    st = lib.fb_batch_solve(arr, len(jobs), C.byref(o))
+    if st not in (FB_OK, 3, 5):
+        _check(st)
+    out = []
+    for i in range(len(jobs)):
+        infos = keep[2 * i + 1]
+        out.append({"status": arr[i].status, "setup_ms": arr[i].setup_ms, "solve_ms": arr[i].solve_ms,
+                    "order": arr[i].order, "infos": [q.as_dict() for q in infos]})
     return out
 
 

@@ -5,6 +5,9 @@
 #include <cstring>
 #include <string>
 
+#include <map>
+#include <mutex>
+
 #include "common.cuh"
 
 // implemented in the other translation units
@@ -20,6 +23,7 @@ fb_status fb_fgmres_impl(fb_op*, fb_precond*, const cd*, cd*, const fb_solver_op
 fb_status fb_fgmres_multi_impl(fb_op*, fb_precond*, const cd*, cd*, int, const fb_solver_opts*, fb_solve_info*,
                                cudaStream_t);
 fb_status fb_precond_create_impl(fb_op*, int, cudaStream_t, fb_precond**);
+fb_status fb_batch_solve_impl(fb_batch_job*, int, const fb_batch_opts*);
 void fb_precond_free(fb_precond*);
 fb_status fb_alu_peaks_impl(double*, double*, cudaStream_t);
 
@@ -28,6 +32,18 @@ void fb_count_launch(long long n) { g_launches += n; }
 
 static thread_local fb_status g_last_code = FB_OK;
 static thread_local char g_last_msg[1024] = "";
+
+fb_status fb_smem_cap(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<const void*, size_t> cap;
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& c = cap[func];
+    if (bytes <= c) return FB_OK;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return fb_fail(FB_ERR_CUDA, std::string("shared-memory opt-in: ") + cudaGetErrorString(e));
+    c = bytes;
+    return FB_OK;
+}
 
 void fb_set_error(fb_status code, const std::string& msg) {
     g_last_code = code;
@@ -519,6 +535,11 @@ fb_status fb_fgmres_solve_multi(fb_op* A, fb_precond* pc, const double* b, doubl
     if (st != FB_OK && st != FB_ERR_NOCONV && st != FB_ERR_NAN) return st;
     fb_status st2 = stage_out_finish(bytes, memspace, x, sx, s);
     return st != FB_OK ? st : st2;
+}
+
+fb_status fb_batch_solve(fb_batch_job* jobs, int njobs, const fb_batch_opts* opts) {
+    if ((!jobs && njobs > 0) || njobs < 0 || !opts) return fb_fail(FB_ERR_ARG, "bad batch arguments");
+    return fb_batch_solve_impl(jobs, njobs, opts);
 }
 
 fb_status fb_eval_field(const fb_mesh* m, double k, const double* psi_sc, const double* gamma, const double* src,

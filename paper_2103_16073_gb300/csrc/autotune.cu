@@ -58,8 +58,10 @@ void free_rcr(RcrPlan& p) {
 // times[4 * l + {0,1,2,3}] = M2L RCR, M2L tensor, M2M+L2L RCR, M2M+L2L tensor
 // (ms, -1 when not a candidate) for l = 0..L; choice[l] bit 0 = M2L on the
 // tensor cores, bit 1 = M2M/L2L into level l on the tensor cores.
-fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times, int* choice) {
+fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_out, int* choice) {
     if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;
+    double times_local[4 * (FB_MAXLEV + 1)];
+    double* times = times_out ? times_out : times_local;   // callers may pass NULL
     const fb_tree* t = op->tree;
     const int L = op->L;
     const int64_t cnt = op->lev_off[L + 1];

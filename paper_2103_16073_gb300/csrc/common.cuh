@@ -57,6 +57,11 @@ template <> __host__ __device__ __forceinline__ cf from_d<float>(cd a) { return 
 
 // --------------------------------------------------------- error state ----
 void fb_set_error(fb_status code, const std::string& msg);
+// Raises a kernel's dynamic shared-memory cap to at least `bytes`, never
+// lowering it, so launches from several host threads cannot race on the
+// attribute (thread-safe).  Call it before every launch with dynamic shared
+// memory: the default cap is 48 KB minus the kernel's static shared memory.
+fb_status fb_smem_cap(const void* func, size_t bytes);
 fb_status fb_fail(fb_status code, const std::string& msg);
 
 #define FB_CUDA(call)                                                               \
@@ -64,7 +69,8 @@ fb_status fb_fail(fb_status code, const std::string& msg);
         cudaError_t e_ = (call);                                                    \
         if (e_ != cudaSuccess) {                                                    \
             return fb_fail(e_ == cudaErrorMemoryAllocation ? FB_ERR_OOM : FB_ERR_CUDA, \
-                           std::string(#call " failed: ") + cudaGetErrorString(e_));  \
+                           std::string(#call " failed at " __FILE__ ":") +           \
+                               std::to_string(__LINE__) + ": " + cudaGetErrorString(e_)); \
         }                                                                           \
     } while (0)
 

@@ -437,8 +437,7 @@ static fb_status run_rcr(RcrPlan& pl, const RotArgs<R>& rot, const cx<R>* coax, 
     size_t smem = 0;
     FB_CHECK(rcr_tiles_for(pl, nrhs, &tiles, &ntiles, &smem));
     if (ntiles == 0) return FB_OK;
-    if (smem > 48 * 1024)
-        FB_CUDA(cudaFuncSetAttribute(k_rcr<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    FB_CHECK(fb_smem_cap((const void*)k_rcr<R>, smem));
     k_rcr<R><<<ntiles, 256, smem, s>>>(pl.tasks, tiles, rot.d, rot.ph, rot.per_dir, rot.prot, coax, pl.src_idx,
                                        pl.dst_idx, src, dst, nrhs, rstride);
     FB_LAUNCH_CHECK();
@@ -561,8 +560,7 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
     const cx<R>* locL = loc + op->lev_off[L];
     if (nrhs == 1) {
         size_t smem = sizeof(cx<R>) * (maxK + PL);
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_near_l2p<R, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        FB_CHECK(fb_smem_cap((const void*)k_near_l2p<R, 1>, smem));
         k_near_l2p<R, 1><<<nleaf, 256, smem, s>>>(PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off,
                                                   op->nf_ncol, A, V, locL, x, y, 1, n, cnt);
     } else {
@@ -570,8 +568,7 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
         int nr = std::min(nrhs, NB);
         size_t smem = sizeof(cx<R>) * (size_t)nr * (maxK + PL);
         if (smem > 227 * 1024) return fb_fail(FB_ERR_ARG, "near-field tile exceeds shared memory");
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(k_near_l2p<R, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        FB_CHECK(fb_smem_cap((const void*)k_near_l2p<R, NB>, smem));
         k_near_l2p<R, NB><<<dim3(nleaf, div_up(nrhs, NB)), 256, smem, s>>>(
             PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off, op->nf_ncol, A, V, locL, x, y, nrhs, n, cnt);
     }

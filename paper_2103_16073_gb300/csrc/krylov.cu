@@ -881,6 +881,7 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
     FB_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
     k_bj_extract<<<nleaf, 256, 0, s>>>(op->nf64, op->nf_off, op->nf_ncol, t->leaf_start, t->ucnt, t->ulist,
                                        pc->blk_off, pc->inv64);
+    FB_CHECK(fb_smem_cap((const void*)k_bj_invert, sizeof(cd) * std::max(maxn, 1)));
     k_bj_invert<<<nleaf, 256, sizeof(cd) * std::max(maxn, 1), s>>>(t->leaf_start, pc->blk_off, pc->inv64, piv, sing);
     int hs = 0;
     FB_CUDA(cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -911,6 +912,8 @@ fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, 
     int maxn = 0;
     for (int b = 0; b < nleaf; ++b) maxn = std::max(maxn, t->h_leaf_start[b + 1] - t->h_leaf_start[b]);
     dim3 g(nleaf, nrhs);
+    FB_CHECK(fb_smem_cap(pc->inv32 ? (const void*)k_bj_apply<float> : (const void*)k_bj_apply<double>,
+                         (pc->inv32 ? sizeof(cf) : sizeof(cd)) * maxn));
     if (pc->inv32) {
         k_bj_apply<float><<<g, 128, sizeof(cf) * maxn, s>>>(t->leaf_start, t->perm, pc->blk_off, pc->inv32, x, y, n);
     } else {

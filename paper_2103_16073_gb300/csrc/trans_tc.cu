@@ -435,7 +435,7 @@ fb_status fb_tc_build_groups(fb_op* op, const std::vector<TcGroup>& groups, cons
             op->T64 + jb.t_off, tk.p_out2, jb.p_in * jb.p_in, tk.nrt, tk.nkc, pl->A + tk.a_off);
     }
     FB_LAUNCH_CHECK();
-    FB_CUDA(cudaFuncSetAttribute(k_trans_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb_tc_smem_bytes()));
+    FB_CHECK(fb_smem_cap((const void*)k_trans_tc, fb_tc_smem_bytes()));
     return FB_OK;
 }
 

@@ -250,3 +250,26 @@ def paper_shoebox_counts(lx=8.0, ly=6.0, lz=3.0, max_edge=0.02):
     """Rectangle counts for the 8x6x3 m room of Sec. 4 meshed with maximum
     edge (the hypotenuse) `max_edge`: legs max_edge/sqrt(2)."""
     return shoebox_counts_for_h(lx, ly, lz, max_edge / math.sqrt(2.0))
+
+
+def lroom_sweep(nfreq=64, f_lo=100.0, f_hi=2000.0, nsrc=8, per_wavelength=8, config_index=2):
+    """Batching workload: the L-shaped room (5x4x3 m box joined to a 3x3x3 m
+    box) at `nfreq` log-spaced frequencies, each meshed with legs
+    lambda/per_wavelength (uneven N), one admittance per wall part drawn
+    uniform in [0.05, 0.5], `nsrc` seeded interior sources per frequency
+    (>= 0.3 m from every wall)."""
+    rng = seeded_rng(config_index)
+    beta_wall = rng.uniform(0.05, 0.5, size=10)
+    out = []
+    for f in np.geomspace(f_lo, f_hi, nfreq):
+        h = SOUND_SPEED / f / per_wavelength
+        verts, tris, wall = lroom_mesh(h)
+        src = []
+        while len(src) < nsrc:
+            p = np.array([8.0, 4.0, 3.0]) * rng.random(3)
+            if lroom_inside(p, 0.3)[0]:
+                src.append(p)
+        out.append(Workload(f"lroom-{f:.1f}Hz-N{tris.shape[0]}", verts, tris, wall, float(f), wavenumber(f),
+                            beta_wall[wall].astype(np.complex128), np.asarray(src), np.zeros((0, 3)),
+                            room=(8.0, 4.0, 3.0)))
+    return out
