@@ -249,6 +249,16 @@ FB_API fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y
  * the stream. */
 FB_API fb_status fb_measure_alu_peaks(double* fp32_tflops, double* fp64_tflops, void* stream);
 
+/* CUDA-graph replay: when enabled, every application of the FMM operator
+ * (or of the learned preconditioner) inside the library replays a captured
+ * graph of its kernels (one per number of right-hand sides) on staging
+ * vectors, with one copy in and one copy out per call.  Captured graphs are
+ * dropped when the translation method or autotuned forms change.  Kernels
+ * that apply the operator through a graph must not be changed concurrently.
+ * Errors: FB_ERR_ARG for NULL handles. */
+FB_API fb_status fb_operator_use_graphs(fb_op* op, int enable);
+FB_API fb_status fb_precond_use_graphs(fb_precond* pc, int enable);
+
 /* Operator applied to nrhs right-hand sides at once (Y = Op X; X, Y:
  * nrhs x N complex, rhs-major, in memspace, distinct).  The FMM kernels take
  * every right-hand side in one launch (near-field, P2M/L2P and translation

@@ -31,7 +31,7 @@ __all__ = [
     "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
     "fb_precond_create_learned", "fb_learned_params", "fb_learned_set_objective",
     "FB_LOSS_ERROR", "FB_LOSS_RESIDUAL", "fb_learned_loss_and_grad", "fb_learned_train_step",
-    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune", "fb_batch_solve",
+    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune", "fb_batch_solve", "fb_operator_use_graphs", "fb_precond_use_graphs",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -457,6 +457,20 @@ def fb_batch_solve(jobs, tol=1e-4, restart=40, maxit=3000, d0=6.0, pmin=12, auto
         out.append({"status": arr[i].status, "setup_ms": arr[i].setup_ms, "solve_ms": arr[i].solve_ms,
                     "order": arr[i].order, "infos": [q.as_dict() for q in infos]})
     return out
+
+
+lib.fb_operator_use_graphs.restype = C.c_int
+lib.fb_operator_use_graphs.argtypes = [C.c_void_p, C.c_int]
+lib.fb_precond_use_graphs.restype = C.c_int
+lib.fb_precond_use_graphs.argtypes = [C.c_void_p, C.c_int]
+
+
+def fb_operator_use_graphs(op, enable=True):
+    _check(lib.fb_operator_use_graphs(op, int(bool(enable))))
+
+
+def fb_precond_use_graphs(pc, enable=True):
+    _check(lib.fb_precond_use_graphs(pc, int(bool(enable))))
 
 
 FB_TRANS_AUTO, FB_TRANS_COMPOSED, FB_TRANS_RCR, FB_TRANS_TENSOR = 0, 1, 2, 3

@@ -91,10 +91,18 @@ static fb_status stage_out_finish(size_t bytes, int memspace, void* user, const 
     return FB_OK;
 }
 
+long long fb_launch_count() { return g_launches.load(); }
+
 fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs) {
     if (op->prec == FB_PREC_FP64_DENSE) {
         for (int r = 0; r < nrhs; ++r) FB_CHECK(fb_dense_apply(op, x + r * op->n, y + r * op->n, s));
         return FB_OK;
+    }
+    if (op->use_graphs) {
+        const int64_t e = op->n * nrhs;
+        return fb_graph_run(op->graphs, nrhs, e, e, x, y, s, [op, nrhs](const cd* gx, cd* gy, cudaStream_t st) {
+            return fb_fmm_apply(op, gx, gy, st, nullptr, nrhs);
+        });
     }
     return fb_fmm_apply(op, x, y, s, nullptr, nrhs);
 }
@@ -324,6 +332,21 @@ fb_status fb_operator_set_translation(fb_op* op, int method) {
         }
     }
     op->method = method;
+    fb_graph_free(op->graphs);
+    return FB_OK;
+}
+
+fb_status fb_operator_use_graphs(fb_op* op, int enable) {
+    if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
+    op->use_graphs = enable ? 1 : 0;
+    if (!enable) fb_graph_free(op->graphs);
+    return FB_OK;
+}
+
+fb_status fb_precond_use_graphs(fb_precond* pc, int enable) {
+    if (!pc) return fb_fail(FB_ERR_ARG, "NULL preconditioner");
+    pc->use_graphs = enable ? 1 : 0;
+    if (!enable) fb_graph_free(pc->graphs);
     return FB_OK;
 }
 
@@ -335,6 +358,7 @@ fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times,
         for (int i = 0; i < 4 * (FB_MAXLEV + 1); ++i) times[i] = -1.0;
     if (choice)
         for (int i = 0; i <= FB_MAXLEV; ++i) choice[i] = 0;
+    fb_graph_free(op->graphs);
     return fb_autotune_impl(op, nrhs, as_stream(stream), times, choice);
 }
 
@@ -412,6 +436,7 @@ void fb_operator_destroy(fb_op* op) {
     fb_fmm_destroy(op);
     dfree(op->io_x);
     dfree(op->io_y);
+    fb_graph_free(op->graphs);
     delete op;
 }
 

@@ -62,6 +62,13 @@ void fb_set_error(fb_status code, const std::string& msg);
 // attribute (thread-safe).  Call it before every launch with dynamic shared
 // memory: the default cap is 48 KB minus the kernel's static shared memory.
 fb_status fb_smem_cap(const void* func, size_t bytes);
+// CUDA-graph replay helpers (graphs.cu): `cache` is an opaque per-object
+// cache; body(x, y, s) is the work replayed (run uncaptured once, then
+// captured on x/y staging vectors of in_elems / out_elems complex entries).
+#include <functional>
+fb_status fb_graph_run(void*& cache, int key, int64_t in_elems, int64_t out_elems, const cd* x, cd* y,
+                       cudaStream_t s, const std::function<fb_status(const cd*, cd*, cudaStream_t)>& body);
+void fb_graph_free(void*& cache);
 fb_status fb_fail(fb_status code, const std::string& msg);
 
 #define FB_CUDA(call)                                                               \
@@ -315,6 +322,9 @@ struct fb_op {
     // device vectors for host-memspace calls
     cd* io_x = nullptr;
     cd* io_y = nullptr;
+    // CUDA-graph replay of the FMM matvec (fb_operator_use_graphs)
+    int use_graphs = 0;
+    void* graphs = nullptr;
 };
 
 struct LearnedNet;
@@ -327,6 +337,8 @@ struct fb_precond {
     cf* inv32 = nullptr;
     LearnedNet* net = nullptr;     // learned preconditioner (refines `base`)
     const fb_precond* base = nullptr;
+    int use_graphs = 0;            // CUDA-graph replay of the apply (fb_precond_use_graphs)
+    void* graphs = nullptr;
 };
 
 // ------------------------------------------------------ launch counting ----

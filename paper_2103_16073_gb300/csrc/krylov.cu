@@ -904,6 +904,15 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
 fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, int nrhs) {
     const int64_t n = pc->n;
     if (pc->net) {
+        if (pc->use_graphs) {
+            fb_precond* mpc = const_cast<fb_precond*>(pc);
+            for (int r = 0; r < nrhs; ++r)
+                FB_CHECK(fb_graph_run(mpc->graphs, 1, n, n, x + r * n, y + r * n, s,
+                                      [mpc](const cd* gx, cd* gy, cudaStream_t st) {
+                                          return fb_learned_forward(mpc->net, gx, gy, st);
+                                      }));
+            return FB_OK;
+        }
         for (int r = 0; r < nrhs; ++r) FB_CHECK(fb_learned_forward(pc->net, x + r * n, y + r * n, s));
         return FB_OK;
     }
@@ -926,6 +935,7 @@ fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, 
 
 void fb_precond_free(fb_precond* pc) {
     if (!pc) return;
+    fb_graph_free(pc->graphs);
     fb_learned_free(pc->net);
     dfree(pc->blk_off);
     dfree(pc->inv64);
