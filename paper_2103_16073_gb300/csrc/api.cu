@@ -100,9 +100,10 @@ fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs) 
     }
     if (op->use_graphs) {
         const int64_t e = op->n * nrhs;
-        return fb_graph_run(op->graphs, nrhs, e, e, x, y, s, [op, nrhs](const cd* gx, cd* gy, cudaStream_t st) {
-            return fb_fmm_apply(op, gx, gy, st, nullptr, nrhs);
-        });
+        return fb_graph_run(
+            op->graphs, nrhs, e, e, x, y, s,
+            [op, nrhs](const cd* gx, cd* gy, cudaStream_t st) { return fb_fmm_apply(op, gx, gy, st, nullptr, nrhs); },
+            &op->buf_gen);
     }
     return fb_fmm_apply(op, x, y, s, nullptr, nrhs);
 }

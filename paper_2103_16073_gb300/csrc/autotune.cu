@@ -77,6 +77,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
         FB_CHECK(dalloc((cf**)&op->mp, cnt * nrhs));
         FB_CHECK(dalloc((cf**)&op->loc, cnt * nrhs));
         op->exp_nrhs = nrhs;
+        op->buf_gen++;
     }
     cf* mp = (cf*)op->mp;
     cf* loc = (cf*)op->loc;

@@ -67,7 +67,8 @@ fb_status fb_smem_cap(const void* func, size_t bytes);
 // captured on x/y staging vectors of in_elems / out_elems complex entries).
 #include <functional>
 fb_status fb_graph_run(void*& cache, int key, int64_t in_elems, int64_t out_elems, const cd* x, cd* y,
-                       cudaStream_t s, const std::function<fb_status(const cd*, cd*, cudaStream_t)>& body);
+                       cudaStream_t s, const std::function<fb_status(const cd*, cd*, cudaStream_t)>& body,
+                       const long long* gen = nullptr);
 void fb_graph_free(void*& cache);
 fb_status fb_fail(fb_status code, const std::string& msg);
 
@@ -325,6 +326,7 @@ struct fb_op {
     // CUDA-graph replay of the FMM matvec (fb_operator_use_graphs)
     int use_graphs = 0;
     void* graphs = nullptr;
+    long long buf_gen = 0;                   // bumped when a buffer a graph may capture is reallocated
 };
 
 struct LearnedNet;
@@ -369,6 +371,7 @@ fb_status fb_compose_all(fb_op* op, cudaStream_t s);
 fb_status fb_learned_alloc(LearnedNet*& net, const fb_op* op, const fb_precond* bj, cudaStream_t s);
 void fb_learned_free(LearnedNet*& net);
 fb_status fb_learned_forward(LearnedNet* net, const cd* v, cd* z, cudaStream_t s);
+fb_status fb_learned_apply(LearnedNet* net, const cd* v, cd* z, cudaStream_t s);
 fb_status fb_learned_loss_grad(LearnedNet* net, const cd* R, const cd* E, int npairs, double* loss, cudaStream_t s);
 fb_status fb_learned_adam_step(LearnedNet* net, double lr, cudaStream_t s);
 fb_status fb_learned_init(LearnedNet* net, uint64_t seed, cudaStream_t s);

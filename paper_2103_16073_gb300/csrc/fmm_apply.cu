@@ -500,6 +500,7 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
         FB_CHECK(dalloc((cx<R>**)&op->mp, cnt * nrhs));
         FB_CHECK(dalloc((cx<R>**)&op->loc, cnt * nrhs));
         op->exp_nrhs = nrhs;
+        op->buf_gen++;   // captured graphs of this operator refer to the old buffers
     }
     cx<R>* mp = scratch ? (cx<R>*)scratch : (cx<R>*)op->mp;
     cx<R>* loc = scratch ? (cx<R>*)scratch + cnt * nrhs : (cx<R>*)op->loc;

@@ -6,7 +6,9 @@
 // pointers are fixed); a replay copies the caller's input in, launches the
 // graph and copies the result out.  One graph per number of right-hand
 // sides; the body runs once uncaptured first so that every lazily built
-// buffer or tile list exists before capture.  Capture uses a private
+// buffer or tile list exists before capture.  An owner that reallocates a
+// buffer a graph may have captured bumps its generation counter; graphs of
+// an older generation are captured again before their next replay.  Capture uses a private
 // stream; replays go to the caller's stream.
 #include <atomic>
 #include <functional>
@@ -20,6 +22,7 @@ struct GraphEntry {
     cd* gx = nullptr;
     cd* gy = nullptr;
     long long kernels = 0;
+    long long gen = -1;           // owner's buffer generation at capture
 };
 struct GraphCache {
     std::map<int, GraphEntry> m;
@@ -42,11 +45,27 @@ void fb_graph_free(void*& cache) {
     cache = nullptr;
 }
 
+static void drop_entry(GraphEntry& e) {
+    if (e.exec) cudaGraphExecDestroy(e.exec);
+    if (e.graph) cudaGraphDestroy(e.graph);
+    dfree(e.gx);
+    dfree(e.gy);
+    e = GraphEntry{};
+}
+
 fb_status fb_graph_run(void*& cache, int key, int64_t in_elems, int64_t out_elems, const cd* x, cd* y,
-                       cudaStream_t s, const std::function<fb_status(const cd*, cd*, cudaStream_t)>& body) {
+                       cudaStream_t s, const std::function<fb_status(const cd*, cd*, cudaStream_t)>& body,
+                       const long long* gen) {
     if (!cache) cache = new GraphCache();
     GraphCache* gc = (GraphCache*)cache;
     auto it = gc->m.find(key);
+    if (it != gc->m.end() && gen && it->second.gen != *gen) {
+        // the owner reallocated buffers the graph captured: capture again
+        FB_CUDA(cudaStreamSynchronize(s));
+        drop_entry(it->second);
+        gc->m.erase(it);
+        it = gc->m.end();
+    }
     if (it == gc->m.end()) {
         GraphEntry e;
         FB_CHECK(dalloc(&e.gx, in_elems));
@@ -71,6 +90,7 @@ fb_status fb_graph_run(void*& cache, int key, int64_t in_elems, int64_t out_elem
         }
         e.graph = g;
         e.kernels = captured;
+        e.gen = gen ? *gen : 0;   // read after the uncaptured run, which may have grown buffers
         cudaError_t ie = cudaGraphInstantiate(&e.exec, g, 0);
         if (ie != cudaSuccess) {
             cudaGraphDestroy(g);

@@ -909,11 +909,11 @@ fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, 
             for (int r = 0; r < nrhs; ++r)
                 FB_CHECK(fb_graph_run(mpc->graphs, 1, n, n, x + r * n, y + r * n, s,
                                       [mpc](const cd* gx, cd* gy, cudaStream_t st) {
-                                          return fb_learned_forward(mpc->net, gx, gy, st);
+                                          return fb_learned_apply(mpc->net, gx, gy, st);
                                       }));
             return FB_OK;
         }
-        for (int r = 0; r < nrhs; ++r) FB_CHECK(fb_learned_forward(pc->net, x + r * n, y + r * n, s));
+        for (int r = 0; r < nrhs; ++r) FB_CHECK(fb_learned_apply(pc->net, x + r * n, y + r * n, s));
         return FB_OK;
     }
     const fb_tree* t = pc->op->tree;

@@ -347,6 +347,253 @@ __global__ void k_adam(float* w, const float* gr, float* m, float* v, int64_t n,
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// ------------------------------------------------ fused inference path ----
+// Applying the trained network inside FGMRES needs no activations for a
+// backward pass, so the element-level layers run fused: pass 1 computes the
+// element encoder H0 and its leaf means in one CTA per leaf; pass 2
+// recomputes H0 per 64-element tile, joins it with the leaf's down-sweep
+// feature, runs the W_h layer on the tensor cores (mma.sync BF16, FP32
+// accumulation) and the W_o layer and the output z = u + s ph O in
+// registers.  Operands are rounded to BF16 where the training path rounds
+// them, so both evaluate the same network.
+__device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+__device__ __forceinline__ void elem_features(const Geom& g, const int32_t* perm, const cd* v, const cd* u,
+                                              const double* st, int64_t n, int64_t pos, float f[NF]) {
+    double s = sqrt(st[0] / (double)n);
+    double inv = s > 0.0 ? 1.0 / s : 0.0;
+    cd ph = input_phase(st);
+    cd rot = mk(ph.re * inv, -ph.im * inv);
+    int64_t e = perm[pos];
+    cd vv = v[e] * rot, uu = u[e] * rot;
+    f[0] = bfr((float)vv.re);
+    f[1] = bfr((float)vv.im);
+    f[2] = bfr((float)uu.re);
+    f[3] = bfr((float)uu.im);
+    f[4] = bfr((float)g.nx[e]);
+    f[5] = bfr((float)g.ny[e]);
+    f[6] = bfr((float)g.nz[e]);
+    f[7] = 1.f;
+}
+
+// G_L[leaf][c] = mean over the leaf's elements of silu(F W0 + b0)[c]; one CTA
+// of 64 threads (one per feature column) per leaf.
+__global__ void __launch_bounds__(64) k_inf_pass1(Geom g, const int32_t* perm, const int32_t* leaf_start,
+                                                  const cd* v, const cd* u, const double* st, int64_t n,
+                                                  const float* W0, const float* b0, float* GL) {
+    int leaf = blockIdx.x, c = threadIdx.x;
+    int a = leaf_start[leaf], b = leaf_start[leaf + 1];
+    float w[NF];
+#pragma unroll
+    for (int k = 0; k < NF; ++k) w[k] = bfr(W0[k * HW + c]);
+    float bias = b0[c];
+    __shared__ float fs[64][NF];
+    float acc = 0.f;
+    for (int e0 = a; e0 < b; e0 += 64) {
+        int cnt = min(64, b - e0);
+        __syncthreads();
+        if (c < cnt) {
+            float f[NF];
+            elem_features(g, perm, v, u, st, n, e0 + c, f);
+#pragma unroll
+            for (int k = 0; k < NF; ++k) fs[c][k] = f[k];
+        }
+        __syncthreads();
+        for (int i = 0; i < cnt; ++i) {
+            float h = bias;
+#pragma unroll
+            for (int k = 0; k < NF; ++k) h = fmaf(fs[i][k], w[k], h);
+            acc += silu(h);
+        }
+    }
+    GL[(int64_t)leaf * HW + c] = b > a ? acc / (float)(b - a) : 0.f;
+}
+
+// 64 elements per CTA (tree order), 128 threads = 4 warps x 16 rows.
+__global__ void __launch_bounds__(128) k_inf_pass2(Geom g, const int32_t* perm, const int32_t* leaf_of,
+                                                   const cd* v, const cd* u, const double* st, int64_t n,
+                                                   const float* W0, const float* b0, const float* DL,
+                                                   const float* Wh, const float* bh, const float* Wo,
+                                                   const float* bo, cd* z) {
+    __shared__ uint32_t Es[64][HW + 4];        // [row][k pair]: 128 bf16 per row (+pad)
+    __shared__ uint32_t Ws[HW][HW + 4];        // W_h as [col n][k pair]
+    __shared__ float fs[64][NF];
+    __shared__ float w0s[NF][HW];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t r0 = (int64_t)blockIdx.x * 64;
+    for (int i = tid; i < NF * HW; i += blockDim.x) w0s[i / HW][i % HW] = bfr(W0[i]);
+    // W_h [128 x 64] (in x out) -> Ws[n][kp] = (W[2kp][n], W[2kp+1][n])
+    for (int i = tid; i < HW * HW; i += blockDim.x) {   // coalesced reads along n
+        int kp = i / HW, nn = i % HW;
+        Ws[nn][kp] = pack_bf16(Wh[(2 * kp) * HW + nn], Wh[(2 * kp + 1) * HW + nn]);
+    }
+    if (tid < 64) {
+        int64_t pos = r0 + tid;
+        float f[NF];
+        if (pos < n) elem_features(g, perm, v, u, st, n, pos, f);
+        else
+            for (int k = 0; k < NF; ++k) f[k] = 0.f;
+        for (int k = 0; k < NF; ++k) fs[tid][k] = f[k];
+    }
+    __syncthreads();
+    // E = [H0, D_L(leaf)] as bf16 pairs
+    for (int i = tid; i < 64 * HW; i += blockDim.x) {
+        int r = i / HW, kp = i % HW;
+        int64_t pos = r0 + r;
+        float x0 = 0.f, x1 = 0.f;
+        if (pos < n) {
+            if (kp < HW / 2) {
+                int c0 = 2 * kp;
+                float h0 = b0[c0], h1 = b0[c0 + 1];
+#pragma unroll
+                for (int k = 0; k < NF; ++k) {
+                    h0 = fmaf(fs[r][k], w0s[k][c0], h0);
+                    h1 = fmaf(fs[r][k], w0s[k][c0 + 1], h1);
+                }
+                x0 = silu(h0);
+                x1 = silu(h1);
+            } else {
+                const float* d = DL + (int64_t)leaf_of[pos] * HW + 2 * (kp - HW / 2);
+                x0 = d[0];
+                x1 = d[1];
+            }
+        }
+        Es[r][kp] = pack_bf16(x0, x1);
+    }
+    __syncthreads();
+    // H1 = silu(E W_h + b_h): warp rows [16 warp, +16), 64 columns (8 n-tiles)
+    float acc[8][4];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
+    const int row = warp * 16 + (lane >> 2), kq = lane & 3;
+#pragma unroll
+    for (int k0 = 0; k0 < 2 * HW; k0 += 16) {
+        int kb = k0 / 2;
+        uint32_t a0 = Es[row][kb + kq], a1 = Es[row + 8][kb + kq], a2 = Es[row][kb + kq + 4],
+                 a3 = Es[row + 8][kb + kq + 4];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int col = t * 8 + (lane >> 2);
+            uint32_t b0r = Ws[col][kb + kq], b1r = Ws[col][kb + kq + 4];
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+f"(acc[t][0]), "+f"(acc[t][1]), "+f"(acc[t][2]), "+f"(acc[t][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0r), "r"(b1r));
+        }
+    }
+    // O = H1 W_o + b_o: each lane holds rows (lane>>2) and +8, columns t*8 + 2*(lane&3) + {0,1}
+    float o[2][2] = {{0.f, 0.f}, {0.f, 0.f}};   // [row half][re/im]
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int col = t * 8 + (lane & 3) * 2 + (q & 1);
+            float h = bfr(silu(acc[t][q] + bh[col]));
+            int half = q >> 1;
+            o[half][0] = fmaf(h, bfr(Wo[col * 2]), o[half][0]);
+            o[half][1] = fmaf(h, bfr(Wo[col * 2 + 1]), o[half][1]);
+        }
+#pragma unroll
+    for (int half = 0; half < 2; ++half)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            o[half][j] += __shfl_xor_sync(0xffffffffu, o[half][j], 1);
+            o[half][j] += __shfl_xor_sync(0xffffffffu, o[half][j], 2);
+        }
+    if ((lane & 3) == 0) {
+        double s = sqrt(st[0] / (double)n);
+        cd ph = input_phase(st);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            int64_t pos = r0 + row + half * 8;
+            if (pos >= n) continue;
+            int64_t e = perm[pos];
+            cd oo = mk(s * (double)(o[half][0] + bo[0]), s * (double)(o[half][1] + bo[1])) * ph;
+            z[e] = u[e] + oo;
+        }
+    }
+}
+
+// One coarse layer of the inference path, fused: rows b of a level (64 per
+// CTA) gather their input, Y[b] = silu(X[b] W + bias), W (K x 64, K = 64 or
+// 128) staged once per CTA as BF16, X rounded to BF16, FP32 accumulation.
+//   mode 0 (up-sweep):   X[b] = mean of Gc[c], c in [cs[b], cs[b+1])        (K = 64)
+//   mode 1 (down-sweep): X[b] = [G[b], Dp[parent[b]]]                        (K = 128)
+template <int K>
+__global__ void __launch_bounds__(128) k_inf_layer(int mode, int M, const float* __restrict__ G,
+                                                   const int32_t* __restrict__ idx, const float* __restrict__ Dp,
+                                                   const float* __restrict__ W, const float* __restrict__ bias,
+                                                   float* __restrict__ Y) {
+    constexpr int KP = K / 2;
+    __shared__ uint32_t Xs[64][KP + 4];
+    __shared__ uint32_t Ws[HW][KP + 4];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b0 = blockIdx.x * 64;
+    for (int i = tid; i < KP * HW; i += blockDim.x) {
+        int kp = i / HW, nn = i % HW;
+        Ws[nn][kp] = pack_bf16(W[(2 * kp) * HW + nn], W[(2 * kp + 1) * HW + nn]);
+    }
+    for (int i = tid; i < 64 * KP; i += blockDim.x) {
+        int r = i / KP, kp = i % KP;
+        int b = b0 + r;
+        float x0 = 0.f, x1 = 0.f;
+        if (b < M) {
+            if (mode == 0) {
+                int c0 = idx[b], c1 = idx[b + 1];
+                for (int c = c0; c < c1; ++c) {
+                    x0 += G[(int64_t)c * HW + 2 * kp];
+                    x1 += G[(int64_t)c * HW + 2 * kp + 1];
+                }
+                float inv = c1 > c0 ? 1.f / (float)(c1 - c0) : 0.f;
+                x0 *= inv;
+                x1 *= inv;
+            } else if (kp < HW / 2) {
+                x0 = G[(int64_t)b * HW + 2 * kp];
+                x1 = G[(int64_t)b * HW + 2 * kp + 1];
+            } else {
+                const float* d = Dp + (int64_t)idx[b] * HW + 2 * (kp - HW / 2);
+                x0 = d[0];
+                x1 = d[1];
+            }
+        }
+        Xs[r][kp] = pack_bf16(x0, x1);
+    }
+    __syncthreads();
+    float acc[8][4];
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
+    const int row = warp * 16 + (lane >> 2), kq = lane & 3;
+#pragma unroll
+    for (int k0 = 0; k0 < K; k0 += 16) {
+        int kb = k0 / 2;
+        uint32_t a0 = Xs[row][kb + kq], a1 = Xs[row + 8][kb + kq], a2 = Xs[row][kb + kq + 4],
+                 a3 = Xs[row + 8][kb + kq + 4];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int col = t * 8 + (lane >> 2);
+            uint32_t b0r = Ws[col][kb + kq], b1r = Ws[col][kb + kq + 4];
+            asm volatile(
+                "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};\n"
+                : "+f"(acc[t][0]), "+f"(acc[t][1]), "+f"(acc[t][2]), "+f"(acc[t][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0r), "r"(b1r));
+        }
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int b = b0 + row + (q >> 1) * 8;
+            int col = t * 8 + (lane & 3) * 2 + (q & 1);
+            if (b < M) Y[(int64_t)b * HW + col] = silu(acc[t][q] + bias[col]);
+        }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host ----
@@ -548,6 +795,44 @@ fb_status fb_learned_forward(LearnedNet* net, const cd* v, cd* z, cudaStream_t s
     gemm(s, net->E, 2 * HW, 1, w + net->oWh, HW, 1, net->H1, HW, 1, (int)n, HW, 2 * HW, w + net->obh, net->preh, 1);
     gemm(s, net->H1, HW, 1, w + net->oWo, 2, 1, net->O, 2, 1, (int)n, 2, HW, w + net->obo, nullptr, 0);
     k_output<<<div_up(n, 256), 256, 0, s>>>(t->perm, net->u, net->O, net->scal, n, z);
+    fb_count_launch();
+    FB_LAUNCH_CHECK();
+    return FB_OK;
+}
+
+// Inference forward (no stored activations): fused element passes around the
+// coarse up/down sweeps.
+fb_status fb_learned_apply(LearnedNet* net, const cd* v, cd* z, cudaStream_t s) {
+    const fb_tree* t = net->op->tree;
+    const Geom& g = net->op->mesh->g;
+    int L = net->L, Ltop = L - net->depth;
+    int64_t n = net->n;
+    int nleaf = t->nbox[L];
+    const float* w = net->w;
+    FB_CHECK(fb_pc_apply(net->bj, v, net->u, s));
+    FB_CUDA(cudaMemsetAsync(net->scal, 0, 8 * sizeof(double), s));
+    k_stats<<<std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(v, n, net->scal);
+    k_inf_pass1<<<nleaf, 64, 0, s>>>(g, t->perm, t->leaf_start, v, net->u, net->scal, n, w + net->oW0,
+                                     w + net->ob0, net->G[L]);
+    fb_count_launch(2);
+    for (int l = L - 1, k = 0; l >= Ltop; --l, ++k) {
+        int nb = t->nbox[l];
+        k_inf_layer<HW><<<div_up(nb, 64), 128, 0, s>>>(0, nb, net->G[l + 1], net->child_start[l], nullptr,
+                                                       w + net->oWu[k], w + net->obu[k], net->G[l]);
+        fb_count_launch();
+    }
+    // D_top = G_top: the first down-sweep layer reads G_top as its parent feature
+    const float* Dprev = net->G[Ltop];
+    for (int l = Ltop + 1, k = 0; l <= L; ++l, ++k) {
+        int nb = t->nbox[l];
+        k_inf_layer<2 * HW><<<div_up(nb, 64), 128, 0, s>>>(1, nb, net->G[l], t->parent[l], Dprev,
+                                                           w + net->oWd[k], w + net->obd[k], net->D[l]);
+        fb_count_launch();
+        Dprev = net->D[l];
+    }
+    k_inf_pass2<<<div_up(n, 64), 128, 0, s>>>(g, t->perm, net->leaf_of, v, net->u, net->scal, n, w + net->oW0,
+                                             w + net->ob0, Dprev, w + net->oWh, w + net->obh, w + net->oWo,
+                                             w + net->obo, z);
     fb_count_launch();
     FB_LAUNCH_CHECK();
     return FB_OK;

@@ -469,6 +469,7 @@ fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t 
             FB_CHECK(dalloc(&pl->plane_hi, pl->plane_floats * nrhs));
             FB_CHECK(dalloc(&pl->plane_lo, pl->plane_floats * nrhs));
             pl->plane_nrhs = nrhs;
+            op->buf_gen++;   // captured graphs of this operator refer to the old planes
         }
         auto it = pl->multi.find(nrhs);
         if (it == pl->multi.end()) {

@@ -133,3 +133,33 @@ def test_block_jacobi_fallback_on_bad_network(small):
         assert torch.isfinite(torch.view_as_real(x)).all()
     finally:
         fb.fb_precond_destroy(pc)
+
+
+def test_inference_apply_matches_reference(small):
+    """The fused inference path used inside FGMRES (fb_precond_apply) against
+    the FP64 reference network on the same weights and input."""
+    from oracle import learned
+    from oracle.octree import Octree
+    wl, mesh, tree, A, bj = small
+    pc = fb.fb_precond_create_learned(A, bj)
+    try:
+        _, total = learned.layout()
+        rng = np.random.default_rng(8)
+        theta = (rng.standard_normal(total) * 0.15).astype(np.float32)
+        fb.fb_learned_params(pc, theta)
+        v = seeded_vector(wl.n, 77)
+        z = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
+        fb.fb_precond_apply(pc, torch.tensor(v, device="cuda"), z)
+        om = oracle_mesh("small")
+        el = om.el
+        T = learned.TreeInfo(Octree(np.concatenate([el.v0, el.v1, el.v2]), el.centroid, om.rc, 64))
+        Ad = oracle_dense("small")["A"]
+        u = learned.block_jacobi(lambda i, j: Ad[np.ix_(i, j)], T, v)
+        zo, _ = learned.forward(theta.astype(np.float64), T, v, u, el.normal)
+        # the network's correction z - u carries the BF16 error; u itself is exact to FP32
+        err = rel(z.cpu().numpy() - u, zo - u)
+        print(f"inference correction rel err {err:.2e}; total {rel(z.cpu().numpy(), zo):.2e}")
+        assert err < 2e-2
+        assert rel(z.cpu().numpy(), zo) < 5e-3
+    finally:
+        fb.fb_precond_destroy(pc)

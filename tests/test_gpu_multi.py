@@ -128,6 +128,14 @@ def test_graph_replay_matches(setup):
             for r in range(2):
                 assert rel(Yg[r].cpu().numpy(), Yd[r].cpu().numpy()) < 1e-6
             assert rel(y1g.cpu().numpy(), y1d.cpu().numpy()) < 1e-6
+        # more right-hand sides than ever before grow the expansion buffers;
+        # the graphs captured on the old buffers must be captured again
+        X9 = torch.tensor(np.stack([seeded_vector(wl.n, 600 + r) for r in range(9)]), device="cuda")
+        Y9 = torch.empty_like(X9)
+        fb.fb_operator_apply_multi(A, X9, Y9)
+        y1g = torch.empty_like(X[0])
+        fb.fb_operator_apply(A, X[0].contiguous(), y1g)
+        assert rel(y1g.cpu().numpy(), y1d.cpu().numpy()) < 1e-6
         bj = fb.fb_precond_create(A, fb.FB_PC_BLOCK_JACOBI)
         pcl = fb.fb_precond_create_learned(A, bj)
         z0 = torch.empty_like(X[0])
