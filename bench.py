@@ -109,11 +109,28 @@ def dist_env():
     return ws, rank, local
 
 
-def build_problem(fb, W, torch, rank):
+def rank_source(W, wl, rank):
+    """Source position solved by `rank`: rank 0 the workload's own monopole,
+    every other rank its own seeded position (independent solves, weak scaling)."""
+    if rank == 0:
+        return np.asarray(wl.sources[0], dtype=np.float64)
+    rng = W.seeded_rng(100 + rank)
+    return W.uniform_points_in_box(rng, [0, 0, 0], list(wl.room), 1, 0.25)[0]
+
+
+def reduce_max_ms(ms, dist, device):
+    """Max over ranks of a rank-local time (the job's wall time is its slowest rank)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def build_problem(fb, W, torch, rank, forms=""):
     wl = W.cfg_1khz()
-    if rank > 0:   # each rank solves its own seeded source position
-        rng = W.seeded_rng(100 + rank)
-        wl.sources = W.uniform_points_in_box(rng, [0, 0, 0], list(wl.room), 1, 0.25)
+    wl.sources = rank_source(W, wl, rank)[None, :]
     mesh = fb.fb_mesh_create(wl.verts, wl.tris)
     fb.fb_mesh_set_admittance(mesh, wl.beta)
     tree = fb.fb_tree_build(mesh, 64)
@@ -122,8 +139,14 @@ def build_problem(fb, W, torch, rank):
     L64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_L, fb.FB_PREC_FP64_FMM, 6.0, 12)
     pc32 = fb.fb_precond_create(A32, fb.FB_PC_BLOCK_JACOBI)
     pc64 = fb.fb_precond_create(A64, fb.FB_PC_BLOCK_JACOBI)
-    # per-level translation forms timed on the device, then graph replay of the matvecs
-    tune = fb.fb_operator_autotune(A32, 1)
+    # per-level translation forms timed on the device (or a saved choice, e.g.
+    # under a profiler, whose serialisation would distort the timing), then
+    # graph replay of the matvecs
+    if forms:
+        fb.fb_operator_set_forms(A32, [int(v) for v in forms.split(",")])
+        tune = {"fixed_forms": forms}
+    else:
+        tune = fb.fb_operator_autotune(A32, 1)
     for op in (A32, A64):
         fb.fb_operator_use_graphs(op, True)
     g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
@@ -215,44 +238,75 @@ def rcr_flops(p_out, p_in):
     return 8.0 * (rot + coax)
 
 
-def roofline(fb, op, tree, phases, pk, fp32_peak):
-    """Roofline of the dominant kernel of one mixed matvec (largest phase)."""
-    L, p, tc, pairs, nb = level_counts(fb, op, tree)
-    cand = {k: v for k, v in phases.items() if k != "total"}
-    dom = max(cand, key=cand.get)
-    t = cand[dom] / 1e3
-    if dom == "m2l_tc":
-        alg = sum(float(pairs[l]) * rcr_flops(p[l], p[l]) for l in range(2, L + 1) if tc[l])
-        execd = 0.0
-        for l in range(2, L + 1):
-            if tc[l]:
-                P2 = 2 * p[l] ** 2
-                rows = -(-P2 // 128) * 128
-                kk = -(-P2 // 16) * 16
-                execd += float(pairs[l]) * rows * kk * 2.0 * 3.0
-        # TF32 tensor peak from the measured BF16 peak x nominal TF32/BF16 ratio;
-        # 3 split passes, and one complex MAC (8 algorithmic flops) = 4 real MACs
-        tf32 = float(pk.get("bf16_tflops", 1990.0)) * (1.1 / 2.25)
-        peak = tf32 / 3.0
-        return {"kernel": "k_trans_tc (M2L, tcgen05 3xTF32)", "bound": "tensor",
-                "achieved": round(alg / t / 1e12, 3), "peak": round(peak, 1), "unit": "TFLOP/s",
-                "frac": round(alg / t / 1e12 / peak, 4), "traffic": None,
-                "peak_kind": "measured BF16 burst x 1.1/2.25 (TF32) / 3 passes, of measured",
-                "algorithmic_flops_per_launch": alg, "executed_tensor_flops_per_launch": execd,
-                "executed_tensor_tflops": round(execd / t / 1e12, 1), "launch_ms": round(cand[dom], 4)}
-    if dom in ("m2l", "m2m", "l2l"):
-        if dom == "m2l":
-            alg = sum(float(pairs[l]) * rcr_flops(p[l], p[l]) for l in range(2, L + 1) if not tc[l])
-        elif dom == "m2m":
-            alg = sum(float(nb[l]) * rcr_flops(p[l - 1], p[l]) for l in range(3, L + 1))
-        else:
-            alg = sum(float(nb[l]) * rcr_flops(p[l], p[l - 1]) for l in range(3, L + 1))
-        return {"kernel": f"k_rcr<float> ({dom.upper()})", "bound": "alu", "achieved": round(alg / t / 1e12, 3),
-                "peak": round(fp32_peak, 1), "unit": "TFLOP/s", "frac": round(alg / t / 1e12 / fp32_peak, 4),
-                "traffic": None, "peak_kind": "FP32 FMA throughput measured by fb_measure_alu_peaks",
-                "algorithmic_flops_per_launch": alg, "launch_ms": round(cand[dom], 4)}
-    return {"kernel": dom, "bound": "hbm", "achieved": None, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
-            "frac": None, "traffic": None, "launch_ms": round(cand[dom], 4)}
+def roofline(fb, A32, tree, ph32, ph64, iters, true_mv, pk, fp32_peak, fp64_peak):
+    """Rooflines of the three translation kernels of a solve and the dominant
+    one (largest estimated device time per step: per-launch CUDA-event phase
+    times x launches per step).  Algorithmic flops are the RCR counts of the
+    translations each launch performs (rcr_flops)."""
+    L, p, tc, pairs, nb = level_counts(fb, A32, tree)
+    t_rcr = 0.0
+    # k_rcr<double>: the FP64 operator's M2L (all levels) in the true residual
+    alg64 = sum(float(pairs[l]) * rcr_flops(p[l], p[l]) for l in range(2, L + 1))
+    t64 = ph64["m2l"] / 1e3
+    # k_rcr<float>: M2L of the levels not on the tensor cores, per Krylov matvec
+    alg32 = sum(float(pairs[l]) * rcr_flops(p[l], p[l]) for l in range(2, L + 1) if not tc[l])
+    t32 = ph32["m2l"] / 1e3
+    # k_trans_tc: M2L of the tensor-core levels (3xTF32), per Krylov matvec
+    algtc = sum(float(pairs[l]) * rcr_flops(p[l], p[l]) for l in range(2, L + 1) if tc[l])
+    ttc = ph32["m2l_tc"] / 1e3
+    execd = 0.0
+    for l in range(2, L + 1):
+        if tc[l]:
+            P2 = 2 * p[l] ** 2
+            execd += float(pairs[l]) * (-(-P2 // 128) * 128) * (-(-P2 // 16) * 16) * 2.0 * 3.0
+    # TF32 tensor peak from the measured BF16 peak x nominal TF32/BF16 ratio; 3 split passes
+    tf32 = float(pk.get("bf16_tflops", 1990.0)) * (1.1 / 2.25)
+    kern = {
+        "k_rcr<double>": {"what": "M2L of the FP64 operator (true residual), all levels", "bound": "alu",
+                          "launch_ms": t64 * 1e3, "per_step_ms": (ph64["m2l"] + ph64["m2m"] + ph64["l2l"]) * true_mv,
+                          "alg": alg64, "peak": fp64_peak,
+                          "peak_kind": "FP64 FMA throughput measured by fb_measure_alu_peaks"},
+        "k_rcr<float>": {"what": "M2L of the mixed operator, RCR levels", "bound": "alu", "launch_ms": t32 * 1e3,
+                         "per_step_ms": (ph32["m2l"] + ph32["m2m"] + ph32["l2l"]) * iters, "alg": alg32,
+                         "peak": fp32_peak, "peak_kind": "FP32 FMA throughput measured by fb_measure_alu_peaks"},
+        "k_trans_tc": {"what": "M2L of the mixed operator, tensor-core levels (tcgen05 3xTF32)", "bound": "tensor",
+                       "launch_ms": ttc * 1e3, "per_step_ms": ph32["m2l_tc"] * iters, "alg": algtc,
+                       "peak": tf32 / 3.0,
+                       "peak_kind": "measured BF16 burst x 1.1/2.25 (TF32) / 3 split passes, of measured"},
+    }
+    out = {}
+    for name, k in kern.items():
+        t = k["launch_ms"] / 1e3
+        ach = k["alg"] / t / 1e12 if t > 0 and k["alg"] > 0 else 0.0
+        out[name] = {"what": k["what"], "bound": k["bound"], "achieved": round(ach, 3), "peak": round(k["peak"], 3),
+                     "unit": "TFLOP/s", "frac": round(ach / k["peak"], 4) if k["peak"] else None,
+                     "launch_ms": round(k["launch_ms"], 4), "est_ms_per_step": round(k["per_step_ms"], 3),
+                     "algorithmic_flops_per_launch": k["alg"], "peak_kind": k["peak_kind"]}
+    out["k_trans_tc"]["executed_tensor_flops_per_launch"] = execd
+    out["k_trans_tc"]["executed_tensor_tflops"] = round(execd / ttc / 1e12, 1) if ttc > 0 else None
+    dom = max(out, key=lambda k: out[k]["est_ms_per_step"])
+    d = out[dom]
+    rf = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
+          "frac": d["frac"], "traffic": traffic_for(dom), "peak_kind": d["peak_kind"],
+          "algorithmic_flops_per_launch": d["algorithmic_flops_per_launch"], "launch_ms": d["launch_ms"],
+          "what": d["what"]}
+    return rf, out
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when the kernel source changed since the counters were taken."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path)).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != d["sha256"]:
+        return None
+    return d["dram_bytes_per_launch"]
 
 
 def run_ours(args):
@@ -266,7 +320,7 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
-    P = build_problem(fb, W, torch, rank)
+    P = build_problem(fb, W, torch, rank, args.forms)
     wl = P["wl"]
     n = wl.n
     stream = torch.cuda.current_stream()
@@ -307,11 +361,8 @@ def run_ours(args):
         barrier()
         torch.cuda.nvtx.range_pop()
     launches = fb.fb_kernel_launches() - launches0
-    ms_total = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = reduce_max_ms(e0.elapsed_time(e1), dist, "cuda" if dist is not None and
+                             dist.get_backend() == "nccl" else "cpu")
     ms_step = ms_total / args.steps
     iters = statistics.mean(i["iters"] for i in infos)
     relres = max(i["true_relres"] for i in infos)
@@ -409,7 +460,8 @@ def run_ours(args):
     e2e_s = statistics.median(e2e_t)
 
     fp32_peak, fp64_peak = fb.fb_measure_alu_peaks()
-    rf = roofline(fb, P["A32"], P["tree"], ph, pk, fp32_peak)
+    rf, kernels = roofline(fb, P["A32"], P["tree"], ph, ph64, iters, res_true_matvecs(infos), pk, fp32_peak,
+                           fp64_peak)
     res = {
         "metric": METRIC,
         "value": round(ws / (ms_step / 1e3), 4),
@@ -456,6 +508,7 @@ def run_ours(args):
                 "d2h_bytes_per_step": 16 * n},
         "gpu_launches": int(launches),
         "roofline": rf,
+        "kernels": kernels,
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
@@ -533,6 +586,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--precond", default="learned", choices=["learned", "bj"])
+    ap.add_argument("--forms", default="", help="fixed per-level translation forms instead of autotuning "
+                                                "(comma-separated choice ints by level, as fb_operator_set_forms)")
     ap.add_argument("--train-sources", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=200)
     ap.add_argument("--ref-matvecs", type=int, default=60,

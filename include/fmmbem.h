@@ -279,6 +279,12 @@ FB_API fb_status fb_precond_use_graphs(fb_precond* pc, int enable);
  * the tensor cores, bit 1 = M2M/L2L into level l on the tensor cores.
  * FP64 operators (RCR only) are left unchanged.  Errors: FB_ERR_ARG. */
 FB_API fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times, int* choice);
+
+/* Installs a per-level choice in the format the autotuner returns (13 ints,
+ * bit 0: M2L of level l on the tensor cores, bit 1: M2M/L2L into level l on
+ * the tensor cores), so that a tuned configuration can be saved and restored
+ * without timing.  Mixed-precision FMM operators only.  Errors: FB_ERR_ARG. */
+FB_API fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream);
 FB_API fb_status fb_operator_apply_multi(fb_op* op, const double* x, double* y, int nrhs, int memspace,
                                          void* stream);
 

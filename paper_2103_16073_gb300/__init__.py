@@ -31,7 +31,7 @@ __all__ = [
     "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
     "fb_precond_create_learned", "fb_learned_params", "fb_learned_set_objective",
     "FB_LOSS_ERROR", "FB_LOSS_RESIDUAL", "fb_learned_loss_and_grad", "fb_learned_train_step",
-    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune", "fb_batch_solve", "fb_operator_use_graphs", "fb_precond_use_graphs",
+    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune", "fb_operator_set_forms", "fb_batch_solve", "fb_operator_use_graphs", "fb_precond_use_graphs",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -471,6 +471,22 @@ def fb_operator_use_graphs(op, enable=True):
 
 def fb_precond_use_graphs(pc, enable=True):
     _check(lib.fb_precond_use_graphs(pc, int(bool(enable))))
+
+
+lib.fb_operator_set_forms.restype = C.c_int
+lib.fb_operator_set_forms.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
+
+
+def fb_operator_set_forms(op, forms, stream=None):
+    """forms: {level: {"m2l_on_tensor": bool, "m2m_l2l_on_tensor": bool}} (as
+    fb_operator_autotune returns) or a sequence of 13 choice ints."""
+    ch = np.zeros(13, np.int32)
+    if isinstance(forms, dict):
+        for l, v in forms.items():
+            ch[int(l)] = (1 if v.get("m2l_on_tensor") else 0) | (2 if v.get("m2m_l2l_on_tensor") else 0)
+    else:
+        ch[:len(forms)] = np.asarray(forms, np.int32)
+    _check(lib.fb_operator_set_forms(op, ch.ctypes.data, _stream(stream)))
 
 
 FB_TRANS_AUTO, FB_TRANS_COMPOSED, FB_TRANS_RCR, FB_TRANS_TENSOR = 0, 1, 2, 3

@@ -363,6 +363,14 @@ fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times,
     return fb_autotune_impl(op, nrhs, as_stream(stream), times, choice);
 }
 
+fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream) {
+    if (!op || !choice) return fb_fail(FB_ERR_ARG, "NULL argument");
+    fb_graph_free(op->graphs);
+    fb_status st = fb_set_forms_impl(op, choice, as_stream(stream));
+    if (st == FB_OK) op->method = FB_TRANS_AUTO;
+    return st;
+}
+
 fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
     if (n) *n = op->n;

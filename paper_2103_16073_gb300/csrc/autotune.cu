@@ -58,6 +58,8 @@ void free_rcr(RcrPlan& p) {
 // times[4 * l + {0,1,2,3}] = M2L RCR, M2L tensor, M2M+L2L RCR, M2M+L2L tensor
 // (ms, -1 when not a candidate) for l = 0..L; choice[l] bit 0 = M2L on the
 // tensor cores, bit 1 = M2M/L2L into level l on the tensor cores.
+fb_status fb_install_forms(fb_op* op, const std::vector<int>& tc_m2l, cudaStream_t s);
+
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_out, int* choice) {
     if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;
     double times_local[4 * (FB_MAXLEV + 1)];
@@ -157,7 +159,22 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
         }
         if (choice) choice[l] = ch;
     }
-    // ---- install the M2L choice: tensor-core plan of the chosen levels, RCR for the rest
+    FB_CUDA(cudaStreamSynchronize(s));
+    return fb_install_forms(op, tc_m2l, s);
+}
+
+// Installs per-level M2L forms: tensor-core plan of `tc_m2l` levels, RCR for
+// the rest.
+fb_status fb_install_forms(fb_op* op, const std::vector<int>& tc_m2l, cudaStream_t s) {
+    const fb_tree* t = op->tree;
+    const size_t csz = sizeof(cf);
+    if (!tc_m2l.empty()) {
+        std::vector<int> need;
+        for (size_t j = 0; j < op->h_jobs.size(); ++j)
+            if (op->h_job_m2l[j] && std::find(tc_m2l.begin(), tc_m2l.end(), op->h_job_level[j]) != tc_m2l.end())
+                need.push_back((int)j);
+        FB_CHECK(fb_compose_jobs(op, need, s));
+    }
     FB_CUDA(cudaStreamSynchronize(s));
     fb_tc_free(op->tc_plan);
     free_rcr(op->m2l_rcr_rest);
@@ -174,4 +191,42 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
     FB_CUDA(cudaStreamSynchronize(s));
     op->method = FB_TRANS_AUTO;
     return FB_OK;
+}
+
+// Installs a given per-level choice (bits as returned by the autotuner):
+// bit 0 = M2L of level l on the tensor cores, bit 1 = M2M/L2L into level l on
+// the tensor cores; lets a tuned configuration be saved and restored.
+fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s) {
+    if (op->prec != FB_PREC_MIXED_FMM) return fb_fail(FB_ERR_ARG, "translation forms apply to mixed operators");
+    const fb_tree* t = op->tree;
+    const int L = op->L;
+    std::vector<int> tc_m2l;
+    for (int l = 2; l <= L; ++l) {
+        if (choice[l] & 1) tc_m2l.push_back(l);
+        if (l < 3) continue;
+        bool want = (choice[l] & 2) != 0;
+        if (!want) {
+            FB_CUDA(cudaStreamSynchronize(s));
+            fb_tc_free(op->tc_m2m[l]);
+            fb_tc_free(op->tc_l2l[l]);
+        } else if (!op->tc_m2m[l] || !op->tc_l2l[l]) {
+            std::vector<int> need;
+            std::vector<TcGroup> up, down;
+            for (int o = 0; o < 8; ++o) {
+                int64_t g0 = t->oct_group[l][o], g1 = t->oct_group[l][o + 1];
+                if (g1 == g0) continue;
+                need.push_back(op->m2m_job[l][o]);
+                need.push_back(op->l2l_job[l][o]);
+                up.push_back(TcGroup{op->m2m_job[l][o], g0, (int32_t)(g1 - g0), l, l - 1});
+                down.push_back(TcGroup{op->l2l_job[l][o], g0, (int32_t)(g1 - g0), l - 1, l});
+            }
+            if (up.empty()) continue;
+            FB_CHECK(fb_compose_jobs(op, need, s));
+            if (!op->tc_m2m[l])
+                FB_CHECK(fb_tc_build_groups(op, up, t->oct_child[l], t->oct_parent[l], &op->tc_m2m[l], s));
+            if (!op->tc_l2l[l])
+                FB_CHECK(fb_tc_build_groups(op, down, t->oct_parent[l], t->oct_child[l], &op->tc_l2l[l], s));
+        }
+    }
+    return fb_install_forms(op, tc_m2l, s);
 }

@@ -367,6 +367,7 @@ fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, 
 fb_status fb_compose_jobs(fb_op* op, const std::vector<int>& which, cudaStream_t s);
 fb_status fb_rcr_run_op(fb_op* op, RcrPlan& pl, void* src, void* dst, cudaStream_t s, int nrhs, int64_t rstride);
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times, int* choice);
+fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s);
 fb_status fb_compose_all(fb_op* op, cudaStream_t s);
 fb_status fb_learned_alloc(LearnedNet*& net, const fb_op* op, const fb_precond* bj, cudaStream_t s);
 void fb_learned_free(LearnedNet*& net);

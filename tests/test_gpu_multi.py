@@ -104,6 +104,12 @@ def test_autotune_keeps_results(setup):
     for r in range(3):
         assert rel(Y[r].cpu().numpy(), Yref[r].cpu().numpy()) < 1e-5
     assert rel(y1.cpu().numpy(), Yref[0].cpu().numpy()) < 1e-5
+    # the tuned choice can be saved and installed again without timing
+    fb.fb_operator_set_forms(A, [0] * 13)
+    fb.fb_operator_set_forms(A, rep)
+    y2 = torch.empty_like(X[0])
+    fb.fb_operator_apply(A, X[0].contiguous(), y2)
+    assert rel(y2.cpu().numpy(), y1.cpu().numpy()) < 1e-6
     print(rep)
 
 
