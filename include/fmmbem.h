@@ -66,6 +66,11 @@ typedef int fb_status;
 #define FB_OP_M 1  /* double layer          M[s](x) = int s dG/dn_y dS_y     */
 #define FB_OP_LP 2 /* adjoint double layer L'[s](x) = int s dG/dn_x dS_y     */
 #define FB_OP_A 3  /* direct-BEM system     A = 1/2 I + M - ik L diag(beta)  */
+#define FB_OP_MP 4 /* hypersingular        M'[s](x) = d/dn_x int s dG/dn_y dS_y
+                      (Eq. ibem3, finite part; near/self entries by the flat-element
+                      form (n_x.n)[k^2 S + sum_e int_e grad_y G.m dl]
+                      + sum_e int_e (n.grad_x G)(t.m) dl, far by the 3-point rule
+                      of d2G/dn_x dn_y; FMM: dipole P2M and normal-gradient L2P) */
 
 /* How an operator is applied. */
 #define FB_PREC_FP64_DENSE 0 /* stored dense N x N complex128 matrix        */

@@ -21,7 +21,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "FBError", "lib", "FB_OP_L", "FB_OP_M", "FB_OP_LP", "FB_OP_A", "FB_PREC_FP64_DENSE",
+    "FBError", "lib", "FB_OP_L", "FB_OP_M", "FB_OP_LP", "FB_OP_A", "FB_OP_MP", "FB_PREC_FP64_DENSE",
     "FB_PREC_FP64_FMM", "FB_PREC_MIXED_FMM", "FB_PC_NONE", "FB_PC_BLOCK_JACOBI",
     "fb_version", "fb_mesh_create", "fb_mesh_set_admittance", "fb_mesh_info", "fb_mesh_geometry",
     "fb_mesh_destroy", "fb_tree_build", "fb_tree_info", "fb_tree_export", "fb_tree_destroy",
@@ -36,7 +36,7 @@ __all__ = [
 ]
 
 FB_OK = 0
-FB_OP_L, FB_OP_M, FB_OP_LP, FB_OP_A = 0, 1, 2, 3
+FB_OP_L, FB_OP_M, FB_OP_LP, FB_OP_A, FB_OP_MP = 0, 1, 2, 3, 4
 FB_PREC_FP64_DENSE, FB_PREC_FP64_FMM, FB_PREC_MIXED_FMM = 0, 1, 2
 FB_MEM_HOST, FB_MEM_DEVICE = 0, 1
 FB_PC_NONE, FB_PC_BLOCK_JACOBI = 0, 1

@@ -187,7 +187,7 @@ fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k,
     if (!mesh || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
     *out = nullptr;
     if (!(k > 0.0)) return fb_fail(FB_ERR_ARG, "k must be > 0");
-    if (kind < FB_OP_L || kind > FB_OP_A) return fb_fail(FB_ERR_ARG, "unknown operator kind");
+    if (kind < FB_OP_L || kind > FB_OP_MP) return fb_fail(FB_ERR_ARG, "unknown operator kind");
     if (precision < FB_PREC_FP64_DENSE || precision > FB_PREC_MIXED_FMM)
         return fb_fail(FB_ERR_ARG, "unknown precision");
     if (precision != FB_PREC_FP64_DENSE) {

@@ -52,6 +52,19 @@ __global__ void k_near_fill(Geom g, int kind, double k, double rc, const int32_t
     }
 }
 
+// max |z| over a complex array (non-negative doubles compare as integers)
+__global__ void k_absmax(const cd* a, int64_t n, double* out) {
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double v = sqrt(abs2(a[i]));
+        if (!(v <= 1e300)) v = 1e300;   // inf and NaN count as out of range
+        m = fmax(m, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax((unsigned long long*)out, (unsigned long long)__double_as_longlong(m));
+}
+
 // ----------------------------------------------------------- P2M / L2P ----
 // W[pos][nm] = ik A_j sum_q w_q [dip n_j.grad R_n^{-m}(y_q - c) + mono_j R_n^{-m}(y_q - c)]
 // V[pos][nm] = R_n^m(x_i - c)  (L' : n_i . grad R_n^m(x_i - c))
@@ -75,7 +88,7 @@ __global__ void k_p2m_l2p(Geom g, int kind, double k, int P, int64_t n, const in
         cd mono = mk(0.0, 0.0);
         double dip = 0.0;
         if (kind == FB_OP_L || kind == FB_OP_LP) mono = mk(1.0, 0.0);
-        if (kind == FB_OP_M) dip = 1.0;
+        if (kind == FB_OP_M || kind == FB_OP_MP) dip = 1.0;
         if (kind == FB_OP_A) {
             cd b = g.beta[e];
             mono = mk(k * b.im, -k * b.re);   // -i k beta
@@ -95,7 +108,7 @@ __global__ void k_p2m_l2p(Geom g, int kind, double k, int P, int64_t n, const in
         }
         V3 x = v3(g.cx[e], g.cy[e], g.cz[e]);
         regular_all(Pp1, k, x - c, wrk, Rv);
-        if (kind == FB_OP_LP) {
+        if (kind == FB_OP_LP || kind == FB_OP_MP) {
             V3 ni = nj;
             for (int nn = 0; nn < P; ++nn)
                 for (int m = -nn; m <= nn; ++m) Vr[nm_idx(nn, m)] = ndot_grad_regular(Rv, P, k, ni, nn, m);
@@ -819,7 +832,25 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         }
         op->method = FB_TRANS_AUTO;
     }
-    // ---- FP32 copies for the mixed path
+    // ---- FP32 copies for the mixed path.  High orders at small k tau give
+    // coaxial coefficients (spherical Hankel functions of high order) beyond
+    // the FP32 range; the mixed form is refused for such operators instead of
+    // producing overflowed translations (the FP64 form handles them).
+    if (op->prec == FB_PREC_MIXED_FMM) {
+        double* dmax = nullptr;
+        FB_CHECK(dalloc(&dmax, 1));
+        FB_CUDA(cudaMemsetAsync(dmax, 0, sizeof(double), s));
+        k_absmax<<<std::min(div_up(op->coax_count, 256), 1024), 256, 0, s>>>(op->coax64, op->coax_count, dmax);
+        double hmax = 0.0;
+        cudaError_t ce = cudaMemcpyAsync(&hmax, dmax, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+        dfree(dmax);
+        if (ce != cudaSuccess) return fb_fail(FB_ERR_CUDA, cudaGetErrorString(ce));
+        if (!(hmax < 1e37))
+            return fb_fail(FB_ERR_ARG, "mixed precision: translation coefficients reach " + std::to_string(hmax) +
+                                           ", beyond the FP32 range at this order and wavenumber; use "
+                                           "FB_PREC_FP64_FMM or a lower p_min");
+    }
     if (op->prec == FB_PREC_MIXED_FMM) {
         FB_CHECK(dalloc(&op->nf32, op->nf_count));
         FB_CHECK(dalloc(&op->w32, (size_t)n * PL));

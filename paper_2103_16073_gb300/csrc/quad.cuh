@@ -214,11 +214,96 @@ __device__ inline Entry pair_entry(const Geom& g, int64_t j, V3 x, V3 nxv, bool 
     return out;
 }
 
+// ------------------------------------------------ hypersingular M' ----
+// Point kernel d2G/dn_x dn_y (r = y - x):
+//   -e^{ikR}/(4 pi R^3) [(3 - 3ikR - k^2R^2)(n_x.r)(n_y.r)/R^2 + (ikR - 1)(n_x.n_y)]
+__device__ __forceinline__ cd kernel_nn(double k, V3 r, V3 nx, V3 ny) {
+    double R = norm(r);
+    double kr = k * R;
+    double s, c;
+    sincos(kr, &s, &c);
+    double a = dot(nx, r) * dot(ny, r) / (R * R);
+    double b = dot(nx, ny);
+    cd t = mk((3.0 - kr * kr) * a - b, -3.0 * kr * a + kr * b);   // (3 - 3ikR - k^2R^2) a + (ikR - 1) b
+    cd e = mk(c, s);
+    double f = -FB_INV4PI / (R * R * R);
+    return (f * e) * t;
+}
+
+// Gauss-Legendre, 8 points on [-1, 1]
+__device__ __forceinline__ void gl8(int q, double& x, double& w) {
+    const double X[4] = {0.18343464249564978, 0.525532409916329, 0.7966664774136267, 0.9602898564975362};
+    const double Wt[4] = {0.36268378337836166, 0.3137066458778869, 0.22238103445337443, 0.10122853629037706};
+    int h = q < 4 ? 3 - q : q - 4;
+    x = q < 4 ? -X[h] : X[h];
+    w = Wt[h];
+}
+
+// Edge integrals of the flat-element form of M' for target x (normal nx):
+//   A = sum_e int_e grad_y G . m dl,   B = sum_e int_e (n . grad_x G)(t . m) dl,
+// t = nx - (nx.n) n, m the outward in-plane edge normal; 8-point
+// Gauss-Legendre on min(16, ceil(2 l_e / d_e)) segments (d_e = distance from
+// x to the edge).
+__device__ inline void mp_edges(double k, V3 x, V3 nxv, const Tri& t, cd& A, cd& B) {
+    A = mk(0.0, 0.0);
+    B = mk(0.0, 0.0);
+    V3 tv = nxv - dot(nxv, t.n) * t.n;
+    V3 vs[3] = {t.a, t.b, t.c};
+    for (int e = 0; e < 3; ++e) {
+        V3 p0 = vs[e], p1 = vs[(e + 1) % 3];
+        V3 d = p1 - p0;
+        double le = norm(d);
+        V3 m = cross((1.0 / le) * d, t.n);
+        double sp = fmin(fmax(dot(x - p0, d) / dot(d, d), 0.0), 1.0);
+        double de = norm(x - (p0 + sp * d));
+        int ns = (int)fmin(16.0, fmax(1.0, ceil(2.0 * le / de)));
+        double tm = dot(tv, m);
+        for (int sgi = 0; sgi < ns; ++sgi)
+            for (int q = 0; q < 8; ++q) {
+                double gx, gw;
+                gl8(q, gx, gw);
+                double u = (sgi + 0.5 * (gx + 1.0)) / ns;
+                double w = gw * 0.5 / ns * le;
+                V3 r = (p0 + u * d) - x;
+                double R = norm(r);
+                double kr = k * R;
+                double s, c;
+                sincos(kr, &s, &c);
+                // g'(R) = e^{ikR}(ikR - 1)/(4 pi R^2)
+                cd gp = (FB_INV4PI / (R * R)) * (mk(c, s) * mk(-1.0, kr));
+                A = A + (w * dot(r, m) / R) * gp;
+                B = B + (-w * dot(r, t.n) / R * tm) * gp;
+            }
+    }
+}
+
+// M' entry for target point x (normal nx), element j (self: x = centroid of j):
+//   far:  three-point rule of d2G/dn_x dn_y;
+//   near / self:  (nx.n)[k^2 S + A] + B, S the single-layer entry of the pair.
+__device__ inline cd mp_entry(const Geom& g, int64_t j, V3 x, V3 nxv, bool self, double k, double rc) {
+    Tri t = load_tri(g, j);
+    V3 cj = v3(g.cx[j], g.cy[j], g.cz[j]);
+    V3 dc = x - cj;
+    if (self || dot(dc, dc) < rc * rc) {
+        Entry e = pair_entry(g, j, x, nxv, self, k, rc);
+        cd A, B;
+        mp_edges(k, x, nxv, t, A, B);
+        return dot(nxv, t.n) * (((k * k) * e.L) + A) + B;
+    }
+    cd out = mk(0.0, 0.0);
+    for (int q = 0; q < 3; ++q) {
+        V3 y = v3(g.gx[3 * j + q], g.gy[3 * j + q], g.gz[3 * j + q]);
+        out = out + (t.area / 3.0) * kernel_nn(k, y - x, nxv, t.n);
+    }
+    return out;
+}
+
 // Operator entry of kind FB_OP_* for collocation row i (element i) and column j.
 __device__ __forceinline__ cd op_entry(const Geom& g, int kind, int64_t i, int64_t j, double k,
                                        double rc) {
     V3 x = v3(g.cx[i], g.cy[i], g.cz[i]);
     V3 nv = v3(g.nx[i], g.ny[i], g.nz[i]);
+    if (kind == FB_OP_MP) return mp_entry(g, j, x, nv, i == j, k, rc);
     Entry e = pair_entry(g, j, x, nv, i == j, k, rc);
     switch (kind) {
         case FB_OP_L: return e.L;
