@@ -274,7 +274,7 @@ FB_API fb_status fb_precond_use_graphs(fb_precond* pc, int enable);
 #define FB_MAX_RHS 64
 
 /* Autotuner of the translation passes of a mixed-precision FMM operator: for
- * every level it times on the device (median of 5, nrhs right-hand sides)
+ * every level it times on the device (median of 3, nrhs right-hand sides)
  * the per-pair rotation-coaxial-rotation kernel (Sec. 3.3) against the
  * stacked tensor-core GEMM of composed matrices, for M2L and for the
  * M2M/L2L passes into the level, and installs the faster form per level

@@ -1,12 +1,13 @@
 // Autotuner of the translation passes (mixed precision).  For every level it
-// times, on the device and for a given number of right-hand sides, the
-// per-pair rotation-coaxial-rotation kernel (RCR) against the stacked
-// tensor-core GEMM of composed matrices (3xTF32), for M2L and for the M2M /
-// L2L passes into that level, and keeps the faster form.  The tensor-core
-// candidate of a level is skipped when its composed matrices would exceed a
-// memory cap.  The result replaces the operator's rule-based choice
-// (>= 48 pairs per translation vector); FP64 operators have only the RCR
-// form and are left unchanged.
+// times (median of 3), on the device and for a given number of right-hand
+// sides, the per-pair rotation-coaxial-rotation kernel (RCR) against the
+// stacked tensor-core GEMM of composed matrices (3xTF32), for M2L and for the
+// M2M / L2L passes into that level, and keeps the faster form.  The
+// tensor-core candidate of an M2L level is skipped when its order exceeds
+// 20, when it has fewer than 16 box pairs per translation vector on average,
+// or when its composed matrices would exceed a memory cap.  The result
+// replaces the operator's rule-based choice (>= 48 pairs per translation
+// vector); FP64 operators have only the RCR form and are left unchanged.
 #include <algorithm>
 #include <vector>
 
@@ -68,7 +69,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
     const int L = op->L;
     const int64_t cnt = op->lev_off[L + 1];
     const size_t csz = sizeof(cf);
-    const int reps = 5;
+    const int reps = 3;
     const double cap_bytes = 8.0e9;   // composed FP64 + packed TF32 tiles of one level
     // expansion buffers for nrhs sets (contents do not matter for timing)
     if (nrhs > op->exp_nrhs) {
@@ -101,10 +102,19 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             FB_CHECK(st);
             int64_t p2 = (int64_t)op->p[l] * op->p[l];
             double bytes = 0;
-            for (int c = 0; c < FB_NOFF; ++c)
-                if (t->m2l_group[(size_t)l * FB_NOFF + c + 1] > t->m2l_group[(size_t)l * FB_NOFF + c])
+            int64_t groups = 0, pairs = 0;
+            for (int c = 0; c < FB_NOFF; ++c) {
+                int64_t g = t->m2l_group[(size_t)l * FB_NOFF + c + 1] - t->m2l_group[(size_t)l * FB_NOFF + c];
+                if (g > 0) {
                     bytes += (double)p2 * p2 * (16.0 + 2 * 8.0);
-            if (bytes <= cap_bytes) {
+                    ++groups;
+                    pairs += g;
+                }
+            }
+            // the composed form costs ~p/4 times the RCR arithmetic: only dense
+            // levels of moderate order are worth timing
+            const bool candidate = op->p[l] <= 20 && pairs >= 16 * groups;
+            if (candidate && bytes <= cap_bytes) {
                 std::vector<int> need;
                 for (size_t j = 0; j < op->h_jobs.size(); ++j)
                     if (op->h_job_m2l[j] && op->h_job_level[j] == l) need.push_back((int)j);
