@@ -502,6 +502,8 @@ fb_status fb_learned_params(fb_precond* pc, float* host_out, const float* host_i
     if (host_in) {
         if (*count != np) return fb_fail(FB_ERR_ARG, "parameter count mismatch");
         FB_CUDA(cudaMemcpy(fb_learned_weights(pc->net), host_in, sizeof(float) * np, cudaMemcpyHostToDevice));
+        FB_CHECK(fb_learned_params_changed(pc->net, nullptr));
+        FB_CUDA(cudaDeviceSynchronize());
     }
     *count = np;
     if (host_out) FB_CUDA(cudaMemcpy(host_out, fb_learned_weights(pc->net), sizeof(float) * np, cudaMemcpyDeviceToHost));

@@ -378,6 +378,7 @@ fb_status fb_learned_adam_step(LearnedNet* net, double lr, cudaStream_t s);
 fb_status fb_learned_init(LearnedNet* net, uint64_t seed, cudaStream_t s);
 fb_status fb_learned_adjoint_ops(LearnedNet* net, cudaStream_t s);
 fb_status fb_learned_set_objective(LearnedNet* net, int objective);
+fb_status fb_learned_params_changed(LearnedNet* net, cudaStream_t s);
 int64_t fb_learned_nparam(const LearnedNet* net);
 float* fb_learned_weights(LearnedNet* net);
 float* fb_learned_grads(LearnedNet* net);

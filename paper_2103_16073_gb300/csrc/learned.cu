@@ -347,6 +347,32 @@ __global__ void k_adam(float* w, const float* gr, float* m, float* v, int64_t n,
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// Packed BF16 copies of the 64-column weight matrices for the inference
+// kernels: W (K x 64, K = 64 or 128) -> P[n][kp] = (W[2kp][n], W[2kp+1][n]),
+// so a CTA stages a layer's weights with 16-byte loads.  Rebuilt after every
+// parameter change (initialisation, upload, Adam step).
+__global__ void k_pack_w(const float* __restrict__ W, int K, uint32_t* __restrict__ P) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int KP = K / 2;
+    if (i >= HW * KP) return;
+    int n = i / KP, kp = i % KP;
+    P[i] = pack_bf16(W[(2 * kp) * HW + n], W[(2 * kp + 1) * HW + n]);
+}
+
+// Stages a packed K x 64 weight block into shared memory rows of KP + 4 words.
+template <int KP>
+__device__ __forceinline__ void stage_w(const uint32_t* __restrict__ P, uint32_t (*Ws)[KP + 4], int tid, int nth) {
+    constexpr int V = KP / 4;   // uint4 per row
+    for (int i = tid; i < HW * V; i += nth) {
+        int n = i / V, q = i % V;
+        uint4 x = reinterpret_cast<const uint4*>(P + n * KP)[q];
+        Ws[n][4 * q] = x.x;
+        Ws[n][4 * q + 1] = x.y;
+        Ws[n][4 * q + 2] = x.z;
+        Ws[n][4 * q + 3] = x.w;
+    }
+}
+
 // ------------------------------------------------ fused inference path ----
 // Applying the trained network inside FGMRES needs no activations for a
 // backward pass, so the element-level layers run fused: pass 1 computes the
@@ -409,24 +435,22 @@ __global__ void __launch_bounds__(64) k_inf_pass1(Geom g, const int32_t* perm, c
     GL[(int64_t)leaf * HW + c] = b > a ? acc / (float)(b - a) : 0.f;
 }
 
-// 64 elements per CTA (tree order), 128 threads = 4 warps x 16 rows.
-__global__ void __launch_bounds__(128) k_inf_pass2(Geom g, const int32_t* perm, const int32_t* leaf_of,
+// 64 elements per CTA (tree order), 256 threads = 8 warps: warp w computes
+// rows 16 (w & 3) .. +16 and the 32 columns 32 (w >> 2) .. +32 of H1.
+__global__ void __launch_bounds__(256) k_inf_pass2(Geom g, const int32_t* perm, const int32_t* leaf_of,
                                                    const cd* v, const cd* u, const double* st, int64_t n,
                                                    const float* W0, const float* b0, const float* DL,
-                                                   const float* Wh, const float* bh, const float* Wo,
+                                                   const uint32_t* Whp, const float* bh, const float* Wo,
                                                    const float* bo, cd* z) {
-    __shared__ uint32_t Es[64][HW + 4];        // [row][k pair]: 128 bf16 per row (+pad)
-    __shared__ uint32_t Ws[HW][HW + 4];        // W_h as [col n][k pair]
+    __shared__ __align__(16) uint32_t Es[64][HW + 4];   // [row][k pair]: 128 bf16 per row (+pad)
+    __shared__ __align__(16) uint32_t Ws[HW][HW + 4];   // W_h as [col n][k pair]
     __shared__ float fs[64][NF];
     __shared__ float w0s[NF][HW];
+    __shared__ float opart[2][64][2];                  // output partial sums per column half
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t r0 = (int64_t)blockIdx.x * 64;
     for (int i = tid; i < NF * HW; i += blockDim.x) w0s[i / HW][i % HW] = bfr(W0[i]);
-    // W_h [128 x 64] (in x out) -> Ws[n][kp] = (W[2kp][n], W[2kp+1][n])
-    for (int i = tid; i < HW * HW; i += blockDim.x) {   // coalesced reads along n
-        int kp = i / HW, nn = i % HW;
-        Ws[nn][kp] = pack_bf16(Wh[(2 * kp) * HW + nn], Wh[(2 * kp + 1) * HW + nn]);
-    }
+    stage_w<HW>(Whp, Ws, tid, blockDim.x);   // W_h [128 x 64] packed as [n][k pair]
     if (tid < 64) {
         int64_t pos = r0 + tid;
         float f[NF];
@@ -436,46 +460,48 @@ __global__ void __launch_bounds__(128) k_inf_pass2(Geom g, const int32_t* perm, 
         for (int k = 0; k < NF; ++k) fs[tid][k] = f[k];
     }
     __syncthreads();
-    // E = [H0, D_L(leaf)] as bf16 pairs
-    for (int i = tid; i < 64 * HW; i += blockDim.x) {
-        int r = i / HW, kp = i % HW;
-        int64_t pos = r0 + r;
+    // E = [H0, D_L(leaf)] as bf16 pairs: H0 pairs, then D_L in 4-float pieces
+    for (int i = tid; i < 64 * (HW / 2); i += blockDim.x) {
+        int r = i / (HW / 2), kp = i % (HW / 2);
+        int c0 = 2 * kp;
         float x0 = 0.f, x1 = 0.f;
-        if (pos < n) {
-            if (kp < HW / 2) {
-                int c0 = 2 * kp;
-                float h0 = b0[c0], h1 = b0[c0 + 1];
+        if (r0 + r < n) {
+            float h0 = b0[c0], h1 = b0[c0 + 1];
 #pragma unroll
-                for (int k = 0; k < NF; ++k) {
-                    h0 = fmaf(fs[r][k], w0s[k][c0], h0);
-                    h1 = fmaf(fs[r][k], w0s[k][c0 + 1], h1);
-                }
-                x0 = silu(h0);
-                x1 = silu(h1);
-            } else {
-                const float* d = DL + (int64_t)leaf_of[pos] * HW + 2 * (kp - HW / 2);
-                x0 = d[0];
-                x1 = d[1];
+            for (int k = 0; k < NF; ++k) {
+                h0 = fmaf(fs[r][k], w0s[k][c0], h0);
+                h1 = fmaf(fs[r][k], w0s[k][c0 + 1], h1);
             }
+            x0 = silu(h0);
+            x1 = silu(h1);
         }
         Es[r][kp] = pack_bf16(x0, x1);
     }
+    for (int i = tid; i < 64 * (HW / 4); i += blockDim.x) {
+        int r = i / (HW / 4), q = i % (HW / 4);
+        int64_t pos = r0 + r;
+        float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (pos < n) d = reinterpret_cast<const float4*>(DL + (int64_t)leaf_of[pos] * HW)[q];
+        Es[r][HW / 2 + 2 * q] = pack_bf16(d.x, d.y);
+        Es[r][HW / 2 + 2 * q + 1] = pack_bf16(d.z, d.w);
+    }
     __syncthreads();
-    // H1 = silu(E W_h + b_h): warp rows [16 warp, +16), 64 columns (8 n-tiles)
-    float acc[8][4];
+    // H1 = silu(E W_h + b_h)
+    float acc[4][4];
 #pragma unroll
-    for (int t = 0; t < 8; ++t)
+    for (int t = 0; t < 4; ++t)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
-    const int row = warp * 16 + (lane >> 2), kq = lane & 3;
+    const int row = (warp & 3) * 16 + (lane >> 2), kq = lane & 3;
+    const int half = warp >> 2, cbase = half * 32;
 #pragma unroll
     for (int k0 = 0; k0 < 2 * HW; k0 += 16) {
         int kb = k0 / 2;
         uint32_t a0 = Es[row][kb + kq], a1 = Es[row + 8][kb + kq], a2 = Es[row][kb + kq + 4],
                  a3 = Es[row + 8][kb + kq + 4];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            int col = t * 8 + (lane >> 2);
+        for (int t = 0; t < 4; ++t) {
+            int col = cbase + t * 8 + (lane >> 2);
             uint32_t b0r = Ws[col][kb + kq], b1r = Ws[col][kb + kq + 4];
             asm volatile(
                 "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -484,35 +510,42 @@ __global__ void __launch_bounds__(128) k_inf_pass2(Geom g, const int32_t* perm, 
                 : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0r), "r"(b1r));
         }
     }
-    // O = H1 W_o + b_o: each lane holds rows (lane>>2) and +8, columns t*8 + 2*(lane&3) + {0,1}
-    float o[2][2] = {{0.f, 0.f}, {0.f, 0.f}};   // [row half][re/im]
+    // O = H1 W_o + b_o over this warp's 32 columns; rows (lane >> 2) and +8
+    float o[2][2] = {{0.f, 0.f}, {0.f, 0.f}};
 #pragma unroll
-    for (int t = 0; t < 8; ++t)
+    for (int t = 0; t < 4; ++t)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-            int col = t * 8 + (lane & 3) * 2 + (q & 1);
+            int col = cbase + t * 8 + (lane & 3) * 2 + (q & 1);
             float h = bfr(silu(acc[t][q] + bh[col]));
-            int half = q >> 1;
-            o[half][0] = fmaf(h, bfr(Wo[col * 2]), o[half][0]);
-            o[half][1] = fmaf(h, bfr(Wo[col * 2 + 1]), o[half][1]);
+            int hr = q >> 1;
+            o[hr][0] = fmaf(h, bfr(Wo[col * 2]), o[hr][0]);
+            o[hr][1] = fmaf(h, bfr(Wo[col * 2 + 1]), o[hr][1]);
         }
 #pragma unroll
-    for (int half = 0; half < 2; ++half)
+    for (int hr = 0; hr < 2; ++hr)
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            o[half][j] += __shfl_xor_sync(0xffffffffu, o[half][j], 1);
-            o[half][j] += __shfl_xor_sync(0xffffffffu, o[half][j], 2);
+            o[hr][j] += __shfl_xor_sync(0xffffffffu, o[hr][j], 1);
+            o[hr][j] += __shfl_xor_sync(0xffffffffu, o[hr][j], 2);
         }
     if ((lane & 3) == 0) {
-        double s = sqrt(st[0] / (double)n);
-        cd ph = input_phase(st);
 #pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            int64_t pos = r0 + row + half * 8;
-            if (pos >= n) continue;
+        for (int hr = 0; hr < 2; ++hr) {
+            opart[half][row + hr * 8][0] = o[hr][0];
+            opart[half][row + hr * 8][1] = o[hr][1];
+        }
+    }
+    __syncthreads();
+    if (tid < 64) {
+        int64_t pos = r0 + tid;
+        if (pos < n) {
+            double sc = sqrt(st[0] / (double)n);
+            cd ph = input_phase(st);
+            float oa = opart[0][tid][0] + opart[1][tid][0] + bo[0];
+            float ob = opart[0][tid][1] + opart[1][tid][1] + bo[1];
             int64_t e = perm[pos];
-            cd oo = mk(s * (double)(o[half][0] + bo[0]), s * (double)(o[half][1] + bo[1])) * ph;
-            z[e] = u[e] + oo;
+            z[e] = u[e] + mk(sc * (double)oa, sc * (double)ob) * ph;
         }
     }
 }
@@ -523,59 +556,64 @@ __global__ void __launch_bounds__(128) k_inf_pass2(Geom g, const int32_t* perm, 
 //   mode 0 (up-sweep):   X[b] = mean of Gc[c], c in [cs[b], cs[b+1])        (K = 64)
 //   mode 1 (down-sweep): X[b] = [G[b], Dp[parent[b]]]                        (K = 128)
 template <int K>
-__global__ void __launch_bounds__(128) k_inf_layer(int mode, int M, const float* __restrict__ G,
+__global__ void __launch_bounds__(256) k_inf_layer(int mode, int M, const float* __restrict__ G,
                                                    const int32_t* __restrict__ idx, const float* __restrict__ Dp,
-                                                   const float* __restrict__ W, const float* __restrict__ bias,
+                                                   const uint32_t* __restrict__ Wp, const float* __restrict__ bias,
                                                    float* __restrict__ Y) {
+    // 32 rows per CTA, 8 warps: warp w computes rows 16 (w & 1) .. +16 and the
+    // 16 columns 16 (w >> 1) .. +16 (two n-tiles of 8)
     constexpr int KP = K / 2;
-    __shared__ uint32_t Xs[64][KP + 4];
-    __shared__ uint32_t Ws[HW][KP + 4];
+    constexpr int ROWS = 32;
+    __shared__ __align__(16) uint32_t Xs[ROWS][KP + 4];
+    __shared__ __align__(16) uint32_t Ws[HW][KP + 4];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int b0 = blockIdx.x * 64;
-    for (int i = tid; i < KP * HW; i += blockDim.x) {
-        int kp = i / HW, nn = i % HW;
-        Ws[nn][kp] = pack_bf16(W[(2 * kp) * HW + nn], W[(2 * kp + 1) * HW + nn]);
-    }
-    for (int i = tid; i < 64 * KP; i += blockDim.x) {
-        int r = i / KP, kp = i % KP;
+    const int b0 = blockIdx.x * ROWS;
+    stage_w<KP>(Wp, Ws, tid, blockDim.x);
+    // X rows in 4-float pieces (row-major feature arrays are 16-byte aligned)
+    constexpr int Q = K / 4;
+    for (int i = tid; i < ROWS * Q; i += blockDim.x) {
+        int r = i / Q, q = i % Q;
         int b = b0 + r;
-        float x0 = 0.f, x1 = 0.f;
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         if (b < M) {
             if (mode == 0) {
                 int c0 = idx[b], c1 = idx[b + 1];
-                for (int c = c0; c < c1; ++c) {
-                    x0 += G[(int64_t)c * HW + 2 * kp];
-                    x1 += G[(int64_t)c * HW + 2 * kp + 1];
+                float4 y[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c)   // an octree box has at most 8 children
+                    y[c] = c0 + c < c1 ? reinterpret_cast<const float4*>(G + (int64_t)(c0 + c) * HW)[q]
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    x.x += y[c].x; x.y += y[c].y; x.z += y[c].z; x.w += y[c].w;
                 }
                 float inv = c1 > c0 ? 1.f / (float)(c1 - c0) : 0.f;
-                x0 *= inv;
-                x1 *= inv;
-            } else if (kp < HW / 2) {
-                x0 = G[(int64_t)b * HW + 2 * kp];
-                x1 = G[(int64_t)b * HW + 2 * kp + 1];
+                x.x *= inv; x.y *= inv; x.z *= inv; x.w *= inv;
+            } else if (q < HW / 4) {
+                x = reinterpret_cast<const float4*>(G + (int64_t)b * HW)[q];
             } else {
-                const float* d = Dp + (int64_t)idx[b] * HW + 2 * (kp - HW / 2);
-                x0 = d[0];
-                x1 = d[1];
+                x = reinterpret_cast<const float4*>(Dp + (int64_t)idx[b] * HW)[q - HW / 4];
             }
         }
-        Xs[r][kp] = pack_bf16(x0, x1);
+        Xs[r][2 * q] = pack_bf16(x.x, x.y);
+        Xs[r][2 * q + 1] = pack_bf16(x.z, x.w);
     }
     __syncthreads();
-    float acc[8][4];
+    float acc[2][4];
 #pragma unroll
-    for (int t = 0; t < 8; ++t)
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[t][q] = 0.f;
-    const int row = warp * 16 + (lane >> 2), kq = lane & 3;
+    const int row = (warp & 1) * 16 + (lane >> 2), kq = lane & 3;
+    const int cbase = (warp >> 1) * 16;
 #pragma unroll
     for (int k0 = 0; k0 < K; k0 += 16) {
         int kb = k0 / 2;
         uint32_t a0 = Xs[row][kb + kq], a1 = Xs[row + 8][kb + kq], a2 = Xs[row][kb + kq + 4],
                  a3 = Xs[row + 8][kb + kq + 4];
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            int col = t * 8 + (lane >> 2);
+        for (int t = 0; t < 2; ++t) {
+            int col = cbase + t * 8 + (lane >> 2);
             uint32_t b0r = Ws[col][kb + kq], b1r = Ws[col][kb + kq + 4];
             asm volatile(
                 "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -585,11 +623,11 @@ __global__ void __launch_bounds__(128) k_inf_layer(int mode, int M, const float*
         }
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t)
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             int b = b0 + row + (q >> 1) * 8;
-            int col = t * 8 + (lane & 3) * 2 + (q & 1);
+            int col = cbase + t * 8 + (lane & 3) * 2 + (q & 1);
             if (b < M) Y[(int64_t)b * HW + col] = silu(acc[t][q] + bias[col]);
         }
 }
@@ -608,6 +646,8 @@ struct LearnedNet {
     int64_t nparam = 0;
     int64_t oW0, ob0, oWu[DEPTH], obu[DEPTH], oWd[DEPTH], obd[DEPTH], oWh, obh, oWo, obo;
     float *w = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
+    uint32_t* wpk = nullptr;                 // packed BF16 weights for inference
+    int64_t pWu[DEPTH], pWd[DEPTH], pWh;     // offsets in wpk
     int64_t adam_t = 0;
     // activations (tree order)
     float *F = nullptr, *pre0 = nullptr, *H0 = nullptr, *E = nullptr, *preh = nullptr, *H1 = nullptr, *O = nullptr;
@@ -693,6 +733,14 @@ fb_status fb_learned_alloc(LearnedNet*& net, const fb_op* op, const fb_precond* 
     FB_CHECK(dalloc(&net->grad, o));
     FB_CHECK(dalloc(&net->m1, o));
     FB_CHECK(dalloc(&net->m2, o));
+    {   // packed inference weights: Wu_k (64 x 32 words), Wd_k and Wh (64 x 64 words)
+        int64_t q = 0;
+        for (int k = 0; k < DEPTH; ++k) { net->pWu[k] = q; q += HW * (HW / 2); }
+        for (int k = 0; k < DEPTH; ++k) { net->pWd[k] = q; q += HW * HW; }
+        net->pWh = q;
+        q += HW * HW;
+        FB_CHECK(dalloc(&net->wpk, q));
+    }
     FB_CUDA(cudaMemsetAsync(net->m1, 0, sizeof(float) * o, s));
     FB_CUDA(cudaMemsetAsync(net->m2, 0, sizeof(float) * o, s));
     FB_CHECK(dalloc(&net->F, n * NF));
@@ -742,6 +790,7 @@ void fb_learned_free(LearnedNet*& net) {
     float** fl[] = {&net->w, &net->grad, &net->m1, &net->m2, &net->F, &net->pre0, &net->H0, &net->E, &net->preh,
                     &net->H1, &net->O, &net->dH0, &net->dE, &net->dH1, &net->dO, &net->dtmp};
     for (auto p : fl) dfree(*p);
+    dfree(net->wpk);
     for (int l = 0; l <= FB_MAXLEV; ++l) {
         dfree(net->G[l]); dfree(net->Pm[l]); dfree(net->preu[l]); dfree(net->D[l]); dfree(net->Cc[l]);
         dfree(net->pred[l]); dfree(net->dG[l]); dfree(net->dD[l]); dfree(net->dC[l]); dfree(net->dPm[l]);
@@ -817,21 +866,21 @@ fb_status fb_learned_apply(LearnedNet* net, const cd* v, cd* z, cudaStream_t s) 
     fb_count_launch(2);
     for (int l = L - 1, k = 0; l >= Ltop; --l, ++k) {
         int nb = t->nbox[l];
-        k_inf_layer<HW><<<div_up(nb, 64), 128, 0, s>>>(0, nb, net->G[l + 1], net->child_start[l], nullptr,
-                                                       w + net->oWu[k], w + net->obu[k], net->G[l]);
+        k_inf_layer<HW><<<div_up(nb, 32), 256, 0, s>>>(0, nb, net->G[l + 1], net->child_start[l], nullptr,
+                                                       net->wpk + net->pWu[k], w + net->obu[k], net->G[l]);
         fb_count_launch();
     }
     // D_top = G_top: the first down-sweep layer reads G_top as its parent feature
     const float* Dprev = net->G[Ltop];
     for (int l = Ltop + 1, k = 0; l <= L; ++l, ++k) {
         int nb = t->nbox[l];
-        k_inf_layer<2 * HW><<<div_up(nb, 64), 128, 0, s>>>(1, nb, net->G[l], t->parent[l], Dprev,
-                                                           w + net->oWd[k], w + net->obd[k], net->D[l]);
+        k_inf_layer<2 * HW><<<div_up(nb, 32), 256, 0, s>>>(1, nb, net->G[l], t->parent[l], Dprev,
+                                                           net->wpk + net->pWd[k], w + net->obd[k], net->D[l]);
         fb_count_launch();
         Dprev = net->D[l];
     }
-    k_inf_pass2<<<div_up(n, 64), 128, 0, s>>>(g, t->perm, net->leaf_of, v, net->u, net->scal, n, w + net->oW0,
-                                             w + net->ob0, Dprev, w + net->oWh, w + net->obh, w + net->oWo,
+    k_inf_pass2<<<div_up(n, 64), 256, 0, s>>>(g, t->perm, net->leaf_of, v, net->u, net->scal, n, w + net->oW0,
+                                             w + net->ob0, Dprev, net->wpk + net->pWh, w + net->obh, w + net->oWo,
                                              w + net->obo, z);
     fb_count_launch();
     FB_LAUNCH_CHECK();
@@ -974,6 +1023,19 @@ fb_status fb_learned_loss_grad(LearnedNet* net, const cd* R, const cd* E, int np
     return FB_OK;
 }
 
+// Rebuilds the packed inference weights from the FP32 parameters.
+fb_status fb_learned_pack(LearnedNet* net, cudaStream_t s) {
+    const float* w = net->w;
+    for (int k = 0; k < DEPTH; ++k) {
+        k_pack_w<<<div_up(HW * (HW / 2), 256), 256, 0, s>>>(w + net->oWu[k], HW, net->wpk + net->pWu[k]);
+        k_pack_w<<<div_up(HW * HW, 256), 256, 0, s>>>(w + net->oWd[k], 2 * HW, net->wpk + net->pWd[k]);
+    }
+    k_pack_w<<<div_up(HW * HW, 256), 256, 0, s>>>(w + net->oWh, 2 * HW, net->wpk + net->pWh);
+    fb_count_launch(2 * DEPTH + 1);
+    FB_LAUNCH_CHECK();
+    return FB_OK;
+}
+
 fb_status fb_learned_adam_step(LearnedNet* net, double lr, cudaStream_t s) {
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     net->adam_t++;
@@ -982,6 +1044,7 @@ fb_status fb_learned_adam_step(LearnedNet* net, double lr, cudaStream_t s) {
                                                     b2, eps, c1, c2);
     fb_count_launch();
     FB_LAUNCH_CHECK();
+    FB_CHECK(fb_learned_pack(net, s));
     return FB_OK;
 }
 
@@ -1032,9 +1095,12 @@ fb_status fb_learned_init(LearnedNet* net, uint64_t seed, cudaStream_t s) {
     net->adam_t = 0;
     FB_CUDA(cudaMemsetAsync(net->m1, 0, sizeof(float) * net->nparam, s));
     FB_CUDA(cudaMemsetAsync(net->m2, 0, sizeof(float) * net->nparam, s));
+    FB_CHECK(fb_learned_pack(net, s));
     return FB_OK;
 }
 
 int64_t fb_learned_nparam(const LearnedNet* net) { return net->nparam; }
 float* fb_learned_weights(LearnedNet* net) { return net->w; }
 float* fb_learned_grads(LearnedNet* net) { return net->grad; }
+
+fb_status fb_learned_params_changed(LearnedNet* net, cudaStream_t s) { return fb_learned_pack(net, s); }
