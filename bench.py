@@ -590,8 +590,9 @@ def main():
                                                 "(comma-separated choice ints by level, as fb_operator_set_forms)")
     ap.add_argument("--train-sources", type=int, default=4)
     ap.add_argument("--train-steps", type=int, default=200)
-    ap.add_argument("--ref-matvecs", type=int, default=60,
-                    help="matvecs per solve used to extrapolate the reference arm")
+    ap.add_argument("--ref-matvecs", type=int, default=18,
+                    help="matvecs per solve used to extrapolate the reference arm (default: the GPU "
+                         "solve's 17 block-Jacobi iterations + 1 true residual, i.e. the same work)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
