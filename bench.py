@@ -9,11 +9,13 @@ p_min = 12).  Synthetic seeded input; see the design doc.
 
 A step is one solve A x = b of Eq. (dbem4) with the mixed operator (FP32 near
 field, P2M/L2P and translations, FP64 Arnoldi) right-preconditioned by the
-learned octree network over block Jacobi (trained before the timed region on
-pairs logged from block-Jacobi solves for other source positions), judged by
-the true residual of the FP64 FMM operator.  The same solve under block Jacobi
-alone and the plain FP64 path (FP64 FMM + FP64 block Jacobi) are timed beside
-it.  N GPUs (torchrun) each solve their own source position: weak scaling, no
+learned octree network (trained before the timed region on pairs logged from
+block-Jacobi solves for other source positions) refining the inner-outer
+preconditioner of Sec. 4 (a few GMRES steps on a low-accuracy FMM), judged by
+the true residual of the FP64 FMM operator.  The same solve under the
+inner-outer preconditioner alone, under block Jacobi alone, and the plain
+FP64 path (FP64 FMM + FP64 block Jacobi) are timed beside it.  N GPUs
+(torchrun) each solve their own source position: weak scaling, no
 data-path collective.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
@@ -42,6 +44,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FGMRES time-to-solve @1e-4 & matvecs/s: mixed+learned vs plain FP64, 1 GB300"
 TOL = 1e-4
 RESTART = 40
+INNER_D0, INNER_PMIN, INNER_ITERS = 2.0, 4, 5   # inner-outer preconditioner (low-accuracy FMM)
 
 
 def peaks():
@@ -149,18 +152,30 @@ def build_problem(fb, W, torch, rank, forms=""):
         tune = fb.fb_operator_autotune(A32, 1)
     for op in (A32, A64):
         fb.fb_operator_use_graphs(op, True)
+    # the paper's inner-outer preconditioner: GMRES steps on a low-accuracy
+    # mixed FMM (d0 = 2, p_min = 4) with its own block Jacobi
+    Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, INNER_D0, INNER_PMIN)
+    if forms:
+        fb.fb_operator_set_forms(Alow, [0] * 13)
+    else:
+        fb.fb_operator_autotune(Alow, 1)
+    fb.fb_operator_use_graphs(Alow, True)
+    pclow = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
+    inner = fb.fb_precond_create_inner(A32, Alow, pclow, INNER_ITERS)
     g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
     fb.fb_gamma_monopole(mesh, wl.k, wl.sources[0], g)
     b = torch.empty_like(g)
     fb.fb_operator_apply(L64, g, b)
     torch.cuda.synchronize()
-    return dict(wl=wl, mesh=mesh, tree=tree, A32=A32, A64=A64, L64=L64, pc32=pc32, pc64=pc64, b=b, tune=tune)
+    return dict(wl=wl, mesh=mesh, tree=tree, A32=A32, A64=A64, L64=L64, pc32=pc32, pc64=pc64, b=b, tune=tune,
+                Alow=Alow, pclow=pclow, inner=inner)
 
 
-def train_learned(fb, W, torch, P, nsrc, steps):
-    """Learned preconditioner for the mixed operator: pairs (r, e) from
-    truncated block-Jacobi solves for `nsrc` seeded source positions other than
-    the benchmarked one, joined by as many white-noise inputs, residual
+def train_learned(fb, W, torch, P, nsrc, steps, base):
+    """Learned preconditioner for the mixed operator over `base` (block
+    Jacobi or the inner-outer preconditioner): pairs (r, e) from truncated
+    block-Jacobi solves for `nsrc` seeded source positions other than the
+    benchmarked one, joined by as many white-noise inputs, residual
     objective, Adam; the parameters kept are those with the fewest FGMRES
     iterations on one more held-out source (the initial state included).
     Returns the handle and a summary."""
@@ -189,7 +204,7 @@ def train_learned(fb, W, torch, P, nsrc, steps):
     R, E = training.augment_noise(R, E, npairs, seed=7)
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    pc = fb.fb_precond_create_learned(P["A32"], P["pc32"])
+    pc = fb.fb_precond_create_learned(P["A32"], base)
     fb.fb_learned_set_objective(pc, fb.FB_LOSS_RESIDUAL)
     bval = rhs[nsrc]
 
@@ -199,9 +214,9 @@ def train_learned(fb, W, torch, P, nsrc, steps):
         return info["iters"]
 
     x = torch.zeros_like(bval)
-    bj_val = fb.fb_fgmres_solve(P["A32"], bval, x, pc=P["pc32"], tol=TOL, restart=RESTART, maxit=3000,
-                                max_refine=4)["iters"]
-    res_bj = training.residual_error(P["A32"], P["pc32"], R[:npairs])
+    base_val = fb.fb_fgmres_solve(P["A32"], bval, x, pc=base, tol=TOL, restart=RESTART, maxit=3000,
+                                  max_refine=4)["iters"]
+    res_base = training.residual_error(P["A32"], base, R[:npairs])
     before = training.evaluate(pc, R, E)
     hist, vlog = training.train(pc, R, E, steps=steps, lr=1e-3, batch=8, validate=validate, every=10)
     after = training.evaluate(pc, R, E)
@@ -211,8 +226,8 @@ def train_learned(fb, W, torch, P, nsrc, steps):
     info = {"train_sources": nsrc, "pairs": npairs, "noise_inputs": npairs, "objective": "residual",
             "adam_steps": steps, "batch": 8, "lr": 1e-3,
             "loss_init": round(before, 5), "loss_selected": round(after, 5),
-            "residual_error_on_pairs": {"block_jacobi": round(res_bj, 4), "learned": round(res_l, 4)},
-            "validation_iterations": {"block_jacobi": bj_val, "selected": min(v for _, v in vlog),
+            "residual_error_on_pairs": {"base": round(res_base, 4), "learned": round(res_l, 4)},
+            "validation_iterations": {"base": base_val, "selected": min(v for _, v in vlog),
                                       "log": vlog[:: max(1, len(vlog) // 8)]},
             "collect_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3)}
     del R, E, Rs, Es
@@ -238,10 +253,11 @@ def rcr_flops(p_out, p_in):
     return 8.0 * (rot + coax)
 
 
-def roofline(fb, A32, tree, ph32, ph64, iters, true_mv, pk, fp32_peak, fp64_peak):
+def roofline(fb, A32, tree, ph32, ph64, iters, true_mv, pk, fp32_peak, fp64_peak, ph_low=None, low_mv=0):
     """Rooflines of the three translation kernels of a solve and the dominant
     one (largest estimated device time per step: per-launch CUDA-event phase
-    times x launches per step).  Algorithmic flops are the RCR counts of the
+    times x launches per step, the inner operator's matvecs included).
+    Algorithmic flops are the RCR counts of the
     translations each launch performs (rcr_flops)."""
     L, p, tc, pairs, nb = level_counts(fb, A32, tree)
     t_rcr = 0.0
@@ -267,10 +283,14 @@ def roofline(fb, A32, tree, ph32, ph64, iters, true_mv, pk, fp32_peak, fp64_peak
                           "alg": alg64, "peak": fp64_peak,
                           "peak_kind": "FP64 FMA throughput measured by fb_measure_alu_peaks"},
         "k_rcr<float>": {"what": "M2L of the mixed operator, RCR levels", "bound": "alu", "launch_ms": t32 * 1e3,
-                         "per_step_ms": (ph32["m2l"] + ph32["m2m"] + ph32["l2l"]) * iters, "alg": alg32,
+                         "per_step_ms": (ph32["m2l"] + ph32["m2m"] + ph32["l2l"]) * iters
+                         + ((ph_low["m2l"] + ph_low["m2m"] + ph_low["l2l"]) * low_mv if ph_low else 0.0),
+                         "alg": alg32,
                          "peak": fp32_peak, "peak_kind": "FP32 FMA throughput measured by fb_measure_alu_peaks"},
         "k_trans_tc": {"what": "M2L of the mixed operator, tensor-core levels (tcgen05 3xTF32)", "bound": "tensor",
-                       "launch_ms": ttc * 1e3, "per_step_ms": ph32["m2l_tc"] * iters, "alg": algtc,
+                       "launch_ms": ttc * 1e3,
+                       "per_step_ms": ph32["m2l_tc"] * iters + (ph_low["m2l_tc"] * low_mv if ph_low else 0.0),
+                       "alg": algtc,
                        "peak": tf32 / 3.0,
                        "peak_kind": "measured BF16 burst x 1.1/2.25 (TF32) / 3 split passes, of measured"},
     }
@@ -325,11 +345,12 @@ def run_ours(args):
     n = wl.n
     stream = torch.cuda.current_stream()
     learned_info = None
+    base = P["inner"] if args.base == "inner" else P["pc32"]
     if args.precond == "learned":
-        pc_main, learned_info = train_learned(fb, W, torch, P, args.train_sources, args.train_steps)
+        pc_main, learned_info = train_learned(fb, W, torch, P, args.train_sources, args.train_steps, base)
         fb.fb_precond_use_graphs(pc_main, True)
     else:
-        pc_main = P["pc32"]
+        pc_main = base
 
     def solve_mixed(x, pc=pc_main):
         return fb.fb_fgmres_solve(P["A32"], P["b"], x, pc=pc, tol=TOL, restart=RESTART, maxit=3000,
@@ -399,6 +420,20 @@ def run_ours(args):
     torch.cuda.synchronize()
     mv64_ms = b0.elapsed_time(b1) / nmv64
     ph64 = fb.fb_operator_apply_timed(P["A64"], xv, yv)
+    ph_low = fb.fb_operator_apply_timed(P["Alow"], xv, yv)
+
+    # the same mixed solve under the inner-outer preconditioner alone
+    io_t, io_infos = [], []
+    for _ in range(3):
+        xb = torch.zeros_like(P["b"])
+        d0 = torch.cuda.Event(enable_timing=True)
+        d1 = torch.cuda.Event(enable_timing=True)
+        d0.record(stream)
+        io_infos.append(solve_mixed(xb, P["inner"]))
+        d1.record(stream)
+        torch.cuda.synchronize()
+        io_t.append(d0.elapsed_time(d1) / 1e3)
+    io_s = statistics.median(io_t)
 
     # the same mixed solve under block Jacobi alone
     bj_t, bj_infos = [], []
@@ -460,8 +495,9 @@ def run_ours(args):
     e2e_s = statistics.median(e2e_t)
 
     fp32_peak, fp64_peak = fb.fb_measure_alu_peaks()
+    low_mv = iters * INNER_ITERS if args.base == "inner" else 0
     rf, kernels = roofline(fb, P["A32"], P["tree"], ph, ph64, iters, res_true_matvecs(infos), pk, fp32_peak,
-                           fp64_peak)
+                           fp64_peak, ph_low, low_mv)
     res = {
         "metric": METRIC,
         "value": round(ws / (ms_step / 1e3), 4),
@@ -476,10 +512,12 @@ def run_ours(args):
         "dtype": "f32+f64",
         "data": "synthetic",
         "config": {"workload": "shoebox 3.0x2.4x2.0 m, 1 kHz, N=39368 flat triangles (lambda/8), "
-                               f"beta=0.2, FMM leaf<=64, d0=6 pmin=12, FGMRES(40)+{args.precond}, tol 1e-4",
+                               f"beta=0.2, FMM leaf<=64, d0=6 pmin=12, FGMRES(40)+{args.precond}({args.base}), tol 1e-4",
                    "n_elements": n, "frequency_hz": wl.freq_hz, "solver": "FGMRES restart 40",
-                   "precond": ("learned octree network over block Jacobi (BF16 tensor-core kernels)"
-                               if args.precond == "learned" else "block-Jacobi (leaf self blocks)"),
+                   "precond": (("learned octree network (BF16 tensor-core kernels) over " if args.precond == "learned"
+                                else "") + ("inner-outer: 5 GMRES steps on a low-accuracy mixed FMM (d0=2, "
+                                            "p_min=4) with block Jacobi" if args.base == "inner"
+                                            else "block Jacobi (leaf self blocks)")),
                    "operator": "mixed FP32 FMM, FP64 Arnoldi",
                    "true_residual": "FP64 FMM", "l2": "working set > L2 (translation matrices alone > 129 MB)",
                    "parallelism": f"replicas x{ws} (one (f, source) solve per GPU)"},
@@ -492,6 +530,10 @@ def run_ours(args):
         "phase_ms": {k: round(v, 4) for k, v in ph.items()},
         "pc_fallbacks": max(i.get("pc_fallbacks", 0) for i in infos),
         "learned": learned_info,
+        "mixed_inner_outer": {"time_to_solve_s": round(io_s, 5), "iterations": io_infos[-1]["iters"],
+                              "true_relres": io_infos[-1]["true_relres"],
+                              "inner": {"d0": INNER_D0, "p_min": INNER_PMIN, "iters": INNER_ITERS,
+                                        "preconditioner": "block Jacobi of the inner operator"}},
         "mixed_block_jacobi": {"time_to_solve_s": round(bj_s, 5), "iterations": bj_infos[-1]["iters"],
                                "true_relres": bj_infos[-1]["true_relres"]},
         "plain_fp64": {"time_to_solve_s": round(t64, 4), "iterations": info64["iters"],
@@ -512,7 +554,9 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        res["cpu_baseline"] = cpu_baseline(wl, iters + res_true_matvecs(infos), budget_s=args.cpu_seconds)
+        # the oracle's dense matvec, counted like the plain method's solve
+        # (block-Jacobi iterations + one true residual), as the reference arm does
+        res["cpu_baseline"] = cpu_baseline(wl, bj_infos[-1]["iters"] + 1, budget_s=args.cpu_seconds)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -585,7 +629,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precond", default="learned", choices=["learned", "bj"])
+    ap.add_argument("--precond", default="learned", choices=["learned", "base"])
+    ap.add_argument("--base", default="inner", choices=["inner", "bj"],
+                    help="preconditioner the learned network refines (or used alone with --precond base)")
     ap.add_argument("--forms", default="", help="fixed per-level translation forms instead of autotuning "
                                                 "(comma-separated choice ints by level, as fb_operator_set_forms)")
     ap.add_argument("--train-sources", type=int, default=4)

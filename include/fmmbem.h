@@ -319,6 +319,18 @@ FB_API void fb_precond_destroy(fb_precond* pc);
  * Errors: FB_ERR_ARG for NULL or overlapping arrays. */
 FB_API fb_status fb_precond_apply(const fb_precond* pc, const double* x, double* y, int memspace, void* stream);
 
+/* Inner-outer preconditioner (Sec. 4: flexible GMRES preconditioned by a few
+ * GMRES iterations of a low-accuracy FMM): P(v) = d_k, the k-step GMRES
+ * approximation (zero initial guess, one cycle, no restart) of
+ * inner_op d = v, right-preconditioned by inner_pc (e.g. block Jacobi of
+ * inner_op; may be NULL).  op is the outer operator the preconditioner is
+ * used with (its size must match inner_op's); inner_op and inner_pc must
+ * outlive it.  The inner steps run without host synchronisation.  P is not a
+ * fixed linear map, which flexible GMRES admits.  Errors: FB_ERR_ARG. */
+#define FB_PC_INNER 3
+FB_API fb_status fb_precond_create_inner(fb_op* op, fb_op* inner_op, const fb_precond* inner_pc, int iters,
+                                         void* stream, fb_precond** out);
+
 /* Learned octree preconditioner (the variable preconditioner that flexible
  * GMRES admits, Sec. 3.1 / Sec. 4): z = BJ(v) + s ph N(conj(ph) v / s,
  * conj(ph) BJ(v) / s), where BJ is the block-Jacobi `base` of the same FMM
@@ -330,7 +342,9 @@ FB_API fb_status fb_precond_apply(const fb_precond* pc, const double* x, double*
  * on the tensor cores in BF16 with FP32 accumulation; parameters, gradients
  * and Adam moments are FP32.  Parameters start from a deterministic seeded
  * initialisation with a small output layer (close to block Jacobi).
- * Errors: FB_ERR_ARG if base is not block Jacobi of op. */
+ * The base may also be an inner-outer preconditioner of op (FB_PC_INNER);
+ * the network then refines its output the same way.
+ * Errors: FB_ERR_ARG if base is neither block Jacobi nor inner-outer of op. */
 FB_API fb_status fb_precond_create_learned(fb_op* op, const fb_precond* base, uint64_t seed, void* stream,
                                            fb_precond** out);
 

@@ -30,6 +30,7 @@ __all__ = [
     "fb_precond_apply", "fb_fgmres_solve", "fb_eval_field", "fb_operator_apply_timed", "fb_kernel_launches",
     "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
     "fb_precond_create_learned", "fb_learned_params", "fb_learned_set_objective",
+    "fb_precond_create_inner", "FB_PC_INNER", "FB_PC_LEARNED",
     "FB_LOSS_ERROR", "FB_LOSS_RESIDUAL", "fb_learned_loss_and_grad", "fb_learned_train_step",
     "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune", "fb_operator_set_forms", "fb_batch_solve", "fb_operator_use_graphs", "fb_precond_use_graphs",
     "SolverOpts", "SolveInfo",
@@ -510,6 +511,18 @@ def fb_measure_alu_peaks(stream=None):
 
 
 FB_PC_LEARNED = 2
+FB_PC_INNER = 3
+lib.fb_precond_create_inner.restype = C.c_int
+lib.fb_precond_create_inner.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                        C.POINTER(C.c_void_p)]
+
+
+def fb_precond_create_inner(op, inner_op, inner_pc=None, iters=4, stream=None):
+    """Inner-outer preconditioner: `iters` GMRES steps on inner_op (right-
+    preconditioned by inner_pc) per application."""
+    out = C.c_void_p()
+    _check(lib.fb_precond_create_inner(op, inner_op, inner_pc, int(iters), _stream(stream), C.byref(out)))
+    return out
 lib.fb_precond_create_learned.restype = C.c_int
 lib.fb_precond_create_learned.argtypes = [C.c_void_p, C.c_void_p, C.c_uint64, C.c_void_p, C.POINTER(C.c_void_p)]
 lib.fb_learned_params.restype = C.c_int

@@ -468,12 +468,37 @@ fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out)
 
 void fb_precond_destroy(fb_precond* pc) { fb_precond_free(pc); }
 
+fb_status fb_precond_create_inner(fb_op* op, fb_op* inner_op, const fb_precond* inner_pc, int iters, void* stream,
+                                  fb_precond** out) {
+    if (!op || !inner_op || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    if (inner_op->n != op->n) return fb_fail(FB_ERR_ARG, "inner operator size differs");
+    if (iters < 1 || iters > 200) return fb_fail(FB_ERR_ARG, "iters must be in [1, 200]");
+    if (inner_pc && inner_pc->op != inner_op)
+        return fb_fail(FB_ERR_ARG, "the inner preconditioner must belong to the inner operator");
+    fb_precond* pc = new fb_precond();
+    pc->op = op;
+    pc->kind = FB_PC_INNER;
+    pc->n = op->n;
+    pc->inner_op = inner_op;
+    pc->inner_its = iters;
+    pc->base = inner_pc;
+    fb_status st = fb_inner_create(pc, as_stream(stream));
+    if (st != FB_OK) {
+        fb_precond_free(pc);
+        return st;
+    }
+    *out = pc;
+    return FB_OK;
+}
+
 fb_status fb_precond_create_learned(fb_op* op, const fb_precond* base, uint64_t seed, void* stream,
                                     fb_precond** out) {
     if (!op || !base || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
     *out = nullptr;
-    if (base->kind != FB_PC_BLOCK_JACOBI || base->op != op)
-        return fb_fail(FB_ERR_ARG, "the base must be a block-Jacobi preconditioner of the same operator");
+    if ((base->kind != FB_PC_BLOCK_JACOBI && base->kind != FB_PC_INNER) || base->op != op)
+        return fb_fail(FB_ERR_ARG, "the base must be a block-Jacobi or inner-outer preconditioner of the same "
+                                   "operator");
     cudaStream_t s = as_stream(stream);
     fb_precond* pc = new fb_precond();
     pc->op = op;

@@ -341,7 +341,14 @@ struct fb_precond {
     const fb_precond* base = nullptr;
     int use_graphs = 0;            // CUDA-graph replay of the apply (fb_precond_use_graphs)
     void* graphs = nullptr;
+    // inner-outer preconditioner: `inner_its` GMRES steps on `inner_op`
+    // (right-preconditioned by `base`), work buffers in `inner`
+    fb_op* inner_op = nullptr;
+    int inner_its = 0;
+    void* inner = nullptr;
 };
+fb_status fb_inner_create(fb_precond* pc, cudaStream_t s);
+void fb_inner_free(void*& inner);
 
 // ------------------------------------------------------ launch counting ----
 // Running total of kernel launches issued by the library (tracing aid,

@@ -56,6 +56,12 @@ static void drop_entry(GraphEntry& e) {
 fb_status fb_graph_run(void*& cache, int key, int64_t in_elems, int64_t out_elems, const cd* x, cd* y,
                        cudaStream_t s, const std::function<fb_status(const cd*, cd*, cudaStream_t)>& body,
                        const long long* gen) {
+    // inside another object's capture (e.g. a preconditioner whose base
+    // applies a graphed operator): run the body directly, it is captured
+    // into the enclosing graph
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FB_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return body(x, y, s);
     if (!cache) cache = new GraphCache();
     GraphCache* gc = (GraphCache*)cache;
     auto it = gc->m.find(key);

@@ -163,7 +163,9 @@ __device__ void backsolve(const Hess& hs, int j1) {
         for (int q = i + 1; q < j1; ++q) acc = acc - hs.H[q * ld + i] * hs.y[q];
         cd d = hs.H[i * ld + i];
         double dd = abs2(d);
-        hs.y[i] = (1.0 / dd) * (acc * conjg(d));
+        // a zero pivot only follows an exact breakdown (or a zero right-hand
+        // side); the Krylov space ended there, so the coefficient is 0
+        hs.y[i] = dd > 0.0 ? (1.0 / dd) * (acc * conjg(d)) : mk(0.0, 0.0);
     }
 }
 __global__ void k_backsolve(Hess hs, int j1) { backsolve(hs, j1); }
@@ -199,6 +201,94 @@ struct Work {
         if (host) cudaFreeHost(host);
     }
 };
+
+static fb_status work_alloc(Work& W, int64_t n, int m, bool with_z) {
+    W.n = n;
+    W.m = m;
+    FB_CHECK(dalloc(&W.V, (size_t)(m + 1) * n));
+    if (with_z) FB_CHECK(dalloc(&W.Z, (size_t)m * n));
+    FB_CHECK(dalloc(&W.w, n));
+    FB_CHECK(dalloc(&W.r, n));
+    FB_CHECK(dalloc(&W.d, n));
+    FB_CHECK(dalloc(&W.tmp, n));
+    size_t nsmall = (size_t)(m + 1) * m + 4 * (m + 1) + 2 * m + 8;
+    FB_CHECK(dalloc(&W.small, nsmall));
+    FB_CHECK(dalloc(&W.scal, 8));
+    FB_CUDA(cudaMallocHost((void**)&W.host, sizeof(double) * 4));
+    cd* sp = W.small;
+    W.hs.m = m;
+    W.hs.H = sp; sp += (size_t)(m + 1) * m;
+    W.hs.cs = sp; sp += m + 1;
+    W.hs.sn = sp; sp += m + 1;
+    W.hs.g = sp; sp += m + 1;
+    W.hs.h = sp; sp += m + 1;
+    W.hs.y = sp;
+    W.hs.nrm2 = W.scal;
+    W.hs.inv = W.scal + 1;
+    W.hs.est = W.scal + 2;
+    return FB_OK;
+}
+
+// k steps of GMRES (one cycle, no restart, no host synchronisation) on
+// A d = rhs from d = 0, right-preconditioned by pc; the result in W.d.  Used
+// as the inner solver of the inner-outer preconditioner (Sec. 4: FGMRES
+// preconditioned by a few GMRES iterations on a low-accuracy FMM).
+static fb_status gmres_fixed(fb_op* A, const fb_precond* pc, Work& W, const cd* rhs, int k, cudaStream_t s) {
+    const int64_t n = W.n;
+    FB_CUDA(cudaMemsetAsync(W.d, 0, sizeof(cd) * n, s));
+    FB_CHECK(norm2(rhs, n, W.hs.nrm2, s));
+    k_cycle_start<<<1, 1, 0, s>>>(W.hs);
+    k_scale<<<grid_for(n), KB, 0, s>>>(W.V, rhs, n, W.hs.inv);
+    FB_LAUNCH_CHECK();
+    cnt(2);
+    for (int j = 0; j < k; ++j) {
+        cd* vj = W.V + (int64_t)j * n;
+        cd* zj = vj;
+        if (pc) {
+            zj = W.Z + (int64_t)j * n;
+            FB_CHECK(fb_pc_apply(pc, vj, zj, s));
+        }
+        FB_CHECK(fb_apply_any(A, zj, W.w, s));
+        for (int pass = 0; pass < 2; ++pass) {
+            FB_CUDA(cudaMemsetAsync(W.hs.h, 0, sizeof(cd) * (j + 1), s));
+            dim3 g(std::min(grid_for(n), 64), j + 1);
+            k_mdot<<<g, KB, 0, s>>>(W.V, n, W.w, W.hs.h);
+            k_gs_update<<<grid_for(n), KB, 0, s>>>(W.V, n, j + 1, W.hs.h, W.w);
+            k_accum_h<<<1, 1024, 0, s>>>(W.hs, j);
+            cnt(3);
+        }
+        FB_CHECK(norm2(W.w, n, W.hs.nrm2, s));
+        k_arnoldi_close<<<1, 1, 0, s>>>(W.hs, j);
+        k_scale<<<grid_for(n), KB, 0, s>>>(W.V + (int64_t)(j + 1) * n, W.w, n, W.hs.inv);
+        FB_LAUNCH_CHECK();
+        cnt(2);
+    }
+    k_backsolve<<<1, 1, 0, s>>>(W.hs, k);
+    k_update_x<<<grid_for(n), KB, 0, s>>>(W.d, pc ? W.Z : W.V, n, k, W.hs.y);
+    FB_LAUNCH_CHECK();
+    cnt(2);
+    return FB_OK;
+}
+
+struct InnerSolver {
+    Work W;
+};
+
+fb_status fb_inner_create(fb_precond* pc, cudaStream_t s) {
+    InnerSolver* in = new InnerSolver();
+    fb_status st = work_alloc(in->W, pc->n, pc->inner_its, pc->base != nullptr);
+    if (st != FB_OK) {
+        delete in;
+        return st;
+    }
+    pc->inner = in;
+    return FB_OK;
+}
+
+void fb_inner_free(void*& inner) {
+    delete (InnerSolver*)inner;
+    inner = nullptr;
+}
 
 // Inner restarted FGMRES on A d = rhs from d = 0 until the Arnoldi estimate
 // reaches rel_tol * ||rhs|| or the iteration budget is spent.
@@ -290,29 +380,7 @@ fb_status fb_fgmres_impl(fb_op* A, fb_precond* pc, const cd* b, cd* x, const fb_
     int64_t n = A->n;
     int m = opts.restart;
     Work W;
-    W.n = n;
-    W.m = m;
-    FB_CHECK(dalloc(&W.V, (size_t)(m + 1) * n));
-    if (pc) FB_CHECK(dalloc(&W.Z, (size_t)m * n));
-    FB_CHECK(dalloc(&W.w, n));
-    FB_CHECK(dalloc(&W.r, n));
-    FB_CHECK(dalloc(&W.d, n));
-    FB_CHECK(dalloc(&W.tmp, n));
-    size_t nsmall = (size_t)(m + 1) * m + 4 * (m + 1) + 2 * m + 8;
-    FB_CHECK(dalloc(&W.small, nsmall));
-    FB_CHECK(dalloc(&W.scal, 8));
-    FB_CUDA(cudaMallocHost((void**)&W.host, sizeof(double) * 4));
-    cd* sp = W.small;
-    W.hs.m = m;
-    W.hs.H = sp; sp += (size_t)(m + 1) * m;
-    W.hs.cs = sp; sp += m + 1;
-    W.hs.sn = sp; sp += m + 1;
-    W.hs.g = sp; sp += m + 1;
-    W.hs.h = sp; sp += m + 1;
-    W.hs.y = sp;
-    W.hs.nrm2 = W.scal;
-    W.hs.inv = W.scal + 1;
-    W.hs.est = W.scal + 2;
+    FB_CHECK(work_alloc(W, n, m, pc != nullptr));
     double* bnorm2 = W.scal + 3;
 
     fb_solve_info inf{};
@@ -903,6 +971,14 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
 
 fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, int nrhs) {
     const int64_t n = pc->n;
+    if (pc->kind == FB_PC_INNER) {
+        InnerSolver* in = (InnerSolver*)pc->inner;
+        for (int r = 0; r < nrhs; ++r) {
+            FB_CHECK(gmres_fixed(pc->inner_op, pc->base, in->W, x + r * n, pc->inner_its, s));
+            FB_CUDA(cudaMemcpyAsync(y + r * n, in->W.d, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s));
+        }
+        return FB_OK;
+    }
     if (pc->net) {
         if (pc->use_graphs) {
             fb_precond* mpc = const_cast<fb_precond*>(pc);
@@ -935,6 +1011,7 @@ fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, 
 
 void fb_precond_free(fb_precond* pc) {
     if (!pc) return;
+    fb_inner_free(pc->inner);
     fb_graph_free(pc->graphs);
     fb_learned_free(pc->net);
     dfree(pc->blk_off);

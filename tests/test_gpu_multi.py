@@ -163,3 +163,44 @@ def test_graph_replay_matches(setup):
         fb.fb_precond_destroy(bj)
     finally:
         fb.fb_operator_use_graphs(A, False)
+
+
+def test_inner_outer_preconditioner(setup):
+    """FGMRES preconditioned by a few GMRES steps on a low-accuracy FMM
+    (Sec. 4): one inner step reproduces block Jacobi (a scaled copy of its
+    output, so the same outer iterations); four inner steps need fewer outer
+    iterations; both meet the FP64 true-residual tolerance."""
+    wl, mesh, op = setup
+    A = op(fb.FB_PREC_MIXED_FMM)
+    A64 = op(fb.FB_PREC_FP64_FMM)
+    tree = fb.fb_tree_build(mesh, 64)
+    Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 2.0, 6)
+    bj = fb.fb_precond_create(A, fb.FB_PC_BLOCK_JACOBI)
+    bjl = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
+    pcs = {k: fb.fb_precond_create_inner(A, Alow, bjl, k) for k in (1, 4)}
+    try:
+        b = torch.tensor(seeded_vector(wl.n, 77), device="cuda")
+        its = {}
+        for name, pc in (("bj", bj), ("inner1", pcs[1]), ("inner4", pcs[4])):
+            x = torch.zeros_like(b)
+            info = fb.fb_fgmres_solve(A, b, x, pc=pc, tol=1e-6, restart=30, true_op=A64)
+            assert info["status"] == 0 and info["true_relres"] <= 1e-6, name
+            its[name] = info["iters"]
+        # the learned network over the inner-outer base (graph replay of both)
+        pcl = fb.fb_precond_create_learned(A, pcs[4])
+        fb.fb_precond_use_graphs(pcl, True)
+        x = torch.zeros_like(b)
+        info = fb.fb_fgmres_solve(A, b, x, pc=pcl, tol=1e-6, restart=30, true_op=A64)
+        fb.fb_precond_destroy(pcl)
+        assert info["status"] == 0 and info["true_relres"] <= 1e-6
+        its["learned_over_inner4"] = info["iters"]
+        print("outer iterations", its)
+        assert abs(its["inner1"] - its["bj"]) <= 1
+        assert its["inner4"] < its["bj"]
+    finally:
+        for pc in pcs.values():
+            fb.fb_precond_destroy(pc)
+        fb.fb_precond_destroy(bjl)
+        fb.fb_precond_destroy(bj)
+        fb.fb_operator_destroy(Alow)
+        fb.fb_tree_destroy(tree)
