@@ -328,6 +328,13 @@ FB_API fb_status fb_precond_apply(const fb_precond* pc, const double* x, double*
  * outlive it.  The inner steps run without host synchronisation.  P is not a
  * fixed linear map, which flexible GMRES admits.  Errors: FB_ERR_ARG. */
 #define FB_PC_INNER 3
+
+/* Training-data helper for learned preconditioners: the first k+1 Arnoldi
+ * vectors of the right-preconditioned Krylov space of A from start vector b
+ * (the vectors a preconditioner receives in the first k iterations of
+ * flexible GMRES), computed by k GMRES steps with CGS2.  b: N complex,
+ * V: (k+1) x N complex, both device.  Errors: FB_ERR_ARG. */
+FB_API fb_status fb_krylov_basis(fb_op* A, const fb_precond* pc, const double* b, int k, double* V, void* stream);
 FB_API fb_status fb_precond_create_inner(fb_op* op, fb_op* inner_op, const fb_precond* inner_pc, int iters,
                                          void* stream, fb_precond** out);
 

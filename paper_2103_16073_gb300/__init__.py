@@ -30,7 +30,7 @@ __all__ = [
     "fb_precond_apply", "fb_fgmres_solve", "fb_eval_field", "fb_operator_apply_timed", "fb_kernel_launches",
     "fb_operator_apply_noalloc", "fb_operator_set_translation", "fb_measure_alu_peaks",
     "fb_precond_create_learned", "fb_learned_params", "fb_learned_set_objective",
-    "fb_precond_create_inner", "FB_PC_INNER", "FB_PC_LEARNED",
+    "fb_precond_create_inner", "FB_PC_INNER", "FB_PC_LEARNED", "fb_krylov_basis",
     "FB_LOSS_ERROR", "FB_LOSS_RESIDUAL", "fb_learned_loss_and_grad", "fb_learned_train_step",
     "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune", "fb_operator_set_forms", "fb_batch_solve", "fb_operator_use_graphs", "fb_precond_use_graphs",
     "SolverOpts", "SolveInfo",
@@ -515,6 +515,22 @@ FB_PC_INNER = 3
 lib.fb_precond_create_inner.restype = C.c_int
 lib.fb_precond_create_inner.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
                                         C.POINTER(C.c_void_p)]
+
+
+lib.fb_krylov_basis.restype = C.c_int
+lib.fb_krylov_basis.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]
+
+
+def fb_krylov_basis(A, pc, b, k, stream=None):
+    """First k+1 Arnoldi vectors (CUDA complex128 [k+1, N]) of the right-
+    preconditioned Krylov space of A from b (CUDA complex128 [N])."""
+    import torch
+    if not _is_cuda_tensor(b):
+        raise ValueError("b must be a CUDA tensor")
+    V = torch.empty((int(k) + 1, b.numel()), dtype=b.dtype, device=b.device)
+    _check(lib.fb_krylov_basis(A, pc, C.c_void_p(b.data_ptr()), int(k), C.c_void_p(V.data_ptr()),
+                               _stream(stream)))
+    return V
 
 
 def fb_precond_create_inner(op, inner_op, inner_pc=None, iters=4, stream=None):

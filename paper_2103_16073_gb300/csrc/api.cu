@@ -24,6 +24,7 @@ fb_status fb_fgmres_multi_impl(fb_op*, fb_precond*, const cd*, cd*, int, const f
                                cudaStream_t);
 fb_status fb_precond_create_impl(fb_op*, int, cudaStream_t, fb_precond**);
 fb_status fb_batch_solve_impl(fb_batch_job*, int, const fb_batch_opts*);
+fb_status fb_krylov_basis_impl(fb_op*, const fb_precond*, const cd*, int, cd*, cudaStream_t);
 void fb_precond_free(fb_precond*);
 fb_status fb_alu_peaks_impl(double*, double*, cudaStream_t);
 
@@ -467,6 +468,13 @@ fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out)
 }
 
 void fb_precond_destroy(fb_precond* pc) { fb_precond_free(pc); }
+
+fb_status fb_krylov_basis(fb_op* A, const fb_precond* pc, const double* b, int k, double* V, void* stream) {
+    if (!A || !b || !V) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (k < 1 || k > 200) return fb_fail(FB_ERR_ARG, "k must be in [1, 200]");
+    if (pc && pc->op != A) return fb_fail(FB_ERR_ARG, "preconditioner built for another operator");
+    return fb_krylov_basis_impl(A, pc, (const cd*)b, k, (cd*)V, as_stream(stream));
+}
 
 fb_status fb_precond_create_inner(fb_op* op, fb_op* inner_op, const fb_precond* inner_pc, int iters, void* stream,
                                   fb_precond** out) {

@@ -274,6 +274,18 @@ struct InnerSolver {
     Work W;
 };
 
+// The first k+1 Arnoldi vectors of the right-preconditioned Krylov space of
+// A for the start vector b (the inputs a preconditioner sees in the first k
+// iterations of a solve), written to V [(k+1) x N].
+fb_status fb_krylov_basis_impl(fb_op* A, const fb_precond* pc, const cd* b, int k, cd* V, cudaStream_t s) {
+    Work W;
+    FB_CHECK(work_alloc(W, A->n, k, pc != nullptr));
+    FB_CHECK(gmres_fixed(A, pc, W, b, k, s));
+    FB_CUDA(cudaMemcpyAsync(V, W.V, sizeof(cd) * (size_t)(k + 1) * A->n, cudaMemcpyDeviceToDevice, s));
+    FB_CUDA(cudaStreamSynchronize(s));
+    return FB_OK;
+}
+
 fb_status fb_inner_create(fb_precond* pc, cudaStream_t s) {
     InnerSolver* in = new InnerSolver();
     fb_status st = work_alloc(in->W, pc->n, pc->inner_its, pc->base != nullptr);

@@ -40,6 +40,14 @@ def collect_pairs(A, bj, b, iterates=(1, 2, 3, 4, 6, 8, 10, 13, 16), restart=40,
     return R, E
 
 
+def krylov_inputs(A, pc, b, k=6):
+    """Inputs the preconditioner meets inside a solve: the first k+1
+    Arnoldi vectors of the solve of A x = b preconditioned by pc (residual
+    objective only; returned with zero E rows)."""
+    V = fb.fb_krylov_basis(A, pc, b, k)
+    return V, torch.zeros_like(V)
+
+
 def augment_noise(R, E, count, seed=0):
     """Appends `count` white-noise inputs (for the residual objective only;
     their E rows are zero and unused)."""

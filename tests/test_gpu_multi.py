@@ -204,3 +204,27 @@ def test_inner_outer_preconditioner(setup):
         fb.fb_precond_destroy(bj)
         fb.fb_operator_destroy(Alow)
         fb.fb_tree_destroy(tree)
+
+
+def test_krylov_basis_is_arnoldi(setup):
+    """fb_krylov_basis returns an orthonormal basis that starts at b/||b||
+    and satisfies the Arnoldi relation A V_j in span(V_0..V_{j+1})."""
+    wl, mesh, op = setup
+    A = op(fb.FB_PREC_MIXED_FMM)
+    b = torch.tensor(seeded_vector(wl.n, 77), device="cuda")
+    k = 5
+    V = fb.fb_krylov_basis(A, None, b, k)
+    assert V.shape == (k + 1, wl.n)
+    Vn = V.cpu().numpy()
+    G = Vn.conj() @ Vn.T
+    assert np.max(np.abs(G - np.eye(k + 1))) < 1e-10
+    bn = b.cpu().numpy()
+    assert rel(Vn[0], bn / np.linalg.norm(bn)) < 1e-13
+    y = torch.empty_like(b)
+    for j in range(k):
+        fb.fb_operator_apply(A, V[j].contiguous(), y)
+        w = y.cpu().numpy()
+        proj = Vn[:j + 2].T @ (Vn[:j + 2].conj() @ w)
+        assert rel(proj, w) < 1e-6, j
+    with pytest.raises(fb.FBError):
+        fb.fb_krylov_basis(A, None, b, 0)
