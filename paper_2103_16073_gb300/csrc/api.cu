@@ -320,7 +320,13 @@ fb_status fb_operator_set_translation(fb_op* op, int method) {
     if (method < FB_TRANS_AUTO || method > FB_TRANS_TENSOR) return fb_fail(FB_ERR_ARG, "unknown translation method");
     if (method == FB_TRANS_TENSOR && op->prec != FB_PREC_MIXED_FMM)
         return fb_fail(FB_ERR_ARG, "tensor-core translations need the mixed precision");
-    if (method == FB_TRANS_COMPOSED || method == FB_TRANS_TENSOR) FB_CHECK(fb_compose_all(op, nullptr));
+    if (method == FB_TRANS_COMPOSED || method == FB_TRANS_TENSOR) {
+        for (int l = 2; l <= op->L; ++l)
+            if (!fb_composable(op, l, l >= 3))
+                return fb_fail(FB_ERR_ARG, "composed and tensor-core translations need every level's order <= " +
+                                               std::to_string(FB_COMPOSE_PMAX));
+        FB_CHECK(fb_compose_all(op, nullptr));
+    }
     if (method == FB_TRANS_TENSOR) {
         if (!op->tc_plan_all) {
             std::vector<int> all;
@@ -333,6 +339,7 @@ fb_status fb_operator_set_translation(fb_op* op, int method) {
             FB_CUDA(cudaStreamSynchronize(nullptr));
         }
     }
+    if (op->method != method) op->buf_gen++;   // captured graphs hold the previous method
     op->method = method;
     fb_graph_free(op->graphs);
     return FB_OK;
@@ -368,7 +375,10 @@ fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream) {
     if (!op || !choice) return fb_fail(FB_ERR_ARG, "NULL argument");
     fb_graph_free(op->graphs);
     fb_status st = fb_set_forms_impl(op, choice, as_stream(stream));
-    if (st == FB_OK) op->method = FB_TRANS_AUTO;
+    if (st == FB_OK) {
+        op->method = FB_TRANS_AUTO;
+        op->buf_gen++;
+    }
     return st;
 }
 
@@ -419,6 +429,7 @@ fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t inde
             }
         } else if (which == 3) {
             if (level < 2 || level > L || index < 0 || index >= FB_NOFF) return fb_fail(FB_ERR_ARG, "bad level/offset");
+            if (!fb_composable(op, level, false)) return fb_fail(FB_ERR_ARG, "no composed matrix above order 32");
             FB_CHECK(fb_compose_all(const_cast<fb_op*>(op), nullptr));
             int64_t off = op->m2l_toff[(size_t)level * FB_NOFF + index];
             if (off < 0) return fb_fail(FB_ERR_ARG, "offset not used at this level");
@@ -426,6 +437,7 @@ fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t inde
             cnt = (int64_t)op->p[level] * op->p[level] * op->p[level] * op->p[level];
         } else if (which == 4 || which == 5) {
             if (level < 3 || level > L || index < 0 || index > 7) return fb_fail(FB_ERR_ARG, "bad level/octant");
+            if (!fb_composable(op, level, true)) return fb_fail(FB_ERR_ARG, "no composed matrix above order 32");
             FB_CHECK(fb_compose_all(const_cast<fb_op*>(op), nullptr));
             int64_t off = which == 4 ? op->m2m_toff[level][index] : op->l2l_toff[level][index];
             if (off < 0) return fb_fail(FB_ERR_ARG, "octant not used at this level");

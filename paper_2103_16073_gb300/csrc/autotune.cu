@@ -148,7 +148,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                 up.push_back(TcGroup{op->m2m_job[l][o], g0, (int32_t)(g1 - g0), l, l - 1});
                 down.push_back(TcGroup{op->l2l_job[l][o], g0, (int32_t)(g1 - g0), l - 1, l});
             }
-            if (!up.empty()) {
+            if (!up.empty() && fb_composable(op, l, true)) {
                 FB_CHECK(fb_compose_jobs(op, need, s));
                 if (!op->tc_m2m[l])
                     FB_CHECK(fb_tc_build_groups(op, up, t->oct_child[l], t->oct_parent[l], &op->tc_m2m[l], s));
@@ -186,6 +186,7 @@ fb_status fb_install_forms(fb_op* op, const std::vector<int>& tc_m2l, cudaStream
         FB_CHECK(fb_compose_jobs(op, need, s));
     }
     FB_CUDA(cudaStreamSynchronize(s));
+    op->buf_gen++;   // captured graphs refer to the plans replaced here
     fb_tc_free(op->tc_plan);
     free_rcr(op->m2l_rcr_rest);
     op->m2l_rcr_rest.h_tasks.clear();
@@ -212,11 +213,18 @@ fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s) {
     const int L = op->L;
     std::vector<int> tc_m2l;
     for (int l = 2; l <= L; ++l) {
+        if ((choice[l] & 1) && !fb_composable(op, l, false))
+            return fb_fail(FB_ERR_ARG, "tensor-core M2L needs order <= " + std::to_string(FB_COMPOSE_PMAX));
+        if (l >= 3 && (choice[l] & 2) && !fb_composable(op, l, true))
+            return fb_fail(FB_ERR_ARG, "tensor-core M2M/L2L needs order <= " + std::to_string(FB_COMPOSE_PMAX));
+    }
+    for (int l = 2; l <= L; ++l) {
         if (choice[l] & 1) tc_m2l.push_back(l);
         if (l < 3) continue;
         bool want = (choice[l] & 2) != 0;
         if (!want) {
             FB_CUDA(cudaStreamSynchronize(s));
+            op->buf_gen++;
             fb_tc_free(op->tc_m2m[l]);
             fb_tc_free(op->tc_l2l[l]);
         } else if (!op->tc_m2m[l] || !op->tc_l2l[l]) {

@@ -376,6 +376,15 @@ fb_status fb_rcr_run_op(fb_op* op, RcrPlan& pl, void* src, void* dst, cudaStream
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times, int* choice);
 fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s);
 fb_status fb_compose_all(fb_op* op, cudaStream_t s);
+// Composed p^2 x p^2 translation matrices exist only for orders up to this
+// bound: above it one matrix outgrows the RCR arithmetic it replaces (the
+// dense form costs ~p/4 times RCR) and a level's set reaches tens of GB.
+constexpr int FB_COMPOSE_PMAX = 32;
+// M2L of level l (pair = false) or M2M/L2L between levels l-1 and l (pair = true)
+// has composed matrices.
+inline bool fb_composable(const fb_op* op, int l, bool pair) {
+    return op->p[l] <= FB_COMPOSE_PMAX && (!pair || op->p[l - 1] <= FB_COMPOSE_PMAX);
+}
 fb_status fb_learned_alloc(LearnedNet*& net, const fb_op* op, const fb_precond* bj, cudaStream_t s);
 void fb_learned_free(LearnedNet*& net);
 fb_status fb_learned_forward(LearnedNet* net, const cd* v, cd* z, cudaStream_t s);

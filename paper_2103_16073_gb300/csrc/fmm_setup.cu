@@ -361,9 +361,15 @@ __global__ void k_compose(const ComposeJob* jobs, const cd* __restrict__ rot, in
 // yet (T = D_out^H C D_in in FP64), plus their FP32 copies when present.
 fb_status fb_compose_jobs(fb_op* op, const std::vector<int>& which, cudaStream_t s) {
     std::vector<ComposeJob> todo;
-    for (int j : which)
+    for (int j : which) {
+        if (op->h_jobs[j].t_off < 0)
+            return fb_fail(FB_ERR_ARG, "composed translation matrices exist only up to order " +
+                                           std::to_string(FB_COMPOSE_PMAX));
         if (!op->job_done[j]) todo.push_back(op->h_jobs[j]);
+    }
     if (todo.empty()) return FB_OK;
+    if (!op->T64) FB_CHECK(dalloc(&op->T64, std::max<int64_t>(op->T_count, 1)));
+    if (op->prec == FB_PREC_MIXED_FMM && !op->T32) FB_CHECK(dalloc(&op->T32, std::max<int64_t>(op->T_count, 1)));
     ComposeJob* djobs = nullptr;
     FB_CHECK(dalloc(&djobs, todo.size()));
     FB_CUDA(cudaMemcpyAsync(djobs, todo.data(), sizeof(ComposeJob) * todo.size(), cudaMemcpyHostToDevice, s));
@@ -388,8 +394,9 @@ fb_status fb_compose_jobs(fb_op* op, const std::vector<int>& which, cudaStream_t
 }
 
 fb_status fb_compose_all(fb_op* op, cudaStream_t s) {
-    std::vector<int> all(op->h_jobs.size());
-    for (size_t j = 0; j < all.size(); ++j) all[j] = (int)j;
+    std::vector<int> all;
+    for (size_t j = 0; j < op->h_jobs.size(); ++j)
+        if (op->h_jobs[j].t_off >= 0) all.push_back((int)j);
     return fb_compose_jobs(op, all, s);
 }
 
@@ -697,23 +704,21 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
     int64_t T_total = 0;
     for (auto& r : reqs) {
         ComposeJob jb;
-        jb.t_off = T_total;
+        const bool fits = r.pout <= FB_COMPOSE_PMAX && r.pin <= FB_COMPOSE_PMAX;
+        jb.t_off = fits ? T_total : -1;
         jb.rot_off = (int64_t)r.dir * per_dir;
         jb.coax_off = sets[r.set].out_off;
         jb.p_out = r.pout;
         jb.p_in = r.pin;
         jb.pc = sets[r.set].p;
         jobs.push_back(jb);
-        if (r.which == 0) op->m2l_toff[(size_t)r.level * FB_NOFF + r.code] = T_total;
-        else if (r.which == 1) op->m2m_toff[r.level][r.code] = T_total;
-        else op->l2l_toff[r.level][r.code] = T_total;
-        T_total += (int64_t)r.pout * r.pout * r.pin * r.pin;
+        if (r.which == 0) op->m2l_toff[(size_t)r.level * FB_NOFF + r.code] = jb.t_off;
+        else if (r.which == 1) op->m2m_toff[r.level][r.code] = jb.t_off;
+        else op->l2l_toff[r.level][r.code] = jb.t_off;
+        if (fits) T_total += (int64_t)r.pout * r.pout * r.pin * r.pin;
     }
+    // the matrix buffers are allocated by the first composition
     op->T_count = T_total;
-    if ((st = dalloc(&op->T64, std::max<int64_t>(T_total, 1)))) {
-        free_coax();
-        return st;
-    }
     cudaError_t e = cudaStreamSynchronize(s);
     // the rotation blocks and coaxial sets stay with the operator (RCR form)
     op->coax64 = coax;
@@ -774,7 +779,7 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
                     int64_t cnt = t->m2l_group[(size_t)l * FB_NOFF + c + 1] - t->m2l_group[(size_t)l * FB_NOFF + c];
                     if (cnt) { pairs += cnt; ++groups; }
                 }
-                if (groups && pairs >= 48 * groups) {
+                if (groups && pairs >= 48 * groups && fb_composable(op, l, false)) {
                     tc_levels.push_back(l);
                     op->tc_level[l] = 1;
                 }
@@ -810,7 +815,7 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         // M2M / L2L of child levels with >= 48 boxes per octant on average
         if (op->prec == FB_PREC_MIXED_FMM) {
             for (int l = 3; l <= L; ++l) {
-                if (t->nbox[l] < 48 * 8) continue;
+                if (t->nbox[l] < 48 * 8 || !fb_composable(op, l, true)) continue;
                 std::vector<int> need;
                 std::vector<TcGroup> up, down;
                 for (int o = 0; o < 8; ++o) {
@@ -855,7 +860,6 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         FB_CHECK(dalloc(&op->nf32, op->nf_count));
         FB_CHECK(dalloc(&op->w32, (size_t)n * PL));
         FB_CHECK(dalloc(&op->v32, (size_t)n * PL));
-        FB_CHECK(dalloc(&op->T32, std::max<int64_t>(T_total, 1)));
         k_d2f<<<div_up(op->nf_count, 256), 256, 0, s>>>(op->nf64, op->nf32, op->nf_count);
         k_d2f<<<div_up(n * PL, 256), 256, 0, s>>>(op->w64, op->w32, n * PL);
         k_d2f<<<div_up(n * PL, 256), 256, 0, s>>>(op->v64, op->v32, n * PL);

@@ -32,9 +32,15 @@ def _grid_face(origin, ea, eb, na, nb):
     origin, ea, eb: 3-vectors; the wall is origin + s*ea + t*eb, s,t in [0,1].
     Triangles are ordered so that (ea x eb) is their right-hand normal.
     """
-    s = np.linspace(0.0, 1.0, na + 1)
-    t = np.linspace(0.0, 1.0, nb + 1)
+    return _grid_face_st(origin, ea, eb, np.linspace(0.0, 1.0, na + 1), np.linspace(0.0, 1.0, nb + 1))
+
+
+def _grid_face_st(origin, ea, eb, s, t):
+    """As _grid_face with explicit grid lines s[0..na], t[0..nb] in [0,1].
+    Rectangle (i, j) = [s_i, s_i+1] x [t_j, t_j+1] gives triangles 2(i nb + j)
+    and 2(i nb + j) + 1."""
     S, T = np.meshgrid(s, t, indexing="ij")
+    na, nb = s.size - 1, t.size - 1
     verts = (np.asarray(origin, float)[None, None, :]
              + S[..., None] * np.asarray(ea, float)[None, None, :]
              + T[..., None] * np.asarray(eb, float)[None, None, :]).reshape(-1, 3)
@@ -129,6 +135,131 @@ def lroom_inside(p, margin=0.0):
     inB = ((p[:, 0] > 5 - margin) & (p[:, 0] < 8 - margin) & (p[:, 1] > margin)
            & (p[:, 1] < 3 - margin) & (p[:, 2] > margin) & (p[:, 2] < 3 - margin))
     return inA | inB
+
+
+def _breaks(length, cuts, h):
+    """Grid lines (as fractions of `length`) with every cut point a line and
+    legs <= h between consecutive lines."""
+    pts = [0.0] + sorted(cuts) + [float(length)]
+    out = [0.0]
+    for a, b in zip(pts[:-1], pts[1:]):
+        n = max(1, int(math.ceil((b - a) / h - 1e-9)))
+        out.extend(a + (b - a) * np.arange(1, n + 1) / n)
+    out = np.asarray(out) / float(length)
+    out[-1] = 1.0
+    return out
+
+
+# Room with a door and a free-standing baffle (the learned-preconditioner
+# geometry of Sec. 4's scale): shoebox 5x4x3 m, door on the wall y = 0 at
+# x in [0.5, 1.4], z in [0, 2.0]; baffle in the plane x = 2.5 over
+# y in [1.0, 3.0], z in [0.5, 2.0].
+BAFFLE_ROOM = (5.0, 4.0, 3.0)
+DOOR_X = (0.5, 1.4)
+DOOR_Z = (0.0, 2.0)
+BAFFLE_X = 2.5
+BAFFLE_Y = (1.0, 3.0)
+BAFFLE_Z = (0.5, 2.0)
+WALL_DOOR = 6
+WALL_BAFFLE = 7
+
+
+def baffle_room_mesh(h, thickness=0.02):
+    """The door-and-baffle room meshed with legs <= h.
+
+    The direct formulation needs a closed boundary, so the baffle is a closed
+    box of the given thickness centred on its plane (x in 2.5 -/+ t/2).  The
+    normal of every triangle points out of the air: out of the room on the
+    walls, into the baffle's box on its six faces.  The wall y = 0 has grid
+    lines on the door's edges; its door rectangles get wall id 6, the
+    baffle's faces id 7, the walls ids 0..5 as in shoebox_mesh.
+    Returns (verts f64, tris i32, wall i32)."""
+    lx, ly, lz = BAFFLE_ROOM
+    X, Y, Z = np.eye(3)
+    parts, ids = [], []
+
+    def add(vt, wid):
+        parts.append(vt)
+        ids.append(wid if np.ndim(wid) else np.full(vt[1].shape[0], wid, np.int32))
+
+    add(_rect_wall([0, 0, 0], Z * lz, Y * ly, h, h), 0)
+    add(_rect_wall([lx, 0, 0], Y * ly, Z * lz, h, h), 1)
+    s = _breaks(lx, list(DOOR_X), h)
+    t = _breaks(lz, [DOOR_Z[1]], h)
+    v, tr = _grid_face_st([0, 0, 0], X * lx, Z * lz, s, t)
+    sm = 0.5 * (s[:-1] + s[1:]) * lx
+    tm = 0.5 * (t[:-1] + t[1:]) * lz
+    door = ((sm[:, None] > DOOR_X[0]) & (sm[:, None] < DOOR_X[1])
+            & (tm[None, :] > DOOR_Z[0]) & (tm[None, :] < DOOR_Z[1])).ravel()
+    add((v, tr), np.where(np.repeat(door, 2), WALL_DOOR, 2).astype(np.int32))
+    add(_rect_wall([0, ly, 0], Z * lz, X * lx, h, h), 3)
+    add(_rect_wall([0, 0, 0], Y * ly, X * lx, h, h), 4)
+    add(_rect_wall([0, 0, lz], X * lx, Y * ly, h, h), 5)
+    x0, x1 = BAFFLE_X - 0.5 * thickness, BAFFLE_X + 0.5 * thickness
+    wy, wz = BAFFLE_Y[1] - BAFFLE_Y[0], BAFFLE_Z[1] - BAFFLE_Z[0]
+    y0, z0, z1 = BAFFLE_Y[0], BAFFLE_Z[0], BAFFLE_Z[1]
+    y1 = BAFFLE_Y[1]
+    faces = [
+        ([x0, y0, z0], Y * wy, Z * wz),          # x = x0, normal +x (into the box)
+        ([x1, y0, z0], Z * wz, Y * wy),          # x = x1, normal -x
+        ([x0, y0, z0], Z * wz, X * thickness),   # y = y0, normal +y
+        ([x0, y1, z0], X * thickness, Z * wz),   # y = y1, normal -y
+        ([x0, y0, z0], X * thickness, Y * wy),   # z = z0, normal +z
+        ([x0, y0, z1], Y * wy, X * thickness),   # z = z1, normal -z
+    ]
+    for o, ea, eb in faces:
+        add(_rect_wall(o, ea, eb, h, h), WALL_BAFFLE)
+    verts, tris, _ = _concat(parts)
+    return verts, tris, np.concatenate(ids).astype(np.int32)
+
+
+def baffle_room_inside(p, margin=0.0, thickness=0.02):
+    """Points of the air at least `margin` from the walls and the baffle."""
+    p = np.atleast_2d(p)
+    lx, ly, lz = BAFFLE_ROOM
+    inroom = np.all((p > margin) & (p < np.array([lx, ly, lz]) - margin), axis=1)
+    lo = np.array([BAFFLE_X - 0.5 * thickness, BAFFLE_Y[0], BAFFLE_Z[0]]) - margin
+    hi = np.array([BAFFLE_X + 0.5 * thickness, BAFFLE_Y[1], BAFFLE_Z[1]]) + margin
+    inbaffle = np.all((p > lo) & (p < hi), axis=1)
+    return inroom & ~inbaffle
+
+
+def baffle_workload(freq_hz=2000.0, per_wavelength=10.0, nsrc=8, nrec=64, wall_beta=0.2,
+                    door_beta=1.0, baffle_beta=1.0, thickness=0.02, h=None, config_index=3):
+    """Door-and-baffle room at one frequency: walls admittance 0.2, door and
+    baffle 1.0, legs h = lambda/per_wavelength (or the given h), `nsrc`
+    sources and `nrec` receivers seeded uniform in the air (>= 0.25 m from
+    walls and baffle, receivers >= 0.1 m from sources)."""
+    if h is None:
+        h = SOUND_SPEED / freq_hz / per_wavelength
+    verts, tris, wall = baffle_room_mesh(h, thickness)
+    beta = np.full(tris.shape[0], complex(wall_beta), dtype=np.complex128)
+    beta[wall == WALL_DOOR] = door_beta
+    beta[wall == WALL_BAFFLE] = baffle_beta
+    rng = seeded_rng(config_index)
+    pts = []
+    while len(pts) < nsrc + nrec:
+        p = np.array(BAFFLE_ROOM) * rng.random(3)
+        if not baffle_room_inside(p, 0.25, thickness)[0]:
+            continue
+        if len(pts) >= nsrc and np.min(np.linalg.norm(np.asarray(pts[:nsrc]) - p, axis=1)) < 0.1:
+            continue
+        pts.append(p)
+    pts = np.asarray(pts)
+    return Workload(f"baffle-room-5x4x3-{freq_hz:.0f}Hz-N{tris.shape[0]}", verts, tris, wall, float(freq_hz),
+                    wavenumber(freq_hz), beta, pts[:nsrc], pts[nsrc:], room=BAFFLE_ROOM,
+                    extra={"h": h, "thickness": thickness})
+
+
+def cfg_baffle(nsrc=8, nrec=64):
+    """The door-and-baffle room at 2 kHz, legs lambda/10 (N = 685,272)."""
+    return baffle_workload(2000.0, 10.0, nsrc, nrec)
+
+
+def cfg_baffle_sub(nsrc=4, nrec=16):
+    """Small instance of the same geometry for dense parity: 250 Hz, legs
+    0.25 m."""
+    return baffle_workload(250.0, h=0.25, nsrc=nsrc, nrec=nrec)
 
 
 def seeded_rng(config_index: int) -> np.random.Generator:

@@ -29,6 +29,8 @@ def workload(name):
         "small": W.cfg_small,
         "sub": W.cfg_1khz_sub,
         "full": W.cfg_1khz,
+        "baffle_sub": W.cfg_baffle_sub,
+        "baffle": W.cfg_baffle,
         # a small room with walls of different admittance and a ragged count
         "ragged": lambda: W.shoebox_workload("ragged-1.3x1.1x0.9-700Hz", 1.3, 1.1, 0.9, (11, 9, 7),
                                              700.0, 0.2, (0.31, 0.42, 0.27), 16, 7,

@@ -187,3 +187,33 @@ def test_fgmres_matches_direct_solve():
     # exact solution in one step for A = I (happy breakdown)
     x3, info3 = fgmres.fgmres(lambda v: v, b, tol=1e-14)
     assert info3["iters"] == 1 and np.allclose(x3, b)
+
+
+def test_baffle_room_exterior_source():
+    """Door-and-baffle room (a closed thin box inside the room, its normals
+    pointing into the box, out of the air): the exterior-source field solves
+    Eq. (dbem4) on the whole boundary, baffle included, and the error falls
+    under refinement; with the baffle's normals flipped it does not."""
+    room = W.BAFFLE_ROOM
+    k = W.wavenumber(125.0)
+    xe = W.exterior_source(room)
+
+    def err(h, flip=False):
+        v, t, wall = W.baffle_room_mesh(h)
+        bf = wall == W.WALL_BAFFLE
+        if flip:
+            t = t.copy()
+            t[bf] = t[bf][:, [0, 2, 1]]
+        mesh = bem.Mesh(v, t)
+        el = mesh.el
+        beta = np.where(bf, 1.0, 0.2).astype(complex)
+        u, gu = bem.incident(el.centroid, xe, k)
+        g = bem.gamma_field(mesh, k, beta, u, np.sum(gu * el.normal, 1))
+        psi, _, _ = _solve(mesh, k, beta, g)
+        return np.linalg.norm(psi - u) / np.linalg.norm(u), np.linalg.norm((psi - u)[bf]) / np.linalg.norm(u[bf])
+
+    e0, b0 = err(0.5)
+    e1, b1 = err(0.35)
+    assert e1 < 0.6 * e0 and b1 < 0.6 * b0 and e1 < 0.03
+    ef, _ = err(0.5, flip=True)
+    assert ef > 0.3
