@@ -343,9 +343,11 @@ FB_API fb_status fb_precond_create_inner(fb_op* op, fb_op* inner_op, const fb_pr
  * conj(ph) BJ(v) / s), where BJ is the block-Jacobi `base` of the same FMM
  * operator (which must outlive it), s = rms(v), ph the unit phase of sum v
  * (so z(a v) = a z(v) for complex a), and N a hierarchical network over the
- * octree (element
- * encoder, leaf pooling, 3 coarser pooling levels, down-sweep back to the
- * leaves, element decoder; 64-wide features, SiLU).  Its matrix products run
+ * octree (element encoder, leaf pooling, 3 coarser pooling levels, down-sweep
+ * back to the leaves, element decoder; 64-wide features, SiLU).  Per element
+ * it sees the two normalised inputs, the normal, the admittance and k times
+ * the leaf side, so one parameter set can serve several frequencies and
+ * wall materials (fb_learned_params moves it between operators).  Its matrix products run
  * on the tensor cores in BF16 with FP32 accumulation; parameters, gradients
  * and Adam moments are FP32.  Parameters start from a deterministic seeded
  * initialisation with a small output layer (close to block Jacobi).

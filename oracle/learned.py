@@ -5,11 +5,14 @@ The network refines block Jacobi, z = u + s N(F), u = BJ(v), s = rms(v), and
 is applied as the variable right preconditioner flexible GMRES admits
 (Sec. 3.1, Sec. 4).  Layout of the flat parameter vector (FP32 on the GPU,
 FP64 here), weights W as [in x out] with Y = X W + b:
-    W0[8x64] b0[64] | Wu_k[64x64] bu_k[64] (k=0..2) | Wd_k[128x64] bd_k[64]
+    W0[11x64] b0[64] | Wu_k[64x64] bu_k[64] (k=0..2) | Wd_k[128x64] bd_k[64]
     (k=0..2) | Wh[128x64] bh[64] | Wo[64x2] bo[2]
 Forward (elements in tree order, SiLU activations):
-    F = [Re v', Im v', Re u', Im u', n_x, n_y, n_z, 1],  v' = conj(ph) v / s,
-        u' = conj(ph) u / s, s = rms(v), ph = sum(v) / |sum(v)| (1 if zero)
+    F = [Re v', Im v', Re u', Im u', n_x, n_y, n_z, 1, Re beta, Im beta, k delta_L],
+        v' = conj(ph) v / s, u' = conj(ph) u / s, s = rms(v),
+        ph = sum(v) / |sum(v)| (1 if zero), beta the element's admittance,
+        k delta_L the wavenumber times the leaf box side (so one network can
+        serve several frequencies and wall materials)
     H0 = silu(F W0 + b0);  G_L = leaf means of H0
     G_l = silu(mean over children of G_{l+1} Wu_k + bu_k),  l = L-1-k
     D_{L-3} = G_{L-3};  D_l = silu([G_l, D_{l-1}[parent]] Wd_k + bd_k),  l = L-2+k
@@ -28,7 +31,7 @@ from __future__ import annotations
 
 import numpy as np
 
-HW, NF, DEPTH = 64, 8, 3
+HW, NF, DEPTH = 64, 11, 3
 
 
 def layout():
@@ -79,6 +82,7 @@ class TreeInfo:
         self.leaf_of = np.repeat(np.arange(len(tree.leaf_start)), tree.leaf_count)
         self.nbox = {l: len(tree.levels[l]) for l in range(tree.L + 1)}
         self.parent = {l: tree.parent_index(l) for l in range(1, tree.L + 1)}
+        self.leaf_side = tree.delta(tree.L)
 
 
 def _segmean(X, seg_id, nseg):
@@ -88,8 +92,9 @@ def _segmean(X, seg_id, nseg):
     return out / np.maximum(cnt, 1)[:, None], cnt
 
 
-def forward(theta, T, v, u, normals):
-    """z (element order) and a cache for the backward pass."""
+def forward(theta, T, v, u, normals, beta=None, k=0.0):
+    """z (element order) and a cache for the backward pass.  beta: admittance
+    per element (zero when None); k: wavenumber."""
     P = unpack(theta)
     n, L = T.n, T.L
     depth = min(DEPTH, L)
@@ -100,7 +105,9 @@ def forward(theta, T, v, u, normals):
     ph = tot / abs(tot) if abs(tot) > 0 else 1.0 + 0j
     rot = np.conj(ph) * inv
     vp, up, nrm = v[T.perm] * rot, u[T.perm] * rot, normals[T.perm]
-    F = np.column_stack([vp.real, vp.imag, up.real, up.imag, nrm, np.ones(n)])
+    b = np.zeros(n, np.complex128) if beta is None else np.broadcast_to(np.asarray(beta, np.complex128), (n,))[T.perm]
+    F = np.column_stack([vp.real, vp.imag, up.real, up.imag, nrm, np.ones(n), b.real, b.imag,
+                         np.full(n, k * T.leaf_side)])
     c = {"F": F, "s": s, "ph": ph}
     c["pre0"] = F @ P["W0"] + P["b0"]
     H0 = silu(c["pre0"])
@@ -147,11 +154,11 @@ def approx_adjoint(L, LP, area, beta, k):
     return apply
 
 
-def loss_grad(theta, T, r, e, u, normals, objective="error", A=None, adjoint=None):
+def loss_grad(theta, T, r, e, u, normals, objective="error", A=None, adjoint=None, beta=None, k=0.0):
     """(loss, gradient) for one pair; gradient in the flat layout.  The
     residual objective needs A (matrix) and adjoint (callable w -> ~A^H w)."""
     P = unpack(theta)
-    z, c = forward(theta, T, r, u, normals)
+    z, c = forward(theta, T, r, u, normals, beta, k)
     L, top, depth = T.L, c["top"], c["depth"]
     if objective == "error":
         e2 = np.sum(np.abs(e) ** 2)

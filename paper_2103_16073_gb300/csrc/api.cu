@@ -419,6 +419,8 @@ fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t inde
         int PL = op->p[L] * op->p[L];
         if (which >= 0 && which <= 2) {
             if (index < 0 || index >= nleaf) return fb_fail(FB_ERR_ARG, "leaf out of range");
+            if (!op->nf64)
+                return fb_fail(FB_ERR_ARG, "mixed operators keep FP32 entries only: export from an FP64 operator");
             int r0 = t->h_leaf_start[index], nr = t->h_leaf_start[index + 1] - r0;
             if (which == 0) {
                 src = op->nf64 + op->h_nf_off[index];

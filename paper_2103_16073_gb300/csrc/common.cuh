@@ -280,8 +280,9 @@ struct fb_op {
     int32_t* nf_ncol = nullptr;              // per leaf, columns K_t
     std::vector<int64_t> h_nf_off;
     std::vector<int32_t> h_nf_ncol;
-    cd* nf64 = nullptr;
+    cd* nf64 = nullptr;                      // FP64 operators only
     cf* nf32 = nullptr;
+    cd* self64 = nullptr;                    // mixed: FP64 leaf self-blocks (nr x nr, leaf-major)
     cd* w64 = nullptr; cf* w32 = nullptr;    // P2M, [N sorted][P_L]
     cd* v64 = nullptr; cf* v32 = nullptr;    // L2P, [N sorted][P_L]
     void* mp = nullptr;                      // multipoles (all levels; exp_nrhs sets)
@@ -376,6 +377,8 @@ fb_status fb_rcr_run_op(fb_op* op, RcrPlan& pl, void* src, void* dst, cudaStream
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times, int* choice);
 fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s);
 fb_status fb_compose_all(fb_op* op, cudaStream_t s);
+// Leaf self-blocks of the FP64 near-field entries (leaf t at d_off[t], nr x nr).
+fb_status fb_self_blocks(const fb_op* op, const int64_t* d_off, cd* out, cudaStream_t s);
 // Composed p^2 x p^2 translation matrices exist only for orders up to this
 // bound: above it one matrix outgrows the RCR arithmetic it replaces (the
 // dense form costs ~p/4 times RCR) and a level's set reaches tens of GB.

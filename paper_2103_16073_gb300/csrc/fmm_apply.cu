@@ -611,6 +611,7 @@ void fb_fmm_destroy(fb_op* op) {
     dfree(op->nf_ncol);
     dfree(op->nf64);
     dfree(op->nf32);
+    dfree(op->self64);
     dfree(op->w64);
     dfree(op->w32);
     dfree(op->v64);

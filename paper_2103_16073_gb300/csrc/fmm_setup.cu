@@ -868,6 +868,30 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         FB_LAUNCH_CHECK();
         FB_CHECK(dalloc((cf**)&op->mp, mp_count));
         FB_CHECK(dalloc((cf**)&op->loc, mp_count));
+        // of the FP64 entries only the leaf self-blocks stay (block-Jacobi
+        // factorisation); the rest are dropped once the FP32 copies exist
+        {
+            int nleaf = t->nbox[L];
+            std::vector<int64_t> off(nleaf + 1, 0);
+            for (int b = 0; b < nleaf; ++b) {
+                int64_t nb = t->h_leaf_start[b + 1] - t->h_leaf_start[b];
+                off[b + 1] = off[b] + nb * nb;
+            }
+            int64_t* d_off = nullptr;
+            FB_CHECK(dalloc(&d_off, nleaf + 1));
+            fb_status st2 = dalloc(&op->self64, std::max<int64_t>(off[nleaf], 1));
+            if (st2 == FB_OK) {
+                cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * (nleaf + 1), cudaMemcpyHostToDevice, s);
+                st2 = fb_self_blocks(op, d_off, op->self64, s);
+            }
+            cudaError_t e2 = cudaStreamSynchronize(s);
+            dfree(d_off);
+            FB_CHECK(st2);
+            if (e2 != cudaSuccess) return fb_fail(FB_ERR_CUDA, std::string("self blocks: ") + cudaGetErrorString(e2));
+            dfree(op->nf64);
+            dfree(op->w64);
+            dfree(op->v64);
+        }
     } else {
         FB_CHECK(dalloc((cd**)&op->mp, mp_count));
         FB_CHECK(dalloc((cd**)&op->loc, mp_count));

@@ -480,6 +480,15 @@ __global__ void k_bj_extract(const cd* nf, const int64_t* nf_off, const int32_t*
     }
 }
 
+fb_status fb_self_blocks(const fb_op* op, const int64_t* d_off, cd* out, cudaStream_t s) {
+    const fb_tree* t = op->tree;
+    int nleaf = t->nbox[t->L];
+    k_bj_extract<<<nleaf, 256, 0, s>>>(op->nf64, op->nf_off, op->nf_ncol, t->leaf_start, t->ucnt, t->ulist, d_off,
+                                       out);
+    FB_LAUNCH_CHECK();
+    return FB_OK;
+}
+
 __global__ void k_bj_invert(const int32_t* leaf_start, const int64_t* blk_off, cd* blocks, int* piv_scr,
                             int* singular) {
     int t = blockIdx.x;
@@ -959,8 +968,8 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
         return fail(st);
     FB_CUDA(cudaMemcpyAsync(pc->blk_off, off.data(), sizeof(int64_t) * (nleaf + 1), cudaMemcpyHostToDevice, s));
     FB_CUDA(cudaMemsetAsync(sing, 0, sizeof(int), s));
-    k_bj_extract<<<nleaf, 256, 0, s>>>(op->nf64, op->nf_off, op->nf_ncol, t->leaf_start, t->ucnt, t->ulist,
-                                       pc->blk_off, pc->inv64);
+    if (op->nf64) FB_CHECK(fb_self_blocks(op, pc->blk_off, pc->inv64, s));
+    else FB_CUDA(cudaMemcpyAsync(pc->inv64, op->self64, sizeof(cd) * off[nleaf], cudaMemcpyDeviceToDevice, s));
     FB_CHECK(fb_smem_cap((const void*)k_bj_invert, sizeof(cd) * std::max(maxn, 1)));
     k_bj_invert<<<nleaf, 256, sizeof(cd) * std::max(maxn, 1), s>>>(t->leaf_start, pc->blk_off, pc->inv64, piv, sing);
     int hs = 0;

@@ -6,9 +6,11 @@
 // ||z(r) - e||^2 / ||e||^2.
 //
 // Network (64-wide features, SiLU, weights W as [in x out], Y = X W + b):
-//   features f_i = (Re, Im of v_i conj(ph), u_i conj(ph))/s, n_i, 1
+//   features f_i = (Re, Im of v_i conj(ph), u_i conj(ph))/s, n_i, 1,
+//                  Re, Im beta_i, k delta_L
 //                  (u = BJ(v), s = rms of v, ph = unit phase of sum_i v_i,
-//                  elements in tree order)
+//                  beta the admittance, k delta_L the wavenumber times the
+//                  leaf side; elements in tree order)
 //   H0 = silu(F W0 + b0)                                  elements
 //   G_L = mean of H0 over each leaf                       leaves
 //   G_l = silu(mean of G_{l+1} over children W_up,k + b)  3 coarser levels
@@ -29,7 +31,7 @@
 namespace {
 
 constexpr int HW = 64;       // feature width
-constexpr int NF = 8;        // element input features
+constexpr int NF = 11;       // element input features
 constexpr int DEPTH = 3;     // coarser levels above the leaves
 
 // ---------------------------------------------------------------- GEMM ----
@@ -177,7 +179,7 @@ __device__ __forceinline__ cd input_phase(const double* st) {
 // features in tree order: (v, u) rotated by the conjugate input phase and
 // divided by s
 __global__ void k_features(Geom g, const int32_t* perm, const cd* v, const cd* u, const double* st,
-                           int64_t n, float* F) {
+                           int64_t n, float kd, float* F) {
     int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (pos >= n) return;
     double s = sqrt(st[0] / (double)n);
@@ -195,6 +197,9 @@ __global__ void k_features(Geom g, const int32_t* perm, const cd* v, const cd* u
     f[5] = (float)g.ny[e];
     f[6] = (float)g.nz[e];
     f[7] = 1.f;
+    f[8] = (float)g.beta[e].re;
+    f[9] = (float)g.beta[e].im;
+    f[10] = kd;
 }
 
 // mean of rows [start[s], start[s+1]) of X (width HW) -> Y[s]
@@ -385,7 +390,7 @@ __device__ __forceinline__ void stage_w(const uint32_t* __restrict__ P, uint32_t
 __device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
 __device__ __forceinline__ void elem_features(const Geom& g, const int32_t* perm, const cd* v, const cd* u,
-                                              const double* st, int64_t n, int64_t pos, float f[NF]) {
+                                              const double* st, int64_t n, float kd, int64_t pos, float f[NF]) {
     double s = sqrt(st[0] / (double)n);
     double inv = s > 0.0 ? 1.0 / s : 0.0;
     cd ph = input_phase(st);
@@ -400,13 +405,16 @@ __device__ __forceinline__ void elem_features(const Geom& g, const int32_t* perm
     f[5] = bfr((float)g.ny[e]);
     f[6] = bfr((float)g.nz[e]);
     f[7] = 1.f;
+    f[8] = bfr((float)g.beta[e].re);
+    f[9] = bfr((float)g.beta[e].im);
+    f[10] = bfr(kd);
 }
 
 // G_L[leaf][c] = mean over the leaf's elements of silu(F W0 + b0)[c]; one CTA
 // of 64 threads (one per feature column) per leaf.
 __global__ void __launch_bounds__(64) k_inf_pass1(Geom g, const int32_t* perm, const int32_t* leaf_start,
                                                   const cd* v, const cd* u, const double* st, int64_t n,
-                                                  const float* W0, const float* b0, float* GL) {
+                                                  float kd, const float* W0, const float* b0, float* GL) {
     int leaf = blockIdx.x, c = threadIdx.x;
     int a = leaf_start[leaf], b = leaf_start[leaf + 1];
     float w[NF];
@@ -420,7 +428,7 @@ __global__ void __launch_bounds__(64) k_inf_pass1(Geom g, const int32_t* perm, c
         __syncthreads();
         if (c < cnt) {
             float f[NF];
-            elem_features(g, perm, v, u, st, n, e0 + c, f);
+            elem_features(g, perm, v, u, st, n, kd, e0 + c, f);
 #pragma unroll
             for (int k = 0; k < NF; ++k) fs[c][k] = f[k];
         }
@@ -439,7 +447,7 @@ __global__ void __launch_bounds__(64) k_inf_pass1(Geom g, const int32_t* perm, c
 // rows 16 (w & 3) .. +16 and the 32 columns 32 (w >> 2) .. +32 of H1.
 __global__ void __launch_bounds__(256) k_inf_pass2(Geom g, const int32_t* perm, const int32_t* leaf_of,
                                                    const cd* v, const cd* u, const double* st, int64_t n,
-                                                   const float* W0, const float* b0, const float* DL,
+                                                   float kd, const float* W0, const float* b0, const float* DL,
                                                    const uint32_t* Whp, const float* bh, const float* Wo,
                                                    const float* bo, cd* z) {
     __shared__ __align__(16) uint32_t Es[64][HW + 4];   // [row][k pair]: 128 bf16 per row (+pad)
@@ -454,7 +462,7 @@ __global__ void __launch_bounds__(256) k_inf_pass2(Geom g, const int32_t* perm, 
     if (tid < 64) {
         int64_t pos = r0 + tid;
         float f[NF];
-        if (pos < n) elem_features(g, perm, v, u, st, n, pos, f);
+        if (pos < n) elem_features(g, perm, v, u, st, n, kd, pos, f);
         else
             for (int k = 0; k < NF; ++k) f[k] = 0.f;
         for (int k = 0; k < NF; ++k) fs[tid][k] = f[k];
@@ -643,6 +651,7 @@ struct LearnedNet {
     const fb_precond* bj = nullptr;
     int L = 0, depth = 0;
     int64_t n = 0;
+    float kd = 0.f;                          // k times the leaf side (input feature)
     int64_t nparam = 0;
     int64_t oW0, ob0, oWu[DEPTH], obu[DEPTH], oWd[DEPTH], obd[DEPTH], oWh, obh, oWo, obo;
     float *w = nullptr, *grad = nullptr, *m1 = nullptr, *m2 = nullptr;
@@ -717,6 +726,7 @@ fb_status fb_learned_alloc(LearnedNet*& net, const fb_op* op, const fb_precond* 
     net->L = t->L;
     net->depth = std::min(DEPTH, t->L);
     net->n = op->n;
+    net->kd = (float)(op->k * t->side / (double)(1 << t->L));
     int64_t o = 0;
     auto take = [&](int64_t c) { int64_t r = o; o += c; return r; };
     net->oW0 = take(NF * HW);
@@ -817,7 +827,7 @@ fb_status fb_learned_forward(LearnedNet* net, const cd* v, cd* z, cudaStream_t s
     FB_CHECK(fb_pc_apply(net->bj, v, net->u, s));
     FB_CUDA(cudaMemsetAsync(net->scal, 0, 8 * sizeof(double), s));
     k_stats<<<std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(v, n, net->scal);
-    k_features<<<div_up(n, 256), 256, 0, s>>>(g, t->perm, v, net->u, net->scal, n, net->F);
+    k_features<<<div_up(n, 256), 256, 0, s>>>(g, t->perm, v, net->u, net->scal, n, net->kd, net->F);
     fb_count_launch(2);
     const float* w = net->w;
     gemm(s, net->F, NF, 1, w + net->oW0, HW, 1, net->H0, HW, 1, (int)n, HW, NF, w + net->ob0, net->pre0, 1);
@@ -861,7 +871,7 @@ fb_status fb_learned_apply(LearnedNet* net, const cd* v, cd* z, cudaStream_t s) 
     FB_CHECK(fb_pc_apply(net->bj, v, net->u, s));
     FB_CUDA(cudaMemsetAsync(net->scal, 0, 8 * sizeof(double), s));
     k_stats<<<std::min<int64_t>(div_up(n, 256), 1024), 256, 0, s>>>(v, n, net->scal);
-    k_inf_pass1<<<nleaf, 64, 0, s>>>(g, t->perm, t->leaf_start, v, net->u, net->scal, n, w + net->oW0,
+    k_inf_pass1<<<nleaf, 64, 0, s>>>(g, t->perm, t->leaf_start, v, net->u, net->scal, n, net->kd, w + net->oW0,
                                      w + net->ob0, net->G[L]);
     fb_count_launch(2);
     for (int l = L - 1, k = 0; l >= Ltop; --l, ++k) {
@@ -879,7 +889,8 @@ fb_status fb_learned_apply(LearnedNet* net, const cd* v, cd* z, cudaStream_t s) 
         fb_count_launch();
         Dprev = net->D[l];
     }
-    k_inf_pass2<<<div_up(n, 64), 256, 0, s>>>(g, t->perm, net->leaf_of, v, net->u, net->scal, n, w + net->oW0,
+    k_inf_pass2<<<div_up(n, 64), 256, 0, s>>>(g, t->perm, net->leaf_of, v, net->u, net->scal, n, net->kd,
+                                             w + net->oW0,
                                              w + net->ob0, Dprev, net->wpk + net->pWh, w + net->obh, w + net->oWo,
                                              w + net->obo, z);
     fb_count_launch();

@@ -56,7 +56,8 @@ def test_loss_and_gradient_match_reference(small, objective):
         Ad = D["A"]
         u = learned.block_jacobi(lambda i, j: Ad[np.ix_(i, j)], T, r)
         adj = learned.approx_adjoint(D["L"], D["LP"], el.area, wl.beta, wl.k)
-        loss_o, grad_o = learned.loss_grad(theta.astype(np.float64), T, r, e, u, el.normal, objective, Ad, adj)
+        loss_o, grad_o = learned.loss_grad(theta.astype(np.float64), T, r, e, u, el.normal, objective, Ad, adj,
+                                           beta=wl.beta, k=wl.k)
         print(f"{objective}: loss {loss_g:.6f} vs {loss_o:.6f}; grad rel {rel(grad_g, grad_o):.2e}")
         assert abs(loss_g - loss_o) < 1e-2 * loss_o
         assert rel(grad_g, grad_o) < 3e-2
@@ -155,7 +156,7 @@ def test_inference_apply_matches_reference(small):
         T = learned.TreeInfo(Octree(np.concatenate([el.v0, el.v1, el.v2]), el.centroid, om.rc, 64))
         Ad = oracle_dense("small")["A"]
         u = learned.block_jacobi(lambda i, j: Ad[np.ix_(i, j)], T, v)
-        zo, _ = learned.forward(theta.astype(np.float64), T, v, u, el.normal)
+        zo, _ = learned.forward(theta.astype(np.float64), T, v, u, el.normal, wl.beta, wl.k)
         # the network's correction z - u carries the BF16 error; u itself is exact to FP32
         err = rel(z.cpu().numpy() - u, zo - u)
         print(f"inference correction rel err {err:.2e}; total {rel(z.cpu().numpy(), zo):.2e}")

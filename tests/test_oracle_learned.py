@@ -7,6 +7,8 @@ from oracle import bem, learned
 from oracle.octree import Octree
 from paper_2103_16073_gb300 import workloads as W
 
+BETA, K = None, 0.0   # admittance and wavenumber features (set by _setup)
+
 
 def _setup():
     v, t, _ = W.shoebox_mesh(1.0, 0.8, 0.6, 8, 6, 5)
@@ -21,30 +23,35 @@ def _setup():
     u = 0.7 * r + 0.1j * r
     _, total = learned.layout()
     theta = rng.standard_normal(total) * 0.2
+    global BETA, K
+    BETA = rng.uniform(0.05, 0.5, n) + 1j * rng.uniform(-0.1, 0.1, n)
+    K = 7.0
     return T, r, e, u, el.normal, theta
 
 
 def test_gradient_matches_finite_differences():
     T, r, e, u, nrm, theta = _setup()
     assert T.L == 3
-    loss, g = learned.loss_grad(theta, T, r, e, u, nrm)
+    loss, g = learned.loss_grad(theta, T, r, e, u, nrm, beta=BETA, k=K)
     rng = np.random.default_rng(1)
     h = 1e-6
     for _ in range(6):
         d = rng.standard_normal(theta.size)
-        lp, _ = learned.loss_grad(theta + h * d, T, r, e, u, nrm)
-        lm, _ = learned.loss_grad(theta - h * d, T, r, e, u, nrm)
+        lp, _ = learned.loss_grad(theta + h * d, T, r, e, u, nrm, beta=BETA, k=K)
+        lm, _ = learned.loss_grad(theta - h * d, T, r, e, u, nrm, beta=BETA, k=K)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g @ d) < 1e-6 * max(1.0, abs(fd))
     # single-block directions too (weights of every layer are reached)
     lay, _ = learned.layout()
-    for name in ("W0", "Wu0", "Wd2", "Wh", "Wo", "bo"):
+    for name, j in (("W0", None), ("W0", 8 * 64 + 5), ("W0", 9 * 64 + 17), ("W0", 10 * 64 + 40), ("Wu0", None),
+                    ("Wd2", None), ("Wh", None), ("Wo", None), ("bo", None)):
         o, n = lay[name]
+        j = n // 3 if j is None else j
         d = np.zeros(theta.size)
-        d[o + n // 3] = 1.0
-        lp, _ = learned.loss_grad(theta + h * d, T, r, e, u, nrm)
-        lm, _ = learned.loss_grad(theta - h * d, T, r, e, u, nrm)
-        assert abs((lp - lm) / (2 * h) - g[o + n // 3]) < 1e-6 * max(1.0, abs(g[o + n // 3]))
+        d[o + j] = 1.0
+        lp, _ = learned.loss_grad(theta + h * d, T, r, e, u, nrm, beta=BETA, k=K)
+        lm, _ = learned.loss_grad(theta - h * d, T, r, e, u, nrm, beta=BETA, k=K)
+        assert abs((lp - lm) / (2 * h) - g[o + j]) < 1e-6 * max(1.0, abs(g[o + j]))
 
 
 def test_zero_output_layer_is_block_jacobi():
@@ -53,7 +60,7 @@ def test_zero_output_layer_is_block_jacobi():
     for name in ("Wo", "bo"):
         o, n = lay[name]
         theta[o:o + n] = 0.0
-    z, _ = learned.forward(theta, T, r, u, nrm)
+    z, _ = learned.forward(theta, T, r, u, nrm, BETA, K)
     assert np.max(np.abs(z - u)) == 0.0
 
 
@@ -61,15 +68,15 @@ def test_complex_homogeneous():
     """The network's input normalisation (rms scale, phase of sum v) makes the
     map commute with complex scaling, as a linear preconditioner does."""
     T, r, e, u, nrm, theta = _setup()
-    z, _ = learned.forward(theta, T, r, u, nrm)
+    z, _ = learned.forward(theta, T, r, u, nrm, BETA, K)
     for a in (2.5, -1.0, 1j, 0.3 * np.exp(2.1j)):
-        za, _ = learned.forward(theta, T, a * r, a * u, nrm)
+        za, _ = learned.forward(theta, T, a * r, a * u, nrm, BETA, K)
         assert np.max(np.abs(za - a * z)) < 1e-12 * abs(a) * np.max(np.abs(z))
     # and the map is not linear (the network is not a fixed matrix)
     r2 = np.roll(r, 7)
     u2 = np.roll(u, 7)
-    z2, _ = learned.forward(theta, T, r2, u2, nrm)
-    z12, _ = learned.forward(theta, T, r + r2, u + u2, nrm)
+    z2, _ = learned.forward(theta, T, r2, u2, nrm, BETA, K)
+    z12, _ = learned.forward(theta, T, r + r2, u + u2, nrm, BETA, K)
     assert np.max(np.abs(z12 - z - z2)) > 1e-3 * np.max(np.abs(z))
 
 
@@ -90,15 +97,15 @@ def test_residual_objective_exact_adjoint_gradient():
     assert mesh.n == r.size
     AH = A.conj().T
     adj = lambda w: AH @ w
-    loss, g = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, adj)
-    z, _ = learned.forward(theta, T, r, u, nrm)
+    loss, g = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, adj, beta=BETA, k=K)
+    z, _ = learned.forward(theta, T, r, u, nrm, BETA, K)
     assert abs(loss - np.linalg.norm(A @ z - r) ** 2 / np.linalg.norm(r) ** 2) < 1e-12 * loss
     rng = np.random.default_rng(3)
     h = 1e-6
     for _ in range(4):
         d = rng.standard_normal(theta.size)
-        lp, _ = learned.loss_grad(theta + h * d, T, r, e, u, nrm, "residual", A, adj)
-        lm, _ = learned.loss_grad(theta - h * d, T, r, e, u, nrm, "residual", A, adj)
+        lp, _ = learned.loss_grad(theta + h * d, T, r, e, u, nrm, "residual", A, adj, beta=BETA, k=K)
+        lm, _ = learned.loss_grad(theta - h * d, T, r, e, u, nrm, "residual", A, adj, beta=BETA, k=K)
         fd = (lp - lm) / (2 * h)
         assert abs(fd - g @ d) < 1e-6 * max(1.0, abs(fd))
 
@@ -115,6 +122,6 @@ def test_approximate_adjoint_is_close():
     w = rng.standard_normal(mesh.n) + 1j * rng.standard_normal(mesh.n)
     ex = A.conj().T @ w
     assert np.linalg.norm(adj(w) - ex) / np.linalg.norm(ex) < 0.1
-    _, g_ex = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, lambda x: A.conj().T @ x)
-    _, g_ap = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, adj)
+    _, g_ex = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, lambda x: A.conj().T @ x, beta=BETA, k=K)
+    _, g_ap = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, adj, beta=BETA, k=K)
     assert g_ap @ g_ex > 0.9 * np.linalg.norm(g_ap) * np.linalg.norm(g_ex)
