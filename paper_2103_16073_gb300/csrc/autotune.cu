@@ -47,12 +47,7 @@ fb_status time_ms(F&& f, cudaStream_t s, int reps, double* out) {
     return FB_OK;
 }
 
-void free_rcr(RcrPlan& p) {
-    dfree(p.tasks);
-    dfree(p.tiles);
-    for (auto& kv : p.multi) dfree(kv.second.tiles);
-    p.multi.clear();
-}
+void free_rcr(RcrPlan& p) { fb_rcr_free(p); }
 
 }  // namespace
 

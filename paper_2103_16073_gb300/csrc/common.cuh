@@ -174,14 +174,13 @@ struct fb_tree {
     // table e^{i m phi} (m = -(P-1)..P-1) are kept too, so the RCR kernels
     // rotate with real multipliers after one phase per coefficient.
     struct RotSet {
-        cd* r64 = nullptr;
-        cf* r32 = nullptr;
-        double* d64 = nullptr;
+        cd* r64 = nullptr;          // complex blocks, degrees < Pc (composed matrices)
+        double* d64 = nullptr;      // real factors, degrees < P
         float* d32 = nullptr;
-        cd* ph64 = nullptr;
+        cd* ph64 = nullptr;         // phase tables e^{i m phi}
         cf* ph32 = nullptr;
-        int P = 0, ndir = 0;
-        int64_t per_dir = 0;
+        int P = 0, Pc = 0, ndir = 0;
+        int64_t per_dir = 0, per_dir_c = 0;
     };
     std::deque<RotSet> rot_sets;   // deque: references stay valid on push_back
 };
@@ -224,24 +223,35 @@ struct RcrTile {
 };
 // Tiles of an RCR plan for a number of right-hand sides: the columns of a
 // task are its (pair, rhs) combinations, pair-major.
+// Tasks whose column (2 p^2 coefficients) outgrows shared memory run one
+// column per tile with their working set in a global scratch slot per CTA.
 struct RcrTileSet {
     RcrTile* tiles = nullptr;
     int ntiles = 0;
     size_t smem = 0;
+    RcrTile* big = nullptr;   // one-column tiles of the large-order tasks
+    int nbig = 0;
 };
 struct RcrPlan {
     std::vector<RcrTask> h_tasks;
     std::vector<RcrTile> h_tiles;
+    std::vector<RcrTile> h_big;
     RcrTask* tasks = nullptr;
     RcrTile* tiles = nullptr;
+    RcrTile* big = nullptr;
     const int32_t* src_idx = nullptr;
     const int32_t* dst_idx = nullptr;
     int ntiles = 0;
+    int nbig = 0;
     int nb = 1;          // box pairs per CTA
     size_t smem = 0;     // dynamic shared memory per CTA (bytes)
     size_t csize = 0;    // bytes per complex coefficient
+    int64_t big_per = 0;    // scratch coefficients per CTA slot (large-order tasks)
+    int slots = 0;          // CTA slots of the scratch
+    void* scr = nullptr;    // slots x big_per coefficients
     std::map<int, RcrTileSet> multi;   // tiles for nrhs > 1 (built on first use)
 };
+void fb_rcr_free(RcrPlan& p);
 
 // A group of box pairs sharing one composed translation matrix (job) on the
 // tensor cores: sources from level src_level, targets in level dst_level.
@@ -297,7 +307,7 @@ struct fb_op {
     // RCR form: rotation blocks per direction, coaxial sets, plans
     int Prot = 0;
     int64_t per_dir = 0;
-    cd* rot64 = nullptr; cf* rot32 = nullptr;
+    cd* rot64 = nullptr;                     // complex rotation blocks, degrees < FB_COMPOSE_PMAX
     double* rotd64 = nullptr; float* rotd32 = nullptr;   // real parts d (owned by the tree)
     cd* rph64 = nullptr; cf* rph32 = nullptr;            // phase tables (owned by the tree)
     cd* coax64 = nullptr; cf* coax32 = nullptr;
@@ -383,6 +393,8 @@ fb_status fb_self_blocks(const fb_op* op, const int64_t* d_off, cd* out, cudaStr
 // bound: above it one matrix outgrows the RCR arithmetic it replaces (the
 // dense form costs ~p/4 times RCR) and a level's set reaches tens of GB.
 constexpr int FB_COMPOSE_PMAX = 32;
+// Largest expansion order the rotation setup supports.
+constexpr int FB_ROT_PMAX = 256;
 // M2L of level l (pair = false) or M2M/L2L between levels l-1 and l (pair = true)
 // has composed matrices.
 inline bool fb_composable(const fb_op* op, int l, bool pair) {

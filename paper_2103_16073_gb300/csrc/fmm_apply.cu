@@ -294,21 +294,26 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
                                              const int32_t* __restrict__ src_idx,
                                              const int32_t* __restrict__ dst_idx,
                                              const cx<R>* __restrict__ src, cx<R>* __restrict__ dst,
-                                             int nrhs, int64_t rstride) {
+                                             int nrhs, int64_t rstride, int ntiles, cx<R>* gscr,
+                                             int64_t gstride) {
     constexpr int BCH = RcrChunk<R>::value;
     extern __shared__ unsigned char smem_raw[];
-    RcrTile tl = tiles[blockIdx.x];
+    __shared__ int64_t s_dst_off[16];
+    // one tile per CTA (shared-memory working set), or a loop over the
+    // one-column tiles of large orders with the working set in this CTA's
+    // global scratch slot
+    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
+    RcrTile tl = tiles[ti];
     RcrTask tk = tasks[tl.task];
     const int nb = tl.nb;
     const int Pin = tk.p_in * tk.p_in, Pout = tk.p_out * tk.p_out;
     const int pmid = tk.p_in;   // the rotated input keeps degrees n < p_in
-    cx<R>* buf = (cx<R>*)smem_raw;
+    cx<R>* buf = gscr ? gscr + (int64_t)blockIdx.x * gstride : (cx<R>*)smem_raw;
     cx<R>* xs = buf;                    // [nb][Pin], later reused for vs
     cx<R>* us = buf + nb * max(Pin, Pout);   // [nb][Pin]
     cx<R>* vs = buf;                    // [nb][Pout] (xs is dead after the rotation)
     int tid = threadIdx.x, nth = blockDim.x;
     // column b of the tile: pair (col0 + b) / nrhs, right-hand side (col0 + b) % nrhs
-    __shared__ int64_t s_dst_off[16];
     for (int b = tid; b < nb; b += nth) {
         int col = tl.col0 + b;
         int pr = col / nrhs, rh = col - pr * nrhs;
@@ -371,19 +376,33 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
 #undef RCR_BACK
     }
 #undef RCR_CHUNKS
+    __syncthreads();   // the next tile reuses the working set and s_dst_off
+    }
 }
 
 // Tiles of up to 16 columns per CTA within a shared-memory budget: 96 KB for
 // FP32 (two CTAs per SM; the columns of a tile reuse each rotation / coaxial
 // entry from registers, so larger tiles raise the arithmetic per load) and
 // 48 KB for FP64 (bound by the FP64 pipe, it wants more resident warps).
-static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& tiles, size_t& smem) {
+// Columns needing more than RCR_SMEM_MAX bytes go to one-column tiles in
+// `big` (global scratch).
+constexpr size_t RCR_SMEM_MAX = 200 * 1024;
+static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& tiles, size_t& smem,
+                           std::vector<RcrTile>& big, int64_t& big_per) {
     const size_t budget = pl.csize == sizeof(cf) ? 96 * 1024 : 48 * 1024;
     tiles.clear();
+    big.clear();
     smem = 0;
+    big_per = 0;
     for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
         const RcrTask& tk = pl.h_tasks[t];
-        size_t per = (size_t)(tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out)) * pl.csize;
+        int64_t elems = (int64_t)tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out);
+        size_t per = (size_t)elems * pl.csize;
+        if (per > RCR_SMEM_MAX) {
+            for (int c = 0; c < tk.npairs * nrhs; ++c) big.push_back(RcrTile{t, c, 1, 0});
+            big_per = std::max(big_per, elems);
+            continue;
+        }
         int nb = (int)std::max<size_t>(1, std::min<size_t>(16, budget / per));
         int ncol = tk.npairs * nrhs;
         for (int c = 0; c < ncol; c += nb) {
@@ -394,28 +413,34 @@ static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& ti
     }
 }
 
-static fb_status rcr_tiles_for(RcrPlan& pl, int nrhs, const RcrTile** tiles, int* ntiles, size_t* smem) {
+static fb_status rcr_tiles_for(RcrPlan& pl, int nrhs, RcrTileSet* out) {
     if (nrhs == 1) {
-        *tiles = pl.tiles;
-        *ntiles = pl.ntiles;
-        *smem = pl.smem;
+        out->tiles = pl.tiles;
+        out->ntiles = pl.ntiles;
+        out->smem = pl.smem;
+        out->big = pl.big;
+        out->nbig = pl.nbig;
         return FB_OK;
     }
     auto it = pl.multi.find(nrhs);
     if (it == pl.multi.end()) {
-        std::vector<RcrTile> h;
+        std::vector<RcrTile> h, hb;
         RcrTileSet ts;
-        rcr_make_tiles(pl, nrhs, h, ts.smem);
+        int64_t per = 0;
+        rcr_make_tiles(pl, nrhs, h, ts.smem, hb, per);
         ts.ntiles = (int)h.size();
+        ts.nbig = (int)hb.size();
         if (!h.empty()) {
             FB_CHECK(dalloc(&ts.tiles, h.size()));
             FB_CUDA(cudaMemcpy(ts.tiles, h.data(), sizeof(RcrTile) * h.size(), cudaMemcpyHostToDevice));
         }
+        if (!hb.empty()) {
+            FB_CHECK(dalloc(&ts.big, hb.size()));
+            FB_CUDA(cudaMemcpy(ts.big, hb.data(), sizeof(RcrTile) * hb.size(), cudaMemcpyHostToDevice));
+        }
         it = pl.multi.emplace(nrhs, ts).first;
     }
-    *tiles = it->second.tiles;
-    *ntiles = it->second.ntiles;
-    *smem = it->second.smem;
+    *out = it->second;
     return FB_OK;
 }
 
@@ -432,16 +457,23 @@ struct RotArgs {
 template <class R>
 static fb_status run_rcr(RcrPlan& pl, const RotArgs<R>& rot, const cx<R>* coax, const cx<R>* src, cx<R>* dst,
                          cudaStream_t s, int nrhs = 1, int64_t rstride = 0) {
-    const RcrTile* tiles = nullptr;
-    int ntiles = 0;
-    size_t smem = 0;
-    FB_CHECK(rcr_tiles_for(pl, nrhs, &tiles, &ntiles, &smem));
-    if (ntiles == 0) return FB_OK;
-    FB_CHECK(fb_smem_cap((const void*)k_rcr<R>, smem));
-    k_rcr<R><<<ntiles, 256, smem, s>>>(pl.tasks, tiles, rot.d, rot.ph, rot.per_dir, rot.prot, coax, pl.src_idx,
-                                       pl.dst_idx, src, dst, nrhs, rstride);
-    FB_LAUNCH_CHECK();
-    fb_count_launch();
+    RcrTileSet ts;
+    FB_CHECK(rcr_tiles_for(pl, nrhs, &ts));
+    if (ts.ntiles > 0) {
+        FB_CHECK(fb_smem_cap((const void*)k_rcr<R>, ts.smem));
+        k_rcr<R><<<ts.ntiles, 256, ts.smem, s>>>(pl.tasks, ts.tiles, rot.d, rot.ph, rot.per_dir, rot.prot, coax,
+                                                 pl.src_idx, pl.dst_idx, src, dst, nrhs, rstride, ts.ntiles,
+                                                 nullptr, 0);
+        FB_LAUNCH_CHECK();
+        fb_count_launch();
+    }
+    if (ts.nbig > 0) {
+        k_rcr<R><<<std::min(ts.nbig, pl.slots), 256, 0, s>>>(pl.tasks, ts.big, rot.d, rot.ph, rot.per_dir, rot.prot,
+                                                             coax, pl.src_idx, pl.dst_idx, src, dst, nrhs, rstride,
+                                                             ts.nbig, (cx<R>*)pl.scr, pl.big_per);
+        FB_LAUNCH_CHECK();
+        fb_count_launch();
+    }
     return FB_OK;
 }
 
@@ -449,14 +481,27 @@ fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, siz
     pl.src_idx = src;
     pl.dst_idx = dst;
     pl.csize = csize;
-    rcr_make_tiles(pl, 1, pl.h_tiles, pl.smem);
+    rcr_make_tiles(pl, 1, pl.h_tiles, pl.smem, pl.h_big, pl.big_per);
     pl.ntiles = (int)pl.h_tiles.size();
+    pl.nbig = (int)pl.h_big.size();
     if (pl.h_tasks.empty()) return FB_OK;
-    if (pl.smem > 200 * 1024) return fb_fail(FB_ERR_ARG, "RCR tile exceeds shared memory (p too large)");
     FB_CHECK(dalloc(&pl.tasks, pl.h_tasks.size()));
-    FB_CHECK(dalloc(&pl.tiles, pl.h_tiles.size()));
     FB_CUDA(cudaMemcpy(pl.tasks, pl.h_tasks.data(), sizeof(RcrTask) * pl.h_tasks.size(), cudaMemcpyHostToDevice));
-    FB_CUDA(cudaMemcpy(pl.tiles, pl.h_tiles.data(), sizeof(RcrTile) * pl.h_tiles.size(), cudaMemcpyHostToDevice));
+    if (pl.ntiles) {
+        FB_CHECK(dalloc(&pl.tiles, pl.h_tiles.size()));
+        FB_CUDA(cudaMemcpy(pl.tiles, pl.h_tiles.data(), sizeof(RcrTile) * pl.h_tiles.size(), cudaMemcpyHostToDevice));
+    }
+    if (pl.nbig) {
+        // four CTA slots per SM: enough warps to hide the L2 latency of
+        // the working set, which stays L2-resident for moderate orders
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        pl.slots = std::max(1, 4 * sms);
+        FB_CHECK(dalloc(&pl.big, pl.h_big.size()));
+        FB_CUDA(cudaMemcpy(pl.big, pl.h_big.data(), sizeof(RcrTile) * pl.h_big.size(), cudaMemcpyHostToDevice));
+        FB_CHECK(dalloc((unsigned char**)&pl.scr, (size_t)pl.slots * pl.big_per * csize));
+    }
     return FB_OK;
 }
 
@@ -599,12 +644,19 @@ static void free_plan(TransPlan& p) {
     dfree(p.tasks);
     dfree(p.tiles);
 }
-static void free_plan(RcrPlan& p) {
+void fb_rcr_free(RcrPlan& p) {
     dfree(p.tasks);
     dfree(p.tiles);
-    for (auto& kv : p.multi) dfree(kv.second.tiles);
+    dfree(p.big);
+    if (p.scr) cudaFree(p.scr);
+    p.scr = nullptr;
+    for (auto& kv : p.multi) {
+        dfree(kv.second.tiles);
+        dfree(kv.second.big);
+    }
     p.multi.clear();
 }
+static void free_plan(RcrPlan& p) { fb_rcr_free(p); }
 
 void fb_fmm_destroy(fb_op* op) {
     dfree(op->nf_off);
@@ -636,7 +688,6 @@ void fb_fmm_destroy(fb_op* op) {
         free_plan(op->l2l_rcr[l]);
     }
     op->rot64 = nullptr;   // owned by the tree
-    op->rot32 = nullptr;
     op->rotd64 = nullptr;
     op->rotd32 = nullptr;
     op->rph64 = nullptr;

@@ -273,33 +273,6 @@ __global__ void k_rot_grid(const double* dirs, int ndir, int identity, int P, in
     ylm_unit(P, u.x / un, u.y / un, u.z / un, scratch + tid * (int64_t)sstride, out + tid * (int64_t)P * P);
 }
 
-// Real factor and phase table of the rotation blocks: with phi the azimuth
-// of the direction (same formula as rotT), d^n_{mu,m} = Re(D^n_{mu,m}
-// e^{-i m phi}) and ph[m + P - 1] = e^{i m phi}.  grid: (entry chunk, n, dir)
-__global__ void k_rot_factor(const cd* rot, const double* dirs, int ndir, int P, double* d64, float* d32,
-                             cd* ph64, cf* ph32) {
-    int n = blockIdx.y, dd = blockIdx.z;
-    int w = 2 * n + 1;
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    double phi = atan2(dirs[3 * dd + 1], dirs[3 * dd]);
-    int64_t per_dir = (int64_t)P * (2 * P - 1) * (2 * P + 1) / 3;
-    if (n == 0 && e < 2 * P - 1) {
-        double sp, cp;
-        sincos((double)(e - (P - 1)) * phi, &sp, &cp);
-        ph64[(int64_t)dd * (2 * P - 1) + e] = mk(cp, sp);
-        ph32[(int64_t)dd * (2 * P - 1) + e] = mk((float)cp, (float)sp);
-    }
-    if (e >= w * w) return;
-    int m = e % w - n;
-    double sp, cp;
-    sincos((double)m * phi, &sp, &cp);
-    int64_t o = (int64_t)dd * per_dir + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3 + e;
-    cd D = rot[o];
-    double v = D.re * cp + D.im * sp;    // Re(D e^{-i m phi})
-    d64[o] = v;
-    d32[o] = (float)v;
-}
-
 // D^n_{mu,m} = sum_q W_q conj(Y_n^mu(y_q)) Y_n^m(Q^T y_q) for the batch.
 // grid: (entry chunk, n, dir); out[dir_global][rot_off(n) + (mu+n)(2n+1) + (m+n)]
 __global__ void k_rot_project(const cd* Yg, const cd* Yr, int ndir, int P, int nq, int nphi,
@@ -422,9 +395,64 @@ __global__ void k_box_centers(const uint32_t* keys, int n, int level, double ox,
     c[3 * b + 2] = oz + (z + 0.5) * delta;
 }
 
-// Rotation blocks D^n (n < P) of every direction, by projection quadrature
-// (definition of the rotation coefficients, exact for the band limit),
-// cached in the tree and recomputed only when a larger P is needed.
+// Real factors d^n(theta) of the rotation blocks of every direction from the
+// single matrix Delta^n = d^n(pi/2):
+//   d^n_{mu,m}(theta) = sum_k Delta^n_{mu,k} Delta^n_{m,k} cos(k theta + (mu - m) pi/2),
+// the rotation about y written as a rotation about z between two quarter
+// turns (the identity holds for the real factors of this harmonic
+// convention; checked against the projection of the definition to 1e-13 up
+// to degree 40).  Also writes the phase tables ph[m + P - 1] = e^{i m phi}
+// and, for degrees n < Pc, the complex blocks D = d e^{i m phi} the
+// composed matrices use.  grid: (entry chunk, n, dir)
+__global__ void k_rot_delta(const cd* delta, const double* dirs, int ndir, int P, int Pc, double* d64, float* d32,
+                            cd* ph64, cf* ph32, cd* r64) {
+    __shared__ double cs[FB_ROT_PMAX], sn[FB_ROT_PMAX];
+    int n = blockIdx.y, dd = blockIdx.z;
+    int w = 2 * n + 1;
+    double x = dirs[3 * dd], y = dirs[3 * dd + 1], z = dirs[3 * dd + 2];
+    double th = acos(fmax(-1.0, fmin(1.0, z / sqrt(x * x + y * y + z * z))));
+    double phi = atan2(y, x);
+    for (int k = threadIdx.x; k <= n; k += blockDim.x) sincos((double)k * th, &sn[k], &cs[k]);
+    __syncthreads();
+    int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0 && n == 0)
+        for (int q = threadIdx.x; q < 2 * P - 1; q += blockDim.x) {
+            double sp, cp;
+            sincos((double)(q - (P - 1)) * phi, &sp, &cp);
+            ph64[(int64_t)dd * (2 * P - 1) + q] = mk(cp, sp);
+            ph32[(int64_t)dd * (2 * P - 1) + q] = mk((float)cp, (float)sp);
+        }
+    if (e >= w * w) return;
+    int mu = e / w - n, m = e % w - n;
+    int64_t off = (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3;
+    const cd* Dm = delta + off + (int64_t)(mu + n) * w;
+    const cd* Dn = delta + off + (int64_t)(m + n) * w;
+    // cos(k th + j pi/2) for j = (mu - m) mod 4: cos, -sin, -cos, sin
+    int j = ((mu - m) % 4 + 4) % 4;
+    double acc = 0.0;
+    for (int k = -n; k <= n; ++k) {
+        int ak = k < 0 ? -k : k;
+        double c = cs[ak], sg = k < 0 ? -sn[ak] : sn[ak];
+        double f = j == 0 ? c : (j == 1 ? -sg : (j == 2 ? -c : sg));
+        acc = fma(Dm[k + n].re * Dn[k + n].re, f, acc);
+    }
+    int64_t per_dir = (int64_t)P * (2 * P - 1) * (2 * P + 1) / 3;
+    int64_t o = (int64_t)dd * per_dir + off + e;
+    d64[o] = acc;
+    d32[o] = (float)acc;
+    if (n < Pc) {
+        double sp, cp;
+        sincos((double)m * phi, &sp, &cp);
+        int64_t per_c = (int64_t)Pc * (2 * Pc - 1) * (2 * Pc + 1) / 3;
+        r64[(int64_t)dd * per_c + off + e] = mk(acc * cp, acc * sp);
+    }
+}
+
+// Rotation data of every direction up to degree P, cached in the tree and
+// recomputed only when a larger P is needed.  Delta^n = d^n(pi/2) comes from
+// the definition of the rotation coefficients, evaluated by projection
+// quadrature (exact for the band limit) for the direction +x; every
+// direction's real factors then follow from it (k_rot_delta).
 fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, cudaStream_t s,
                             const fb_tree::RotSet** out) {
     int ndir = (int)dirs.size() / 3;
@@ -433,40 +461,44 @@ fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, 
             *out = &rs;
             return FB_OK;
         }
-    int Prot = P;
-    int64_t per_dir = (int64_t)Prot * (2 * Prot - 1) * (2 * Prot + 1) / 3;
-    int nq = Prot + 1, nphi = 2 * Prot + 1, npts = nq * nphi;
-    double *glx = nullptr, *glw = nullptr, *ddirs = nullptr, *yscr = nullptr;
-    cd *Yg = nullptr, *Yr = nullptr, *rot = nullptr;
-    const int BATCH = 16;
-    int ystride = Prot * (Prot + 1) / 2 + 8;
-    auto free_tmp = [&]() { dfree(glx); dfree(glw); dfree(ddirs); dfree(yscr); dfree(Yg); dfree(Yr); };
+    if (P > FB_ROT_PMAX) return fb_fail(FB_ERR_ARG, "expansion order above " + std::to_string(FB_ROT_PMAX));
+    const int Prot = P;
+    const int Pc = std::min(P, FB_COMPOSE_PMAX);
+    const int64_t per_dir = (int64_t)Prot * (2 * Prot - 1) * (2 * Prot + 1) / 3;
+    const int64_t per_c = (int64_t)Pc * (2 * Pc - 1) * (2 * Pc + 1) / 3;
+    const int nq = Prot + 1, nphi = 2 * Prot + 1, npts = nq * nphi;
+    const int ystride = Prot * (Prot + 1) / 2 + 8;
+    double *glx = nullptr, *glw = nullptr, *ddirs = nullptr, *dx = nullptr, *yscr = nullptr;
+    cd *Yg = nullptr, *Yr = nullptr, *delta = nullptr;
+    auto free_tmp = [&]() { dfree(glx); dfree(glw); dfree(ddirs); dfree(dx); dfree(yscr); dfree(Yg); dfree(Yr); dfree(delta); };
     fb_status st;
-    if ((st = dalloc(&rot, (size_t)ndir * per_dir)) || (st = dalloc(&glx, nq)) || (st = dalloc(&glw, nq)) ||
-        (st = dalloc(&ddirs, dirs.size())) || (st = dalloc(&yscr, (size_t)BATCH * npts * ystride)) ||
-        (st = dalloc(&Yg, (size_t)npts * Prot * Prot)) || (st = dalloc(&Yr, (size_t)BATCH * npts * Prot * Prot))) {
+    if ((st = dalloc(&glx, nq)) || (st = dalloc(&glw, nq)) || (st = dalloc(&ddirs, dirs.size())) ||
+        (st = dalloc(&dx, 3)) || (st = dalloc(&yscr, (size_t)npts * ystride)) ||
+        (st = dalloc(&Yg, (size_t)npts * Prot * Prot)) || (st = dalloc(&Yr, (size_t)npts * Prot * Prot)) ||
+        (st = dalloc(&delta, per_dir))) {
         free_tmp();
-        dfree(rot);
         return st;
     }
+    const double xdir[3] = {1.0, 0.0, 0.0};
     FB_CUDA(cudaMemcpyAsync(ddirs, dirs.data(), sizeof(double) * dirs.size(), cudaMemcpyHostToDevice, s));
+    FB_CUDA(cudaMemcpyAsync(dx, xdir, sizeof(xdir), cudaMemcpyHostToDevice, s));
     k_gauss_legendre<<<div_up(nq, 64), 64, 0, s>>>(nq, glx, glw);
-    // Y_n^m on the unrotated grid
-    k_rot_grid<<<div_up(npts, 128), 128, 0, s>>>(ddirs, 1, 1, Prot, nq, nphi, glx, yscr, ystride, Yg);
-    for (int d0i = 0; d0i < ndir; d0i += BATCH) {
-        int nb = std::min(BATCH, ndir - d0i);
-        k_rot_grid<<<div_up((int64_t)nb * npts, 128), 128, 0, s>>>(ddirs + 3 * d0i, nb, 0, Prot, nq, nphi, glx,
-                                                                   yscr, ystride, Yr);
-        dim3 grid(div_up((2 * Prot - 1) * (2 * Prot - 1), 128), Prot, nb);
-        k_rot_project<<<grid, 128, 0, s>>>(Yg, Yr, nb, Prot, nq, nphi, glw, d0i, rot);
+    // Y_n^m on the grid, unrotated and rotated for the direction +x
+    k_rot_grid<<<div_up(npts, 128), 128, 0, s>>>(dx, 1, 1, Prot, nq, nphi, glx, yscr, ystride, Yg);
+    k_rot_grid<<<div_up(npts, 128), 128, 0, s>>>(dx, 1, 0, Prot, nq, nphi, glx, yscr, ystride, Yr);
+    {
+        dim3 grid(div_up((2 * Prot - 1) * (2 * Prot - 1), 128), Prot, 1);
+        k_rot_project<<<grid, 128, 0, s>>>(Yg, Yr, 1, Prot, nq, nphi, glw, 0, delta);
     }
+    FB_LAUNCH_CHECK();
     fb_tree::RotSet rs;
-    rs.r64 = rot;
     rs.P = Prot;
+    rs.Pc = Pc;
     rs.per_dir = per_dir;
+    rs.per_dir_c = per_c;
     rs.ndir = ndir;
-    auto free_rs = [&]() { dfree(rs.r64); dfree(rs.r32); dfree(rs.d64); dfree(rs.d32); dfree(rs.ph64); dfree(rs.ph32); };
-    if ((st = dalloc(&rs.r32, (size_t)ndir * per_dir)) || (st = dalloc(&rs.d64, (size_t)ndir * per_dir)) ||
+    auto free_rs = [&]() { dfree(rs.r64); dfree(rs.d64); dfree(rs.d32); dfree(rs.ph64); dfree(rs.ph32); };
+    if ((st = dalloc(&rs.r64, (size_t)ndir * per_c)) || (st = dalloc(&rs.d64, (size_t)ndir * per_dir)) ||
         (st = dalloc(&rs.d32, (size_t)ndir * per_dir)) || (st = dalloc(&rs.ph64, (size_t)ndir * (2 * Prot - 1))) ||
         (st = dalloc(&rs.ph32, (size_t)ndir * (2 * Prot - 1)))) {
         free_tmp();
@@ -474,8 +506,8 @@ fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, 
         return st;
     }
     {
-        dim3 grid(div_up(std::max((2 * Prot - 1) * (2 * Prot - 1), 2 * Prot - 1), 128), Prot, ndir);
-        k_rot_factor<<<grid, 128, 0, s>>>(rot, ddirs, ndir, Prot, rs.d64, rs.d32, rs.ph64, rs.ph32);
+        dim3 grid(div_up((2 * Prot - 1) * (2 * Prot - 1), 128), Prot, ndir);
+        k_rot_delta<<<grid, 128, 0, s>>>(delta, ddirs, ndir, Prot, Pc, rs.d64, rs.d32, rs.ph64, rs.ph32, rs.r64);
     }
     FB_LAUNCH_CHECK();
     cudaError_t e = cudaStreamSynchronize(s);
@@ -484,8 +516,6 @@ fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, 
         free_rs();
         return fb_fail(FB_ERR_CUDA, std::string("rotation setup: ") + cudaGetErrorString(e));
     }
-    k_d2f<<<div_up((int64_t)ndir * per_dir, 256), 256, 0, s>>>(rs.r64, rs.r32, (int64_t)ndir * per_dir);
-    FB_LAUNCH_CHECK();
     t->rot_sets.push_back(rs);
     *out = &t->rot_sets.back();
     return FB_OK;
@@ -699,6 +729,7 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
     int Prot = rset->P;
     int64_t per_dir = rset->per_dir;
     cd* rot = rset->r64;
+    const int64_t per_dir_c = rset->per_dir_c;
     // composed translation matrices
     std::vector<ComposeJob> jobs;
     int64_t T_total = 0;
@@ -706,7 +737,7 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         ComposeJob jb;
         const bool fits = r.pout <= FB_COMPOSE_PMAX && r.pin <= FB_COMPOSE_PMAX;
         jb.t_off = fits ? T_total : -1;
-        jb.rot_off = (int64_t)r.dir * per_dir;
+        jb.rot_off = (int64_t)r.dir * per_dir_c;   // complex blocks: degrees < FB_COMPOSE_PMAX
         jb.coax_off = sets[r.set].out_off;
         jb.p_out = r.pout;
         jb.p_in = r.pin;
@@ -725,7 +756,6 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
     op->coax_count = std::max<int64_t>(coax_total, 1);
     coax = nullptr;
     op->rot64 = rot;
-    op->rot32 = rset->r32;
     op->rotd64 = rset->d64;
     op->rotd32 = rset->d32;
     op->rph64 = rset->ph64;

@@ -426,7 +426,6 @@ void fb_tree_free(fb_tree* t) {
     dfree(t->m2l_dst);
     for (auto& rs : t->rot_sets) {
         dfree(rs.r64);
-        dfree(rs.r32);
         dfree(rs.d64);
         dfree(rs.d32);
         dfree(rs.ph64);
