@@ -262,6 +262,22 @@ def cfg_baffle_sub(nsrc=4, nrec=16):
     return baffle_workload(250.0, h=0.25, nsrc=nsrc, nrec=nrec)
 
 
+def cfg_largest(nrec=1024):
+    """Largest room: shoebox 6.5 x 5.5 x 4.2 m at 5 kHz, legs lambda/6
+    (569 x 482 x 368 rectangles, N = 2,644,104), one admittance per wall
+    drawn uniform in [0.05, 0.3], a seeded monopole and `nrec` receivers
+    (>= 0.25 m from the walls, >= 0.1 m from the source)."""
+    lx, ly, lz = 6.5, 5.5, 4.2
+    h = SOUND_SPEED / 5000.0 / 6.0
+    rng = seeded_rng(4)
+    beta_wall = rng.uniform(0.05, 0.3, size=6)
+    src = uniform_points_in_box(rng, [0, 0, 0], [lx, ly, lz], 1, 0.25)
+    wl = shoebox_workload(f"shoebox-{lx}x{ly}x{lz}-5kHz", lx, ly, lz, shoebox_counts_for_h(lx, ly, lz, h),
+                          5000.0, 0.0, src[0], nrec, 4, beta_per_wall=beta_wall)
+    wl.name += f"-N{wl.n}"
+    return wl
+
+
 def seeded_rng(config_index: int) -> np.random.Generator:
     """numpy PCG64 seeded with 2103_16073 + config index."""
     return np.random.Generator(np.random.PCG64(2103_16073 + int(config_index)))

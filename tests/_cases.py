@@ -35,6 +35,7 @@ def workload(name):
         "high_order": lambda: W.shoebox_workload("shoebox-3.0x2.4x2.0-7.5kHz-N3072", 3.0, 2.4, 2.0, (16, 16, 16),
                                                  7500.0, 0.2, (0.7, 0.6, 0.5), 8, 0),
         "baffle": W.cfg_baffle,
+        "largest": W.cfg_largest,
         # a small room with walls of different admittance and a ragged count
         "ragged": lambda: W.shoebox_workload("ragged-1.3x1.1x0.9-700Hz", 1.3, 1.1, 0.9, (11, 9, 7),
                                              700.0, 0.2, (0.31, 0.42, 0.27), 16, 7,

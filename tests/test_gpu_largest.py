@@ -1,0 +1,94 @@
+"""The largest room (shoebox 6.5 x 5.5 x 4.2 m at 5 kHz, legs lambda/6,
+N = 2,644,104, expansion orders up to 159) in the launch configuration of a
+solve (mixed FMM with autotuned forms and graph replay, FP64 FMM true
+residual): sampled rows of both matvecs against the oracle's rows, and the
+exterior-source test on the full mesh, on the surface and at receivers
+(the field of a monopole outside the room solves the interior problem
+exactly, so the discrete solution and the receiver field of Eq. (dbem1)
+approach it)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2103_16073_gb300 as fb
+from paper_2103_16073_gb300 import workloads as W
+from _cases import oracle_mesh, rel, seeded_vector, workload
+
+
+@pytest.fixture(scope="module")
+def largest():
+    wl = workload("largest")
+    mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+    fb.fb_mesh_set_admittance(mesh, wl.beta)
+    tree = fb.fb_tree_build(mesh, 64)
+    A32 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 12)
+    fb.fb_operator_autotune(A32, 1)
+    fb.fb_operator_use_graphs(A32, True)
+    A64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, 12)
+    yield wl, mesh, tree, A32, A64
+    for op in (A32, A64):
+        fb.fb_operator_destroy(op)
+    fb.fb_tree_destroy(tree)
+    fb.fb_mesh_destroy(mesh)
+
+
+def test_largest_matvec_sampled_rows(largest):
+    from oracle import bem
+    wl, mesh, tree, A32, A64 = largest
+    assert wl.n == 2644104
+    n, L, p = fb.fb_operator_info(A64)
+    assert max(p) >= 150
+    om = oracle_mesh("largest")
+    rows = np.sort(np.random.default_rng(9).choice(wl.n, size=16, replace=False))
+    Ar = bem.system_rows(om, wl.k, wl.beta, rows)
+    x = seeded_vector(wl.n, 91)
+    xd = torch.tensor(x, device="cuda")
+    yd = torch.empty_like(xd)
+    for op, tol in ((A64, 1e-5), (A32, 2e-5)):
+        fb.fb_operator_apply(op, xd, yd)
+        torch.cuda.synchronize()
+        err = rel(yd.cpu().numpy()[rows], Ar @ x)
+        print(f"sampled rows rel err {err:.2e}")
+        assert err < tol
+
+
+def test_largest_exterior_source(largest):
+    from oracle import bem
+    wl, mesh, tree, A32, A64 = largest
+    om = oracle_mesh("largest")
+    xe = W.exterior_source(wl.room)
+    u, gu = bem.incident(om.el.centroid, xe, wl.k)
+    gam = bem.gamma_field(om, wl.k, wl.beta, u, np.sum(gu * om.el.normal, 1))
+    gd = torch.tensor(gam, device="cuda")
+    L64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_L, fb.FB_PREC_FP64_FMM, 6.0, 12)
+    Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 2.0, 4)
+    pclow = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
+    inner = fb.fb_precond_create_inner(A32, Alow, pclow, 8)
+    try:
+        b = torch.empty_like(gd)
+        fb.fb_operator_apply(L64, gd, b)
+        x = torch.zeros_like(b)
+        info = fb.fb_fgmres_solve(A32, b, x, pc=inner, tol=1e-5, restart=40, maxit=400, max_refine=6,
+                                  true_op=A64)
+        assert info["status"] == 0 and info["true_relres"] <= 1e-5
+        psi = x.cpu().numpy()
+        e_surf = rel(psi, u)
+        rcv = wl.receivers
+        out = torch.empty(rcv.shape[0], dtype=torch.complex128, device="cuda")
+        fb.fb_eval_field(mesh, wl.k, x, gd, torch.tensor(rcv, device="cuda"), out)
+        got = out.cpu().numpy()
+        ue, _ = bem.incident(rcv, xe, wl.k)
+        e_rcv = rel(got, ue)
+        ref = bem.receiver_field(om, wl.k, wl.beta, psi, gam, rcv[:8])
+        e_par = rel(got[:8], ref)
+        print(f"iterations {info['iters']}; exterior source: surface {e_surf:.3e}, 1024 receivers {e_rcv:.3e}; "
+              f"receiver field vs oracle {e_par:.1e}")
+        assert e_par < 1e-10
+        assert e_surf < 0.045 and e_rcv < 0.04   # discretisation error at 6 elements per wavelength
+    finally:
+        fb.fb_precond_destroy(inner)
+        fb.fb_precond_destroy(pclow)
+        fb.fb_operator_destroy(Alow)
+        fb.fb_operator_destroy(L64)
