@@ -54,3 +54,37 @@ def test_sweep_batch(lookahead):
         for b in built:
             fb.fb_tree_destroy(b["tree"])
             fb.fb_mesh_destroy(b["mesh"])
+
+
+def test_sweep_top_frequency_full_size():
+    """The sweep's largest job at full size (2 kHz, legs lambda/8,
+    N = 567,592, 8 sources in one lockstep batch, orders above one shared-
+    memory tile in FP64): every solve meets the FP64 true residual, and one
+    solution's residual on sampled rows of the oracle's A and L stays at
+    the tolerance."""
+    from oracle import bem
+    wl = sweep.W.lroom_sweep(nfreq=64, f_lo=100.0, f_hi=2000.0, nsrc=8)[-1]
+    assert wl.n == 567592
+    mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+    fb.fb_mesh_set_admittance(mesh, wl.beta)
+    tree = fb.fb_tree_build(mesh, 64)
+    job = dict(mesh=mesh, tree=tree, k=wl.k, src=wl.sources,
+               x=torch.zeros((8, wl.n), dtype=torch.complex128, device="cuda"))
+    try:
+        (r,) = fb.fb_batch_solve([job], tol=1e-4, max_rhs=8, autotune=True, lookahead=False)
+        assert r["status"] == 0
+        assert all(i["status"] == 0 and i["true_relres"] <= 1e-4 for i in r["infos"])
+        om = bem.Mesh(wl.verts, wl.tris)
+        rows = np.sort(np.random.default_rng(12).choice(wl.n, size=16, replace=False))
+        Ar = bem.system_rows(om, wl.k, wl.beta, rows)
+        Lr, _, _ = bem.operator_rows(om, wl.k, om.el.centroid[rows], om.el.normal[rows], rows)
+        q = 5
+        gam = bem.gamma_monopole(om, wl.k, wl.beta, wl.sources[q])
+        b_rows = Lr @ gam
+        res = b_rows - Ar @ job["x"][q].cpu().numpy()
+        err = np.linalg.norm(res) / np.linalg.norm(b_rows)
+        print(f"iterations {[i['iters'] for i in r['infos']]}, sampled-row residual {err:.2e}")
+        assert err < 5e-4
+    finally:
+        fb.fb_tree_destroy(tree)
+        fb.fb_mesh_destroy(mesh)
