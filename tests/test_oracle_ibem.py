@@ -1,0 +1,75 @@
+"""Pins for the oracle's indirect formulation (Eqs. ibem1-ibem5).
+
+Two-sided exact solution: with boundary data built from a field u regular
+inside the room (a monopole outside) on the - side and a field v regular and
+radiating outside (a monopole inside) on the + side, the solution of
+Eq. (ibem5) is psi- = u, psi+ = v up to the discretisation; both errors fall
+under refinement.  Flipping the sign of M' or M, dropping the (a+ psi+ -
+a- psi-)/2 term, transposing L' or swapping the sides each raise the + side
+error above 14 % at the finer mesh, where the correct system gives 2.9 %.
+Cross-validation: for a monopole inside an absorbing room, the receiver
+field of the indirect solution approaches that of the direct formulation
+(Eq. dbem4) under refinement."""
+import functools
+
+import numpy as np
+
+from oracle import bem, hypersingular, ibem
+from paper_2103_16073_gb300 import workloads as W
+
+ROOM = (1.0, 0.8, 0.6)
+K = 6.0
+X_IN = np.array([0.31, 0.42, 0.27])
+X_OUT = np.array([1.73, 0.37, 0.41])
+
+
+@functools.lru_cache(maxsize=None)
+def _ops(nn):
+    v, t, _ = W.shoebox_mesh(*ROOM, nn, nn, nn)
+    mesh = bem.Mesh(v, t)
+    L, M, LP = bem.dense_operators(mesh, K)
+    return mesh, L, M, LP, hypersingular.dense_mp(mesh, K)
+
+
+def _two_sided(nn):
+    mesh, L, M, LP, MP = _ops(nn)
+    el, n = mesh.el, mesh.n
+    bp = np.full(n, 0.3 + 0.1j)
+    bm = np.full(n, 0.2 + 0j)
+    u, gu = bem.incident(el.centroid, X_OUT, K)
+    v, gv = bem.incident(el.centroid, X_IN, K)
+    gp, gm = ibem.gammas_two_sided(K, bp, bm, v, np.sum(gv * el.normal, 1), u, np.sum(gu * el.normal, 1))
+    x = np.linalg.solve(ibem.system(L, M, LP, MP, K, bp, bm), ibem.rhs(L, LP, gp, gm))
+    sig, mu = ibem.densities(K, bp, bm, x[:n], x[n:], gp, gm)
+    xr = np.array([[0.5, 0.4, 0.3], [0.2, 0.6, 0.45]])
+    f = ibem.field(mesh, K, sig, mu, xr)
+    fu, _ = bem.incident(xr, X_OUT, K)
+    return (np.linalg.norm(x[n:] - u) / np.linalg.norm(u), np.linalg.norm(x[:n] - v) / np.linalg.norm(v),
+            np.linalg.norm(f - fu) / np.linalg.norm(fu))
+
+
+def test_two_sided_exact_solution():
+    m4, p4, f4 = _two_sided(4)
+    m6, p6, f6 = _two_sided(6)
+    assert p6 < 0.04 and p6 < 0.7 * p4
+    assert m6 < 0.25 and m6 < 0.8 * m4
+    assert f6 < 0.8 * f4
+
+
+def test_direct_indirect_cross_validation():
+    xr = np.array([[0.7, 0.3, 0.35], [0.5, 0.55, 0.2], [0.25, 0.2, 0.4]])
+    diffs = []
+    for nn in (4, 6):
+        mesh, L, M, LP, MP = _ops(nn)
+        el, n = mesh.el, mesh.n
+        beta = np.full(n, 0.2 + 0j)
+        g = bem.gamma_monopole(mesh, K, beta, X_IN)
+        psi = np.linalg.solve(bem.system_matrix(L, M, K, beta), L @ g)
+        fd = bem.receiver_field(mesh, K, beta, psi, g, xr, X_IN)
+        u, gu = bem.incident(el.centroid, X_IN, K)
+        gp, gm = ibem.gammas_incident(K, beta, beta, u, np.sum(gu * el.normal, 1))
+        x = np.linalg.solve(ibem.system(L, M, LP, MP, K, beta, beta), ibem.rhs(L, LP, gp, gm))
+        sig, mu = ibem.densities(K, beta, beta, x[:n], x[n:], gp, gm)
+        fi = ibem.field(mesh, K, sig, mu, xr) + bem.incident(xr, X_IN, K)[0]
+        diffs.append(np.linalg.norm(fd - fi) / np.linalg.norm(fd))
+    assert diffs[1] < 0.07 and diffs[1] < 0.75 * diffs[0]
