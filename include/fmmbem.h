@@ -71,6 +71,18 @@ typedef int fb_status;
                       form (n_x.n)[k^2 S + sum_e int_e grad_y G.m dl]
                       + sum_e int_e (n.grad_x G)(t.m) dl, far by the 3-point rule
                       of d2G/dn_x dn_y; FMM: dipole P2M and normal-gradient L2P) */
+#define FB_OP_IBEM 5 /* indirect-BEM system of Eq. ibem5 with two unknowns per
+                      element, x = [psi+ (N), psi- (N)] (scattered field on the
+                      side the normal points to, and on the other side), 2N x 2N:
+                        row 1: (psi- + psi+)/2 - M[psi+ - psi-] + L[a- psi- + a+ psi+]
+                        row 2: -M'[psi+ - psi-] + (a+ psi+ - a- psi-)/2
+                               + L'[a- psi- + a+ psi+]
+                      with a = k/(i zeta) = -i k beta per side (beta- = the mesh
+                      admittance, beta+ = fb_mesh_set_admittance_plus, default
+                      beta-), both copied at creation.  Composed of the L, M, L',
+                      M' operators of the given precision on the same tree; block
+                      Jacobi and the learned network do not apply to it (the
+                      inner-outer preconditioner does). */
 
 /* How an operator is applied. */
 #define FB_PREC_FP64_DENSE 0 /* stored dense N x N complex128 matrix        */
@@ -114,6 +126,12 @@ FB_API fb_status fb_mesh_create(const double* verts, int64_t nv, const int32_t* 
 /* Per-element complex admittance beta = 1/zeta (Eq. sp4; beta = 0 is the
  * rigid wall of Eq. sp5), nt interleaved complex values in `memspace`. */
 FB_API fb_status fb_mesh_set_admittance(fb_mesh* mesh, const double* beta, int memspace, void* stream);
+
+/* Admittance of the + side of every element for the indirect system
+ * (FB_OP_IBEM; Eq. ibem4: the side the normal points to), nt interleaved
+ * complex values in `memspace`.  Until set, the + side takes the admittance
+ * of fb_mesh_set_admittance. */
+FB_API fb_status fb_mesh_set_admittance_plus(fb_mesh* mesh, const double* beta, int memspace, void* stream);
 
 /* Element count, near-field cutoff r_c and longest edge. */
 FB_API fb_status fb_mesh_info(const fb_mesh* mesh, int64_t* nt, double* rc, double* max_edge);
@@ -328,6 +346,24 @@ FB_API fb_status fb_precond_apply(const fb_precond* pc, const double* x, double*
  * outlive it.  The inner steps run without host synchronisation.  P is not a
  * fixed linear map, which flexible GMRES admits.  Errors: FB_ERR_ARG. */
 #define FB_PC_INNER 3
+
+/* Indirect system (FB_OP_IBEM) helpers, device pointers, enqueued on `stream`.
+ * fb_ibem_gammas_monopole: boundary data of Eq. (ibem4) for a monopole at
+ *   src (3 doubles, host): gamma+ = d psi_in/dn - a+ psi_in and
+ *   gamma- = -d psi_in/dn - a- psi_in at the centroids (N complex each).
+ * fb_ibem_rhs: right-hand side of Eq. (ibem5), b = [L(gamma- + gamma+),
+ *   (gamma+ - gamma-)/2 + L'(gamma- + gamma+)] (2N complex).
+ * fb_ibem_field: scattered field off the surface, psi_sc = L[sigma] + M[mu]
+ *   (Eq. ibem1) with mu = psi+ - psi- and sigma = gamma- + gamma+ - a- psi-
+ *   - a+ psi+ (Eq. ibem4), from a solution x (2N) at nr receivers rcv
+ *   (nr x 3 doubles, device), by direct summation into out (nr complex).
+ *   The mesh admittance must still be the one the operator was built with.
+ * Errors: FB_ERR_ARG if op is not FB_OP_IBEM. */
+FB_API fb_status fb_ibem_gammas_monopole(fb_op* op, const double* src, double* gamma_p, double* gamma_m,
+                                         void* stream);
+FB_API fb_status fb_ibem_rhs(fb_op* op, const double* gamma_p, const double* gamma_m, double* b, void* stream);
+FB_API fb_status fb_ibem_field(fb_op* op, const double* x, const double* gamma_p, const double* gamma_m,
+                               const double* rcv, int64_t nr, double* out, void* stream);
 
 /* Training-data helper for learned preconditioners: the first k+1 Arnoldi
  * vectors of the right-preconditioned Krylov space of A from start vector b

@@ -37,7 +37,7 @@ __all__ = [
 ]
 
 FB_OK = 0
-FB_OP_L, FB_OP_M, FB_OP_LP, FB_OP_A, FB_OP_MP = 0, 1, 2, 3, 4
+FB_OP_L, FB_OP_M, FB_OP_LP, FB_OP_A, FB_OP_MP, FB_OP_IBEM = 0, 1, 2, 3, 4, 5
 FB_PREC_FP64_DENSE, FB_PREC_FP64_FMM, FB_PREC_MIXED_FMM = 0, 1, 2
 FB_MEM_HOST, FB_MEM_DEVICE = 0, 1
 FB_PC_NONE, FB_PC_BLOCK_JACOBI = 0, 1
@@ -599,3 +599,59 @@ def fb_learned_train_step(pc, R, E, lr, stream=None):
     _check(lib.fb_learned_train_step(pc, C.c_void_p(R.data_ptr()), C.c_void_p(E.data_ptr()), R.shape[0],
                                      float(lr), C.byref(loss), _stream(stream)))
     return loss.value
+
+
+lib.fb_mesh_set_admittance_plus.restype = C.c_int
+lib.fb_mesh_set_admittance_plus.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+lib.fb_ibem_gammas_monopole.restype = C.c_int
+lib.fb_ibem_gammas_monopole.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+lib.fb_ibem_rhs.restype = C.c_int
+lib.fb_ibem_rhs.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+lib.fb_ibem_field.restype = C.c_int
+lib.fb_ibem_field.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                              C.c_void_p]
+
+
+def fb_mesh_set_admittance_plus(mesh, beta, stream=None):
+    """Admittance of the + side (the side the normal points to) for the
+    indirect system FB_OP_IBEM."""
+    p, ms, keep = _ptr(beta, np.complex128)
+    _check(lib.fb_mesh_set_admittance_plus(mesh, p, ms, _stream(stream)))
+
+
+def _cuda_ptr(t, name):
+    if not _is_cuda_tensor(t):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def fb_ibem_gammas_monopole(op, src, stream=None):
+    """(gamma+, gamma-) of Eq. (ibem4) for a monopole at src: CUDA complex128
+    tensors of N values each (op: an FB_OP_IBEM operator)."""
+    import torch
+    n = fb_operator_info(op)[0] // 2
+    gp = torch.empty(n, dtype=torch.complex128, device="cuda")
+    gm = torch.empty_like(gp)
+    s = np.ascontiguousarray(src, dtype=np.float64)
+    _check(lib.fb_ibem_gammas_monopole(op, s.ctypes.data, C.c_void_p(gp.data_ptr()), C.c_void_p(gm.data_ptr()),
+                                       _stream(stream)))
+    return gp, gm
+
+
+def fb_ibem_rhs(op, gamma_p, gamma_m, stream=None):
+    """Right-hand side of Eq. (ibem5) (CUDA complex128, 2N) from gamma+/-."""
+    import torch
+    b = torch.empty(2 * gamma_p.numel(), dtype=torch.complex128, device="cuda")
+    _check(lib.fb_ibem_rhs(op, _cuda_ptr(gamma_p, "gamma_p"), _cuda_ptr(gamma_m, "gamma_m"), C.c_void_p(b.data_ptr()),
+                           _stream(stream)))
+    return b
+
+
+def fb_ibem_field(op, x, gamma_p, gamma_m, rcv, stream=None):
+    """Scattered field L[sigma] + M[mu] (Eq. ibem1) of a solution x (2N) at
+    receivers rcv (CUDA float64 [nr, 3]); returns CUDA complex128 [nr]."""
+    import torch
+    out = torch.empty(rcv.shape[0], dtype=torch.complex128, device="cuda")
+    _check(lib.fb_ibem_field(op, _cuda_ptr(x, "x"), _cuda_ptr(gamma_p, "gamma_p"), _cuda_ptr(gamma_m, "gamma_m"),
+                             _cuda_ptr(rcv, "rcv"), int(rcv.shape[0]), C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out

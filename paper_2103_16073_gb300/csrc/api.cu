@@ -25,6 +25,9 @@ fb_status fb_fgmres_multi_impl(fb_op*, fb_precond*, const cd*, cd*, int, const f
 fb_status fb_precond_create_impl(fb_op*, int, cudaStream_t, fb_precond**);
 fb_status fb_batch_solve_impl(fb_batch_job*, int, const fb_batch_opts*);
 fb_status fb_krylov_basis_impl(fb_op*, const fb_precond*, const cd*, int, cd*, cudaStream_t);
+fb_status fb_ibem_gammas_impl(fb_op*, const double*, cd*, cd*, cudaStream_t);
+fb_status fb_ibem_rhs_impl(fb_op*, const cd*, const cd*, cd*, cudaStream_t);
+fb_status fb_ibem_field_impl(fb_op*, const cd*, const cd*, const cd*, const double*, int64_t, cd*, cudaStream_t);
 void fb_precond_free(fb_precond*);
 fb_status fb_alu_peaks_impl(double*, double*, cudaStream_t);
 
@@ -95,6 +98,7 @@ static fb_status stage_out_finish(size_t bytes, int memspace, void* user, const 
 long long fb_launch_count() { return g_launches.load(); }
 
 fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs) {
+    if (op->kind == FB_OP_IBEM) return fb_ibem_apply(op, x, y, s, nrhs);
     if (op->prec == FB_PREC_FP64_DENSE) {
         for (int r = 0; r < nrhs; ++r) FB_CHECK(fb_dense_apply(op, x + r * op->n, y + r * op->n, s));
         return FB_OK;
@@ -183,12 +187,14 @@ fb_status fb_tree_export(const fb_tree* t, int which, int level, int64_t* out, i
 
 void fb_tree_destroy(fb_tree* t) { fb_tree_free(t); }
 
-fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k, int kind, int precision,
-                             double d0, int pmin, void* stream, fb_op** out) {
+}  // extern "C"
+
+fb_status fb_operator_create_impl(const fb_mesh* mesh, const fb_tree* tree, double k, int kind, int precision,
+                                  double d0, int pmin, cudaStream_t s, fb_op** out) {
     if (!mesh || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
     *out = nullptr;
     if (!(k > 0.0)) return fb_fail(FB_ERR_ARG, "k must be > 0");
-    if (kind < FB_OP_L || kind > FB_OP_MP) return fb_fail(FB_ERR_ARG, "unknown operator kind");
+    if (kind < FB_OP_L || kind > FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "unknown operator kind");
     if (precision < FB_PREC_FP64_DENSE || precision > FB_PREC_MIXED_FMM)
         return fb_fail(FB_ERR_ARG, "unknown precision");
     if (precision != FB_PREC_FP64_DENSE) {
@@ -196,7 +202,6 @@ fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k,
         if (tree->mesh != mesh) return fb_fail(FB_ERR_ARG, "tree was built from another mesh");
         if (!(d0 > 0.0) || pmin < 1) return fb_fail(FB_ERR_ARG, "need d0 > 0 and pmin >= 1");
     }
-    cudaStream_t s = as_stream(stream);
     fb_op* op = new fb_op();
     op->mesh = mesh;
     op->tree = tree;
@@ -207,7 +212,9 @@ fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k,
     op->d0 = d0;
     op->pmin = pmin;
     op->n = mesh->n;
-    fb_status st = precision == FB_PREC_FP64_DENSE ? fb_dense_create(op, s) : fb_fmm_create(op, d0, pmin, s);
+    fb_status st = kind == FB_OP_IBEM                  ? fb_ibem_create(op, s)
+                   : precision == FB_PREC_FP64_DENSE ? fb_dense_create(op, s)
+                                                     : fb_fmm_create(op, d0, pmin, s);
     if (st == FB_OK) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = fb_fail(FB_ERR_CUDA, std::string("operator setup: ") + cudaGetErrorString(e));
@@ -218,6 +225,50 @@ fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k,
     }
     *out = op;
     return FB_OK;
+}
+
+extern "C" {
+
+fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k, int kind, int precision,
+                             double d0, int pmin, void* stream, fb_op** out) {
+    return fb_operator_create_impl(mesh, tree, k, kind, precision, d0, pmin, as_stream(stream), out);
+}
+
+fb_status fb_mesh_set_admittance_plus(fb_mesh* m, const double* beta, int memspace, void* stream) {
+    if (!m || !beta) return fb_fail(FB_ERR_ARG, "NULL argument");
+    cudaStream_t s = as_stream(stream);
+    if (!m->beta_p) FB_CHECK(dalloc(&m->beta_p, (size_t)m->n));
+    size_t bytes = sizeof(cd) * m->n;
+    if (memspace == FB_MEM_DEVICE) {
+        FB_CUDA(cudaMemcpyAsync(m->beta_p, beta, bytes, cudaMemcpyDeviceToDevice, s));
+    } else if (memspace == FB_MEM_HOST) {
+        FB_CUDA(cudaMemcpyAsync(m->beta_p, beta, bytes, cudaMemcpyHostToDevice, s));
+        FB_CUDA(cudaStreamSynchronize(s));
+    } else {
+        return fb_fail(FB_ERR_ARG, "bad memspace");
+    }
+    return FB_OK;
+}
+
+fb_status fb_ibem_gammas_monopole(fb_op* op, const double* src, double* gamma_p, double* gamma_m, void* stream) {
+    if (!op || !src || !gamma_p || !gamma_m) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (op->kind != FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "not an indirect-system operator");
+    return fb_ibem_gammas_impl(op, src, (cd*)gamma_p, (cd*)gamma_m, as_stream(stream));
+}
+
+fb_status fb_ibem_rhs(fb_op* op, const double* gamma_p, const double* gamma_m, double* b, void* stream) {
+    if (!op || !gamma_p || !gamma_m || !b) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (op->kind != FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "not an indirect-system operator");
+    return fb_ibem_rhs_impl(op, (const cd*)gamma_p, (const cd*)gamma_m, (cd*)b, as_stream(stream));
+}
+
+fb_status fb_ibem_field(fb_op* op, const double* x, const double* gamma_p, const double* gamma_m, const double* rcv,
+                        int64_t nr, double* out, void* stream) {
+    if (!op || !x || !gamma_p || !gamma_m || !rcv || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (op->kind != FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "not an indirect-system operator");
+    if (nr < 0) return fb_fail(FB_ERR_ARG, "nr < 0");
+    return fb_ibem_field_impl(op, (const cd*)x, (const cd*)gamma_p, (const cd*)gamma_m, rcv, nr, (cd*)out,
+                              as_stream(stream));
 }
 
 fb_status fb_operator_apply(fb_op* op, const double* x, double* y, int memspace, void* stream) {
@@ -272,6 +323,7 @@ fb_status fb_measure_alu_peaks(double* fp32_tflops, double* fp64_tflops, void* s
 
 fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* stream, double* phase_ms) {
     if (!op || !x || !y || !phase_ms) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (op->kind == FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "phase timing is per FMM operator");
     cudaStream_t s = as_stream(stream);
     for (int i = 0; i < FB_NPHASE; ++i) phase_ms[i] = 0.0;
     if (op->prec == FB_PREC_FP64_DENSE) {
@@ -311,11 +363,16 @@ fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* s
 fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y, void* stream) {
     if (!op || !x || !y) return fb_fail(FB_ERR_ARG, "NULL argument");
     if (x == y) return fb_fail(FB_ERR_ARG, "x and y must not overlap");
+    if (op->kind == FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "the indirect system keeps its own work space");
     return fb_fmm_apply_noalloc(op, (const cd*)x, (cd*)y, as_stream(stream));
 }
 
 fb_status fb_operator_set_translation(fb_op* op, int method) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
+    if (op->kind == FB_OP_IBEM) {
+        for (int q = 0; q < 4; ++q) FB_CHECK(fb_operator_set_translation(op->sub[q], method));
+        return FB_OK;
+    }
     if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "dense operators have no translations");
     if (method < FB_TRANS_AUTO || method > FB_TRANS_TENSOR) return fb_fail(FB_ERR_ARG, "unknown translation method");
     if (method == FB_TRANS_TENSOR && op->prec != FB_PREC_MIXED_FMM)
@@ -347,6 +404,10 @@ fb_status fb_operator_set_translation(fb_op* op, int method) {
 
 fb_status fb_operator_use_graphs(fb_op* op, int enable) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
+    if (op->kind == FB_OP_IBEM) {
+        for (int q = 0; q < 4; ++q) FB_CHECK(fb_operator_use_graphs(op->sub[q], enable));
+        return FB_OK;
+    }
     op->use_graphs = enable ? 1 : 0;
     if (!enable) fb_graph_free(op->graphs);
     return FB_OK;
@@ -367,12 +428,21 @@ fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times,
         for (int i = 0; i < 4 * (FB_MAXLEV + 1); ++i) times[i] = -1.0;
     if (choice)
         for (int i = 0; i <= FB_MAXLEV; ++i) choice[i] = 0;
+    if (op->kind == FB_OP_IBEM) {   // each constituent operator; times/choice of the first
+        for (int q = 0; q < 4; ++q)
+            FB_CHECK(fb_operator_autotune(op->sub[q], nrhs, stream, q == 0 ? times : nullptr, q == 0 ? choice : nullptr));
+        return FB_OK;
+    }
     fb_graph_free(op->graphs);
     return fb_autotune_impl(op, nrhs, as_stream(stream), times, choice);
 }
 
 fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream) {
     if (!op || !choice) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (op->kind == FB_OP_IBEM) {
+        for (int q = 0; q < 4; ++q) FB_CHECK(fb_operator_set_forms(op->sub[q], choice, stream));
+        return FB_OK;
+    }
     fb_graph_free(op->graphs);
     fb_status st = fb_set_forms_impl(op, choice, as_stream(stream));
     if (st == FB_OK) {
@@ -384,6 +454,11 @@ fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream) {
 
 fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
+    if (op->kind == FB_OP_IBEM) {
+        FB_CHECK(fb_operator_info(op->sub[0], nullptr, leaf_level, p));
+        if (n) *n = op->n;
+        return FB_OK;
+    }
     if (n) *n = op->n;
     if (leaf_level) *leaf_level = op->L;
     if (p) for (int l = 0; l <= op->L; ++l) p[l] = op->p[l];
@@ -392,6 +467,7 @@ fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p)
 
 fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t index, double* out, int64_t* count) {
     if (!op || !count) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (op->kind == FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "export the constituent operators instead");
     const cd* src = nullptr;
     int64_t cnt = 0;
     if (which == 7) {
@@ -456,6 +532,7 @@ fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t inde
 
 void fb_operator_destroy(fb_op* op) {
     if (!op) return;
+    fb_ibem_free(op);
     dfree(op->dense);
     fb_fmm_destroy(op);
     dfree(op->io_x);
@@ -478,6 +555,8 @@ fb_status fb_gamma_monopole(const fb_mesh* m, double k, const double* src, doubl
 
 fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out) {
     if (!op || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (op->kind == FB_OP_IBEM && kind != FB_PC_NONE)
+        return fb_fail(FB_ERR_ARG, "block Jacobi needs a single FMM operator (use the inner-outer preconditioner)");
     return fb_precond_create_impl(op, kind, as_stream(stream), out);
 }
 
@@ -518,6 +597,7 @@ fb_status fb_precond_create_learned(fb_op* op, const fb_precond* base, uint64_t 
                                     fb_precond** out) {
     if (!op || !base || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
     *out = nullptr;
+    if (op->kind == FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "the learned network serves single-unknown systems");
     if ((base->kind != FB_PC_BLOCK_JACOBI && base->kind != FB_PC_INNER) || base->op != op)
         return fb_fail(FB_ERR_ARG, "the base must be a block-Jacobi or inner-outer preconditioner of the same "
                                    "operator");

@@ -130,6 +130,7 @@ struct fb_mesh {
     int64_t n = 0;
     double* buf = nullptr;          // 16 n doubles + 9 n Gauss coordinates
     cd* beta = nullptr;
+    cd* beta_p = nullptr;           // admittance of the + side (indirect system; NULL = same as beta)
     double rc = 0, max_edge = 0;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};   // bounding box of the vertices
     Geom g{};
@@ -279,6 +280,10 @@ struct fb_op {
     double d0 = 0;           // order rule parameters (FMM)
     int pmin = 0;
     int64_t n = 0;
+    // indirect system (FB_OP_IBEM): constituent M, L, M', L' and work space
+    fb_op* sub[4] = {nullptr, nullptr, nullptr, nullptr};
+    cd* ib_work = nullptr;                   // 6 N
+    cd *ib_beta_p = nullptr, *ib_beta_m = nullptr;
     // dense
     cd* dense = nullptr;
     // FMM
@@ -422,5 +427,9 @@ fb_status fb_tc_check(const fb_op* op);
 void fb_tc_free(void*& plan);
 void fb_fmm_destroy(fb_op* op);
 fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs = 1);
+fb_status fb_ibem_create(fb_op* op, cudaStream_t s);
+void fb_ibem_free(fb_op* op);
+fb_status fb_ibem_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs);
+extern "C" void fb_operator_destroy(fb_op* op);
 fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, int nrhs = 1);
 int fb_order_rule(double k, double delta, double d0, int pmin);

@@ -275,5 +275,6 @@ void fb_mesh_free(fb_mesh* m) {
     if (!m) return;
     dfree(m->buf);
     dfree(m->beta);
+    dfree(m->beta_p);
     delete m;
 }
