@@ -11,11 +11,20 @@ iterations and time to a true relative residual (FP64 FMM) of 1e-4:
 block Jacobi alone, the learned network over block Jacobi, the inner-outer
 preconditioner of Sec. 4, and the plain FP64 path.
 
+With --cross-validate it instead solves the same room twice for one
+source: the 2 cm baffle box in the direct formulation (Eq. dbem4) and a
+zero-thickness baffle sheet in the indirect one (Eq. ibem5, two unknowns per
+element, walls and door with the same admittance on both sides), each with
+the inner-outer preconditioner and an FP64 true residual, and compares the
+fields at 64 receivers (Sec. 4 compares its direct and indirect solutions
+the same way).
+
 Orchestration only: every solve, matvec, network pass and Adam step runs in
 the library.
 
     python -m paper_2103_16073_gb300.baffle_study [--train-freqs 1600,1800,2200,2400]
         [--train-sources 2] [--eval-sources 3] [--steps 200] [--out result.json]
+    python -m paper_2103_16073_gb300.baffle_study --cross-validate [--out result.json]
 """
 from __future__ import annotations
 
@@ -198,6 +207,77 @@ def run(train_freqs, ntrain, neval, steps, every=10, lr=1e-3, batch=8, log=print
     return out
 
 
+def cross_validate(log=print):
+    thick = W.cfg_baffle(nsrc=1, nrec=64)
+    thin = W.baffle_workload(2000.0, 10.0, nsrc=1, nrec=64, thickness=0.0)
+    src = thick.sources[0]
+    rcv = torch.tensor(thick.receivers, device="cuda")
+    k = thick.k
+    out = {"freq_hz": thick.freq_hz, "source": src.tolist(), "receivers": int(rcv.shape[0])}
+    fields = {}
+    for name, wl in (("direct_thick_baffle", thick), ("indirect_thin_baffle", thin)):
+        t0 = _now()
+        mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+        fb.fb_mesh_set_admittance(mesh, wl.beta)
+        tree = fb.fb_tree_build(mesh, 64)
+        indirect = name.startswith("indirect")
+        kind = fb.FB_OP_IBEM if indirect else fb.FB_OP_A
+        pmin = 14 if indirect else PMIN   # M' and L' need 14 for 1e-5 (the single operators' rule)
+        A32 = fb.fb_operator_create(mesh, tree, k, kind, fb.FB_PREC_MIXED_FMM, D0, pmin)
+        fb.fb_operator_autotune(A32, 1)
+        fb.fb_operator_use_graphs(A32, True)
+        A64 = fb.fb_operator_create(mesh, tree, k, kind, fb.FB_PREC_FP64_FMM, D0, pmin)
+        fb.fb_operator_use_graphs(A64, True)
+        Alow = fb.fb_operator_create(mesh, tree, k, kind, fb.FB_PREC_MIXED_FMM, INNER[0], INNER[1])
+        fb.fb_operator_autotune(Alow, 1)
+        fb.fb_operator_use_graphs(Alow, True)
+        pclow = None if indirect else fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
+        inner = fb.fb_precond_create_inner(A32, Alow, pclow, INNER[2])
+        L64 = None
+        if indirect:
+            gp, gm = fb.fb_ibem_gammas_monopole(A64, src)
+            b = fb.fb_ibem_rhs(A64, gp, gm)
+        else:
+            L64 = fb.fb_operator_create(mesh, tree, k, fb.FB_OP_L, fb.FB_PREC_FP64_FMM, D0, PMIN)
+            g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
+            fb.fb_gamma_monopole(mesh, k, src, g)
+            b = torch.empty_like(g)
+            fb.fb_operator_apply(L64, g, b)
+        t_setup = _now() - t0
+        _solve(A32, b, inner, A64)   # warm-up (graph capture)
+        x = torch.zeros_like(b)
+        t1 = _now()
+        info = fb.fb_fgmres_solve(A32, b, x, pc=inner, tol=TOL, restart=RESTART, maxit=3000, max_refine=4,
+                                  true_op=A64)
+        info["ms"] = (_now() - t1) * 1e3
+        if indirect:
+            f = fb.fb_ibem_field(A64, x, gp, gm, rcv)
+            d = rcv - torch.tensor(src, device="cuda")
+            R = torch.linalg.norm(d, dim=1)
+            f = f + torch.exp(1j * k * R) / (4 * np.pi * R)   # plus the incident field
+        else:
+            f = torch.empty(rcv.shape[0], dtype=torch.complex128, device="cuda")
+            fb.fb_eval_field(mesh, k, x, g, rcv, f, src=src)
+        fields[name] = f.cpu().numpy()
+        out[name] = {"n_elements": wl.n, "unknowns": int(b.numel()), "setup_s": round(t_setup, 1),
+                     "iterations": info["iters"], "solve_ms": round(info["ms"], 1),
+                     "true_relres": float(f"{info['true_relres']:.3e}")}
+        log(f"{name}: {out[name]}")
+        fb.fb_precond_destroy(inner)
+        if pclow is not None:
+            fb.fb_precond_destroy(pclow)
+        for h in (A32, A64, Alow, L64):
+            if h is not None:
+                fb.fb_operator_destroy(h)
+        fb.fb_tree_destroy(tree)
+        fb.fb_mesh_destroy(mesh)
+    a, c = fields["direct_thick_baffle"], fields["indirect_thin_baffle"]
+    out["receiver_rel_difference"] = float(np.linalg.norm(a - c) / np.linalg.norm(a))
+    out["receiver_rel_difference_median"] = float(np.median(np.abs(a - c) / np.abs(a)))
+    log(f"receiver difference {out['receiver_rel_difference']:.3e}")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--train-freqs", default="1600,1800,2200,2400")
@@ -205,9 +285,18 @@ def main():
     ap.add_argument("--eval-sources", type=int, default=3)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--cross-validate", action="store_true")
     ap.add_argument("--out", default="")
     a = ap.parse_args()
     freqs = [float(v) for v in a.train_freqs.split(",")]
+    if a.cross_validate:
+        res = cross_validate(log=lambda s: print(s, flush=True))
+        txt = json.dumps(res)
+        print(txt)
+        if a.out:
+            with open(a.out, "w") as f:
+                f.write(txt + "\n")
+        return
     res = run(freqs, a.train_sources, a.eval_sources, a.steps, lr=a.lr, log=lambda s: print(s, flush=True))
     txt = json.dumps(res)
     print(txt)

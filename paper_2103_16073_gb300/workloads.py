@@ -167,12 +167,14 @@ WALL_BAFFLE = 7
 def baffle_room_mesh(h, thickness=0.02):
     """The door-and-baffle room meshed with legs <= h.
 
-    The direct formulation needs a closed boundary, so the baffle is a closed
-    box of the given thickness centred on its plane (x in 2.5 -/+ t/2).  The
-    normal of every triangle points out of the air: out of the room on the
-    walls, into the baffle's box on its six faces.  The wall y = 0 has grid
-    lines on the door's edges; its door rectangles get wall id 6, the
-    baffle's faces id 7, the walls ids 0..5 as in shoebox_mesh.
+    thickness > 0 (the direct formulation, which needs a closed boundary):
+    the baffle is a closed box of that thickness centred on its plane
+    (x in 2.5 -/+ t/2), every normal pointing out of the air: out of the room
+    on the walls, into the baffle's box on its six faces.
+    thickness = 0 (the indirect formulation): the baffle is one sheet in the
+    plane x = 2.5 with normal +x (its + side faces +x).
+    The wall y = 0 has grid lines on the door's edges; its door rectangles
+    get wall id 6, the baffle id 7, the walls ids 0..5 as in shoebox_mesh.
     Returns (verts f64, tris i32, wall i32)."""
     lx, ly, lz = BAFFLE_ROOM
     X, Y, Z = np.eye(3)
@@ -207,6 +209,8 @@ def baffle_room_mesh(h, thickness=0.02):
         ([x0, y0, z0], X * thickness, Y * wy),   # z = z0, normal +z
         ([x0, y0, z1], Y * wy, X * thickness),   # z = z1, normal -z
     ]
+    if thickness == 0:
+        faces = faces[:1]
     for o, ea, eb in faces:
         add(_rect_wall(o, ea, eb, h, h), WALL_BAFFLE)
     verts, tris, _ = _concat(parts)
