@@ -83,6 +83,12 @@ typedef int fb_status;
                       M' operators of the given precision on the same tree; block
                       Jacobi and the learned network do not apply to it (the
                       inner-outer preconditioner does). */
+#define FB_OP_DBEM5 6 /* direct-BEM system of Eq. dbem5 for the unknown
+                      q = d psi_sc/dn (N x N): 1/2 q + (1/zeta) M[zeta q]
+                      + (k/(i zeta)) L[q], i.e. 1/2 q + beta M[q/beta]
+                      - i k beta L[q]; needs beta != 0 on every element
+                      (FB_ERR_ARG otherwise).  Composed of M and L; right-hand
+                      side and psi_sc by fb_dbem5_rhs / fb_dbem5_psi. */
 
 /* How an operator is applied. */
 #define FB_PREC_FP64_DENSE 0 /* stored dense N x N complex128 matrix        */
@@ -364,6 +370,13 @@ FB_API fb_status fb_ibem_gammas_monopole(fb_op* op, const double* src, double* g
 FB_API fb_status fb_ibem_rhs(fb_op* op, const double* gamma_p, const double* gamma_m, double* b, void* stream);
 FB_API fb_status fb_ibem_field(fb_op* op, const double* x, const double* gamma_p, const double* gamma_m,
                                const double* rcv, int64_t nr, double* out, void* stream);
+
+/* Eq. dbem5 helpers (FB_OP_DBEM5), device pointers, N complex each:
+ * fb_dbem5_rhs: b = 1/2 gamma + (1/zeta) M[zeta gamma];
+ * fb_dbem5_psi: psi_sc = (q - gamma) / (i k beta) (the boundary condition).
+ * Errors: FB_ERR_ARG if op is not FB_OP_DBEM5. */
+FB_API fb_status fb_dbem5_rhs(fb_op* op, const double* gamma, double* b, void* stream);
+FB_API fb_status fb_dbem5_psi(fb_op* op, const double* q, const double* gamma, double* psi, void* stream);
 
 /* Training-data helper for learned preconditioners: the first k+1 Arnoldi
  * vectors of the right-preconditioned Krylov space of A from start vector b

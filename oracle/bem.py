@@ -169,6 +169,28 @@ def system_matrix(L, M, k, beta):
     return A
 
 
+def system_matrix_dbem5(L, M, k, beta):
+    """Eq. (dbem5) for the unknown q = d psi_sc/dn:
+    1/2 q + (1/zeta) M[zeta q] + (k/(i zeta)) L[q] with zeta = 1/beta, i.e.
+    1/2 I + diag(beta) M diag(1/beta) - i k diag(beta) L (beta != 0)."""
+    b = np.asarray(beta, dtype=np.complex128)
+    A = b[:, None] * M / b[None, :] - 1j * k * b[:, None] * L
+    A[np.diag_indices_from(A)] += 0.5
+    return A
+
+
+def rhs_dbem5(M, beta, gamma):
+    """Right-hand side of Eq. (dbem5): 1/2 gamma + (1/zeta) M[zeta gamma]."""
+    b = np.asarray(beta, dtype=np.complex128)
+    return 0.5 * gamma + b * (M @ (gamma / b))
+
+
+def psi_from_dnpsi(q, gamma, k, beta):
+    """psi_sc from q = d psi_sc/dn by the boundary condition of Eq. (sp7):
+    q - i k beta psi_sc = gamma."""
+    return (q - gamma) / (1j * k * np.asarray(beta))
+
+
 def system_rows(mesh, k, beta, rows):
     """Rows of A (Eq. dbem4) for element indices ``rows`` (for sampled checks)."""
     rows = np.asarray(rows)

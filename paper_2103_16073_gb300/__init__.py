@@ -37,7 +37,7 @@ __all__ = [
 ]
 
 FB_OK = 0
-FB_OP_L, FB_OP_M, FB_OP_LP, FB_OP_A, FB_OP_MP, FB_OP_IBEM = 0, 1, 2, 3, 4, 5
+FB_OP_L, FB_OP_M, FB_OP_LP, FB_OP_A, FB_OP_MP, FB_OP_IBEM, FB_OP_DBEM5 = 0, 1, 2, 3, 4, 5, 6
 FB_PREC_FP64_DENSE, FB_PREC_FP64_FMM, FB_PREC_MIXED_FMM = 0, 1, 2
 FB_MEM_HOST, FB_MEM_DEVICE = 0, 1
 FB_PC_NONE, FB_PC_BLOCK_JACOBI = 0, 1
@@ -655,3 +655,26 @@ def fb_ibem_field(op, x, gamma_p, gamma_m, rcv, stream=None):
     _check(lib.fb_ibem_field(op, _cuda_ptr(x, "x"), _cuda_ptr(gamma_p, "gamma_p"), _cuda_ptr(gamma_m, "gamma_m"),
                              _cuda_ptr(rcv, "rcv"), int(rcv.shape[0]), C.c_void_p(out.data_ptr()), _stream(stream)))
     return out
+
+
+lib.fb_dbem5_rhs.restype = C.c_int
+lib.fb_dbem5_rhs.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+lib.fb_dbem5_psi.restype = C.c_int
+lib.fb_dbem5_psi.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+
+
+def fb_dbem5_rhs(op, gamma, stream=None):
+    """Right-hand side of Eq. (dbem5) (CUDA complex128, N) from gamma."""
+    import torch
+    b = torch.empty_like(gamma)
+    _check(lib.fb_dbem5_rhs(op, _cuda_ptr(gamma, "gamma"), C.c_void_p(b.data_ptr()), _stream(stream)))
+    return b
+
+
+def fb_dbem5_psi(op, q, gamma, stream=None):
+    """psi_sc from the Eq. (dbem5) solution q = d psi_sc/dn."""
+    import torch
+    psi = torch.empty_like(q)
+    _check(lib.fb_dbem5_psi(op, _cuda_ptr(q, "q"), _cuda_ptr(gamma, "gamma"), C.c_void_p(psi.data_ptr()),
+                            _stream(stream)))
+    return psi

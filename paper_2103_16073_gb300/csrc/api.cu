@@ -28,6 +28,8 @@ fb_status fb_krylov_basis_impl(fb_op*, const fb_precond*, const cd*, int, cd*, c
 fb_status fb_ibem_gammas_impl(fb_op*, const double*, cd*, cd*, cudaStream_t);
 fb_status fb_ibem_rhs_impl(fb_op*, const cd*, const cd*, cd*, cudaStream_t);
 fb_status fb_ibem_field_impl(fb_op*, const cd*, const cd*, const cd*, const double*, int64_t, cd*, cudaStream_t);
+fb_status fb_dbem5_rhs_impl(fb_op*, const cd*, cd*, cudaStream_t);
+fb_status fb_dbem5_psi_impl(fb_op*, const cd*, const cd*, cd*, cudaStream_t);
 void fb_precond_free(fb_precond*);
 fb_status fb_alu_peaks_impl(double*, double*, cudaStream_t);
 
@@ -99,6 +101,7 @@ long long fb_launch_count() { return g_launches.load(); }
 
 fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs) {
     if (op->kind == FB_OP_IBEM) return fb_ibem_apply(op, x, y, s, nrhs);
+    if (op->kind == FB_OP_DBEM5) return fb_dbem5_apply(op, x, y, s, nrhs);
     if (op->prec == FB_PREC_FP64_DENSE) {
         for (int r = 0; r < nrhs; ++r) FB_CHECK(fb_dense_apply(op, x + r * op->n, y + r * op->n, s));
         return FB_OK;
@@ -194,7 +197,7 @@ fb_status fb_operator_create_impl(const fb_mesh* mesh, const fb_tree* tree, doub
     if (!mesh || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
     *out = nullptr;
     if (!(k > 0.0)) return fb_fail(FB_ERR_ARG, "k must be > 0");
-    if (kind < FB_OP_L || kind > FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "unknown operator kind");
+    if (kind < FB_OP_L || kind > FB_OP_DBEM5) return fb_fail(FB_ERR_ARG, "unknown operator kind");
     if (precision < FB_PREC_FP64_DENSE || precision > FB_PREC_MIXED_FMM)
         return fb_fail(FB_ERR_ARG, "unknown precision");
     if (precision != FB_PREC_FP64_DENSE) {
@@ -213,6 +216,7 @@ fb_status fb_operator_create_impl(const fb_mesh* mesh, const fb_tree* tree, doub
     op->pmin = pmin;
     op->n = mesh->n;
     fb_status st = kind == FB_OP_IBEM                  ? fb_ibem_create(op, s)
+                   : kind == FB_OP_DBEM5             ? fb_dbem5_create(op, s)
                    : precision == FB_PREC_FP64_DENSE ? fb_dense_create(op, s)
                                                      : fb_fmm_create(op, d0, pmin, s);
     if (st == FB_OK) {
@@ -271,6 +275,18 @@ fb_status fb_ibem_field(fb_op* op, const double* x, const double* gamma_p, const
                               as_stream(stream));
 }
 
+fb_status fb_dbem5_rhs(fb_op* op, const double* gamma, double* b, void* stream) {
+    if (!op || !gamma || !b) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (op->kind != FB_OP_DBEM5) return fb_fail(FB_ERR_ARG, "not an FB_OP_DBEM5 operator");
+    return fb_dbem5_rhs_impl(op, (const cd*)gamma, (cd*)b, as_stream(stream));
+}
+
+fb_status fb_dbem5_psi(fb_op* op, const double* q, const double* gamma, double* psi, void* stream) {
+    if (!op || !q || !gamma || !psi) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (op->kind != FB_OP_DBEM5) return fb_fail(FB_ERR_ARG, "not an FB_OP_DBEM5 operator");
+    return fb_dbem5_psi_impl(op, (const cd*)q, (const cd*)gamma, (cd*)psi, as_stream(stream));
+}
+
 fb_status fb_operator_apply(fb_op* op, const double* x, double* y, int memspace, void* stream) {
     if (!op || !x || !y) return fb_fail(FB_ERR_ARG, "NULL argument");
     if (x == y) return fb_fail(FB_ERR_ARG, "x and y must not overlap");
@@ -323,7 +339,7 @@ fb_status fb_measure_alu_peaks(double* fp32_tflops, double* fp64_tflops, void* s
 
 fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* stream, double* phase_ms) {
     if (!op || !x || !y || !phase_ms) return fb_fail(FB_ERR_ARG, "NULL argument");
-    if (op->kind == FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "phase timing is per FMM operator");
+    if (fb_is_composite(op)) return fb_fail(FB_ERR_ARG, "phase timing is per FMM operator");
     cudaStream_t s = as_stream(stream);
     for (int i = 0; i < FB_NPHASE; ++i) phase_ms[i] = 0.0;
     if (op->prec == FB_PREC_FP64_DENSE) {
@@ -363,14 +379,14 @@ fb_status fb_operator_apply_timed(fb_op* op, const double* x, double* y, void* s
 fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y, void* stream) {
     if (!op || !x || !y) return fb_fail(FB_ERR_ARG, "NULL argument");
     if (x == y) return fb_fail(FB_ERR_ARG, "x and y must not overlap");
-    if (op->kind == FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "the indirect system keeps its own work space");
+    if (fb_is_composite(op)) return fb_fail(FB_ERR_ARG, "composite systems keep their own work space");
     return fb_fmm_apply_noalloc(op, (const cd*)x, (cd*)y, as_stream(stream));
 }
 
 fb_status fb_operator_set_translation(fb_op* op, int method) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
-    if (op->kind == FB_OP_IBEM) {
-        for (int q = 0; q < 4; ++q) FB_CHECK(fb_operator_set_translation(op->sub[q], method));
+    if (fb_is_composite(op)) {
+        for (int q = 0; q < 4 && op->sub[q]; ++q) FB_CHECK(fb_operator_set_translation(op->sub[q], method));
         return FB_OK;
     }
     if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "dense operators have no translations");
@@ -404,8 +420,8 @@ fb_status fb_operator_set_translation(fb_op* op, int method) {
 
 fb_status fb_operator_use_graphs(fb_op* op, int enable) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
-    if (op->kind == FB_OP_IBEM) {
-        for (int q = 0; q < 4; ++q) FB_CHECK(fb_operator_use_graphs(op->sub[q], enable));
+    if (fb_is_composite(op)) {
+        for (int q = 0; q < 4 && op->sub[q]; ++q) FB_CHECK(fb_operator_use_graphs(op->sub[q], enable));
         return FB_OK;
     }
     op->use_graphs = enable ? 1 : 0;
@@ -428,8 +444,8 @@ fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times,
         for (int i = 0; i < 4 * (FB_MAXLEV + 1); ++i) times[i] = -1.0;
     if (choice)
         for (int i = 0; i <= FB_MAXLEV; ++i) choice[i] = 0;
-    if (op->kind == FB_OP_IBEM) {   // each constituent operator; times/choice of the first
-        for (int q = 0; q < 4; ++q)
+    if (fb_is_composite(op)) {   // each constituent operator; times/choice of the first
+        for (int q = 0; q < 4 && op->sub[q]; ++q)
             FB_CHECK(fb_operator_autotune(op->sub[q], nrhs, stream, q == 0 ? times : nullptr, q == 0 ? choice : nullptr));
         return FB_OK;
     }
@@ -439,8 +455,8 @@ fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times,
 
 fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream) {
     if (!op || !choice) return fb_fail(FB_ERR_ARG, "NULL argument");
-    if (op->kind == FB_OP_IBEM) {
-        for (int q = 0; q < 4; ++q) FB_CHECK(fb_operator_set_forms(op->sub[q], choice, stream));
+    if (fb_is_composite(op)) {
+        for (int q = 0; q < 4 && op->sub[q]; ++q) FB_CHECK(fb_operator_set_forms(op->sub[q], choice, stream));
         return FB_OK;
     }
     fb_graph_free(op->graphs);
@@ -454,7 +470,7 @@ fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream) {
 
 fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
-    if (op->kind == FB_OP_IBEM) {
+    if (fb_is_composite(op)) {
         FB_CHECK(fb_operator_info(op->sub[0], nullptr, leaf_level, p));
         if (n) *n = op->n;
         return FB_OK;
@@ -467,7 +483,7 @@ fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p)
 
 fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t index, double* out, int64_t* count) {
     if (!op || !count) return fb_fail(FB_ERR_ARG, "NULL argument");
-    if (op->kind == FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "export the constituent operators instead");
+    if (fb_is_composite(op)) return fb_fail(FB_ERR_ARG, "export the constituent operators instead");
     const cd* src = nullptr;
     int64_t cnt = 0;
     if (which == 7) {
@@ -555,7 +571,7 @@ fb_status fb_gamma_monopole(const fb_mesh* m, double k, const double* src, doubl
 
 fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out) {
     if (!op || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
-    if (op->kind == FB_OP_IBEM && kind != FB_PC_NONE)
+    if (fb_is_composite(op) && kind != FB_PC_NONE)
         return fb_fail(FB_ERR_ARG, "block Jacobi needs a single FMM operator (use the inner-outer preconditioner)");
     return fb_precond_create_impl(op, kind, as_stream(stream), out);
 }
@@ -597,7 +613,7 @@ fb_status fb_precond_create_learned(fb_op* op, const fb_precond* base, uint64_t 
                                     fb_precond** out) {
     if (!op || !base || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
     *out = nullptr;
-    if (op->kind == FB_OP_IBEM) return fb_fail(FB_ERR_ARG, "the learned network serves single-unknown systems");
+    if (fb_is_composite(op)) return fb_fail(FB_ERR_ARG, "the learned network serves single FMM operators");
     if ((base->kind != FB_PC_BLOCK_JACOBI && base->kind != FB_PC_INNER) || base->op != op)
         return fb_fail(FB_ERR_ARG, "the base must be a block-Jacobi or inner-outer preconditioner of the same "
                                    "operator");

@@ -430,6 +430,10 @@ fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs =
 fb_status fb_ibem_create(fb_op* op, cudaStream_t s);
 void fb_ibem_free(fb_op* op);
 fb_status fb_ibem_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs);
+fb_status fb_dbem5_create(fb_op* op, cudaStream_t s);
+fb_status fb_dbem5_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs);
+// operators composed of other operators (no near field or tree data of their own)
+inline bool fb_is_composite(const fb_op* op) { return op->kind == FB_OP_IBEM || op->kind == FB_OP_DBEM5; }
 extern "C" void fb_operator_destroy(fb_op* op);
 fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, int nrhs = 1);
 int fb_order_rule(double k, double delta, double d0, int pmin);

@@ -217,3 +217,42 @@ def test_baffle_room_exterior_source():
     assert e1 < 0.6 * e0 and b1 < 0.6 * b0 and e1 < 0.03
     ef, _ = err(0.5, flip=True)
     assert ef > 0.3
+
+
+def test_dbem5_formulation():
+    """Eq. (dbem5) (unknown d psi/dn): with constant zeta its matrix is the
+    matrix of Eq. (dbem4) and its right-hand side (1/2 I + M) gamma, as the
+    paper states; with zeta varying per wall the collocated system is
+    diag(beta) A4 diag(1/beta), so psi recovered from its solution through
+    the boundary condition equals the dbem4 solution to round-off; and in the
+    exterior-source test its solution approaches du/dn under refinement."""
+    room = (1.0, 0.8, 0.6)
+    k = 6.0
+    xs = np.array([0.31, 0.42, 0.27])
+    v, t, wall = W.shoebox_mesh(*room, 6, 6, 6)
+    mesh = bem.Mesh(v, t)
+    L, M, _ = bem.dense_operators(mesh, k)
+    beta0 = np.full(mesh.n, 0.2 + 0.05j)
+    A4 = bem.system_matrix(L, M, k, beta0)
+    assert np.max(np.abs(bem.system_matrix_dbem5(L, M, k, beta0) - A4)) < 1e-14
+    g = bem.gamma_monopole(mesh, k, beta0, xs)
+    b5 = bem.rhs_dbem5(M, beta0, g)
+    assert np.max(np.abs(b5 - (0.5 * g + M @ g))) < 1e-14
+    beta = np.array([1.0, 0.002, 0.5, 0.01, 0.3, 0.05 + 0.02j])[wall]
+    g = bem.gamma_monopole(mesh, k, beta, xs)
+    psi4 = np.linalg.solve(bem.system_matrix(L, M, k, beta), L @ g)
+    q = np.linalg.solve(bem.system_matrix_dbem5(L, M, k, beta), bem.rhs_dbem5(M, beta, g))
+    assert np.linalg.norm(bem.psi_from_dnpsi(q, g, k, beta) - psi4) < 1e-11 * np.linalg.norm(psi4)
+    xe = W.exterior_source(room)
+    errs = []
+    for nn in (4, 6):
+        v, t, wall = W.shoebox_mesh(*room, nn, nn, nn)
+        m = bem.Mesh(v, t)
+        Lm, Mm, _ = bem.dense_operators(m, k)
+        bm = np.array([1.0, 0.002, 0.5, 0.01, 0.3, 0.05 + 0.02j])[wall]
+        u, gu = bem.incident(m.el.centroid, xe, k)
+        dudn = np.sum(gu * m.el.normal, 1)
+        gam = bem.gamma_field(m, k, bm, u, dudn)
+        qq = np.linalg.solve(bem.system_matrix_dbem5(Lm, Mm, k, bm), bem.rhs_dbem5(Mm, bm, gam))
+        errs.append(np.linalg.norm(qq - dudn) / np.linalg.norm(dudn))
+    assert errs[1] < 0.8 * errs[0]
