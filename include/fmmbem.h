@@ -378,6 +378,27 @@ FB_API fb_status fb_ibem_field(fb_op* op, const double* x, const double* gamma_p
 FB_API fb_status fb_dbem5_rhs(fb_op* op, const double* gamma, double* b, void* stream);
 FB_API fb_status fb_dbem5_psi(fb_op* op, const double* q, const double* gamma, double* psi, void* stream);
 
+/* ------------------------------------------------------- broadband -- */
+
+/* Image-source field of a shoebox room (Sec. 4, Eq. an2; images of Allen
+ * and Berkley): out[m][r] = sum_j A_j e^{i k_m R_j}/(4 pi R_j) over the
+ * source and its images, A_j the product of the wall reflection
+ * coefficients met (R_walls: 6 complex, walls x=0, x=lx, y=0, y=ly, z=0,
+ * z=lz), images with |A_j| < a_th dropped (Sec. 4 uses 1e-7).  room, src:
+ * 3 doubles (host); k: nf wavenumbers (host); rcv: nr x 3 doubles and out:
+ * nf x nr complex (device).  Synchronous.  Errors: FB_ERR_ARG. */
+FB_API fb_status fb_image_field(const double* room, const double* src, const double* R_walls, double a_th,
+                                const double* k, int nf, const double* rcv, int64_t nr, double* out, void* stream);
+
+/* Time-domain response to the pulse of Eq. (an3), f(t) = delta(t - Dt) -
+ * delta(t + Dt), from frequency-domain solutions psi (nf x nr complex,
+ * device; unit monopole, time convention e^{-i omega t}) at frequencies
+ * freqs (nf Hz, host, spacing df):
+ *   out[n][r] = 2 df Re sum_m psi[m][r] 2 i sin(2 pi f_m Dt) e^{-i 2 pi f_m n dt},
+ * n = 0..nt-1 (device, nt x nr doubles).  Synchronous.  Errors: FB_ERR_ARG. */
+FB_API fb_status fb_pulse_synthesis(const double* psi, const double* freqs, int nf, int64_t nr, double df, double dt,
+                                    int nt, double pulse_dt, double* out, void* stream);
+
 /* Training-data helper for learned preconditioners: the first k+1 Arnoldi
  * vectors of the right-preconditioned Krylov space of A from start vector b
  * (the vectors a preconditioner receives in the first k iterations of

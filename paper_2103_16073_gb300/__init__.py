@@ -678,3 +678,37 @@ def fb_dbem5_psi(op, q, gamma, stream=None):
     _check(lib.fb_dbem5_psi(op, _cuda_ptr(q, "q"), _cuda_ptr(gamma, "gamma"), C.c_void_p(psi.data_ptr()),
                             _stream(stream)))
     return psi
+
+
+lib.fb_image_field.restype = C.c_int
+lib.fb_image_field.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_int, C.c_void_p,
+                               C.c_int64, C.c_void_p, C.c_void_p]
+lib.fb_pulse_synthesis.restype = C.c_int
+lib.fb_pulse_synthesis.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_double, C.c_int,
+                                   C.c_double, C.c_void_p, C.c_void_p]
+
+
+def fb_image_field(room, src, R_walls, k, rcv, a_th=1e-7, stream=None):
+    """Image-source field (Eq. an2) at receivers rcv (CUDA float64 [nr, 3])
+    for wavenumbers k; returns CUDA complex128 [nf, nr]."""
+    import torch
+    room = np.ascontiguousarray(room, dtype=np.float64)
+    src = np.ascontiguousarray(src, dtype=np.float64)
+    Rw = np.ascontiguousarray(np.broadcast_to(np.asarray(R_walls, dtype=np.complex128), (6,)))
+    kk = np.ascontiguousarray(np.atleast_1d(k), dtype=np.float64)
+    out = torch.empty((kk.size, rcv.shape[0]), dtype=torch.complex128, device="cuda")
+    _check(lib.fb_image_field(room.ctypes.data, src.ctypes.data, Rw.ctypes.data, float(a_th), kk.ctypes.data,
+                              int(kk.size), _cuda_ptr(rcv, "rcv"), int(rcv.shape[0]), C.c_void_p(out.data_ptr()),
+                              _stream(stream)))
+    return out
+
+
+def fb_pulse_synthesis(psi, freqs, df, dt, nt, pulse_dt, stream=None):
+    """Time response (CUDA float64 [nt, nr]) to the pulse of Eq. (an3) from
+    psi (CUDA complex128 [nf, nr]) at frequencies freqs (spacing df)."""
+    import torch
+    f = np.ascontiguousarray(freqs, dtype=np.float64)
+    out = torch.empty((int(nt), psi.shape[1]), dtype=torch.float64, device="cuda")
+    _check(lib.fb_pulse_synthesis(_cuda_ptr(psi, "psi"), f.ctypes.data, int(f.size), int(psi.shape[1]), float(df),
+                                  float(dt), int(nt), float(pulse_dt), C.c_void_p(out.data_ptr()), _stream(stream)))
+    return out

@@ -29,6 +29,10 @@ fb_status fb_ibem_gammas_impl(fb_op*, const double*, cd*, cd*, cudaStream_t);
 fb_status fb_ibem_rhs_impl(fb_op*, const cd*, const cd*, cd*, cudaStream_t);
 fb_status fb_ibem_field_impl(fb_op*, const cd*, const cd*, const cd*, const double*, int64_t, cd*, cudaStream_t);
 fb_status fb_dbem5_rhs_impl(fb_op*, const cd*, cd*, cudaStream_t);
+fb_status fb_image_field_impl(const double*, const double*, const cd*, double, const double*, int, const double*,
+                              int64_t, cd*, cudaStream_t);
+fb_status fb_pulse_synthesis_impl(const cd*, const double*, int, int64_t, double, double, int, double, double*,
+                                  cudaStream_t);
 fb_status fb_dbem5_psi_impl(fb_op*, const cd*, const cd*, cd*, cudaStream_t);
 void fb_precond_free(fb_precond*);
 fb_status fb_alu_peaks_impl(double*, double*, cudaStream_t);
@@ -273,6 +277,23 @@ fb_status fb_ibem_field(fb_op* op, const double* x, const double* gamma_p, const
     if (nr < 0) return fb_fail(FB_ERR_ARG, "nr < 0");
     return fb_ibem_field_impl(op, (const cd*)x, (const cd*)gamma_p, (const cd*)gamma_m, rcv, nr, (cd*)out,
                               as_stream(stream));
+}
+
+fb_status fb_image_field(const double* room, const double* src, const double* R_walls, double a_th,
+                         const double* k, int nf, const double* rcv, int64_t nr, double* out, void* stream) {
+    if (!room || !src || !R_walls || !k || !rcv || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (nf < 1 || nr < 0 || !(a_th > 0.0)) return fb_fail(FB_ERR_ARG, "need nf >= 1, nr >= 0, a_th > 0");
+    for (int d = 0; d < 3; ++d)
+        if (!(room[d] > 0.0) || !(src[d] > 0.0 && src[d] < room[d]))
+            return fb_fail(FB_ERR_ARG, "room sides must be > 0 and the source inside the room");
+    return fb_image_field_impl(room, src, (const cd*)R_walls, a_th, k, nf, rcv, nr, (cd*)out, as_stream(stream));
+}
+
+fb_status fb_pulse_synthesis(const double* psi, const double* freqs, int nf, int64_t nr, double df, double dt, int nt,
+                             double pulse_dt, double* out, void* stream) {
+    if (!psi || !freqs || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (nf < 1 || nr < 0 || nt < 1 || !(df > 0.0) || !(dt > 0.0)) return fb_fail(FB_ERR_ARG, "bad sizes or steps");
+    return fb_pulse_synthesis_impl((const cd*)psi, freqs, nf, nr, df, dt, nt, pulse_dt, out, as_stream(stream));
 }
 
 fb_status fb_dbem5_rhs(fb_op* op, const double* gamma, double* b, void* stream) {

@@ -282,6 +282,41 @@ def cfg_largest(nrec=1024):
     return wl
 
 
+IR_ROOM = (8.0, 6.0, 3.0)       # the rectangular room of Sec. 4's image-source comparison
+IR_SOURCE = (3.0, 2.0, 1.75)
+IR_ZETA = 9.0                   # R = (zeta - 1)/(zeta + 1) = 0.8
+
+
+def ir_receivers(spacing=0.25, margin=0.25, z=1.75, avoid=IR_SOURCE, avoid_dist=0.1):
+    """Receiver grid in the source's horizontal plane (Sec. 4 images the
+    plane z = 1.75 m), `margin` from the walls, none within `avoid_dist` of
+    the source."""
+    lx, ly, _ = IR_ROOM
+    xs = np.arange(margin, lx - margin + 1e-9, spacing)
+    ys = np.arange(margin, ly - margin + 1e-9, spacing)
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    P = np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], 1)
+    keep = np.linalg.norm(P - np.asarray(avoid), axis=1) >= avoid_dist
+    return P[keep]
+
+
+def ir_sweep(f_max=640.0, df=10.0, per_wavelength=8.0, h_max=0.5):
+    """Equispaced frequencies f_m = m df (m = 1..f_max/df) for the broadband
+    response of the 8 x 6 x 3 m room (uniform zeta = 9, source at
+    (3, 2, 1.75) m), each meshed with legs min(lambda/per_wavelength, h_max)."""
+    out = []
+    rec = ir_receivers()
+    for m in range(1, int(round(f_max / df)) + 1):
+        f = m * df
+        h = min(SOUND_SPEED / f / per_wavelength, h_max)
+        counts = shoebox_counts_for_h(*IR_ROOM, h)
+        verts, tris, wall = shoebox_mesh(*IR_ROOM, *counts)
+        beta = np.full(tris.shape[0], 1.0 / IR_ZETA, dtype=np.complex128)
+        out.append(Workload(f"ir-room-8x6x3-{f:.0f}Hz-N{tris.shape[0]}", verts, tris, wall, f, wavenumber(f), beta,
+                            np.asarray([IR_SOURCE], dtype=np.float64), rec, room=IR_ROOM))
+    return out
+
+
 def seeded_rng(config_index: int) -> np.random.Generator:
     """numpy PCG64 seeded with 2103_16073 + config index."""
     return np.random.Generator(np.random.PCG64(2103_16073 + int(config_index)))
