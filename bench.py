@@ -44,7 +44,7 @@ sys.path.insert(0, ROOT)
 METRIC = "FGMRES time-to-solve @1e-4 & matvecs/s: mixed+learned vs plain FP64, 1 GB300"
 TOL = 1e-4
 RESTART = 40
-INNER_D0, INNER_PMIN, INNER_ITERS = 2.0, 4, 5   # inner-outer preconditioner (low-accuracy FMM)
+INNER_D0, INNER_PMIN, INNER_ITERS = 1.0, 4, 6   # inner-outer preconditioner (low-accuracy FMM)
 
 
 def peaks():
