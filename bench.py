@@ -515,8 +515,8 @@ def run_ours(args):
                                f"beta=0.2, FMM leaf<=64, d0=6 pmin=12, FGMRES(40)+{args.precond}({args.base}), tol 1e-4",
                    "n_elements": n, "frequency_hz": wl.freq_hz, "solver": "FGMRES restart 40",
                    "precond": (("learned octree network (BF16 tensor-core kernels) over " if args.precond == "learned"
-                                else "") + ("inner-outer: 5 GMRES steps on a low-accuracy mixed FMM (d0=2, "
-                                            "p_min=4) with block Jacobi" if args.base == "inner"
+                                else "") + (f"inner-outer: {INNER_ITERS} GMRES steps on a low-accuracy mixed FMM "
+                                            f"(d0={INNER_D0:g}, p_min={INNER_PMIN}) with block Jacobi" if args.base == "inner"
                                             else "block Jacobi (leaf self blocks)")),
                    "operator": "mixed FP32 FMM, FP64 Arnoldi",
                    "true_residual": "FP64 FMM", "l2": "working set > L2 (translation matrices alone > 129 MB)",
