@@ -153,7 +153,7 @@ def build_problem(fb, W, torch, rank, forms=""):
     for op in (A32, A64):
         fb.fb_operator_use_graphs(op, True)
     # the paper's inner-outer preconditioner: GMRES steps on a low-accuracy
-    # mixed FMM (d0 = 2, p_min = 4) with its own block Jacobi
+    # mixed FMM (INNER_D0, INNER_PMIN) with its own block Jacobi
     Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, INNER_D0, INNER_PMIN)
     if forms:
         fb.fb_operator_set_forms(Alow, [0] * 13)
