@@ -356,6 +356,7 @@ struct fb_precond {
     LearnedNet* net = nullptr;     // learned preconditioner (refines `base`)
     const fb_precond* base = nullptr;
     int use_graphs = 0;            // CUDA-graph replay of the apply (fb_precond_use_graphs)
+    int ibem = 0;                  // block Jacobi of the indirect system: 2 x 2 leaf blocks
     void* graphs = nullptr;
     // inner-outer preconditioner: `inner_its` GMRES steps on `inner_op`
     // (right-preconditioned by `base`), work buffers in `inner`

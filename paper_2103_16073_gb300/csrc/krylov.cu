@@ -489,12 +489,14 @@ fb_status fb_self_blocks(const fb_op* op, const int64_t* d_off, cd* out, cudaStr
     return FB_OK;
 }
 
+// In-place Gauss-Jordan inverse with partial pivoting of the block of leaf t
+// (order `scale` x its element count; scale 2 for the indirect system).
 __global__ void k_bj_invert(const int32_t* leaf_start, const int64_t* blk_off, cd* blocks, int* piv_scr,
-                            int* singular) {
+                            int* singular, int scale) {
     int t = blockIdx.x;
-    int n = leaf_start[t + 1] - leaf_start[t];
+    int n = scale * (leaf_start[t + 1] - leaf_start[t]);
     cd* a = blocks + blk_off[t];
-    int* piv = piv_scr + leaf_start[t];
+    int* piv = piv_scr + scale * leaf_start[t];
     extern __shared__ cd fcol[];
     __shared__ int s_p;
     __shared__ cd s_inv;
@@ -572,6 +574,139 @@ __global__ void k_bj_apply(const int32_t* leaf_start, const int32_t* perm, const
         }
         if (lane == 0) y[perm[r0 + r]] = mk<double>((double)acc.re, (double)acc.im);
     }
+}
+
+// Block Jacobi of the indirect system (FB_OP_IBEM, Eq. ibem5): per leaf the
+// 2n x 2n matrix coupling its n elements' two equations to their psi+ and
+// psi-, from the self-blocks of M, L, M', L' (tree order, row = target):
+//   [ I/2 - M + L a+      I/2 + M + L a-     ]   a = -i k beta of the
+//   [ -M' + a+/2 + L' a+   M' - a-/2 + L' a- ]   column (diagonal: row) element
+__global__ void k_ibem_bj_assemble(const int32_t* leaf_start, const int32_t* perm, const int64_t* off1,
+                                   const int64_t* off2, const cd* Mb, const cd* Lb, const cd* MPb, const cd* LPb,
+                                   const cd* bp, const cd* bm, double k, cd* out) {
+    int t = blockIdx.x;
+    int r0 = leaf_start[t], n = leaf_start[t + 1] - r0, w = 2 * n;
+    cd* B = out + off2[t];
+    const int64_t o = off1[t];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e / n, j = e % n;
+        int ei = perm[r0 + i], ej = perm[r0 + j];
+        cd apj = mk(k * bp[ej].im, -k * bp[ej].re), amj = mk(k * bm[ej].im, -k * bm[ej].re);
+        cd m = Mb[o + e], l = Lb[o + e], mp = MPb[o + e], lp = LPb[o + e];
+        cd h = mk(i == j ? 0.5 : 0.0, 0.0);
+        B[(int64_t)i * w + j] = h - m + l * apj;
+        B[(int64_t)i * w + n + j] = h + m + l * amj;
+        cd d21 = mk(0.0, 0.0), d22 = mk(0.0, 0.0);
+        if (i == j) {
+            d21 = mk(0.5 * k * bp[ei].im, -0.5 * k * bp[ei].re);    // a+/2
+            d22 = mk(-0.5 * k * bm[ei].im, 0.5 * k * bm[ei].re);    // -a-/2
+        }
+        B[(int64_t)(n + i) * w + j] = d21 - mp + lp * apj;
+        B[(int64_t)(n + i) * w + n + j] = d22 + mp + lp * amj;
+    }
+}
+
+// z = B^-1 r per leaf: rows 0..n-1 of r are the first equations of the
+// leaf's elements (r[e]), rows n..2n-1 the second (r[N + e]); columns map to
+// psi+ (z[e]) and psi- (z[N + e]).
+__global__ void k_ibem_bj_apply(const int32_t* leaf_start, const int32_t* perm, const int64_t* off2, const cd* inv,
+                                const cd* __restrict__ x, cd* __restrict__ y, int64_t N) {
+    int t = blockIdx.x;
+    int r0 = leaf_start[t], n = leaf_start[t + 1] - r0, w = 2 * n;
+    extern __shared__ unsigned char raw[];
+    cd* xs = (cd*)raw;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        int e = perm[r0 + i];
+        xs[i] = x[e];
+        xs[n + i] = x[N + e];
+    }
+    __syncthreads();
+    const cd* a = inv + off2[t];
+    int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = warp; r < w; r += nw) {
+        cd acc = mk(0.0, 0.0);
+        for (int c = lane; c < w; c += 32) cmac(acc, a[(int64_t)r * w + c], xs[c]);
+        for (int q = 16; q > 0; q >>= 1) {
+            acc.re += __shfl_xor_sync(0xffffffffu, acc.re, q);
+            acc.im += __shfl_xor_sync(0xffffffffu, acc.im, q);
+        }
+        if (lane == 0) y[r < n ? perm[r0 + r] : N + perm[r0 + r - n]] = acc;
+    }
+}
+
+void fb_precond_free(fb_precond* pc);
+
+static fb_status ibem_bj_create(fb_op* op, cudaStream_t s, fb_precond** out) {
+    const fb_tree* t = op->tree;
+    if (!t || op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "block Jacobi needs an FMM operator");
+    const int nleaf = t->nbox[t->L];
+    std::vector<int64_t> off1(nleaf + 1, 0), off2(nleaf + 1, 0);
+    int maxn = 0;
+    for (int b = 0; b < nleaf; ++b) {
+        int64_t nb = t->h_leaf_start[b + 1] - t->h_leaf_start[b];
+        maxn = std::max<int>(maxn, (int)nb);
+        off1[b + 1] = off1[b] + nb * nb;
+        off2[b + 1] = off2[b] + 4 * nb * nb;
+    }
+    fb_precond* pc = new fb_precond();
+    pc->op = op;
+    pc->kind = FB_PC_BLOCK_JACOBI;
+    pc->n = op->n;
+    pc->ibem = 1;
+    int64_t* d_off1 = nullptr;
+    cd* tmp[4] = {nullptr, nullptr, nullptr, nullptr};
+    const cd* self[4] = {nullptr, nullptr, nullptr, nullptr};
+    int* piv = nullptr;
+    int* sing = nullptr;
+    auto cleanup = [&]() {
+        dfree(d_off1);
+        for (int q = 0; q < 4; ++q) dfree(tmp[q]);
+        dfree(piv);
+        dfree(sing);
+    };
+    fb_status st = FB_OK;
+    if ((st = dalloc(&d_off1, nleaf + 1)) || (st = dalloc(&pc->blk_off, nleaf + 1)) ||
+        (st = dalloc(&pc->inv64, off2[nleaf])) || (st = dalloc(&piv, 2 * op->n)) || (st = dalloc(&sing, 1))) {
+        cleanup();
+        fb_precond_free(pc);
+        return st;
+    }
+    cudaMemcpyAsync(d_off1, off1.data(), sizeof(int64_t) * (nleaf + 1), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(pc->blk_off, off2.data(), sizeof(int64_t) * (nleaf + 1), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(sing, 0, sizeof(int), s);
+    for (int q = 0; q < 4 && st == FB_OK; ++q) {
+        const fb_op* sub = op->sub[q];
+        if (sub->nf64) {
+            if ((st = dalloc(&tmp[q], std::max<int64_t>(off1[nleaf], 1))) == FB_OK)
+                st = fb_self_blocks(sub, d_off1, tmp[q], s);
+            self[q] = tmp[q];
+        } else {
+            self[q] = sub->self64;
+        }
+    }
+    if (st == FB_OK) {
+        // sub-operators: 0 = M, 1 = L, 2 = M', 3 = L'
+        k_ibem_bj_assemble<<<nleaf, 256, 0, s>>>(t->leaf_start, t->perm, d_off1, pc->blk_off, self[0], self[1],
+                                                 self[2], self[3], op->ib_beta_p, op->ib_beta_m, op->k, pc->inv64);
+        st = fb_smem_cap((const void*)k_bj_invert, sizeof(cd) * 2 * std::max(maxn, 1));
+    }
+    if (st == FB_OK) {
+        k_bj_invert<<<nleaf, 256, sizeof(cd) * 2 * std::max(maxn, 1), s>>>(t->leaf_start, pc->blk_off, pc->inv64,
+                                                                            piv, sing, 2);
+        int hs = 0;
+        cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fb_fail(FB_ERR_CUDA, std::string("indirect block Jacobi: ") + cudaGetErrorString(e));
+        else if (hs) st = fb_fail(FB_ERR_BREAKDOWN, "singular leaf block in the indirect block-Jacobi setup");
+    }
+    cleanup();
+    if (st != FB_OK) {
+        fb_precond_free(pc);
+        return st;
+    }
+    fb_count_launch(2);
+    *out = pc;
+    return FB_OK;
 }
 
 __global__ void k_d2f_bj(const cd* a, cf* b, int64_t n) {
@@ -945,6 +1080,7 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
     *out = nullptr;
     if (kind == FB_PC_NONE) return FB_OK;
     if (kind != FB_PC_BLOCK_JACOBI) return fb_fail(FB_ERR_ARG, "unknown preconditioner kind");
+    if (op->kind == FB_OP_IBEM) return ibem_bj_create(op, s, out);
     if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "block Jacobi needs an FMM operator");
     const fb_tree* t = op->tree;
     int nleaf = t->nbox[t->L];
@@ -971,7 +1107,7 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
     if (op->nf64) FB_CHECK(fb_self_blocks(op, pc->blk_off, pc->inv64, s));
     else FB_CUDA(cudaMemcpyAsync(pc->inv64, op->self64, sizeof(cd) * off[nleaf], cudaMemcpyDeviceToDevice, s));
     FB_CHECK(fb_smem_cap((const void*)k_bj_invert, sizeof(cd) * std::max(maxn, 1)));
-    k_bj_invert<<<nleaf, 256, sizeof(cd) * std::max(maxn, 1), s>>>(t->leaf_start, pc->blk_off, pc->inv64, piv, sing);
+    k_bj_invert<<<nleaf, 256, sizeof(cd) * std::max(maxn, 1), s>>>(t->leaf_start, pc->blk_off, pc->inv64, piv, sing, 1);
     int hs = 0;
     FB_CUDA(cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, s));
     FB_CUDA(cudaStreamSynchronize(s));
@@ -1017,6 +1153,15 @@ fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, 
     int nleaf = t->nbox[t->L];
     int maxn = 0;
     for (int b = 0; b < nleaf; ++b) maxn = std::max(maxn, t->h_leaf_start[b + 1] - t->h_leaf_start[b]);
+    if (pc->ibem) {
+        FB_CHECK(fb_smem_cap((const void*)k_ibem_bj_apply, sizeof(cd) * 2 * maxn));
+        for (int r = 0; r < nrhs; ++r)
+            k_ibem_bj_apply<<<nleaf, 128, sizeof(cd) * 2 * maxn, s>>>(t->leaf_start, t->perm, pc->blk_off, pc->inv64,
+                                                                      x + r * n, y + r * n, n / 2);
+        FB_LAUNCH_CHECK();
+        fb_count_launch(nrhs);
+        return FB_OK;
+    }
     dim3 g(nleaf, nrhs);
     FB_CHECK(fb_smem_cap(pc->inv32 ? (const void*)k_bj_apply<float> : (const void*)k_bj_apply<double>,
                          (pc->inv32 ? sizeof(cf) : sizeof(cd)) * maxn));

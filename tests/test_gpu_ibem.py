@@ -65,7 +65,7 @@ def test_dense_composite_matches_oracle():
         f = fb.fb_ibem_field(op, xs, gp, gm, torch.tensor(rcv, device="cuda"))
         sig, mu = ibem.densities(K_SMALL, bp, bm, xref[:n], xref[n:], rp, rm)
         assert rel(f.cpu().numpy(), ibem.field(om, K_SMALL, sig, mu, rcv)) < 1e-8
-        # the composite refuses the single-operator preconditioners
+        # block Jacobi needs the FMM composite (leaf blocks from the tree)
         with pytest.raises(fb.FBError):
             fb.fb_precond_create(op, fb.FB_PC_BLOCK_JACOBI)
     finally:
@@ -112,25 +112,50 @@ def test_fmm_composite_and_mixed_solve():
             fb.fb_operator_apply(op, xd, yd)
             torch.cuda.synchronize()
             assert rel(yd.cpu().numpy(), ref) < tol
-        # mixed solve, inner-outer on a low-accuracy mixed composite, FP64 judge
+        # block Jacobi of the 2 x 2 leaf blocks against the oracle's matrix
+        # restricted to the same blocks (tree order of the bit-exact octree)
+        from oracle.octree import Octree
+        om = oracle_mesh("small")
+        el = om.el
+        T = Octree(np.concatenate([el.v0, el.v1, el.v2]), el.centroid, om.rc, 64)
+        bj64 = fb.fb_precond_create(A64, fb.FB_PC_BLOCK_JACOBI)
+        r = np.concatenate([seeded_vector(n, 25), seeded_vector(n, 26)])
+        z = torch.empty_like(xd)
+        fb.fb_precond_apply(bj64, torch.tensor(r, device="cuda"), z)
+        fb.fb_precond_destroy(bj64)
+        zref = np.zeros(2 * n, np.complex128)
+        starts = np.append(T.leaf_start, n)
+        for b in range(len(T.leaf_start)):
+            idx = T.perm[starts[b]:starts[b + 1]]
+            ii = np.concatenate([idx, n + idx])
+            zref[ii] = np.linalg.solve(A[np.ix_(ii, ii)], r[ii])
+        assert rel(z.cpu().numpy(), zref) < 1e-9
+        # mixed solves judged by the FP64 composite: block Jacobi, and
+        # inner-outer on a low-accuracy mixed composite with its block Jacobi
         Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_IBEM, fb.FB_PREC_MIXED_FMM, 2.0, 4)
         ops.append(Alow)
         fb.fb_operator_use_graphs(A32, True)
-        pc = fb.fb_precond_create_inner(A32, Alow, None, 6)
+        bj = fb.fb_precond_create(A32, fb.FB_PC_BLOCK_JACOBI)
+        bjlow = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
+        inner = fb.fb_precond_create_inner(A32, Alow, bjlow, 6)
         src = wl.sources[0]
         gp, gm = fb.fb_ibem_gammas_monopole(A64, src)
         b = fb.fb_ibem_rhs(A64, gp, gm)
-        xs = torch.zeros_like(b)
-        info = fb.fb_fgmres_solve(A32, b, xs, pc=pc, tol=1e-6, restart=40, maxit=400, max_refine=6, true_op=A64)
-        fb.fb_precond_destroy(pc)
-        assert info["status"] == 0 and info["true_relres"] <= 1e-6
-        om = oracle_mesh("small")
         u, gu = bem.incident(om.el.centroid, src, wl.k)
         rp, rm = ibem.gammas_incident(wl.k, bp, wl.beta, u, np.sum(gu * om.el.normal, 1))
         xref = np.linalg.solve(A, ibem.rhs(D["L"], D["LP"], rp, rm))
-        err = rel(xs.cpu().numpy(), xref)
-        print(f"indirect mixed solve: {info['iters']} iterations, solution vs oracle {err:.2e}")
-        assert err < 1e-4
+        its = {}
+        for name, pc in (("block Jacobi", bj), ("inner-outer", inner)):
+            xs = torch.zeros_like(b)
+            info = fb.fb_fgmres_solve(A32, b, xs, pc=pc, tol=1e-6, restart=40, maxit=400, max_refine=6, true_op=A64)
+            assert info["status"] == 0 and info["true_relres"] <= 1e-6
+            err = rel(xs.cpu().numpy(), xref)
+            assert err < 1e-4
+            its[name] = info["iters"]
+        for pc in (inner, bjlow, bj):
+            fb.fb_precond_destroy(pc)
+        print(f"indirect mixed solves, outer iterations: {its} (75 with inner-outer alone)")
+        assert its["inner-outer"] < 40
     finally:
         for op in ops:
             fb.fb_operator_destroy(op)
