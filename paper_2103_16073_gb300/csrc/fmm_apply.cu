@@ -384,9 +384,23 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
 // FP32 (two CTAs per SM; the columns of a tile reuse each rotation / coaxial
 // entry from registers, so larger tiles raise the arithmetic per load) and
 // 48 KB for FP64 (bound by the FP64 pipe, it wants more resident warps).
-// Columns needing more than RCR_SMEM_MAX bytes go to one-column tiles in
-// `big` (global scratch).
+// Columns needing more than RCR_SMEM_MAX bytes go to tiles in `big` whose
+// working set lives in a global scratch slot; up to RCR_BIG_COLS columns per
+// tile share each rotation / coaxial coefficient from registers, as long as
+// the plan keeps at least two such tiles per SM.
 constexpr size_t RCR_SMEM_MAX = 200 * 1024;
+constexpr int RCR_BIG_COLS = 4;
+
+static int sm_count() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms < 1) sms = 1;
+    }
+    return sms;
+}
 static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& tiles, size_t& smem,
                            std::vector<RcrTile>& big, int64_t& big_per) {
     const size_t budget = pl.csize == sizeof(cf) ? 96 * 1024 : 48 * 1024;
@@ -394,13 +408,23 @@ static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& ti
     big.clear();
     smem = 0;
     big_per = 0;
+    int64_t big_cols = 0;
+    for (const RcrTask& tk : pl.h_tasks) {
+        size_t per = (size_t)(tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out)) * pl.csize;
+        if (per > RCR_SMEM_MAX) big_cols += (int64_t)tk.npairs * nrhs;
+    }
+    const int nbig = (int)std::max<int64_t>(1, std::min<int64_t>(RCR_BIG_COLS, big_cols / (2 * sm_count())));
     for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
         const RcrTask& tk = pl.h_tasks[t];
         int64_t elems = (int64_t)tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out);
         size_t per = (size_t)elems * pl.csize;
         if (per > RCR_SMEM_MAX) {
-            for (int c = 0; c < tk.npairs * nrhs; ++c) big.push_back(RcrTile{t, c, 1, 0});
-            big_per = std::max(big_per, elems);
+            const int ncol = tk.npairs * nrhs;
+            for (int c = 0; c < ncol; c += nbig) big.push_back(RcrTile{t, c, std::min(nbig, ncol - c), 0});
+            // slots always hold RCR_BIG_COLS columns, so the tile sets built
+            // later for several right-hand sides (more columns, wider tiles)
+            // fit the scratch allocated with the plan
+            big_per = std::max(big_per, elems * RCR_BIG_COLS);
             continue;
         }
         int nb = (int)std::max<size_t>(1, std::min<size_t>(16, budget / per));
