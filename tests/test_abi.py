@@ -39,3 +39,33 @@ def test_argument_errors_are_reported_without_device_work():
     with pytest.raises(fb.FBError) as e:
         fb.fb_mesh_create(np.zeros((3, 3)), np.array([[0, 1, 5]]))   # index out of range
     assert e.value.code == 1
+
+
+def test_new_entry_points_validate_arguments_on_the_host():
+    """Argument checks of the broadband, indirect and dbem5 entry points run
+    before any device work and report FB_ERR_ARG."""
+    import ctypes as C
+    import numpy as np
+    lib = fb.lib
+    room = np.array([8.0, 6.0, 3.0])
+    outside = np.array([9.0, 2.0, 1.0])
+    Rw = np.zeros(12)
+    k = np.array([1.0])
+    dummy = C.c_void_p(16)
+    # source outside the room, no wavenumbers, non-positive threshold
+    assert lib.fb_image_field(room.ctypes.data, outside.ctypes.data, Rw.ctypes.data, 1e-7, k.ctypes.data, 1,
+                              dummy, 1, dummy, None) == 1
+    src = np.array([3.0, 2.0, 1.0])
+    assert lib.fb_image_field(room.ctypes.data, src.ctypes.data, Rw.ctypes.data, 1e-7, k.ctypes.data, 0,
+                              dummy, 1, dummy, None) == 1
+    assert lib.fb_image_field(room.ctypes.data, src.ctypes.data, Rw.ctypes.data, 0.0, k.ctypes.data, 1,
+                              dummy, 1, dummy, None) == 1
+    f = np.array([10.0])
+    assert lib.fb_pulse_synthesis(dummy, f.ctypes.data, 1, 1, 0.0, 1e-3, 8, 1e-3, dummy, None) == 1   # df = 0
+    assert lib.fb_pulse_synthesis(dummy, f.ctypes.data, 1, 1, 10.0, 1e-3, 0, 1e-3, dummy, None) == 1  # nt = 0
+    # NULL handles
+    assert lib.fb_ibem_rhs(None, dummy, dummy, dummy, None) == 1
+    assert lib.fb_ibem_field(None, dummy, dummy, dummy, dummy, 1, dummy, None) == 1
+    assert lib.fb_dbem5_rhs(None, dummy, dummy, None) == 1
+    assert lib.fb_dbem5_psi(None, dummy, dummy, dummy, None) == 1
+    assert lib.fb_krylov_basis(None, None, dummy, 3, dummy, None) == 1
