@@ -24,7 +24,7 @@ KINDS = {"A": fb.FB_OP_A, "L": fb.FB_OP_L, "M": fb.FB_OP_M, "LP": fb.FB_OP_LP}
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="1khz", choices=["1khz", "sub", "small"])
+    ap.add_argument("--workload", default="1khz", choices=["1khz", "sub", "small", "high_order"])
     ap.add_argument("--prec", default="mixed", choices=list(PRECS))
     ap.add_argument("--kind", default="A", choices=list(KINDS))
     ap.add_argument("--matvecs", type=int, default=3)
@@ -33,7 +33,8 @@ def main():
     ap.add_argument("--forms", default="", help="fixed per-level choice, comma-separated ints by level "
                                                 "(bit 0 M2L on tensor cores, bit 1 M2M/L2L), e.g. 0,0,0,2,0,1")
     args = ap.parse_args()
-    wl = {"1khz": W.cfg_1khz, "sub": W.cfg_1khz_sub, "small": W.cfg_small}[args.workload]()
+    wl = {"1khz": W.cfg_1khz, "sub": W.cfg_1khz_sub, "small": W.cfg_small,
+          "high_order": W.cfg_high_order}[args.workload]()
     torch.cuda.set_device(0)
     mesh = fb.fb_mesh_create(wl.verts, wl.tris)
     fb.fb_mesh_set_admittance(mesh, wl.beta)

@@ -389,6 +389,15 @@ def cfg_1khz_sub(nrec=64):
                             (22, 18, 15), 1000.0, 0.2, (0.7, 0.6, 0.5), nrec, 1)
 
 
+def cfg_high_order(nrec=8):
+    """Coarse mesh at a high frequency: the 3.0 x 2.4 x 2.0 m shoebox with
+    16 x 16 x 16 rectangles per edge (N = 3,072) at 7.5 kHz, so the
+    expansion orders (116 on level 2, 66 on level 3) exceed what one
+    shared-memory tile holds."""
+    return shoebox_workload("shoebox-3.0x2.4x2.0-7.5kHz-N3072", 3.0, 2.4, 2.0, (16, 16, 16), 7500.0, 0.2,
+                            (0.7, 0.6, 0.5), nrec, 0)
+
+
 def exterior_source(room, dist=0.5):
     """A point at least `dist` outside the room's bounding box (for the
     exterior-source test: its field is regular inside the room)."""

@@ -32,8 +32,7 @@ def workload(name):
         "baffle_sub": W.cfg_baffle_sub,
         # coarse mesh at a high frequency: expansion orders 116 (root children)
         # and 66, above what one shared-memory tile holds
-        "high_order": lambda: W.shoebox_workload("shoebox-3.0x2.4x2.0-7.5kHz-N3072", 3.0, 2.4, 2.0, (16, 16, 16),
-                                                 7500.0, 0.2, (0.7, 0.6, 0.5), 8, 0),
+        "high_order": W.cfg_high_order,
         "baffle": W.cfg_baffle,
         "largest": W.cfg_largest,
         # a small room with walls of different admittance and a ragged count
