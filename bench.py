@@ -5,7 +5,8 @@ Workload: shoebox 3.0 x 2.4 x 2.0 m at 1 kHz (kD ~ 81), flat triangles with
 legs lambda/8 (70 x 56 x 47 rectangles per edge) -> N = 39,368 elements,
 uniform admittance 0.2, monopole at (0.7, 0.6, 0.5) m; octree leaves <= 64
 elements; FMM order per level from the excess-bandwidth rule (d0 = 6,
-p_min = 12).  Synthetic seeded input; see the design doc.
+p_min = 12).  Synthetic input: a structured mesh; ranks other than 0 solve
+for seeded source positions.
 
 A step is one solve A x = b of Eq. (dbem4) with the mixed operator (FP32 near
 field, P2M/L2P and translations, FP64 Arnoldi) right-preconditioned by the
@@ -34,6 +35,7 @@ import math
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -60,7 +62,10 @@ class ClockSampler:
     """nvidia-smi clock/throttle sampling during the timed region."""
 
     def __init__(self, gpu_index=0):
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # raw samples go to FB_BENCH_LOG_DIR (default: the temporary directory);
+        # the JSON line carries their summary
+        out_dir = os.environ.get("FB_BENCH_LOG_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"clocks_gpu{gpu_index}.csv")
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
