@@ -197,3 +197,26 @@ def test_multipole_to_multipole_translation():
     lhs = sph.singular(p_in, k, r + t)
     rhs = T.T @ sph.singular(p_out, k, r)
     assert np.max(np.abs(lhs - rhs)) < 1e-10 * np.max(np.abs(lhs))
+
+
+def test_rotation_factors_from_quarter_turn_identity():
+    """The real factors d^n(theta) of the rotation blocks (D = d e^{i m phi})
+    follow from the single matrix Delta^n = d^n(pi/2) by
+    d_{mu,m}(theta) = sum_k Delta_{mu,k} Delta_{m,k} cos(k theta + (mu - m) pi/2)
+    (a rotation about y written as a rotation about z between quarter turns);
+    checked against the projection of the rotation definition for axis,
+    diagonal and general directions up to degree 39."""
+    p = 40
+    Dl = [b.real for b in sph.rotation_blocks(sph.rotation_to_z(np.array([1.0, 0.0, 0.0])), p)]
+    worst = 0.0
+    for t in ([0, 0, 1.0], [0, 0, -1.0], [2, -3, 1.0], [-1, -1, -3.0], [3, 3, 3.0], [1, 0, -2.0]):
+        t = np.asarray(t)
+        th = np.arccos(t[2] / np.linalg.norm(t))
+        ph = np.arctan2(t[1], t[0])
+        D = sph.rotation_blocks(sph.rotation_to_z(t), p)
+        for n in range(p):
+            m = np.arange(-n, n + 1)
+            C = np.cos(m[None, None, :] * th + (m[:, None, None] - m[None, :, None]) * np.pi / 2)
+            d = np.einsum("ak,bk,abk->ab", Dl[n], Dl[n], C)
+            worst = max(worst, float(np.max(np.abs(d * np.exp(1j * m[None, :] * ph) - D[n]))))
+    assert worst < 1e-12
