@@ -384,7 +384,9 @@ FB_API fb_status fb_dbem5_psi(fb_op* op, const double* q, const double* gamma, d
  * and Berkley): out[m][r] = sum_j A_j e^{i k_m R_j}/(4 pi R_j) over the
  * source and its images, A_j the product of the wall reflection
  * coefficients met (R_walls: 6 complex, walls x=0, x=lx, y=0, y=ly, z=0,
- * z=lz), images with |A_j| < a_th dropped (Sec. 4 uses 1e-7).  room, src:
+ * z=lz), images with |A_j| < a_th dropped (Sec. 4 uses 1e-7; refused with
+ * FB_ERR_ARG when that needs more than 64 image orders per axis; with
+ * |R| >= 1, 20 orders per axis are kept).  room, src:
  * 3 doubles (host); k: nf wavenumbers (host); rcv: nr x 3 doubles and out:
  * nf x nr complex (device).  Synchronous.  Errors: FB_ERR_ARG. */
 FB_API fb_status fb_image_field(const double* room, const double* src, const double* R_walls, double a_th,

@@ -65,7 +65,13 @@ fb_status fb_image_field_impl(const double* room, const double* src, const cd* R
                               int nf, const double* rcv, int64_t nr, cd* out, cudaStream_t s) {
     double rmax = 0.0;
     for (int w = 0; w < 6; ++w) rmax = std::max(rmax, std::hypot(Rw[w].re, Rw[w].im));
-    int qmax = rmax < 1.0 ? (int)std::ceil(std::log(a_th) / std::log(rmax) / 2.0) + 1 : 20;
+    // images per axis: enough for |A| >= a_th, at most 2 x 64 + 2 (about
+    // 2.2 million candidates in all); |R| >= 1 keeps 20 orders per axis
+    const double qneed = rmax < 1.0 ? std::ceil(std::log(a_th) / std::log(rmax) / 2.0) + 1.0 : 20.0;
+    if (!(qneed <= 64.0))
+        return fb_fail(FB_ERR_ARG, "reflection coefficients this close to 1 need more than 64 image orders per "
+                                   "axis for a_th; raise a_th");
+    const int qmax = (int)qneed;
     struct Ax {
         std::vector<double> pos;
         std::vector<cd> amp;

@@ -69,3 +69,17 @@ def test_new_entry_points_validate_arguments_on_the_host():
     assert lib.fb_dbem5_rhs(None, dummy, dummy, None) == 1
     assert lib.fb_dbem5_psi(None, dummy, dummy, dummy, None) == 1
     assert lib.fb_krylov_basis(None, None, dummy, 3, dummy, None) == 1
+
+
+def test_image_field_refuses_excessive_image_orders():
+    """|R| = 0.999 with a_th = 1e-7 would need thousands of image orders per
+    axis: refused on the host before any allocation."""
+    import ctypes as C
+    import numpy as np
+    room = np.array([8.0, 6.0, 3.0])
+    src = np.array([3.0, 2.0, 1.0])
+    Rw = np.array([0.999, 0.0] * 6)
+    k = np.array([1.0])
+    dummy = C.c_void_p(16)
+    assert fb.lib.fb_image_field(room.ctypes.data, src.ctypes.data, Rw.ctypes.data, 1e-7, k.ctypes.data, 1,
+                                 dummy, 1, dummy, None) == 1
