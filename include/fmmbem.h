@@ -80,15 +80,18 @@ typedef int fb_status;
                       with a = k/(i zeta) = -i k beta per side (beta- = the mesh
                       admittance, beta+ = fb_mesh_set_admittance_plus, default
                       beta-), both copied at creation.  Composed of the L, M, L',
-                      M' operators of the given precision on the same tree; block
-                      Jacobi and the learned network do not apply to it (the
-                      inner-outer preconditioner does). */
+                      M' operators of the given precision on the same tree.
+                      fb_precond_create builds its block Jacobi from 2n x 2n leaf
+                      blocks (FMM precisions); the learned network does not
+                      apply to it. */
 #define FB_OP_DBEM5 6 /* direct-BEM system of Eq. dbem5 for the unknown
                       q = d psi_sc/dn (N x N): 1/2 q + (1/zeta) M[zeta q]
                       + (k/(i zeta)) L[q], i.e. 1/2 q + beta M[q/beta]
                       - i k beta L[q]; needs beta != 0 on every element
                       (FB_ERR_ARG otherwise).  Composed of M and L; right-hand
-                      side and psi_sc by fb_dbem5_rhs / fb_dbem5_psi. */
+                      side and psi_sc by fb_dbem5_rhs / fb_dbem5_psi; block
+                      Jacobi from the leaf blocks 1/2 + beta_i M_ij / beta_j
+                      - i k beta_i L_ij (FMM precisions). */
 
 /* How an operator is applied. */
 #define FB_PREC_FP64_DENSE 0 /* stored dense N x N complex128 matrix        */

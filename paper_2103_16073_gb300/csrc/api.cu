@@ -592,8 +592,6 @@ fb_status fb_gamma_monopole(const fb_mesh* m, double k, const double* src, doubl
 
 fb_status fb_precond_create(fb_op* op, int kind, void* stream, fb_precond** out) {
     if (!op || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
-    if (op->kind == FB_OP_DBEM5 && kind != FB_PC_NONE)
-        return fb_fail(FB_ERR_ARG, "block Jacobi is not built for Eq. dbem5 (use the inner-outer preconditioner)");
     return fb_precond_create_impl(op, kind, as_stream(stream), out);
 }
 

@@ -636,6 +636,87 @@ __global__ void k_ibem_bj_apply(const int32_t* leaf_start, const int32_t* perm, 
 
 void fb_precond_free(fb_precond* pc);
 
+// Block Jacobi of Eq. (dbem5) (FB_OP_DBEM5): per leaf
+//   B_ij = delta_ij / 2 + beta_i M_ij / beta_j - i k beta_i L_ij
+// from the self-blocks of M and L (tree order, row = target).
+__global__ void k_d5_bj_assemble(const int32_t* leaf_start, const int32_t* perm, const int64_t* off1,
+                                 const cd* Mb, const cd* Lb, const cd* beta, double k, cd* out) {
+    int t = blockIdx.x;
+    int r0 = leaf_start[t], n = leaf_start[t + 1] - r0;
+    const int64_t o = off1[t];
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+        int i = e / n, j = e % n;
+        cd bi = beta[perm[r0 + i]], bj = beta[perm[r0 + j]];
+        double d = bj.re * bj.re + bj.im * bj.im;
+        cd ratio = bi * mk(bj.re / d, -bj.im / d);
+        cd ikb = mk(-k * bi.im, k * bi.re);
+        out[o + e] = mk(i == j ? 0.5 : 0.0, 0.0) + ratio * Mb[o + e] - ikb * Lb[o + e];
+    }
+}
+
+static fb_status dbem5_bj_create(fb_op* op, cudaStream_t s, fb_precond** out) {
+    const fb_tree* t = op->tree;
+    if (!t || op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "block Jacobi needs an FMM operator");
+    const int nleaf = t->nbox[t->L];
+    std::vector<int64_t> off(nleaf + 1, 0);
+    int maxn = 0;
+    for (int b = 0; b < nleaf; ++b) {
+        int64_t nb = t->h_leaf_start[b + 1] - t->h_leaf_start[b];
+        maxn = std::max<int>(maxn, (int)nb);
+        off[b + 1] = off[b] + nb * nb;
+    }
+    fb_precond* pc = new fb_precond();
+    pc->op = op;
+    pc->kind = FB_PC_BLOCK_JACOBI;
+    pc->n = op->n;
+    cd* tmp[2] = {nullptr, nullptr};
+    const cd* self[2] = {nullptr, nullptr};
+    int* piv = nullptr;
+    int* sing = nullptr;
+    auto cleanup = [&]() { dfree(tmp[0]); dfree(tmp[1]); dfree(piv); dfree(sing); };
+    fb_status st = FB_OK;
+    if ((st = dalloc(&pc->blk_off, nleaf + 1)) || (st = dalloc(&pc->inv64, std::max<int64_t>(off[nleaf], 1))) ||
+        (st = dalloc(&piv, op->n)) || (st = dalloc(&sing, 1))) {
+        cleanup();
+        fb_precond_free(pc);
+        return st;
+    }
+    cudaMemcpyAsync(pc->blk_off, off.data(), sizeof(int64_t) * (nleaf + 1), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(sing, 0, sizeof(int), s);
+    for (int q = 0; q < 2 && st == FB_OK; ++q) {   // sub-operators: 0 = M, 1 = L
+        const fb_op* sub = op->sub[q];
+        if (sub->nf64) {
+            if ((st = dalloc(&tmp[q], std::max<int64_t>(off[nleaf], 1))) == FB_OK)
+                st = fb_self_blocks(sub, pc->blk_off, tmp[q], s);
+            self[q] = tmp[q];
+        } else {
+            self[q] = sub->self64;
+        }
+    }
+    if (st == FB_OK) {
+        k_d5_bj_assemble<<<nleaf, 256, 0, s>>>(t->leaf_start, t->perm, pc->blk_off, self[0], self[1], op->ib_beta_m,
+                                               op->k, pc->inv64);
+        st = fb_smem_cap((const void*)k_bj_invert, sizeof(cd) * std::max(maxn, 1));
+    }
+    if (st == FB_OK) {
+        k_bj_invert<<<nleaf, 256, sizeof(cd) * std::max(maxn, 1), s>>>(t->leaf_start, pc->blk_off, pc->inv64, piv,
+                                                                        sing, 1);
+        int hs = 0;
+        cudaMemcpyAsync(&hs, sing, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fb_fail(FB_ERR_CUDA, std::string("dbem5 block Jacobi: ") + cudaGetErrorString(e));
+        else if (hs) st = fb_fail(FB_ERR_BREAKDOWN, "singular leaf block in the dbem5 block-Jacobi setup");
+    }
+    cleanup();
+    if (st != FB_OK) {
+        fb_precond_free(pc);
+        return st;
+    }
+    fb_count_launch(2);
+    *out = pc;
+    return FB_OK;
+}
+
 static fb_status ibem_bj_create(fb_op* op, cudaStream_t s, fb_precond** out) {
     const fb_tree* t = op->tree;
     if (!t || op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "block Jacobi needs an FMM operator");
@@ -1081,6 +1162,7 @@ fb_status fb_precond_create_impl(fb_op* op, int kind, cudaStream_t s, fb_precond
     if (kind == FB_PC_NONE) return FB_OK;
     if (kind != FB_PC_BLOCK_JACOBI) return fb_fail(FB_ERR_ARG, "unknown preconditioner kind");
     if (op->kind == FB_OP_IBEM) return ibem_bj_create(op, s, out);
+    if (op->kind == FB_OP_DBEM5) return dbem5_bj_create(op, s, out);
     if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "block Jacobi needs an FMM operator");
     const fb_tree* t = op->tree;
     int nleaf = t->nbox[t->L];

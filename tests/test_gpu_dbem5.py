@@ -111,6 +111,33 @@ def test_fmm_dbem5_and_convergence_contrast():
         i4 = fb.fb_fgmres_solve(A4, b4, x4, tol=1e-6, restart=40, maxit=3000)
         i5 = fb.fb_fgmres_solve(ops[1], b5, q, tol=1e-6, restart=40, maxit=3000)
         assert i4["status"] == 0 and i5["status"] == 0
+        # block Jacobi of the dbem5 leaf blocks against the oracle's matrix
+        # restricted to the same blocks, and a preconditioned solve
+        from oracle.octree import Octree
+        om = oracle_mesh("small")
+        el = om.el
+        T = Octree(np.concatenate([el.v0, el.v1, el.v2]), el.centroid, om.rc, 64)
+        bj = fb.fb_precond_create(ops[0], fb.FB_PC_BLOCK_JACOBI)
+        r = seeded_vector(wl.n, 29)
+        z = torch.empty_like(xd)
+        fb.fb_precond_apply(bj, torch.tensor(r, device="cuda"), z)
+        fb.fb_precond_destroy(bj)
+        zref = np.zeros(wl.n, np.complex128)
+        starts = np.append(T.leaf_start, wl.n)
+        for blk in range(len(T.leaf_start)):
+            idx = T.perm[starts[blk]:starts[blk + 1]]
+            zref[idx] = np.linalg.solve(A5[np.ix_(idx, idx)], r[idx])
+        assert rel(z.cpu().numpy(), zref) < 1e-9
+        bj5 = fb.fb_precond_create(ops[1], fb.FB_PC_BLOCK_JACOBI)
+        bj4 = fb.fb_precond_create(A4, fb.FB_PC_BLOCK_JACOBI)
+        x4b = torch.zeros_like(g)
+        q5b = torch.zeros_like(g)
+        j4 = fb.fb_fgmres_solve(A4, b4, x4b, pc=bj4, tol=1e-6, restart=40, maxit=3000)
+        j5 = fb.fb_fgmres_solve(ops[1], b5, q5b, pc=bj5, tol=1e-6, restart=40, maxit=3000)
+        fb.fb_precond_destroy(bj5)
+        fb.fb_precond_destroy(bj4)
+        assert j4["status"] == 0 and j5["status"] == 0
+        print(f"block-Jacobi FGMRES at 1e-6 (mixed FMM): dbem4 {j4['iters']}, dbem5 {j5['iters']} iterations")
         # the unknowns agree to the FMM accuracy: q = gamma + i k beta psi
         q4 = g + 1j * wl.k * torch.tensor(beta, device="cuda") * x4
         assert rel(q.cpu().numpy(), q4.cpu().numpy()) < 1e-3
