@@ -1,37 +1,38 @@
 """Benchmark: FGMRES time-to-solve at true relative residual 1e-4 and
 matvecs/s of the FMM-accelerated Helmholtz BEM on one GB300.
 
-Workload: shoebox 3.0 x 2.4 x 2.0 m at 1 kHz (kD ~ 81), flat triangles with
-legs lambda/8 (70 x 56 x 47 rectangles per edge) -> N = 39,368 elements,
-uniform admittance 0.2, monopole at (0.7, 0.6, 0.5) m; octree leaves <= 64
-elements; FMM order per level from the excess-bandwidth rule (d0 = 6,
-p_min = 12).  Synthetic input: a structured mesh; ranks other than 0 solve
-for seeded source positions.
+Workload (default): the largest room, shoebox 6.5 x 5.5 x 4.2 m at 5 kHz
+(kD ~ 870), flat triangles with legs lambda/6 (569 x 482 x 368 rectangles)
+-> N = 2,644,104 elements, one admittance per wall drawn uniform in
+[0.05, 0.3] (seeded), one seeded monopole; octree leaves <= 64 elements; FMM
+order per level from the excess-bandwidth rule (d0 = 6, p_min = 12): orders
+159 / 89 / 52 / 32 / 20 / 14 on levels 2-7.  Synthetic input: a structured
+mesh; ranks other than 0 solve for their own seeded source positions.  The
+1 kHz shoebox (3.0 x 2.4 x 2.0 m, N = 39,368) is measured beside it as a
+secondary workload.
 
-A step is one solve A x = b of Eq. (dbem4) with the mixed operator (FP32 near
-field, P2M/L2P and translations, FP64 Arnoldi) right-preconditioned by the
-learned octree network (trained before the timed region on pairs logged from
-block-Jacobi solves for other source positions) refining the inner-outer
-preconditioner of Sec. 4 (a few GMRES steps on a low-accuracy FMM), judged by
-the true residual of the FP64 FMM operator.  The same solve under the
-inner-outer preconditioner alone, under block Jacobi alone, and the plain
-FP64 path (FP64 FMM + FP64 block Jacobi) are timed beside it.  N GPUs
-(torchrun) each solve their own source position: weak scaling, no
-data-path collective.
+A step is one solve A x = b of Eq. (dbem4), b = L gamma, with the mixed
+operator (FP32 near field, P2M/L2P and translations, FP64 Arnoldi) right-
+preconditioned by the inner-outer preconditioner of Sec. 4 (a few GMRES
+steps on a low-accuracy mixed FMM with its own block Jacobi), judged by the
+true residual of the FP64 FMM operator.  The plain FP64 path (FP64 FMM +
+FP64 block Jacobi) is timed beside it.  N GPUs (torchrun) each solve their
+own source position: weak scaling, no data-path collective.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload largest|shoebox_1khz]
 """
 from __future__ import annotations
 
 import os
 
-# the CPU oracle legs run on one host thread; keep BLAS from spreading
+# the host work of this process (and of the oracle worker processes it
+# spawns, which inherit the environment) runs one BLAS thread per process
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
 import argparse
 import json
-import math
 import statistics
 import subprocess
 import sys
@@ -46,7 +47,14 @@ sys.path.insert(0, ROOT)
 METRIC = "FGMRES time-to-solve @1e-4 & matvecs/s: mixed+learned vs plain FP64, 1 GB300"
 TOL = 1e-4
 RESTART = 40
+D0, PMIN = 6.0, 12                              # order rule of the operators (1e-5 FP64 FMM target)
 INNER_D0, INNER_PMIN, INNER_ITERS = 1.0, 4, 6   # inner-outer preconditioner (low-accuracy FMM)
+
+WORKLOADS = {
+    "largest": ("cfg_largest", "shoebox 6.5x5.5x4.2 m, 5 kHz, N=2644104 flat triangles (lambda/6), "
+                               "per-wall beta ~ U[0.05,0.3]"),
+    "shoebox_1khz": ("cfg_1khz", "shoebox 3.0x2.4x2.0 m, 1 kHz, N=39368 flat triangles (lambda/8), beta=0.2"),
+}
 
 
 def peaks():
@@ -71,7 +79,7 @@ class ClockSampler:
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         self.cmd = ["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                    "-lms", "50"]
+                    "-lms", "200"]
         self.proc = None
 
     def __enter__(self):
@@ -143,15 +151,37 @@ def reduce_max_ms(ms, dist, device):
     return float(t.item())
 
 
-def build_problem(fb, W, torch, rank, forms=""):
-    wl = W.cfg_1khz()
+def load_workload(name):
+    from paper_2103_16073_gb300 import workloads as W
+    return getattr(W, WORKLOADS[name][0])()
+
+
+def bench_config(name, wl, ws):
+    """The `config` object of the JSON line (identical for both arms)."""
+    return {"workload": WORKLOADS[name][1], "n_elements": int(wl.n), "frequency_hz": wl.freq_hz,
+            "fmm": f"leaf<=64, order rule d0={D0:g} p_min={PMIN}",
+            "solver": "FGMRES(40), FP64 Arnoldi (CGS2), tol 1e-4 on the FP64 FMM true residual",
+            "step": "one solve A x = b (Eq. dbem4), b = L gamma of a monopole",
+            "precond": (f"inner-outer (Sec. 4): {INNER_ITERS} GMRES steps on a low-accuracy mixed FMM "
+                        f"(d0={INNER_D0:g}, p_min={INNER_PMIN}) with block Jacobi"),
+            "operator": "mixed: FP32 near field, P2M/L2P and translations",
+            "l2": "inputs larger than L2 (near-field entries and translation data of GB size)",
+            "parallelism": f"replicas x{ws} (one (f, source) solve per GPU)"}
+
+
+def build_problem(fb, W, torch, wl, rank, forms=""):
+    """Mesh, tree and the operators of a solve: mixed A (autotuned translation
+    forms, graph replay), FP64 A (true residual, plain method), FP64 L
+    (b = L gamma), block Jacobi of each, and the inner-outer preconditioner
+    on a low-accuracy mixed FMM."""
     wl.sources = rank_source(W, wl, rank)[None, :]
+    t0 = time.perf_counter()
     mesh = fb.fb_mesh_create(wl.verts, wl.tris)
     fb.fb_mesh_set_admittance(mesh, wl.beta)
     tree = fb.fb_tree_build(mesh, 64)
-    A32 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 12)
-    A64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, 12)
-    L64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_L, fb.FB_PREC_FP64_FMM, 6.0, 12)
+    A32 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, D0, PMIN)
+    A64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, D0, PMIN)
+    L64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_L, fb.FB_PREC_FP64_FMM, D0, PMIN)
     pc32 = fb.fb_precond_create(A32, fb.FB_PC_BLOCK_JACOBI)
     pc64 = fb.fb_precond_create(A64, fb.FB_PC_BLOCK_JACOBI)
     # per-level translation forms timed on the device (or a saved choice, e.g.
@@ -164,8 +194,6 @@ def build_problem(fb, W, torch, rank, forms=""):
         tune = fb.fb_operator_autotune(A32, 1)
     for op in (A32, A64):
         fb.fb_operator_use_graphs(op, True)
-    # the paper's inner-outer preconditioner: GMRES steps on a low-accuracy
-    # mixed FMM (INNER_D0, INNER_PMIN) with its own block Jacobi
     Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, INNER_D0, INNER_PMIN)
     if forms:
         fb.fb_operator_set_forms(Alow, [0] * 13)
@@ -180,70 +208,16 @@ def build_problem(fb, W, torch, rank, forms=""):
     fb.fb_operator_apply(L64, g, b)
     torch.cuda.synchronize()
     return dict(wl=wl, mesh=mesh, tree=tree, A32=A32, A64=A64, L64=L64, pc32=pc32, pc64=pc64, b=b, tune=tune,
-                Alow=Alow, pclow=pclow, inner=inner)
+                Alow=Alow, pclow=pclow, inner=inner, setup_s=time.perf_counter() - t0)
 
 
-def train_learned(fb, W, torch, P, nsrc, steps, base):
-    """Learned preconditioner for the mixed operator over `base` (block
-    Jacobi or the inner-outer preconditioner): pairs (r, e) from truncated
-    block-Jacobi solves for `nsrc` seeded source positions other than the
-    benchmarked one, joined by as many white-noise inputs, residual
-    objective, Adam; the parameters kept are those with the fewest FGMRES
-    iterations on one more held-out source (the initial state included).
-    Returns the handle and a summary."""
-    from paper_2103_16073_gb300 import training
-    wl = P["wl"]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rng = W.seeded_rng(200)
-    srcs = W.uniform_points_in_box(rng, [0, 0, 0], list(wl.room), nsrc + 1, 0.3, avoid=wl.sources,
-                                   avoid_dist=0.3)
-    rhs = []
-    for src in srcs:
-        g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
-        fb.fb_gamma_monopole(P["mesh"], wl.k, src, g)
-        b = torch.empty_like(g)
-        fb.fb_operator_apply(P["L64"], g, b)
-        rhs.append(b)
-    Rs, Es = [], []
-    for b in rhs[:nsrc]:
-        R, E = training.collect_pairs(P["A32"], P["pc32"], b)
-        Rs.append(R)
-        Es.append(E)
-    R = torch.cat(Rs)
-    E = torch.cat(Es)
-    npairs = int(R.shape[0])
-    R, E = training.augment_noise(R, E, npairs, seed=7)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    pc = fb.fb_precond_create_learned(P["A32"], base)
-    fb.fb_learned_set_objective(pc, fb.FB_LOSS_RESIDUAL)
-    bval = rhs[nsrc]
-
-    def validate():
-        x = torch.zeros_like(bval)
-        info = fb.fb_fgmres_solve(P["A32"], bval, x, pc=pc, tol=TOL, restart=RESTART, maxit=3000, max_refine=4)
-        return info["iters"]
-
-    x = torch.zeros_like(bval)
-    base_val = fb.fb_fgmres_solve(P["A32"], bval, x, pc=base, tol=TOL, restart=RESTART, maxit=3000,
-                                  max_refine=4)["iters"]
-    res_base = training.residual_error(P["A32"], base, R[:npairs])
-    before = training.evaluate(pc, R, E)
-    hist, vlog = training.train(pc, R, E, steps=steps, lr=1e-3, batch=8, validate=validate, every=10)
-    after = training.evaluate(pc, R, E)
-    res_l = training.residual_error(P["A32"], pc, R[:npairs])
-    torch.cuda.synchronize()
-    t2 = time.perf_counter()
-    info = {"train_sources": nsrc, "pairs": npairs, "noise_inputs": npairs, "objective": "residual",
-            "adam_steps": steps, "batch": 8, "lr": 1e-3,
-            "loss_init": round(before, 5), "loss_selected": round(after, 5),
-            "residual_error_on_pairs": {"base": round(res_base, 4), "learned": round(res_l, 4)},
-            "validation_iterations": {"base": base_val, "selected": min(v for _, v in vlog),
-                                      "log": vlog[:: max(1, len(vlog) // 8)]},
-            "collect_s": round(t1 - t0, 3), "train_s": round(t2 - t1, 3)}
-    del R, E, Rs, Es
-    return pc, info
+def destroy_problem(fb, P):
+    for pc in ("inner", "pclow", "pc32", "pc64"):
+        fb.fb_precond_destroy(P[pc])
+    for op in ("Alow", "A32", "A64", "L64"):
+        fb.fb_operator_destroy(P[op])
+    fb.fb_tree_destroy(P["tree"])
+    fb.fb_mesh_destroy(P["mesh"])
 
 
 def level_counts(fb, op, tree):
@@ -266,13 +240,12 @@ def rcr_flops(p_out, p_in):
 
 
 def roofline(fb, A32, tree, ph32, ph64, iters, true_mv, pk, fp32_peak, fp64_peak, ph_low=None, low_mv=0):
-    """Rooflines of the three translation kernels of a solve and the dominant
-    one (largest estimated device time per step: per-launch CUDA-event phase
+    """Rooflines of the translation kernels of a solve and the dominant one
+    (largest estimated device time per step: per-launch CUDA-event phase
     times x launches per step, the inner operator's matvecs included).
-    Algorithmic flops are the RCR counts of the
-    translations each launch performs (rcr_flops)."""
+    Algorithmic flops are the RCR counts of the translations each launch
+    performs (rcr_flops)."""
     L, p, tc, pairs, nb = level_counts(fb, A32, tree)
-    t_rcr = 0.0
     # k_rcr<double>: the FP64 operator's M2L (all levels) in the true residual
     alg64 = sum(float(pairs[l]) * rcr_flops(p[l], p[l]) for l in range(2, L + 1))
     t64 = ph64["m2l"] / 1e3
@@ -341,6 +314,56 @@ def traffic_for(kernel):
     return d["dram_bytes_per_launch"]
 
 
+def timed(torch, stream, fn, reps=1):
+    """Device time (s) of `reps` calls of fn on `stream` (CUDA events, synchronised)."""
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    out = [fn() for _ in range(reps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps, out
+
+
+def matvec_rate(fb, torch, stream, op, n, reps):
+    xv = torch.randn(n, dtype=torch.complex128, device="cuda")
+    yv = torch.empty_like(xv)
+    for _ in range(2):
+        fb.fb_operator_apply(op, xv, yv)
+    t, _ = timed(torch, stream, lambda: fb.fb_operator_apply(op, xv, yv), reps)
+    ph = [fb.fb_operator_apply_timed(op, xv, yv) for _ in range(3)]
+    return t, {k: statistics.median(p[k] for p in ph) for k in ph[0]}
+
+
+def secondary(fb, W, torch, stream, name):
+    """Mixed + inner-outer and plain FP64 on a second workload (median of 3
+    mixed solves, one plain solve)."""
+    wl = load_workload(name)
+    P = build_problem(fb, W, torch, wl, 0)
+    try:
+        def solve(pc, A, T):
+            x = torch.zeros_like(P["b"])
+            return fb.fb_fgmres_solve(A, P["b"], x, pc=pc, tol=TOL, restart=RESTART, maxit=3000, max_refine=4,
+                                      true_op=T)
+        solve(P["inner"], P["A32"], P["A64"])
+        ts = [timed(torch, stream, lambda: solve(P["inner"], P["A32"], P["A64"])) for _ in range(3)]
+        t_io = statistics.median(t for t, _ in ts)
+        t64, (i64,) = timed(torch, stream, lambda: solve(P["pc64"], P["A64"], None))
+        mv32, _ = matvec_rate(fb, torch, stream, P["A32"], wl.n, 20)
+        mv64, _ = matvec_rate(fb, torch, stream, P["A64"], wl.n, 5)
+        info = ts[-1][1][0]
+        return {"workload": WORKLOADS[name][1], "n_elements": wl.n,
+                "mixed_inner_outer": {"time_to_solve_s": round(t_io, 5), "solves_per_s": round(1 / t_io, 3),
+                                      "iterations": info["iters"], "true_relres": info["true_relres"],
+                                      "matvecs_per_s": round(1 / mv32, 2)},
+                "plain_fp64": {"time_to_solve_s": round(t64, 4), "iterations": i64["iters"],
+                               "true_relres": i64["true_relres"], "matvecs_per_s": round(1 / mv64, 2)},
+                "speedup_vs_plain_fp64": round(t64 / t_io, 2)}
+    finally:
+        destroy_problem(fb, P)
+
+
 def run_ours(args):
     import torch
     import paper_2103_16073_gb300 as fb
@@ -352,17 +375,11 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
-    P = build_problem(fb, W, torch, rank, args.forms)
-    wl = P["wl"]
+    wl = load_workload(args.workload)
+    P = build_problem(fb, W, torch, wl, rank, args.forms)
     n = wl.n
     stream = torch.cuda.current_stream()
-    learned_info = None
-    base = P["inner"] if args.base == "inner" else P["pc32"]
-    if args.precond == "learned":
-        pc_main, learned_info = train_learned(fb, W, torch, P, args.train_sources, args.train_steps, base)
-        fb.fb_precond_use_graphs(pc_main, True)
-    else:
-        pc_main = base
+    pc_main = P["inner"]
 
     def solve_mixed(x, pc=pc_main):
         return fb.fb_fgmres_solve(P["A32"], P["b"], x, pc=pc, tol=TOL, restart=RESTART, maxit=3000,
@@ -402,95 +419,17 @@ def run_ours(args):
     ok = all(i["status"] == 0 for i in infos)
     clocks = sampler.summary(pk.get("sm_max_mhz"))
 
-    # matvecs/s of the mixed operator and the phase split (device pointers)
-    xv = torch.randn(n, dtype=torch.complex128, device="cuda")
-    yv = torch.empty_like(xv)
-    for _ in range(3):
-        fb.fb_operator_apply(P["A32"], xv, yv)
-    torch.cuda.synchronize()
-    nmv = 50
-    a0 = torch.cuda.Event(enable_timing=True)
-    a1 = torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for _ in range(nmv):
-        fb.fb_operator_apply(P["A32"], xv, yv)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    mv_ms = a0.elapsed_time(a1) / nmv
-    phases = [fb.fb_operator_apply_timed(P["A32"], xv, yv) for _ in range(10)]
-    ph = {k: statistics.median(p[k] for p in phases) for k in phases[0]}
-    for _ in range(2):
-        fb.fb_operator_apply(P["A64"], xv, yv)
-    torch.cuda.synchronize()
-    b0 = torch.cuda.Event(enable_timing=True)
-    b1 = torch.cuda.Event(enable_timing=True)
-    nmv64 = 5
-    b0.record(stream)
-    for _ in range(nmv64):
-        fb.fb_operator_apply(P["A64"], xv, yv)
-    b1.record(stream)
-    torch.cuda.synchronize()
-    mv64_ms = b0.elapsed_time(b1) / nmv64
-    ph64 = fb.fb_operator_apply_timed(P["A64"], xv, yv)
-    ph_low = fb.fb_operator_apply_timed(P["Alow"], xv, yv)
-
-    # the same mixed solve under the inner-outer preconditioner alone
-    io_t, io_infos = [], []
-    for _ in range(3):
-        xb = torch.zeros_like(P["b"])
-        d0 = torch.cuda.Event(enable_timing=True)
-        d1 = torch.cuda.Event(enable_timing=True)
-        d0.record(stream)
-        io_infos.append(solve_mixed(xb, P["inner"]))
-        d1.record(stream)
-        torch.cuda.synchronize()
-        io_t.append(d0.elapsed_time(d1) / 1e3)
-    io_s = statistics.median(io_t)
-
-    # the same mixed solve under block Jacobi alone
-    bj_t, bj_infos = [], []
-    for _ in range(3):
-        xb = torch.zeros_like(P["b"])
-        d0 = torch.cuda.Event(enable_timing=True)
-        d1 = torch.cuda.Event(enable_timing=True)
-        d0.record(stream)
-        bj_infos.append(solve_mixed(xb, P["pc32"]))
-        d1.record(stream)
-        torch.cuda.synchronize()
-        bj_t.append(d0.elapsed_time(d1) / 1e3)
-    bj_s = statistics.median(bj_t)
+    # matvecs/s and phase split of the three operators of the solve
+    mv_s, ph = matvec_rate(fb, torch, stream, P["A32"], n, args.matvecs)
+    mv64_s, ph64 = matvec_rate(fb, torch, stream, P["A64"], n, max(2, args.matvecs // 5))
+    mvlow_s, ph_low = matvec_rate(fb, torch, stream, P["Alow"], n, args.matvecs)
 
     # plain FP64 path: FP64 FMM + FP64 block Jacobi, one solve
     x64 = torch.zeros_like(P["b"])
-    c0 = torch.cuda.Event(enable_timing=True)
-    c1 = torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    info64 = fb.fb_fgmres_solve(P["A64"], P["b"], x64, pc=P["pc64"], tol=TOL, restart=RESTART, maxit=3000)
-    c1.record(stream)
-    torch.cuda.synchronize()
-    t64 = c0.elapsed_time(c1) / 1e3
-
-    # eight source positions of the same frequency solved together (lockstep
-    # batched FGMRES, one multi-RHS matvec per Arnoldi step)
-    rng8 = W.seeded_rng(77)
-    srcs8 = W.uniform_points_in_box(rng8, [0, 0, 0], list(wl.room), 8, 0.3)
-    B8 = torch.empty((8, n), dtype=torch.complex128, device="cuda")
-    g8 = torch.empty(n, dtype=torch.complex128, device="cuda")
-    for r8, s8 in enumerate(srcs8):
-        fb.fb_gamma_monopole(P["mesh"], wl.k, s8, g8)
-        fb.fb_operator_apply(P["L64"], g8, B8[r8])
-    X8 = torch.zeros_like(B8)
-    fb.fb_fgmres_solve_multi(P["A32"], B8, X8, pc=P["pc32"], tol=TOL, restart=RESTART, maxit=3000, max_refine=4,
-                             true_op=P["A64"])   # warm-up (multi-RHS tiles, graphs)
-    m0 = torch.cuda.Event(enable_timing=True)
-    m1 = torch.cuda.Event(enable_timing=True)
-    X8.zero_()
-    m0.record(stream)
-    infos8 = fb.fb_fgmres_solve_multi(P["A32"], B8, X8, pc=P["pc32"], tol=TOL, restart=RESTART, maxit=3000,
-                                      max_refine=4, true_op=P["A64"])
-    m1.record(stream)
-    torch.cuda.synchronize()
-    t8 = m0.elapsed_time(m1) / 1e3
+    t64, (info64,) = timed(torch, stream, lambda: fb.fb_fgmres_solve(
+        P["A64"], P["b"], x64, pc=P["pc64"], tol=TOL, restart=RESTART, maxit=3000))
+    # agreement of the two solutions (both judged by the FP64 operator)
+    sol_diff = float((x - x64).norm() / x64.norm())
 
     # end to end through the public API with host (pinned) buffers
     bh = torch.empty(n, dtype=torch.complex128, pin_memory=True)
@@ -498,7 +437,7 @@ def run_ours(args):
     xh = torch.zeros(n, dtype=torch.complex128, pin_memory=True)
     xn = xh.numpy()
     e2e_t = []
-    for _ in range(max(1, min(args.steps, 5))):
+    for _ in range(max(1, min(args.steps, args.e2e_steps))):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         fb.fb_fgmres_solve(P["A32"], bh, xn, pc=pc_main, tol=TOL, restart=RESTART, maxit=3000,
@@ -507,12 +446,18 @@ def run_ours(args):
     e2e_s = statistics.median(e2e_t)
 
     fp32_peak, fp64_peak = fb.fb_measure_alu_peaks()
-    low_mv = iters * INNER_ITERS if args.base == "inner" else 0
+    low_mv = iters * INNER_ITERS
     rf, kernels = roofline(fb, P["A32"], P["tree"], ph, ph64, iters, res_true_matvecs(infos), pk, fp32_peak,
                            fp64_peak, ph_low, low_mv)
+    L, p, tc, pairs, nb = level_counts(fb, P["A32"], P["tree"])
+    setup_s = P["setup_s"]
+    destroy_problem(fb, P)
+    sec = None
+    if rank == 0 and args.secondary and args.workload != "shoebox_1khz":
+        sec = secondary(fb, W, torch, stream, "shoebox_1khz")
     res = {
         "metric": METRIC,
-        "value": round(ws / (ms_step / 1e3), 4),
+        "value": round(ws / (ms_step / 1e3), 5),
         "unit": "solves/s",
         "n_gpus": ws,
         "steps": args.steps,
@@ -523,52 +468,44 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32+f64",
         "data": "synthetic",
-        "config": {"workload": "shoebox 3.0x2.4x2.0 m, 1 kHz, N=39368 flat triangles (lambda/8), "
-                               f"beta=0.2, FMM leaf<=64, d0=6 pmin=12, FGMRES(40)+{args.precond}({args.base}), tol 1e-4",
-                   "n_elements": n, "frequency_hz": wl.freq_hz, "solver": "FGMRES restart 40",
-                   "precond": (("learned octree network (BF16 tensor-core kernels) over " if args.precond == "learned"
-                                else "") + (f"inner-outer: {INNER_ITERS} GMRES steps on a low-accuracy mixed FMM "
-                                            f"(d0={INNER_D0:g}, p_min={INNER_PMIN}) with block Jacobi" if args.base == "inner"
-                                            else "block Jacobi (leaf self blocks)")),
-                   "operator": "mixed FP32 FMM, FP64 Arnoldi",
-                   "true_residual": "FP64 FMM", "l2": "working set > L2 (translation matrices alone > 129 MB)",
-                   "parallelism": f"replicas x{ws} (one (f, source) solve per GPU)"},
+        "config": bench_config(args.workload, wl, ws),
         "time_to_solve_s": round(ms_step / 1e3, 5),
         "iterations": iters,
+        "inner_iterations_per_outer": INNER_ITERS,
         "true_relres": relres,
+        "true_matvecs_per_solve": res_true_matvecs(infos),
         "converged": ok,
-        "matvecs_per_s": round(1e3 / mv_ms, 2),
-        "matvec_ms": round(mv_ms, 4),
-        "phase_ms": {k: round(v, 4) for k, v in ph.items()},
-        "pc_fallbacks": max(i.get("pc_fallbacks", 0) for i in infos),
-        "learned": learned_info,
-        "mixed_inner_outer": {"time_to_solve_s": round(io_s, 5), "iterations": io_infos[-1]["iters"],
-                              "true_relres": io_infos[-1]["true_relres"],
-                              "inner": {"d0": INNER_D0, "p_min": INNER_PMIN, "iters": INNER_ITERS,
-                                        "preconditioner": "block Jacobi of the inner operator"}},
-        "mixed_block_jacobi": {"time_to_solve_s": round(bj_s, 5), "iterations": bj_infos[-1]["iters"],
-                               "true_relres": bj_infos[-1]["true_relres"]},
+        "setup_s": round(setup_s, 2),
+        "orders_per_level": [int(v) for v in p[2:]],
+        "m2l_pairs_per_level": [int(v) for v in pairs[2:]],
+        "matvecs_per_s": {"mixed": round(1 / mv_s, 3), "fp64": round(1 / mv64_s, 3),
+                          "inner_low_accuracy": round(1 / mvlow_s, 3)},
+        "matvec_ms": {"mixed": round(mv_s * 1e3, 3), "fp64": round(mv64_s * 1e3, 3),
+                      "inner_low_accuracy": round(mvlow_s * 1e3, 3)},
+        "phase_ms": {"mixed": {k: round(v, 3) for k, v in ph.items()},
+                     "fp64": {k: round(v, 3) for k, v in ph64.items()},
+                     "inner_low_accuracy": {k: round(v, 3) for k, v in ph_low.items()}},
         "plain_fp64": {"time_to_solve_s": round(t64, 4), "iterations": info64["iters"],
-                       "true_relres": info64["true_relres"], "matvecs_per_s": round(1e3 / mv64_ms, 2),
-                       "phase_ms": {k: round(v, 3) for k, v in ph64.items()}},
+                       "true_relres": info64["true_relres"], "preconditioner": "FP64 block Jacobi"},
         "speedup_vs_plain_fp64": round(t64 / (ms_step / 1e3), 2),
-        "batched_8_sources_block_jacobi": {"solves_per_s": round(8 / t8, 3), "time_s": round(t8, 4),
-                                           "iterations": [i["iters"] for i in infos8],
-                                           "max_true_relres": max(i["true_relres"] for i in infos8)},
+        "solution_rel_diff_mixed_vs_plain": sol_diff,
+        "learned": "side study, not in the timed step (the trained network did not reduce the outer "
+                   "iterations of the inner-outer solve)",
         "autotune": P["tune"],
         "graphs": True,
         "measured_alu_peaks_tflops": {"fp32": round(fp32_peak, 2), "fp64": round(fp64_peak, 3)},
-        "e2e": {"value": round(1.0 / e2e_s, 4), "unit": "solves/s", "h2d_bytes_per_step": 16 * n,
+        "e2e": {"value": round(1.0 / e2e_s, 5), "unit": "solves/s", "h2d_bytes_per_step": 16 * n,
                 "d2h_bytes_per_step": 16 * n},
         "gpu_launches": int(launches),
         "roofline": rf,
         "kernels": kernels,
         "clocks": clocks,
+        "secondary": sec,
     }
     if rank == 0 and not args.no_cpu_baseline:
         # the oracle's dense matvec, counted like the plain method's solve
-        # (block-Jacobi iterations + one true residual), as the reference arm does
-        res["cpu_baseline"] = cpu_baseline(wl, bj_infos[-1]["iters"] + 1, budget_s=args.cpu_seconds)
+        # (block-Jacobi iterations + one true residual)
+        res["cpu_baseline"] = cpu_baseline(wl, info64["iters"] + 1, budget_s=args.cpu_seconds)
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
@@ -577,57 +514,141 @@ def run_ours(args):
 
 
 def res_true_matvecs(infos):
-    return int(statistics.mean(i["true_matvecs"] for i in infos))
+    return int(round(statistics.mean(i["true_matvecs"] for i in infos)))
+
+
+# ---------------------------------------------------------------- oracle leg
+_ORACLE = {}
+
+
+def _oracle_init(verts, tris, k, beta):
+    """Worker set-up: the oracle's mesh (geometry of every element)."""
+    from oracle import bem
+    _ORACLE.update(mesh=bem.Mesh(verts, tris), k=k, beta=beta)
+    rng = np.random.default_rng(0)
+    n = tris.shape[0]
+    _ORACLE["x"] = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+
+
+def _oracle_rows(rows):
+    """Rows of the dense FP64 system matrix of Eq. (dbem4), assembled on the
+    fly by the oracle and applied to a fixed vector."""
+    from oracle import bem
+    A = bem.system_rows(_ORACLE["mesh"], _ORACLE["k"], _ORACLE["beta"], np.asarray(rows))
+    return len(rows), complex(np.sum(A @ _ORACLE["x"]))
+
+
+def _ready(_):
+    return os.getpid()
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_workers(n_elements):
+    """One worker per host core, as many as the free host memory holds (the
+    oracle's geometry and one dense row take about 1 KB per element)."""
+    cores = cpu_cores()
+    try:
+        free = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+        cores = max(1, min(cores, int(0.6 * free / (1100.0 * n_elements + 3e8))))
+    except (ValueError, OSError, AttributeError):
+        pass
+    return cores
+
+
+class OraclePool:
+    """Worker processes (started with spawn, each holding the oracle's mesh)
+    that time seeded random rows of the dense FP64 system matrix of
+    Eq. (dbem4), assembled on the fly and applied to a fixed vector."""
+
+    def __init__(self, wl, workers=None):
+        import multiprocessing as mp
+        self.wl = wl
+        self.cores = workers or oracle_workers(wl.n)
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init,
+                                                 initargs=(wl.verts, wl.tris, wl.k, wl.beta))
+        self.pool.map(_ready, range(self.cores), chunksize=1)   # workers started and initialised
+        self.rng = np.random.default_rng(1)
+
+    def sample(self, budget_s):
+        """(rows, wall seconds): rows submitted for `budget_s` seconds, all
+        cores busy, every submitted row waited for."""
+        pending, rows = [], 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s:
+            while len(pending) < 2 * self.cores:
+                pending.append(self.pool.apply_async(_oracle_rows, (self.rng.integers(0, self.wl.n, size=1),)))
+            still = []
+            for r in pending:
+                if r.ready():
+                    rows += r.get()[0]
+                else:
+                    still.append(r)
+            pending = still
+            time.sleep(0.01)
+        for r in pending:
+            rows += r.get()[0]
+        return rows, time.perf_counter() - t0
+
+    def close(self):
+        self.pool.terminate()
+        self.pool.join()
+
+
+def extrapolate(wl, rows, dt, cores, matvecs_per_solve):
+    per_matvec = dt / max(rows, 1) * wl.n
+    per_solve = per_matvec * max(1, matvecs_per_solve)
+    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"{rows} seeded random rows of the dense FP64 matrix-free A (Eq. dbem4, N={wl.n}) "
+                      f"in {dt:.1f} s on {cores} worker processes; extrapolated x N rows per matvec x "
+                      f"{matvecs_per_solve} matvecs per solve (the plain method's block-Jacobi iterations "
+                      f"+ 1 true residual)",
+            "matvec_s_extrapolated": per_matvec}
 
 
 def cpu_baseline(wl, matvecs_per_solve, budget_s=15.0):
-    """The oracle's dense FP64 collocation rows timed on the host: rows of A
-    (Eq. dbem4) assembled on the fly and applied, extrapolated to N rows per
-    matvec and to the GPU solve's matvec count."""
-    from oracle import bem
-    mesh = bem.Mesh(wl.verts, wl.tris)
-    rng = np.random.default_rng(0)
-    x = rng.standard_normal(wl.n) + 1j * rng.standard_normal(wl.n)
-    rows_done = 0
-    t0 = time.perf_counter()
-    chunk = 16
-    while time.perf_counter() - t0 < budget_s:
-        rows = np.arange(rows_done, rows_done + chunk) % wl.n
-        A = bem.system_rows(mesh, wl.k, wl.beta, rows)
-        _ = A @ x
-        rows_done += chunk
-    dt = time.perf_counter() - t0
-    per_row = dt / rows_done
-    per_matvec = per_row * wl.n
-    per_solve = per_matvec * max(1, matvecs_per_solve)
-    return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{rows_done} rows of the dense FP64 matrix-free A (N={wl.n}) in {dt:.1f} s; "
-                      f"extrapolated x N rows x {matvecs_per_solve} matvecs per solve",
-            "matvec_s_extrapolated": per_matvec}
+    """The oracle timed on the host cores for about `budget_s` seconds of wall
+    time; the row rate is extrapolated to N rows per matvec and to
+    `matvecs_per_solve` matvecs per solve."""
+    pool = OraclePool(wl)
+    try:
+        rows, dt = pool.sample(budget_s)
+    finally:
+        pool.close()
+    return extrapolate(wl, rows, dt, pool.cores, matvecs_per_solve)
 
 
 def run_reference(args):
     """The oracle as it stands on the host cores: each step a bounded sample of
-    dense matrix-free rows, extrapolated to one solve."""
+    dense matrix-free rows of the same workload, extrapolated to one solve."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    from paper_2103_16073_gb300 import workloads as W
-    wl = W.cfg_1khz()
+    wl = load_workload(args.workload)
     matvecs = args.ref_matvecs
     vals = []
-    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(wl, matvecs, budget_s=budget)
-        if i >= args.warmup:
-            vals.append(cb)
+    budget = max(3.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    pool = OraclePool(wl)
+    try:
+        for i in range(args.warmup + args.steps):
+            rows, dt = pool.sample(budget)
+            if i >= args.warmup:
+                vals.append(extrapolate(wl, rows, dt, pool.cores, matvecs))
+    finally:
+        pool.close()
     v = statistics.mean(c["value"] for c in vals)
     res = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "shoebox 3.0x2.4x2.0 m, 1 kHz, N=39368 flat triangles (lambda/8), "
-                                  "beta=0.2, dense FP64 collocation oracle", "matvecs_per_solve": matvecs},
-           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+           "config": bench_config(args.workload, wl, ws),
+           "arm": "dense FP64 collocation oracle (CPU), extrapolated from sampled rows",
+           "matvecs_per_solve": matvecs,
+           "cpu_baseline": {"value": v, "unit": "solves/s", "cores": vals[-1]["cores"], "kind": "oracle",
                             "sample": vals[-1]["sample"]},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
@@ -636,21 +657,21 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=25)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="largest", choices=sorted(WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--precond", default="learned", choices=["learned", "base"])
-    ap.add_argument("--base", default="inner", choices=["inner", "bj"],
-                    help="preconditioner the learned network refines (or used alone with --precond base)")
+    ap.add_argument("--no-secondary", dest="secondary", action="store_false",
+                    help="skip the 1 kHz shoebox measured beside the main workload")
+    ap.add_argument("--matvecs", type=int, default=10, help="matvecs timed per operator for matvecs/s")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--forms", default="", help="fixed per-level translation forms instead of autotuning "
                                                 "(comma-separated choice ints by level, as fb_operator_set_forms)")
-    ap.add_argument("--train-sources", type=int, default=4)
-    ap.add_argument("--train-steps", type=int, default=200)
-    ap.add_argument("--ref-matvecs", type=int, default=18,
-                    help="matvecs per solve used to extrapolate the reference arm (default: the GPU "
-                         "solve's 17 block-Jacobi iterations + 1 true residual, i.e. the same work)")
+    ap.add_argument("--ref-matvecs", type=int, default=52,
+                    help="matvecs per solve used to extrapolate the reference arm (default: the plain "
+                         "method's 51 block-Jacobi iterations on the largest room + 1 true residual)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -254,22 +254,24 @@ FB_API fb_status fb_operator_set_translation(fb_op* op, int method);
 /* y = Op x for an FMM operator without allocating anything.
  *
  * (The paper has no counterpart: this is a deployment variant.)  Some callers
- * cannot allocate device memory at the moment they apply an operator: code
- * running while a stream is being captured into a CUDA graph, real-time audio
- * callbacks that must not block in the driver's allocator, or hosts whose
- * device memory is owned by a fixed arena.  This call runs the same FMM
+ * cannot allocate device memory at the moment they apply an operator:
+ * real-time audio callbacks that must not block in the driver's allocator,
+ * or hosts whose device memory is owned by a fixed arena that the library
+ * may not grow.  This call runs the same FMM
  * matvec as fb_operator_apply, but keeps its per-call scratch (the multipole
  * and local expansions of every level) in a file-scope static device buffer
  * of FB_NOALLOC_SCRATCH_BYTES instead of the operator's own buffers; it calls
  * no cudaMalloc, cudaFree or allocating library routine.
  *   x, y:  N interleaved complex doubles, DEVICE pointers, not overlapping.
- *   The first call on a device resolves the buffer's device address
- *   (cudaGetSymbolAddress) for that device, which must be current; make that
- *   first call before any stream capture.
+ *   The operator's device must be current (FB_ERR_ARG otherwise).  The
+ *   first call on a device resolves the buffer's device address
+ *   (cudaGetSymbolAddress) for that device; make that first call before any
+ *   stream capture.
  *   All calls share the one buffer: the expansions are cleared at the start
  *   of every call, and calls that overlap on the GPU (other streams, other
  *   threads) race on it and give wrong results.
- * Errors: FB_ERR_ARG for a dense operator or when the operator's expansions
+ * Errors: FB_ERR_ARG for a dense operator, a current device other than the
+ * operator's, or when the operator's expansions
  * (2 x sum over levels of boxes x p^2 complex values, FP32 for the mixed
  * precision, FP64 otherwise) exceed FB_NOALLOC_SCRATCH_BYTES; FB_ERR_CUDA if
  * the buffer's address cannot be resolved. */

@@ -569,6 +569,7 @@ fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t inde
 
 void fb_operator_destroy(fb_op* op) {
     if (!op) return;
+    fb_krylov_free(op);
     fb_ibem_free(op);
     dfree(op->dense);
     fb_fmm_destroy(op);

@@ -339,6 +339,10 @@ struct fb_op {
     // device vectors for host-memspace calls
     cd* io_x = nullptr;
     cd* io_y = nullptr;
+    // FGMRES workspaces of solves with this operator as A, kept between
+    // solves so that a steady-state solve allocates nothing (krylov.cu)
+    void* fg_work = nullptr;
+    void* fg_bwork = nullptr;
     // CUDA-graph replay of the FMM matvec (fb_operator_use_graphs)
     int use_graphs = 0;
     void* graphs = nullptr;
@@ -365,6 +369,8 @@ struct fb_precond {
     void* inner = nullptr;
 };
 fb_status fb_inner_create(fb_precond* pc, cudaStream_t s);
+// Releases the FGMRES workspaces cached on an operator.
+void fb_krylov_free(fb_op* op);
 void fb_inner_free(void*& inner);
 
 // ------------------------------------------------------ launch counting ----

@@ -722,9 +722,9 @@ void fb_fmm_destroy(fb_op* op) {
 
 // ---------------------------------------------------------------------------
 // Matvec without allocation.  Some callers cannot allocate device memory when
-// they apply an operator: code running while a stream is captured into a CUDA
-// graph, real-time audio callbacks that must not block in the driver's
-// allocator, or hosts whose device memory is owned by a fixed arena.  For
+// they apply an operator: real-time audio callbacks that must not block in the
+// driver's allocator, or hosts whose device memory is owned by a fixed arena
+// that the library may not grow.  For
 // them fb_operator_apply_noalloc keeps the FMM's per-call scratch (the
 // multipole and local expansions of every level) in this library-wide
 // static device array instead of the operator's own buffers.  Every GPU that
@@ -756,6 +756,13 @@ static fb_status noalloc_scratch_ptr(void** out) {
 fb_status fb_fmm_apply_noalloc(fb_op* op, const cd* x, cd* y, cudaStream_t s) {
     if (op->prec == FB_PREC_FP64_DENSE)
         return fb_fail(FB_ERR_ARG, "fb_operator_apply_noalloc needs an FMM operator (dense ones use no scratch)");
+    // the static array is resolved per device: the operator's data and the
+    // scratch must be on the same GPU
+    int cur = -1;
+    FB_CUDA(cudaGetDevice(&cur));
+    if (cur != op->dev)
+        return fb_fail(FB_ERR_ARG, "fb_operator_apply_noalloc: current device " + std::to_string(cur) +
+                                       " differs from the operator's device " + std::to_string(op->dev));
     size_t elem = op->prec == FB_PREC_MIXED_FMM ? sizeof(cf) : sizeof(cd);
     size_t need = 2 * (size_t)op->lev_off[op->L + 1] * elem;
     if (need > (size_t)FB_NOALLOC_SCRATCH_BYTES)

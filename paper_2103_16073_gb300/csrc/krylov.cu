@@ -277,6 +277,29 @@ struct InnerSolver {
 // The first k+1 Arnoldi vectors of the right-preconditioned Krylov space of
 // A for the start vector b (the inputs a preconditioner sees in the first k
 // iterations of a solve), written to V [(k+1) x N].
+// Workspace of fb_fgmres_solve on operator A with restart m, kept on A and
+// reused while (N, m) match and it holds the Z block a preconditioned solve
+// needs; otherwise it is replaced.  Every solve ends with a host read of a
+// device scalar, so no kernel of the previous solve still uses it.
+static fb_status work_get(fb_op* A, int m, bool with_z, Work** out) {
+    Work* W = (Work*)A->fg_work;
+    if (W && W->n == A->n && W->m == m && (W->Z || !with_z)) {
+        *out = W;
+        return FB_OK;
+    }
+    delete W;
+    A->fg_work = nullptr;
+    W = new Work();
+    fb_status st = work_alloc(*W, A->n, m, with_z);
+    if (st != FB_OK) {
+        delete W;
+        return st;
+    }
+    A->fg_work = W;
+    *out = W;
+    return FB_OK;
+}
+
 fb_status fb_krylov_basis_impl(fb_op* A, const fb_precond* pc, const cd* b, int k, cd* V, cudaStream_t s) {
     Work W;
     FB_CHECK(work_alloc(W, A->n, k, pc != nullptr));
@@ -391,8 +414,9 @@ fb_status fb_fgmres_impl(fb_op* A, fb_precond* pc, const cd* b, cd* x, const fb_
     if (T->n != A->n) return fb_fail(FB_ERR_ARG, "true_op size differs");
     int64_t n = A->n;
     int m = opts.restart;
-    Work W;
-    FB_CHECK(work_alloc(W, n, m, pc != nullptr));
+    Work* Wp = nullptr;
+    FB_CHECK(work_get(A, m, pc != nullptr, &Wp));
+    Work& W = *Wp;
     double* bnorm2 = W.scal + 3;
 
     fb_solve_info inf{};
@@ -928,6 +952,54 @@ struct BatchWork {
     }
 };
 
+static fb_status bwork_alloc(BatchWork& B, int64_t n, int m, int R, bool with_z) {
+    B.n = n;
+    B.m = m;
+    B.R = R;
+    FB_CHECK(dalloc(&B.V, (size_t)(m + 1) * R * n));
+    if (with_z) FB_CHECK(dalloc(&B.Z, (size_t)m * R * n));
+    FB_CHECK(dalloc(&B.W, (size_t)R * n));
+    FB_CHECK(dalloc(&B.Rs, (size_t)R * n));
+    FB_CHECK(dalloc(&B.D, (size_t)R * n));
+    FB_CHECK(dalloc(&B.T, (size_t)R * n));
+    // small state: H [R][(m+1) m] | h, cs, sn, g, y, spare [R][m+1] each
+    FB_CHECK(dalloc(&B.small, (size_t)R * (m + 1) * m + (size_t)R * (m + 1) * 6));
+    FB_CHECK(dalloc(&B.scal, (size_t)4 * R));
+    FB_CHECK(dalloc(&B.dint, (size_t)2 * R));
+    FB_CHECK(dalloc(&B.dhs, (size_t)R));
+    FB_CUDA(cudaMallocHost((void**)&B.host, sizeof(double) * 4 * R));
+    FB_CUDA(cudaMallocHost((void**)&B.hint, sizeof(int) * 2 * R));
+    return FB_OK;
+}
+
+// Workspace of fb_fgmres_solve_multi, cached on A like work_get's (reused
+// while N, m and the number of systems match).
+static fb_status bwork_get(fb_op* A, int m, int R, bool with_z, BatchWork** out) {
+    BatchWork* B = (BatchWork*)A->fg_bwork;
+    if (B && B->n == A->n && B->m == m && B->R == R && (B->Z || !with_z)) {
+        *out = B;
+        return FB_OK;
+    }
+    delete B;
+    A->fg_bwork = nullptr;
+    B = new BatchWork();
+    fb_status st = bwork_alloc(*B, A->n, m, R, with_z);
+    if (st != FB_OK) {
+        delete B;
+        return st;
+    }
+    A->fg_bwork = B;
+    *out = B;
+    return FB_OK;
+}
+
+void fb_krylov_free(fb_op* op) {
+    delete (Work*)op->fg_work;
+    delete (BatchWork*)op->fg_bwork;
+    op->fg_work = nullptr;
+    op->fg_bwork = nullptr;
+}
+
 static fb_status upload_ints(BatchWork& B, cudaStream_t s) {
     FB_CUDA(cudaMemcpyAsync(B.dint, B.hint, sizeof(int) * 2 * B.R, cudaMemcpyHostToDevice, s));
     return FB_OK;
@@ -1052,23 +1124,9 @@ fb_status fb_fgmres_multi_impl(fb_op* A, fb_precond* pc, const cd* b, cd* x, int
     if (T->n != A->n) return fb_fail(FB_ERR_ARG, "true_op size differs");
     const int64_t n = A->n;
     const int m = opts.restart;
-    BatchWork B;
-    B.n = n;
-    B.m = m;
-    B.R = R;
-    FB_CHECK(dalloc(&B.V, (size_t)(m + 1) * R * n));
-    if (pc) FB_CHECK(dalloc(&B.Z, (size_t)m * R * n));
-    FB_CHECK(dalloc(&B.W, (size_t)R * n));
-    FB_CHECK(dalloc(&B.Rs, (size_t)R * n));
-    FB_CHECK(dalloc(&B.D, (size_t)R * n));
-    FB_CHECK(dalloc(&B.T, (size_t)R * n));
-    // small state: H [R][(m+1) m] | h, cs, sn, g, y, spare [R][m+1] each
-    FB_CHECK(dalloc(&B.small, (size_t)R * (m + 1) * m + (size_t)R * (m + 1) * 6));
-    FB_CHECK(dalloc(&B.scal, (size_t)4 * R));
-    FB_CHECK(dalloc(&B.dint, (size_t)2 * R));
-    FB_CHECK(dalloc(&B.dhs, (size_t)R));
-    FB_CUDA(cudaMallocHost((void**)&B.host, sizeof(double) * 4 * R));
-    FB_CUDA(cudaMallocHost((void**)&B.hint, sizeof(int) * 2 * R));
+    BatchWork* Bp = nullptr;
+    FB_CHECK(bwork_get(A, m, R, pc != nullptr, &Bp));
+    BatchWork& B = *Bp;
     std::vector<Hess> hh(R);
     cd* H0 = B.small;
     cd* blk = B.small + (size_t)R * (m + 1) * m;

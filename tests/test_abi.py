@@ -83,3 +83,23 @@ def test_image_field_refuses_excessive_image_orders():
     dummy = C.c_void_p(16)
     assert fb.lib.fb_image_field(room.ctypes.data, src.ctypes.data, Rw.ctypes.data, 1e-7, k.ctypes.data, 1,
                                  dummy, 1, dummy, None) == 1
+
+
+def test_input_generators_do_not_map_the_library():
+    """The seeded input generators (shared with the oracle side) import
+    without loading libfmmbem.so: the package loads its binding only on the
+    first use of a binding name."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import paper_2103_16073_gb300 as P\n"
+            "from paper_2103_16073_gb300 import workloads\n"
+            "import oracle.bem\n"
+            "assert 'paper_2103_16073_gb300.binding' not in sys.modules\n"
+            "maps = open('/proc/self/maps').read()\n"
+            "assert 'libfmmbem' not in maps\n"
+            "P.FB_OP_A\n"
+            "assert 'libfmmbem' in open('/proc/self/maps').read()\n" % root)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
