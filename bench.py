@@ -169,7 +169,7 @@ def bench_config(name, wl, ws):
             "parallelism": f"replicas x{ws} (one (f, source) solve per GPU)"}
 
 
-def build_problem(fb, W, torch, wl, rank, forms=""):
+def build_problem(fb, W, torch, wl, rank, forms="", forms_inner=""):
     """Mesh, tree and the operators of a solve: mixed A (autotuned translation
     forms, graph replay), FP64 A (true residual, plain method), FP64 L
     (b = L gamma), block Jacobi of each, and the inner-outer preconditioner
@@ -191,14 +191,19 @@ def build_problem(fb, W, torch, wl, rank, forms=""):
         fb.fb_operator_set_forms(A32, [int(v) for v in forms.split(",")])
         tune = {"fixed_forms": forms}
     else:
-        tune = fb.fb_operator_autotune(A32, 1)
+        tune = {"mixed": fb.fb_operator_autotune(A32, 1)}
+    if forms:
+        fb.fb_operator_set_forms(A64, [int(v) & 12 for v in forms.split(",")])
+    else:
+        tune["fp64"] = fb.fb_operator_autotune(A64, 1)
     for op in (A32, A64):
         fb.fb_operator_use_graphs(op, True)
     Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, INNER_D0, INNER_PMIN)
-    if forms:
-        fb.fb_operator_set_forms(Alow, [0] * 13)
+    if forms_inner:
+        fb.fb_operator_set_forms(Alow, [int(v) for v in forms_inner.split(",")])
+        tune["inner_fixed_forms"] = forms_inner
     else:
-        fb.fb_operator_autotune(Alow, 1)
+        tune["inner"] = fb.fb_operator_autotune(Alow, 1)
     fb.fb_operator_use_graphs(Alow, True)
     pclow = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
     inner = fb.fb_precond_create_inner(A32, Alow, pclow, INNER_ITERS)
@@ -376,7 +381,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
     wl = load_workload(args.workload)
-    P = build_problem(fb, W, torch, wl, rank, args.forms)
+    P = build_problem(fb, W, torch, wl, rank, args.forms, args.forms_inner)
     n = wl.n
     stream = torch.cuda.current_stream()
     pc_main = P["inner"]
@@ -667,8 +672,10 @@ def main():
                     help="skip the 1 kHz shoebox measured beside the main workload")
     ap.add_argument("--matvecs", type=int, default=10, help="matvecs timed per operator for matvecs/s")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--forms", default="", help="fixed per-level translation forms instead of autotuning "
-                                                "(comma-separated choice ints by level, as fb_operator_set_forms)")
+    ap.add_argument("--forms", default="", help="fixed per-level translation forms of the mixed and FP64 "
+                                                "operators instead of autotuning (comma-separated choice ints "
+                                                "by level, as fb_operator_set_forms; the FP64 one takes bits 2-3)")
+    ap.add_argument("--forms-inner", default="", help="the same for the low-accuracy inner operator")
     ap.add_argument("--ref-matvecs", type=int, default=52,
                     help="matvecs per solve used to extrapolate the reference arm (default: the plain "
                          "method's 51 block-Jacobi iterations on the largest room + 1 true residual)")

@@ -302,22 +302,31 @@ FB_API fb_status fb_precond_use_graphs(fb_precond* pc, int enable);
  * to nrhs sets on first use.  Errors: FB_ERR_ARG. */
 #define FB_MAX_RHS 64
 
-/* Autotuner of the translation passes of a mixed-precision FMM operator: for
- * every level it times on the device (median of 3, nrhs right-hand sides)
- * the per-pair rotation-coaxial-rotation kernel (Sec. 3.3) against the
- * stacked tensor-core GEMM of composed matrices, for M2L and for the
- * M2M/L2L passes into the level, and installs the faster form per level
- * (translation method FB_TRANS_AUTO).  times: 4*13 doubles or NULL,
- * times[4l + 0..3] = M2L RCR, M2L tensor, M2M+L2L RCR, M2M+L2L tensor in ms
- * (-1: not a candidate); choice: 13 ints or NULL, bit 0 = M2L of level l on
- * the tensor cores, bit 1 = M2M/L2L into level l on the tensor cores.
- * FP64 operators (RCR only) are left unchanged.  Errors: FB_ERR_ARG. */
+/* Autotuner of the translation passes of an FMM operator: for every level
+ * it times on the device (median of 3, nrhs right-hand sides) the forms a
+ * pass can take and installs the fastest per level (translation method
+ * FB_TRANS_AUTO), for M2L and for the M2M/L2L passes into the level:
+ *   - rotation-coaxial-rotation (Sec. 3.3) as per-pair tiles (orders whose
+ *     per-pair working set fits one CTA's shared memory),
+ *   - rotation-coaxial-rotation as staged batched GEMMs (the pairs of a
+ *     level grouped by the polar angle of their translation direction for
+ *     the rotations and by |t| for the coaxial step),
+ *   - mixed precision only: the stacked tensor-core GEMM of composed
+ *     matrices (3xTF32).
+ * times: 6*13 doubles or NULL, times[6l + 0..5] = M2L RCR tiles, M2L tensor,
+ * M2M+L2L RCR tiles, M2M+L2L tensor, M2L RCR staged, M2M+L2L RCR staged in
+ * ms (-1: not a candidate); choice: 13 ints or NULL, bit 0 = M2L of level l
+ * on the tensor cores, bit 1 = M2M/L2L into level l on the tensor cores,
+ * bit 2 = M2L of level l by staged RCR, bit 3 = M2M/L2L into level l by
+ * staged RCR.  Rebuilds the operator's translation plans (synchronises the
+ * device).  Errors: FB_ERR_ARG. */
 FB_API fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times, int* choice);
 
 /* Installs a per-level choice in the format the autotuner returns (13 ints,
- * bit 0: M2L of level l on the tensor cores, bit 1: M2M/L2L into level l on
- * the tensor cores), so that a tuned configuration can be saved and restored
- * without timing.  Mixed-precision FMM operators only.  Errors: FB_ERR_ARG. */
+ * bits as above), so that a tuned configuration can be saved and restored
+ * without timing.  Levels whose per-pair RCR working set does not fit one
+ * CTA run staged whatever bit 2/3 says.  Tensor-core bits need a
+ * mixed-precision operator.  Errors: FB_ERR_ARG. */
 FB_API fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream);
 FB_API fb_status fb_operator_apply_multi(fb_op* op, const double* x, double* y, int nrhs, int memspace,
                                          void* stream);

@@ -398,21 +398,26 @@ lib.fb_operator_autotune.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p
 
 
 def fb_operator_autotune(op, nrhs=1, stream=None):
-    """Times RCR vs tensor-core translations per level and installs the faster
-    form; returns {level: {"m2l_rcr", "m2l_tensor", "m2m_l2l_rcr",
-    "m2m_l2l_tensor" (ms, None if not a candidate), "m2l_on_tensor",
-    "m2m_l2l_on_tensor"}}."""
-    times = np.full(4 * 13, -1.0)
+    """Times the translation forms per level (RCR as per-pair tiles, RCR as
+    staged GEMM passes, tensor-core composed GEMMs for mixed operators) and
+    installs the fastest; returns {level: {"m2l_rcr", "m2l_tensor",
+    "m2m_l2l_rcr", "m2m_l2l_tensor", "m2l_staged", "m2m_l2l_staged" (ms, None
+    if not a candidate), "m2l_on_tensor", "m2m_l2l_on_tensor", "m2l_staged_on",
+    "m2m_l2l_staged_on", "choice"}}."""
+    times = np.full(6 * 13, -1.0)
     choice = np.zeros(13, np.int32)
     _check(lib.fb_operator_autotune(op, int(nrhs), _stream(stream), times.ctypes.data, choice.ctypes.data))
     out = {}
     for l in range(13):
-        t = times[4 * l:4 * l + 4]
+        t = times[6 * l:6 * l + 6]
         if np.all(t < 0):
             continue
         f = lambda v: None if v < 0 else round(float(v), 4)
         out[l] = {"m2l_rcr": f(t[0]), "m2l_tensor": f(t[1]), "m2m_l2l_rcr": f(t[2]), "m2m_l2l_tensor": f(t[3]),
-                  "m2l_on_tensor": bool(choice[l] & 1), "m2m_l2l_on_tensor": bool(choice[l] & 2)}
+                  "m2l_staged": f(t[4]), "m2m_l2l_staged": f(t[5]),
+                  "m2l_on_tensor": bool(choice[l] & 1), "m2m_l2l_on_tensor": bool(choice[l] & 2),
+                  "m2l_staged_on": bool(choice[l] & 4), "m2m_l2l_staged_on": bool(choice[l] & 8),
+                  "choice": int(choice[l])}
     return out
 
 

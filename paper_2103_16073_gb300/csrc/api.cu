@@ -462,7 +462,7 @@ fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times,
     if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "dense operators have no translations");
     if (nrhs < 1 || nrhs > FB_MAX_RHS) return fb_fail(FB_ERR_ARG, "nrhs must be in [1, FB_MAX_RHS]");
     if (times)
-        for (int i = 0; i < 4 * (FB_MAXLEV + 1); ++i) times[i] = -1.0;
+        for (int i = 0; i < 6 * (FB_MAXLEV + 1); ++i) times[i] = -1.0;
     if (choice)
         for (int i = 0; i <= FB_MAXLEV; ++i) choice[i] = 0;
     if (fb_is_composite(op)) {   // each constituent operator; times/choice of the first

@@ -1,13 +1,17 @@
-// Autotuner of the translation passes (mixed precision).  For every level it
-// times (median of 3), on the device and for a given number of right-hand
-// sides, the per-pair rotation-coaxial-rotation kernel (RCR) against the
-// stacked tensor-core GEMM of composed matrices (3xTF32), for M2L and for the
-// M2M / L2L passes into that level, and keeps the faster form.  The
-// tensor-core candidate of an M2L level is skipped when its order exceeds
-// 20, when it has fewer than 16 box pairs per translation vector on average,
-// or when its composed matrices would exceed a memory cap.  The result
-// replaces the operator's rule-based choice (>= 48 pairs per translation
-// vector); FP64 operators have only the RCR form and are left unchanged.
+// Autotuner of the translation passes.  For every level it times (median of
+// 3), on the device and for a given number of right-hand sides, the forms a
+// translation pass can take and keeps the fastest:
+//   * rotation - coaxial - rotation (RCR, Sec. 3.3) as per-pair tiles
+//     (where a pair's working set fits a CTA's shared memory),
+//   * RCR as staged batched GEMM passes (pairs grouped by polar angle and by
+//     |t|; rcr_staged.cu),
+//   * mixed precision only: the stacked tensor-core GEMM of composed
+//     matrices (3xTF32),
+// for M2L and for the M2M / L2L passes into that level.  The tensor-core
+// candidate of an M2L level is skipped when its order exceeds 20, when it
+// has fewer than 16 box pairs per translation vector on average, or when
+// its composed matrices would exceed a memory cap.  The result replaces the
+// operator's rule-based choice.
 #include <algorithm>
 #include <vector>
 
@@ -51,19 +55,43 @@ void free_rcr(RcrPlan& p) { fb_rcr_free(p); }
 
 }  // namespace
 
-// times[4 * l + {0,1,2,3}] = M2L RCR, M2L tensor, M2M+L2L RCR, M2M+L2L tensor
-// (ms, -1 when not a candidate) for l = 0..L; choice[l] bit 0 = M2L on the
-// tensor cores, bit 1 = M2M/L2L into level l on the tensor cores.
 fb_status fb_install_forms(fb_op* op, const std::vector<int>& tc_m2l, cudaStream_t s);
 
+// Times the tasks of `base` that `pick` selects, with their RCR form set to
+// `staged`, as a temporary plan on the expansion buffers (-1: no task).
+template <class Pick>
+fb_status time_rcr(fb_op* op, const RcrPlan& base, Pick pick, int staged, void* src, void* dst, cudaStream_t s,
+                   int nrhs, int64_t cnt, int reps, double* ms) {
+    *ms = -1.0;
+    RcrPlan pl;
+    for (const RcrTask& tk : base.h_tasks)
+        if (pick(tk)) {
+            RcrTask t2 = tk;
+            t2.staged = staged;
+            pl.h_tasks.push_back(t2);
+        }
+    if (pl.h_tasks.empty()) return FB_OK;
+    const size_t csz = op->prec == FB_PREC_MIXED_FMM ? sizeof(cf) : sizeof(cd);
+    fb_status st = fb_rcr_upload(op, pl, base.src_idx, base.dst_idx, csz);
+    if (st == FB_OK) st = time_ms([&]() { return fb_rcr_run_op(op, pl, src, dst, s, nrhs, cnt); }, s, reps, ms);
+    cudaStreamSynchronize(s);
+    free_rcr(pl);
+    return st;
+}
+
+// times[6 * l + {0..5}] = M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles,
+// M2M+L2L tensor, M2L RCR staged, M2M+L2L RCR staged (ms, -1 when not a
+// candidate) for l = 0..L; choice[l] bit 0 = M2L on the tensor cores, bit 1 =
+// M2M/L2L into level l on the tensor cores, bit 2 = M2L by staged RCR, bit 3
+// = M2M/L2L into level l by staged RCR.
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_out, int* choice) {
-    if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;
-    double times_local[4 * (FB_MAXLEV + 1)];
+    const bool mixed = op->prec == FB_PREC_MIXED_FMM;
+    double times_local[6 * (FB_MAXLEV + 1)];
     double* times = times_out ? times_out : times_local;   // callers may pass NULL
     const fb_tree* t = op->tree;
     const int L = op->L;
     const int64_t cnt = op->lev_off[L + 1];
-    const size_t csz = sizeof(cf);
+    const size_t csz = mixed ? sizeof(cf) : sizeof(cd);
     const int reps = 3;
     const double cap_bytes = 8.0e9;   // composed FP64 + packed TF32 tiles of one level
     // expansion buffers for nrhs sets (contents do not matter for timing)
@@ -72,29 +100,33 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
         dfree(op->mp);
         dfree(op->loc);
         op->mp = op->loc = nullptr;
-        FB_CHECK(dalloc((cf**)&op->mp, cnt * nrhs));
-        FB_CHECK(dalloc((cf**)&op->loc, cnt * nrhs));
+        FB_CHECK(dalloc((unsigned char**)&op->mp, (size_t)cnt * nrhs * csz));
+        FB_CHECK(dalloc((unsigned char**)&op->loc, (size_t)cnt * nrhs * csz));
         op->exp_nrhs = nrhs;
         op->buf_gen++;
     }
-    cf* mp = (cf*)op->mp;
-    cf* loc = (cf*)op->loc;
-    FB_CUDA(cudaMemsetAsync(mp, 0, sizeof(cf) * cnt * nrhs, s));
-    FB_CUDA(cudaMemsetAsync(loc, 0, sizeof(cf) * cnt * nrhs, s));
+    void* mp = op->mp;
+    void* loc = op->loc;
+    FB_CUDA(cudaMemsetAsync(mp, 0, csz * cnt * nrhs, s));
+    FB_CUDA(cudaMemsetAsync(loc, 0, csz * cnt * nrhs, s));
     std::vector<int> tc_m2l;
+    int stg_m2l[FB_MAXLEV + 1] = {0}, stg_pair[FB_MAXLEV + 1] = {0};
     for (int l = 2; l <= L; ++l) {
-        double* tl = times + 4 * l;
-        tl[0] = tl[1] = tl[2] = tl[3] = -1.0;
+        double* tl = times + 6 * l;
+        for (int q = 0; q < 6; ++q) tl[q] = -1.0;
         int ch = 0;
-        // ---- M2L of level l
-        RcrPlan pl;
-        for (const RcrTask& tk : op->m2l_rcr.h_tasks)
-            if (tk.src_base == op->lev_off[l]) pl.h_tasks.push_back(tk);
-        if (!pl.h_tasks.empty()) {
-            FB_CHECK(fb_rcr_upload(pl, t->m2l_src, t->m2l_dst, csz));
-            fb_status st = time_ms([&]() { return fb_rcr_run_op(op, pl, mp, loc, s, nrhs, cnt); }, s, reps, &tl[0]);
-            free_rcr(pl);
-            FB_CHECK(st);
+        // ---- M2L of level l: RCR tiles, RCR staged, tensor cores
+        auto at_level = [&](const RcrTask& tk) { return tk.src_base == op->lev_off[l] && tk.dst_base == tk.src_base; };
+        if (fb_rcr_tile_fits(op->p[l], op->p[l], csz))
+            FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 0, mp, loc, s, nrhs, cnt, reps, &tl[0]));
+        FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 1, mp, loc, s, nrhs, cnt, reps, &tl[4]));
+        double best = -1.0;
+        if (tl[0] >= 0) best = tl[0];
+        if (tl[4] >= 0 && (best < 0 || tl[4] < best)) {
+            best = tl[4];
+            stg_m2l[l] = 1;
+        }
+        if (mixed && best >= 0) {
             int64_t p2 = (int64_t)op->p[l] * op->p[l];
             double bytes = 0;
             int64_t groups = 0, pairs = 0;
@@ -117,22 +149,42 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                 void* plan = nullptr;
                 fb_status st2 = fb_tc_build(op, {l}, &plan, s);
                 if (st2 == FB_OK)
-                    st2 = time_ms([&]() { return fb_tc_run(op, plan, mp, loc, s, nrhs, cnt); }, s, reps, &tl[1]);
+                    st2 = time_ms([&]() { return fb_tc_run(op, plan, (const cf*)mp, (cf*)loc, s, nrhs, cnt); }, s,
+                                  reps, &tl[1]);
                 cudaStreamSynchronize(s);
                 fb_tc_free(plan);
                 FB_CHECK(st2);
-                if (tl[1] < tl[0]) {
+                if (tl[1] < best) {
                     ch |= 1;
                     tc_m2l.push_back(l);
                 }
             }
         }
+        if (stg_m2l[l] && !(ch & 1)) ch |= 4;
         // ---- M2M + L2L between levels l-1 and l
         if (l >= 3) {
-            double r_ms = 0, r2 = 0;
-            FB_CHECK(time_ms([&]() { return fb_rcr_run_op(op, op->m2m_rcr[l], mp, mp, s, nrhs, cnt); }, s, reps, &r_ms));
-            FB_CHECK(time_ms([&]() { return fb_rcr_run_op(op, op->l2l_rcr[l], loc, loc, s, nrhs, cnt); }, s, reps, &r2));
-            tl[2] = r_ms + r2;
+            const int pm = std::max(op->p[l], op->p[l - 1]);
+            auto all = [](const RcrTask&) { return true; };
+            double rt = -1.0, rs = -1.0;
+            if (fb_rcr_tile_fits(pm, pm, csz)) {
+                double a = 0, b = 0;
+                FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 0, mp, mp, s, nrhs, cnt, reps, &a));
+                FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 0, loc, loc, s, nrhs, cnt, reps, &b));
+                rt = std::max(a, 0.0) + std::max(b, 0.0);
+            }
+            {
+                double a = 0, b = 0;
+                FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 1, mp, mp, s, nrhs, cnt, reps, &a));
+                FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 1, loc, loc, s, nrhs, cnt, reps, &b));
+                rs = std::max(a, 0.0) + std::max(b, 0.0);
+            }
+            tl[2] = rt;
+            tl[5] = rs;
+            double best2 = rt;
+            if (rt < 0 || rs < rt) {
+                best2 = rs;
+                stg_pair[l] = 1;
+            }
             std::vector<int> need;
             std::vector<TcGroup> up, down;
             for (int o = 0; o < 8; ++o) {
@@ -143,17 +195,19 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                 up.push_back(TcGroup{op->m2m_job[l][o], g0, (int32_t)(g1 - g0), l, l - 1});
                 down.push_back(TcGroup{op->l2l_job[l][o], g0, (int32_t)(g1 - g0), l - 1, l});
             }
-            if (!up.empty() && fb_composable(op, l, true)) {
+            if (mixed && !up.empty() && fb_composable(op, l, true)) {
                 FB_CHECK(fb_compose_jobs(op, need, s));
                 if (!op->tc_m2m[l])
                     FB_CHECK(fb_tc_build_groups(op, up, t->oct_child[l], t->oct_parent[l], &op->tc_m2m[l], s));
                 if (!op->tc_l2l[l])
                     FB_CHECK(fb_tc_build_groups(op, down, t->oct_parent[l], t->oct_child[l], &op->tc_l2l[l], s));
                 double a = 0, b = 0;
-                FB_CHECK(time_ms([&]() { return fb_tc_run(op, op->tc_m2m[l], mp, mp, s, nrhs, cnt); }, s, reps, &a));
-                FB_CHECK(time_ms([&]() { return fb_tc_run(op, op->tc_l2l[l], loc, loc, s, nrhs, cnt); }, s, reps, &b));
+                FB_CHECK(time_ms([&]() { return fb_tc_run(op, op->tc_m2m[l], (const cf*)mp, (cf*)mp, s, nrhs, cnt); },
+                                 s, reps, &a));
+                FB_CHECK(time_ms([&]() { return fb_tc_run(op, op->tc_l2l[l], (const cf*)loc, (cf*)loc, s, nrhs, cnt); },
+                                 s, reps, &b));
                 tl[3] = a + b;
-                if (tl[3] < tl[2]) {
+                if (tl[3] < best2) {
                     ch |= 2;
                 } else {
                     cudaStreamSynchronize(s);
@@ -161,10 +215,13 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                     fb_tc_free(op->tc_l2l[l]);
                 }
             }
+            if (stg_pair[l] && !(ch & 2)) ch |= 8;
         }
         if (choice) choice[l] = ch;
     }
     FB_CUDA(cudaStreamSynchronize(s));
+    FB_CHECK(fb_rcr_restage(op, stg_m2l, stg_pair));
+    if (!mixed) return FB_OK;
     return fb_install_forms(op, tc_m2l, s);
 }
 
@@ -192,7 +249,7 @@ fb_status fb_install_forms(fb_op* op, const std::vector<int>& tc_m2l, cudaStream
         for (int l : tc_m2l) tc = tc || tk.src_base == op->lev_off[l];
         if (!tc) op->m2l_rcr_rest.h_tasks.push_back(tk);
     }
-    FB_CHECK(fb_rcr_upload(op->m2l_rcr_rest, t->m2l_src, t->m2l_dst, csz));
+    FB_CHECK(fb_rcr_upload(op, op->m2l_rcr_rest, t->m2l_src, t->m2l_dst, csz));
     if (!tc_m2l.empty()) FB_CHECK(fb_tc_build(op, tc_m2l, &op->tc_plan, s));
     FB_CUDA(cudaStreamSynchronize(s));
     op->method = FB_TRANS_AUTO;
@@ -203,9 +260,17 @@ fb_status fb_install_forms(fb_op* op, const std::vector<int>& tc_m2l, cudaStream
 // bit 0 = M2L of level l on the tensor cores, bit 1 = M2M/L2L into level l on
 // the tensor cores; lets a tuned configuration be saved and restored.
 fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s) {
-    if (op->prec != FB_PREC_MIXED_FMM) return fb_fail(FB_ERR_ARG, "translation forms apply to mixed operators");
     const fb_tree* t = op->tree;
     const int L = op->L;
+    int stg_m2l[FB_MAXLEV + 1] = {0}, stg_pair[FB_MAXLEV + 1] = {0};
+    for (int l = 2; l <= L; ++l) {
+        if (op->prec != FB_PREC_MIXED_FMM && (choice[l] & 3))
+            return fb_fail(FB_ERR_ARG, "tensor-core forms apply to mixed operators");
+        stg_m2l[l] = (choice[l] & 4) ? 1 : 0;
+        stg_pair[l] = (choice[l] & 8) ? 1 : 0;
+    }
+    FB_CHECK(fb_rcr_restage(op, stg_m2l, stg_pair));
+    if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;
     std::vector<int> tc_m2l;
     for (int l = 2; l <= L; ++l) {
         if ((choice[l] & 1) && !fb_composable(op, l, false))

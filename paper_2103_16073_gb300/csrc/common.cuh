@@ -218,41 +218,52 @@ struct RcrTask {
     int64_t pair_off;
     int32_t npairs, p_out, p_in, pc;
     int64_t src_base, dst_base;
+    int32_t staged;      // 1: run by the staged GEMM passes, 0: per-pair tiles
+    int32_t pad;
 };
 struct RcrTile {
     int32_t task, col0, nb, pad;
 };
 // Tiles of an RCR plan for a number of right-hand sides: the columns of a
 // task are its (pair, rhs) combinations, pair-major.
-// Tasks whose column (2 p^2 coefficients) outgrows shared memory run one
-// column per tile with their working set in a global scratch slot per CTA.
 struct RcrTileSet {
     RcrTile* tiles = nullptr;
     int ntiles = 0;
     size_t smem = 0;
-    RcrTile* big = nullptr;   // one-column tiles of the large-order tasks
-    int nbig = 0;
 };
+// Large orders run as staged batched GEMM passes (rcr_staged.cu) instead of
+// per-pair tiles: a pair's rotation and coaxial blocks must then be shared
+// by many pairs to be read at a useful rate.  By default a level is staged
+// from order FB_STG_PMIN on, and always when a pair's working set
+// (p_in^2 + max(p_in, p_out)^2 coefficients) exceeds what one CTA's shared
+// memory holds; the autotuner and fb_operator_set_forms choose per level.
+constexpr int FB_STG_PMIN = 40;
+bool fb_rcr_tile_fits(int p_in, int p_out, size_t csize);
+int fb_rcr_default_staged(int p_in, int p_out, size_t csize);
 struct RcrPlan {
     std::vector<RcrTask> h_tasks;
     std::vector<RcrTile> h_tiles;
-    std::vector<RcrTile> h_big;
     RcrTask* tasks = nullptr;
     RcrTile* tiles = nullptr;
-    RcrTile* big = nullptr;
     const int32_t* src_idx = nullptr;
     const int32_t* dst_idx = nullptr;
     int ntiles = 0;
-    int nbig = 0;
     int nb = 1;          // box pairs per CTA
     size_t smem = 0;     // dynamic shared memory per CTA (bytes)
     size_t csize = 0;    // bytes per complex coefficient
-    int64_t big_per = 0;    // scratch coefficients per CTA slot (large-order tasks)
-    int slots = 0;          // CTA slots of the scratch
-    void* scr = nullptr;    // slots x big_per coefficients
+    void* stg = nullptr;        // staged passes of the large-order tasks
+    int64_t stg_elems = 0;      // staging coefficients they need per buffer
     std::map<int, RcrTileSet> multi;   // tiles for nrhs > 1 (built on first use)
 };
 void fb_rcr_free(RcrPlan& p);
+bool fb_stg_staged(const RcrTask& tk);
+fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_rep, int64_t per_dir, void** out,
+                       int64_t* elems);
+void fb_stg_free(void*& plan);
+fb_status fb_stg_run_f(void* plan, const float* rotd, const cf* rph, int64_t per_dir, int prot, const cf* coax,
+                       const cf* src, cf* dst, cf* U, cf* V, cudaStream_t s, int nrhs, int64_t rstride);
+fb_status fb_stg_run_d(void* plan, const double* rotd, const cd* rph, int64_t per_dir, int prot, const cd* coax,
+                       const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride);
 
 // A group of box pairs sharing one composed translation matrix (job) on the
 // tensor cores: sources from level src_level, targets in level dst_level.
@@ -317,6 +328,17 @@ struct fb_op {
     cd* rph64 = nullptr; cf* rph32 = nullptr;            // phase tables (owned by the tree)
     cd* coax64 = nullptr; cf* coax32 = nullptr;
     int64_t coax_count = 0, rot_count = 0;
+    // per direction: a direction with the same polar angle (shares d^n)
+    std::vector<int> theta_rep;
+    // RCR form per level: 1 = staged passes, 0 = per-pair tiles (M2L of
+    // level l; M2M and L2L between levels l-1 and l)
+    int stg_m2l[FB_MAXLEV + 1] = {0};
+    int stg_pair[FB_MAXLEV + 1] = {0};
+    // staging buffers of the large-order RCR passes (U, V: stg_elems
+    // complex values each, in the operator's precision)
+    void* stg_u = nullptr;
+    void* stg_v = nullptr;
+    int64_t stg_elems = 0;
     RcrPlan m2l_rcr, m2m_rcr[FB_MAXLEV + 1], l2l_rcr[FB_MAXLEV + 1];
     // tensor-core (3xTF32) stacked M2L: dense levels (auto) / every level
     void* tc_plan = nullptr;
@@ -391,11 +413,15 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s);
 fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt = nullptr,
                        int nrhs = 1);
 fb_status fb_fmm_apply_noalloc(fb_op* op, const cd* x, cd* y, cudaStream_t s);
-fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize);
+fb_status fb_rcr_upload(fb_op* op, RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize);
 fb_status fb_tree_rotations(fb_tree* t, int P, const std::vector<double>& dirs, cudaStream_t s,
                             const fb_tree::RotSet** out);
 fb_status fb_compose_jobs(fb_op* op, const std::vector<int>& which, cudaStream_t s);
 fb_status fb_rcr_run_op(fb_op* op, RcrPlan& pl, void* src, void* dst, cudaStream_t s, int nrhs, int64_t rstride);
+// Installs per-level RCR forms (m2l[l], pair[l]: 1 = staged; levels whose
+// per-pair working set does not fit a CTA are staged regardless) and
+// rebuilds the affected plans.
+fb_status fb_rcr_restage(fb_op* op, const int* m2l, const int* pair);
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times, int* choice);
 fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s);
 fb_status fb_compose_all(fb_op* op, cudaStream_t s);

@@ -294,21 +294,16 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
                                              const int32_t* __restrict__ src_idx,
                                              const int32_t* __restrict__ dst_idx,
                                              const cx<R>* __restrict__ src, cx<R>* __restrict__ dst,
-                                             int nrhs, int64_t rstride, int ntiles, cx<R>* gscr,
-                                             int64_t gstride) {
+                                             int nrhs, int64_t rstride) {
     constexpr int BCH = RcrChunk<R>::value;
     extern __shared__ unsigned char smem_raw[];
     __shared__ int64_t s_dst_off[16];
-    // one tile per CTA (shared-memory working set), or a loop over the
-    // one-column tiles of large orders with the working set in this CTA's
-    // global scratch slot
-    for (int ti = blockIdx.x; ti < ntiles; ti += gridDim.x) {
-    RcrTile tl = tiles[ti];
+    RcrTile tl = tiles[blockIdx.x];
     RcrTask tk = tasks[tl.task];
     const int nb = tl.nb;
     const int Pin = tk.p_in * tk.p_in, Pout = tk.p_out * tk.p_out;
     const int pmid = tk.p_in;   // the rotated input keeps degrees n < p_in
-    cx<R>* buf = gscr ? gscr + (int64_t)blockIdx.x * gstride : (cx<R>*)smem_raw;
+    cx<R>* buf = (cx<R>*)smem_raw;
     cx<R>* xs = buf;                    // [nb][Pin], later reused for vs
     cx<R>* us = buf + nb * max(Pin, Pout);   // [nb][Pin]
     cx<R>* vs = buf;                    // [nb][Pout] (xs is dead after the rotation)
@@ -376,57 +371,22 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
 #undef RCR_BACK
     }
 #undef RCR_CHUNKS
-    __syncthreads();   // the next tile reuses the working set and s_dst_off
-    }
 }
 
 // Tiles of up to 16 columns per CTA within a shared-memory budget: 96 KB for
 // FP32 (two CTAs per SM; the columns of a tile reuse each rotation / coaxial
 // entry from registers, so larger tiles raise the arithmetic per load) and
 // 48 KB for FP64 (bound by the FP64 pipe, it wants more resident warps).
-// Columns needing more than RCR_SMEM_MAX bytes go to tiles in `big` whose
-// working set lives in a global scratch slot; up to RCR_BIG_COLS columns per
-// tile share each rotation / coaxial coefficient from registers, as long as
-// the plan keeps at least two such tiles per SM.
-constexpr size_t RCR_SMEM_MAX = 200 * 1024;
-constexpr int RCR_BIG_COLS = 4;
-
-static int sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms < 1) sms = 1;
-    }
-    return sms;
-}
-static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& tiles, size_t& smem,
-                           std::vector<RcrTile>& big, int64_t& big_per) {
+// Tasks of large order are left to the staged passes (fb_stg_staged).
+static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& tiles, size_t& smem) {
     const size_t budget = pl.csize == sizeof(cf) ? 96 * 1024 : 48 * 1024;
     tiles.clear();
-    big.clear();
     smem = 0;
-    big_per = 0;
-    int64_t big_cols = 0;
-    for (const RcrTask& tk : pl.h_tasks) {
-        size_t per = (size_t)(tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out)) * pl.csize;
-        if (per > RCR_SMEM_MAX) big_cols += (int64_t)tk.npairs * nrhs;
-    }
-    const int nbig = (int)std::max<int64_t>(1, std::min<int64_t>(RCR_BIG_COLS, big_cols / (2 * sm_count())));
     for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
         const RcrTask& tk = pl.h_tasks[t];
+        if (fb_stg_staged(tk)) continue;
         int64_t elems = (int64_t)tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out);
         size_t per = (size_t)elems * pl.csize;
-        if (per > RCR_SMEM_MAX) {
-            const int ncol = tk.npairs * nrhs;
-            for (int c = 0; c < ncol; c += nbig) big.push_back(RcrTile{t, c, std::min(nbig, ncol - c), 0});
-            // slots always hold RCR_BIG_COLS columns, so the tile sets built
-            // later for several right-hand sides (more columns, wider tiles)
-            // fit the scratch allocated with the plan
-            big_per = std::max(big_per, elems * RCR_BIG_COLS);
-            continue;
-        }
         int nb = (int)std::max<size_t>(1, std::min<size_t>(16, budget / per));
         int ncol = tk.npairs * nrhs;
         for (int c = 0; c < ncol; c += nb) {
@@ -442,25 +402,17 @@ static fb_status rcr_tiles_for(RcrPlan& pl, int nrhs, RcrTileSet* out) {
         out->tiles = pl.tiles;
         out->ntiles = pl.ntiles;
         out->smem = pl.smem;
-        out->big = pl.big;
-        out->nbig = pl.nbig;
         return FB_OK;
     }
     auto it = pl.multi.find(nrhs);
     if (it == pl.multi.end()) {
-        std::vector<RcrTile> h, hb;
+        std::vector<RcrTile> h;
         RcrTileSet ts;
-        int64_t per = 0;
-        rcr_make_tiles(pl, nrhs, h, ts.smem, hb, per);
+        rcr_make_tiles(pl, nrhs, h, ts.smem);
         ts.ntiles = (int)h.size();
-        ts.nbig = (int)hb.size();
         if (!h.empty()) {
             FB_CHECK(dalloc(&ts.tiles, h.size()));
             FB_CUDA(cudaMemcpy(ts.tiles, h.data(), sizeof(RcrTile) * h.size(), cudaMemcpyHostToDevice));
-        }
-        if (!hb.empty()) {
-            FB_CHECK(dalloc(&ts.big, hb.size()));
-            FB_CUDA(cudaMemcpy(ts.big, hb.data(), sizeof(RcrTile) * hb.size(), cudaMemcpyHostToDevice));
         }
         it = pl.multi.emplace(nrhs, ts).first;
     }
@@ -476,7 +428,28 @@ struct RotArgs {
     const cx<R>* ph;
     int64_t per_dir;
     int prot;
+    cx<R>* U;   // staging buffers of the large-order passes
+    cx<R>* V;
 };
+template <class R>
+static RotArgs<R> rot_args(const fb_op* op) {
+    RotArgs<R> a;
+    a.d = (const R*)(sizeof(R) == 8 ? (const void*)op->rotd64 : (const void*)op->rotd32);
+    a.ph = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->rph64 : (const void*)op->rph32);
+    a.per_dir = op->per_dir;
+    a.prot = op->Prot;
+    a.U = (cx<R>*)op->stg_u;
+    a.V = (cx<R>*)op->stg_v;
+    return a;
+}
+static fb_status stg_run(void* plan, const RotArgs<float>& r, const cf* coax, const cf* src, cf* dst,
+                         cudaStream_t s, int nrhs, int64_t rstride) {
+    return fb_stg_run_f(plan, r.d, r.ph, r.per_dir, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride);
+}
+static fb_status stg_run(void* plan, const RotArgs<double>& r, const cd* coax, const cd* src, cd* dst,
+                         cudaStream_t s, int nrhs, int64_t rstride) {
+    return fb_stg_run_d(plan, r.d, r.ph, r.per_dir, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride);
+}
 
 template <class R>
 static fb_status run_rcr(RcrPlan& pl, const RotArgs<R>& rot, const cx<R>* coax, const cx<R>* src, cx<R>* dst,
@@ -486,28 +459,27 @@ static fb_status run_rcr(RcrPlan& pl, const RotArgs<R>& rot, const cx<R>* coax, 
     if (ts.ntiles > 0) {
         FB_CHECK(fb_smem_cap((const void*)k_rcr<R>, ts.smem));
         k_rcr<R><<<ts.ntiles, 256, ts.smem, s>>>(pl.tasks, ts.tiles, rot.d, rot.ph, rot.per_dir, rot.prot, coax,
-                                                 pl.src_idx, pl.dst_idx, src, dst, nrhs, rstride, ts.ntiles,
-                                                 nullptr, 0);
+                                                 pl.src_idx, pl.dst_idx, src, dst, nrhs, rstride);
         FB_LAUNCH_CHECK();
         fb_count_launch();
     }
-    if (ts.nbig > 0) {
-        k_rcr<R><<<std::min(ts.nbig, pl.slots), 256, 0, s>>>(pl.tasks, ts.big, rot.d, rot.ph, rot.per_dir, rot.prot,
-                                                             coax, pl.src_idx, pl.dst_idx, src, dst, nrhs, rstride,
-                                                             ts.nbig, (cx<R>*)pl.scr, pl.big_per);
-        FB_LAUNCH_CHECK();
-        fb_count_launch();
-    }
+    if (pl.stg) FB_CHECK(stg_run(pl.stg, rot, coax, src, dst, s, nrhs, rstride));
     return FB_OK;
 }
 
-fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize) {
+// Uploads an RCR plan: per-pair tiles for the tasks of moderate order and the
+// staged passes of the large-order ones, whose staging buffers (shared by
+// every plan of the operator: the passes of one matvec run one after the
+// other) grow to the largest level's need.
+fb_status fb_rcr_upload(fb_op* op, RcrPlan& pl, const int32_t* src, const int32_t* dst, size_t csize) {
     pl.src_idx = src;
     pl.dst_idx = dst;
     pl.csize = csize;
-    rcr_make_tiles(pl, 1, pl.h_tiles, pl.smem, pl.h_big, pl.big_per);
+    // a pair whose working set does not fit one CTA can only run staged
+    for (RcrTask& tk : pl.h_tasks)
+        if (!tk.staged && !fb_rcr_tile_fits(tk.p_in, tk.p_out, csize)) tk.staged = 1;
+    rcr_make_tiles(pl, 1, pl.h_tiles, pl.smem);
     pl.ntiles = (int)pl.h_tiles.size();
-    pl.nbig = (int)pl.h_big.size();
     if (pl.h_tasks.empty()) return FB_OK;
     FB_CHECK(dalloc(&pl.tasks, pl.h_tasks.size()));
     FB_CUDA(cudaMemcpy(pl.tasks, pl.h_tasks.data(), sizeof(RcrTask) * pl.h_tasks.size(), cudaMemcpyHostToDevice));
@@ -515,16 +487,16 @@ fb_status fb_rcr_upload(RcrPlan& pl, const int32_t* src, const int32_t* dst, siz
         FB_CHECK(dalloc(&pl.tiles, pl.h_tiles.size()));
         FB_CUDA(cudaMemcpy(pl.tiles, pl.h_tiles.data(), sizeof(RcrTile) * pl.h_tiles.size(), cudaMemcpyHostToDevice));
     }
-    if (pl.nbig) {
-        // four CTA slots per SM: enough warps to hide the L2 latency of
-        // the working set, which stays L2-resident for moderate orders
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        pl.slots = std::max(1, 4 * sms);
-        FB_CHECK(dalloc(&pl.big, pl.h_big.size()));
-        FB_CUDA(cudaMemcpy(pl.big, pl.h_big.data(), sizeof(RcrTile) * pl.h_big.size(), cudaMemcpyHostToDevice));
-        FB_CHECK(dalloc((unsigned char**)&pl.scr, (size_t)pl.slots * pl.big_per * csize));
+    FB_CHECK(fb_stg_build(pl, op->theta_rep, op->per_dir, &pl.stg, &pl.stg_elems));
+    if (pl.stg_elems > op->stg_elems) {
+        FB_CUDA(cudaDeviceSynchronize());
+        dfree(op->stg_u);
+        dfree(op->stg_v);
+        op->stg_elems = 0;
+        FB_CHECK(dalloc((unsigned char**)&op->stg_u, (size_t)pl.stg_elems * csize));
+        FB_CHECK(dalloc((unsigned char**)&op->stg_v, (size_t)pl.stg_elems * csize));
+        op->stg_elems = pl.stg_elems;
+        op->buf_gen++;   // captured graphs refer to the old buffers
     }
     return FB_OK;
 }
@@ -581,11 +553,7 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
     FB_LAUNCH_CHECK();
     fb_count_launch();
     mark(1);
-    RotArgs<R> rot;
-    rot.d = (const R*)(sizeof(R) == 8 ? (const void*)op->rotd64 : (const void*)op->rotd32);
-    rot.ph = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->rph64 : (const void*)op->rph32);
-    rot.per_dir = op->per_dir;
-    rot.prot = op->Prot;
+    const RotArgs<R> rot = rot_args<R>(op);
     const cx<R>* coax = (const cx<R>*)(sizeof(R) == 8 ? (const void*)op->coax64 : (const void*)op->coax32);
     const bool auto_tc = sizeof(R) == 4 && op->method == FB_TRANS_AUTO;
     for (int l = L; l >= 3; --l) {
@@ -648,14 +616,62 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
     return FB_OK;
 }
 
+static size_t op_csize(const fb_op* op) { return op->prec == FB_PREC_MIXED_FMM ? sizeof(cf) : sizeof(cd); }
+
+// Level whose RCR flag governs a task: M2L tasks read and write one level;
+// M2M / L2L tasks are governed by their finer (child) level, whose
+// expansions lie after the parent's in the level arrays.  Levels 0 and 1
+// hold no expansions (their offsets equal level 2's), so the search starts
+// at level 2.
+static int task_level(const fb_op* op, const RcrTask& tk, bool* m2l) {
+    *m2l = tk.src_base == tk.dst_base;
+    const int64_t b = std::max(tk.src_base, tk.dst_base);
+    for (int l = 2; l <= op->L; ++l)
+        if (op->lev_off[l] == b) return l;
+    return 2;
+}
+
+fb_status fb_rcr_restage(fb_op* op, const int* m2l, const int* pair) {
+    const size_t csz = op_csize(op);
+    for (int l = 2; l <= op->L; ++l) {
+        op->stg_m2l[l] = (m2l[l] || !fb_rcr_tile_fits(op->p[l], op->p[l], csz)) ? 1 : 0;
+        if (l >= 3) {
+            const int pm = std::max(op->p[l], op->p[l - 1]);
+            op->stg_pair[l] = (pair[l] || !fb_rcr_tile_fits(pm, pm, csz)) ? 1 : 0;
+        }
+    }
+    FB_CUDA(cudaDeviceSynchronize());
+    op->buf_gen++;   // captured graphs refer to the plans rebuilt here
+    auto redo = [&](RcrPlan& pl) -> fb_status {
+        if (pl.h_tasks.empty()) return FB_OK;
+        bool changed = false;
+        for (RcrTask& tk : pl.h_tasks) {
+            bool is_m2l = false;
+            const int l = task_level(op, tk, &is_m2l);
+            const int want = is_m2l ? op->stg_m2l[l] : op->stg_pair[l];
+            changed = changed || tk.staged != want;
+            tk.staged = want;
+        }
+        if (!changed) return FB_OK;
+        const int32_t* si = pl.src_idx;
+        const int32_t* di = pl.dst_idx;
+        fb_rcr_free(pl);
+        return fb_rcr_upload(op, pl, si, di, csz);
+    };
+    FB_CHECK(redo(op->m2l_rcr));
+    FB_CHECK(redo(op->m2l_rcr_rest));
+    for (int l = 3; l <= op->L; ++l) {
+        FB_CHECK(redo(op->m2m_rcr[l]));
+        FB_CHECK(redo(op->l2l_rcr[l]));
+    }
+    return FB_OK;
+}
+
 // One RCR plan on the operator's expansion buffers (precision of the op).
 fb_status fb_rcr_run_op(fb_op* op, RcrPlan& pl, void* src, void* dst, cudaStream_t s, int nrhs, int64_t rstride) {
-    if (op->prec == FB_PREC_MIXED_FMM) {
-        RotArgs<float> rot{op->rotd32, (const cf*)op->rph32, op->per_dir, op->Prot};
-        return run_rcr<float>(pl, rot, op->coax32, (const cf*)src, (cf*)dst, s, nrhs, rstride);
-    }
-    RotArgs<double> rot{op->rotd64, (const cd*)op->rph64, op->per_dir, op->Prot};
-    return run_rcr<double>(pl, rot, op->coax64, (const cd*)src, (cd*)dst, s, nrhs, rstride);
+    if (op->prec == FB_PREC_MIXED_FMM)
+        return run_rcr<float>(pl, rot_args<float>(op), op->coax32, (const cf*)src, (cf*)dst, s, nrhs, rstride);
+    return run_rcr<double>(pl, rot_args<double>(op), op->coax64, (const cd*)src, (cd*)dst, s, nrhs, rstride);
 }
 
 fb_status fb_fmm_apply(fb_op* op, const cd* x, cd* y, cudaStream_t s, PhaseTimer* pt, int nrhs) {
@@ -671,13 +687,9 @@ static void free_plan(TransPlan& p) {
 void fb_rcr_free(RcrPlan& p) {
     dfree(p.tasks);
     dfree(p.tiles);
-    dfree(p.big);
-    if (p.scr) cudaFree(p.scr);
-    p.scr = nullptr;
-    for (auto& kv : p.multi) {
-        dfree(kv.second.tiles);
-        dfree(kv.second.big);
-    }
+    fb_stg_free(p.stg);
+    p.stg_elems = 0;
+    for (auto& kv : p.multi) dfree(kv.second.tiles);
     p.multi.clear();
 }
 static void free_plan(RcrPlan& p) { fb_rcr_free(p); }
@@ -718,6 +730,9 @@ void fb_fmm_destroy(fb_op* op) {
     op->rph32 = nullptr;
     dfree(op->coax64);
     dfree(op->coax32);
+    dfree(op->stg_u);
+    dfree(op->stg_v);
+    op->stg_elems = 0;
 }
 
 // ---------------------------------------------------------------------------

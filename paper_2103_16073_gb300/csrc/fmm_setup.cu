@@ -656,6 +656,24 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         oct_dir_l2l[o] = get_dir(-sx, -sy, -sz);  // child - parent
     }
     int ndir = (int)dirs.size() / 3;
+    // directions sharing a polar angle share their real rotation factors d^n
+    // (D^n_{mu,m} = d^n_{mu,m}(theta) e^{i m phi}): representative of each
+    // direction = the first direction with the same cos(theta) = dz / |d|,
+    // compared exactly on the integer vectors (dz^2 |d'|^2 = dz'^2 |d|^2,
+    // same sign of dz)
+    op->theta_rep.assign(ndir, -1);
+    for (int a = 0; a < ndir; ++a) {
+        const int64_t za = (int64_t)dirs[3 * a + 2];
+        const int64_t na = (int64_t)(dirs[3 * a] * dirs[3 * a] + dirs[3 * a + 1] * dirs[3 * a + 1] + za * za);
+        for (int b = 0; b <= a; ++b) {
+            const int64_t zb = (int64_t)dirs[3 * b + 2];
+            const int64_t nb = (int64_t)(dirs[3 * b] * dirs[3 * b] + dirs[3 * b + 1] * dirs[3 * b + 1] + zb * zb);
+            if ((za > 0) == (zb > 0) && (za < 0) == (zb < 0) && za * za * nb == zb * zb * na) {
+                op->theta_rep[a] = b;
+                break;
+            }
+        }
+    }
     // coaxial sets
     std::vector<CoaxSet> sets;
     std::map<std::tuple<int, int, int64_t>, int> set_index;   // (kind, p, ktau bits)
@@ -797,8 +815,20 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
             tk.pc = sets[r.set].p;
             tk.src_base = src_base;
             tk.dst_base = dst_base;
+            tk.staged = r.which == 0 ? op->stg_m2l[r.level] : op->stg_pair[r.level];
+            tk.pad = 0;
             return tk;
         };
+        {
+            const size_t cs = op->prec == FB_PREC_MIXED_FMM ? sizeof(cf) : sizeof(cd);
+            for (int l = 2; l <= L; ++l) {
+                op->stg_m2l[l] = fb_rcr_default_staged(op->p[l], op->p[l], cs);
+                if (l >= 3) {
+                    const int pm = std::max(op->p[l], op->p[l - 1]);
+                    op->stg_pair[l] = fb_rcr_default_staged(pm, pm, cs);
+                }
+            }
+        }
         // levels whose M2L groups are dense enough for the tensor-core form
         // (mixed precision): on average >= 48 box pairs per translation vector
         std::vector<int> tc_levels;
@@ -833,8 +863,8 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
             }
         }
         size_t csz = op->prec == FB_PREC_MIXED_FMM ? sizeof(cf) : sizeof(cd);
-        FB_CHECK(fb_rcr_upload(op->m2l_rcr, t->m2l_src, t->m2l_dst, csz));
-        FB_CHECK(fb_rcr_upload(op->m2l_rcr_rest, t->m2l_src, t->m2l_dst, csz));
+        FB_CHECK(fb_rcr_upload(op, op->m2l_rcr, t->m2l_src, t->m2l_dst, csz));
+        FB_CHECK(fb_rcr_upload(op, op->m2l_rcr_rest, t->m2l_src, t->m2l_dst, csz));
         if (!tc_levels.empty()) {
             std::vector<int> need;
             for (size_t j = 0; j < op->h_jobs.size(); ++j)
@@ -862,8 +892,8 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
             }
         }
         for (int l = 3; l <= L; ++l) {
-            FB_CHECK(fb_rcr_upload(op->m2m_rcr[l], t->oct_child[l], t->oct_parent[l], csz));
-            FB_CHECK(fb_rcr_upload(op->l2l_rcr[l], t->oct_parent[l], t->oct_child[l], csz));
+            FB_CHECK(fb_rcr_upload(op, op->m2m_rcr[l], t->oct_child[l], t->oct_parent[l], csz));
+            FB_CHECK(fb_rcr_upload(op, op->l2l_rcr[l], t->oct_parent[l], t->oct_child[l], csz));
         }
         op->method = FB_TRANS_AUTO;
     }

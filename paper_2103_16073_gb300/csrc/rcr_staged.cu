@@ -1,0 +1,558 @@
+// Rotation - coaxial translation - back-rotation (Sec. 3.3) for large
+// expansion orders, staged through global memory as three batched GEMM
+// passes per level.  At order p one box pair needs the rotation blocks of its
+// direction (sum_n (2n+1)^2 ~ 4p^3/3 coefficients, twice) and the coaxial
+// blocks of its |t| (sum_m (p-|m|)^2 ~ 2p^3/3); at p = 159 that is ~40 MB per
+// pair, so the translation only runs near the arithmetic roofline when every
+// coefficient block is applied to many pairs at once.  The passes group the
+// pairs so that it is:
+//
+//   R  rotate:       u_n = d^n(theta) (e^{i m phi} x_n)       per (theta, n)
+//      The real factor d^n depends on the polar angle theta of the
+//      translation direction only (D^n_{mu,m} = d^n_{mu,m}(theta) e^{i m phi}
+//      for Q = R_y(-theta) R_z(-phi)), so all pairs of a level whose
+//      directions share theta (290 directions, 49 polar angles) form the
+//      columns of one real GEMM per degree n; the phase e^{i m phi} of each
+//      pair's own direction is applied while staging its input.
+//   C  coaxial:      v^{+-m} = C^{|m|}(|t|) u^{+-m}             per (|t|, |m|)
+//      The coaxial block of order |m| depends on the translation distance
+//      only: all pairs of a level with one |t|, both signs of m, are the
+//      columns of one complex GEMM per |m|.
+//   B  back-rotate:  y_n' = e^{-i m' phi} d^{n'}(theta)^T v_n'   per (theta, n')
+//      then scatter-added into the target boxes (atomic adds: several pairs
+//      share a target).
+//
+// u is kept per pair in degree-major order (the order of the expansions,
+// (n, m) at n^2 + n + m) and v in order-major order (order m, degrees
+// |m|..p_out-1, contiguous), so each pass writes contiguous runs and the
+// strided gathers fall on reads only.  One CTA computes a 64 x 64 tile of
+// one GEMM (256 threads, 4 x 4 complex outputs each, K in chunks of 16,
+// double-buffered shared memory).
+#include <algorithm>
+#include <map>
+#include <tuple>
+#include <vector>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr int SBM = 64;   // rows per tile
+constexpr int SBN = 64;   // complex columns per tile
+constexpr int SBK = 16;   // K chunk
+constexpr int STHREADS = 256;
+
+// one pair (column) of a staged level
+struct StgSlot {
+    int64_t src_off;   // first coefficient of the source expansion
+    int64_t dst_off;   // first coefficient of the target expansion
+    int32_t dir;       // translation direction (phase table)
+    int32_t pad;
+};
+// tile of pass R (degree n) or B (degree n'): slots [col0, col0 + ncol) of
+// one polar-angle group, rows [row0, row0 + 64) of the block
+struct StgTile {
+    int32_t col0, ncol;
+    int32_t n, row0;
+    int32_t adir;      // a direction of the group (its real factors d^n)
+    int32_t pad;
+};
+// tile of pass C: virtual columns [vc0, vc0 + nvc) of one |t| group
+// (virtual column v = slot cidx[c0 + v] for m = 0, else (slot cidx[c0 + v/2],
+// sign + for even v, - for odd v))
+struct StgCTile {
+    int64_t a_off;     // C^{|m|}_{|m|,|m|} of the set
+    int32_t c0, vc0, nvc;
+    int32_t am, row0, pc;
+    int32_t M, K;
+};
+
+__host__ __device__ __forceinline__ int64_t rot_off(int n) { return (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3; }
+// start of order m in the order-major layout of an order-p expansion
+// (orders -(p-1) .. p-1, order m holding degrees |m| .. p-1)
+__host__ __device__ __forceinline__ int moff(int m, int p) {
+    if (m <= 0) {
+        int a = p + m;   // p - |m|
+        return (a - 1) * a / 2;
+    }
+    return (p - 1) * p / 2 + m * p - m * (m - 1) / 2;
+}
+
+template <class R, bool CA>
+struct StgSmem {
+    using AT = typename std::conditional<CA, cx<R>, R>::type;
+    alignas(16) AT A[2][SBK][SBM + (CA ? 2 : 4)];   // padded rows (16-byte aligned, fewer bank conflicts)
+    alignas(16) cx<R> X[2][SBK][SBN + 2];
+    int64_t col_off[SBN];
+    int32_t col_aux[SBN];
+};
+
+template <class R>
+__device__ __forceinline__ void fma_ax(cx<R>& acc, R a, const cx<R>& x) {
+    acc.re = fma(a, x.re, acc.re);
+    acc.im = fma(a, x.im, acc.im);
+}
+template <class R>
+__device__ __forceinline__ void fma_ax(cx<R>& acc, const cx<R>& a, const cx<R>& x) {
+    acc.re = fma(a.re, x.re, acc.re);
+    acc.re = fma(-a.im, x.im, acc.re);
+    acc.im = fma(a.re, x.im, acc.im);
+    acc.im = fma(a.im, x.re, acc.im);
+}
+// four consecutive shared-memory operands (16-byte aligned) in vector loads
+__device__ __forceinline__ void ld4(float (&o)[4], const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+__device__ __forceinline__ void ld4(double (&o)[4], const double* p) {
+    const double2 a = *reinterpret_cast<const double2*>(p), b = *reinterpret_cast<const double2*>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+__device__ __forceinline__ void ld4(cf (&o)[4], const cf* p) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 2);
+    o[0] = mk(a.x, a.y); o[1] = mk(a.z, a.w); o[2] = mk(b.x, b.y); o[3] = mk(b.z, b.w);
+}
+__device__ __forceinline__ void ld4(cd (&o)[4], const cd* p) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double2 a = *reinterpret_cast<const double2*>(p + i);
+        o[i] = mk(a.x, a.y);
+    }
+}
+
+// acc[i][j] (rows ty*4+i, columns tx*4+j) += sum_k A[row][k] X[k][col] over
+// k < K.  load_a(r, k) / load_x(c, k) return the (bounds-checked) operands;
+// AK: A is contiguous along k (staging threads walk k fastest).
+template <class R, bool CA, bool AK, class LA, class LX>
+__device__ __forceinline__ void stg_mainloop(StgSmem<R, CA>& sm, int K, LA load_a, LX load_x, cx<R> (&acc)[4][4]) {
+    using AT = typename StgSmem<R, CA>::AT;
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    AT ra[4];
+    cx<R> rx[4];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = tid + i * STHREADS;
+            const int r = AK ? e / SBK : e % SBM;
+            const int k = AK ? e % SBK : e / SBM;
+            ra[i] = load_a(r, k0 + k);
+            const int c = e / SBK, kk = e % SBK;
+            rx[i] = load_x(c, k0 + kk);
+        }
+    };
+    auto stash = [&](int b) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int e = tid + i * STHREADS;
+            const int r = AK ? e / SBK : e % SBM;
+            const int k = AK ? e % SBK : e / SBM;
+            sm.A[b][k][r] = ra[i];
+            const int c = e / SBK, kk = e % SBK;
+            sm.X[b][kk][c] = rx[i];
+        }
+    };
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = mk<R>(0, 0);
+    fetch(0);
+    stash(0);
+    __syncthreads();
+    int cur = 0;
+    for (int k0 = 0; k0 < K; k0 += SBK) {
+        const bool more = k0 + SBK < K;
+        if (more) fetch(k0 + SBK);
+#pragma unroll
+        for (int kk = 0; kk < SBK; ++kk) {
+            AT a[4];
+            cx<R> x[4];
+            ld4(a, &sm.A[cur][kk][ty * 4]);
+            ld4(x, &sm.X[cur][kk][tx * 4]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) fma_ax(acc[i][j], a[i], x[j]);
+        }
+        if (more) stash(cur ^ 1);
+        __syncthreads();
+        cur ^= 1;
+    }
+}
+
+// ------------------------------------------------------------- pass R ----
+// U[slot][n^2 + row] = sum_m d^n_{row-n, m-n} e^{i (m-n) phi_slot} src[slot][n^2 + m]
+template <class R>
+__global__ void __launch_bounds__(STHREADS, 2) k_stg_rot(const StgTile* __restrict__ tiles,
+                                                      const StgSlot* __restrict__ slots,
+                                                      const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
+                                                      int64_t per_dir, int prot, const cx<R>* __restrict__ src,
+                                                      cx<R>* __restrict__ U, int S) {
+    extern __shared__ __align__(16) unsigned char stg_smem[];
+    StgSmem<R, false>& sm = *reinterpret_cast<StgSmem<R, false>*>(stg_smem);
+    const StgTile tl = tiles[blockIdx.x];
+    const int n = tl.n, w = 2 * n + 1;
+    const int tid = threadIdx.x;
+    if (tid < SBN) {
+        if (tid < tl.ncol) {
+            StgSlot sl = slots[tl.col0 + tid];
+            sm.col_off[tid] = sl.src_off + (int64_t)n * n;
+            sm.col_aux[tid] = sl.dir;
+        } else {
+            sm.col_off[tid] = -1;
+            sm.col_aux[tid] = 0;
+        }
+    }
+    __syncthreads();
+    const R* A = rotd + (int64_t)tl.adir * per_dir + rot_off(n) + (int64_t)tl.row0 * w;
+    const int M = min(SBM, w - tl.row0);
+    auto load_a = [&](int r, int k) -> R { return (r < M && k < w) ? A[(int64_t)r * w + k] : R(0); };
+    auto load_x = [&](int c, int k) -> cx<R> {
+        const int64_t o = sm.col_off[c];
+        if (o < 0 || k >= w) return mk<R>(0, 0);
+        const cx<R> ph = rph[(int64_t)sm.col_aux[c] * (2 * prot - 1) + (prot - 1) + (k - n)];
+        return src[o + k] * ph;
+    };
+    cx<R> acc[4][4];
+    stg_mainloop<R, false, true>(sm, w, load_a, load_x, acc);
+    const int ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = tx * 4 + j;
+        if (c >= tl.ncol) continue;
+        cx<R>* u = U + (int64_t)(tl.col0 + c) * S + (int64_t)n * n + tl.row0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = ty * 4 + i;
+            if (r < M) u[r] = acc[i][j];
+        }
+    }
+}
+
+// ------------------------------------------------------------- pass C ----
+// V[slot][moff(s am) + row] = sum_k C^{am}_{am+row, am+k} U[slot][(am+k)^2 + (am+k) + s am]
+template <class R>
+__global__ void __launch_bounds__(STHREADS, 2) k_stg_coax(const StgCTile* __restrict__ tiles,
+                                                       const int32_t* __restrict__ cidx,
+                                                       const cx<R>* __restrict__ coax, const cx<R>* __restrict__ U,
+                                                       cx<R>* __restrict__ V, int S, int pout) {
+    extern __shared__ __align__(16) unsigned char stg_smem[];
+    StgSmem<R, true>& sm = *reinterpret_cast<StgSmem<R, true>*>(stg_smem);
+    const StgCTile tl = tiles[blockIdx.x];
+    const int am = tl.am;
+    const int tid = threadIdx.x;
+    if (tid < SBN) {
+        if (tid < tl.nvc) {
+            const int v = tl.vc0 + tid;
+            const int slot = am == 0 ? cidx[tl.c0 + v] : cidx[tl.c0 + (v >> 1)];
+            const int sg = (am == 0 || !(v & 1)) ? 1 : -1;
+            sm.col_off[tid] = (int64_t)slot * S;
+            sm.col_aux[tid] = sg * am;   // the order m of this column
+        } else {
+            sm.col_off[tid] = -1;
+            sm.col_aux[tid] = 0;
+        }
+    }
+    __syncthreads();
+    const cx<R>* A = coax + tl.a_off + (int64_t)tl.row0 * tl.pc;
+    const int M = min(SBM, tl.M - tl.row0);
+    const int K = tl.K, pc = tl.pc;
+    auto load_a = [&](int r, int k) -> cx<R> {
+        return (r < M && k < K) ? A[(int64_t)r * pc + k] : mk<R>(0, 0);
+    };
+    auto load_x = [&](int c, int k) -> cx<R> {
+        const int64_t o = sm.col_off[c];
+        if (o < 0 || k >= K) return mk<R>(0, 0);
+        const int nn = am + k;
+        return U[o + (int64_t)nn * nn + nn + sm.col_aux[c]];
+    };
+    cx<R> acc[4][4];
+    stg_mainloop<R, true, true>(sm, K, load_a, load_x, acc);
+    const int ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = tx * 4 + j;
+        if (c >= tl.nvc) continue;
+        cx<R>* v = V + sm.col_off[c] + moff(sm.col_aux[c], pout) + tl.row0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = ty * 4 + i;
+            if (r < M) v[r] = acc[i][j];
+        }
+    }
+}
+
+// ------------------------------------------------------------- pass B ----
+// dst[slot][n'^2 + row] += e^{-i m' phi} sum_mu d^{n'}_{mu, m'} V[slot][moff(mu) + n' - |mu|],
+// m' = row - n', |mu| <= min(n', p_in - 1)
+template <class R>
+__device__ __forceinline__ void atomic_add_cx(cx<R>* d, const cx<R>& v);
+template <>
+__device__ __forceinline__ void atomic_add_cx<float>(cf* d, const cf& v) {
+    atomicAdd(reinterpret_cast<float2*>(d), make_float2(v.re, v.im));
+}
+template <>
+__device__ __forceinline__ void atomic_add_cx<double>(cd* d, const cd& v) {
+    atomicAdd(&d->re, v.re);
+    atomicAdd(&d->im, v.im);
+}
+
+template <class R>
+__global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restrict__ tiles,
+                                                       const StgSlot* __restrict__ slots,
+                                                       const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
+                                                       int64_t per_dir, int prot, const cx<R>* __restrict__ V,
+                                                       cx<R>* __restrict__ dst, int S, int pin, int pout) {
+    extern __shared__ __align__(16) unsigned char stg_smem[];
+    StgSmem<R, false>& sm = *reinterpret_cast<StgSmem<R, false>*>(stg_smem);
+    const StgTile tl = tiles[blockIdx.x];
+    const int n = tl.n, w = 2 * n + 1;
+    const int mmax = min(n, pin - 1);
+    const int K = 2 * mmax + 1;
+    const int tid = threadIdx.x;
+    if (tid < SBN) {
+        if (tid < tl.ncol) {
+            StgSlot sl = slots[tl.col0 + tid];
+            sm.col_off[tid] = sl.dst_off;
+            sm.col_aux[tid] = sl.dir;
+        } else {
+            sm.col_off[tid] = -1;
+            sm.col_aux[tid] = 0;
+        }
+    }
+    __syncthreads();
+    // A[row][k] = d^{n}_{mu, m'} with mu = k - mmax, m' = row0 + row - n
+    const R* A = rotd + (int64_t)tl.adir * per_dir + rot_off(n) + (int64_t)(n - mmax) * w + tl.row0;
+    const int M = min(SBM, w - tl.row0);
+    auto load_a = [&](int r, int k) -> R { return (r < M && k < K) ? A[(int64_t)k * w + r] : R(0); };
+    const int64_t col_base = (int64_t)tl.col0 * S;
+    auto load_x = [&](int c, int k) -> cx<R> {
+        if (c >= tl.ncol || k >= K) return mk<R>(0, 0);
+        const int mu = k - mmax;
+        const int amu = mu < 0 ? -mu : mu;
+        return V[col_base + (int64_t)c * S + moff(mu, pout) + (n - amu)];
+    };
+    cx<R> acc[4][4];
+    stg_mainloop<R, false, false>(sm, K, load_a, load_x, acc);
+    const int ty = tid >> 4, tx = tid & 15;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int c = tx * 4 + j;
+        if (c >= tl.ncol) continue;
+        const cx<R>* ph = rph + (int64_t)sm.col_aux[c] * (2 * prot - 1) + (prot - 1);
+        cx<R>* d = dst + sm.col_off[c] + (int64_t)n * n + tl.row0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int r = ty * 4 + i;
+            if (r >= M) continue;
+            const int m1 = tl.row0 + r - n;
+            atomic_add_cx<R>(d + r, acc[i][j] * conjg(ph[m1]));
+        }
+    }
+}
+
+// ------------------------------------------------------------ host plan ----
+struct StgLevel {
+    int p_in = 0, p_out = 0, S = 0, nslot = 0;
+    StgSlot* slots = nullptr;
+    int32_t* cidx = nullptr;
+    StgTile* rt = nullptr;
+    StgCTile* ct = nullptr;
+    StgTile* bt = nullptr;
+    int nrt = 0, nct = 0, nbt = 0;
+};
+
+struct StgPlanImpl {
+    std::vector<StgLevel> levels;
+};
+
+void free_level(StgLevel& lv) {
+    dfree(lv.slots);
+    dfree(lv.cidx);
+    dfree(lv.rt);
+    dfree(lv.ct);
+    dfree(lv.bt);
+}
+
+template <class T>
+fb_status upload(T** d, const std::vector<T>& h) {
+    if (h.empty()) return FB_OK;
+    FB_CHECK(dalloc(d, h.size()));
+    FB_CUDA(cudaMemcpy(*d, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+    return FB_OK;
+}
+
+}  // namespace
+
+bool fb_stg_staged(const RcrTask& tk) { return tk.staged != 0; }
+
+bool fb_rcr_tile_fits(int p_in, int p_out, size_t csize) {
+    const size_t per = (size_t)((int64_t)p_in * p_in + std::max<int64_t>((int64_t)p_in * p_in, (int64_t)p_out * p_out));
+    return per * csize <= 200 * 1024;
+}
+int fb_rcr_default_staged(int p_in, int p_out, size_t csize) {
+    return !fb_rcr_tile_fits(p_in, p_out, csize) || std::max(p_in, p_out) >= FB_STG_PMIN;
+}
+
+// Builds the staged passes of the tasks of `pl` that fb_stg_staged selects.
+// theta_rep[dir] is a direction with the same polar angle as dir (the
+// group's representative; its real factors d^n serve the whole group).
+// *elems receives the complex coefficients one staging buffer needs (the
+// largest level: pairs x max(p_in, p_out)^2).
+fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_rep, int64_t per_dir, void** out,
+                       int64_t* elems) {
+    *out = nullptr;
+    *elems = 0;
+    // tasks by level (same source and target level arrays and orders)
+    std::map<std::tuple<int64_t, int64_t, int, int>, std::vector<int>> by_level;
+    for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
+        const RcrTask& tk = pl.h_tasks[t];
+        if (!fb_stg_staged(tk) || tk.npairs == 0) continue;
+        by_level[std::make_tuple(tk.src_base, tk.dst_base, tk.p_in, tk.p_out)].push_back(t);
+    }
+    if (by_level.empty()) return FB_OK;
+    StgPlanImpl* P = new StgPlanImpl();
+    auto fail = [&](fb_status st) {
+        for (auto& lv : P->levels) free_level(lv);
+        delete P;
+        return st;
+    };
+    for (auto& kv : by_level) {
+        const std::vector<int>& ts = kv.second;
+        const int p_in = std::get<2>(kv.first), p_out = std::get<3>(kv.first);
+        StgLevel lv;
+        lv.p_in = p_in;
+        lv.p_out = p_out;
+        lv.S = std::max(p_in * p_in, p_out * p_out);
+        // polar-angle groups of the tasks, in order of first appearance
+        std::map<int, std::vector<int>> groups;   // representative direction -> tasks
+        std::vector<int> group_order;
+        for (int t : ts) {
+            int dir = (int)(pl.h_tasks[t].rot_off / per_dir);
+            int rep = theta_rep.at(dir);
+            if (!groups.count(rep)) group_order.push_back(rep);
+            groups[rep].push_back(t);
+        }
+        std::vector<StgSlot> slots;
+        std::vector<int> slot_task;
+        std::vector<StgTile> rt, bt;
+        for (int rep : group_order) {
+            const int g0 = (int)slots.size();
+            for (int t : groups[rep]) {
+                const RcrTask& tk = pl.h_tasks[t];
+                std::vector<int32_t> si(tk.npairs), di(tk.npairs);
+                if (cudaMemcpy(si.data(), pl.src_idx + tk.pair_off, sizeof(int32_t) * tk.npairs,
+                               cudaMemcpyDeviceToHost) != cudaSuccess ||
+                    cudaMemcpy(di.data(), pl.dst_idx + tk.pair_off, sizeof(int32_t) * tk.npairs,
+                               cudaMemcpyDeviceToHost) != cudaSuccess)
+                    return fail(fb_fail(FB_ERR_CUDA, "staged RCR: pair index copy failed"));
+                const int dir = (int)(tk.rot_off / per_dir);
+                for (int j = 0; j < tk.npairs; ++j) {
+                    StgSlot s;
+                    s.src_off = tk.src_base + (int64_t)si[j] * p_in * p_in;
+                    s.dst_off = tk.dst_base + (int64_t)di[j] * p_out * p_out;
+                    s.dir = dir;
+                    s.pad = 0;
+                    slots.push_back(s);
+                    slot_task.push_back(t);
+                }
+            }
+            const int g1 = (int)slots.size();
+            for (int n = 0; n < p_in; ++n)
+                for (int r0 = 0; r0 < 2 * n + 1; r0 += SBM)
+                    for (int c0 = g0; c0 < g1; c0 += SBN)
+                        rt.push_back(StgTile{c0, std::min(SBN, g1 - c0), n, r0, rep, 0});
+            for (int n = 0; n < p_out; ++n)
+                for (int r0 = 0; r0 < 2 * n + 1; r0 += SBM)
+                    for (int c0 = g0; c0 < g1; c0 += SBN)
+                        bt.push_back(StgTile{c0, std::min(SBN, g1 - c0), n, r0, rep, 0});
+        }
+        // |t| groups (coaxial sets) of the slots
+        std::map<int64_t, std::vector<int32_t>> sets;   // coax_off -> slots
+        std::map<int64_t, int> set_pc;
+        for (int s = 0; s < (int)slots.size(); ++s) {
+            const RcrTask& tk = pl.h_tasks[slot_task[s]];
+            sets[tk.coax_off].push_back(s);
+            set_pc[tk.coax_off] = tk.pc;
+        }
+        std::vector<int32_t> cidx;
+        std::vector<StgCTile> ct;
+        const int q = std::min(p_in, p_out);
+        for (auto& sv : sets) {
+            const int c0 = (int)cidx.size();
+            cidx.insert(cidx.end(), sv.second.begin(), sv.second.end());
+            const int ns = (int)sv.second.size();
+            const int pc = set_pc[sv.first];
+            for (int am = 0; am < q; ++am) {
+                const int nvc = am == 0 ? ns : 2 * ns;
+                const int M = p_out - am, K = p_in - am;
+                const int64_t a_off = sv.first + ((int64_t)am * pc + am) * pc + am;
+                for (int r0 = 0; r0 < M; r0 += SBM)
+                    for (int v0 = 0; v0 < nvc; v0 += SBN)
+                        ct.push_back(StgCTile{a_off, c0, v0, std::min(SBN, nvc - v0), am, r0, pc, M, K});
+            }
+        }
+        lv.nslot = (int)slots.size();
+        lv.nrt = (int)rt.size();
+        lv.nct = (int)ct.size();
+        lv.nbt = (int)bt.size();
+        fb_status st;
+        if ((st = upload(&lv.slots, slots)) || (st = upload(&lv.cidx, cidx)) || (st = upload(&lv.rt, rt)) ||
+            (st = upload(&lv.ct, ct)) || (st = upload(&lv.bt, bt))) {
+            free_level(lv);
+            return fail(st);
+        }
+        *elems = std::max(*elems, (int64_t)lv.nslot * lv.S);
+        P->levels.push_back(lv);
+    }
+    *out = P;
+    return FB_OK;
+}
+
+void fb_stg_free(void*& plan) {
+    StgPlanImpl* P = (StgPlanImpl*)plan;
+    if (!P) return;
+    for (auto& lv : P->levels) free_level(lv);
+    delete P;
+    plan = nullptr;
+}
+
+// Runs the staged passes of a plan for nrhs right-hand sides (set r of the
+// expansions at src / dst + r * rstride), one right-hand side and one level
+// at a time through the staging buffers U and V.
+template <class R>
+static fb_status stg_run(void* plan, const R* rotd, const cx<R>* rph, int64_t per_dir, int prot,
+                         const cx<R>* coax, const cx<R>* src, cx<R>* dst, cx<R>* U, cx<R>* V, cudaStream_t s,
+                         int nrhs, int64_t rstride) {
+    StgPlanImpl* P = (StgPlanImpl*)plan;
+    if (!P) return FB_OK;
+    if (!U || !V) return fb_fail(FB_ERR_STATE, "staged RCR: staging buffers missing");
+    const size_t sm_rc = sizeof(StgSmem<R, false>), sm_c = sizeof(StgSmem<R, true>);
+    FB_CHECK(fb_smem_cap((const void*)k_stg_rot<R>, sm_rc));
+    FB_CHECK(fb_smem_cap((const void*)k_stg_coax<R>, sm_c));
+    FB_CHECK(fb_smem_cap((const void*)k_stg_back<R>, sm_rc));
+    for (int r = 0; r < nrhs; ++r) {
+        const cx<R>* sr = src + r * rstride;
+        cx<R>* dr = dst + r * rstride;
+        for (const StgLevel& lv : P->levels) {
+            if (lv.nrt)
+                k_stg_rot<R><<<lv.nrt, STHREADS, sm_rc, s>>>(lv.rt, lv.slots, rotd, rph, per_dir, prot, sr, U, lv.S);
+            if (lv.nct) k_stg_coax<R><<<lv.nct, STHREADS, sm_c, s>>>(lv.ct, lv.cidx, coax, U, V, lv.S, lv.p_out);
+            if (lv.nbt)
+                k_stg_back<R><<<lv.nbt, STHREADS, sm_rc, s>>>(lv.bt, lv.slots, rotd, rph, per_dir, prot, V, dr, lv.S,
+                                                              lv.p_in, lv.p_out);
+            FB_LAUNCH_CHECK();
+            fb_count_launch(3);
+        }
+    }
+    return FB_OK;
+}
+
+fb_status fb_stg_run_f(void* plan, const float* rotd, const cf* rph, int64_t per_dir, int prot, const cf* coax,
+                       const cf* src, cf* dst, cf* U, cf* V, cudaStream_t s, int nrhs, int64_t rstride) {
+    return stg_run<float>(plan, rotd, rph, per_dir, prot, coax, src, dst, U, V, s, nrhs, rstride);
+}
+fb_status fb_stg_run_d(void* plan, const double* rotd, const cd* rph, int64_t per_dir, int prot, const cd* coax,
+                       const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride) {
+    return stg_run<double>(plan, rotd, rph, per_dir, prot, coax, src, dst, U, V, s, nrhs, rstride);
+}
