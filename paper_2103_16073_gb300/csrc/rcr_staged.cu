@@ -22,10 +22,12 @@
 //      then scatter-added into the target boxes (atomic adds: several pairs
 //      share a target).
 //
-// u is kept per pair in degree-major order (the order of the expansions,
-// (n, m) at n^2 + n + m) and v in order-major order (order m, degrees
-// |m|..p_out-1, contiguous), so each pass writes contiguous runs and the
-// strided gathers fall on reads only.  One CTA computes a 64 x 64 tile of
+// The rotations run folded (even / odd in m, see below: half the
+// multipliers).  u is kept per pair in degree-major order (degree n at n^2,
+// folded within the degree) and v in order-major order (the even part of
+// order m >= 0 at moff(m), the odd part at moff(-m), degrees |m|..p_out-1
+// contiguous), so each pass writes contiguous runs and the strided gathers
+// fall on reads only.  One CTA computes a 64 x 64 tile of
 // one GEMM (256 threads, 4 x 4 complex outputs each, K in chunks of 16,
 // double-buffered shared memory).
 #include <algorithm>
@@ -50,12 +52,12 @@ struct StgSlot {
     int32_t pad;
 };
 // tile of pass R (degree n) or B (degree n'): slots [col0, col0 + ncol) of
-// one polar-angle group, rows [row0, row0 + 64) of the block
+// one polar-angle group, rows [row0, row0 + 64) of the even or odd block
 struct StgTile {
     int32_t col0, ncol;
     int32_t n, row0;
     int32_t adir;      // a direction of the group (its real factors d^n)
-    int32_t pad;
+    int32_t part;      // 0: even (E, Y+) block, 1: odd (O, Y-) block of the folded rotation
 };
 // tile of pass C: virtual columns [vc0, vc0 + nvc) of one |t| group
 // (virtual column v = slot cidx[c0 + v] for m = 0, else (slot cidx[c0 + v/2],
@@ -180,23 +182,41 @@ __device__ __forceinline__ void stg_mainloop(StgSmem<R, CA>& sm, int K, LA load_
     }
 }
 
+// The real factors obey d^n_{-mu,-m} = d^n_{mu,m} (for Q = R_y(-theta)
+// R_z(-phi); equivalently d_{mu,-m} = d_{-mu,m}), so each rotation folds
+// into an "even" and an "odd" GEMM of about half the size: with
+// s_m = x_m + x_{-m}, t_m = x_m - x_{-m} (m > 0), s_0 = x_0,
+//   E_mu = u_mu + u_{-mu} = 2 d_{mu,0} s_0 + sum_{m>0} (d_{mu,m} + d_{mu,-m}) s_m   (mu = 0..n)
+//   O_mu = u_mu - u_{-mu} =                  sum_{m>0} (d_{mu,m} - d_{mu,-m}) t_m   (mu = 1..n)
+// ((n+1)^2 + n^2 real multipliers instead of (2n+1)^2).  The coaxial blocks
+// depend on |m| only, so they map E to E and O to O; the back-rotation
+// folds the same way (y_{-m'} = sum_mu d_{mu,m'} v_{-mu}):
+//   Y+_{m'} = y_{m'} + y_{-m'} = d_{0,m'} E_0 + sum_{mu>0} (d_{mu,m'} + d_{-mu,m'}) E_mu
+//   Y-_{m'} = y_{m'} - y_{-m'} =               sum_{mu>0} (d_{mu,m'} - d_{-mu,m'}) O_mu
+// and y_{+-m'} = (Y+ +- Y-)/2.  Folded layout of a degree-n block of u and
+// v: E_0..E_n at offsets 0..n, O_1..O_n at n+1..2n.
+//
 // ------------------------------------------------------------- pass R ----
-// U[slot][n^2 + row] = sum_m d^n_{row-n, m-n} e^{i (m-n) phi_slot} src[slot][n^2 + m]
+// part 0: U[slot][n^2 + mu] = E_mu (mu = 0..n); part 1: U[slot][n^2 + n + mu] = O_mu
+// (mu = 1..n), from x_m = e^{i m phi_slot} src[slot][n^2 + n + m].
 template <class R>
 __global__ void __launch_bounds__(STHREADS, 2) k_stg_rot(const StgTile* __restrict__ tiles,
-                                                      const StgSlot* __restrict__ slots,
-                                                      const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
-                                                      int64_t per_dir, int prot, const cx<R>* __restrict__ src,
-                                                      cx<R>* __restrict__ U, int S) {
+                                                         const StgSlot* __restrict__ slots,
+                                                         const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
+                                                         int64_t per_dir, int prot, const cx<R>* __restrict__ src,
+                                                         cx<R>* __restrict__ U, int S) {
     extern __shared__ __align__(16) unsigned char stg_smem[];
     StgSmem<R, false>& sm = *reinterpret_cast<StgSmem<R, false>*>(stg_smem);
     const StgTile tl = tiles[blockIdx.x];
     const int n = tl.n, w = 2 * n + 1;
+    const int part = tl.part;
+    const int lo = part;                  // first mu (rows) and first m (K) of the block
+    const int nb = n + 1 - part;          // rows = K = n + 1 (even) or n (odd)
     const int tid = threadIdx.x;
     if (tid < SBN) {
         if (tid < tl.ncol) {
             StgSlot sl = slots[tl.col0 + tid];
-            sm.col_off[tid] = sl.src_off + (int64_t)n * n;
+            sm.col_off[tid] = sl.src_off + (int64_t)n * n + n;   // entry (n, 0)
             sm.col_aux[tid] = sl.dir;
         } else {
             sm.col_off[tid] = -1;
@@ -204,23 +224,34 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_rot(const StgTile* __restri
         }
     }
     __syncthreads();
-    const R* A = rotd + (int64_t)tl.adir * per_dir + rot_off(n) + (int64_t)tl.row0 * w;
-    const int M = min(SBM, w - tl.row0);
-    auto load_a = [&](int r, int k) -> R { return (r < M && k < w) ? A[(int64_t)r * w + k] : R(0); };
+    const R* Dc = rotd + (int64_t)tl.adir * per_dir + rot_off(n) + (int64_t)n * w + n;   // d_{0,0}
+    const int M = min(SBM, nb - tl.row0);
+    auto load_a = [&](int r, int k) -> R {
+        if (r >= M || k >= nb) return R(0);
+        const int mu = lo + tl.row0 + r, m = lo + k;
+        const R* row = Dc + (int64_t)mu * w;
+        if (m == 0) return R(2) * row[0];
+        return part ? row[m] - row[-m] : row[m] + row[-m];
+    };
     auto load_x = [&](int c, int k) -> cx<R> {
         const int64_t o = sm.col_off[c];
-        if (o < 0 || k >= w) return mk<R>(0, 0);
-        const cx<R> ph = rph[(int64_t)sm.col_aux[c] * (2 * prot - 1) + (prot - 1) + (k - n)];
-        return src[o + k] * ph;
+        if (o < 0 || k >= nb) return mk<R>(0, 0);
+        const int m = lo + k;
+        const cx<R>* ph = rph + (int64_t)sm.col_aux[c] * (2 * prot - 1) + (prot - 1);
+        const cx<R> xp = src[o + m] * ph[m];
+        if (m == 0) return xp;
+        const cx<R> xm = src[o - m] * ph[-m];
+        return part ? xp - xm : xp + xm;
     };
     cx<R> acc[4][4];
-    stg_mainloop<R, false, true>(sm, w, load_a, load_x, acc);
+    stg_mainloop<R, false, true>(sm, nb, load_a, load_x, acc);
     const int ty = tid >> 4, tx = tid & 15;
+    const int obase = n * n + (part ? n : 0) + lo + tl.row0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int c = tx * 4 + j;
         if (c >= tl.ncol) continue;
-        cx<R>* u = U + (int64_t)(tl.col0 + c) * S + (int64_t)n * n + tl.row0;
+        cx<R>* u = U + (int64_t)(tl.col0 + c) * S + obase;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = ty * 4 + i;
@@ -230,12 +261,14 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_rot(const StgTile* __restri
 }
 
 // ------------------------------------------------------------- pass C ----
-// V[slot][moff(s am) + row] = sum_k C^{am}_{am+row, am+k} U[slot][(am+k)^2 + (am+k) + s am]
+// V[slot][moff(+am) + row] = sum_k C^{am}_{am+row, am+k} E^{am}_{am+k}   (even columns)
+// V[slot][moff(-am) + row] = sum_k C^{am}_{am+row, am+k} O^{am}_{am+k}   (odd columns, am > 0)
+// with E^{am}_n = U[slot][n^2 + am], O^{am}_n = U[slot][n^2 + n + am].
 template <class R>
 __global__ void __launch_bounds__(STHREADS, 2) k_stg_coax(const StgCTile* __restrict__ tiles,
-                                                       const int32_t* __restrict__ cidx,
-                                                       const cx<R>* __restrict__ coax, const cx<R>* __restrict__ U,
-                                                       cx<R>* __restrict__ V, int S, int pout) {
+                                                          const int32_t* __restrict__ cidx,
+                                                          const cx<R>* __restrict__ coax, const cx<R>* __restrict__ U,
+                                                          cx<R>* __restrict__ V, int S, int pout) {
     extern __shared__ __align__(16) unsigned char stg_smem[];
     StgSmem<R, true>& sm = *reinterpret_cast<StgSmem<R, true>*>(stg_smem);
     const StgCTile tl = tiles[blockIdx.x];
@@ -245,9 +278,9 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_coax(const StgCTile* __rest
         if (tid < tl.nvc) {
             const int v = tl.vc0 + tid;
             const int slot = am == 0 ? cidx[tl.c0 + v] : cidx[tl.c0 + (v >> 1)];
-            const int sg = (am == 0 || !(v & 1)) ? 1 : -1;
+            const int odd = (am != 0 && (v & 1)) ? 1 : 0;
             sm.col_off[tid] = (int64_t)slot * S;
-            sm.col_aux[tid] = sg * am;   // the order m of this column
+            sm.col_aux[tid] = odd;
         } else {
             sm.col_off[tid] = -1;
             sm.col_aux[tid] = 0;
@@ -264,7 +297,7 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_coax(const StgCTile* __rest
         const int64_t o = sm.col_off[c];
         if (o < 0 || k >= K) return mk<R>(0, 0);
         const int nn = am + k;
-        return U[o + (int64_t)nn * nn + nn + sm.col_aux[c]];
+        return U[o + (int64_t)nn * nn + (sm.col_aux[c] ? nn : 0) + am];
     };
     cx<R> acc[4][4];
     stg_mainloop<R, true, true>(sm, K, load_a, load_x, acc);
@@ -273,7 +306,7 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_coax(const StgCTile* __rest
     for (int j = 0; j < 4; ++j) {
         const int c = tx * 4 + j;
         if (c >= tl.nvc) continue;
-        cx<R>* v = V + sm.col_off[c] + moff(sm.col_aux[c], pout) + tl.row0;
+        cx<R>* v = V + sm.col_off[c] + moff(sm.col_aux[c] ? -am : am, pout) + tl.row0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = ty * 4 + i;
@@ -283,8 +316,9 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_coax(const StgCTile* __rest
 }
 
 // ------------------------------------------------------------- pass B ----
-// dst[slot][n'^2 + row] += e^{-i m' phi} sum_mu d^{n'}_{mu, m'} V[slot][moff(mu) + n' - |mu|],
-// m' = row - n', |mu| <= min(n', p_in - 1)
+// part 0: Y+_{m'} (m' = 0..n) from E_mu = V[slot][moff(+mu) + n - mu], mu = 0..mmax;
+// part 1: Y-_{m'} (m' = 1..n) from O_mu = V[slot][moff(-mu) + n - mu], mu = 1..mmax;
+// mmax = min(n, p_in - 1).  dst[slot][n^2 + n +- m'] += e^{-+ i m' phi} (Y+ +- Y-)/2.
 template <class R>
 __device__ __forceinline__ void atomic_add_cx(cx<R>* d, const cx<R>& v);
 template <>
@@ -299,21 +333,24 @@ __device__ __forceinline__ void atomic_add_cx<double>(cd* d, const cd& v) {
 
 template <class R>
 __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restrict__ tiles,
-                                                       const StgSlot* __restrict__ slots,
-                                                       const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
-                                                       int64_t per_dir, int prot, const cx<R>* __restrict__ V,
-                                                       cx<R>* __restrict__ dst, int S, int pin, int pout) {
+                                                          const StgSlot* __restrict__ slots,
+                                                          const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
+                                                          int64_t per_dir, int prot, const cx<R>* __restrict__ V,
+                                                          cx<R>* __restrict__ dst, int S, int pin, int pout) {
     extern __shared__ __align__(16) unsigned char stg_smem[];
     StgSmem<R, false>& sm = *reinterpret_cast<StgSmem<R, false>*>(stg_smem);
     const StgTile tl = tiles[blockIdx.x];
     const int n = tl.n, w = 2 * n + 1;
+    const int part = tl.part;
+    const int lo = part;
     const int mmax = min(n, pin - 1);
-    const int K = 2 * mmax + 1;
+    const int nrow = n + 1 - part;          // m' = lo .. n
+    const int K = mmax + 1 - part;          // mu = lo .. mmax
     const int tid = threadIdx.x;
     if (tid < SBN) {
         if (tid < tl.ncol) {
             StgSlot sl = slots[tl.col0 + tid];
-            sm.col_off[tid] = sl.dst_off;
+            sm.col_off[tid] = sl.dst_off + (int64_t)n * n + n;   // entry (n, 0)
             sm.col_aux[tid] = sl.dir;
         } else {
             sm.col_off[tid] = -1;
@@ -321,32 +358,43 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restr
         }
     }
     __syncthreads();
-    // A[row][k] = d^{n}_{mu, m'} with mu = k - mmax, m' = row0 + row - n
-    const R* A = rotd + (int64_t)tl.adir * per_dir + rot_off(n) + (int64_t)(n - mmax) * w + tl.row0;
-    const int M = min(SBM, w - tl.row0);
-    auto load_a = [&](int r, int k) -> R { return (r < M && k < K) ? A[(int64_t)k * w + r] : R(0); };
+    const R* Dc = rotd + (int64_t)tl.adir * per_dir + rot_off(n) + (int64_t)n * w + n;   // d_{0,0}
+    const int M = min(SBM, nrow - tl.row0);
+    auto load_a = [&](int r, int k) -> R {
+        if (r >= M || k >= K) return R(0);
+        const int mp = lo + tl.row0 + r, mu = lo + k;
+        if (mu == 0) return Dc[mp];
+        const R a = Dc[(int64_t)mu * w + mp], b = Dc[-(int64_t)mu * w + mp];
+        return part ? a - b : a + b;
+    };
     const int64_t col_base = (int64_t)tl.col0 * S;
     auto load_x = [&](int c, int k) -> cx<R> {
         if (c >= tl.ncol || k >= K) return mk<R>(0, 0);
-        const int mu = k - mmax;
-        const int amu = mu < 0 ? -mu : mu;
-        return V[col_base + (int64_t)c * S + moff(mu, pout) + (n - amu)];
+        const int mu = lo + k;
+        return V[col_base + (int64_t)c * S + moff(part ? -mu : mu, pout) + (n - mu)];
     };
     cx<R> acc[4][4];
     stg_mainloop<R, false, false>(sm, K, load_a, load_x, acc);
     const int ty = tid >> 4, tx = tid & 15;
+    const R sgn = part ? R(-1) : R(1);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int c = tx * 4 + j;
         if (c >= tl.ncol) continue;
         const cx<R>* ph = rph + (int64_t)sm.col_aux[c] * (2 * prot - 1) + (prot - 1);
-        cx<R>* d = dst + sm.col_off[c] + (int64_t)n * n + tl.row0;
+        cx<R>* d = dst + sm.col_off[c];   // entry (n, 0) of the target
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = ty * 4 + i;
             if (r >= M) continue;
-            const int m1 = tl.row0 + r - n;
-            atomic_add_cx<R>(d + r, acc[i][j] * conjg(ph[m1]));
+            const int mp = lo + tl.row0 + r;
+            const cx<R> h = R(0.5) * acc[i][j];
+            if (mp == 0) {
+                atomic_add_cx<R>(d, h);
+            } else {
+                atomic_add_cx<R>(d + mp, h * conjg(ph[mp]));
+                atomic_add_cx<R>(d - mp, sgn * (h * ph[mp]));
+            }
         }
     }
 }
@@ -458,14 +506,21 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_rep, int
                 }
             }
             const int g1 = (int)slots.size();
+            // folded blocks: even rows n + 1, odd rows n (none for n = 0)
             for (int n = 0; n < p_in; ++n)
-                for (int r0 = 0; r0 < 2 * n + 1; r0 += SBM)
-                    for (int c0 = g0; c0 < g1; c0 += SBN)
-                        rt.push_back(StgTile{c0, std::min(SBN, g1 - c0), n, r0, rep, 0});
-            for (int n = 0; n < p_out; ++n)
-                for (int r0 = 0; r0 < 2 * n + 1; r0 += SBM)
-                    for (int c0 = g0; c0 < g1; c0 += SBN)
-                        bt.push_back(StgTile{c0, std::min(SBN, g1 - c0), n, r0, rep, 0});
+                for (int part = 0; part < 2; ++part)
+                    for (int r0 = 0; r0 < n + 1 - part; r0 += SBM)
+                        for (int c0 = g0; c0 < g1; c0 += SBN)
+                            rt.push_back(StgTile{c0, std::min(SBN, g1 - c0), n, r0, rep, part});
+            for (int n = 0; n < p_out; ++n) {
+                const int mmax = std::min(n, p_in - 1);
+                for (int part = 0; part < 2; ++part) {
+                    if (mmax + 1 - part <= 0) continue;   // no inner terms
+                    for (int r0 = 0; r0 < n + 1 - part; r0 += SBM)
+                        for (int c0 = g0; c0 < g1; c0 += SBN)
+                            bt.push_back(StgTile{c0, std::min(SBN, g1 - c0), n, r0, rep, part});
+                }
+            }
         }
         // |t| groups (coaxial sets) of the slots
         std::map<int64_t, std::vector<int32_t>> sets;   // coax_off -> slots
