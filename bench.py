@@ -244,62 +244,81 @@ def rcr_flops(p_out, p_in):
     return 8.0 * (rot + coax)
 
 
-def roofline(fb, A32, tree, ph32, ph64, iters, true_mv, pk, fp32_peak, fp64_peak, ph_low=None, low_mv=0):
-    """Rooflines of the translation kernels of a solve and the dominant one
-    (largest estimated device time per step: per-launch CUDA-event phase
-    times x launches per step, the inner operator's matvecs included).
-    Algorithmic flops are the RCR counts of the translations each launch
-    performs (rcr_flops)."""
-    L, p, tc, pairs, nb = level_counts(fb, A32, tree)
-    # k_rcr<double>: the FP64 operator's M2L (all levels) in the true residual
-    alg64 = sum(float(pairs[l]) * rcr_flops(p[l], p[l]) for l in range(2, L + 1))
-    t64 = ph64["m2l"] / 1e3
-    # k_rcr<float>: M2L of the levels not on the tensor cores, per Krylov matvec
-    alg32 = sum(float(pairs[l]) * rcr_flops(p[l], p[l]) for l in range(2, L + 1) if not tc[l])
-    t32 = ph32["m2l"] / 1e3
-    # k_trans_tc: M2L of the tensor-core levels (3xTF32), per Krylov matvec
-    algtc = sum(float(pairs[l]) * rcr_flops(p[l], p[l]) for l in range(2, L + 1) if tc[l])
-    ttc = ph32["m2l_tc"] / 1e3
-    execd = 0.0
-    for l in range(2, L + 1):
-        if tc[l]:
-            P2 = 2 * p[l] ** 2
-            execd += float(pairs[l]) * (-(-P2 // 128) * 128) * (-(-P2 // 16) * 16) * 2.0 * 3.0
-    # TF32 tensor peak from the measured BF16 peak x nominal TF32/BF16 ratio; 3 split passes
-    tf32 = float(pk.get("bf16_tflops", 1990.0)) * (1.1 / 2.25)
-    kern = {
-        "k_rcr<double>": {"what": "M2L of the FP64 operator (true residual), all levels", "bound": "alu",
-                          "launch_ms": t64 * 1e3, "per_step_ms": (ph64["m2l"] + ph64["m2m"] + ph64["l2l"]) * true_mv,
-                          "alg": alg64, "peak": fp64_peak,
-                          "peak_kind": "FP64 FMA throughput measured by fb_measure_alu_peaks"},
-        "k_rcr<float>": {"what": "M2L of the mixed operator, RCR levels", "bound": "alu", "launch_ms": t32 * 1e3,
-                         "per_step_ms": (ph32["m2l"] + ph32["m2m"] + ph32["l2l"]) * iters
-                         + ((ph_low["m2l"] + ph_low["m2m"] + ph_low["l2l"]) * low_mv if ph_low else 0.0),
-                         "alg": alg32,
-                         "peak": fp32_peak, "peak_kind": "FP32 FMA throughput measured by fb_measure_alu_peaks"},
-        "k_trans_tc": {"what": "M2L of the mixed operator, tensor-core levels (tcgen05 3xTF32)", "bound": "tensor",
-                       "launch_ms": ttc * 1e3,
-                       "per_step_ms": ph32["m2l_tc"] * iters + (ph_low["m2l_tc"] * low_mv if ph_low else 0.0),
-                       "alg": algtc,
-                       "peak": tf32 / 3.0,
-                       "peak_kind": "measured BF16 burst x 1.1/2.25 (TF32) / 3 split passes, of measured"},
-    }
+FAMILY = {("f32", "stg"): "k_stg<float>", ("f32", "tiles"): "k_rcr<float>", ("f32", "tc"): "k_trans_tc",
+          ("f64", "stg"): "k_stg<double>", ("f64", "tiles"): "k_rcr<double>"}
+FAMILY_WHAT = {
+    "k_stg<float>": "staged RCR M2L (k_stg_rot / k_stg_coax / k_stg_back, FP32): batched GEMMs per polar angle "
+                    "and per |t|",
+    "k_rcr<float>": "per-pair RCR M2L tiles (FP32)",
+    "k_trans_tc": "tensor-core M2L (tcgen05 3xTF32, composed matrices)",
+    "k_stg<double>": "staged RCR M2L (FP64, true residual)",
+    "k_rcr<double>": "per-pair RCR M2L tiles (FP64, true residual)",
+}
+
+
+def m2l_levels(tune, p, pairs):
+    """Per level of an autotuned operator: (form, device ms of its M2L pass,
+    algorithmic flops) from the autotuner's timings of the installed form."""
     out = {}
-    for name, k in kern.items():
-        t = k["launch_ms"] / 1e3
-        ach = k["alg"] / t / 1e12 if t > 0 and k["alg"] > 0 else 0.0
-        out[name] = {"what": k["what"], "bound": k["bound"], "achieved": round(ach, 3), "peak": round(k["peak"], 3),
-                     "unit": "TFLOP/s", "frac": round(ach / k["peak"], 4) if k["peak"] else None,
-                     "launch_ms": round(k["launch_ms"], 4), "est_ms_per_step": round(k["per_step_ms"], 3),
-                     "algorithmic_flops_per_launch": k["alg"], "peak_kind": k["peak_kind"]}
-    out["k_trans_tc"]["executed_tensor_flops_per_launch"] = execd
-    out["k_trans_tc"]["executed_tensor_tflops"] = round(execd / ttc / 1e12, 1) if ttc > 0 else None
+    for l, t in (tune or {}).items():
+        l = int(l)
+        ch = t["choice"]
+        form, ms = ("tc", t["m2l_tensor"]) if ch & 1 else (("stg", t["m2l_staged"]) if ch & 4 else
+                                                            ("tiles", t["m2l_rcr"]))
+        if ms is None:
+            continue
+        out[l] = (form, ms, float(pairs[l]) * rcr_flops(int(p[l]), int(p[l])))
+    return out
+
+
+def roofline(fb, P, iters, true_mv, pk, fp32_peak, fp64_peak):
+    """Rooflines of the M2L kernel families of a solve and the dominant one.
+    A family's launch is its part of one M2L pass of one operator (the levels
+    the autotuner gave it, timed there with CUDA events on the device); its
+    achieved rate is algorithmic flops (rcr_flops per box pair, summed over
+    those levels) over that time, weighted over the operators by how often a
+    solve applies each (mixed: outer iterations, inner low-accuracy operator:
+    outer x inner iterations, FP64: true residuals)."""
+    tune = P["tune"]
+    L, _, _, pairs, _ = level_counts(fb, P["A32"], P["tree"])
+    tf32 = float(pk.get("bf16_tflops", 1990.0)) * (1.1 / 2.25)
+    peaks_ = {"f32": (fp32_peak, "FP32 FMA throughput measured by fb_measure_alu_peaks"),
+              "f64": (fp64_peak, "FP64 FMA throughput measured by fb_measure_alu_peaks")}
+    fam = {}
+    for key, op, prec, count in (("mixed", "A32", "f32", iters), ("inner", "Alow", "f32", iters * INNER_ITERS),
+                                 ("fp64", "A64", "f64", true_mv)):
+        p = fb.fb_operator_info(P[op])[2]
+        for l, (form, ms, alg) in m2l_levels(tune.get(key), p, pairs).items():
+            name = FAMILY[(prec, form)]
+            f = fam.setdefault(name, {"ms": 0.0, "alg": 0.0, "step_ms": 0.0, "per_op": {}, "prec": prec})
+            f["ms"] += ms * count
+            f["alg"] += alg * count
+            f["step_ms"] += ms * count
+            po = f["per_op"].setdefault(key, {"levels": [], "launch_ms": 0.0, "alg_flops": 0.0, "per_step": count})
+            po["levels"].append(l)
+            po["launch_ms"] = round(po["launch_ms"] + ms, 4)
+            po["alg_flops"] += alg
+    out = {}
+    for name, f in fam.items():
+        if name == "k_trans_tc":
+            peak, kind, bound = tf32 / 3.0, "measured BF16 burst x 1.1/2.25 (TF32) / 3 split passes, of measured", "tensor"
+        else:
+            (peak, kind), bound = peaks_[f["prec"]], "alu"
+        ach = f["alg"] / (f["ms"] / 1e3) / 1e12 if f["ms"] > 0 else 0.0
+        out[name] = {"what": FAMILY_WHAT[name], "bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3),
+                     "unit": "TFLOP/s", "frac": round(ach / peak, 4) if peak else None,
+                     "est_ms_per_step": round(f["step_ms"], 2), "per_operator": f["per_op"], "peak_kind": kind}
+    if not out:
+        return None, out
     dom = max(out, key=lambda k: out[k]["est_ms_per_step"])
     d = out[dom]
+    launches = [v for v in d["per_operator"].values()]
     rf = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
-          "frac": d["frac"], "traffic": traffic_for(dom), "peak_kind": d["peak_kind"],
-          "algorithmic_flops_per_launch": d["algorithmic_flops_per_launch"], "launch_ms": d["launch_ms"],
-          "what": d["what"]}
+          "frac": d["frac"], "traffic": traffic_for(dom), "peak_kind": d["peak_kind"], "what": d["what"],
+          "est_ms_per_step": d["est_ms_per_step"],
+          "launch": {k: {"levels": v["levels"], "launch_ms": v["launch_ms"], "algorithmic_flops": v["alg_flops"]}
+                     for k, v in d["per_operator"].items()},
+          "algorithmic_flops": "rcr_flops per box pair: 8 x (sum_{n<p}(2n+1)^2 x 2 + sum_m (p-|m|)^2)"}
     return rf, out
 
 
@@ -451,9 +470,7 @@ def run_ours(args):
     e2e_s = statistics.median(e2e_t)
 
     fp32_peak, fp64_peak = fb.fb_measure_alu_peaks()
-    low_mv = iters * INNER_ITERS
-    rf, kernels = roofline(fb, P["A32"], P["tree"], ph, ph64, iters, res_true_matvecs(infos), pk, fp32_peak,
-                           fp64_peak, ph_low, low_mv)
+    rf, kernels = roofline(fb, P, iters, res_true_matvecs(infos), pk, fp32_peak, fp64_peak)
     L, p, tc, pairs, nb = level_counts(fb, P["A32"], P["tree"])
     setup_s = P["setup_s"]
     destroy_problem(fb, P)

@@ -566,6 +566,16 @@ typedef struct fb_batch_opts {
  * solve converged, else the first failing status (per-job status set). */
 FB_API fb_status fb_batch_solve(fb_batch_job* jobs, int njobs, const fb_batch_opts* opts);
 
+/* Partition of independent jobs (the (frequency, source) solves of a sweep,
+ * Sec. 4: every frequency and source is solved on its own, so a sweep
+ * shards over GPUs without any exchange) across nranks ranks: largest cost
+ * first, each job to the least loaded rank so far (ties: lower job index
+ * first, lower rank).  cost: njobs finite values >= 0 (host; e.g. the
+ * predicted time, N x iterations); owner: njobs ints (host, out); load:
+ * nranks doubles (host, out, may be NULL).  Host only: launches nothing and
+ * needs no GPU.  Errors: FB_ERR_ARG. */
+FB_API fb_status fb_batch_partition(const double* cost, int njobs, int nranks, int* owner, double* load);
+
 /* ------------------------------------------------------------ receivers -- */
 
 /* Field at interior points by Green's identity (Eq. dbem1):

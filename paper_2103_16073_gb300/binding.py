@@ -718,3 +718,17 @@ def fb_pulse_synthesis(psi, freqs, df, dt, nt, pulse_dt, stream=None):
     _check(lib.fb_pulse_synthesis(_cuda_ptr(psi, "psi"), f.ctypes.data, int(f.size), int(psi.shape[1]), float(df),
                                   float(dt), int(nt), float(pulse_dt), C.c_void_p(out.data_ptr()), _stream(stream)))
     return out
+
+
+lib.fb_batch_partition.restype = C.c_int
+lib.fb_batch_partition.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p]
+
+
+def fb_batch_partition(costs, nranks):
+    """Owner rank of every job (largest cost first to the least loaded rank)
+    and the resulting load per rank (host only, no GPU)."""
+    c = np.ascontiguousarray(costs, dtype=np.float64)
+    owner = np.zeros(c.shape[0], np.int32)
+    load = np.zeros(int(nranks), np.float64)
+    _check(lib.fb_batch_partition(c.ctypes.data, c.shape[0], int(nranks), owner.ctypes.data, load.ctypes.data))
+    return owner, load

@@ -165,3 +165,31 @@ fb_status fb_batch_solve_impl(fb_batch_job* jobs, int njobs, const fb_batch_opts
     if (worst != FB_OK) fb_set_error(worst, first_msg);
     return worst;
 }
+
+// Largest-first greedy bin-packing of independent jobs over ranks (Sec. 4:
+// frequencies and sources are independent solves, so a sweep shards over
+// GPUs without any exchange): jobs in order of decreasing cost (index order
+// on ties), each to the rank with the least load so far (lowest rank on
+// ties).  The makespan is within 4/3 of the optimum (Graham's bound for
+// this rule).  Host only.
+extern "C" fb_status fb_batch_partition(const double* cost, int njobs, int nranks, int* owner, double* load) {
+    if (njobs < 0 || nranks < 1 || (njobs > 0 && (!cost || !owner)))
+        return fb_fail(FB_ERR_ARG, "fb_batch_partition: bad arguments");
+    for (int i = 0; i < njobs; ++i)
+        if (!(cost[i] >= 0.0) || !std::isfinite(cost[i]))
+            return fb_fail(FB_ERR_ARG, "fb_batch_partition: costs must be finite and >= 0");
+    std::vector<int> order(njobs);
+    for (int i = 0; i < njobs; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+    std::vector<double> ld(nranks, 0.0);
+    for (int i : order) {
+        int r = 0;
+        for (int q = 1; q < nranks; ++q)
+            if (ld[q] < ld[r]) r = q;
+        owner[i] = r;
+        ld[r] += cost[i];
+    }
+    if (load)
+        for (int q = 0; q < nranks; ++q) load[q] = ld[q];
+    return FB_OK;
+}
