@@ -48,7 +48,7 @@ METRIC = "FGMRES time-to-solve @1e-4 & matvecs/s: mixed+learned vs plain FP64, 1
 TOL = 1e-4
 RESTART = 40
 D0, PMIN = 6.0, 12                              # order rule of the operators (1e-5 FP64 FMM target)
-INNER_D0, INNER_PMIN, INNER_ITERS = 1.0, 4, 6   # inner-outer preconditioner (low-accuracy FMM)
+INNER_D0, INNER_PMIN, INNER_ITERS = 0.5, 2, 14  # inner-outer preconditioner (low-accuracy FMM)
 
 WORKLOADS = {
     "largest": ("cfg_largest", "shoebox 6.5x5.5x4.2 m, 5 kHz, N=2644104 flat triangles (lambda/6), "
@@ -207,6 +207,7 @@ def build_problem(fb, W, torch, wl, rank, forms="", forms_inner=""):
     fb.fb_operator_use_graphs(Alow, True)
     pclow = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
     inner = fb.fb_precond_create_inner(A32, Alow, pclow, INNER_ITERS)
+    fb.fb_precond_use_graphs(inner, True)
     g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
     fb.fb_gamma_monopole(mesh, wl.k, wl.sources[0], g)
     b = torch.empty_like(g)

@@ -553,14 +553,21 @@ typedef struct fb_batch_opts {
     int max_rhs;              /* sources per batched solve (<= 0: 8)          */
     int fp64_judge;           /* 1: true residual by the FP64 FMM operator    */
     int lookahead;            /* 1: build job i+1 while job i solves          */
+    int inner_iters;          /* > 0: inner-outer preconditioner (Sec. 4) with
+                                 this many GMRES steps on a low-accuracy mixed
+                                 FMM (all sources of a batch in lockstep,
+                                 replayed as captured graphs); 0: block Jacobi */
+    double inner_d0;          /* order rule of the inner operator (<= 0: 0.5) */
+    int inner_pmin;           /* (<= 0: 2)                                    */
 } fb_batch_opts;
 
 /* Runs a batch (a frequency sweep with several sources per frequency, as in
  * the paper's experiments, Sec. 4): jobs in order of decreasing predicted
  * cost (sources x N x p_leaf^2); per job the mixed FMM operator, block
- * Jacobi, the FP64 operators (b = L gamma, true residual) and, if asked, the
- * autotuned translation forms are built once, then the job's sources are
- * solved max_rhs at a time by fb_fgmres_solve_multi.  With lookahead a host
+ * Jacobi (or the inner-outer preconditioner on a low-accuracy FMM), the FP64
+ * operators (b = L gamma, true residual) and, if asked, the autotuned
+ * translation forms are built once, then the job's sources are solved
+ * max_rhs at a time by fb_fgmres_solve_multi.  With lookahead a host
  * thread builds the next job on a second stream while the current one
  * solves.  Operators are released after each job.  Returns FB_OK when every
  * solve converged, else the first failing status (per-job status set). */

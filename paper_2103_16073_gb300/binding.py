@@ -430,7 +430,7 @@ class BatchJob(C.Structure):
 class BatchOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int), ("d0", C.c_double),
                 ("pmin", C.c_int), ("autotune", C.c_int), ("max_rhs", C.c_int), ("fp64_judge", C.c_int),
-                ("lookahead", C.c_int)]
+                ("lookahead", C.c_int), ("inner_iters", C.c_int), ("inner_d0", C.c_double), ("inner_pmin", C.c_int)]
 
 
 lib.fb_batch_solve.restype = C.c_int
@@ -438,7 +438,7 @@ lib.fb_batch_solve.argtypes = [C.POINTER(BatchJob), C.c_int, C.POINTER(BatchOpts
 
 
 def fb_batch_solve(jobs, tol=1e-4, restart=40, maxit=3000, d0=6.0, pmin=12, autotune=True, max_rhs=8,
-                   fp64_judge=True, lookahead=True):
+                   fp64_judge=True, lookahead=True, inner_iters=0, inner_d0=0.5, inner_pmin=2):
     """jobs: list of dicts {mesh, tree, k, src [nsrc,3], x (CUDA complex128 [nsrc,N])}.
     Returns one dict per job: {status, setup_ms, solve_ms, order, infos}."""
     arr = (BatchJob * len(jobs))()
@@ -454,7 +454,7 @@ def fb_batch_solve(jobs, tol=1e-4, restart=40, maxit=3000, d0=6.0, pmin=12, auto
                           j["tree"].value if hasattr(j["tree"], "value") else j["tree"], float(j["k"]),
                           src.shape[0], src.ctypes.data, x.data_ptr(), infos, 0.0, 0.0, 0, -1)
     o = BatchOpts(float(tol), int(restart), int(maxit), float(d0), int(pmin), int(bool(autotune)), int(max_rhs),
-                  int(bool(fp64_judge)), int(bool(lookahead)))
+                  int(bool(fp64_judge)), int(bool(lookahead)), int(inner_iters), float(inner_d0), int(inner_pmin))
     st = lib.fb_batch_solve(arr, len(jobs), C.byref(o))
     if st not in (FB_OK, 3, 5):
         _check(st)

@@ -26,10 +26,18 @@ struct JobState {
     fb_op* A64 = nullptr;
     fb_op* L64 = nullptr;
     fb_precond* pc = nullptr;
+    fb_op* Alow = nullptr;        // inner-outer: low-accuracy operator,
+    fb_precond* pclow = nullptr;  // its block Jacobi,
+    fb_precond* inner = nullptr;  // and the preconditioner of the solve
     fb_status st = FB_OK;
     std::string msg;          // error text of a failed setup (kept per thread by the library)
     double setup_ms = 0;
     void release() {
+        fb_precond_destroy(inner);
+        fb_precond_destroy(pclow);
+        fb_operator_destroy(Alow);
+        inner = pclow = nullptr;
+        Alow = nullptr;
         fb_precond_destroy(pc);
         fb_operator_destroy(A32);
         fb_operator_destroy(A64);
@@ -52,9 +60,16 @@ void setup_job(const fb_batch_job& jb, const fb_batch_opts& o, cudaStream_t s, J
         if (o.fp64_judge)
             FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_FP64_FMM, o.d0, o.pmin, s, &js.A64));
         FB_CHECK(fb_precond_create(js.A32, FB_PC_BLOCK_JACOBI, s, &js.pc));
-        if (o.autotune) {
-            int nrhs = std::max(1, std::min(jb.nsrc, o.max_rhs));
-            FB_CHECK(fb_operator_autotune(js.A32, nrhs, s, nullptr, nullptr));
+        const int nrhs = std::max(1, std::min(jb.nsrc, o.max_rhs));
+        if (o.autotune) FB_CHECK(fb_operator_autotune(js.A32, nrhs, s, nullptr, nullptr));
+        if (o.inner_iters > 0) {
+            FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_MIXED_FMM, o.inner_d0, o.inner_pmin, s,
+                                        &js.Alow));
+            if (o.autotune) FB_CHECK(fb_operator_autotune(js.Alow, nrhs, s, nullptr, nullptr));
+            FB_CHECK(fb_precond_create(js.Alow, FB_PC_BLOCK_JACOBI, s, &js.pclow));
+            FB_CHECK(fb_precond_create_inner(js.A32, js.Alow, js.pclow, o.inner_iters, s, &js.inner));
+            FB_CHECK(fb_operator_use_graphs(js.Alow, 1));
+            FB_CHECK(fb_precond_use_graphs(js.inner, 1));
         }
         FB_CUDA(cudaStreamSynchronize(s));
         return FB_OK;
@@ -86,7 +101,8 @@ fb_status solve_job(fb_batch_job& jb, const fb_batch_opts& o, cudaStream_t s, Jo
         st = fb_operator_apply_multi(js.L64, (const double*)(G + q0 * n), (double*)(B + q0 * n), r, FB_MEM_DEVICE, s);
         if (st != FB_OK) break;
         fb_solver_opts so{o.tol, o.restart, o.maxit, 4, 0.0, js.A64};
-        fb_status sv = fb_fgmres_solve_multi(js.A32, js.pc, (const double*)(B + q0 * n), jb.x + 2 * q0 * n, r, &so,
+        fb_status sv = fb_fgmres_solve_multi(js.A32, js.inner ? js.inner : js.pc, (const double*)(B + q0 * n),
+                                             jb.x + 2 * q0 * n, r, &so,
                                              jb.info ? jb.info + q0 : nullptr, FB_MEM_DEVICE, s);
         if (sv != FB_OK && jb.status == FB_OK) jb.status = sv;
         if (sv != FB_OK && sv != FB_ERR_NOCONV && sv != FB_ERR_NAN) st = sv;
@@ -107,6 +123,9 @@ fb_status fb_batch_solve_impl(fb_batch_job* jobs, int njobs, const fb_batch_opts
     if (o.maxit < 1) o.maxit = 3000;
     if (!(o.d0 > 0)) o.d0 = 6.0;
     if (o.pmin < 1) o.pmin = 12;
+    if (o.inner_iters < 0) o.inner_iters = 0;
+    if (!(o.inner_d0 > 0)) o.inner_d0 = 0.5;
+    if (o.inner_pmin < 1) o.inner_pmin = 2;
     for (int i = 0; i < njobs; ++i) {
         const fb_batch_job& jb = jobs[i];
         if (!jb.mesh || !jb.tree || !jb.src || !jb.x || jb.nsrc < 1 || !(jb.k > 0))

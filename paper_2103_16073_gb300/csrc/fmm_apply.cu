@@ -199,96 +199,205 @@ __global__ void k_near_l2p(int P, const int32_t* __restrict__ leaf_start, const 
 // ------------------------------------------------------- RCR translation ----
 // Rotation - coaxial translation - back-rotation (Sec. 3.3) applied per box
 // pair: for a group of pairs sharing one translation vector (one direction,
-// one |t|) each CTA takes nb pairs:
-//   rotate       u_n^mu   = sum_m   D^n_{mu,m} x_n^m              (n < p_in)
-//   coaxial      v_{n'}^mu = sum_n   C^{|mu|}_{n'n} u_n^mu          (n' < p_out)
-//   back-rotate  y_{n'}^m' = sum_mu conj(D^{n'}_{mu,m'}) v_{n'}^mu
-//   dst[target] += y                                  (atomic adds)
+// one |t|) each CTA takes nb pairs.  The rotations run folded by the
+// symmetry of the real factors, d^n_{-mu,-m} = d^n_{mu,m}: with the phased
+// input x_m = e^{i m phi} src_m and s_m = x_m + x_{-m}, t_m = x_m - x_{-m}
+// (m > 0), s_0 = x_0,
+//   E_mu = u_mu + u_{-mu} = 2 d_{mu,0} s_0 + sum_{m>0} (d_{mu,m} + d_{mu,-m}) s_m   (mu = 0..n)
+//   O_mu = u_mu - u_{-mu} =                  sum_{m>0} (d_{mu,m} - d_{mu,-m}) t_m   (mu = 1..n)
+// (half the multiplications of u = d x); the coaxial blocks, which depend
+// on |m| only, map E to E and O to O; the back-rotation folds the same way,
+//   Y+_{m'} = y_{m'} + y_{-m'} = d_{0,m'} E_0 + sum_{mu>0} (d_{mu,m'} + d_{-mu,m'}) E_mu
+//   Y-_{m'} = y_{m'} - y_{-m'} =               sum_{mu>0} (d_{mu,m'} - d_{-mu,m'}) O_mu
+// and y_{+-m'} = (Y+ +- Y-)/2, e^{-+ i m' phi} applied, scatter-added into the
+// target (atomic adds: the groups of one launch may share targets).  Folded
+// layout of degree n within a vector: [0..n] even part, [n+1..2n] odd part.
 __device__ __forceinline__ void nm_of(int e, int& n, int& m) {
     n = (int)sqrtf((float)e);
     while (n * n > e) --n;
     while ((n + 1) * (n + 1) <= e) ++n;
     m = e - n * n - n;
 }
+// (n, j) of a folded degree-major index e = n^2 + j, j in [0, 2n]
+__device__ __forceinline__ void nj_of(int e, int& n, int& j) {
+    nm_of(e, n, j);
+    j += n;
+}
+// pair index e -> (n1, m') for m' = 0..n1 (e = n1 (n1 + 1) / 2 + m')
+__device__ __forceinline__ void tri_of(int e, int& n, int& m) {
+    n = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+    while (n * (n + 1) / 2 > e) --n;
+    while ((n + 1) * (n + 2) / 2 <= e) ++n;
+    m = e - n * (n + 1) / 2;
+}
 
-// Each thread owns one coefficient index and computes it for a chunk of W
+// Each thread owns one (folded) coefficient and computes it for a chunk of W
 // pairs at once, so every rotation / coaxial entry it loads is used W times
 // from registers; the pair operands come from shared memory, where the
 // threads of a warp that share a degree read the same word (broadcast).
 // Full chunks use W = RcrChunk, the remainder of a tile one pair at a time.
 template <class R> struct RcrChunk { static constexpr int value = 8; };
 template <> struct RcrChunk<double> { static constexpr int value = 4; };
+// CTAs per SM the register budget must allow: FP64 tiles (48 KB of shared
+// memory each) are latency bound and want four resident CTAs, FP32 tiles
+// (96 KB) fit two.
+template <class R> struct RcrMinBlocks { static constexpr int value = 2; };
+template <> struct RcrMinBlocks<double> { static constexpr int value = 4; };
 
-// acc += d x for real d
+// acc += a x for real a
 template <class R>
-__device__ __forceinline__ void rmac(cx<R>& acc, R d, const cx<R>& x) {
-    acc.re = fma(d, x.re, acc.re);
-    acc.im = fma(d, x.im, acc.im);
+__device__ __forceinline__ void rmac(cx<R>& acc, R a, const cx<R>& x) {
+    acc.re = fma(a, x.re, acc.re);
+    acc.im = fma(a, x.im, acc.im);
 }
 
-// rotation with the real factor d of the block (the phase e^{i m phi} has
-// been applied to the input while staging it)
+// folded rotation of degree n, output j (E_j for j <= n, O_{j-n} otherwise);
+// Dc points at d_{0,0} of the degree-n block (row stride w = 2n + 1)
 template <int W, class R>
-__device__ __forceinline__ void rcr_rotate(const R* dn, int n, const cx<R>* xs, int Pin, int b0, int e,
+__device__ __forceinline__ void rcr_rotate(const R* Dc, int n, int j, const cx<R>* xs, int Pin, int b0, int e,
                                            cx<R>* us) {
     cx<R> acc[W];
 #pragma unroll
-    for (int j = 0; j < W; ++j) acc[j] = mk<R>(0, 0);
+    for (int q = 0; q < W; ++q) acc[q] = mk<R>(0, 0);
+    const int w = 2 * n + 1;
+    const cx<R>* xb = xs + b0 * Pin + n * n;
+    if (j <= n) {
+        const R* row = Dc + (int64_t)j * w;
+        {
+            const R a = R(2) * row[0];
+#pragma unroll
+            for (int q = 0; q < W; ++q) rmac(acc[q], a, xb[q * Pin]);
+        }
+#pragma unroll 4
+        for (int m = 1; m <= n; ++m) {
+            const R a = row[m] + row[-m];
+#pragma unroll
+            for (int q = 0; q < W; ++q) rmac(acc[q], a, xb[q * Pin + m]);
+        }
+    } else {
+        const R* row = Dc + (int64_t)(j - n) * w;
+#pragma unroll 4
+        for (int m = 1; m <= n; ++m) {
+            const R a = row[m] - row[-m];
+#pragma unroll
+            for (int q = 0; q < W; ++q) rmac(acc[q], a, xb[q * Pin + n + m]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q) us[(b0 + q) * Pin + e] = acc[q];
+}
+
+// coaxial step on folded data: output (n1, j1) of order am (even or odd part)
+// input of degree n at n^2 + withn * n + a: folded even part (withn = 0,
+// a = am), folded odd part (1, am), or unfolded order mu (1, mu)
+template <int W, class R>
+__device__ __forceinline__ void rcr_coax(const cx<R>* Cr, int am, int withn, int a, int pmid, const cx<R>* us,
+                                         int Pin, int Pout, int b0, int e, cx<R>* vs) {
+    cx<R> acc[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) acc[q] = mk<R>(0, 0);
+    const cx<R>* ub = us + b0 * Pin;
+#pragma unroll 4
+    for (int n = am; n < pmid; ++n) {
+        cx<R> c = Cr[n];
+        int o = n * n + withn * n + a;
+#pragma unroll
+        for (int q = 0; q < W; ++q) cmac(acc[q], c, ub[q * Pin + o]);
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q) vs[(b0 + q) * Pout + e] = acc[q];
+}
+
+// folded back-rotation of degree n1 for the output pair +-m' (m' >= 0),
+// inner range |mu| <= mmax; Dc at d_{0,0} of the degree-n1 block
+template <int W, class R>
+__device__ __forceinline__ void rcr_back(const R* Dc, int n1, int mp, int mmax, cx<R> ph, const cx<R>* vs,
+                                         int Pout, int b0, const int64_t* dsto, cx<R>* dst) {
+    cx<R> yp[W], ym[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        yp[q] = mk<R>(0, 0);
+        ym[q] = mk<R>(0, 0);
+    }
+    const int w = 2 * n1 + 1;
+    const cx<R>* vb = vs + b0 * Pout + n1 * n1;
+    {
+        const R a = Dc[mp];
+#pragma unroll
+        for (int q = 0; q < W; ++q) rmac(yp[q], a, vb[q * Pout]);
+    }
+#pragma unroll 4
+    for (int mu = 1; mu <= mmax; ++mu) {
+        const R dp = Dc[(int64_t)mu * w + mp], dm = Dc[-(int64_t)mu * w + mp];
+        const R ap = dp + dm, am = dp - dm;
+#pragma unroll
+        for (int q = 0; q < W; ++q) {
+            rmac(yp[q], ap, vb[q * Pout + mu]);
+            rmac(ym[q], am, vb[q * Pout + n1 + mu]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+        cx<R>* d = dst + dsto[b0 + q] + n1 * n1 + n1;
+        if (mp == 0) {
+            const cx<R> y = R(0.5) * yp[q];
+            atomicAdd(&d->re, y.re);
+            atomicAdd(&d->im, y.im);
+        } else {
+            const cx<R> y1 = (R(0.5) * (yp[q] + ym[q])) * conjg(ph);
+            const cx<R> y2 = (R(0.5) * (yp[q] - ym[q])) * ph;
+            atomicAdd(&d[mp].re, y1.re);
+            atomicAdd(&d[mp].im, y1.im);
+            atomicAdd(&d[-mp].re, y2.re);
+            atomicAdd(&d[-mp].im, y2.im);
+        }
+    }
+}
+
+// Unfolded forms (u = d x over all m, each output m' on its own), used by the
+// FP64 tiles: they are bound by FP64 latency rather than multiplies, and the
+// folded form's wider per-thread state costs them more than it saves.
+template <int W, class R>
+__device__ __forceinline__ void rcr_rotate_full(const R* dn, int n, const cx<R>* xs, int Pin, int b0, int e,
+                                                cx<R>* us) {
+    cx<R> acc[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) acc[q] = mk<R>(0, 0);
     const cx<R>* xb = xs + b0 * Pin + n * n;
 #pragma unroll 4
     for (int m = 0; m <= 2 * n; ++m) {
         R d = dn[m];
 #pragma unroll
-        for (int j = 0; j < W; ++j) rmac(acc[j], d, xb[j * Pin + m]);
+        for (int q = 0; q < W; ++q) rmac(acc[q], d, xb[q * Pin + m]);
     }
 #pragma unroll
-    for (int j = 0; j < W; ++j) us[(b0 + j) * Pin + e] = acc[j];
+    for (int q = 0; q < W; ++q) us[(b0 + q) * Pin + e] = acc[q];
 }
-
 template <int W, class R>
-__device__ __forceinline__ void rcr_coax(const cx<R>* Cr, int am, int mu, int pmid, const cx<R>* us, int Pin,
-                                         int Pout, int b0, int e, cx<R>* vs) {
+__device__ __forceinline__ void rcr_back_full(const R* dn, int n1, cx<R> phc, const cx<R>* vs, int Pout, int b0,
+                                              int e, const int64_t* dsto, cx<R>* dst) {
     cx<R> acc[W];
 #pragma unroll
-    for (int j = 0; j < W; ++j) acc[j] = mk<R>(0, 0);
-    const cx<R>* ub = us + b0 * Pin;
-#pragma unroll 4
-    for (int n = am; n < pmid; ++n) {
-        cx<R> c = Cr[n];
-        int o = n * n + n + mu;
-#pragma unroll
-        for (int j = 0; j < W; ++j) cmac(acc[j], c, ub[j * Pin + o]);
-    }
-#pragma unroll
-    for (int j = 0; j < W; ++j) vs[(b0 + j) * Pout + e] = acc[j];
-}
-
-// back-rotation: y^{m'} = e^{-i m' phi} sum_mu d_{mu,m'} v^mu  (phc = e^{-i m' phi})
-template <int W, class R>
-__device__ __forceinline__ void rcr_back(const R* dn, int n1, cx<R> phc, const cx<R>* vs, int Pout, int b0, int e,
-                                         const int64_t* dsto, cx<R>* dst) {
-    cx<R> acc[W];
-#pragma unroll
-    for (int j = 0; j < W; ++j) acc[j] = mk<R>(0, 0);
+    for (int q = 0; q < W; ++q) acc[q] = mk<R>(0, 0);
     int w = 2 * n1 + 1;
     const cx<R>* vb = vs + b0 * Pout + n1 * n1;
 #pragma unroll 4
     for (int mu = 0; mu < w; ++mu) {
         R d = dn[(int64_t)mu * w];
 #pragma unroll
-        for (int j = 0; j < W; ++j) rmac(acc[j], d, vb[j * Pout + mu]);
+        for (int q = 0; q < W; ++q) rmac(acc[q], d, vb[q * Pout + mu]);
     }
 #pragma unroll
-    for (int j = 0; j < W; ++j) {
-        cx<R> y = acc[j] * phc;
-        cx<R>* d = dst + dsto[b0 + j] + e;
+    for (int q = 0; q < W; ++q) {
+        cx<R> y = acc[q] * phc;
+        cx<R>* d = dst + dsto[b0 + q] + e;
         atomicAdd(&d->re, y.re);
         atomicAdd(&d->im, y.im);
     }
 }
 
 template <class R>
-__global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, const RcrTile* __restrict__ tiles,
+__global__ void __launch_bounds__(256, RcrMinBlocks<R>::value) k_rcr(const RcrTask* __restrict__ tasks, const RcrTile* __restrict__ tiles,
                                              const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
                                              int64_t per_dir, int prot, const cx<R>* __restrict__ coax,
                                              const int32_t* __restrict__ src_idx,
@@ -296,6 +405,7 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
                                              const cx<R>* __restrict__ src, cx<R>* __restrict__ dst,
                                              int nrhs, int64_t rstride) {
     constexpr int BCH = RcrChunk<R>::value;
+    constexpr bool kFold = sizeof(R) == 4;   // FP32: folded rotations; FP64: unfolded
     extern __shared__ unsigned char smem_raw[];
     __shared__ int64_t s_dst_off[16];
     RcrTile tl = tiles[blockIdx.x];
@@ -304,7 +414,7 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
     const int Pin = tk.p_in * tk.p_in, Pout = tk.p_out * tk.p_out;
     const int pmid = tk.p_in;   // the rotated input keeps degrees n < p_in
     cx<R>* buf = (cx<R>*)smem_raw;
-    cx<R>* xs = buf;                    // [nb][Pin], later reused for vs
+    cx<R>* xs = buf;                    // [nb][Pin] folded phased input, later reused for vs
     cx<R>* us = buf + nb * max(Pin, Pout);   // [nb][Pin]
     cx<R>* vs = buf;                    // [nb][Pout] (xs is dead after the rotation)
     int tid = threadIdx.x, nth = blockDim.x;
@@ -321,9 +431,20 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
         int col = tl.col0 + b;
         int pr = col / nrhs, rh = col - pr * nrhs;
         int sb = src_idx[tk.pair_off + pr];
-        int n, m;
-        nm_of(e, n, m);
-        xs[q] = src[rh * rstride + tk.src_base + (int64_t)sb * Pin + e] * ph[m];
+        int n, j;
+        nj_of(e, n, j);
+        const cx<R>* x = src + rh * rstride + tk.src_base + (int64_t)sb * Pin + (int64_t)n * n + n;   // (n, 0)
+        cx<R> v;
+        if (!kFold) {
+            v = x[j - n] * ph[j - n];   // plain phased input, degree-major
+        } else if (j == 0) {
+            v = x[0];
+        } else {
+            const int m = j <= n ? j : j - n;
+            const cx<R> xp = x[m] * ph[m], xm = x[-m] * ph[-m];
+            v = j <= n ? xp + xm : xp - xm;
+        }
+        xs[q] = v;
     }
     __syncthreads();
     const R* D = rotd + tk.rot_off;
@@ -336,37 +457,64 @@ __global__ void __launch_bounds__(256) k_rcr(const RcrTask* __restrict__ tasks, 
         if (b0 + 2 <= nb) { CALL(2); b0 += 2; }                       \
         if (b0 < nb) CALL(1);                                         \
     }
-    // rotate: u_n^mu = sum_m D^n_{mu,m} x_n^m
+    // rotation: folded E_j / O_{j-n}, or u_{n,mu} = sum_m d_{mu,m} x_m unfolded
     for (int e = tid; e < Pin; e += nth) {
-        int n, mu;
-        nm_of(e, n, mu);
-        const R* Dn = D + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3 + (int64_t)(mu + n) * (2 * n + 1);
-#define RCR_ROT(W) rcr_rotate<(W)>(Dn, n, xs, Pin, b0, e, us)
-        RCR_CHUNKS(RCR_ROT)
+        int n, j;
+        nj_of(e, n, j);
+        const R* Dc = D + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3 + (int64_t)n * (2 * n + 1) + n;
+        if (kFold) {
+#define RCR_ROT(W) rcr_rotate<(W)>(Dc, n, j, xs, Pin, b0, e, us)
+            RCR_CHUNKS(RCR_ROT)
 #undef RCR_ROT
+        } else {
+            const R* Dn = Dc + (int64_t)(j - n) * (2 * n + 1) - n;   // row mu = j - n
+#define RCR_ROT(W) rcr_rotate_full<(W)>(Dn, n, xs, Pin, b0, e, us)
+            RCR_CHUNKS(RCR_ROT)
+#undef RCR_ROT
+        }
     }
     __syncthreads();
-    // coaxial: v_{n'}^mu = sum_n C^{|mu|}_{n'n} u_n^mu
+    // coaxial: v^{am}_{n'} = sum_n C^{am}_{n'n} u^{am}_n on the even and odd parts
     const cx<R>* C = coax + tk.coax_off;
     const int pc = tk.pc;
     for (int e = tid; e < Pout; e += nth) {
-        int n1, mu;
-        nm_of(e, n1, mu);
-        int am = abs(mu);
+        int n1, j1;
+        nj_of(e, n1, j1);
+        // folded: even part of order j1 or odd part of order j1 - n1; unfolded:
+        // order mu = j1 - n1 at offset n^2 + n + mu
+        const bool odd = kFold && j1 > n1;
+        const int am = kFold ? (odd ? j1 - n1 : j1) : abs(j1 - n1);
+        const int withn = (kFold && !odd) ? 0 : 1;
+        const int a = kFold ? am : j1 - n1;
         const cx<R>* Cr = C + ((int64_t)am * pc + n1) * pc;
         const int hi = am < pmid ? pmid : am;   // empty sum when |mu| >= p_in
-#define RCR_COAX(W) rcr_coax<(W)>(Cr, am, mu, hi, us, Pin, Pout, b0, e, vs)
+#define RCR_COAX(W) rcr_coax<(W)>(Cr, am, withn, a, hi, us, Pin, Pout, b0, e, vs)
         RCR_CHUNKS(RCR_COAX)
 #undef RCR_COAX
     }
     __syncthreads();
-    // back-rotate: y_{n'}^{m'} = sum_mu conj(D^{n'}_{mu,m'}) v_{n'}^mu, then scatter-add
-    for (int e = tid; e < Pout; e += nth) {
-        int n1, m1;
-        nm_of(e, n1, m1);
-        const R* Dn = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (m1 + n1);
-        const cx<R> phc = conjg(ph[m1]);
-#define RCR_BACK(W) rcr_back<(W)>(Dn, n1, phc, vs, Pout, b0, e, s_dst_off, dst)
+    if (!kFold) {
+        // back-rotate: y_{n'}^{m'} = sum_mu d^{n'}_{mu,m'} v_{n'}^mu, e^{-i m' phi}, scatter-add
+        for (int e = tid; e < Pout; e += nth) {
+            int n1, m1;
+            nm_of(e, n1, m1);
+            const R* Dn = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (m1 + n1);
+            const cx<R> phc = conjg(ph[m1]);
+#define RCR_BACK(W) rcr_back_full<(W)>(Dn, n1, phc, vs, Pout, b0, e, s_dst_off, dst)
+            RCR_CHUNKS(RCR_BACK)
+#undef RCR_BACK
+        }
+        return;
+    }
+    // folded back-rotation of every pair +-m' of every degree n' < p_out, then scatter-add
+    const int npairs_out = tk.p_out * (tk.p_out + 1) / 2;
+    for (int e = tid; e < npairs_out; e += nth) {
+        int n1, mp;
+        tri_of(e, n1, mp);
+        const R* Dc = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (int64_t)n1 * (2 * n1 + 1) + n1;
+        const int mmax = min(n1, pmid - 1);
+        const cx<R> phm = ph[mp];
+#define RCR_BACK(W) rcr_back<(W)>(Dc, n1, mp, mmax, phm, vs, Pout, b0, s_dst_off, dst)
         RCR_CHUNKS(RCR_BACK)
 #undef RCR_BACK
     }

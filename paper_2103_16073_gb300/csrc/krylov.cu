@@ -270,8 +270,14 @@ static fb_status gmres_fixed(fb_op* A, const fb_precond* pc, Work& W, const cd* 
     return FB_OK;
 }
 
+struct InnerBatch;
+// Work buffers of the inner-outer preconditioner: the single-system GMRES
+// and, per number of right-hand sides, the lockstep batch (created on first
+// use outside any capture).
 struct InnerSolver {
     Work W;
+    std::map<int, InnerBatch*> batch;
+    ~InnerSolver();
 };
 
 // The first k+1 Arnoldi vectors of the right-preconditioned Krylov space of
@@ -1000,6 +1006,113 @@ void fb_krylov_free(fb_op* op) {
     op->fg_bwork = nullptr;
 }
 
+// Lockstep fixed-step GMRES of the inner-outer preconditioner on R
+// right-hand sides: the batch workspace with its Hessenberg states, every
+// system active and taking exactly k = B.m steps (set once at creation, so
+// an application uploads nothing and can be captured into a graph).
+struct InnerBatch {
+    BatchWork B;
+};
+InnerSolver::~InnerSolver() {
+    for (auto& kv : batch) delete kv.second;
+}
+
+static fb_status bwork_hess(BatchWork& B) {
+    const int R = B.R, m = B.m;
+    std::vector<Hess> hh(R);
+    cd* H0 = B.small;
+    cd* blk = B.small + (size_t)R * (m + 1) * m;
+    for (int r = 0; r < R; ++r) {
+        Hess& h = hh[r];
+        h.m = m;
+        h.H = H0 + (size_t)r * (m + 1) * m;
+        h.h = blk + (size_t)0 * R * (m + 1) + (size_t)r * (m + 1);
+        h.cs = blk + (size_t)1 * R * (m + 1) + (size_t)r * (m + 1);
+        h.sn = blk + (size_t)2 * R * (m + 1) + (size_t)r * (m + 1);
+        h.g = blk + (size_t)3 * R * (m + 1) + (size_t)r * (m + 1);
+        h.y = blk + (size_t)5 * R * (m + 1) + (size_t)r * (m + 1);
+        h.nrm2 = B.scal + 4 * r;
+        h.inv = B.scal + 4 * r + 1;
+        h.est = B.scal + 4 * r + 2;
+    }
+    FB_CUDA(cudaMemcpy(B.dhs, hh.data(), sizeof(Hess) * R, cudaMemcpyHostToDevice));
+    return FB_OK;
+}
+
+static fb_status inner_batch_get(InnerSolver* in, int64_t n, int k, int R, bool with_z, InnerBatch** out) {
+    auto it = in->batch.find(R);
+    if (it != in->batch.end()) {
+        *out = it->second;
+        return FB_OK;
+    }
+    InnerBatch* ib = new InnerBatch();
+    fb_status st = bwork_alloc(ib->B, n, k, R, with_z);
+    if (st == FB_OK) st = bwork_hess(ib->B);
+    if (st == FB_OK) {
+        std::vector<int> flags(2 * R);
+        for (int r = 0; r < R; ++r) {
+            flags[r] = 1;        // active
+            flags[R + r] = k;    // steps taken
+        }
+        if (cudaMemcpy(ib->B.dint, flags.data(), sizeof(int) * 2 * R, cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fb_fail(FB_ERR_CUDA, "inner batch flags upload failed");
+    }
+    if (st != FB_OK) {
+        delete ib;
+        return st;
+    }
+    in->batch[R] = ib;
+    *out = ib;
+    return FB_OK;
+}
+
+// k = B.m steps of GMRES on A d_r = rhs_r for the R systems of B at once
+// (one multi-RHS matvec and one batched preconditioner application per
+// step, CGS2, no host synchronisation); the results in B.D.
+static fb_status gmres_fixed_multi(fb_op* A, const fb_precond* pc, BatchWork& B, const cd* rhs, cudaStream_t s) {
+    const int64_t n = B.n;
+    const int R = B.R, m = B.m;
+    const int* dact = B.dint;
+    const int* dj1 = B.dint + R;
+    const int gx = std::min(grid_for(n), 64);
+    FB_CUDA(cudaMemsetAsync(B.D, 0, sizeof(cd) * n * R, s));
+    FB_CUDA(cudaMemsetAsync(B.scal, 0, sizeof(double) * 4 * R, s));
+    k_bnorm2<<<dim3(grid_for(n), R), KB, 0, s>>>(rhs, n, B.scal, 4, nullptr);
+    k_bcycle_start<<<R, 1, 0, s>>>(B.dhs, dact);
+    k_bscale<<<dim3(grid_for(n), R), KB, 0, s>>>(B.V, rhs, n, B.scal + 1, 4, dact);
+    FB_LAUNCH_CHECK();
+    cnt(3);
+    cd* h = B.small + (size_t)R * (m + 1) * m;    // [R][m+1] CGS coefficients (Hess.h)
+    for (int j = 0; j < m; ++j) {
+        cd* Vj = B.V + (int64_t)j * R * n;
+        cd* Zj = Vj;
+        if (pc) {
+            Zj = B.Z + (int64_t)j * R * n;
+            FB_CHECK(fb_pc_apply(pc, Vj, Zj, s, R));
+        }
+        FB_CHECK(fb_apply_any(A, Zj, B.W, s, R));
+        for (int pass = 0; pass < 2; ++pass) {
+            FB_CUDA(cudaMemsetAsync(h, 0, sizeof(cd) * R * (m + 1), s));
+            k_bmdot<<<dim3(gx, j + 1, R), KB, 0, s>>>(B.V, n, R, B.W, h, m + 1, dact);
+            k_bgs_update<<<dim3(grid_for(n), R), KB, 0, s>>>(B.V, n, R, j + 1, h, m + 1, B.W, dact);
+            k_baccum_h<<<R, 1024, 0, s>>>(B.dhs, j, dact);
+            cnt(3);
+        }
+        FB_CUDA(cudaMemsetAsync(B.scal, 0, sizeof(double) * 4 * R, s));
+        k_bnorm2<<<dim3(grid_for(n), R), KB, 0, s>>>(B.W, n, B.scal, 4, dact);
+        k_barnoldi_close<<<R, 1, 0, s>>>(B.dhs, j, dact);
+        k_bscale<<<dim3(grid_for(n), R), KB, 0, s>>>(B.V + (int64_t)(j + 1) * R * n, B.W, n, B.scal + 1, 4, dact);
+        FB_LAUNCH_CHECK();
+        cnt(3);
+    }
+    k_bbacksolve<<<R, 1, 0, s>>>(B.dhs, dj1);
+    cd* ys = B.small + (size_t)R * (m + 1) * m + (size_t)R * (m + 1) * 5;   // Hess.y block
+    k_bupdate_x<<<dim3(grid_for(n), R), KB, 0, s>>>(B.D, pc ? B.Z : B.V, n, R, dj1, ys, m + 1);
+    FB_LAUNCH_CHECK();
+    cnt(2);
+    return FB_OK;
+}
+
 static fb_status upload_ints(BatchWork& B, cudaStream_t s) {
     FB_CUDA(cudaMemcpyAsync(B.dint, B.hint, sizeof(int) * 2 * B.R, cudaMemcpyHostToDevice, s));
     return FB_OK;
@@ -1270,11 +1383,27 @@ fb_status fb_pc_apply(const fb_precond* pc, const cd* x, cd* y, cudaStream_t s, 
     const int64_t n = pc->n;
     if (pc->kind == FB_PC_INNER) {
         InnerSolver* in = (InnerSolver*)pc->inner;
-        for (int r = 0; r < nrhs; ++r) {
-            FB_CHECK(gmres_fixed(pc->inner_op, pc->base, in->W, x + r * n, pc->inner_its, s));
-            FB_CUDA(cudaMemcpyAsync(y + r * n, in->W.d, sizeof(cd) * n, cudaMemcpyDeviceToDevice, s));
+        auto body = [pc, in, nrhs, n](const cd* gx, cd* gy, cudaStream_t st) -> fb_status {
+            if (nrhs == 1) {
+                FB_CHECK(gmres_fixed(pc->inner_op, pc->base, in->W, gx, pc->inner_its, st));
+                FB_CUDA(cudaMemcpyAsync(gy, in->W.d, sizeof(cd) * n, cudaMemcpyDeviceToDevice, st));
+                return FB_OK;
+            }
+            // several right-hand sides: one lockstep inner solve, multi-RHS matvecs
+            InnerBatch* ib = nullptr;
+            FB_CHECK(inner_batch_get(in, n, pc->inner_its, nrhs, pc->base != nullptr, &ib));
+            FB_CHECK(gmres_fixed_multi(pc->inner_op, pc->base, ib->B, gx, st));
+            FB_CUDA(cudaMemcpyAsync(gy, ib->B.D, sizeof(cd) * n * nrhs, cudaMemcpyDeviceToDevice, st));
+            return FB_OK;
+        };
+        if (pc->use_graphs) {
+            // the inner steps synchronise nothing: one captured graph per
+            // number of right-hand sides, recaptured when the inner operator
+            // reallocates buffers the graph refers to
+            fb_precond* mpc = const_cast<fb_precond*>(pc);
+            return fb_graph_run(mpc->graphs, nrhs, n * nrhs, n * nrhs, x, y, s, body, &pc->inner_op->buf_gen);
         }
-        return FB_OK;
+        return body(x, y, s);
     }
     if (pc->net) {
         if (pc->use_graphs) {

@@ -42,7 +42,7 @@ def sweep_receivers(n=16, seed=71):
 
 
 def run(nfreq, f_lo, f_hi, nsrc, tol=1e-4, max_rhs=8, autotune=True, lookahead=True, rank=0, world=1,
-        out_dir=None):
+        out_dir=None, inner_iters=0):
     wls = W.lroom_sweep(nfreq=nfreq, f_lo=f_lo, f_hi=f_hi, nsrc=nsrc)
     costs = [D.predicted_cost(wl.n, wl.k, LROOM_DIAMETER, nsrc) for wl in wls]
     owner, load = D.partition(costs, world)
@@ -59,7 +59,8 @@ def run(nfreq, f_lo, f_hi, nsrc, tol=1e-4, max_rhs=8, autotune=True, lookahead=T
         built.append(dict(mesh=mesh, tree=tree, k=wl.k, src=wl.sources, x=x))
     torch.cuda.synchronize()
     t1 = time.perf_counter()
-    res = fb.fb_batch_solve(built, tol=tol, max_rhs=max_rhs, autotune=autotune, lookahead=lookahead)
+    res = fb.fb_batch_solve(built, tol=tol, max_rhs=max_rhs, autotune=autotune, lookahead=lookahead,
+                            inner_iters=inner_iters)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     if out_dir:
@@ -76,6 +77,8 @@ def run(nfreq, f_lo, f_hi, nsrc, tol=1e-4, max_rhs=8, autotune=True, lookahead=T
                                n=np.array(wl.n), iters=np.array(r["infos"][si]["iters"]),
                                true_relres=np.array(r["infos"][si]["true_relres"]), rank=np.array(rank))
     out = {"workload": f"L-room sweep {nfreq} freqs {f_lo:g}-{f_hi:g} Hz, lambda/8, {nsrc} sources each",
+           "preconditioner": (f"inner-outer, {inner_iters} GMRES steps on a low-accuracy FMM" if inner_iters
+                              else "block Jacobi"),
            "rank": rank, "ranks": world, "predicted_load": load,
            "n_elements": [wls[i].n for i in mine], "mesh_tree_s": round(t1 - t0, 3), "batch_s": round(t2 - t1, 3),
            "solves": len(mine) * nsrc, "solves_per_s": round(len(mine) * nsrc / max(t2 - t1, 1e-9), 3),
@@ -99,6 +102,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-lookahead", action="store_true")
     ap.add_argument("--out-dir", default="", help="one result file per (frequency, source) key")
+    ap.add_argument("--inner", type=int, default=0, help="inner-outer preconditioner with this many inner steps")
     a = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -111,7 +115,7 @@ def main():
         dist.init_process_group("gloo")
     t0 = time.perf_counter()
     out, _, _ = run(a.nfreq, a.flo, a.fhi, a.nsrc, max_rhs=a.max_rhs, autotune=not a.no_autotune,
-                    lookahead=not a.no_lookahead, rank=rank, world=world, out_dir=out_dir)
+                    lookahead=not a.no_lookahead, rank=rank, world=world, out_dir=out_dir, inner_iters=a.inner)
     if world > 1:
         dist.barrier()   # every rank's result files are written
     if rank == 0:

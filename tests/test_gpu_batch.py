@@ -13,8 +13,11 @@ from paper_2103_16073_gb300 import sweep
 from _cases import rel
 
 
-@pytest.mark.parametrize("lookahead", [True, False])
-def test_sweep_batch(lookahead):
+@pytest.mark.parametrize("lookahead,inner", [(True, 0), (False, 0), (True, 8)])
+def test_sweep_batch(lookahead, inner):
+    """inner = 0: block Jacobi; inner = 8: the inner-outer preconditioner
+    (8 lockstep GMRES steps on a low-accuracy FMM for all sources of a batch,
+    replayed as captured graphs)."""
     wls = sweep.W.lroom_sweep(nfreq=3, f_lo=100.0, f_hi=200.0, nsrc=3)
     built = []
     for wl in wls:
@@ -24,7 +27,7 @@ def test_sweep_batch(lookahead):
         built.append(dict(mesh=mesh, tree=tree, k=wl.k, src=wl.sources,
                           x=torch.zeros((3, wl.n), dtype=torch.complex128, device="cuda")))
     try:
-        res = fb.fb_batch_solve(built, tol=1e-5, max_rhs=2, autotune=True, lookahead=lookahead)
+        res = fb.fb_batch_solve(built, tol=1e-5, max_rhs=2, autotune=True, lookahead=lookahead, inner_iters=inner)
         for r in res:
             assert r["status"] == 0
             assert all(i["status"] == 0 and i["true_relres"] <= 1e-5 for i in r["infos"])

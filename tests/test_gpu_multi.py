@@ -206,6 +206,54 @@ def test_inner_outer_preconditioner(setup):
         fb.fb_tree_destroy(tree)
 
 
+def test_inner_outer_several_rhs_and_graphs(setup):
+    """The inner-outer preconditioner on several right-hand sides runs one
+    lockstep inner GMRES (one multi-RHS matvec per inner step): in a batched
+    solve each system needs the outer iterations of its single solve (+-1)
+    and meets the tolerance; replayed as captured graphs (one per number of
+    right-hand sides) it gives the same solutions up to the rounding of the
+    FMM's FP32 atomic scatter-adds, whose order varies from run to run."""
+    wl, mesh, op = setup
+    A = op(fb.FB_PREC_MIXED_FMM)
+    A64 = op(fb.FB_PREC_FP64_FMM)
+    tree = fb.fb_tree_build(mesh, 64)
+    Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 0.5, 2)
+    bjl = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
+    inner = fb.fb_precond_create_inner(A, Alow, bjl, 6)
+    try:
+        R = 3
+        B = torch.tensor(np.stack([seeded_vector(wl.n, 130 + r) for r in range(R)]), device="cuda")
+        single = []
+        for r in range(R):
+            x = torch.zeros_like(B[0])
+            info = fb.fb_fgmres_solve(A, B[r].contiguous(), x, pc=inner, tol=1e-6, restart=30, true_op=A64)
+            assert info["status"] == 0
+            single.append((x.cpu().numpy(), info["iters"]))
+        X = torch.zeros_like(B)
+        infos = fb.fb_fgmres_solve_multi(A, B, X, pc=inner, tol=1e-6, restart=30, true_op=A64)
+        for r in range(R):
+            assert infos[r]["status"] == 0 and infos[r]["true_relres"] <= 1e-6
+            assert abs(infos[r]["iters"] - single[r][1]) <= 1
+            assert rel(X[r].cpu().numpy(), single[r][0]) < 1e-5
+        fb.fb_operator_use_graphs(Alow, True)
+        fb.fb_precond_use_graphs(inner, True)
+        for _ in range(2):   # capture, then replay
+            X2 = torch.zeros_like(B)
+            infos2 = fb.fb_fgmres_solve_multi(A, B, X2, pc=inner, tol=1e-6, restart=30, true_op=A64)
+            for r in range(R):
+                assert infos2[r]["status"] == 0 and abs(infos2[r]["iters"] - infos[r]["iters"]) <= 1
+                assert rel(X2[r].cpu().numpy(), X[r].cpu().numpy()) < 1e-6
+            x = torch.zeros_like(B[0])
+            info = fb.fb_fgmres_solve(A, B[0].contiguous(), x, pc=inner, tol=1e-6, restart=30, true_op=A64)
+            assert info["status"] == 0
+            assert rel(x.cpu().numpy(), single[0][0]) < 1e-6
+    finally:
+        fb.fb_precond_destroy(inner)
+        fb.fb_precond_destroy(bjl)
+        fb.fb_operator_destroy(Alow)
+        fb.fb_tree_destroy(tree)
+
+
 def test_krylov_basis_is_arnoldi(setup):
     """fb_krylov_basis returns an orthonormal basis that starts at b/||b||
     and satisfies the Arnoldi relation A V_j in span(V_0..V_{j+1})."""
