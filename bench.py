@@ -54,6 +54,7 @@ WORKLOADS = {
     "largest": ("cfg_largest", "shoebox 6.5x5.5x4.2 m, 5 kHz, N=2644104 flat triangles (lambda/6), "
                                "per-wall beta ~ U[0.05,0.3]"),
     "shoebox_1khz": ("cfg_1khz", "shoebox 3.0x2.4x2.0 m, 1 kHz, N=39368 flat triangles (lambda/8), beta=0.2"),
+    "high_order": ("cfg_high_order", "shoebox 3.0x2.4x2.0 m, 7.5 kHz, N=3072 (orders 116 / 66)"),
 }
 
 
@@ -389,6 +390,34 @@ def secondary(fb, W, torch, stream, name):
         destroy_problem(fb, P)
 
 
+def run_matvecs(args):
+    """Profiling mode: one operator of the workload (autotuned forms unless
+    --forms), `--matvec-only` applications on the device and the per-phase
+    CUDA-event split of one more; prints one JSON line."""
+    import torch
+    import paper_2103_16073_gb300 as fb
+    torch.cuda.set_device(0)
+    wl = load_workload(args.workload)
+    mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+    fb.fb_mesh_set_admittance(mesh, wl.beta)
+    tree = fb.fb_tree_build(mesh, 64)
+    prec = {"mixed": fb.FB_PREC_MIXED_FMM, "fp64": fb.FB_PREC_FP64_FMM}[args.prec]
+    d0, pmin = (INNER_D0, INNER_PMIN) if args.inner_operator else (D0, PMIN)
+    op = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, prec, d0, pmin)
+    if args.forms:
+        fb.fb_operator_set_forms(op, [int(v) for v in args.forms.split(",")])
+    else:
+        fb.fb_operator_autotune(op, 1)
+    stream = torch.cuda.current_stream()
+    t, ph = matvec_rate(fb, torch, stream, op, wl.n, args.matvec_only)
+    print(json.dumps({"workload": WORKLOADS[args.workload][1], "precision": args.prec, "d0": d0, "pmin": pmin,
+                      "orders": [int(v) for v in fb.fb_operator_info(op)[2][2:]], "matvec_ms": round(t * 1e3, 4),
+                      "phase_ms": {k: round(v, 4) for k, v in ph.items()}}))
+    fb.fb_operator_destroy(op)
+    fb.fb_tree_destroy(tree)
+    fb.fb_mesh_destroy(mesh)
+
+
 def run_ours(args):
     import torch
     import paper_2103_16073_gb300 as fb
@@ -697,8 +726,14 @@ def main():
     ap.add_argument("--ref-matvecs", type=int, default=52,
                     help="matvecs per solve used to extrapolate the reference arm (default: the plain "
                          "method's 51 block-Jacobi iterations on the largest room + 1 true residual)")
+    ap.add_argument("--matvec-only", type=int, default=0,
+                    help="profiling mode: time this many matvecs of one operator and exit")
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"], help="operator of --matvec-only")
+    ap.add_argument("--inner-operator", action="store_true", help="--matvec-only on the low-accuracy inner operator")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.matvec_only > 0:
+        run_matvecs(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -213,7 +213,11 @@ FB_API fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, 
  * level `level`, octant `index` (p_l^2 x p_{l-1}^2), 6 = dense matrix row
  * `index` (N complex), 7 = per level 1 + 0i if its M2L runs on the tensor
  * cores under the current translation method, else 0 (leaf_level + 1
- * values).  *count receives the number of complex values. */
+ * values), 8 = real rotation factors d^n of degree n = `level` for the
+ * direction of M2L offset code `index` ((2n+1) x (2n+1), row mu, column m,
+ * returned as complex with zero imaginary part; the rotation block of that
+ * direction is D^n_{mu,m} = d^n_{mu,m} e^{i m phi}, phi its azimuth).
+ * *count receives the number of complex values. */
 FB_API fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t index, double* out,
                              int64_t* count);
 
@@ -313,6 +317,8 @@ FB_API fb_status fb_precond_use_graphs(fb_precond* pc, int enable);
  *     the rotations and by |t| for the coaxial step),
  *   - mixed precision only: the stacked tensor-core GEMM of composed
  *     matrices (3xTF32).
+ * Tiles are timed below order 60, the staged passes from order 24 on (the
+ * measured crossover lies between); a level keeps at least one candidate.
  * times: 6*13 doubles or NULL, times[6l + 0..5] = M2L RCR tiles, M2L tensor,
  * M2M+L2L RCR tiles, M2M+L2L tensor, M2L RCR staged, M2M+L2L RCR staged in
  * ms (-1: not a candidate); choice: 13 ints or NULL, bit 0 = M2L of level l

@@ -253,9 +253,11 @@ def cross_validate(log=print):
         info["ms"] = (_now() - t1) * 1e3
         if indirect:
             f = fb.fb_ibem_field(A64, x, gp, gm, rcv)
-            d = rcv - torch.tensor(src, device="cuda")
-            R = torch.linalg.norm(d, dim=1)
-            f = f + torch.exp(1j * k * R) / (4 * np.pi * R)   # plus the incident field
+            # plus the incident field: Eq. (dbem1) with zero surface densities
+            zero = torch.zeros(wl.n, dtype=torch.complex128, device="cuda")
+            inc = torch.empty_like(f)
+            fb.fb_eval_field(mesh, k, zero, zero, rcv, inc, src=src)
+            f = f + inc
         else:
             f = torch.empty(rcv.shape[0], dtype=torch.complex128, device="cuda")
             fb.fb_eval_field(mesh, k, x, g, rcv, f, src=src)

@@ -519,6 +519,31 @@ fb_status fb_operator_export(const fb_op* op, int which, int level, int64_t inde
             }
         return FB_OK;
     }
+    if (which == 8) {
+        // real rotation factors d^n (n = level) of the direction of M2L offset code `index`
+        if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "not an FMM operator");
+        if (index < 0 || index >= FB_NOFF || (size_t)index >= op->dir_of_code.size() || op->dir_of_code[index] < 0)
+            return fb_fail(FB_ERR_ARG, "offset code is not an M2L translation direction");
+        if (level < 0 || level >= op->Prot) return fb_fail(FB_ERR_ARG, "degree out of range");
+        const int n = level, w = 2 * n + 1;
+        *count = (int64_t)w * w;
+        if (out) {
+            const int64_t off = (int64_t)op->dir_of_code[index] * op->per_dir + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3;
+            std::vector<double> h((size_t)w * w);
+            if (op->prec == FB_PREC_MIXED_FMM) {
+                std::vector<float> f((size_t)w * w);
+                FB_CUDA(cudaMemcpy(f.data(), op->rotd32 + off, sizeof(float) * f.size(), cudaMemcpyDeviceToHost));
+                for (size_t i = 0; i < f.size(); ++i) h[i] = f[i];
+            } else {
+                FB_CUDA(cudaMemcpy(h.data(), op->rotd64 + off, sizeof(double) * h.size(), cudaMemcpyDeviceToHost));
+            }
+            for (size_t i = 0; i < h.size(); ++i) {
+                out[2 * i] = h[i];
+                out[2 * i + 1] = 0.0;
+            }
+        }
+        return FB_OK;
+    }
     if (which == 6) {
         if (!op->dense) return fb_fail(FB_ERR_ARG, "not a dense operator");
         if (index < 0 || index >= op->n) return fb_fail(FB_ERR_ARG, "row out of range");

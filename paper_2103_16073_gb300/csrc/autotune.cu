@@ -53,6 +53,13 @@ fb_status time_ms(F&& f, cudaStream_t s, int reps, double* out) {
 
 void free_rcr(RcrPlan& p) { fb_rcr_free(p); }
 
+// Candidates worth timing (measured crossovers on GB300: per-pair tiles lose
+// to the staged passes from order ~40 on and by ~5x at 89; the staged passes
+// lose below order ~30, where a level's coefficient blocks are small).  A
+// level always keeps at least one candidate.
+bool rcr_tile_candidate(int p, size_t csz) { return fb_rcr_tile_fits(p, p, csz) && p < 60; }
+bool rcr_staged_candidate(int p, size_t csz) { return p >= 24 || !rcr_tile_candidate(p, csz); }
+
 }  // namespace
 
 fb_status fb_install_forms(fb_op* op, const std::vector<int>& tc_m2l, cudaStream_t s);
@@ -117,9 +124,10 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
         int ch = 0;
         // ---- M2L of level l: RCR tiles, RCR staged, tensor cores
         auto at_level = [&](const RcrTask& tk) { return tk.src_base == op->lev_off[l] && tk.dst_base == tk.src_base; };
-        if (fb_rcr_tile_fits(op->p[l], op->p[l], csz))
+        if (rcr_tile_candidate(op->p[l], csz))
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 0, mp, loc, s, nrhs, cnt, reps, &tl[0]));
-        FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 1, mp, loc, s, nrhs, cnt, reps, &tl[4]));
+        if (rcr_staged_candidate(op->p[l], csz))
+            FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 1, mp, loc, s, nrhs, cnt, reps, &tl[4]));
         double best = -1.0;
         if (tl[0] >= 0) best = tl[0];
         if (tl[4] >= 0 && (best < 0 || tl[4] < best)) {
@@ -166,13 +174,13 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             const int pm = std::max(op->p[l], op->p[l - 1]);
             auto all = [](const RcrTask&) { return true; };
             double rt = -1.0, rs = -1.0;
-            if (fb_rcr_tile_fits(pm, pm, csz)) {
+            if (rcr_tile_candidate(pm, csz)) {
                 double a = 0, b = 0;
                 FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 0, mp, mp, s, nrhs, cnt, reps, &a));
                 FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 0, loc, loc, s, nrhs, cnt, reps, &b));
                 rt = std::max(a, 0.0) + std::max(b, 0.0);
             }
-            {
+            if (rcr_staged_candidate(pm, csz)) {
                 double a = 0, b = 0;
                 FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 1, mp, mp, s, nrhs, cnt, reps, &a));
                 FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 1, loc, loc, s, nrhs, cnt, reps, &b));
@@ -181,7 +189,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             tl[2] = rt;
             tl[5] = rs;
             double best2 = rt;
-            if (rt < 0 || rs < rt) {
+            if (rt < 0 || (rs >= 0 && rs < rt)) {
                 best2 = rs;
                 stg_pair[l] = 1;
             }

@@ -65,7 +65,6 @@ void setup_job(const fb_batch_job& jb, const fb_batch_opts& o, cudaStream_t s, J
         if (o.inner_iters > 0) {
             FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_MIXED_FMM, o.inner_d0, o.inner_pmin, s,
                                         &js.Alow));
-            if (o.autotune) FB_CHECK(fb_operator_autotune(js.Alow, nrhs, s, nullptr, nullptr));
             FB_CHECK(fb_precond_create(js.Alow, FB_PC_BLOCK_JACOBI, s, &js.pclow));
             FB_CHECK(fb_precond_create_inner(js.A32, js.Alow, js.pclow, o.inner_iters, s, &js.inner));
             FB_CHECK(fb_operator_use_graphs(js.Alow, 1));

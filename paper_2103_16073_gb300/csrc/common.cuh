@@ -257,13 +257,15 @@ struct RcrPlan {
 };
 void fb_rcr_free(RcrPlan& p);
 bool fb_stg_staged(const RcrTask& tk);
-fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_rep, int64_t per_dir, void** out,
+fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, int64_t per_dir, void** out,
                        int64_t* elems);
 void fb_stg_free(void*& plan);
-fb_status fb_stg_run_f(void* plan, const float* rotd, const cf* rph, int64_t per_dir, int prot, const cf* coax,
+fb_status fb_stg_run_f(void* plan, const float* rf, int64_t fper, const cf* rph, int prot, const cf* coax,
                        const cf* src, cf* dst, cf* U, cf* V, cudaStream_t s, int nrhs, int64_t rstride);
-fb_status fb_stg_run_d(void* plan, const double* rotd, const cd* rph, int64_t per_dir, int prot, const cd* coax,
+fb_status fb_stg_run_d(void* plan, const double* rf, int64_t fper, const cd* rph, int prot, const cd* coax,
                        const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride);
+struct fb_op;
+fb_status fb_stg_tables(fb_op* op, const double* rotd64, cudaStream_t s);
 
 // A group of box pairs sharing one composed translation matrix (job) on the
 // tensor cores: sources from level src_level, targets in level dst_level.
@@ -330,6 +332,11 @@ struct fb_op {
     int64_t coax_count = 0, rot_count = 0;
     // per direction: a direction with the same polar angle (shares d^n)
     std::vector<int> theta_rep;
+    std::vector<int> theta_slot;             // direction -> its polar-angle group
+    std::vector<int> theta_dirs;             // group -> its representative direction
+    void* rotf = nullptr;                    // folded rotation tables (staged RCR), per group
+    int64_t rotf_per = 0;                    // values per group and table
+    std::vector<int> dir_of_code;            // M2L offset code -> direction (-1: near)
     // RCR form per level: 1 = staged passes, 0 = per-pair tiles (M2L of
     // level l; M2M and L2L between levels l-1 and l)
     int stg_m2l[FB_MAXLEV + 1] = {0};

@@ -578,6 +578,8 @@ struct RotArgs {
     int prot;
     cx<R>* U;   // staging buffers of the large-order passes
     cx<R>* V;
+    const void* rf;   // folded rotation tables and their per-group stride
+    int64_t fper;
 };
 template <class R>
 static RotArgs<R> rot_args(const fb_op* op) {
@@ -588,15 +590,17 @@ static RotArgs<R> rot_args(const fb_op* op) {
     a.prot = op->Prot;
     a.U = (cx<R>*)op->stg_u;
     a.V = (cx<R>*)op->stg_v;
+    a.rf = op->rotf;
+    a.fper = op->rotf_per;
     return a;
 }
 static fb_status stg_run(void* plan, const RotArgs<float>& r, const cf* coax, const cf* src, cf* dst,
                          cudaStream_t s, int nrhs, int64_t rstride) {
-    return fb_stg_run_f(plan, r.d, r.ph, r.per_dir, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride);
+    return fb_stg_run_f(plan, (const float*)r.rf, r.fper, r.ph, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride);
 }
 static fb_status stg_run(void* plan, const RotArgs<double>& r, const cd* coax, const cd* src, cd* dst,
                          cudaStream_t s, int nrhs, int64_t rstride) {
-    return fb_stg_run_d(plan, r.d, r.ph, r.per_dir, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride);
+    return fb_stg_run_d(plan, (const double*)r.rf, r.fper, r.ph, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride);
 }
 
 template <class R>
@@ -635,7 +639,7 @@ fb_status fb_rcr_upload(fb_op* op, RcrPlan& pl, const int32_t* src, const int32_
         FB_CHECK(dalloc(&pl.tiles, pl.h_tiles.size()));
         FB_CUDA(cudaMemcpy(pl.tiles, pl.h_tiles.data(), sizeof(RcrTile) * pl.h_tiles.size(), cudaMemcpyHostToDevice));
     }
-    FB_CHECK(fb_stg_build(pl, op->theta_rep, op->per_dir, &pl.stg, &pl.stg_elems));
+    FB_CHECK(fb_stg_build(pl, op->theta_slot, op->per_dir, &pl.stg, &pl.stg_elems));
     if (pl.stg_elems > op->stg_elems) {
         FB_CUDA(cudaDeviceSynchronize());
         dfree(op->stg_u);
@@ -881,6 +885,8 @@ void fb_fmm_destroy(fb_op* op) {
     dfree(op->stg_u);
     dfree(op->stg_v);
     op->stg_elems = 0;
+    if (op->rotf) cudaFree(op->rotf);
+    op->rotf = nullptr;
 }
 
 // ---------------------------------------------------------------------------

@@ -656,6 +656,7 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
         oct_dir_l2l[o] = get_dir(-sx, -sy, -sz);  // child - parent
     }
     int ndir = (int)dirs.size() / 3;
+    op->dir_of_code = dir_of_code;
     // directions sharing a polar angle share their real rotation factors d^n
     // (D^n_{mu,m} = d^n_{mu,m}(theta) e^{i m phi}): representative of each
     // direction = the first direction with the same cos(theta) = dz / |d|,
@@ -672,6 +673,18 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
                 op->theta_rep[a] = b;
                 break;
             }
+        }
+    }
+    // polar-angle groups: one folded rotation table each (staged RCR)
+    op->theta_slot.assign(ndir, -1);
+    op->theta_dirs.clear();
+    for (int a = 0; a < ndir; ++a) {
+        const int rep = op->theta_rep[a];
+        if (rep == a) {
+            op->theta_slot[a] = (int)op->theta_dirs.size();
+            op->theta_dirs.push_back(a);
+        } else {
+            op->theta_slot[a] = op->theta_slot[rep];
         }
     }
     // coaxial sets
@@ -782,6 +795,7 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
     op->Prot = Prot;
     op->per_dir = per_dir;
     free_coax();
+    FB_CHECK(fb_stg_tables(op, rset->d64, s));
     // composed matrices are built on demand (tensor-core levels below,
     // everything for the composed method or for inspection)
     op->h_jobs = jobs;

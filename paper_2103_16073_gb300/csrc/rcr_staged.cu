@@ -196,52 +196,100 @@ __device__ __forceinline__ void stg_mainloop(StgSmem<R, CA>& sm, int K, LA load_
 // and y_{+-m'} = (Y+ +- Y-)/2.  Folded layout of a degree-n block of u and
 // v: E_0..E_n at offsets 0..n, O_1..O_n at n+1..2n.
 //
+// Folded rotation tables of a polar-angle group (per degree n at fo(n)):
+//   R table, part 0: [mu][m] (n+1)^2, m = 0 -> 2 d_{mu,0}, else d_{mu,m} + d_{mu,-m};
+//            part 1: [mu-1][m-1] n^2, d_{mu,m} - d_{mu,-m};
+//   B table, part 0: [m'][mu] (n+1)^2, mu = 0 -> d_{0,m'}, else d_{mu,m'} + d_{-mu,m'};
+//            part 1: [m'-1][mu-1] n^2, d_{mu,m'} - d_{-mu,m'};
+// both row-major with K (the summed index) contiguous.  Group g holds its R
+// table at g * 2 fper and its B table at g * 2 fper + fper.
+__host__ __device__ __forceinline__ int64_t fo(int n) {
+    return (int64_t)(n - 1) * n * (2 * n - 1) / 3 + (int64_t)n * n;
+}
+
+template <class R>
+__global__ void k_fold_tables(const double* __restrict__ rotd, int64_t per_dir, const int* __restrict__ rep_dirs,
+                              int P, R* __restrict__ out, int64_t fper) {
+    const int n = blockIdx.x, g = blockIdx.y;
+    const int w = 2 * n + 1;
+    const double* Dc = rotd + (int64_t)rep_dirs[g] * per_dir + rot_off(n) + (int64_t)n * w + n;   // d_{0,0}
+    R* Rt = out + (int64_t)g * 2 * fper + fo(n);
+    R* Bt = Rt + fper;
+    const int n0 = (n + 1) * (n + 1), n1 = n * n;
+    for (int e = threadIdx.x; e < n0 + n1; e += blockDim.x) {
+        const int part = e < n0 ? 0 : 1;
+        const int q = part ? e - n0 : e;
+        const int nb = n + 1 - part;
+        const int a = q / nb + part, b = q % nb + part;   // (row, column) indices
+        double rv, bv;
+        // R: row mu = a, column m = b;  B: row m' = a, column mu = b
+        if (part == 0) {
+            rv = b == 0 ? 2.0 * Dc[(int64_t)a * w] : Dc[(int64_t)a * w + b] + Dc[(int64_t)a * w - b];
+            bv = b == 0 ? Dc[a] : Dc[(int64_t)b * w + a] + Dc[-(int64_t)b * w + a];
+        } else {
+            rv = Dc[(int64_t)a * w + b] - Dc[(int64_t)a * w - b];
+            bv = Dc[(int64_t)b * w + a] - Dc[-(int64_t)b * w + a];
+        }
+        Rt[e] = (R)rv;
+        Bt[e] = (R)bv;
+    }
+}
+
+// ---------------------------------------------------------- pre-pass P ----
+// X0[slot][n^2 + j]: the folded phased input of each pair (x_m =
+// e^{i m phi_slot} src[slot][n^2 + n + m]; j <= n: s_j, j > n: t_{j-n}),
+// written once so that the rotation GEMMs read contiguous columns.
+template <class R>
+__global__ void k_stg_prep(const StgSlot* __restrict__ slots, int nslot, const cx<R>* __restrict__ src,
+                           const cx<R>* __restrict__ rph, int prot, int Pin, int S, cx<R>* __restrict__ X0) {
+    const int64_t total = (int64_t)nslot * Pin;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        const int sl = (int)(q / Pin), e = (int)(q % Pin);
+        const StgSlot s = slots[sl];
+        int n = (int)sqrtf((float)e);
+        while (n * n > e) --n;
+        while ((n + 1) * (n + 1) <= e) ++n;
+        const int j = e - n * n;
+        const cx<R>* x = src + s.src_off + (int64_t)n * n + n;   // (n, 0)
+        const cx<R>* ph = rph + (int64_t)s.dir * (2 * prot - 1) + (prot - 1);
+        cx<R> v;
+        if (j == 0) {
+            v = x[0];
+        } else {
+            const int m = j <= n ? j : j - n;
+            const cx<R> xp = x[m] * ph[m], xm = x[-m] * ph[-m];
+            v = j <= n ? xp + xm : xp - xm;
+        }
+        X0[(int64_t)sl * S + e] = v;
+    }
+}
+
 // ------------------------------------------------------------- pass R ----
 // part 0: U[slot][n^2 + mu] = E_mu (mu = 0..n); part 1: U[slot][n^2 + n + mu] = O_mu
-// (mu = 1..n), from x_m = e^{i m phi_slot} src[slot][n^2 + n + m].
+// (mu = 1..n), from the folded inputs X0 and the R table.
 template <class R>
 __global__ void __launch_bounds__(STHREADS, 2) k_stg_rot(const StgTile* __restrict__ tiles,
-                                                         const StgSlot* __restrict__ slots,
-                                                         const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
-                                                         int64_t per_dir, int prot, const cx<R>* __restrict__ src,
-                                                         cx<R>* __restrict__ U, int S) {
+                                                         const R* __restrict__ rf, int64_t fper,
+                                                         const cx<R>* __restrict__ X0, cx<R>* __restrict__ U,
+                                                         int S) {
     extern __shared__ __align__(16) unsigned char stg_smem[];
     StgSmem<R, false>& sm = *reinterpret_cast<StgSmem<R, false>*>(stg_smem);
     const StgTile tl = tiles[blockIdx.x];
-    const int n = tl.n, w = 2 * n + 1;
+    const int n = tl.n;
     const int part = tl.part;
     const int lo = part;                  // first mu (rows) and first m (K) of the block
     const int nb = n + 1 - part;          // rows = K = n + 1 (even) or n (odd)
     const int tid = threadIdx.x;
-    if (tid < SBN) {
-        if (tid < tl.ncol) {
-            StgSlot sl = slots[tl.col0 + tid];
-            sm.col_off[tid] = sl.src_off + (int64_t)n * n + n;   // entry (n, 0)
-            sm.col_aux[tid] = sl.dir;
-        } else {
-            sm.col_off[tid] = -1;
-            sm.col_aux[tid] = 0;
-        }
-    }
+    const int64_t xoff = (int64_t)n * n + (part ? n + 1 : 0);
+    if (tid < SBN) sm.col_off[tid] = tid < tl.ncol ? (int64_t)(tl.col0 + tid) * S + xoff : -1;
     __syncthreads();
-    const R* Dc = rotd + (int64_t)tl.adir * per_dir + rot_off(n) + (int64_t)n * w + n;   // d_{0,0}
+    const R* A = rf + (int64_t)tl.adir * 2 * fper + fo(n) + (part ? (int64_t)(n + 1) * (n + 1) : 0) +
+                 (int64_t)tl.row0 * nb;
     const int M = min(SBM, nb - tl.row0);
-    auto load_a = [&](int r, int k) -> R {
-        if (r >= M || k >= nb) return R(0);
-        const int mu = lo + tl.row0 + r, m = lo + k;
-        const R* row = Dc + (int64_t)mu * w;
-        if (m == 0) return R(2) * row[0];
-        return part ? row[m] - row[-m] : row[m] + row[-m];
-    };
+    auto load_a = [&](int r, int k) -> R { return (r < M && k < nb) ? A[(int64_t)r * nb + k] : R(0); };
     auto load_x = [&](int c, int k) -> cx<R> {
         const int64_t o = sm.col_off[c];
-        if (o < 0 || k >= nb) return mk<R>(0, 0);
-        const int m = lo + k;
-        const cx<R>* ph = rph + (int64_t)sm.col_aux[c] * (2 * prot - 1) + (prot - 1);
-        const cx<R> xp = src[o + m] * ph[m];
-        if (m == 0) return xp;
-        const cx<R> xm = src[o - m] * ph[-m];
-        return part ? xp - xm : xp + xm;
+        return (o < 0 || k >= nb) ? mk<R>(0, 0) : X0[o + k];
     };
     cx<R> acc[4][4];
     stg_mainloop<R, false, true>(sm, nb, load_a, load_x, acc);
@@ -334,17 +382,18 @@ __device__ __forceinline__ void atomic_add_cx<double>(cd* d, const cd& v) {
 template <class R>
 __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restrict__ tiles,
                                                           const StgSlot* __restrict__ slots,
-                                                          const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
-                                                          int64_t per_dir, int prot, const cx<R>* __restrict__ V,
-                                                          cx<R>* __restrict__ dst, int S, int pin, int pout) {
+                                                          const R* __restrict__ rf, int64_t fper,
+                                                          const cx<R>* __restrict__ rph, int prot,
+                                                          const cx<R>* __restrict__ V, cx<R>* __restrict__ dst, int S,
+                                                          int pin, int pout) {
     extern __shared__ __align__(16) unsigned char stg_smem[];
     StgSmem<R, false>& sm = *reinterpret_cast<StgSmem<R, false>*>(stg_smem);
     const StgTile tl = tiles[blockIdx.x];
-    const int n = tl.n, w = 2 * n + 1;
+    const int n = tl.n;
     const int part = tl.part;
     const int lo = part;
     const int mmax = min(n, pin - 1);
-    const int nrow = n + 1 - part;          // m' = lo .. n
+    const int nrow = n + 1 - part;          // m' = lo .. n; also the table's row stride
     const int K = mmax + 1 - part;          // mu = lo .. mmax
     const int tid = threadIdx.x;
     if (tid < SBN) {
@@ -358,15 +407,10 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restr
         }
     }
     __syncthreads();
-    const R* Dc = rotd + (int64_t)tl.adir * per_dir + rot_off(n) + (int64_t)n * w + n;   // d_{0,0}
+    const R* A = rf + (int64_t)tl.adir * 2 * fper + fper + fo(n) + (part ? (int64_t)(n + 1) * (n + 1) : 0) +
+                 (int64_t)tl.row0 * nrow;
     const int M = min(SBM, nrow - tl.row0);
-    auto load_a = [&](int r, int k) -> R {
-        if (r >= M || k >= K) return R(0);
-        const int mp = lo + tl.row0 + r, mu = lo + k;
-        if (mu == 0) return Dc[mp];
-        const R a = Dc[(int64_t)mu * w + mp], b = Dc[-(int64_t)mu * w + mp];
-        return part ? a - b : a + b;
-    };
+    auto load_a = [&](int r, int k) -> R { return (r < M && k < K) ? A[(int64_t)r * nrow + k] : R(0); };
     const int64_t col_base = (int64_t)tl.col0 * S;
     auto load_x = [&](int c, int k) -> cx<R> {
         if (c >= tl.ncol || k >= K) return mk<R>(0, 0);
@@ -374,7 +418,7 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restr
         return V[col_base + (int64_t)c * S + moff(part ? -mu : mu, pout) + (n - mu)];
     };
     cx<R> acc[4][4];
-    stg_mainloop<R, false, false>(sm, K, load_a, load_x, acc);
+    stg_mainloop<R, false, true>(sm, K, load_a, load_x, acc);
     const int ty = tid >> 4, tx = tid & 15;
     const R sgn = part ? R(-1) : R(1);
 #pragma unroll
@@ -443,11 +487,11 @@ int fb_rcr_default_staged(int p_in, int p_out, size_t csize) {
 }
 
 // Builds the staged passes of the tasks of `pl` that fb_stg_staged selects.
-// theta_rep[dir] is a direction with the same polar angle as dir (the
-// group's representative; its real factors d^n serve the whole group).
+// theta_slot[dir] is the polar-angle group of direction dir (the index of
+// the group's folded rotation tables).
 // *elems receives the complex coefficients one staging buffer needs (the
 // largest level: pairs x max(p_in, p_out)^2).
-fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_rep, int64_t per_dir, void** out,
+fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, int64_t per_dir, void** out,
                        int64_t* elems) {
     *out = nullptr;
     *elems = 0;
@@ -477,7 +521,7 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_rep, int
         std::vector<int> group_order;
         for (int t : ts) {
             int dir = (int)(pl.h_tasks[t].rot_off / per_dir);
-            int rep = theta_rep.at(dir);
+            int rep = theta_slot.at(dir);
             if (!groups.count(rep)) group_order.push_back(rep);
             groups[rep].push_back(t);
         }
@@ -572,16 +616,48 @@ void fb_stg_free(void*& plan) {
     plan = nullptr;
 }
 
+// Folded rotation tables of an operator (both passes, every polar-angle
+// group, degrees < Prot) from the FP64 real factors, in the operator's
+// precision.
+fb_status fb_stg_tables(fb_op* op, const double* rotd64, cudaStream_t s) {
+    const int ng = (int)op->theta_dirs.size();
+    if (ng == 0 || op->Prot < 1) return FB_OK;
+    const int P = op->Prot;
+    op->rotf_per = fo(P);
+    int* d_dirs = nullptr;
+    FB_CHECK(dalloc(&d_dirs, (size_t)ng));
+    FB_CUDA(cudaMemcpyAsync(d_dirs, op->theta_dirs.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, s));
+    const size_t count = (size_t)ng * 2 * op->rotf_per;
+    fb_status st;
+    if (op->prec == FB_PREC_MIXED_FMM) {
+        float* t = nullptr;
+        st = dalloc(&t, count);
+        if (st == FB_OK) k_fold_tables<float><<<dim3(P, ng), 256, 0, s>>>(rotd64, op->per_dir, d_dirs, P, t, op->rotf_per);
+        op->rotf = t;
+    } else {
+        double* t = nullptr;
+        st = dalloc(&t, count);
+        if (st == FB_OK) k_fold_tables<double><<<dim3(P, ng), 256, 0, s>>>(rotd64, op->per_dir, d_dirs, P, t, op->rotf_per);
+        op->rotf = t;
+    }
+    cudaError_t e = cudaStreamSynchronize(s);
+    dfree(d_dirs);
+    FB_CHECK(st);
+    if (e != cudaSuccess) return fb_fail(FB_ERR_CUDA, std::string("folded rotation tables: ") + cudaGetErrorString(e));
+    fb_count_launch();
+    return FB_OK;
+}
+
 // Runs the staged passes of a plan for nrhs right-hand sides (set r of the
 // expansions at src / dst + r * rstride), one right-hand side and one level
-// at a time through the staging buffers U and V.
+// at a time: pre-pass (src -> V), rotation (V -> U), coaxial (U -> V),
+// back-rotation (V -> dst).
 template <class R>
-static fb_status stg_run(void* plan, const R* rotd, const cx<R>* rph, int64_t per_dir, int prot,
-                         const cx<R>* coax, const cx<R>* src, cx<R>* dst, cx<R>* U, cx<R>* V, cudaStream_t s,
-                         int nrhs, int64_t rstride) {
+static fb_status stg_run(void* plan, const R* rf, int64_t fper, const cx<R>* rph, int prot, const cx<R>* coax,
+                         const cx<R>* src, cx<R>* dst, cx<R>* U, cx<R>* V, cudaStream_t s, int nrhs, int64_t rstride) {
     StgPlanImpl* P = (StgPlanImpl*)plan;
     if (!P) return FB_OK;
-    if (!U || !V) return fb_fail(FB_ERR_STATE, "staged RCR: staging buffers missing");
+    if (!U || !V || !rf) return fb_fail(FB_ERR_STATE, "staged RCR: staging buffers or tables missing");
     const size_t sm_rc = sizeof(StgSmem<R, false>), sm_c = sizeof(StgSmem<R, true>);
     FB_CHECK(fb_smem_cap((const void*)k_stg_rot<R>, sm_rc));
     FB_CHECK(fb_smem_cap((const void*)k_stg_coax<R>, sm_c));
@@ -590,24 +666,26 @@ static fb_status stg_run(void* plan, const R* rotd, const cx<R>* rph, int64_t pe
         const cx<R>* sr = src + r * rstride;
         cx<R>* dr = dst + r * rstride;
         for (const StgLevel& lv : P->levels) {
-            if (lv.nrt)
-                k_stg_rot<R><<<lv.nrt, STHREADS, sm_rc, s>>>(lv.rt, lv.slots, rotd, rph, per_dir, prot, sr, U, lv.S);
+            const int64_t tot = (int64_t)lv.nslot * lv.p_in * lv.p_in;
+            const int pb = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+            k_stg_prep<R><<<pb, 256, 0, s>>>(lv.slots, lv.nslot, sr, rph, prot, lv.p_in * lv.p_in, lv.S, V);
+            if (lv.nrt) k_stg_rot<R><<<lv.nrt, STHREADS, sm_rc, s>>>(lv.rt, rf, fper, V, U, lv.S);
             if (lv.nct) k_stg_coax<R><<<lv.nct, STHREADS, sm_c, s>>>(lv.ct, lv.cidx, coax, U, V, lv.S, lv.p_out);
             if (lv.nbt)
-                k_stg_back<R><<<lv.nbt, STHREADS, sm_rc, s>>>(lv.bt, lv.slots, rotd, rph, per_dir, prot, V, dr, lv.S,
+                k_stg_back<R><<<lv.nbt, STHREADS, sm_rc, s>>>(lv.bt, lv.slots, rf, fper, rph, prot, V, dr, lv.S,
                                                               lv.p_in, lv.p_out);
             FB_LAUNCH_CHECK();
-            fb_count_launch(3);
+            fb_count_launch(4);
         }
     }
     return FB_OK;
 }
 
-fb_status fb_stg_run_f(void* plan, const float* rotd, const cf* rph, int64_t per_dir, int prot, const cf* coax,
+fb_status fb_stg_run_f(void* plan, const float* rf, int64_t fper, const cf* rph, int prot, const cf* coax,
                        const cf* src, cf* dst, cf* U, cf* V, cudaStream_t s, int nrhs, int64_t rstride) {
-    return stg_run<float>(plan, rotd, rph, per_dir, prot, coax, src, dst, U, V, s, nrhs, rstride);
+    return stg_run<float>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride);
 }
-fb_status fb_stg_run_d(void* plan, const double* rotd, const cd* rph, int64_t per_dir, int prot, const cd* coax,
+fb_status fb_stg_run_d(void* plan, const double* rf, int64_t fper, const cd* rph, int prot, const cd* coax,
                        const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride) {
-    return stg_run<double>(plan, rotd, rph, per_dir, prot, coax, src, dst, U, V, s, nrhs, rstride);
+    return stg_run<double>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride);
 }

@@ -92,3 +92,74 @@ def test_largest_exterior_source(largest):
         fb.fb_precond_destroy(pclow)
         fb.fb_operator_destroy(Alow)
         fb.fb_operator_destroy(L64)
+
+
+def test_largest_rotation_factors_to_degree_158(largest):
+    """The rotation data at the largest room's degrees (up to 158; every
+    direction from the quarter-turn identity on the device): each real factor
+    block d^n is orthogonal, obeys d_{-mu,-m} = d_{mu,m} (the folding of the
+    translation kernels relies on it), and its column m = 0 matches the
+    closed form sqrt(4 pi/(2n+1)) conj(Y_n^mu(Q z)) evaluated by the oracle's
+    spherical harmonics at one point (Q: the rotation taking the direction to
+    +z)."""
+    import math
+    from oracle import sph
+    wl, mesh, tree, A32, A64 = largest
+    n_, L, p = fb.fb_operator_info(A64)
+    top = max(p) - 1
+    worst = {"orth": 0.0, "sym": 0.0, "col": 0.0}
+    for d in ((2, 0, 0), (2, 2, 2), (3, -1, 2), (-2, 3, -3)):
+        code = (d[0] + 3) * 49 + (d[1] + 3) * 7 + (d[2] + 3)
+        Q = sph.rotation_to_z(np.array(d, float))
+        qz = Q @ np.array([0.0, 0.0, 1.0])
+        Y = sph.ylm(top + 1, np.array([math.acos(max(-1.0, min(1.0, qz[2])))]),
+                    np.array([math.atan2(qz[1], qz[0])]))[:, 0]
+        for n in (0, 1, 40, 97, 131, top):
+            w = 2 * n + 1
+            dn = fb.fb_operator_export(A64, 8, n, code).real.reshape(w, w)
+            worst["orth"] = max(worst["orth"], float(np.max(np.abs(dn @ dn.T - np.eye(w)))))
+            worst["sym"] = max(worst["sym"], float(np.max(np.abs(dn[::-1, ::-1] - dn))))
+            col = math.sqrt(4 * math.pi / w) * np.conj(Y[n * n:(n + 1) ** 2])
+            worst["col"] = max(worst["col"], float(np.max(np.abs(dn[:, n] - col.real))))
+            assert np.max(np.abs(col.imag)) < 1e-12   # the m = 0 column carries no phase
+    print(f"degree <= {top}: {worst}")
+    assert top >= 150
+    assert worst["orth"] < 1e-11 and worst["sym"] < 1e-12 and worst["col"] < 1e-11
+
+
+def test_largest_image_source_sanity(largest):
+    """The room's own monopole against the truncated image-source sum of
+    Eq. (an2) (images of the shoebox, amplitudes the products of the wall
+    reflection coefficients R = (1 - beta)/(1 + beta), dropped below 1e-7):
+    the image model's angle-independent reflection is not the impedance
+    boundary condition the BEM solves, so the two differ at the level the
+    paper reports (16 %), not to rounding; a sanity bound of 0.3 in relative
+    L2 over the 1,024 receivers."""
+    wl, mesh, tree, A32, A64 = largest
+    L64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_L, fb.FB_PREC_FP64_FMM, 6.0, 12)
+    Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 0.5, 2)
+    pclow = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
+    inner = fb.fb_precond_create_inner(A32, Alow, pclow, 14)
+    try:
+        src = wl.sources[0]
+        g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
+        fb.fb_gamma_monopole(mesh, wl.k, src, g)
+        b = torch.empty_like(g)
+        fb.fb_operator_apply(L64, g, b)
+        x = torch.zeros_like(b)
+        info = fb.fb_fgmres_solve(A32, b, x, pc=inner, tol=1e-5, restart=40, maxit=400, max_refine=6, true_op=A64)
+        assert info["status"] == 0 and info["true_relres"] <= 1e-5
+        rcv = torch.tensor(wl.receivers, device="cuda")
+        bem_field = torch.empty(wl.receivers.shape[0], dtype=torch.complex128, device="cuda")
+        fb.fb_eval_field(mesh, wl.k, x, g, rcv, bem_field, src=src)
+        beta_wall = np.array([wl.beta[wl.wall == w][0] for w in range(6)])
+        R = (1 - beta_wall) / (1 + beta_wall)
+        img = fb.fb_image_field(wl.room, src, R, wl.k, rcv, a_th=1e-7)[0]
+        e = rel(bem_field.cpu().numpy(), img.cpu().numpy())
+        print(f"BEM vs image sources at 1,024 receivers: {e:.3f}; iterations {info['iters']}")
+        assert e <= 0.3
+    finally:
+        fb.fb_precond_destroy(inner)
+        fb.fb_precond_destroy(pclow)
+        fb.fb_operator_destroy(Alow)
+        fb.fb_operator_destroy(L64)

@@ -220,3 +220,103 @@ def test_rotation_factors_from_quarter_turn_identity():
             d = np.einsum("ak,bk,abk->ab", Dl[n], Dl[n], C)
             worst = max(worst, float(np.max(np.abs(d * np.exp(1j * m[None, :] * ph) - D[n]))))
     assert worst < 1e-12
+
+
+def _real_factor(t, p):
+    """d^n of direction t: the rotation blocks with the phase e^{i m phi} of
+    the input index removed (D^n_{mu,m} = d^n_{mu,m} e^{i m phi})."""
+    t = np.asarray(t, float)
+    ph = math.atan2(t[1], t[0])
+    D = sph.rotation_blocks(sph.rotation_to_z(t), p)
+    out = []
+    for n in range(p):
+        m = np.arange(-n, n + 1)
+        d = D[n] * np.exp(-1j * m[None, :] * ph)
+        assert np.max(np.abs(d.imag)) < 1e-13
+        out.append(d.real)
+    return out
+
+
+def test_rotation_factor_symmetry_and_polar_angle_sharing():
+    """The folded rotations of the translation kernels rest on two facts of
+    the definition: d^n_{-mu,-m} = d^n_{mu,m}, and d^n depends on the polar
+    angle of the direction only (directions of equal theta share it)."""
+    p = 24
+    base = _real_factor([2.0, 1.0, 2.0], p)
+    same = [[1.0, 2.0, 2.0], [-2.0, 1.0, 2.0], [2.0, -1.0, 2.0]]   # |t| = 3, t_z = 2: same theta
+    for t in same:
+        d = _real_factor(t, p)
+        for n in range(p):
+            assert np.max(np.abs(d[n] - base[n])) < 1e-13
+    for t in ([2.0, 1.0, 2.0], [1.0, -3.0, -1.0], [0.0, 0.0, 1.0], [1.0, 1.0, 0.0]):
+        d = _real_factor(t, p)
+        for n in range(p):
+            assert np.max(np.abs(d[n][::-1, ::-1] - d[n])) < 1e-13
+
+
+def test_folded_rotation_reproduces_plain_rotation():
+    """Even / odd folding of one rotation block, as the kernels compute it:
+    with s_m = x_m + x_{-m}, t_m = x_m - x_{-m}, s_0 = x_0,
+    E_mu = 2 d_{mu,0} s_0 + sum_{m>0} (d_{mu,m} + d_{mu,-m}) s_m = u_mu + u_{-mu}
+    and O_mu = sum_{m>0} (d_{mu,m} - d_{mu,-m}) t_m = u_mu - u_{-mu} for
+    u = d x; the back-rotation folds the same way with d^T."""
+    rng = np.random.default_rng(11)
+    p = 20
+    d_all = _real_factor([1.0, -2.0, 3.0], p)
+    for n in (0, 1, 7, 19):
+        d = d_all[n]
+        x = rng.standard_normal(2 * n + 1) + 1j * rng.standard_normal(2 * n + 1)
+        u = d @ x
+        c = n   # index of m = 0
+        s = np.array([x[c]] + [x[c + m] + x[c - m] for m in range(1, n + 1)])
+        tt = np.array([x[c + m] - x[c - m] for m in range(1, n + 1)])
+        for mu in range(0, n + 1):
+            E = 2 * d[c + mu, c] * s[0] + sum((d[c + mu, c + m] + d[c + mu, c - m]) * s[m] for m in range(1, n + 1))
+            assert abs(E - (u[c + mu] + u[c - mu])) < 1e-12 * (1 + np.abs(u).max())
+            if mu > 0:
+                O = sum((d[c + mu, c + m] - d[c + mu, c - m]) * tt[m - 1] for m in range(1, n + 1))
+                assert abs(O - (u[c + mu] - u[c - mu])) < 1e-12 * (1 + np.abs(u).max())
+        # back-rotation y = d^T v from the folded v
+        v = rng.standard_normal(2 * n + 1) + 1j * rng.standard_normal(2 * n + 1)
+        y = d.T @ v
+        Ev = np.array([2 * v[c]] + [v[c + mu] + v[c - mu] for mu in range(1, n + 1)])
+        Ov = np.array([v[c + mu] - v[c - mu] for mu in range(1, n + 1)])
+        for mp in range(0, n + 1):
+            Yp = d[c, c + mp] * Ev[0] + sum((d[c + mu, c + mp] + d[c - mu, c + mp]) * Ev[mu] for mu in range(1, n + 1))
+            Ym = sum((d[c + mu, c + mp] - d[c - mu, c + mp]) * Ov[mu - 1] for mu in range(1, n + 1))
+            assert abs((Yp + Ym) / 2 - y[c + mp]) < 1e-12 * (1 + np.abs(y).max())
+            assert abs((Yp - Ym) / 2 - y[c - mp]) < 1e-12 * (1 + np.abs(y).max())
+
+
+def test_rotation_column_closed_form():
+    """Column m = 0 of every block from the addition theorem:
+    D^n_{mu,0} = sqrt(4 pi / (2n+1)) conj(Y_n^mu(Q z)) (the projection of
+    Y_n^0(Q^T y) = sqrt((2n+1)/(4 pi)) P_n((Q z).y) on Y_n^mu), against the
+    projection quadrature of the definition; the closed form needs Y_n^mu at
+    one point only, so it also checks rotation data at degrees the
+    projection cannot reach here."""
+    p = 30
+    rng = np.random.default_rng(12)
+    for t in (rng.standard_normal(3), [1.0, 1.0, 1.0], [0.0, -2.0, 1.0]):
+        t = np.asarray(t, float)
+        Q = sph.rotation_to_z(t)
+        D = sph.rotation_blocks(Q, p)
+        qz = Q @ np.array([0.0, 0.0, 1.0])
+        Y = sph.ylm(p, np.array([math.acos(max(-1.0, min(1.0, qz[2])))]), np.array([math.atan2(qz[1], qz[0])]))[:, 0]
+        for n in range(p):
+            col = math.sqrt(4 * math.pi / (2 * n + 1)) * np.conj(Y[n * n:(n + 1) ** 2])
+            assert np.max(np.abs(D[n][:, n] - col)) < 1e-13
+
+
+def test_ylm_unsold_identity_to_degree_158():
+    """Unsold's theorem, sum_m |Y_n^m(x)|^2 = (2n+1)/(4 pi), at every degree
+    below 159 and several points: the spherical harmonics the closed-form
+    rotation check evaluates at the largest room's degrees."""
+    p = 159
+    rng = np.random.default_rng(13)
+    th = np.concatenate([[0.0, math.pi / 2, 1e-3], rng.uniform(0, math.pi, 5)])
+    ph = rng.uniform(-math.pi, math.pi, th.size)
+    Y = sph.ylm(p, th, ph)
+    for n in range(p):
+        s = np.sum(np.abs(Y[n * n:(n + 1) ** 2]) ** 2, axis=0)
+        assert np.max(np.abs(s - (2 * n + 1) / (4 * math.pi))) < 1e-11 * (2 * n + 1)
