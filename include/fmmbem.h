@@ -281,6 +281,27 @@ FB_API fb_status fb_operator_set_translation(fb_op* op, int method);
  * the buffer's address cannot be resolved. */
 FB_API fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y, void* stream);
 
+/* Failure detection of the device waits.  The tensor-core translation
+ * kernels poll mbarriers in bounded loops; when a bound runs out the kernel
+ * records an error flag, waits for the copies and tensor-core operations it
+ * has already issued (they always complete), releases its tensor memory and
+ * returns, so the context stays usable.
+ * fb_operator_status: synchronises `stream` and returns FB_ERR_TIMEOUT if a
+ *   bounded wait of the operator's kernels ran out since the last check
+ *   (clearing the flag), else FB_OK.  fb_fgmres_solve and
+ *   fb_fgmres_solve_multi check their operators the same way when they end
+ *   and report FB_ERR_TIMEOUT as the solve's status.
+ * fb_set_device_wait_limit: polls per wait before giving up (library-wide,
+ *   default 2^26, >= 1; *previous receives the old value if not NULL).
+ * fb_test_stall_device_waits: test hook; while enabled, every tensor-core
+ *   translation kernel first waits on a barrier nothing signals, so that
+ *   wait runs out and the kernel takes the error path above (no fault, no
+ *   hang: every wait is bounded).
+ * Errors: FB_ERR_ARG (NULL operator, limit < 1). */
+FB_API fb_status fb_operator_status(fb_op* op, void* stream);
+FB_API fb_status fb_set_device_wait_limit(long long limit, long long* previous);
+FB_API fb_status fb_test_stall_device_waits(int enable);
+
 /* Measured FMA throughput of the current device (TFLOP/s, 2 flops per FMA)
  * for FP32 and FP64 (either pointer may be NULL): the ALU ceilings of the
  * CUDA-core kernels.  Launches two short kernels per type and synchronises

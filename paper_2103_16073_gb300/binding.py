@@ -732,3 +732,29 @@ def fb_batch_partition(costs, nranks):
     load = np.zeros(int(nranks), np.float64)
     _check(lib.fb_batch_partition(c.ctypes.data, c.shape[0], int(nranks), owner.ctypes.data, load.ctypes.data))
     return owner, load
+
+
+lib.fb_operator_status.restype = C.c_int
+lib.fb_operator_status.argtypes = [C.c_void_p, C.c_void_p]
+lib.fb_set_device_wait_limit.restype = C.c_int
+lib.fb_set_device_wait_limit.argtypes = [C.c_longlong, C.POINTER(C.c_longlong)]
+lib.fb_test_stall_device_waits.restype = C.c_int
+lib.fb_test_stall_device_waits.argtypes = [C.c_int]
+
+
+def fb_operator_status(op, stream=None):
+    """FB_OK, or raises FBError(FB_ERR_TIMEOUT) if a bounded device wait of the
+    operator's kernels ran out since the last check (the flag is cleared)."""
+    _check(lib.fb_operator_status(op, _stream(stream)))
+
+
+def fb_set_device_wait_limit(limit):
+    """Polls per bounded device wait (library-wide); returns the previous value."""
+    prev = C.c_longlong()
+    _check(lib.fb_set_device_wait_limit(int(limit), C.byref(prev)))
+    return prev.value
+
+
+def fb_test_stall_device_waits(enable):
+    """Test hook: tensor-core kernels first wait on a barrier nothing signals."""
+    _check(lib.fb_test_stall_device_waits(int(bool(enable))))

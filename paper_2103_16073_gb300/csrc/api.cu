@@ -66,6 +66,17 @@ fb_status fb_fail(fb_status code, const std::string& msg) {
 
 static cudaStream_t as_stream(void* s) { return (cudaStream_t)s; }
 
+fb_status fb_op_wait_status(const fb_op* op) {
+    if (!op) return FB_OK;
+    if (fb_is_composite(op)) {
+        for (int q = 0; q < 4 && op->sub[q]; ++q) FB_CHECK(fb_op_wait_status(op->sub[q]));
+        return FB_OK;
+    }
+    if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;
+    return fb_tc_check(op);
+}
+
+
 // Temporary device copy of a caller array for host memspace.
 struct Staged {
     void* d = nullptr;
@@ -499,6 +510,24 @@ fb_status fb_operator_info(const fb_op* op, int64_t* n, int* leaf_level, int* p)
     if (n) *n = op->n;
     if (leaf_level) *leaf_level = op->L;
     if (p) for (int l = 0; l <= op->L; ++l) p[l] = op->p[l];
+    return FB_OK;
+}
+
+fb_status fb_operator_status(fb_op* op, void* stream) {
+    if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
+    FB_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    return fb_op_wait_status(op);
+}
+
+fb_status fb_set_device_wait_limit(long long limit, long long* previous) {
+    if (limit < 1) return fb_fail(FB_ERR_ARG, "wait limit must be >= 1");
+    long long old = fb_tc_set_wait_limit(limit);
+    if (previous) *previous = old;
+    return FB_OK;
+}
+
+fb_status fb_test_stall_device_waits(int enable) {
+    fb_tc_set_inject_stall(enable);
     return FB_OK;
 }
 

@@ -464,6 +464,11 @@ fb_status fb_tc_build_groups(fb_op* op, const std::vector<TcGroup>& groups, cons
 fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t s, int nrhs = 1,
                     int64_t rstride = 0);
 fb_status fb_tc_check(const fb_op* op);
+long long fb_tc_set_wait_limit(long long limit);
+int fb_tc_set_inject_stall(int on);
+// Error status of the bounded device waits of an operator (and of the
+// constituents of a composite); reads and clears the flags.
+fb_status fb_op_wait_status(const fb_op* op);
 void fb_tc_free(void*& plan);
 void fb_fmm_destroy(fb_op* op);
 fb_status fb_apply_any(fb_op* op, const cd* x, cd* y, cudaStream_t s, int nrhs = 1);

@@ -481,6 +481,13 @@ fb_status fb_fgmres_impl(fb_op* A, fb_precond* pc, const cd* b, cd* x, const fb_
     }
     inf.true_relres = rn / bn;
     if (status == FB_OK && !(inf.true_relres <= opts.tol)) status = FB_ERR_NOCONV;
+    {
+        // a bounded device wait that ran out invalidates the products it fed
+        fb_status ws = fb_op_wait_status(A);
+        if (ws == FB_OK && T != A) ws = fb_op_wait_status(T);
+        if (ws == FB_OK && pc && pc->inner_op) ws = fb_op_wait_status(pc->inner_op);
+        if (ws != FB_OK) status = ws;
+    }
     inf.status = status;
     if (info) *info = inf;
     if (status != FB_OK) {
@@ -1313,8 +1320,12 @@ fb_status fb_fgmres_multi_impl(fb_op* A, fb_precond* pc, const cd* b, cd* x, int
             if (!std::isfinite(rn[r])) status[r] = FB_ERR_NAN;
         }
     }
+    fb_status waits = fb_op_wait_status(A);
+    if (waits == FB_OK && T != A) waits = fb_op_wait_status(T);
+    if (waits == FB_OK && pc && pc->inner_op) waits = fb_op_wait_status(pc->inner_op);
     fb_status worst = FB_OK;
     for (int r = 0; r < R; ++r) {
+        if (waits != FB_OK) status[r] = waits;
         inf[r].true_relres = bn[r] > 0 ? rn[r] / bn[r] : 0.0;
         int stt = status[r];
         if (stt == FB_OK && !(inf[r].true_relres <= opts.tol)) stt = FB_ERR_NOCONV;

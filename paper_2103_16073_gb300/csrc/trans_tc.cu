@@ -29,6 +29,7 @@
 // Every mbarrier wait is bounded; on timeout the kernel records an error
 // flag, drains its own copies and MMAs (bounded) and releases tensor memory.
 #include <algorithm>
+#include <atomic>
 
 #include <map>
 
@@ -46,7 +47,9 @@ constexpr int STAGE_FLOATS = 2 * A_BLOCK + 2 * B_BLOCK;
 constexpr int SBO = (TC_KC / 4) * 128;      // bytes between 8-row groups
 constexpr int LBO = 128;                    // bytes between K-adjacent core matrices
 constexpr int NPROD = 192;                  // B producer threads (warps 0-5)
-constexpr long WAIT_LIMIT = 1L << 26;
+// Bound of the drain waits (copies and MMAs this CTA has issued always
+// complete; the bound only keeps a broken device from hanging the kernel).
+constexpr long long DRAIN_LIMIT = 1LL << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -68,8 +71,8 @@ __device__ __forceinline__ float tf32_hi(float v) {
     return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (long it = 0; it < WAIT_LIMIT; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
+    for (long long it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
@@ -163,11 +166,14 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
                                                       const int32_t* __restrict__ dst_idx,
                                                       const float* __restrict__ plane_hi,
                                                       const float* __restrict__ plane_lo, cf* __restrict__ dst,
-                                                      int* __restrict__ err, int nrhs, int64_t rstride) {
+                                                      int* __restrict__ err, int nrhs, int64_t rstride,
+                                                      long long wait_limit, int inject_stall) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[TC_STAGES];
+    __shared__ __align__(8) uint64_t full_bar[TC_STAGES];    // B producers' cp.async pieces
+    __shared__ __align__(8) uint64_t a_bar[TC_STAGES];       // the A producer's bulk copy
     __shared__ __align__(8) uint64_t empty_bar[TC_STAGES];
     __shared__ __align__(8) uint64_t done_bar;
+    __shared__ __align__(8) uint64_t never_bar;              // test hook: nothing arrives on it
     __shared__ uint32_t tmem_holder;
     __shared__ int s_src[TC_NMAX];       // source vector index in the planes (rhs * nbox + box)
     __shared__ int s_dst[TC_NMAX];
@@ -200,10 +206,12 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
     if (tid == 0) {
         s_fail = 0;
         for (int s = 0; s < TC_STAGES; ++s) {
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_bar[s])), "r"(NPROD + 1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full_bar[s])), "r"(NPROD));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&a_bar[s])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty_bar[s])), "r"(1));
         }
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done_bar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&never_bar)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -216,7 +224,7 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
         const int npieces = nmma * (TC_KC / 4) * 2;   // columns x K pieces x {hi, lo}
         for (int c = 0; c < nkc; ++c) {
             const int s = c % TC_STAGES, u = c / TC_STAGES;
-            if (u > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (u - 1) & 1)) {
+            if (u > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (u - 1) & 1, wait_limit)) {
                 atomicExch(&s_fail, 1);
                 break;
             }
@@ -245,20 +253,26 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
         // ---------------- A producer: one bulk copy per stage ----------------
         if (lane == 0) {
             const float* Atile = Abuf + tk.a_off + (int64_t)tl.rt * nkc * 2 * A_BLOCK;
+            int issued = 0;
             for (int c = 0; c < nkc; ++c) {
                 const int s = c % TC_STAGES, u = c / TC_STAGES;
-                if (u > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (u - 1) & 1)) {
+                if (u > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (u - 1) & 1, wait_limit)) {
                     atomicExch(&s_fail, 1);
                     break;
                 }
-                uint32_t fb = smem_u32(&full_bar[s]);
+                uint32_t ab = smem_u32(&a_bar[s]);
                 uint32_t dA = smem_u32(stage0 + s * STAGE_FLOATS);
                 const float* g = Atile + (int64_t)c * 2 * A_BLOCK;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(2 * A_BLOCK * 4));
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(ab), "r"(2 * A_BLOCK * 4));
                 asm volatile(
                     "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dA),
-                    "l"(g), "r"(2 * A_BLOCK * 4), "r"(fb));
+                    "l"(g), "r"(2 * A_BLOCK * 4), "r"(ab));
+                ++issued;
             }
+            // every bulk copy this CTA issued lands before the CTA may exit
+            // (on success the MMA issuer has already waited for each of them)
+            for (int c = max(0, issued - TC_STAGES); c < issued; ++c)
+                mbar_wait(smem_u32(&a_bar[c % TC_STAGES]), (c / TC_STAGES) & 1, DRAIN_LIMIT);
         }
         __syncwarp();
     } else {
@@ -266,9 +280,13 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nmma >> 3) << 17) |
                                    ((uint32_t)(TC_M >> 4) << 24);
-            for (int c = 0; c < nkc; ++c) {
+            // test hook: a wait on a barrier nothing arrives on runs out
+            const bool stalled = inject_stall && !mbar_wait(smem_u32(&never_bar), 0, wait_limit);
+            if (stalled) atomicExch(&s_fail, 1);
+            for (int c = 0; c < nkc && !stalled; ++c) {
                 const int s = c % TC_STAGES, u = c / TC_STAGES;
-                if (!mbar_wait(smem_u32(&full_bar[s]), u & 1)) {
+                if (!mbar_wait(smem_u32(&full_bar[s]), u & 1, wait_limit) ||
+                    !mbar_wait(smem_u32(&a_bar[s]), u & 1, wait_limit)) {
                     atomicExch(&s_fail, 1);
                     break;
                 }
@@ -295,7 +313,7 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
     }
 
     // ---------------- epilogue ------------------------------------------------
-    bool done = mbar_wait(smem_u32(&done_bar), 0);
+    bool done = mbar_wait(smem_u32(&done_bar), 0, DRAIN_LIMIT);
     __syncthreads();
     const bool ok = done && s_fail == 0;
     if (!ok && tid == 0) atomicExch(err, 1);
@@ -329,10 +347,6 @@ __global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ 
                 }
             }
         }
-    } else if (warp == 6 && lane == 0) {
-        // drain the bulk copies this CTA may still have in flight
-        for (int c = max(0, nkc - TC_STAGES); c < nkc; ++c)
-            mbar_wait(smem_u32(&full_bar[c % TC_STAGES]), (c / TC_STAGES) & 1);
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -358,6 +372,13 @@ struct TcPlanImpl {
     int plane_nrhs = 1;                     // right-hand sides the planes hold
     std::map<int, std::pair<TcTile*, int>> multi;   // tiles for nrhs > 1
 };
+
+// Bound of the pipeline's device waits (mbarrier polls) and the test hook
+// that makes one of them run out; library-wide, read at each launch.
+static std::atomic<long long> g_wait_limit{1LL << 26};
+static std::atomic<int> g_inject_stall{0};
+long long fb_tc_set_wait_limit(long long limit) { return g_wait_limit.exchange(limit); }
+int fb_tc_set_inject_stall(int on) { return g_inject_stall.exchange(on ? 1 : 0); }
 
 size_t fb_tc_smem_bytes() { return (size_t)TC_STAGES * STAGE_FLOATS * sizeof(float) + 1024; }
 
@@ -494,13 +515,15 @@ fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t 
                                   rstride);
     k_trans_tc<<<(unsigned)ntiles, 256, fb_tc_smem_bytes(), s>>>(pl->tasks, tiles, pl->A, pl->src_idx,
                                                                  pl->dst_idx, pl->plane_hi, pl->plane_lo, dst,
-                                                                 pl->err, nrhs, rstride);
+                                                                 pl->err, nrhs, rstride, g_wait_limit.load(),
+                                                                 g_inject_stall.load());
     FB_LAUNCH_CHECK();
     fb_count_launch(2);
     return FB_OK;
 }
 
-// Error flag of the tensor-core kernel (1 = a bounded wait ran out).
+// Error flags of the tensor-core kernels of an operator (1 = a bounded wait
+// ran out); read and cleared (the caller has synchronised the work).
 fb_status fb_tc_check(const fb_op* op) {
     std::vector<void*> plans = {op->tc_plan, op->tc_plan_all};
     for (int l = 0; l <= FB_MAXLEV; ++l) {
@@ -512,7 +535,10 @@ fb_status fb_tc_check(const fb_op* op) {
         if (!pl || !pl->err) continue;
         int h = 0;
         FB_CUDA(cudaMemcpy(&h, pl->err, sizeof(int), cudaMemcpyDeviceToHost));
-        if (h) return fb_fail(FB_ERR_TIMEOUT, "tensor-core translation kernel: a bounded wait ran out");
+        if (h) {
+            FB_CUDA(cudaMemset(pl->err, 0, sizeof(int)));
+            return fb_fail(FB_ERR_TIMEOUT, "tensor-core translation kernel: a bounded wait ran out");
+        }
     }
     return FB_OK;
 }
