@@ -80,14 +80,28 @@ __host__ __device__ __forceinline__ int moff(int m, int p) {
     return (p - 1) * p / 2 + m * p - m * (m - 1) / 2;
 }
 
+constexpr int SSTAGES = 3;   // shared-memory stages of the copy pipeline
+
 template <class R, bool CA>
 struct StgSmem {
     using AT = typename std::conditional<CA, cx<R>, R>::type;
-    alignas(16) AT A[2][SBK][SBM + (CA ? 2 : 4)];   // padded rows (16-byte aligned, fewer bank conflicts)
-    alignas(16) cx<R> X[2][SBK][SBN + 2];
+    alignas(16) AT A[SSTAGES][SBK][SBM + (CA ? 2 : 4)];   // padded rows (16-byte aligned, fewer bank conflicts)
+    alignas(16) cx<R> X[SSTAGES][SBK][SBN + 2];
     int64_t col_off[SBN];
     int32_t col_aux[SBN];
 };
+
+// asynchronous global -> shared copy of one operand (BYTES = 4, 8 or 16),
+// zero-filled when `valid` is false (src is then only a valid address)
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const int n = valid ? BYTES : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES), "r"(n));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
 
 template <class R>
 __device__ __forceinline__ void fma_ax(cx<R>& acc, R a, const cx<R>& x) {
@@ -122,64 +136,60 @@ __device__ __forceinline__ void ld4(cd (&o)[4], const cd* p) {
     }
 }
 
-// acc[i][j] (rows ty*4+i, columns tx*4+j) += sum_k A[row][k] X[k][col] over
-// k < K.  load_a(r, k) / load_x(c, k) return the (bounds-checked) operands;
-// AK: A is contiguous along k (staging threads walk k fastest).
-template <class R, bool CA, bool AK, class LA, class LX>
-__device__ __forceinline__ void stg_mainloop(StgSmem<R, CA>& sm, int K, LA load_a, LX load_x, cx<R> (&acc)[4][4]) {
+// acc[i][j] (rows ty*4+i, columns tx+16j) += sum_k A[row][k] X[k][col] over
+// k < K.  aptr(r, k) / xptr(c, k) give the global address of an operand, or
+// nullptr for a zero (outside the block); A is contiguous along k.  The
+// operands of chunk kc + SSTAGES - 1 are copied while chunk kc is computed.
+template <class R, bool CA, class PA, class PX>
+__device__ __forceinline__ void stg_mainloop(StgSmem<R, CA>& sm, int K, PA aptr, PX xptr, const void* dummy,
+                                             cx<R> (&acc)[4][4]) {
     using AT = typename StgSmem<R, CA>::AT;
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
-    AT ra[4];
-    cx<R> rx[4];
-    auto fetch = [&](int k0) {
+    auto issue = [&](int b, int k0) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int e = tid + i * STHREADS;
-            const int r = AK ? e / SBK : e % SBM;
-            const int k = AK ? e % SBK : e / SBM;
-            ra[i] = load_a(r, k0 + k);
-            const int c = e / SBK, kk = e % SBK;
-            rx[i] = load_x(c, k0 + kk);
-        }
-    };
-    auto stash = [&](int b) {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const int e = tid + i * STHREADS;
-            const int r = AK ? e / SBK : e % SBM;
-            const int k = AK ? e % SBK : e / SBM;
-            sm.A[b][k][r] = ra[i];
-            const int c = e / SBK, kk = e % SBK;
-            sm.X[b][kk][c] = rx[i];
+            const int r = e / SBK, k = e % SBK;
+            const AT* pa = aptr(r, k0 + k);
+            cp_async<sizeof(AT)>(&sm.A[b][k][r], pa ? (const void*)pa : dummy, pa != nullptr);
+            const cx<R>* px = xptr(r, k0 + k);   // column r of the X tile, same (e / 16, e % 16) split
+            cp_async<sizeof(cx<R>)>(&sm.X[b][k][r], px ? (const void*)px : dummy, px != nullptr);
         }
     };
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = mk<R>(0, 0);
-    fetch(0);
-    stash(0);
-    __syncthreads();
-    int cur = 0;
-    for (int k0 = 0; k0 < K; k0 += SBK) {
-        const bool more = k0 + SBK < K;
-        if (more) fetch(k0 + SBK);
+    const int nk = (K + SBK - 1) / SBK;
+#pragma unroll
+    for (int st = 0; st < SSTAGES - 1; ++st) {
+        if (st < nk) issue(st, st * SBK);
+        cp_commit();
+    }
+    for (int kc = 0; kc < nk; ++kc) {
+        cp_wait<SSTAGES - 2>();   // chunk kc has landed (this thread's copies)
+        __syncthreads();          // ... and every thread's; chunk kc - 1 is no longer read
+        const int nxt = kc + SSTAGES - 1;
+        if (nxt < nk) issue(nxt % SSTAGES, nxt * SBK);
+        cp_commit();
+        const int b = kc % SSTAGES;
 #pragma unroll
         for (int kk = 0; kk < SBK; ++kk) {
             AT a[4];
             cx<R> x[4];
-            ld4(a, &sm.A[cur][kk][ty * 4]);
-            ld4(x, &sm.X[cur][kk][tx * 4]);
+            ld4(a, &sm.A[b][kk][ty * 4]);
+            // columns tx + 16 j: each load of the half-warp reads 16
+            // consecutive operands (no bank conflicts)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] = sm.X[b][kk][tx + 16 * j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) fma_ax(acc[i][j], a[i], x[j]);
         }
-        if (more) stash(cur ^ 1);
-        __syncthreads();
-        cur ^= 1;
     }
+    cp_wait<0>();
 }
 
 // The real factors obey d^n_{-mu,-m} = d^n_{mu,m} (for Q = R_y(-theta)
@@ -286,18 +296,18 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_rot(const StgTile* __restri
     const R* A = rf + (int64_t)tl.adir * 2 * fper + fo(n) + (part ? (int64_t)(n + 1) * (n + 1) : 0) +
                  (int64_t)tl.row0 * nb;
     const int M = min(SBM, nb - tl.row0);
-    auto load_a = [&](int r, int k) -> R { return (r < M && k < nb) ? A[(int64_t)r * nb + k] : R(0); };
-    auto load_x = [&](int c, int k) -> cx<R> {
+    auto aptr = [&](int r, int k) -> const R* { return (r < M && k < nb) ? A + (int64_t)r * nb + k : nullptr; };
+    auto xptr = [&](int c, int k) -> const cx<R>* {
         const int64_t o = sm.col_off[c];
-        return (o < 0 || k >= nb) ? mk<R>(0, 0) : X0[o + k];
+        return (o < 0 || k >= nb) ? nullptr : X0 + o + k;
     };
     cx<R> acc[4][4];
-    stg_mainloop<R, false, true>(sm, nb, load_a, load_x, acc);
+    stg_mainloop<R, false>(sm, nb, aptr, xptr, (const void*)rf, acc);
     const int ty = tid >> 4, tx = tid & 15;
     const int obase = n * n + (part ? n : 0) + lo + tl.row0;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int c = tx * 4 + j;
+        const int c = tx + 16 * j;
         if (c >= tl.ncol) continue;
         cx<R>* u = U + (int64_t)(tl.col0 + c) * S + obase;
 #pragma unroll
@@ -338,21 +348,19 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_coax(const StgCTile* __rest
     const cx<R>* A = coax + tl.a_off + (int64_t)tl.row0 * tl.pc;
     const int M = min(SBM, tl.M - tl.row0);
     const int K = tl.K, pc = tl.pc;
-    auto load_a = [&](int r, int k) -> cx<R> {
-        return (r < M && k < K) ? A[(int64_t)r * pc + k] : mk<R>(0, 0);
-    };
-    auto load_x = [&](int c, int k) -> cx<R> {
+    auto aptr = [&](int r, int k) -> const cx<R>* { return (r < M && k < K) ? A + (int64_t)r * pc + k : nullptr; };
+    auto xptr = [&](int c, int k) -> const cx<R>* {
         const int64_t o = sm.col_off[c];
-        if (o < 0 || k >= K) return mk<R>(0, 0);
+        if (o < 0 || k >= K) return nullptr;
         const int nn = am + k;
-        return U[o + (int64_t)nn * nn + (sm.col_aux[c] ? nn : 0) + am];
+        return U + o + (int64_t)nn * nn + (sm.col_aux[c] ? nn : 0) + am;
     };
     cx<R> acc[4][4];
-    stg_mainloop<R, true, true>(sm, K, load_a, load_x, acc);
+    stg_mainloop<R, true>(sm, K, aptr, xptr, (const void*)coax, acc);
     const int ty = tid >> 4, tx = tid & 15;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int c = tx * 4 + j;
+        const int c = tx + 16 * j;
         if (c >= tl.nvc) continue;
         cx<R>* v = V + sm.col_off[c] + moff(sm.col_aux[c] ? -am : am, pout) + tl.row0;
 #pragma unroll
@@ -410,20 +418,20 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restr
     const R* A = rf + (int64_t)tl.adir * 2 * fper + fper + fo(n) + (part ? (int64_t)(n + 1) * (n + 1) : 0) +
                  (int64_t)tl.row0 * nrow;
     const int M = min(SBM, nrow - tl.row0);
-    auto load_a = [&](int r, int k) -> R { return (r < M && k < K) ? A[(int64_t)r * nrow + k] : R(0); };
+    auto aptr = [&](int r, int k) -> const R* { return (r < M && k < K) ? A + (int64_t)r * nrow + k : nullptr; };
     const int64_t col_base = (int64_t)tl.col0 * S;
-    auto load_x = [&](int c, int k) -> cx<R> {
-        if (c >= tl.ncol || k >= K) return mk<R>(0, 0);
+    auto xptr = [&](int c, int k) -> const cx<R>* {
+        if (c >= tl.ncol || k >= K) return nullptr;
         const int mu = lo + k;
-        return V[col_base + (int64_t)c * S + moff(part ? -mu : mu, pout) + (n - mu)];
+        return V + col_base + (int64_t)c * S + moff(part ? -mu : mu, pout) + (n - mu);
     };
     cx<R> acc[4][4];
-    stg_mainloop<R, false, true>(sm, K, load_a, load_x, acc);
+    stg_mainloop<R, false>(sm, K, aptr, xptr, (const void*)rf, acc);
     const int ty = tid >> 4, tx = tid & 15;
     const R sgn = part ? R(-1) : R(1);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
-        const int c = tx * 4 + j;
+        const int c = tx + 16 * j;
         if (c >= tl.ncol) continue;
         const cx<R>* ph = rph + (int64_t)sm.col_aux[c] * (2 * prot - 1) + (prot - 1);
         cx<R>* d = dst + sm.col_off[c];   // entry (n, 0) of the target
