@@ -170,7 +170,7 @@ def bench_config(name, wl, ws):
             "parallelism": f"replicas x{ws} (one (f, source) solve per GPU)"}
 
 
-def build_problem(fb, W, torch, wl, rank, forms="", forms_inner=""):
+def build_problem(fb, W, torch, wl, rank, forms="", forms_inner="", forms_fp64=""):
     """Mesh, tree and the operators of a solve: mixed A (autotuned translation
     forms, graph replay), FP64 A (true residual, plain method), FP64 L
     (b = L gamma), block Jacobi of each, and the inner-outer preconditioner
@@ -193,8 +193,9 @@ def build_problem(fb, W, torch, wl, rank, forms="", forms_inner=""):
         tune = {"fixed_forms": forms}
     else:
         tune = {"mixed": fb.fb_operator_autotune(A32, 1)}
-    if forms:
-        fb.fb_operator_set_forms(A64, [int(v) & 12 for v in forms.split(",")])
+    if forms_fp64 or forms:
+        fb.fb_operator_set_forms(A64, [int(v) & 12 for v in (forms_fp64 or forms).split(",")])
+        tune["fp64_fixed_forms"] = forms_fp64 or forms
     else:
         tune["fp64"] = fb.fb_operator_autotune(A64, 1)
     for op in (A32, A64):
@@ -410,9 +411,12 @@ def run_matvecs(args):
         fb.fb_operator_autotune(op, 1)
     stream = torch.cuda.current_stream()
     t, ph = matvec_rate(fb, torch, stream, op, wl.n, args.matvec_only)
+    passes = fb.fb_operator_staged_pass_times(op)
     print(json.dumps({"workload": WORKLOADS[args.workload][1], "precision": args.prec, "d0": d0, "pmin": pmin,
                       "orders": [int(v) for v in fb.fb_operator_info(op)[2][2:]], "matvec_ms": round(t * 1e3, 4),
-                      "phase_ms": {k: round(v, 4) for k, v in ph.items()}}))
+                      "phase_ms": {k: round(v, 4) for k, v in ph.items()},
+                      "staged_pass_ms": {l: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in d.items()}
+                                         for l, d in passes.items()}}))
     fb.fb_operator_destroy(op)
     fb.fb_tree_destroy(tree)
     fb.fb_mesh_destroy(mesh)
@@ -430,7 +434,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl" if dist.is_nccl_available() else "gloo")
     wl = load_workload(args.workload)
-    P = build_problem(fb, W, torch, wl, rank, args.forms, args.forms_inner)
+    P = build_problem(fb, W, torch, wl, rank, args.forms, args.forms_inner, args.forms_fp64)
     n = wl.n
     stream = torch.cuda.current_stream()
     pc_main = P["inner"]
@@ -723,6 +727,7 @@ def main():
                                                 "operators instead of autotuning (comma-separated choice ints "
                                                 "by level, as fb_operator_set_forms; the FP64 one takes bits 2-3)")
     ap.add_argument("--forms-inner", default="", help="the same for the low-accuracy inner operator")
+    ap.add_argument("--forms-fp64", default="", help="the same for the FP64 operator (default: --forms)")
     ap.add_argument("--ref-matvecs", type=int, default=52,
                     help="matvecs per solve used to extrapolate the reference arm (default: the plain "
                          "method's 51 block-Jacobi iterations on the largest room + 1 true residual)")

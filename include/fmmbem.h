@@ -299,6 +299,18 @@ FB_API fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y
  *   hang: every wait is bounded).
  * Errors: FB_ERR_ARG (NULL operator, limit < 1). */
 FB_API fb_status fb_operator_status(fb_op* op, void* stream);
+
+/* Profiling: device time of each pass of the staged RCR M2L (Sec. 3.3) of
+ * every staged level of an FMM operator, one right-hand side, on the
+ * operator's own expansion and staging buffers (their contents are
+ * overwritten; apply the operator again before using its result).  Each
+ * pass is launched alone between CUDA events on `stream`, once untimed and
+ * three times timed (median).  ms: 4*13 doubles, ms[4l + 0..3] = pre-pass
+ * (folded phased inputs), rotation, coaxial, back-rotation of level l (-1:
+ * level not staged); tc: 13 ints, 1 where the level's rotation passes run
+ * on the tensor cores.  Synchronises the device.
+ * Errors: FB_ERR_ARG (NULL argument, dense or composite operator). */
+FB_API fb_status fb_operator_staged_pass_times(fb_op* op, void* stream, double* ms, int* tc);
 FB_API fb_status fb_set_device_wait_limit(long long limit, long long* previous);
 FB_API fb_status fb_test_stall_device_waits(int enable);
 
@@ -336,24 +348,33 @@ FB_API fb_status fb_precond_use_graphs(fb_precond* pc, int enable);
  *   - rotation-coaxial-rotation as staged batched GEMMs (the pairs of a
  *     level grouped by the polar angle of their translation direction for
  *     the rotations and by |t| for the coaxial step),
+ *   - mixed precision only: the staged passes with their two rotation
+ *     passes on the tensor cores (3xTF32 GEMMs of the folded real rotation
+ *     blocks, one polar-angle group and degree at a time),
  *   - mixed precision only: the stacked tensor-core GEMM of composed
  *     matrices (3xTF32).
  * Tiles are timed below order 60, the staged passes from order 24 on (the
  * measured crossover lies between); a level keeps at least one candidate.
- * times: 6*13 doubles or NULL, times[6l + 0..5] = M2L RCR tiles, M2L tensor,
- * M2M+L2L RCR tiles, M2M+L2L tensor, M2L RCR staged, M2M+L2L RCR staged in
- * ms (-1: not a candidate); choice: 13 ints or NULL, bit 0 = M2L of level l
- * on the tensor cores, bit 1 = M2M/L2L into level l on the tensor cores,
- * bit 2 = M2L of level l by staged RCR, bit 3 = M2M/L2L into level l by
- * staged RCR.  Rebuilds the operator's translation plans (synchronises the
- * device).  Errors: FB_ERR_ARG. */
+ * times: FB_TUNE_TIMES*13 doubles or NULL, times[FB_TUNE_TIMES l + 0..7] =
+ * M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles, M2M+L2L tensor, M2L RCR
+ * staged, M2M+L2L RCR staged, M2L RCR staged with tensor-core rotations,
+ * M2M+L2L RCR staged with tensor-core rotations in ms (-1: not a candidate);
+ * choice: 13 ints or NULL, bit 0 = M2L of level l on the tensor cores,
+ * bit 1 = M2M/L2L into level l on the tensor cores, bit 2 = M2L of level l
+ * by staged RCR, bit 3 = M2M/L2L into level l by staged RCR, bit 4 = the
+ * staged M2L's rotations on the tensor cores (with bit 2), bit 5 = the
+ * staged M2M/L2L's rotations on the tensor cores (with bit 3).  Rebuilds the
+ * operator's translation plans (synchronises the device).
+ * Errors: FB_ERR_ARG. */
+#define FB_TUNE_TIMES 8
 FB_API fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times, int* choice);
 
 /* Installs a per-level choice in the format the autotuner returns (13 ints,
  * bits as above), so that a tuned configuration can be saved and restored
  * without timing.  Levels whose per-pair RCR working set does not fit one
- * CTA run staged whatever bit 2/3 says.  Tensor-core bits need a
- * mixed-precision operator.  Errors: FB_ERR_ARG. */
+ * CTA run staged whatever bit 2/3 says.  Tensor-core bits (0, 1, 4, 5) need
+ * a mixed-precision operator; bit 4 needs bit 2 and bit 5 needs bit 3.
+ * Errors: FB_ERR_ARG. */
 FB_API fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream);
 FB_API fb_status fb_operator_apply_multi(fb_op* op, const double* x, double* y, int nrhs, int memspace,
                                          void* stream);

@@ -33,7 +33,7 @@ __all__ = [
     "fb_precond_create_learned", "fb_learned_params", "fb_learned_set_objective",
     "fb_precond_create_inner", "FB_PC_INNER", "FB_PC_LEARNED", "fb_krylov_basis",
     "FB_LOSS_ERROR", "FB_LOSS_RESIDUAL", "fb_learned_loss_and_grad", "fb_learned_train_step",
-    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "fb_operator_autotune", "fb_operator_set_forms", "fb_batch_solve", "fb_operator_use_graphs", "fb_precond_use_graphs",
+    "fb_operator_apply_multi", "fb_fgmres_solve_multi", "FB_MAX_RHS", "FB_TUNE_TIMES", "fb_operator_autotune", "fb_operator_set_forms", "fb_batch_solve", "fb_operator_use_graphs", "fb_precond_use_graphs",
     "SolverOpts", "SolveInfo",
 ]
 
@@ -352,6 +352,7 @@ def fb_operator_apply_noalloc(op, x, y, stream=None):
 
 
 FB_MAX_RHS = 64
+FB_TUNE_TIMES = 8   # autotuner timings per level
 lib.fb_operator_apply_multi.restype = C.c_int
 lib.fb_operator_apply_multi.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
 lib.fb_fgmres_solve_multi.restype = C.c_int
@@ -401,22 +402,26 @@ def fb_operator_autotune(op, nrhs=1, stream=None):
     """Times the translation forms per level (RCR as per-pair tiles, RCR as
     staged GEMM passes, tensor-core composed GEMMs for mixed operators) and
     installs the fastest; returns {level: {"m2l_rcr", "m2l_tensor",
-    "m2m_l2l_rcr", "m2m_l2l_tensor", "m2l_staged", "m2m_l2l_staged" (ms, None
-    if not a candidate), "m2l_on_tensor", "m2m_l2l_on_tensor", "m2l_staged_on",
-    "m2m_l2l_staged_on", "choice"}}."""
-    times = np.full(6 * 13, -1.0)
+    "m2m_l2l_rcr", "m2m_l2l_tensor", "m2l_staged", "m2m_l2l_staged",
+    "m2l_staged_tc", "m2m_l2l_staged_tc" (ms, None if not a candidate),
+    "m2l_on_tensor", "m2m_l2l_on_tensor", "m2l_staged_on", "m2m_l2l_staged_on",
+    "m2l_staged_tc_on", "m2m_l2l_staged_tc_on", "choice"}}."""
+    nt = FB_TUNE_TIMES
+    times = np.full(nt * 13, -1.0)
     choice = np.zeros(13, np.int32)
     _check(lib.fb_operator_autotune(op, int(nrhs), _stream(stream), times.ctypes.data, choice.ctypes.data))
     out = {}
     for l in range(13):
-        t = times[6 * l:6 * l + 6]
+        t = times[nt * l:nt * l + nt]
         if np.all(t < 0):
             continue
         f = lambda v: None if v < 0 else round(float(v), 4)
         out[l] = {"m2l_rcr": f(t[0]), "m2l_tensor": f(t[1]), "m2m_l2l_rcr": f(t[2]), "m2m_l2l_tensor": f(t[3]),
-                  "m2l_staged": f(t[4]), "m2m_l2l_staged": f(t[5]),
+                  "m2l_staged": f(t[4]), "m2m_l2l_staged": f(t[5]), "m2l_staged_tc": f(t[6]),
+                  "m2m_l2l_staged_tc": f(t[7]),
                   "m2l_on_tensor": bool(choice[l] & 1), "m2m_l2l_on_tensor": bool(choice[l] & 2),
                   "m2l_staged_on": bool(choice[l] & 4), "m2m_l2l_staged_on": bool(choice[l] & 8),
+                  "m2l_staged_tc_on": bool(choice[l] & 16), "m2m_l2l_staged_tc_on": bool(choice[l] & 32),
                   "choice": int(choice[l])}
     return out
 
@@ -740,6 +745,27 @@ lib.fb_set_device_wait_limit.restype = C.c_int
 lib.fb_set_device_wait_limit.argtypes = [C.c_longlong, C.POINTER(C.c_longlong)]
 lib.fb_test_stall_device_waits.restype = C.c_int
 lib.fb_test_stall_device_waits.argtypes = [C.c_int]
+
+
+lib.fb_operator_staged_pass_times.restype = C.c_int
+lib.fb_operator_staged_pass_times.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+
+
+def fb_operator_staged_pass_times(op, stream=None):
+    """{level: {"prep", "rot", "coax", "back" (device ms of each staged M2L
+    pass alone), "tensor_rot" (rotations on the tensor cores)}} for the
+    operator's staged levels; overwrites its expansion buffers."""
+    ms = np.full(4 * 13, -1.0)
+    tc = np.zeros(13, np.int32)
+    _check(lib.fb_operator_staged_pass_times(op, _stream(stream), ms.ctypes.data, tc.ctypes.data))
+    out = {}
+    for l in range(13):
+        t = ms[4 * l:4 * l + 4]
+        if np.all(t < 0):
+            continue
+        out[l] = {"prep": float(t[0]), "rot": float(t[1]), "coax": float(t[2]), "back": float(t[3]),
+                  "tensor_rot": bool(tc[l])}
+    return out
 
 
 def fb_operator_status(op, stream=None):

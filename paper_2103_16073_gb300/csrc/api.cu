@@ -473,7 +473,7 @@ fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times,
     if (op->prec == FB_PREC_FP64_DENSE) return fb_fail(FB_ERR_ARG, "dense operators have no translations");
     if (nrhs < 1 || nrhs > FB_MAX_RHS) return fb_fail(FB_ERR_ARG, "nrhs must be in [1, FB_MAX_RHS]");
     if (times)
-        for (int i = 0; i < 6 * (FB_MAXLEV + 1); ++i) times[i] = -1.0;
+        for (int i = 0; i < FB_TUNE_TIMES * (FB_MAXLEV + 1); ++i) times[i] = -1.0;
     if (choice)
         for (int i = 0; i <= FB_MAXLEV; ++i) choice[i] = 0;
     if (fb_is_composite(op)) {   // each constituent operator; times/choice of the first
@@ -517,6 +517,13 @@ fb_status fb_operator_status(fb_op* op, void* stream) {
     if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
     FB_CUDA(cudaStreamSynchronize(as_stream(stream)));
     return fb_op_wait_status(op);
+}
+
+fb_status fb_operator_staged_pass_times(fb_op* op, void* stream, double* ms, int* tc) {
+    if (!op || !ms || !tc) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (fb_is_composite(op) || op->prec == FB_PREC_FP64_DENSE)
+        return fb_fail(FB_ERR_ARG, "staged pass times need an FMM operator");
+    return fb_stg_op_pass_times(op, as_stream(stream), ms, tc);
 }
 
 fb_status fb_set_device_wait_limit(long long limit, long long* previous) {

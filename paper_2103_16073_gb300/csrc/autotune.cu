@@ -4,7 +4,8 @@
 //   * rotation - coaxial - rotation (RCR, Sec. 3.3) as per-pair tiles
 //     (where a pair's working set fits a CTA's shared memory),
 //   * RCR as staged batched GEMM passes (pairs grouped by polar angle and by
-//     |t|; rcr_staged.cu),
+//     |t|; rcr_staged.cu), in mixed precision also with the rotation passes
+//     on the tensor cores (rcr_staged_tc.cu),
 //   * mixed precision only: the stacked tensor-core GEMM of composed
 //     matrices (3xTF32),
 // for M2L and for the M2M / L2L passes into that level.  The tensor-core
@@ -86,14 +87,16 @@ fb_status time_rcr(fb_op* op, const RcrPlan& base, Pick pick, int staged, void* 
     return st;
 }
 
-// times[6 * l + {0..5}] = M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles,
-// M2M+L2L tensor, M2L RCR staged, M2M+L2L RCR staged (ms, -1 when not a
-// candidate) for l = 0..L; choice[l] bit 0 = M2L on the tensor cores, bit 1 =
-// M2M/L2L into level l on the tensor cores, bit 2 = M2L by staged RCR, bit 3
-// = M2M/L2L into level l by staged RCR.
+// times[8 * l + {0..7}] = M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles,
+// M2M+L2L tensor, M2L RCR staged, M2M+L2L RCR staged, M2L RCR staged with
+// tensor-core rotations, M2M+L2L RCR staged with tensor-core rotations (ms, -1
+// when not a candidate) for l = 0..L; choice[l] bit 0 = M2L on the tensor
+// cores, bit 1 = M2M/L2L into level l on the tensor cores, bit 2 = M2L by
+// staged RCR, bit 3 = M2M/L2L into level l by staged RCR, bit 4 = the staged
+// M2L's rotations on the tensor cores, bit 5 = the same for M2M/L2L.
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_out, int* choice) {
     const bool mixed = op->prec == FB_PREC_MIXED_FMM;
-    double times_local[6 * (FB_MAXLEV + 1)];
+    double times_local[FB_TUNE_TIMES * (FB_MAXLEV + 1)];
     double* times = times_out ? times_out : times_local;   // callers may pass NULL
     const fb_tree* t = op->tree;
     const int L = op->L;
@@ -119,20 +122,25 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
     std::vector<int> tc_m2l;
     int stg_m2l[FB_MAXLEV + 1] = {0}, stg_pair[FB_MAXLEV + 1] = {0};
     for (int l = 2; l <= L; ++l) {
-        double* tl = times + 6 * l;
-        for (int q = 0; q < 6; ++q) tl[q] = -1.0;
+        double* tl = times + FB_TUNE_TIMES * l;
+        for (int q = 0; q < FB_TUNE_TIMES; ++q) tl[q] = -1.0;
         int ch = 0;
         // ---- M2L of level l: RCR tiles, RCR staged, tensor cores
         auto at_level = [&](const RcrTask& tk) { return tk.src_base == op->lev_off[l] && tk.dst_base == tk.src_base; };
         if (rcr_tile_candidate(op->p[l], csz))
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 0, mp, loc, s, nrhs, cnt, reps, &tl[0]));
-        if (rcr_staged_candidate(op->p[l], csz))
+        if (rcr_staged_candidate(op->p[l], csz)) {
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 1, mp, loc, s, nrhs, cnt, reps, &tl[4]));
+            if (mixed) FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 2, mp, loc, s, nrhs, cnt, reps, &tl[6]));
+        }
         double best = -1.0;
         if (tl[0] >= 0) best = tl[0];
-        if (tl[4] >= 0 && (best < 0 || tl[4] < best)) {
-            best = tl[4];
-            stg_m2l[l] = 1;
+        for (int form = 1; form <= 2; ++form) {
+            const double v = tl[form == 1 ? 4 : 6];
+            if (v >= 0 && (best < 0 || v < best)) {
+                best = v;
+                stg_m2l[l] = form;
+            }
         }
         if (mixed && best >= 0) {
             int64_t p2 = (int64_t)op->p[l] * op->p[l];
@@ -168,12 +176,12 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                 }
             }
         }
-        if (stg_m2l[l] && !(ch & 1)) ch |= 4;
+        if (stg_m2l[l] && !(ch & 1)) ch |= stg_m2l[l] == 2 ? 4 | 16 : 4;
         // ---- M2M + L2L between levels l-1 and l
         if (l >= 3) {
             const int pm = std::max(op->p[l], op->p[l - 1]);
             auto all = [](const RcrTask&) { return true; };
-            double rt = -1.0, rs = -1.0;
+            double rt = -1.0, rs = -1.0, rc = -1.0;
             if (rcr_tile_candidate(pm, csz)) {
                 double a = 0, b = 0;
                 FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 0, mp, mp, s, nrhs, cnt, reps, &a));
@@ -185,13 +193,23 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                 FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 1, mp, mp, s, nrhs, cnt, reps, &a));
                 FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 1, loc, loc, s, nrhs, cnt, reps, &b));
                 rs = std::max(a, 0.0) + std::max(b, 0.0);
+                if (mixed) {
+                    FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 2, mp, mp, s, nrhs, cnt, reps, &a));
+                    FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 2, loc, loc, s, nrhs, cnt, reps, &b));
+                    rc = std::max(a, 0.0) + std::max(b, 0.0);
+                }
             }
             tl[2] = rt;
             tl[5] = rs;
+            tl[7] = rc;
             double best2 = rt;
             if (rt < 0 || (rs >= 0 && rs < rt)) {
                 best2 = rs;
                 stg_pair[l] = 1;
+            }
+            if (rc >= 0 && rc < best2) {
+                best2 = rc;
+                stg_pair[l] = 2;
             }
             std::vector<int> need;
             std::vector<TcGroup> up, down;
@@ -223,7 +241,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                     fb_tc_free(op->tc_l2l[l]);
                 }
             }
-            if (stg_pair[l] && !(ch & 2)) ch |= 8;
+            if (stg_pair[l] && !(ch & 2)) ch |= stg_pair[l] == 2 ? 8 | 32 : 8;
         }
         if (choice) choice[l] = ch;
     }
@@ -264,18 +282,19 @@ fb_status fb_install_forms(fb_op* op, const std::vector<int>& tc_m2l, cudaStream
     return FB_OK;
 }
 
-// Installs a given per-level choice (bits as returned by the autotuner):
-// bit 0 = M2L of level l on the tensor cores, bit 1 = M2M/L2L into level l on
-// the tensor cores; lets a tuned configuration be saved and restored.
+// Installs a given per-level choice (bits as returned by the autotuner);
+// lets a tuned configuration be saved and restored.
 fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s) {
     const fb_tree* t = op->tree;
     const int L = op->L;
     int stg_m2l[FB_MAXLEV + 1] = {0}, stg_pair[FB_MAXLEV + 1] = {0};
     for (int l = 2; l <= L; ++l) {
-        if (op->prec != FB_PREC_MIXED_FMM && (choice[l] & 3))
+        if (op->prec != FB_PREC_MIXED_FMM && (choice[l] & (1 | 2 | 16 | 32)))
             return fb_fail(FB_ERR_ARG, "tensor-core forms apply to mixed operators");
-        stg_m2l[l] = (choice[l] & 4) ? 1 : 0;
-        stg_pair[l] = (choice[l] & 8) ? 1 : 0;
+        if (((choice[l] & 16) && !(choice[l] & 4)) || ((choice[l] & 32) && !(choice[l] & 8)))
+            return fb_fail(FB_ERR_ARG, "bits 4/5 (tensor-core rotations) refine the staged bits 2/3");
+        stg_m2l[l] = (choice[l] & 4) ? ((choice[l] & 16) ? 2 : 1) : 0;
+        stg_pair[l] = (choice[l] & 8) ? ((choice[l] & 32) ? 2 : 1) : 0;
     }
     FB_CHECK(fb_rcr_restage(op, stg_m2l, stg_pair));
     if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;

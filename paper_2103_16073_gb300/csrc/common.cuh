@@ -260,10 +260,25 @@ bool fb_stg_staged(const RcrTask& tk);
 fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, int64_t per_dir, void** out,
                        int64_t* elems);
 void fb_stg_free(void*& plan);
+// tables of the tensor-core rotation passes of the staged levels that use them
+struct StcTabs {
+    const float* tab;
+    const int64_t* off;
+    int64_t per;
+    int* err;
+};
+// Runs the staged passes of a plan (pass_mask bits: pre-pass, rotation,
+// coaxial, back-rotation; only_level >= 0: that level of the plan alone).
 fb_status fb_stg_run_f(void* plan, const float* rf, int64_t fper, const cf* rph, int prot, const cf* coax,
-                       const cf* src, cf* dst, cf* U, cf* V, cudaStream_t s, int nrhs, int64_t rstride);
+                       const cf* src, cf* dst, cf* U, cf* V, cudaStream_t s, int nrhs, int64_t rstride,
+                       const StcTabs& tc, int only_level = -1, int pass_mask = 15);
+bool fb_stg_uses_tc(const void* plan);
 fb_status fb_stg_run_d(void* plan, const double* rf, int64_t fper, const cd* rph, int prot, const cd* coax,
-                       const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride);
+                       const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride,
+                       int only_level = -1, int pass_mask = 15);
+int fb_stg_level_count(const void* plan);
+fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* tc);
+void fb_stg_level_info(const void* plan, int li, int64_t* src_base, int64_t* dst_base, int* tc);
 struct fb_op;
 fb_status fb_stg_tables(fb_op* op, const double* rotd64, cudaStream_t s);
 
@@ -336,6 +351,11 @@ struct fb_op {
     std::vector<int> theta_dirs;             // group -> its representative direction
     void* rotf = nullptr;                    // folded rotation tables (staged RCR), per group
     int64_t rotf_per = 0;                    // values per group and table
+    float* stc_tab = nullptr;                // pre-split canonical tables of the tensor-core staged passes
+    int64_t* stc_off = nullptr;              // their block offsets per (degree, part)
+    int64_t stc_per = 0;                     // floats per group and table
+    int stc_P = 0;
+    int* stc_err = nullptr;                  // error flag of the tensor-core staged passes
     std::vector<int> dir_of_code;            // M2L offset code -> direction (-1: near)
     // RCR form per level: 1 = staged passes, 0 = per-pair tiles (M2L of
     // level l; M2M and L2L between levels l-1 and l)
@@ -465,6 +485,9 @@ fb_status fb_tc_run(fb_op* op, void* plan, const cf* src, cf* dst, cudaStream_t 
                     int64_t rstride = 0);
 fb_status fb_tc_check(const fb_op* op);
 long long fb_tc_set_wait_limit(long long limit);
+long long fb_tc_wait_limit();
+int fb_tc_inject_stall();
+fb_status fb_stc_tables(fb_op* op, cudaStream_t s);
 int fb_tc_set_inject_stall(int on);
 // Error status of the bounded device waits of an operator (and of the
 // constituents of a composite); reads and clears the flags.

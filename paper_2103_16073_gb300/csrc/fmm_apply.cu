@@ -580,6 +580,7 @@ struct RotArgs {
     cx<R>* V;
     const void* rf;   // folded rotation tables and their per-group stride
     int64_t fper;
+    StcTabs tc;       // tables of the tensor-core staged passes (single precision)
 };
 template <class R>
 static RotArgs<R> rot_args(const fb_op* op) {
@@ -592,15 +593,72 @@ static RotArgs<R> rot_args(const fb_op* op) {
     a.V = (cx<R>*)op->stg_v;
     a.rf = op->rotf;
     a.fper = op->rotf_per;
+    a.tc = StcTabs{op->stc_tab, op->stc_off, op->stc_per, op->stc_err};
     return a;
 }
 static fb_status stg_run(void* plan, const RotArgs<float>& r, const cf* coax, const cf* src, cf* dst,
                          cudaStream_t s, int nrhs, int64_t rstride) {
-    return fb_stg_run_f(plan, (const float*)r.rf, r.fper, r.ph, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride);
+    return fb_stg_run_f(plan, (const float*)r.rf, r.fper, r.ph, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride,
+                        r.tc);
 }
 static fb_status stg_run(void* plan, const RotArgs<double>& r, const cd* coax, const cd* src, cd* dst,
                          cudaStream_t s, int nrhs, int64_t rstride) {
     return fb_stg_run_d(plan, (const double*)r.rf, r.fper, r.ph, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride);
+}
+
+// Device time (ms, median of 3 after one untimed run, one right-hand side)
+// of each pass of every staged M2L level of an operator, on its expansion
+// buffers: ms[4 l + {0..3}] = pre-pass, rotation, coaxial, back-rotation of
+// level l (-1: not staged); tc[l] = 1 where the rotations run on the tensor
+// cores.
+fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* tc) {
+    for (int i = 0; i < 4 * (FB_MAXLEV + 1); ++i) ms[i] = -1.0;
+    for (int l = 0; l <= FB_MAXLEV; ++l) tc[l] = 0;
+    const bool mixed = op->prec == FB_PREC_MIXED_FMM;
+    RcrPlan& pl = (mixed && op->method == FB_TRANS_AUTO && op->tc_plan) ? op->m2l_rcr_rest : op->m2l_rcr;
+    if (!pl.stg || !op->mp || !op->loc) return FB_OK;
+    cudaEvent_t e0, e1;
+    FB_CUDA(cudaEventCreate(&e0));
+    FB_CUDA(cudaEventCreate(&e1));
+    fb_status st = FB_OK;
+    for (int li = 0; li < fb_stg_level_count(pl.stg) && st == FB_OK; ++li) {
+        int64_t sb = 0, db = 0;
+        int t = 0;
+        fb_stg_level_info(pl.stg, li, &sb, &db, &t);
+        int lev = -1;
+        for (int l = 2; l <= op->L; ++l)
+            if (op->lev_off[l] == sb) lev = l;
+        if (lev < 0 || sb != db) continue;
+        tc[lev] = t;
+        for (int pass = 0; pass < 4 && st == FB_OK; ++pass) {
+            auto run = [&]() {
+                return mixed ? fb_stg_run_f(pl.stg, (const float*)op->rotf, op->rotf_per, (const cf*)op->rph32,
+                                            op->Prot, op->coax32, (const cf*)op->mp, (cf*)op->loc, (cf*)op->stg_u,
+                                            (cf*)op->stg_v, s, 1, 0, rot_args<float>(op).tc, li, 1 << pass)
+                             : fb_stg_run_d(pl.stg, (const double*)op->rotf, op->rotf_per, (const cd*)op->rph64,
+                                            op->Prot, op->coax64, (const cd*)op->mp, (cd*)op->loc, (cd*)op->stg_u,
+                                            (cd*)op->stg_v, s, 1, 0, li, 1 << pass);
+            };
+            std::vector<float> v;
+            st = run();
+            for (int r = 0; r < 3 && st == FB_OK; ++r) {
+                cudaEventRecord(e0, s);
+                st = run();
+                cudaEventRecord(e1, s);
+                if (cudaEventSynchronize(e1) != cudaSuccess) st = fb_fail(FB_ERR_CUDA, "staged pass timing failed");
+                float x = 0.f;
+                cudaEventElapsedTime(&x, e0, e1);
+                v.push_back(x);
+            }
+            if (st == FB_OK) {
+                std::sort(v.begin(), v.end());
+                ms[4 * lev + pass] = v[1];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
 }
 
 template <class R>
@@ -639,7 +697,11 @@ fb_status fb_rcr_upload(fb_op* op, RcrPlan& pl, const int32_t* src, const int32_
         FB_CHECK(dalloc(&pl.tiles, pl.h_tiles.size()));
         FB_CUDA(cudaMemcpy(pl.tiles, pl.h_tiles.data(), sizeof(RcrTile) * pl.h_tiles.size(), cudaMemcpyHostToDevice));
     }
+    for (const RcrTask& tk : pl.h_tasks)
+        if (tk.staged == 2 && op->prec != FB_PREC_MIXED_FMM)
+            return fb_fail(FB_ERR_ARG, "tensor-core staged RCR applies to mixed operators");
     FB_CHECK(fb_stg_build(pl, op->theta_slot, op->per_dir, &pl.stg, &pl.stg_elems));
+    if (fb_stg_uses_tc(pl.stg)) FB_CHECK(fb_stc_tables(op, cudaStreamLegacy));
     if (pl.stg_elems > op->stg_elems) {
         FB_CUDA(cudaDeviceSynchronize());
         dfree(op->stg_u);
@@ -786,10 +848,11 @@ static int task_level(const fb_op* op, const RcrTask& tk, bool* m2l) {
 fb_status fb_rcr_restage(fb_op* op, const int* m2l, const int* pair) {
     const size_t csz = op_csize(op);
     for (int l = 2; l <= op->L; ++l) {
-        op->stg_m2l[l] = (m2l[l] || !fb_rcr_tile_fits(op->p[l], op->p[l], csz)) ? 1 : 0;
+        // 1: staged on CUDA cores, 2: staged with the rotations on the tensor cores
+        op->stg_m2l[l] = m2l[l] ? m2l[l] : (!fb_rcr_tile_fits(op->p[l], op->p[l], csz) ? 1 : 0);
         if (l >= 3) {
             const int pm = std::max(op->p[l], op->p[l - 1]);
-            op->stg_pair[l] = (pair[l] || !fb_rcr_tile_fits(pm, pm, csz)) ? 1 : 0;
+            op->stg_pair[l] = pair[l] ? pair[l] : (!fb_rcr_tile_fits(pm, pm, csz) ? 1 : 0);
         }
     }
     FB_CUDA(cudaDeviceSynchronize());
@@ -887,6 +950,9 @@ void fb_fmm_destroy(fb_op* op) {
     op->stg_elems = 0;
     if (op->rotf) cudaFree(op->rotf);
     op->rotf = nullptr;
+    dfree(op->stc_tab);
+    dfree(op->stc_off);
+    dfree(op->stc_err);
 }
 
 // ---------------------------------------------------------------------------

@@ -36,6 +36,9 @@
 #include <vector>
 
 #include "common.cuh"
+#include "rcr_staged.cuh"
+
+using namespace stg;
 
 namespace {
 
@@ -44,13 +47,6 @@ constexpr int SBN = 64;   // complex columns per tile
 constexpr int SBK = 16;   // K chunk
 constexpr int STHREADS = 256;
 
-// one pair (column) of a staged level
-struct StgSlot {
-    int64_t src_off;   // first coefficient of the source expansion
-    int64_t dst_off;   // first coefficient of the target expansion
-    int32_t dir;       // translation direction (phase table)
-    int32_t pad;
-};
 // tile of pass R (degree n) or B (degree n'): slots [col0, col0 + ncol) of
 // one polar-angle group, rows [row0, row0 + 64) of the even or odd block
 struct StgTile {
@@ -68,17 +64,6 @@ struct StgCTile {
     int32_t am, row0, pc;
     int32_t M, K;
 };
-
-__host__ __device__ __forceinline__ int64_t rot_off(int n) { return (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3; }
-// start of order m in the order-major layout of an order-p expansion
-// (orders -(p-1) .. p-1, order m holding degrees |m| .. p-1)
-__host__ __device__ __forceinline__ int moff(int m, int p) {
-    if (m <= 0) {
-        int a = p + m;   // p - |m|
-        return (a - 1) * a / 2;
-    }
-    return (p - 1) * p / 2 + m * p - m * (m - 1) / 2;
-}
 
 constexpr int SSTAGES = 3;   // shared-memory stages of the copy pipeline
 
@@ -213,9 +198,6 @@ __device__ __forceinline__ void stg_mainloop(StgSmem<R, CA>& sm, int K, PA aptr,
 //            part 1: [m'-1][mu-1] n^2, d_{mu,m'} - d_{-mu,m'};
 // both row-major with K (the summed index) contiguous.  Group g holds its R
 // table at g * 2 fper and its B table at g * 2 fper + fper.
-__host__ __device__ __forceinline__ int64_t fo(int n) {
-    return (int64_t)(n - 1) * n * (2 * n - 1) / 3 + (int64_t)n * n;
-}
 
 template <class R>
 __global__ void k_fold_tables(const double* __restrict__ rotd, int64_t per_dir, const int* __restrict__ rep_dirs,
@@ -453,6 +435,7 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restr
 
 // ------------------------------------------------------------ host plan ----
 struct StgLevel {
+    int64_t src_base = 0, dst_base = 0;   // the level arrays it reads and writes
     int p_in = 0, p_out = 0, S = 0, nslot = 0;
     StgSlot* slots = nullptr;
     int32_t* cidx = nullptr;
@@ -460,6 +443,11 @@ struct StgLevel {
     StgCTile* ct = nullptr;
     StgTile* bt = nullptr;
     int nrt = 0, nct = 0, nbt = 0;
+    // rotation passes on the tensor cores (rcr_staged_tc.cu) instead of rt / bt
+    int tc = 0;
+    StcTile* rtc = nullptr;
+    StcTile* btc = nullptr;
+    int nrtc = 0, nbtc = 0;
 };
 
 struct StgPlanImpl {
@@ -472,6 +460,8 @@ void free_level(StgLevel& lv) {
     dfree(lv.rt);
     dfree(lv.ct);
     dfree(lv.bt);
+    dfree(lv.rtc);
+    dfree(lv.btc);
 }
 
 template <class T>
@@ -521,8 +511,11 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
         const std::vector<int>& ts = kv.second;
         const int p_in = std::get<2>(kv.first), p_out = std::get<3>(kv.first);
         StgLevel lv;
+        lv.src_base = std::get<0>(kv.first);
+        lv.dst_base = std::get<1>(kv.first);
         lv.p_in = p_in;
         lv.p_out = p_out;
+        for (int t : ts) lv.tc = lv.tc || pl.h_tasks[t].staged == 2;
         lv.S = std::max(p_in * p_in, p_out * p_out);
         // polar-angle groups of the tasks, in order of first appearance
         std::map<int, std::vector<int>> groups;   // representative direction -> tasks
@@ -536,6 +529,7 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
         std::vector<StgSlot> slots;
         std::vector<int> slot_task;
         std::vector<StgTile> rt, bt;
+        std::vector<StcTile> rtc, btc;
         for (int rep : group_order) {
             const int g0 = (int)slots.size();
             for (int t : groups[rep]) {
@@ -558,6 +552,11 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
                 }
             }
             const int g1 = (int)slots.size();
+            if (lv.tc) {
+                fb_stc_group_tiles(rep, g0, g1, p_in, 0, p_in, rtc);
+                fb_stc_group_tiles(rep, g0, g1, p_out, 1, p_in, btc);
+                continue;
+            }
             // folded blocks: even rows n + 1, odd rows n (none for n = 0)
             for (int n = 0; n < p_in; ++n)
                 for (int part = 0; part < 2; ++part)
@@ -603,9 +602,29 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
         lv.nrt = (int)rt.size();
         lv.nct = (int)ct.size();
         lv.nbt = (int)bt.size();
+        // heaviest tensor-core tiles first (K chunks x columns), for the tail
+        auto heavier = [&](int pass) {
+            return [pass, p_in](const StcTile& x, const StcTile& y) {
+                auto w = [&](const StcTile& t) {
+                    int64_t c = 0;
+                    for (int n = t.n0; n < t.n1; ++n) {
+                        const int N = n + 1 - t.part;
+                        const int K = pass == 0 ? N : std::min(n, p_in - 1) + 1 - t.part;
+                        c += (int64_t)stc_pad16(N) * ((K + 15) / 16);
+                    }
+                    return c;
+                };
+                return w(x) > w(y);
+            };
+        };
+        std::stable_sort(rtc.begin(), rtc.end(), heavier(0));
+        std::stable_sort(btc.begin(), btc.end(), heavier(1));
+        lv.nrtc = (int)rtc.size();
+        lv.nbtc = (int)btc.size();
         fb_status st;
         if ((st = upload(&lv.slots, slots)) || (st = upload(&lv.cidx, cidx)) || (st = upload(&lv.rt, rt)) ||
-            (st = upload(&lv.ct, ct)) || (st = upload(&lv.bt, bt))) {
+            (st = upload(&lv.ct, ct)) || (st = upload(&lv.bt, bt)) || (st = upload(&lv.rtc, rtc)) ||
+            (st = upload(&lv.btc, btc))) {
             free_level(lv);
             return fail(st);
         }
@@ -660,9 +679,24 @@ fb_status fb_stg_tables(fb_op* op, const double* rotd64, cudaStream_t s) {
 // expansions at src / dst + r * rstride), one right-hand side and one level
 // at a time: pre-pass (src -> V), rotation (V -> U), coaxial (U -> V),
 // back-rotation (V -> dst).
+// Tensor-core rotation passes of a level (single precision only).
+static fb_status stc_pass(const StgLevel& lv, int pass, const StcTabs* tc, const cf* X, cf* out, const cf* rph,
+                          int prot, cudaStream_t s) {
+    if (!tc || !tc->tab) return fb_fail(FB_ERR_STATE, "staged RCR: tensor-core tables missing");
+    const int np = std::max(lv.p_in, lv.p_out);
+    return pass == 0 ? fb_stc_run(0, lv.rtc, lv.nrtc, np, tc->off, tc->tab, tc->per, lv.slots, X, out, lv.S, lv.p_in,
+                                  lv.p_out, rph, prot, tc->err, s)
+                     : fb_stc_run(1, lv.btc, lv.nbtc, np, tc->off, tc->tab, tc->per, lv.slots, X, out, lv.S, lv.p_in,
+                                  lv.p_out, rph, prot, tc->err, s);
+}
+static fb_status stc_pass(const StgLevel&, int, const StcTabs*, const cd*, cd*, const cd*, int, cudaStream_t) {
+    return fb_fail(FB_ERR_ARG, "tensor-core staged RCR applies to single precision");
+}
+
 template <class R>
 static fb_status stg_run(void* plan, const R* rf, int64_t fper, const cx<R>* rph, int prot, const cx<R>* coax,
-                         const cx<R>* src, cx<R>* dst, cx<R>* U, cx<R>* V, cudaStream_t s, int nrhs, int64_t rstride) {
+                         const cx<R>* src, cx<R>* dst, cx<R>* U, cx<R>* V, cudaStream_t s, int nrhs, int64_t rstride,
+                         const StcTabs* tc, int only_level, int pass_mask) {
     StgPlanImpl* P = (StgPlanImpl*)plan;
     if (!P) return FB_OK;
     if (!U || !V || !rf) return fb_fail(FB_ERR_STATE, "staged RCR: staging buffers or tables missing");
@@ -673,27 +707,70 @@ static fb_status stg_run(void* plan, const R* rf, int64_t fper, const cx<R>* rph
     for (int r = 0; r < nrhs; ++r) {
         const cx<R>* sr = src + r * rstride;
         cx<R>* dr = dst + r * rstride;
-        for (const StgLevel& lv : P->levels) {
-            const int64_t tot = (int64_t)lv.nslot * lv.p_in * lv.p_in;
-            const int pb = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
-            k_stg_prep<R><<<pb, 256, 0, s>>>(lv.slots, lv.nslot, sr, rph, prot, lv.p_in * lv.p_in, lv.S, V);
-            if (lv.nrt) k_stg_rot<R><<<lv.nrt, STHREADS, sm_rc, s>>>(lv.rt, rf, fper, V, U, lv.S);
-            if (lv.nct) k_stg_coax<R><<<lv.nct, STHREADS, sm_c, s>>>(lv.ct, lv.cidx, coax, U, V, lv.S, lv.p_out);
-            if (lv.nbt)
-                k_stg_back<R><<<lv.nbt, STHREADS, sm_rc, s>>>(lv.bt, lv.slots, rf, fper, rph, prot, V, dr, lv.S,
-                                                              lv.p_in, lv.p_out);
+        for (int li = 0; li < (int)P->levels.size(); ++li) {
+            if (only_level >= 0 && li != only_level) continue;
+            const StgLevel& lv = P->levels[li];
+            if (pass_mask & 1) {
+                const int64_t tot = (int64_t)lv.nslot * lv.p_in * lv.p_in;
+                const int pb = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+                k_stg_prep<R><<<pb, 256, 0, s>>>(lv.slots, lv.nslot, sr, rph, prot, lv.p_in * lv.p_in, lv.S, V);
+                fb_count_launch();
+            }
+            if (pass_mask & 2) {
+                if (lv.tc) {
+                    FB_CHECK(stc_pass(lv, 0, tc, V, U, rph, prot, s));
+                } else if (lv.nrt) {
+                    k_stg_rot<R><<<lv.nrt, STHREADS, sm_rc, s>>>(lv.rt, rf, fper, V, U, lv.S);
+                    fb_count_launch();
+                }
+            }
+            if ((pass_mask & 4) && lv.nct) {
+                k_stg_coax<R><<<lv.nct, STHREADS, sm_c, s>>>(lv.ct, lv.cidx, coax, U, V, lv.S, lv.p_out);
+                fb_count_launch();
+            }
+            if (pass_mask & 8) {
+                if (lv.tc) {
+                    FB_CHECK(stc_pass(lv, 1, tc, V, dr, rph, prot, s));
+                } else if (lv.nbt) {
+                    k_stg_back<R><<<lv.nbt, STHREADS, sm_rc, s>>>(lv.bt, lv.slots, rf, fper, rph, prot, V, dr, lv.S,
+                                                                  lv.p_in, lv.p_out);
+                    fb_count_launch();
+                }
+            }
             FB_LAUNCH_CHECK();
-            fb_count_launch(4);
         }
     }
     return FB_OK;
 }
 
 fb_status fb_stg_run_f(void* plan, const float* rf, int64_t fper, const cf* rph, int prot, const cf* coax,
-                       const cf* src, cf* dst, cf* U, cf* V, cudaStream_t s, int nrhs, int64_t rstride) {
-    return stg_run<float>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride);
+                       const cf* src, cf* dst, cf* U, cf* V, cudaStream_t s, int nrhs, int64_t rstride,
+                       const StcTabs& tc, int only_level, int pass_mask) {
+    return stg_run<float>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride, &tc, only_level,
+                          pass_mask);
 }
 fb_status fb_stg_run_d(void* plan, const double* rf, int64_t fper, const cd* rph, int prot, const cd* coax,
-                       const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride) {
-    return stg_run<double>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride);
+                       const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride,
+                       int only_level, int pass_mask) {
+    return stg_run<double>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride, nullptr, only_level,
+                           pass_mask);
+}
+
+int fb_stg_level_count(const void* plan) {
+    const StgPlanImpl* P = (const StgPlanImpl*)plan;
+    return P ? (int)P->levels.size() : 0;
+}
+void fb_stg_level_info(const void* plan, int li, int64_t* src_base, int64_t* dst_base, int* tc) {
+    const StgLevel& lv = ((const StgPlanImpl*)plan)->levels[li];
+    *src_base = lv.src_base;
+    *dst_base = lv.dst_base;
+    *tc = lv.tc;
+}
+
+bool fb_stg_uses_tc(const void* plan) {
+    const StgPlanImpl* P = (const StgPlanImpl*)plan;
+    if (!P) return false;
+    for (const StgLevel& lv : P->levels)
+        if (lv.tc) return true;
+    return false;
 }

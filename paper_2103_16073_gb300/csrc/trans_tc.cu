@@ -34,6 +34,7 @@
 #include <map>
 
 #include "common.cuh"
+#include "tc_common.cuh"
 
 namespace {
 
@@ -44,52 +45,16 @@ constexpr int TC_STAGES = 4;
 constexpr int A_BLOCK = TC_M * TC_KC;       // floats per (hi or lo) A block
 constexpr int B_BLOCK = TC_NMAX * TC_KC;    // floats per (hi or lo) B block
 constexpr int STAGE_FLOATS = 2 * A_BLOCK + 2 * B_BLOCK;
-constexpr int SBO = (TC_KC / 4) * 128;      // bytes between 8-row groups
-constexpr int LBO = 128;                    // bytes between K-adjacent core matrices
 constexpr int NPROD = 192;                  // B producer threads (warps 0-5)
-// Bound of the drain waits (copies and MMAs this CTA has issued always
-// complete; the bound only keeps a broken device from hanging the kernel).
-constexpr long long DRAIN_LIMIT = 1LL << 26;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ uint64_t umma_desc(uint32_t addr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((addr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((LBO >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((SBO >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version of sm_100-family tcgen05
-    return d;                  // base offset 0, no swizzle
-}
-
-// byte offset of element (row, k) of a K-major block of TC_KC columns
-__host__ __device__ __forceinline__ int canon(int row, int k) {
-    return (row >> 3) * SBO + (k >> 2) * LBO + (row & 7) * 16 + (k & 3) * 4;
-}
-
-__device__ __forceinline__ float tf32_hi(float v) {
-    return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long limit) {
-    for (long long it = 0; it < limit; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred P1;\n\tmbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, P1;\n\t}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity));
-        if (ok) return true;
-    }
-    return false;
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(idesc), "r"(acc));
-}
+using tcx::canon;
+using tcx::DRAIN_LIMIT;
+using tcx::LBO;
+using tcx::mbar_wait;
+using tcx::mma_tf32;
+using tcx::smem_u32;
+using tcx::tf32_hi;
+using tcx::umma_desc;
+static_assert(TC_KC == tcx::KC, "one canonical block width");
 
 }  // namespace
 
@@ -379,6 +344,8 @@ static std::atomic<long long> g_wait_limit{1LL << 26};
 static std::atomic<int> g_inject_stall{0};
 long long fb_tc_set_wait_limit(long long limit) { return g_wait_limit.exchange(limit); }
 int fb_tc_set_inject_stall(int on) { return g_inject_stall.exchange(on ? 1 : 0); }
+long long fb_tc_wait_limit() { return g_wait_limit.load(); }
+int fb_tc_inject_stall() { return g_inject_stall.load(); }
 
 size_t fb_tc_smem_bytes() { return (size_t)TC_STAGES * STAGE_FLOATS * sizeof(float) + 1024; }
 
@@ -529,6 +496,14 @@ fb_status fb_tc_check(const fb_op* op) {
     for (int l = 0; l <= FB_MAXLEV; ++l) {
         plans.push_back(op->tc_m2m[l]);
         plans.push_back(op->tc_l2l[l]);
+    }
+    if (op->stc_err) {   // tensor-core staged rotation passes
+        int h = 0;
+        FB_CUDA(cudaMemcpy(&h, op->stc_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (h) {
+            FB_CUDA(cudaMemset(op->stc_err, 0, sizeof(int)));
+            return fb_fail(FB_ERR_TIMEOUT, "tensor-core staged rotation kernel: a bounded wait ran out");
+        }
     }
     for (void* v : plans) {
         TcPlanImpl* pl = (TcPlanImpl*)v;

@@ -125,3 +125,81 @@ def test_autotuned_large_orders_match_dense():
             fb.fb_operator_destroy(op)
         fb.fb_tree_destroy(tree)
         fb.fb_mesh_destroy(mesh)
+
+
+STAGED_TC = [4 | 8 | 16 | 32] * 13   # bits 4/5: the staged rotations on the tensor cores
+
+
+@pytest.mark.parametrize("pmin", [12, 30])
+@pytest.mark.parametrize("kind", [fb.FB_OP_A, fb.FB_OP_LP])
+def test_staged_tensor_rotations_match_fp64(sub, pmin, kind):
+    """Rotation passes as 3xTF32 tcgen05 GEMMs (every degree from 0 on, both
+    folded parts, M2L, M2M and L2L): the mixed matvec matches the FP64 form
+    within the FP32 tolerance and the CUDA-core staged passes closely."""
+    wl, mesh, tree = sub
+    A64 = fb.fb_operator_create(mesh, tree, wl.k, kind, fb.FB_PREC_FP64_FMM, 6.0, pmin)
+    A32 = fb.fb_operator_create(mesh, tree, wl.k, kind, fb.FB_PREC_MIXED_FMM, 6.0, pmin)
+    try:
+        x = torch.tensor(seeded_vector(wl.n, 43), device="cuda")
+        y64 = apply(A64, x)
+        fb.fb_operator_set_forms(A32, STAGED)
+        y_s = apply(A32, x)
+        fb.fb_operator_set_forms(A32, STAGED_TC)
+        y_tc = apply(A32, x)
+        assert rel(y_tc, y64) < 1e-5
+        assert rel(y_tc, y_s) < 3e-6
+        fb.fb_operator_status(A32)   # no bounded wait ran out
+    finally:
+        fb.fb_operator_destroy(A64)
+        fb.fb_operator_destroy(A32)
+
+
+def test_staged_tensor_rotations_several_rhs(sub):
+    wl, mesh, tree = sub
+    A32 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 30)
+    try:
+        fb.fb_operator_set_forms(A32, STAGED_TC)
+        X = torch.tensor(np.stack([seeded_vector(wl.n, 80 + r) for r in range(3)]), device="cuda")
+        Y = apply(A32, X)
+        for r in range(3):
+            assert rel(apply(A32, X[r].contiguous()), Y[r]) < 1e-6
+    finally:
+        fb.fb_operator_destroy(A32)
+
+
+def test_staged_tensor_rotations_rejected_where_undefined(sub):
+    wl, mesh, tree = sub
+    A64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, 12)
+    A32 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 12)
+    try:
+        with pytest.raises(fb.FBError):
+            fb.fb_operator_set_forms(A64, STAGED_TC)      # FP64: no tensor-core form
+        with pytest.raises(fb.FBError):
+            fb.fb_operator_set_forms(A32, [16 | 32] * 13)  # bits 4/5 refine the staged bits
+    finally:
+        fb.fb_operator_destroy(A64)
+        fb.fb_operator_destroy(A32)
+
+
+def test_staged_tensor_rotations_large_orders_match_dense():
+    """Orders 116 / 66 (degree blocks up to 116 columns, several degrees per
+    tile below): mixed matvec with the tensor-core rotations against the
+    oracle's dense matrix, and the autotuner's report of the form."""
+    wl = workload("high_order")
+    mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+    fb.fb_mesh_set_admittance(mesh, wl.beta)
+    tree = fb.fb_tree_build(mesh, 64)
+    op = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 12)
+    try:
+        x = seeded_vector(wl.n, 73)
+        ref = oracle_dense("high_order")["A"] @ x
+        xd = torch.tensor(x, device="cuda")
+        fb.fb_operator_set_forms(op, STAGED_TC)
+        assert rel(apply(op, xd), ref) < 2e-5
+        tune = fb.fb_operator_autotune(op, 1)
+        assert tune[2]["m2l_staged_tc"] is not None and tune[2]["m2l_staged"] is not None
+        assert rel(apply(op, xd), ref) < 2e-5
+    finally:
+        fb.fb_operator_destroy(op)
+        fb.fb_tree_destroy(tree)
+        fb.fb_mesh_destroy(mesh)

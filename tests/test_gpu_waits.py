@@ -53,3 +53,41 @@ def test_wait_timeout_is_reported_and_context_stays_usable():
         fb.fb_operator_destroy(A)
         fb.fb_tree_destroy(tree)
         fb.fb_mesh_destroy(mesh)
+
+
+def test_staged_tensor_rotation_wait_timeout():
+    """The same for the staged RCR passes whose rotations run on the tensor
+    cores: a bounded wait of their pipeline runs out, the kernel drains its
+    bulk copies, frees its tensor memory and flags the operator; the next
+    matvec computes the same product."""
+    wl = workload("sub")
+    mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+    fb.fb_mesh_set_admittance(mesh, wl.beta)
+    tree = fb.fb_tree_build(mesh, 64)
+    A = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 30)
+    try:
+        fb.fb_operator_set_forms(A, [4 | 8 | 16 | 32] * 13)
+        x = torch.tensor(seeded_vector(wl.n, 83), device="cuda")
+        y0 = torch.empty_like(x)
+        fb.fb_operator_apply(A, x, y0)
+        fb.fb_operator_status(A)
+        prev = fb.fb_set_device_wait_limit(1 << 12)
+        try:
+            fb.fb_test_stall_device_waits(True)
+            y = torch.empty_like(x)
+            fb.fb_operator_apply(A, x, y)
+            with pytest.raises(fb.FBError) as e:
+                fb.fb_operator_status(A)
+            assert e.value.code == 6
+        finally:
+            fb.fb_test_stall_device_waits(False)
+            fb.fb_set_device_wait_limit(prev)
+        y1 = torch.empty_like(x)
+        fb.fb_operator_apply(A, x, y1)
+        fb.fb_operator_status(A)
+        torch.cuda.synchronize()
+        assert rel(y1.cpu().numpy(), y0.cpu().numpy()) < 1e-6
+    finally:
+        fb.fb_operator_destroy(A)
+        fb.fb_tree_destroy(tree)
+        fb.fb_mesh_destroy(mesh)
