@@ -237,37 +237,57 @@ def level_counts(fb, op, tree):
     return L, p, tc, pairs, nb
 
 
-def rcr_flops(p_out, p_in):
-    """Algorithmic flops of one RCR translation: rotations sum (2n+1)^2 for
-    n < p_in and n < p_out, coaxial sum over m of (p_out-|m|)(p_in-|m|),
-    complex MACs x 8 (about (10/3) p^3 x 8 for p_out = p_in)."""
-    rot = sum((2 * n + 1) ** 2 for n in range(p_in)) + sum((2 * n + 1) ** 2 for n in range(p_out))
+def rot_flops(p_out, p_in):
+    """Algorithmic flops of the two rotations of one RCR translation: sum
+    (2n+1)^2 over n < p_in (rotate) and n < p_out (rotate back), complex-by-
+    real MACs counted as complex MACs x 8 (the unfolded count; the folded
+    kernels execute about half)."""
+    return 8.0 * (sum((2 * n + 1) ** 2 for n in range(p_in)) + sum((2 * n + 1) ** 2 for n in range(p_out)))
+
+
+def coax_flops(p_out, p_in):
+    """Algorithmic flops of the coaxial step: sum over m of (p_out-|m|)(p_in-|m|) complex MACs x 8."""
     q = min(p_out, p_in)
-    coax = sum((p_out - abs(m)) * (p_in - abs(m)) for m in range(-q + 1, q))
-    return 8.0 * (rot + coax)
+    return 8.0 * sum((p_out - abs(m)) * (p_in - abs(m)) for m in range(-q + 1, q))
 
 
-FAMILY = {("f32", "stg"): "k_stg<float>", ("f32", "tiles"): "k_rcr<float>", ("f32", "tc"): "k_trans_tc",
-          ("f64", "stg"): "k_stg<double>", ("f64", "tiles"): "k_rcr<double>"}
+def rcr_flops(p_out, p_in):
+    """Algorithmic flops of one RCR translation (rotations + coaxial step),
+    about (10/3) p^3 x 8 for p_out = p_in."""
+    return rot_flops(p_out, p_in) + coax_flops(p_out, p_in)
+
+
+# double-FP32 multiply-accumulate: 12 FP32-pipe operations (df.cuh)
+DF_OPS_PER_MAC = 12
+
+FAMILY = {("f32", "tiles"): "k_rcr<float>", ("f32", "tc"): "k_trans_tc", ("f64", "tiles"): "k_rcr<double>"}
 FAMILY_WHAT = {
-    "k_stg<float>": "staged RCR M2L (k_stg_rot / k_stg_coax / k_stg_back, FP32): batched GEMMs per polar angle "
-                    "and per |t|",
+    "k_stg_tc": "staged RCR rotation passes on the tensor cores (k_stg_tc<0> rotate, k_stg_tc<1> rotate back; "
+                "tcgen05 3xTF32 GEMMs per polar-angle group and degree)",
+    "k_stg_coax<float>": "staged RCR coaxial pass (FP32 CUDA-core GEMMs per |t| and order)",
+    "k_stg_rot+back<float>": "staged RCR rotation passes on CUDA cores (FP32)",
+    "k_stg_prep<float>": "staged RCR pre-pass (folded phased inputs, FP32)",
+    "k_stg<double>": "staged RCR passes in FP64 (true residual)",
+    "k_stg<df>": "staged RCR passes in double-FP32 arithmetic (FP64 true residual; 48-bit significand)",
+    "k_stg_prep<df>": "staged RCR pre-pass of the double-FP32 levels",
+    "k_stg_prep<double>": "staged RCR pre-pass (FP64)",
     "k_rcr<float>": "per-pair RCR M2L tiles (FP32)",
     "k_trans_tc": "tensor-core M2L (tcgen05 3xTF32, composed matrices)",
-    "k_stg<double>": "staged RCR M2L (FP64, true residual)",
     "k_rcr<double>": "per-pair RCR M2L tiles (FP64, true residual)",
 }
 
 
 def m2l_levels(tune, p, pairs):
-    """Per level of an autotuned operator: (form, device ms of its M2L pass,
-    algorithmic flops) from the autotuner's timings of the installed form."""
+    """Per level of an autotuned operator whose M2L is not staged: (form,
+    device ms of its M2L pass, algorithmic flops) from the autotuner's
+    timings of the installed form."""
     out = {}
     for l, t in (tune or {}).items():
         l = int(l)
         ch = t["choice"]
-        form, ms = ("tc", t["m2l_tensor"]) if ch & 1 else (("stg", t["m2l_staged"]) if ch & 4 else
-                                                            ("tiles", t["m2l_rcr"]))
+        if ch & 4 and not ch & 1:
+            continue   # staged: timed pass by pass (fb_operator_staged_pass_times)
+        form, ms = ("tc", t["m2l_tensor"]) if ch & 1 else ("tiles", t["m2l_rcr"])
         if ms is None:
             continue
         out[l] = (form, ms, float(pairs[l]) * rcr_flops(int(p[l]), int(p[l])))
@@ -275,53 +295,83 @@ def m2l_levels(tune, p, pairs):
 
 
 def roofline(fb, P, iters, true_mv, pk, fp32_peak, fp64_peak):
-    """Rooflines of the M2L kernel families of a solve and the dominant one.
-    A family's launch is its part of one M2L pass of one operator (the levels
-    the autotuner gave it, timed there with CUDA events on the device); its
-    achieved rate is algorithmic flops (rcr_flops per box pair, summed over
-    those levels) over that time, weighted over the operators by how often a
-    solve applies each (mixed: outer iterations, inner low-accuracy operator:
-    outer x inner iterations, FP64: true residuals)."""
+    """Rooflines of the M2L kernels of a solve and the dominant one.  The
+    staged levels are timed pass by pass with CUDA events
+    (fb_operator_staged_pass_times: each pass launched alone); the per-pair
+    tiles and composed tensor-core levels by the autotuner's device timings.
+    A kernel's achieved rate is its algorithmic work (flops, or bytes for
+    the pre-pass) over its device time, both summed over the launches of one
+    solve: outer iterations for the mixed operator, outer x inner iterations
+    for the low-accuracy inner operator, true residuals for FP64."""
     tune = P["tune"]
     L, _, _, pairs, _ = level_counts(fb, P["A32"], P["tree"])
     tf32 = float(pk.get("bf16_tflops", 1990.0)) * (1.1 / 2.25)
-    peaks_ = {"f32": (fp32_peak, "FP32 FMA throughput measured by fb_measure_alu_peaks"),
-              "f64": (fp64_peak, "FP64 FMA throughput measured by fb_measure_alu_peaks")}
+    hbm = float(pk.get("hbm_gbs", 6790.7))
+    peaks_ = {
+        "tensor": (tf32 / 3.0, "TFLOP/s", "measured BF16 burst x 1.1/2.25 (TF32) / 3 split passes, of measured"),
+        "f32": (fp32_peak, "TFLOP/s", "FP32 FMA throughput measured by fb_measure_alu_peaks"),
+        "f64": (fp64_peak, "TFLOP/s", "FP64 FMA throughput measured by fb_measure_alu_peaks"),
+        "df": (fp32_peak / DF_OPS_PER_MAC, "TFLOP/s",
+               f"measured FP32 FMA throughput x 2 flops / {DF_OPS_PER_MAC} FP32 operations per double-FP32 MAC"),
+        "hbm": (hbm / 1e3, "TB/s", "measured HBM copy bandwidth (MEASURED_PEAKS.json), of measured"),
+    }
     fam = {}
+
+    def add(name, kind, key, l, count, ms, work):
+        if ms is None or ms <= 0:
+            return
+        f = fam.setdefault(name, {"ms": 0.0, "work": 0.0, "kind": kind, "per_op": {}})
+        f["ms"] += ms * count
+        f["work"] += work * count
+        po = f["per_op"].setdefault(key, {"levels": [], "launch_ms": 0.0, "work": 0.0, "per_step": count})
+        po["levels"].append(l)
+        po["launch_ms"] = round(po["launch_ms"] + ms, 4)
+        po["work"] += work
+
     for key, op, prec, count in (("mixed", "A32", "f32", iters), ("inner", "Alow", "f32", iters * INNER_ITERS),
                                  ("fp64", "A64", "f64", true_mv)):
         p = fb.fb_operator_info(P[op])[2]
+        for l, d in fb.fb_operator_staged_pass_times(P[op]).items():
+            pl, npair = int(p[l]), float(pairs[l])
+            rot, cox = npair * rot_flops(pl, pl), npair * coax_flops(pl, pl)
+            cw = 16 if prec == "f32" else 32   # bytes per complex coefficient read + written
+            if d["form"] == "df":
+                add("k_stg<df>", "df", key, l, count, d["rot"] + d["coax"] + d["back"], rot + cox)
+                add("k_stg_prep<df>", "hbm", key, l, count, d["prep"], npair * pl * pl * cw)
+                continue
+            if prec == "f64":
+                add("k_stg<double>", "f64", key, l, count, d["rot"] + d["coax"] + d["back"], rot + cox)
+                add("k_stg_prep<double>", "hbm", key, l, count, d["prep"], npair * pl * pl * cw)
+                continue
+            if d["form"] == "tensor_rot":
+                add("k_stg_tc", "tensor", key, l, count, d["rot"] + d["back"], rot)
+            else:
+                add("k_stg_rot+back<float>", "f32", key, l, count, d["rot"] + d["back"], rot)
+            add("k_stg_coax<float>", "f32", key, l, count, d["coax"], cox)
+            add("k_stg_prep<float>", "hbm", key, l, count, d["prep"], npair * pl * pl * cw)
         for l, (form, ms, alg) in m2l_levels(tune.get(key), p, pairs).items():
-            name = FAMILY[(prec, form)]
-            f = fam.setdefault(name, {"ms": 0.0, "alg": 0.0, "step_ms": 0.0, "per_op": {}, "prec": prec})
-            f["ms"] += ms * count
-            f["alg"] += alg * count
-            f["step_ms"] += ms * count
-            po = f["per_op"].setdefault(key, {"levels": [], "launch_ms": 0.0, "alg_flops": 0.0, "per_step": count})
-            po["levels"].append(l)
-            po["launch_ms"] = round(po["launch_ms"] + ms, 4)
-            po["alg_flops"] += alg
+            add(FAMILY[(prec, form)], "tensor" if form == "tc" else prec, key, l, count, ms, alg)
     out = {}
     for name, f in fam.items():
-        if name == "k_trans_tc":
-            peak, kind, bound = tf32 / 3.0, "measured BF16 burst x 1.1/2.25 (TF32) / 3 split passes, of measured", "tensor"
-        else:
-            (peak, kind), bound = peaks_[f["prec"]], "alu"
-        ach = f["alg"] / (f["ms"] / 1e3) / 1e12 if f["ms"] > 0 else 0.0
-        out[name] = {"what": FAMILY_WHAT[name], "bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3),
-                     "unit": "TFLOP/s", "frac": round(ach / peak, 4) if peak else None,
-                     "est_ms_per_step": round(f["step_ms"], 2), "per_operator": f["per_op"], "peak_kind": kind}
+        peak, unit, kind = peaks_[f["kind"]]
+        ach = f["work"] / (f["ms"] / 1e3) / 1e12   # TFLOP/s or TB/s
+        bound = {"tensor": "tensor", "hbm": "hbm"}.get(f["kind"], "alu")
+        out[name] = {"what": FAMILY_WHAT.get(name, name), "bound": bound, "achieved": round(ach, 3),
+                     "peak": round(peak, 3), "unit": unit, "frac": round(ach / peak, 4) if peak else None,
+                     "est_ms_per_step": round(f["ms"], 2), "per_operator": f["per_op"], "peak_kind": kind}
     if not out:
         return None, out
     dom = max(out, key=lambda k: out[k]["est_ms_per_step"])
     d = out[dom]
-    launches = [v for v in d["per_operator"].values()]
-    rf = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": "TFLOP/s",
+    work = ("algorithmic bytes (16 B per complex coefficient read and written, 32 B in FP64) per box pair"
+            if d["unit"] == "TB/s" else
+            "algorithmic flops per box pair: rotations 8 x 2 sum_{n<p}(2n+1)^2, coaxial 8 x sum_m (p-|m|)^2")
+    rf = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
           "frac": d["frac"], "traffic": traffic_for(dom), "peak_kind": d["peak_kind"], "what": d["what"],
           "est_ms_per_step": d["est_ms_per_step"],
-          "launch": {k: {"levels": v["levels"], "launch_ms": v["launch_ms"], "algorithmic_flops": v["alg_flops"]}
+          "launch": {k: {"levels": v["levels"], "launch_ms": v["launch_ms"], "work": v["work"]}
                      for k, v in d["per_operator"].items()},
-          "algorithmic_flops": "rcr_flops per box pair: 8 x (sum_{n<p}(2n+1)^2 x 2 + sum_m (p-|m|)^2)"}
+          "work": work}
     return rf, out
 
 
@@ -405,10 +455,11 @@ def run_matvecs(args):
     prec = {"mixed": fb.FB_PREC_MIXED_FMM, "fp64": fb.FB_PREC_FP64_FMM}[args.prec]
     d0, pmin = (INNER_D0, INNER_PMIN) if args.inner_operator else (D0, PMIN)
     op = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, prec, d0, pmin)
+    tune = None
     if args.forms:
         fb.fb_operator_set_forms(op, [int(v) for v in args.forms.split(",")])
     else:
-        fb.fb_operator_autotune(op, 1)
+        tune = fb.fb_operator_autotune(op, 1)
     stream = torch.cuda.current_stream()
     t, ph = matvec_rate(fb, torch, stream, op, wl.n, args.matvec_only)
     passes = fb.fb_operator_staged_pass_times(op)
@@ -416,7 +467,9 @@ def run_matvecs(args):
                       "orders": [int(v) for v in fb.fb_operator_info(op)[2][2:]], "matvec_ms": round(t * 1e3, 4),
                       "phase_ms": {k: round(v, 4) for k, v in ph.items()},
                       "staged_pass_ms": {l: {k: (round(v, 4) if isinstance(v, float) else v) for k, v in d.items()}
-                                         for l, d in passes.items()}}))
+                                         for l, d in passes.items()},
+                      "forms": args.forms or ",".join(str(tune[l]["choice"] if l in tune else 0) for l in range(13)),
+                      "autotune": tune}))
     fb.fb_operator_destroy(op)
     fb.fb_tree_destroy(tree)
     fb.fb_mesh_destroy(mesh)

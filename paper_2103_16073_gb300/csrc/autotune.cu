@@ -5,7 +5,8 @@
 //     (where a pair's working set fits a CTA's shared memory),
 //   * RCR as staged batched GEMM passes (pairs grouped by polar angle and by
 //     |t|; rcr_staged.cu), in mixed precision also with the rotation passes
-//     on the tensor cores (rcr_staged_tc.cu),
+//     on the tensor cores (rcr_staged_tc.cu), in FP64 also in double-FP32
+//     arithmetic,
 //   * mixed precision only: the stacked tensor-core GEMM of composed
 //     matrices (3xTF32),
 // for M2L and for the M2M / L2L passes into that level.  The tensor-core
@@ -60,6 +61,9 @@ void free_rcr(RcrPlan& p) { fb_rcr_free(p); }
 // level always keeps at least one candidate.
 bool rcr_tile_candidate(int p, size_t csz) { return fb_rcr_tile_fits(p, p, csz) && p < 60; }
 bool rcr_staged_candidate(int p, size_t csz) { return p >= 24 || !rcr_tile_candidate(p, csz); }
+// double-FP32 passes: their arithmetic runs several times faster than FP64,
+// which moves the crossover with the FP64 tiles to lower orders
+bool rcr_df_candidate(int p) { return p >= 16; }
 
 }  // namespace
 
@@ -87,13 +91,15 @@ fb_status time_rcr(fb_op* op, const RcrPlan& base, Pick pick, int staged, void* 
     return st;
 }
 
-// times[8 * l + {0..7}] = M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles,
+// times[10 * l + {0..9}] = M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles,
 // M2M+L2L tensor, M2L RCR staged, M2M+L2L RCR staged, M2L RCR staged with
-// tensor-core rotations, M2M+L2L RCR staged with tensor-core rotations (ms, -1
-// when not a candidate) for l = 0..L; choice[l] bit 0 = M2L on the tensor
-// cores, bit 1 = M2M/L2L into level l on the tensor cores, bit 2 = M2L by
-// staged RCR, bit 3 = M2M/L2L into level l by staged RCR, bit 4 = the staged
-// M2L's rotations on the tensor cores, bit 5 = the same for M2M/L2L.
+// tensor-core rotations, M2M+L2L RCR staged with tensor-core rotations, M2L
+// RCR staged in double-FP32, M2M+L2L RCR staged in double-FP32 (ms, -1 when
+// not a candidate) for l = 0..L; choice[l] bit 0 = M2L on the tensor cores,
+// bit 1 = M2M/L2L into level l on the tensor cores, bit 2 = M2L by staged
+// RCR, bit 3 = M2M/L2L into level l by staged RCR, bit 4 = the staged M2L's
+// rotations on the tensor cores, bit 5 = the same for M2M/L2L, bit 6 = the
+// staged M2L in double-FP32, bit 7 = the same for M2M/L2L.
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_out, int* choice) {
     const bool mixed = op->prec == FB_PREC_MIXED_FMM;
     double times_local[FB_TUNE_TIMES * (FB_MAXLEV + 1)];
@@ -133,10 +139,12 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 1, mp, loc, s, nrhs, cnt, reps, &tl[4]));
             if (mixed) FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 2, mp, loc, s, nrhs, cnt, reps, &tl[6]));
         }
+        if (!mixed && rcr_df_candidate(op->p[l]))
+            FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 3, mp, loc, s, nrhs, cnt, reps, &tl[8]));
         double best = -1.0;
         if (tl[0] >= 0) best = tl[0];
-        for (int form = 1; form <= 2; ++form) {
-            const double v = tl[form == 1 ? 4 : 6];
+        for (int form = 1; form <= 3; ++form) {
+            const double v = tl[2 + 2 * form];
             if (v >= 0 && (best < 0 || v < best)) {
                 best = v;
                 stg_m2l[l] = form;
@@ -176,12 +184,12 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                 }
             }
         }
-        if (stg_m2l[l] && !(ch & 1)) ch |= stg_m2l[l] == 2 ? 4 | 16 : 4;
+        if (stg_m2l[l] && !(ch & 1)) ch |= stg_m2l[l] == 2 ? 4 | 16 : (stg_m2l[l] == 3 ? 4 | 64 : 4);
         // ---- M2M + L2L between levels l-1 and l
         if (l >= 3) {
             const int pm = std::max(op->p[l], op->p[l - 1]);
             auto all = [](const RcrTask&) { return true; };
-            double rt = -1.0, rs = -1.0, rc = -1.0;
+            double rt = -1.0, rs = -1.0, rc = -1.0, rd = -1.0;
             if (rcr_tile_candidate(pm, csz)) {
                 double a = 0, b = 0;
                 FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 0, mp, mp, s, nrhs, cnt, reps, &a));
@@ -199,9 +207,16 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                     rc = std::max(a, 0.0) + std::max(b, 0.0);
                 }
             }
+            if (!mixed && rcr_df_candidate(pm)) {
+                double a = 0, b = 0;
+                FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 3, mp, mp, s, nrhs, cnt, reps, &a));
+                FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 3, loc, loc, s, nrhs, cnt, reps, &b));
+                rd = std::max(a, 0.0) + std::max(b, 0.0);
+            }
             tl[2] = rt;
             tl[5] = rs;
             tl[7] = rc;
+            tl[9] = rd;
             double best2 = rt;
             if (rt < 0 || (rs >= 0 && rs < rt)) {
                 best2 = rs;
@@ -210,6 +225,10 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             if (rc >= 0 && rc < best2) {
                 best2 = rc;
                 stg_pair[l] = 2;
+            }
+            if (rd >= 0 && (best2 < 0 || rd < best2)) {
+                best2 = rd;
+                stg_pair[l] = 3;
             }
             std::vector<int> need;
             std::vector<TcGroup> up, down;
@@ -241,7 +260,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                     fb_tc_free(op->tc_l2l[l]);
                 }
             }
-            if (stg_pair[l] && !(ch & 2)) ch |= stg_pair[l] == 2 ? 8 | 32 : 8;
+            if (stg_pair[l] && !(ch & 2)) ch |= stg_pair[l] == 2 ? 8 | 32 : (stg_pair[l] == 3 ? 8 | 128 : 8);
         }
         if (choice) choice[l] = ch;
     }
@@ -289,12 +308,15 @@ fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s) {
     const int L = op->L;
     int stg_m2l[FB_MAXLEV + 1] = {0}, stg_pair[FB_MAXLEV + 1] = {0};
     for (int l = 2; l <= L; ++l) {
-        if (op->prec != FB_PREC_MIXED_FMM && (choice[l] & (1 | 2 | 16 | 32)))
+        const int c = choice[l];
+        if (op->prec != FB_PREC_MIXED_FMM && (c & (1 | 2 | 16 | 32)))
             return fb_fail(FB_ERR_ARG, "tensor-core forms apply to mixed operators");
-        if (((choice[l] & 16) && !(choice[l] & 4)) || ((choice[l] & 32) && !(choice[l] & 8)))
-            return fb_fail(FB_ERR_ARG, "bits 4/5 (tensor-core rotations) refine the staged bits 2/3");
-        stg_m2l[l] = (choice[l] & 4) ? ((choice[l] & 16) ? 2 : 1) : 0;
-        stg_pair[l] = (choice[l] & 8) ? ((choice[l] & 32) ? 2 : 1) : 0;
+        if (op->prec != FB_PREC_FP64_FMM && (c & (64 | 128)))
+            return fb_fail(FB_ERR_ARG, "double-FP32 forms apply to FP64 operators");
+        if (((c & (16 | 64)) && !(c & 4)) || ((c & (32 | 128)) && !(c & 8)))
+            return fb_fail(FB_ERR_ARG, "bits 4-7 refine the staged bits 2/3");
+        stg_m2l[l] = (c & 4) ? ((c & 16) ? 2 : ((c & 64) ? 3 : 1)) : 0;
+        stg_pair[l] = (c & 8) ? ((c & 32) ? 2 : ((c & 128) ? 3 : 1)) : 0;
     }
     FB_CHECK(fb_rcr_restage(op, stg_m2l, stg_pair));
     if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;

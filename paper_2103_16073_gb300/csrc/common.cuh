@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/fmmbem.h"
+#include "df.cuh"
 
 // ------------------------------------------------------------- complex ----
 template <class R>
@@ -260,6 +261,11 @@ bool fb_stg_staged(const RcrTask& tk);
 fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, int64_t per_dir, void** out,
                        int64_t* elems);
 void fb_stg_free(void*& plan);
+// tables of the staged levels that run in double-FP32 arithmetic (FP64 operators)
+struct DfTabs {
+    const df* rf;        // folded rotation tables
+    const cx<df>* coax;  // coaxial sets
+};
 // tables of the tensor-core rotation passes of the staged levels that use them
 struct StcTabs {
     const float* tab;
@@ -275,11 +281,14 @@ fb_status fb_stg_run_f(void* plan, const float* rf, int64_t fper, const cf* rph,
 bool fb_stg_uses_tc(const void* plan);
 fb_status fb_stg_run_d(void* plan, const double* rf, int64_t fper, const cd* rph, int prot, const cd* coax,
                        const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride,
-                       int only_level = -1, int pass_mask = 15);
+                       const DfTabs& dft, int only_level = -1, int pass_mask = 15);
+bool fb_stg_uses_df(const void* plan);
 int fb_stg_level_count(const void* plan);
-fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* tc);
-void fb_stg_level_info(const void* plan, int li, int64_t* src_base, int64_t* dst_base, int* tc);
+// form: 1 CUDA cores, 2 rotations on the tensor cores, 3 double-FP32 arithmetic
+void fb_stg_level_info(const void* plan, int li, int64_t* src_base, int64_t* dst_base, int* form);
 struct fb_op;
+fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* form);
+fb_status fb_stg_df_tables(fb_op* op, cudaStream_t s);
 fb_status fb_stg_tables(fb_op* op, const double* rotd64, cudaStream_t s);
 
 // A group of box pairs sharing one composed translation matrix (job) on the
@@ -356,6 +365,8 @@ struct fb_op {
     int64_t stc_per = 0;                     // floats per group and table
     int stc_P = 0;
     int* stc_err = nullptr;                  // error flag of the tensor-core staged passes
+    df* rotf_df = nullptr;                   // FP64 operators: folded tables and coaxial sets in
+    cx<df>* coax_df = nullptr;               // double-FP32 for the staged levels that use it
     std::vector<int> dir_of_code;            // M2L offset code -> direction (-1: near)
     // RCR form per level: 1 = staged passes, 0 = per-pair tiles (M2L of
     // level l; M2M and L2L between levels l-1 and l)

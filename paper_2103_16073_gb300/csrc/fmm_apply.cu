@@ -581,6 +581,7 @@ struct RotArgs {
     const void* rf;   // folded rotation tables and their per-group stride
     int64_t fper;
     StcTabs tc;       // tables of the tensor-core staged passes (single precision)
+    DfTabs dft;       // tables of the double-FP32 staged passes (FP64 operators)
 };
 template <class R>
 static RotArgs<R> rot_args(const fb_op* op) {
@@ -594,6 +595,7 @@ static RotArgs<R> rot_args(const fb_op* op) {
     a.rf = op->rotf;
     a.fper = op->rotf_per;
     a.tc = StcTabs{op->stc_tab, op->stc_off, op->stc_per, op->stc_err};
+    a.dft = DfTabs{op->rotf_df, op->coax_df};
     return a;
 }
 static fb_status stg_run(void* plan, const RotArgs<float>& r, const cf* coax, const cf* src, cf* dst,
@@ -603,14 +605,15 @@ static fb_status stg_run(void* plan, const RotArgs<float>& r, const cf* coax, co
 }
 static fb_status stg_run(void* plan, const RotArgs<double>& r, const cd* coax, const cd* src, cd* dst,
                          cudaStream_t s, int nrhs, int64_t rstride) {
-    return fb_stg_run_d(plan, (const double*)r.rf, r.fper, r.ph, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride);
+    return fb_stg_run_d(plan, (const double*)r.rf, r.fper, r.ph, r.prot, coax, src, dst, r.U, r.V, s, nrhs, rstride,
+                        r.dft);
 }
 
 // Device time (ms, median of 3 after one untimed run, one right-hand side)
 // of each pass of every staged M2L level of an operator, on its expansion
 // buffers: ms[4 l + {0..3}] = pre-pass, rotation, coaxial, back-rotation of
-// level l (-1: not staged); tc[l] = 1 where the rotations run on the tensor
-// cores.
+// level l (-1: not staged); form[l] = 1 CUDA cores, 2 rotations on the
+// tensor cores, 3 double-FP32 arithmetic (0: not staged).
 fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* tc) {
     for (int i = 0; i < 4 * (FB_MAXLEV + 1); ++i) ms[i] = -1.0;
     for (int l = 0; l <= FB_MAXLEV; ++l) tc[l] = 0;
@@ -637,7 +640,7 @@ fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* tc) {
                                             (cf*)op->stg_v, s, 1, 0, rot_args<float>(op).tc, li, 1 << pass)
                              : fb_stg_run_d(pl.stg, (const double*)op->rotf, op->rotf_per, (const cd*)op->rph64,
                                             op->Prot, op->coax64, (const cd*)op->mp, (cd*)op->loc, (cd*)op->stg_u,
-                                            (cd*)op->stg_v, s, 1, 0, li, 1 << pass);
+                                            (cd*)op->stg_v, s, 1, 0, rot_args<double>(op).dft, li, 1 << pass);
             };
             std::vector<float> v;
             st = run();
@@ -697,11 +700,15 @@ fb_status fb_rcr_upload(fb_op* op, RcrPlan& pl, const int32_t* src, const int32_
         FB_CHECK(dalloc(&pl.tiles, pl.h_tiles.size()));
         FB_CUDA(cudaMemcpy(pl.tiles, pl.h_tiles.data(), sizeof(RcrTile) * pl.h_tiles.size(), cudaMemcpyHostToDevice));
     }
-    for (const RcrTask& tk : pl.h_tasks)
+    for (const RcrTask& tk : pl.h_tasks) {
         if (tk.staged == 2 && op->prec != FB_PREC_MIXED_FMM)
             return fb_fail(FB_ERR_ARG, "tensor-core staged RCR applies to mixed operators");
+        if (tk.staged == 3 && op->prec != FB_PREC_FP64_FMM)
+            return fb_fail(FB_ERR_ARG, "double-FP32 staged RCR applies to FP64 operators");
+    }
     FB_CHECK(fb_stg_build(pl, op->theta_slot, op->per_dir, &pl.stg, &pl.stg_elems));
     if (fb_stg_uses_tc(pl.stg)) FB_CHECK(fb_stc_tables(op, cudaStreamLegacy));
+    if (fb_stg_uses_df(pl.stg)) FB_CHECK(fb_stg_df_tables(op, cudaStreamLegacy));
     if (pl.stg_elems > op->stg_elems) {
         FB_CUDA(cudaDeviceSynchronize());
         dfree(op->stg_u);
@@ -953,6 +960,8 @@ void fb_fmm_destroy(fb_op* op) {
     dfree(op->stc_tab);
     dfree(op->stc_off);
     dfree(op->stc_err);
+    dfree(op->rotf_df);
+    dfree(op->coax_df);
 }
 
 // ---------------------------------------------------------------------------

@@ -36,6 +36,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "df.cuh"
 #include "rcr_staged.cuh"
 
 using namespace stg;
@@ -113,6 +114,31 @@ __device__ __forceinline__ void ld4(cf (&o)[4], const cf* p) {
     const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 2);
     o[0] = mk(a.x, a.y); o[1] = mk(a.z, a.w); o[2] = mk(b.x, b.y); o[3] = mk(b.z, b.w);
 }
+__device__ __forceinline__ void ld4(df (&o)[4], const df* p) {
+    const float4 a = *reinterpret_cast<const float4*>(p), b = *reinterpret_cast<const float4*>(p + 2);
+    o[0] = df(a.x, a.y); o[1] = df(a.z, a.w); o[2] = df(b.x, b.y); o[3] = df(b.z, b.w);
+}
+__device__ __forceinline__ void ld4(cx<df> (&o)[4], const cx<df>* p) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float4 a = *reinterpret_cast<const float4*>(p + i);
+        o[i] = mk(df(a.x, a.y), df(a.z, a.w));
+    }
+}
+// conversions between the storage precision of the expansions (O) and the
+// arithmetic of the staged passes (R): equal types, or FP64 <-> double-FP32
+template <class R>
+__host__ __device__ __forceinline__ R real_from(double v) { return (R)v; }
+template <>
+__host__ __device__ __forceinline__ df real_from<df>(double v) { return df_from(v); }
+template <class R, class O>
+__device__ __forceinline__ cx<R> cx_to(const cx<O>& a) { return mk<R>(real_from<R>(a.re), real_from<R>(a.im)); }
+template <>
+__device__ __forceinline__ cx<float> cx_to<float, float>(const cf& a) { return a; }
+template <class O, class R>
+__device__ __forceinline__ cx<O> cx_out(const cx<R>& a) { return a; }
+template <>
+__device__ __forceinline__ cd cx_out<double, df>(const cx<df>& a) { return mk(df_to(a.re), df_to(a.im)); }
 __device__ __forceinline__ void ld4(cd (&o)[4], const cd* p) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -222,8 +248,8 @@ __global__ void k_fold_tables(const double* __restrict__ rotd, int64_t per_dir, 
             rv = Dc[(int64_t)a * w + b] - Dc[(int64_t)a * w - b];
             bv = Dc[(int64_t)b * w + a] - Dc[-(int64_t)b * w + a];
         }
-        Rt[e] = (R)rv;
-        Bt[e] = (R)bv;
+        Rt[e] = real_from<R>(rv);
+        Bt[e] = real_from<R>(bv);
     }
 }
 
@@ -231,9 +257,9 @@ __global__ void k_fold_tables(const double* __restrict__ rotd, int64_t per_dir, 
 // X0[slot][n^2 + j]: the folded phased input of each pair (x_m =
 // e^{i m phi_slot} src[slot][n^2 + n + m]; j <= n: s_j, j > n: t_{j-n}),
 // written once so that the rotation GEMMs read contiguous columns.
-template <class R>
-__global__ void k_stg_prep(const StgSlot* __restrict__ slots, int nslot, const cx<R>* __restrict__ src,
-                           const cx<R>* __restrict__ rph, int prot, int Pin, int S, cx<R>* __restrict__ X0) {
+template <class R, class O>
+__global__ void k_stg_prep(const StgSlot* __restrict__ slots, int nslot, const cx<O>* __restrict__ src,
+                           const cx<O>* __restrict__ rph, int prot, int Pin, int S, cx<R>* __restrict__ X0) {
     const int64_t total = (int64_t)nslot * Pin;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
         const int sl = (int)(q / Pin), e = (int)(q % Pin);
@@ -242,17 +268,17 @@ __global__ void k_stg_prep(const StgSlot* __restrict__ slots, int nslot, const c
         while (n * n > e) --n;
         while ((n + 1) * (n + 1) <= e) ++n;
         const int j = e - n * n;
-        const cx<R>* x = src + s.src_off + (int64_t)n * n + n;   // (n, 0)
-        const cx<R>* ph = rph + (int64_t)s.dir * (2 * prot - 1) + (prot - 1);
-        cx<R> v;
+        const cx<O>* x = src + s.src_off + (int64_t)n * n + n;   // (n, 0)
+        const cx<O>* ph = rph + (int64_t)s.dir * (2 * prot - 1) + (prot - 1);
+        cx<O> v;
         if (j == 0) {
             v = x[0];
         } else {
             const int m = j <= n ? j : j - n;
-            const cx<R> xp = x[m] * ph[m], xm = x[-m] * ph[-m];
+            const cx<O> xp = x[m] * ph[m], xm = x[-m] * ph[-m];
             v = j <= n ? xp + xm : xp - xm;
         }
-        X0[(int64_t)sl * S + e] = v;
+        X0[(int64_t)sl * S + e] = cx_to<R, O>(v);
     }
 }
 
@@ -369,12 +395,12 @@ __device__ __forceinline__ void atomic_add_cx<double>(cd* d, const cd& v) {
     atomicAdd(&d->im, v.im);
 }
 
-template <class R>
+template <class R, class O>
 __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restrict__ tiles,
                                                           const StgSlot* __restrict__ slots,
                                                           const R* __restrict__ rf, int64_t fper,
-                                                          const cx<R>* __restrict__ rph, int prot,
-                                                          const cx<R>* __restrict__ V, cx<R>* __restrict__ dst, int S,
+                                                          const cx<O>* __restrict__ rph, int prot,
+                                                          const cx<R>* __restrict__ V, cx<O>* __restrict__ dst, int S,
                                                           int pin, int pout) {
     extern __shared__ __align__(16) unsigned char stg_smem[];
     StgSmem<R, false>& sm = *reinterpret_cast<StgSmem<R, false>*>(stg_smem);
@@ -410,24 +436,24 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restr
     cx<R> acc[4][4];
     stg_mainloop<R, false>(sm, K, aptr, xptr, (const void*)rf, acc);
     const int ty = tid >> 4, tx = tid & 15;
-    const R sgn = part ? R(-1) : R(1);
+    const O sgn = part ? O(-1) : O(1);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         const int c = tx + 16 * j;
         if (c >= tl.ncol) continue;
-        const cx<R>* ph = rph + (int64_t)sm.col_aux[c] * (2 * prot - 1) + (prot - 1);
-        cx<R>* d = dst + sm.col_off[c];   // entry (n, 0) of the target
+        const cx<O>* ph = rph + (int64_t)sm.col_aux[c] * (2 * prot - 1) + (prot - 1);
+        cx<O>* d = dst + sm.col_off[c];   // entry (n, 0) of the target
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = ty * 4 + i;
             if (r >= M) continue;
             const int mp = lo + tl.row0 + r;
-            const cx<R> h = R(0.5) * acc[i][j];
+            const cx<O> h = O(0.5) * cx_out<O, R>(acc[i][j]);
             if (mp == 0) {
-                atomic_add_cx<R>(d, h);
+                atomic_add_cx<O>(d, h);
             } else {
-                atomic_add_cx<R>(d + mp, h * conjg(ph[mp]));
-                atomic_add_cx<R>(d - mp, sgn * (h * ph[mp]));
+                atomic_add_cx<O>(d + mp, h * conjg(ph[mp]));
+                atomic_add_cx<O>(d - mp, sgn * (h * ph[mp]));
             }
         }
     }
@@ -445,6 +471,7 @@ struct StgLevel {
     int nrt = 0, nct = 0, nbt = 0;
     // rotation passes on the tensor cores (rcr_staged_tc.cu) instead of rt / bt
     int tc = 0;
+    int df = 0;   // passes in double-FP32 arithmetic (FP64 expansions)
     StcTile* rtc = nullptr;
     StcTile* btc = nullptr;
     int nrtc = 0, nbtc = 0;
@@ -515,7 +542,10 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
         lv.dst_base = std::get<1>(kv.first);
         lv.p_in = p_in;
         lv.p_out = p_out;
-        for (int t : ts) lv.tc = lv.tc || pl.h_tasks[t].staged == 2;
+        for (int t : ts) {
+            lv.tc = lv.tc || pl.h_tasks[t].staged == 2;
+            lv.df = lv.df || pl.h_tasks[t].staged == 3;
+        }
         lv.S = std::max(p_in * p_in, p_out * p_out);
         // polar-angle groups of the tasks, in order of first appearance
         std::map<int, std::vector<int>> groups;   // representative direction -> tasks
@@ -675,6 +705,34 @@ fb_status fb_stg_tables(fb_op* op, const double* rotd64, cudaStream_t s) {
     return FB_OK;
 }
 
+static __global__ void k_cd_to_df(const cd* __restrict__ in, int64_t n, cx<df>* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = mk(df_from(in[i].re), df_from(in[i].im));
+}
+
+// Folded rotation tables and coaxial sets of an FP64 operator in
+// double-FP32, for its staged levels in that arithmetic (built once).
+fb_status fb_stg_df_tables(fb_op* op, cudaStream_t s) {
+    if (op->rotf_df && op->coax_df) return FB_OK;
+    if (op->prec != FB_PREC_FP64_FMM) return fb_fail(FB_ERR_ARG, "double-FP32 staged RCR applies to FP64 operators");
+    const int ng = (int)op->theta_dirs.size();
+    if (ng == 0 || op->Prot < 1 || !op->coax64) return fb_fail(FB_ERR_STATE, "staged RCR: no rotation groups");
+    const int P = op->Prot;
+    int* d_dirs = nullptr;
+    FB_CHECK(dalloc(&d_dirs, (size_t)ng));
+    FB_CHECK(dalloc(&op->rotf_df, (size_t)ng * 2 * op->rotf_per));
+    FB_CHECK(dalloc(&op->coax_df, (size_t)op->coax_count));
+    FB_CUDA(cudaMemcpyAsync(d_dirs, op->theta_dirs.data(), sizeof(int) * ng, cudaMemcpyHostToDevice, s));
+    k_fold_tables<df><<<dim3(P, ng), 256, 0, s>>>(op->rotd64, op->per_dir, d_dirs, P, op->rotf_df, op->rotf_per);
+    k_cd_to_df<<<(unsigned)std::min<int64_t>((op->coax_count + 255) / 256, 4096), 256, 0, s>>>(
+        op->coax64, op->coax_count, op->coax_df);
+    cudaError_t e = cudaStreamSynchronize(s);
+    dfree(d_dirs);
+    if (e != cudaSuccess) return fb_fail(FB_ERR_CUDA, std::string("double-FP32 tables: ") + cudaGetErrorString(e));
+    fb_count_launch(2);
+    return FB_OK;
+}
+
 // Runs the staged passes of a plan for nrhs right-hand sides (set r of the
 // expansions at src / dst + r * rstride), one right-hand side and one level
 // at a time: pre-pass (src -> V), rotation (V -> U), coaxial (U -> V),
@@ -689,55 +747,78 @@ static fb_status stc_pass(const StgLevel& lv, int pass, const StcTabs* tc, const
                      : fb_stc_run(1, lv.btc, lv.nbtc, np, tc->off, tc->tab, tc->per, lv.slots, X, out, lv.S, lv.p_in,
                                   lv.p_out, rph, prot, tc->err, s);
 }
-static fb_status stc_pass(const StgLevel&, int, const StcTabs*, const cd*, cd*, const cd*, int, cudaStream_t) {
+template <class X, class Y, class Ph>
+static fb_status stc_pass(const StgLevel&, int, const StcTabs*, const X*, Y*, const Ph*, int, cudaStream_t) {
     return fb_fail(FB_ERR_ARG, "tensor-core staged RCR applies to single precision");
+}
+
+
+// The four passes of one level and right-hand side: arithmetic in R
+// (tables rf / coax, staging buffers U, V), expansions and phases stored in
+// O (R = O, or R = double-FP32 for FP64 expansions).
+template <class R, class O>
+static fb_status stg_level(const StgLevel& lv, int pass_mask, const R* rf, int64_t fper, const cx<O>* rph, int prot,
+                           const cx<R>* coax, const cx<O>* sr, cx<O>* dr, cx<R>* U, cx<R>* V, cudaStream_t s,
+                           const StcTabs* tc) {
+    const size_t sm_rc = sizeof(StgSmem<R, false>), sm_c = sizeof(StgSmem<R, true>);
+    FB_CHECK(fb_smem_cap((const void*)k_stg_rot<R>, sm_rc));
+    FB_CHECK(fb_smem_cap((const void*)k_stg_coax<R>, sm_c));
+    FB_CHECK(fb_smem_cap((const void*)k_stg_back<R, O>, sm_rc));
+    if (pass_mask & 1) {
+        const int64_t tot = (int64_t)lv.nslot * lv.p_in * lv.p_in;
+        const int pb = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+        k_stg_prep<R, O><<<pb, 256, 0, s>>>(lv.slots, lv.nslot, sr, rph, prot, lv.p_in * lv.p_in, lv.S, V);
+        fb_count_launch();
+    }
+    if (pass_mask & 2) {
+        if (lv.tc) {
+            FB_CHECK(stc_pass(lv, 0, tc, V, U, rph, prot, s));
+        } else if (lv.nrt) {
+            k_stg_rot<R><<<lv.nrt, STHREADS, sm_rc, s>>>(lv.rt, rf, fper, V, U, lv.S);
+            fb_count_launch();
+        }
+    }
+    if ((pass_mask & 4) && lv.nct) {
+        k_stg_coax<R><<<lv.nct, STHREADS, sm_c, s>>>(lv.ct, lv.cidx, coax, U, V, lv.S, lv.p_out);
+        fb_count_launch();
+    }
+    if (pass_mask & 8) {
+        if (lv.tc) {
+            FB_CHECK(stc_pass(lv, 1, tc, V, dr, rph, prot, s));
+        } else if (lv.nbt) {
+            k_stg_back<R, O><<<lv.nbt, STHREADS, sm_rc, s>>>(lv.bt, lv.slots, rf, fper, rph, prot, V, dr, lv.S,
+                                                             lv.p_in, lv.p_out);
+            fb_count_launch();
+        }
+    }
+    FB_LAUNCH_CHECK();
+    return FB_OK;
 }
 
 template <class R>
 static fb_status stg_run(void* plan, const R* rf, int64_t fper, const cx<R>* rph, int prot, const cx<R>* coax,
                          const cx<R>* src, cx<R>* dst, cx<R>* U, cx<R>* V, cudaStream_t s, int nrhs, int64_t rstride,
-                         const StcTabs* tc, int only_level, int pass_mask) {
+                         const StcTabs* tc, const DfTabs* dft, int only_level, int pass_mask) {
     StgPlanImpl* P = (StgPlanImpl*)plan;
     if (!P) return FB_OK;
     if (!U || !V || !rf) return fb_fail(FB_ERR_STATE, "staged RCR: staging buffers or tables missing");
-    const size_t sm_rc = sizeof(StgSmem<R, false>), sm_c = sizeof(StgSmem<R, true>);
-    FB_CHECK(fb_smem_cap((const void*)k_stg_rot<R>, sm_rc));
-    FB_CHECK(fb_smem_cap((const void*)k_stg_coax<R>, sm_c));
-    FB_CHECK(fb_smem_cap((const void*)k_stg_back<R>, sm_rc));
     for (int r = 0; r < nrhs; ++r) {
         const cx<R>* sr = src + r * rstride;
         cx<R>* dr = dst + r * rstride;
         for (int li = 0; li < (int)P->levels.size(); ++li) {
             if (only_level >= 0 && li != only_level) continue;
             const StgLevel& lv = P->levels[li];
-            if (pass_mask & 1) {
-                const int64_t tot = (int64_t)lv.nslot * lv.p_in * lv.p_in;
-                const int pb = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
-                k_stg_prep<R><<<pb, 256, 0, s>>>(lv.slots, lv.nslot, sr, rph, prot, lv.p_in * lv.p_in, lv.S, V);
-                fb_count_launch();
-            }
-            if (pass_mask & 2) {
-                if (lv.tc) {
-                    FB_CHECK(stc_pass(lv, 0, tc, V, U, rph, prot, s));
-                } else if (lv.nrt) {
-                    k_stg_rot<R><<<lv.nrt, STHREADS, sm_rc, s>>>(lv.rt, rf, fper, V, U, lv.S);
-                    fb_count_launch();
+            if constexpr (sizeof(R) == 8) {
+                if (lv.df) {
+                    if (!dft || !dft->rf || !dft->coax)
+                        return fb_fail(FB_ERR_STATE, "staged RCR: double-FP32 tables missing");
+                    // the staging buffers hold complex double-FP32 values (16 bytes, as FP64)
+                    FB_CHECK((stg_level<df, double>(lv, pass_mask, dft->rf, fper, rph, prot, dft->coax, sr, dr,
+                                                    (cx<df>*)U, (cx<df>*)V, s, nullptr)));
+                    continue;
                 }
             }
-            if ((pass_mask & 4) && lv.nct) {
-                k_stg_coax<R><<<lv.nct, STHREADS, sm_c, s>>>(lv.ct, lv.cidx, coax, U, V, lv.S, lv.p_out);
-                fb_count_launch();
-            }
-            if (pass_mask & 8) {
-                if (lv.tc) {
-                    FB_CHECK(stc_pass(lv, 1, tc, V, dr, rph, prot, s));
-                } else if (lv.nbt) {
-                    k_stg_back<R><<<lv.nbt, STHREADS, sm_rc, s>>>(lv.bt, lv.slots, rf, fper, rph, prot, V, dr, lv.S,
-                                                                  lv.p_in, lv.p_out);
-                    fb_count_launch();
-                }
-            }
-            FB_LAUNCH_CHECK();
+            FB_CHECK((stg_level<R, R>(lv, pass_mask, rf, fper, rph, prot, coax, sr, dr, U, V, s, tc)));
         }
     }
     return FB_OK;
@@ -746,25 +827,33 @@ static fb_status stg_run(void* plan, const R* rf, int64_t fper, const cx<R>* rph
 fb_status fb_stg_run_f(void* plan, const float* rf, int64_t fper, const cf* rph, int prot, const cf* coax,
                        const cf* src, cf* dst, cf* U, cf* V, cudaStream_t s, int nrhs, int64_t rstride,
                        const StcTabs& tc, int only_level, int pass_mask) {
-    return stg_run<float>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride, &tc, only_level,
-                          pass_mask);
+    return stg_run<float>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride, &tc, nullptr,
+                          only_level, pass_mask);
 }
 fb_status fb_stg_run_d(void* plan, const double* rf, int64_t fper, const cd* rph, int prot, const cd* coax,
                        const cd* src, cd* dst, cd* U, cd* V, cudaStream_t s, int nrhs, int64_t rstride,
-                       int only_level, int pass_mask) {
-    return stg_run<double>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride, nullptr, only_level,
-                           pass_mask);
+                       const DfTabs& dft, int only_level, int pass_mask) {
+    return stg_run<double>(plan, rf, fper, rph, prot, coax, src, dst, U, V, s, nrhs, rstride, nullptr, &dft,
+                           only_level, pass_mask);
 }
 
 int fb_stg_level_count(const void* plan) {
     const StgPlanImpl* P = (const StgPlanImpl*)plan;
     return P ? (int)P->levels.size() : 0;
 }
-void fb_stg_level_info(const void* plan, int li, int64_t* src_base, int64_t* dst_base, int* tc) {
+void fb_stg_level_info(const void* plan, int li, int64_t* src_base, int64_t* dst_base, int* form) {
     const StgLevel& lv = ((const StgPlanImpl*)plan)->levels[li];
     *src_base = lv.src_base;
     *dst_base = lv.dst_base;
-    *tc = lv.tc;
+    *form = lv.tc ? 2 : (lv.df ? 3 : 1);
+}
+
+bool fb_stg_uses_df(const void* plan) {
+    const StgPlanImpl* P = (const StgPlanImpl*)plan;
+    if (!P) return false;
+    for (const StgLevel& lv : P->levels)
+        if (lv.df) return true;
+    return false;
 }
 
 bool fb_stg_uses_tc(const void* plan) {

@@ -203,3 +203,69 @@ def test_staged_tensor_rotations_large_orders_match_dense():
         fb.fb_operator_destroy(op)
         fb.fb_tree_destroy(tree)
         fb.fb_mesh_destroy(mesh)
+
+
+STAGED_DF = [4 | 8 | 64 | 128] * 13   # bits 6/7: the staged passes in double-FP32 (FP64 operators)
+
+
+@pytest.mark.parametrize("pmin", [12, 30])
+@pytest.mark.parametrize("kind", [fb.FB_OP_A, fb.FB_OP_LP])
+def test_staged_double_float_matches_fp64_tiles(sub, pmin, kind):
+    """Staged passes in double-FP32 arithmetic (48-bit significand) on an
+    FP64 operator: M2L, M2M and L2L against the FP64 per-pair tiles, far
+    inside the FMM's own truncation error."""
+    wl, mesh, tree = sub
+    op = fb.fb_operator_create(mesh, tree, wl.k, kind, fb.FB_PREC_FP64_FMM, 6.0, pmin)
+    try:
+        x = torch.tensor(seeded_vector(wl.n, 45), device="cuda")
+        fb.fb_operator_set_forms(op, TILES)
+        y_t = apply(op, x)
+        fb.fb_operator_set_forms(op, STAGED_DF)
+        y_d = apply(op, x)
+        assert rel(y_d, y_t) < 1e-11
+        X = torch.tensor(np.stack([seeded_vector(wl.n, 90 + r) for r in range(3)]), device="cuda")
+        Y = apply(op, X)
+        for r in range(3):
+            assert rel(apply(op, X[r].contiguous()), Y[r]) < 1e-13
+    finally:
+        fb.fb_operator_destroy(op)
+
+
+def test_staged_double_float_rejected_where_undefined(sub):
+    wl, mesh, tree = sub
+    A32 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 12)
+    A64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, 12)
+    try:
+        with pytest.raises(fb.FBError):
+            fb.fb_operator_set_forms(A32, STAGED_DF)        # double-FP32 forms are for FP64 operators
+        with pytest.raises(fb.FBError):
+            fb.fb_operator_set_forms(A64, [64 | 128] * 13)  # bits 6/7 refine the staged bits
+    finally:
+        fb.fb_operator_destroy(A32)
+        fb.fb_operator_destroy(A64)
+
+
+def test_staged_double_float_large_orders():
+    """Orders 116 / 66: double-FP32 staged passes against the FP64 staged
+    passes and the oracle's dense matrix."""
+    wl = workload("high_order")
+    mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+    fb.fb_mesh_set_admittance(mesh, wl.beta)
+    tree = fb.fb_tree_build(mesh, 64)
+    op = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, 12)
+    try:
+        x = seeded_vector(wl.n, 75)
+        ref = oracle_dense("high_order")["A"] @ x
+        xd = torch.tensor(x, device="cuda")
+        fb.fb_operator_set_forms(op, STAGED)
+        y_s = apply(op, xd)
+        fb.fb_operator_set_forms(op, STAGED_DF)
+        y_d = apply(op, xd)
+        assert rel(y_d, y_s) < 1e-11
+        assert rel(y_d, ref) < 1e-5
+        passes = fb.fb_operator_staged_pass_times(op)
+        assert passes[2]["form"] == "df" and all(passes[2][k] > 0 for k in ("prep", "rot", "coax", "back"))
+    finally:
+        fb.fb_operator_destroy(op)
+        fb.fb_tree_destroy(tree)
+        fb.fb_mesh_destroy(mesh)
