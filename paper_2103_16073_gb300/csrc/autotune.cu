@@ -6,7 +6,7 @@
 //   * RCR as staged batched GEMM passes (pairs grouped by polar angle and by
 //     |t|; rcr_staged.cu), in mixed precision also with the rotation passes
 //     on the tensor cores (rcr_staged_tc.cu), in FP64 also in double-FP32
-//     arithmetic,
+//     arithmetic (as are the FP64 per-pair tiles),
 //   * mixed precision only: the stacked tensor-core GEMM of composed
 //     matrices (3xTF32),
 // for M2L and for the M2M / L2L passes into that level.  The tensor-core
@@ -91,15 +91,17 @@ fb_status time_rcr(fb_op* op, const RcrPlan& base, Pick pick, int staged, void* 
     return st;
 }
 
-// times[10 * l + {0..9}] = M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles,
+// times[12 * l + {0..11}] = M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles,
 // M2M+L2L tensor, M2L RCR staged, M2M+L2L RCR staged, M2L RCR staged with
 // tensor-core rotations, M2M+L2L RCR staged with tensor-core rotations, M2L
-// RCR staged in double-FP32, M2M+L2L RCR staged in double-FP32 (ms, -1 when
-// not a candidate) for l = 0..L; choice[l] bit 0 = M2L on the tensor cores,
-// bit 1 = M2M/L2L into level l on the tensor cores, bit 2 = M2L by staged
-// RCR, bit 3 = M2M/L2L into level l by staged RCR, bit 4 = the staged M2L's
+// RCR staged in double-FP32, M2M+L2L RCR staged in double-FP32, M2L RCR
+// tiles in double-FP32, M2M+L2L RCR tiles in double-FP32 (ms, -1 when not a
+// candidate) for l = 0..L; choice[l] bit 0 = M2L on the tensor cores, bit 1
+// = M2M/L2L into level l on the tensor cores, bit 2 = M2L by staged RCR,
+// bit 3 = M2M/L2L into level l by staged RCR, bit 4 = the staged M2L's
 // rotations on the tensor cores, bit 5 = the same for M2M/L2L, bit 6 = the
-// staged M2L in double-FP32, bit 7 = the same for M2M/L2L.
+// staged M2L in double-FP32, bit 7 = the same for M2M/L2L, bit 8 = the M2L
+// tiles in double-FP32, bit 9 = the same for M2M/L2L.
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_out, int* choice) {
     const bool mixed = op->prec == FB_PREC_MIXED_FMM;
     double times_local[FB_TUNE_TIMES * (FB_MAXLEV + 1)];
@@ -133,8 +135,10 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
         int ch = 0;
         // ---- M2L of level l: RCR tiles, RCR staged, tensor cores
         auto at_level = [&](const RcrTask& tk) { return tk.src_base == op->lev_off[l] && tk.dst_base == tk.src_base; };
-        if (rcr_tile_candidate(op->p[l], csz))
+        if (rcr_tile_candidate(op->p[l], csz)) {
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 0, mp, loc, s, nrhs, cnt, reps, &tl[0]));
+            if (!mixed) FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 4, mp, loc, s, nrhs, cnt, reps, &tl[10]));
+        }
         if (rcr_staged_candidate(op->p[l], csz)) {
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 1, mp, loc, s, nrhs, cnt, reps, &tl[4]));
             if (mixed) FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 2, mp, loc, s, nrhs, cnt, reps, &tl[6]));
@@ -143,7 +147,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 3, mp, loc, s, nrhs, cnt, reps, &tl[8]));
         double best = -1.0;
         if (tl[0] >= 0) best = tl[0];
-        for (int form = 1; form <= 3; ++form) {
+        for (int form = 1; form <= 4; ++form) {
             const double v = tl[2 + 2 * form];
             if (v >= 0 && (best < 0 || v < best)) {
                 best = v;
@@ -184,17 +188,25 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                 }
             }
         }
-        if (stg_m2l[l] && !(ch & 1)) ch |= stg_m2l[l] == 2 ? 4 | 16 : (stg_m2l[l] == 3 ? 4 | 64 : 4);
+        if (stg_m2l[l] && !(ch & 1)) {
+            const int f = stg_m2l[l];
+            ch |= f == 4 ? 256 : (f == 2 ? 4 | 16 : (f == 3 ? 4 | 64 : 4));
+        }
         // ---- M2M + L2L between levels l-1 and l
         if (l >= 3) {
             const int pm = std::max(op->p[l], op->p[l - 1]);
             auto all = [](const RcrTask&) { return true; };
-            double rt = -1.0, rs = -1.0, rc = -1.0, rd = -1.0;
+            double rt = -1.0, rs = -1.0, rc = -1.0, rd = -1.0, rtd = -1.0;
             if (rcr_tile_candidate(pm, csz)) {
                 double a = 0, b = 0;
                 FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 0, mp, mp, s, nrhs, cnt, reps, &a));
                 FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 0, loc, loc, s, nrhs, cnt, reps, &b));
                 rt = std::max(a, 0.0) + std::max(b, 0.0);
+                if (!mixed) {
+                    FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 4, mp, mp, s, nrhs, cnt, reps, &a));
+                    FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 4, loc, loc, s, nrhs, cnt, reps, &b));
+                    rtd = std::max(a, 0.0) + std::max(b, 0.0);
+                }
             }
             if (rcr_staged_candidate(pm, csz)) {
                 double a = 0, b = 0;
@@ -217,6 +229,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             tl[5] = rs;
             tl[7] = rc;
             tl[9] = rd;
+            tl[11] = rtd;
             double best2 = rt;
             if (rt < 0 || (rs >= 0 && rs < rt)) {
                 best2 = rs;
@@ -229,6 +242,10 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             if (rd >= 0 && (best2 < 0 || rd < best2)) {
                 best2 = rd;
                 stg_pair[l] = 3;
+            }
+            if (rtd >= 0 && (best2 < 0 || rtd < best2)) {
+                best2 = rtd;
+                stg_pair[l] = 4;
             }
             std::vector<int> need;
             std::vector<TcGroup> up, down;
@@ -260,7 +277,10 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                     fb_tc_free(op->tc_l2l[l]);
                 }
             }
-            if (stg_pair[l] && !(ch & 2)) ch |= stg_pair[l] == 2 ? 8 | 32 : (stg_pair[l] == 3 ? 8 | 128 : 8);
+            if (stg_pair[l] && !(ch & 2)) {
+                const int f = stg_pair[l];
+                ch |= f == 4 ? 512 : (f == 2 ? 8 | 32 : (f == 3 ? 8 | 128 : 8));
+            }
         }
         if (choice) choice[l] = ch;
     }
@@ -311,12 +331,14 @@ fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s) {
         const int c = choice[l];
         if (op->prec != FB_PREC_MIXED_FMM && (c & (1 | 2 | 16 | 32)))
             return fb_fail(FB_ERR_ARG, "tensor-core forms apply to mixed operators");
-        if (op->prec != FB_PREC_FP64_FMM && (c & (64 | 128)))
+        if (op->prec != FB_PREC_FP64_FMM && (c & (64 | 128 | 256 | 512)))
             return fb_fail(FB_ERR_ARG, "double-FP32 forms apply to FP64 operators");
         if (((c & (16 | 64)) && !(c & 4)) || ((c & (32 | 128)) && !(c & 8)))
             return fb_fail(FB_ERR_ARG, "bits 4-7 refine the staged bits 2/3");
-        stg_m2l[l] = (c & 4) ? ((c & 16) ? 2 : ((c & 64) ? 3 : 1)) : 0;
-        stg_pair[l] = (c & 8) ? ((c & 32) ? 2 : ((c & 128) ? 3 : 1)) : 0;
+        if (((c & 256) && (c & 4)) || ((c & 512) && (c & 8)))
+            return fb_fail(FB_ERR_ARG, "bits 8/9 (tiles in double-FP32) exclude the staged bits 2/3");
+        stg_m2l[l] = (c & 4) ? ((c & 16) ? 2 : ((c & 64) ? 3 : 1)) : ((c & 256) ? 4 : 0);
+        stg_pair[l] = (c & 8) ? ((c & 32) ? 2 : ((c & 128) ? 3 : 1)) : ((c & 512) ? 4 : 0);
     }
     FB_CHECK(fb_rcr_restage(op, stg_m2l, stg_pair));
     if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;

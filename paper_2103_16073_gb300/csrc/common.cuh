@@ -50,6 +50,27 @@ __host__ __device__ __forceinline__ void cmacc(cx<R>& a, cx<R> b, cx<R> c) {
     a.re += b.re * c.re + b.im * c.im;
     a.im += b.re * c.im - b.im * c.re;
 }
+// double-FP32 complex multiply-accumulate (a += b c), four df FMAs
+__device__ __forceinline__ void cmac(cx<df>& a, cx<df> b, cx<df> c) {
+    a.re = fma(b.re, c.re, a.re);
+    a.re = fma(-b.im, c.im, a.re);
+    a.im = fma(b.re, c.im, a.im);
+    a.im = fma(b.im, c.re, a.im);
+}
+// conversions between the storage precision of expansions (O) and the
+// arithmetic of a translation kernel (R): equal types, or FP64 <-> double-FP32
+template <class R>
+__host__ __device__ __forceinline__ R real_from(double v) { return (R)v; }
+template <>
+__host__ __device__ __forceinline__ df real_from<df>(double v) { return df_from(v); }
+template <class R, class O>
+__device__ __forceinline__ cx<R> cx_to(const cx<O>& a) { return mk<R>(real_from<R>(a.re), real_from<R>(a.im)); }
+template <>
+__device__ __forceinline__ cx<float> cx_to<float, float>(const cx<float>& a) { return a; }
+template <class O, class R>
+__device__ __forceinline__ cx<O> cx_out(const cx<R>& a) { return a; }
+template <>
+__device__ __forceinline__ cx<double> cx_out<double, df>(const cx<df>& a) { return mk(df_to(a.re), df_to(a.im)); }
 __host__ __device__ __forceinline__ cf to_f(cd a) { return mk<float>((float)a.re, (float)a.im); }
 __host__ __device__ __forceinline__ cd to_d(cf a) { return mk<double>((double)a.re, (double)a.im); }
 template <class R> __host__ __device__ __forceinline__ cx<R> from_d(cd a);
@@ -219,7 +240,8 @@ struct RcrTask {
     int64_t pair_off;
     int32_t npairs, p_out, p_in, pc;
     int64_t src_base, dst_base;
-    int32_t staged;      // 1: run by the staged GEMM passes, 0: per-pair tiles
+    int32_t staged;      // 0: per-pair tiles, 1: staged GEMM passes, 2: staged with tensor-core
+                         // rotations, 3: staged in double-FP32, 4: per-pair tiles in double-FP32
     int32_t pad;
 };
 struct RcrTile {
@@ -254,7 +276,8 @@ struct RcrPlan {
     size_t csize = 0;    // bytes per complex coefficient
     void* stg = nullptr;        // staged passes of the large-order tasks
     int64_t stg_elems = 0;      // staging coefficients they need per buffer
-    std::map<int, RcrTileSet> multi;   // tiles for nrhs > 1 (built on first use)
+    std::map<int, RcrTileSet> multi;   // tiles for nrhs > 1 (built on first use), key 2 nrhs + df
+    RcrTileSet df_tiles;        // tiles of the double-FP32 tasks (one right-hand side)
 };
 void fb_rcr_free(RcrPlan& p);
 bool fb_stg_staged(const RcrTask& tk);
@@ -289,6 +312,7 @@ void fb_stg_level_info(const void* plan, int li, int64_t* src_base, int64_t* dst
 struct fb_op;
 fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* form);
 fb_status fb_stg_df_tables(fb_op* op, cudaStream_t s);
+fb_status fb_rcr_df_factors(fb_op* op, int P);
 fb_status fb_stg_tables(fb_op* op, const double* rotd64, cudaStream_t s);
 
 // A group of box pairs sharing one composed translation matrix (job) on the
@@ -367,6 +391,9 @@ struct fb_op {
     int* stc_err = nullptr;                  // error flag of the tensor-core staged passes
     df* rotf_df = nullptr;                   // FP64 operators: folded tables and coaxial sets in
     cx<df>* coax_df = nullptr;               // double-FP32 for the staged levels that use it
+    df* rotd_df = nullptr;                   // ... and the real factors of degrees < rotd_df_P
+    int rotd_df_P = 0;                       // (per-pair tiles in double-FP32)
+    int64_t rotd_df_per = 0;                 // values per direction
     std::vector<int> dir_of_code;            // M2L offset code -> direction (-1: near)
     // RCR form per level: 1 = staged passes, 0 = per-pair tiles (M2L of
     // level l; M2M and L2L between levels l-1 and l)

@@ -238,11 +238,13 @@ __device__ __forceinline__ void tri_of(int e, int& n, int& m) {
 // Full chunks use W = RcrChunk, the remainder of a tile one pair at a time.
 template <class R> struct RcrChunk { static constexpr int value = 8; };
 template <> struct RcrChunk<double> { static constexpr int value = 4; };
+template <> struct RcrChunk<df> { static constexpr int value = 4; };
 // CTAs per SM the register budget must allow: FP64 tiles (48 KB of shared
 // memory each) are latency bound and want four resident CTAs, FP32 tiles
 // (96 KB) fit two.
 template <class R> struct RcrMinBlocks { static constexpr int value = 2; };
 template <> struct RcrMinBlocks<double> { static constexpr int value = 4; };
+template <> struct RcrMinBlocks<df> { static constexpr int value = 4; };
 
 // acc += a x for real a
 template <class R>
@@ -373,9 +375,9 @@ __device__ __forceinline__ void rcr_rotate_full(const R* dn, int n, const cx<R>*
 #pragma unroll
     for (int q = 0; q < W; ++q) us[(b0 + q) * Pin + e] = acc[q];
 }
-template <int W, class R>
-__device__ __forceinline__ void rcr_back_full(const R* dn, int n1, cx<R> phc, const cx<R>* vs, int Pout, int b0,
-                                              int e, const int64_t* dsto, cx<R>* dst) {
+template <int W, class R, class O>
+__device__ __forceinline__ void rcr_back_full(const R* dn, int n1, cx<O> phc, const cx<R>* vs, int Pout, int b0,
+                                              int e, const int64_t* dsto, cx<O>* dst) {
     cx<R> acc[W];
 #pragma unroll
     for (int q = 0; q < W; ++q) acc[q] = mk<R>(0, 0);
@@ -389,23 +391,27 @@ __device__ __forceinline__ void rcr_back_full(const R* dn, int n1, cx<R> phc, co
     }
 #pragma unroll
     for (int q = 0; q < W; ++q) {
-        cx<R> y = acc[q] * phc;
-        cx<R>* d = dst + dsto[b0 + q] + e;
+        cx<O> y = cx_out<O, R>(acc[q]) * phc;
+        cx<O>* d = dst + dsto[b0 + q] + e;
         atomicAdd(&d->re, y.re);
         atomicAdd(&d->im, y.im);
     }
 }
 
-template <class R>
+// R: arithmetic and tables (rotd, coax), O: expansions and phases (R = O,
+// or R = double-FP32 on FP64 expansions); rot_stride: values per direction
+// in rotd.
+template <class R, class O>
 __global__ void __launch_bounds__(256, RcrMinBlocks<R>::value) k_rcr(const RcrTask* __restrict__ tasks, const RcrTile* __restrict__ tiles,
-                                             const R* __restrict__ rotd, const cx<R>* __restrict__ rph,
-                                             int64_t per_dir, int prot, const cx<R>* __restrict__ coax,
+                                             const R* __restrict__ rotd, const cx<O>* __restrict__ rph,
+                                             int64_t per_dir, int64_t rot_stride, int prot,
+                                             const cx<R>* __restrict__ coax,
                                              const int32_t* __restrict__ src_idx,
                                              const int32_t* __restrict__ dst_idx,
-                                             const cx<R>* __restrict__ src, cx<R>* __restrict__ dst,
+                                             const cx<O>* __restrict__ src, cx<O>* __restrict__ dst,
                                              int nrhs, int64_t rstride) {
     constexpr int BCH = RcrChunk<R>::value;
-    constexpr bool kFold = sizeof(R) == 4;   // FP32: folded rotations; FP64: unfolded
+    constexpr bool kFold = sizeof(R) == 4;   // FP32: folded rotations; FP64, double-FP32: unfolded
     extern __shared__ unsigned char smem_raw[];
     __shared__ int64_t s_dst_off[16];
     RcrTile tl = tiles[blockIdx.x];
@@ -425,7 +431,7 @@ __global__ void __launch_bounds__(256, RcrMinBlocks<R>::value) k_rcr(const RcrTa
         s_dst_off[b] = rh * rstride + tk.dst_base + (int64_t)dst_idx[tk.pair_off + pr] * Pout;
     }
     const int64_t dir = tk.rot_off / per_dir;
-    const cx<R>* ph = rph + dir * (2 * prot - 1) + (prot - 1);   // ph[m] = e^{i m phi}
+    const cx<O>* ph = rph + dir * (2 * prot - 1) + (prot - 1);   // ph[m] = e^{i m phi}
     for (int q = tid; q < nb * Pin; q += nth) {
         int b = q / Pin, e = q % Pin;
         int col = tl.col0 + b;
@@ -433,21 +439,21 @@ __global__ void __launch_bounds__(256, RcrMinBlocks<R>::value) k_rcr(const RcrTa
         int sb = src_idx[tk.pair_off + pr];
         int n, j;
         nj_of(e, n, j);
-        const cx<R>* x = src + rh * rstride + tk.src_base + (int64_t)sb * Pin + (int64_t)n * n + n;   // (n, 0)
-        cx<R> v;
-        if (!kFold) {
+        const cx<O>* x = src + rh * rstride + tk.src_base + (int64_t)sb * Pin + (int64_t)n * n + n;   // (n, 0)
+        cx<O> v;
+        if constexpr (!kFold) {
             v = x[j - n] * ph[j - n];   // plain phased input, degree-major
         } else if (j == 0) {
             v = x[0];
         } else {
             const int m = j <= n ? j : j - n;
-            const cx<R> xp = x[m] * ph[m], xm = x[-m] * ph[-m];
+            const cx<O> xp = x[m] * ph[m], xm = x[-m] * ph[-m];
             v = j <= n ? xp + xm : xp - xm;
         }
-        xs[q] = v;
+        xs[q] = cx_to<R, O>(v);
     }
     __syncthreads();
-    const R* D = rotd + tk.rot_off;
+    const R* D = rotd + dir * rot_stride;
     // chunk widths BCH, then 4, 2, 1 for the rest of the tile
 #define RCR_CHUNKS(CALL)                                              \
     {                                                                 \
@@ -462,7 +468,7 @@ __global__ void __launch_bounds__(256, RcrMinBlocks<R>::value) k_rcr(const RcrTa
         int n, j;
         nj_of(e, n, j);
         const R* Dc = D + (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3 + (int64_t)n * (2 * n + 1) + n;
-        if (kFold) {
+        if constexpr (kFold) {
 #define RCR_ROT(W) rcr_rotate<(W)>(Dc, n, j, xs, Pin, b0, e, us)
             RCR_CHUNKS(RCR_ROT)
 #undef RCR_ROT
@@ -493,30 +499,30 @@ __global__ void __launch_bounds__(256, RcrMinBlocks<R>::value) k_rcr(const RcrTa
 #undef RCR_COAX
     }
     __syncthreads();
-    if (!kFold) {
+    if constexpr (!kFold) {
         // back-rotate: y_{n'}^{m'} = sum_mu d^{n'}_{mu,m'} v_{n'}^mu, e^{-i m' phi}, scatter-add
         for (int e = tid; e < Pout; e += nth) {
             int n1, m1;
             nm_of(e, n1, m1);
             const R* Dn = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (m1 + n1);
-            const cx<R> phc = conjg(ph[m1]);
+            const cx<O> phc = conjg(ph[m1]);
 #define RCR_BACK(W) rcr_back_full<(W)>(Dn, n1, phc, vs, Pout, b0, e, s_dst_off, dst)
             RCR_CHUNKS(RCR_BACK)
 #undef RCR_BACK
         }
-        return;
-    }
-    // folded back-rotation of every pair +-m' of every degree n' < p_out, then scatter-add
-    const int npairs_out = tk.p_out * (tk.p_out + 1) / 2;
-    for (int e = tid; e < npairs_out; e += nth) {
-        int n1, mp;
-        tri_of(e, n1, mp);
-        const R* Dc = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (int64_t)n1 * (2 * n1 + 1) + n1;
-        const int mmax = min(n1, pmid - 1);
-        const cx<R> phm = ph[mp];
+    } else {
+        // folded back-rotation of every pair +-m' of every degree n' < p_out, then scatter-add
+        const int npairs_out = tk.p_out * (tk.p_out + 1) / 2;
+        for (int e = tid; e < npairs_out; e += nth) {
+            int n1, mp;
+            tri_of(e, n1, mp);
+            const R* Dc = D + (int64_t)n1 * (2 * n1 - 1) * (2 * n1 + 1) / 3 + (int64_t)n1 * (2 * n1 + 1) + n1;
+            const int mmax = min(n1, pmid - 1);
+            const cx<R> phm = ph[mp];
 #define RCR_BACK(W) rcr_back<(W)>(Dc, n1, mp, mmax, phm, vs, Pout, b0, s_dst_off, dst)
-        RCR_CHUNKS(RCR_BACK)
+            RCR_CHUNKS(RCR_BACK)
 #undef RCR_BACK
+        }
     }
 #undef RCR_CHUNKS
 }
@@ -526,13 +532,16 @@ __global__ void __launch_bounds__(256, RcrMinBlocks<R>::value) k_rcr(const RcrTa
 // entry from registers, so larger tiles raise the arithmetic per load) and
 // 48 KB for FP64 (bound by the FP64 pipe, it wants more resident warps).
 // Tasks of large order are left to the staged passes (fb_stg_staged).
-static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& tiles, size_t& smem) {
+// want_df: the tiles of the tasks in double-FP32 arithmetic (staged == 4),
+// else the others.
+static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& tiles, size_t& smem,
+                           bool want_df = false) {
     const size_t budget = pl.csize == sizeof(cf) ? 96 * 1024 : 48 * 1024;
     tiles.clear();
     smem = 0;
     for (int t = 0; t < (int)pl.h_tasks.size(); ++t) {
         const RcrTask& tk = pl.h_tasks[t];
-        if (fb_stg_staged(tk)) continue;
+        if (fb_stg_staged(tk) || (tk.staged == 4) != want_df) continue;
         int64_t elems = (int64_t)tk.p_in * tk.p_in + std::max(tk.p_in * tk.p_in, tk.p_out * tk.p_out);
         size_t per = (size_t)elems * pl.csize;
         int nb = (int)std::max<size_t>(1, std::min<size_t>(16, budget / per));
@@ -545,24 +554,28 @@ static void rcr_make_tiles(const RcrPlan& pl, int nrhs, std::vector<RcrTile>& ti
     }
 }
 
-static fb_status rcr_tiles_for(RcrPlan& pl, int nrhs, RcrTileSet* out) {
+static fb_status rcr_tiles_for(RcrPlan& pl, int nrhs, RcrTileSet* out, bool want_df = false) {
     if (nrhs == 1) {
+        if (want_df) {
+            *out = pl.df_tiles;
+            return FB_OK;
+        }
         out->tiles = pl.tiles;
         out->ntiles = pl.ntiles;
         out->smem = pl.smem;
         return FB_OK;
     }
-    auto it = pl.multi.find(nrhs);
+    auto it = pl.multi.find(2 * nrhs + (want_df ? 1 : 0));
     if (it == pl.multi.end()) {
         std::vector<RcrTile> h;
         RcrTileSet ts;
-        rcr_make_tiles(pl, nrhs, h, ts.smem);
+        rcr_make_tiles(pl, nrhs, h, ts.smem, want_df);
         ts.ntiles = (int)h.size();
         if (!h.empty()) {
             FB_CHECK(dalloc(&ts.tiles, h.size()));
             FB_CUDA(cudaMemcpy(ts.tiles, h.data(), sizeof(RcrTile) * h.size(), cudaMemcpyHostToDevice));
         }
-        it = pl.multi.emplace(nrhs, ts).first;
+        it = pl.multi.emplace(2 * nrhs + (want_df ? 1 : 0), ts).first;
     }
     *out = it->second;
     return FB_OK;
@@ -582,6 +595,8 @@ struct RotArgs {
     int64_t fper;
     StcTabs tc;       // tables of the tensor-core staged passes (single precision)
     DfTabs dft;       // tables of the double-FP32 staged passes (FP64 operators)
+    const df* d_df;   // real factors in double-FP32 (degrees < the tiles' largest order)
+    int64_t per_dir_df;
 };
 template <class R>
 static RotArgs<R> rot_args(const fb_op* op) {
@@ -596,6 +611,8 @@ static RotArgs<R> rot_args(const fb_op* op) {
     a.fper = op->rotf_per;
     a.tc = StcTabs{op->stc_tab, op->stc_off, op->stc_per, op->stc_err};
     a.dft = DfTabs{op->rotf_df, op->coax_df};
+    a.d_df = op->rotd_df;
+    a.per_dir_df = op->rotd_df_per;
     return a;
 }
 static fb_status stg_run(void* plan, const RotArgs<float>& r, const cf* coax, const cf* src, cf* dst,
@@ -670,13 +687,55 @@ static fb_status run_rcr(RcrPlan& pl, const RotArgs<R>& rot, const cx<R>* coax, 
     RcrTileSet ts;
     FB_CHECK(rcr_tiles_for(pl, nrhs, &ts));
     if (ts.ntiles > 0) {
-        FB_CHECK(fb_smem_cap((const void*)k_rcr<R>, ts.smem));
-        k_rcr<R><<<ts.ntiles, 256, ts.smem, s>>>(pl.tasks, ts.tiles, rot.d, rot.ph, rot.per_dir, rot.prot, coax,
-                                                 pl.src_idx, pl.dst_idx, src, dst, nrhs, rstride);
+        FB_CHECK(fb_smem_cap((const void*)k_rcr<R, R>, ts.smem));
+        k_rcr<R, R><<<ts.ntiles, 256, ts.smem, s>>>(pl.tasks, ts.tiles, rot.d, rot.ph, rot.per_dir, rot.per_dir,
+                                                    rot.prot, coax, pl.src_idx, pl.dst_idx, src, dst, nrhs, rstride);
         FB_LAUNCH_CHECK();
         fb_count_launch();
     }
+    if constexpr (sizeof(R) == 8) {
+        // tiles in double-FP32 arithmetic on the FP64 expansions
+        FB_CHECK(rcr_tiles_for(pl, nrhs, &ts, true));
+        if (ts.ntiles > 0) {
+            if (!rot.d_df || !rot.dft.coax) return fb_fail(FB_ERR_STATE, "RCR tiles: double-FP32 tables missing");
+            FB_CHECK(fb_smem_cap((const void*)k_rcr<df, double>, ts.smem));
+            k_rcr<df, double><<<ts.ntiles, 256, ts.smem, s>>>(pl.tasks, ts.tiles, rot.d_df, rot.ph, rot.per_dir,
+                                                              rot.per_dir_df, rot.prot, rot.dft.coax, pl.src_idx,
+                                                              pl.dst_idx, src, dst, nrhs, rstride);
+            FB_LAUNCH_CHECK();
+            fb_count_launch();
+        }
+    }
     if (pl.stg) FB_CHECK(stg_run(pl.stg, rot, coax, src, dst, s, nrhs, rstride));
+    return FB_OK;
+}
+
+static __global__ void k_d_to_df(const double* __restrict__ in, int64_t per_in, int64_t per_out, int ndir,
+                                 df* __restrict__ out) {
+    const int64_t total = (int64_t)ndir * per_out;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = i / per_out, e = i - d * per_out;
+        out[i] = df_from(in[d * per_in + e]);
+    }
+}
+
+// Real rotation factors of every direction in double-FP32, degrees < P (the
+// largest order of the tiles that use them), rebuilt when a larger P is asked.
+fb_status fb_rcr_df_factors(fb_op* op, int P) {
+    if (op->rotd_df && op->rotd_df_P >= P) return FB_OK;
+    if (!op->rotd64 || P > op->Prot) return fb_fail(FB_ERR_STATE, "RCR tiles: no FP64 rotation factors");
+    const int ndir = (int)(op->rot_count / op->per_dir);
+    const int64_t per = (int64_t)P * (2 * P - 1) * (2 * P + 1) / 3;   // sum_{n<P} (2n+1)^2
+    FB_CUDA(cudaDeviceSynchronize());
+    dfree(op->rotd_df);
+    FB_CHECK(dalloc(&op->rotd_df, (size_t)ndir * per));
+    k_d_to_df<<<(unsigned)std::min<int64_t>(((int64_t)ndir * per + 255) / 256, 8192), 256>>>(op->rotd64, op->per_dir,
+                                                                                          per, ndir, op->rotd_df);
+    FB_CUDA(cudaDeviceSynchronize());
+    op->rotd_df_P = P;
+    op->rotd_df_per = per;
+    op->buf_gen++;   // captured graphs refer to the old factors
+    fb_count_launch();
     return FB_OK;
 }
 
@@ -688,9 +747,16 @@ fb_status fb_rcr_upload(fb_op* op, RcrPlan& pl, const int32_t* src, const int32_
     pl.src_idx = src;
     pl.dst_idx = dst;
     pl.csize = csize;
+    for (const RcrTask& tk : pl.h_tasks) {
+        if (tk.staged == 2 && op->prec != FB_PREC_MIXED_FMM)
+            return fb_fail(FB_ERR_ARG, "tensor-core staged RCR applies to mixed operators");
+        if ((tk.staged == 3 || tk.staged == 4) && op->prec != FB_PREC_FP64_FMM)
+            return fb_fail(FB_ERR_ARG, "double-FP32 RCR applies to FP64 operators");
+    }
     // a pair whose working set does not fit one CTA can only run staged
     for (RcrTask& tk : pl.h_tasks)
-        if (!tk.staged && !fb_rcr_tile_fits(tk.p_in, tk.p_out, csize)) tk.staged = 1;
+        if ((tk.staged == 0 || tk.staged == 4) && !fb_rcr_tile_fits(tk.p_in, tk.p_out, csize))
+            tk.staged = tk.staged == 4 ? 3 : 1;
     rcr_make_tiles(pl, 1, pl.h_tiles, pl.smem);
     pl.ntiles = (int)pl.h_tiles.size();
     if (pl.h_tasks.empty()) return FB_OK;
@@ -700,11 +766,19 @@ fb_status fb_rcr_upload(fb_op* op, RcrPlan& pl, const int32_t* src, const int32_
         FB_CHECK(dalloc(&pl.tiles, pl.h_tiles.size()));
         FB_CUDA(cudaMemcpy(pl.tiles, pl.h_tiles.data(), sizeof(RcrTile) * pl.h_tiles.size(), cudaMemcpyHostToDevice));
     }
-    for (const RcrTask& tk : pl.h_tasks) {
-        if (tk.staged == 2 && op->prec != FB_PREC_MIXED_FMM)
-            return fb_fail(FB_ERR_ARG, "tensor-core staged RCR applies to mixed operators");
-        if (tk.staged == 3 && op->prec != FB_PREC_FP64_FMM)
-            return fb_fail(FB_ERR_ARG, "double-FP32 staged RCR applies to FP64 operators");
+    {
+        std::vector<RcrTile> h;
+        rcr_make_tiles(pl, 1, h, pl.df_tiles.smem, true);
+        pl.df_tiles.ntiles = (int)h.size();
+        if (!h.empty()) {
+            int pmax = 0;
+            for (const RcrTask& tk : pl.h_tasks)
+                if (tk.staged == 4) pmax = std::max(pmax, std::max(tk.p_in, tk.p_out));
+            FB_CHECK(fb_rcr_df_factors(op, pmax));
+            FB_CHECK(fb_stg_df_tables(op, cudaStreamLegacy));   // coaxial sets in double-FP32
+            FB_CHECK(dalloc(&pl.df_tiles.tiles, h.size()));
+            FB_CUDA(cudaMemcpy(pl.df_tiles.tiles, h.data(), sizeof(RcrTile) * h.size(), cudaMemcpyHostToDevice));
+        }
     }
     FB_CHECK(fb_stg_build(pl, op->theta_slot, op->per_dir, &pl.stg, &pl.stg_elems));
     if (fb_stg_uses_tc(pl.stg)) FB_CHECK(fb_stc_tables(op, cudaStreamLegacy));
@@ -909,6 +983,8 @@ static void free_plan(TransPlan& p) {
 void fb_rcr_free(RcrPlan& p) {
     dfree(p.tasks);
     dfree(p.tiles);
+    dfree(p.df_tiles.tiles);
+    p.df_tiles = RcrTileSet();
     fb_stg_free(p.stg);
     p.stg_elems = 0;
     for (auto& kv : p.multi) dfree(kv.second.tiles);
@@ -962,6 +1038,7 @@ void fb_fmm_destroy(fb_op* op) {
     dfree(op->stc_err);
     dfree(op->rotf_df);
     dfree(op->coax_df);
+    dfree(op->rotd_df);
 }
 
 // ---------------------------------------------------------------------------

@@ -125,20 +125,6 @@ __device__ __forceinline__ void ld4(cx<df> (&o)[4], const cx<df>* p) {
         o[i] = mk(df(a.x, a.y), df(a.z, a.w));
     }
 }
-// conversions between the storage precision of the expansions (O) and the
-// arithmetic of the staged passes (R): equal types, or FP64 <-> double-FP32
-template <class R>
-__host__ __device__ __forceinline__ R real_from(double v) { return (R)v; }
-template <>
-__host__ __device__ __forceinline__ df real_from<df>(double v) { return df_from(v); }
-template <class R, class O>
-__device__ __forceinline__ cx<R> cx_to(const cx<O>& a) { return mk<R>(real_from<R>(a.re), real_from<R>(a.im)); }
-template <>
-__device__ __forceinline__ cx<float> cx_to<float, float>(const cf& a) { return a; }
-template <class O, class R>
-__device__ __forceinline__ cx<O> cx_out(const cx<R>& a) { return a; }
-template <>
-__device__ __forceinline__ cd cx_out<double, df>(const cx<df>& a) { return mk(df_to(a.re), df_to(a.im)); }
 __device__ __forceinline__ void ld4(cd (&o)[4], const cd* p) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -501,7 +487,7 @@ fb_status upload(T** d, const std::vector<T>& h) {
 
 }  // namespace
 
-bool fb_stg_staged(const RcrTask& tk) { return tk.staged != 0; }
+bool fb_stg_staged(const RcrTask& tk) { return tk.staged >= 1 && tk.staged <= 3; }
 
 bool fb_rcr_tile_fits(int p_in, int p_out, size_t csize) {
     const size_t per = (size_t)((int64_t)p_in * p_in + std::max<int64_t>((int64_t)p_in * p_in, (int64_t)p_out * p_out));

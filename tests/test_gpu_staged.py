@@ -269,3 +269,45 @@ def test_staged_double_float_large_orders():
         fb.fb_operator_destroy(op)
         fb.fb_tree_destroy(tree)
         fb.fb_mesh_destroy(mesh)
+
+
+TILES_DF = [256 | 512] * 13   # bits 8/9: per-pair tiles in double-FP32 (FP64 operators)
+
+
+@pytest.mark.parametrize("pmin", [12, 30])
+def test_tiles_double_float_match_fp64_tiles(sub, pmin):
+    """Per-pair RCR tiles in double-FP32 arithmetic: M2L, M2M and L2L against
+    the FP64 tiles, one and several right-hand sides; levels whose tiles do
+    not fit run staged in double-FP32."""
+    wl, mesh, tree = sub
+    op = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, pmin)
+    try:
+        x = torch.tensor(seeded_vector(wl.n, 47), device="cuda")
+        fb.fb_operator_set_forms(op, TILES)
+        y_t = apply(op, x)
+        fb.fb_operator_set_forms(op, TILES_DF)
+        y_d = apply(op, x)
+        assert rel(y_d, y_t) < 1e-11
+        X = torch.tensor(np.stack([seeded_vector(wl.n, 95 + r) for r in range(3)]), device="cuda")
+        Y = apply(op, X)
+        for r in range(3):
+            assert rel(apply(op, X[r].contiguous()), Y[r]) < 1e-13
+        with pytest.raises(fb.FBError):
+            fb.fb_operator_set_forms(op, [4 | 256] * 13)   # tiles and staged at once
+    finally:
+        fb.fb_operator_destroy(op)
+
+
+def test_autotune_fp64_reports_double_float_forms(sub):
+    wl, mesh, tree = sub
+    op = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, 30)
+    try:
+        x = torch.tensor(seeded_vector(wl.n, 62), device="cuda")
+        fb.fb_operator_set_forms(op, TILES)
+        y0 = apply(op, x)
+        tune = fb.fb_operator_autotune(op, 1)
+        assert all(v["m2l_tiles_df"] is not None and v["m2l_staged_df"] is not None for v in tune.values())
+        assert all(v["m2l_staged_tc"] is None for v in tune.values())
+        assert rel(apply(op, x), y0) < 1e-11
+    finally:
+        fb.fb_operator_destroy(op)
