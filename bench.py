@@ -194,10 +194,13 @@ def build_problem(fb, W, torch, wl, rank, forms="", forms_inner="", forms_fp64="
     else:
         tune = {"mixed": fb.fb_operator_autotune(A32, 1)}
     if forms_fp64 or forms:
-        fb.fb_operator_set_forms(A64, [int(v) & 12 for v in (forms_fp64 or forms).split(",")])
-        tune["fp64_fixed_forms"] = forms_fp64 or forms
+        f64 = [int(v) for v in forms_fp64.split(",")] if forms_fp64 else [int(v) & 12 for v in forms.split(",")]
+        fb.fb_operator_set_forms(A64, f64)
+        tune["fp64_fixed_forms"] = ",".join(str(v) for v in f64)
+        a64_forms = f64
     else:
         tune["fp64"] = fb.fb_operator_autotune(A64, 1)
+        a64_forms = [tune["fp64"][l]["choice"] if l in tune["fp64"] else 0 for l in range(13)]
     for op in (A32, A64):
         fb.fb_operator_use_graphs(op, True)
     Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, INNER_D0, INNER_PMIN)
@@ -216,7 +219,7 @@ def build_problem(fb, W, torch, wl, rank, forms="", forms_inner="", forms_fp64="
     fb.fb_operator_apply(L64, g, b)
     torch.cuda.synchronize()
     return dict(wl=wl, mesh=mesh, tree=tree, A32=A32, A64=A64, L64=L64, pc32=pc32, pc64=pc64, b=b, tune=tune,
-                Alow=Alow, pclow=pclow, inner=inner, setup_s=time.perf_counter() - t0)
+                Alow=Alow, pclow=pclow, inner=inner, A64_forms=a64_forms, setup_s=time.perf_counter() - t0)
 
 
 def destroy_problem(fb, P):
@@ -260,11 +263,14 @@ def rcr_flops(p_out, p_in):
 # double-FP32 multiply-accumulate: 12 FP32-pipe operations (df.cuh)
 DF_OPS_PER_MAC = 12
 
-FAMILY = {("f32", "tiles"): "k_rcr<float>", ("f32", "tc"): "k_trans_tc", ("f64", "tiles"): "k_rcr<double>"}
+FAMILY = {("f32", "tiles"): "k_rcr<float>", ("f32", "tc"): "k_trans_tc", ("f64", "tiles"): "k_rcr<double>",
+          ("f64", "tiles_df"): "k_rcr<df>"}
 FAMILY_WHAT = {
     "k_stg_tc": "staged RCR rotation passes on the tensor cores (k_stg_tc<0> rotate, k_stg_tc<1> rotate back; "
                 "tcgen05 3xTF32 GEMMs per polar-angle group and degree)",
     "k_stg_coax<float>": "staged RCR coaxial pass (FP32 CUDA-core GEMMs per |t| and order)",
+    "k_stc_coax": "staged RCR coaxial pass on the tensor cores (tcgen05 3xTF32, complex blocks in real form per "
+                  "|t| and order)",
     "k_stg_rot+back<float>": "staged RCR rotation passes on CUDA cores (FP32)",
     "k_stg_prep<float>": "staged RCR pre-pass (folded phased inputs, FP32)",
     "k_stg<double>": "staged RCR passes in FP64 (true residual)",
@@ -274,7 +280,26 @@ FAMILY_WHAT = {
     "k_rcr<float>": "per-pair RCR M2L tiles (FP32)",
     "k_trans_tc": "tensor-core M2L (tcgen05 3xTF32, composed matrices)",
     "k_rcr<double>": "per-pair RCR M2L tiles (FP64, true residual)",
+    "k_rcr<df>": "per-pair RCR M2L tiles in double-FP32 arithmetic (FP64 true residual; 48-bit significand)",
 }
+
+
+def fp64_only_forms(tune):
+    """Per-level forms of an FP64 operator restricted to FP64 arithmetic
+    (per-pair tiles or staged passes, whichever the autotuner timed faster),
+    for the plain FP64 baseline."""
+    out = [0] * 13
+    for l, t in (tune or {}).items():
+        l = int(l)
+        c = 0
+        a, b = t["m2l_rcr"], t["m2l_staged"]
+        if b is not None and (a is None or b < a):
+            c |= 4
+        a, b = t["m2m_l2l_rcr"], t["m2m_l2l_staged"]
+        if b is not None and (a is None or b < a):
+            c |= 8
+        out[l] = c
+    return out
 
 
 def m2l_levels(tune, p, pairs):
@@ -287,7 +312,12 @@ def m2l_levels(tune, p, pairs):
         ch = t["choice"]
         if ch & 4 and not ch & 1:
             continue   # staged: timed pass by pass (fb_operator_staged_pass_times)
-        form, ms = ("tc", t["m2l_tensor"]) if ch & 1 else ("tiles", t["m2l_rcr"])
+        if ch & 1:
+            form, ms = "tc", t["m2l_tensor"]
+        elif ch & 256:
+            form, ms = "tiles_df", t["m2l_tiles_df"]
+        else:
+            form, ms = "tiles", t["m2l_rcr"]
         if ms is None:
             continue
         out[l] = (form, ms, float(pairs[l]) * rcr_flops(int(p[l]), int(p[l])))
@@ -343,14 +373,18 @@ def roofline(fb, P, iters, true_mv, pk, fp32_peak, fp64_peak):
                 add("k_stg<double>", "f64", key, l, count, d["rot"] + d["coax"] + d["back"], rot + cox)
                 add("k_stg_prep<double>", "hbm", key, l, count, d["prep"], npair * pl * pl * cw)
                 continue
-            if d["form"] == "tensor_rot":
+            if d["form"] == "tensor_rot_coax":
                 add("k_stg_tc", "tensor", key, l, count, d["rot"] + d["back"], rot)
+                add("k_stc_coax", "tensor", key, l, count, d["coax"], cox)
+            elif d["form"] == "tensor_rot":
+                add("k_stg_tc", "tensor", key, l, count, d["rot"] + d["back"], rot)
+                add("k_stg_coax<float>", "f32", key, l, count, d["coax"], cox)
             else:
                 add("k_stg_rot+back<float>", "f32", key, l, count, d["rot"] + d["back"], rot)
-            add("k_stg_coax<float>", "f32", key, l, count, d["coax"], cox)
+                add("k_stg_coax<float>", "f32", key, l, count, d["coax"], cox)
             add("k_stg_prep<float>", "hbm", key, l, count, d["prep"], npair * pl * pl * cw)
         for l, (form, ms, alg) in m2l_levels(tune.get(key), p, pairs).items():
-            add(FAMILY[(prec, form)], "tensor" if form == "tc" else prec, key, l, count, ms, alg)
+            add(FAMILY[(prec, form)], {"tc": "tensor", "tiles_df": "df"}.get(form, prec), key, l, count, ms, alg)
     out = {}
     for name, f in fam.items():
         peak, unit, kind = peaks_[f["kind"]]
@@ -426,8 +460,9 @@ def secondary(fb, W, torch, stream, name):
         solve(P["inner"], P["A32"], P["A64"])
         ts = [timed(torch, stream, lambda: solve(P["inner"], P["A32"], P["A64"])) for _ in range(3)]
         t_io = statistics.median(t for t, _ in ts)
-        t64, (i64,) = timed(torch, stream, lambda: solve(P["pc64"], P["A64"], None))
         mv32, _ = matvec_rate(fb, torch, stream, P["A32"], wl.n, 20)
+        fb.fb_operator_set_forms(P["A64"], fp64_only_forms(P["tune"]["fp64"]))   # FP64 arithmetic
+        t64, (i64,) = timed(torch, stream, lambda: solve(P["pc64"], P["A64"], None))
         mv64, _ = matvec_rate(fb, torch, stream, P["A64"], wl.n, 5)
         info = ts[-1][1][0]
         return {"workload": WORKLOADS[name][1], "n_elements": wl.n,
@@ -535,12 +570,26 @@ def run_ours(args):
     mv64_s, ph64 = matvec_rate(fb, torch, stream, P["A64"], n, max(2, args.matvecs // 5))
     mvlow_s, ph_low = matvec_rate(fb, torch, stream, P["Alow"], n, args.matvecs)
 
-    # plain FP64 path: FP64 FMM + FP64 block Jacobi, one solve
-    x64 = torch.zeros_like(P["b"])
-    t64, (info64,) = timed(torch, stream, lambda: fb.fb_fgmres_solve(
-        P["A64"], P["b"], x64, pc=P["pc64"], tol=TOL, restart=RESTART, maxit=3000))
-    # agreement of the two solutions (both judged by the FP64 operator)
+    # plain FP64 path: FP64 FMM + FP64 block Jacobi, one solve, with the
+    # FP64 operator restricted to FP64 arithmetic; then the same method with
+    # the operator's autotuned forms (double-FP32 translations included)
+    fp64_forms = fp64_only_forms(P["tune"].get("fp64")) if "fp64" in P["tune"] else \
+        [int(v) & 12 for v in P["tune"]["fp64_fixed_forms"].split(",")]
+    tuned_forms = P["A64_forms"]
+
+    def plain_solve():
+        x64 = torch.zeros_like(P["b"])
+        t, (inf,) = timed(torch, stream, lambda: fb.fb_fgmres_solve(
+            P["A64"], P["b"], x64, pc=P["pc64"], tol=TOL, restart=RESTART, maxit=3000))
+        return t, inf, x64
+    fb.fb_operator_set_forms(P["A64"], fp64_forms)
+    mv64p_s, _ = matvec_rate(fb, torch, stream, P["A64"], n, max(2, args.matvecs // 5))
+    t64, info64, x64 = plain_solve()
+    fb.fb_operator_set_forms(P["A64"], tuned_forms)
+    t64d, info64d, x64d = plain_solve()
+    # agreement of the solutions (all judged by the FP64 operator)
     sol_diff = float((x - x64).norm() / x64.norm())
+    sol_diff_df = float((x64d - x64).norm() / x64.norm())
 
     # end to end through the public API with host (pinned) buffers
     bh = torch.empty(n, dtype=torch.complex128, pin_memory=True)
@@ -588,14 +637,21 @@ def run_ours(args):
         "orders_per_level": [int(v) for v in p[2:]],
         "m2l_pairs_per_level": [int(v) for v in pairs[2:]],
         "matvecs_per_s": {"mixed": round(1 / mv_s, 3), "fp64": round(1 / mv64_s, 3),
+                          "fp64_arithmetic_only": round(1 / mv64p_s, 3),
                           "inner_low_accuracy": round(1 / mvlow_s, 3)},
         "matvec_ms": {"mixed": round(mv_s * 1e3, 3), "fp64": round(mv64_s * 1e3, 3),
+                      "fp64_arithmetic_only": round(mv64p_s * 1e3, 3),
                       "inner_low_accuracy": round(mvlow_s * 1e3, 3)},
         "phase_ms": {"mixed": {k: round(v, 3) for k, v in ph.items()},
                      "fp64": {k: round(v, 3) for k, v in ph64.items()},
                      "inner_low_accuracy": {k: round(v, 3) for k, v in ph_low.items()}},
         "plain_fp64": {"time_to_solve_s": round(t64, 4), "iterations": info64["iters"],
                        "true_relres": info64["true_relres"], "preconditioner": "FP64 block Jacobi"},
+        "plain_fp64_df_translations": {
+            "time_to_solve_s": round(t64d, 4), "iterations": info64d["iters"],
+            "true_relres": info64d["true_relres"], "solution_rel_diff_vs_plain_fp64": sol_diff_df,
+            "what": "the plain method with the FP64 operator's autotuned forms (translations in double-FP32 "
+                    "arithmetic, 48-bit significand, where faster); the mixed solve's true residual uses them"},
         "speedup_vs_plain_fp64": round(t64 / (ms_step / 1e3), 2),
         "solution_rel_diff_mixed_vs_plain": sol_diff,
         "learned": "side study, not in the timed step (the trained network did not reduce the outer "

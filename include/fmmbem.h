@@ -308,8 +308,8 @@ FB_API fb_status fb_operator_status(fb_op* op, void* stream);
  * three times timed (median).  ms: 4*13 doubles, ms[4l + 0..3] = pre-pass
  * (folded phased inputs), rotation, coaxial, back-rotation of level l (-1:
  * level not staged); form: 13 ints, 1 = passes on CUDA cores, 2 = rotation
- * passes on the tensor cores, 3 = passes in double-FP32 arithmetic (0: not
- * staged).  Synchronises the device.
+ * passes on the tensor cores, 3 = passes in double-FP32 arithmetic, 5 =
+ * rotation and coaxial passes on the tensor cores (0: not staged).  Synchronises the device.
  * Errors: FB_ERR_ARG (NULL argument, dense or composite operator). */
 FB_API fb_status fb_operator_staged_pass_times(fb_op* op, void* stream, double* ms, int* form);
 FB_API fb_status fb_set_device_wait_limit(long long limit, long long* previous);
@@ -351,7 +351,8 @@ FB_API fb_status fb_precond_use_graphs(fb_precond* pc, int enable);
  *     the rotations and by |t| for the coaxial step),
  *   - mixed precision only: the staged passes with their two rotation
  *     passes on the tensor cores (3xTF32 GEMMs of the folded real rotation
- *     blocks, one polar-angle group and degree at a time),
+ *     blocks, one polar-angle group and degree at a time), and optionally
+ *     the coaxial step too (complex blocks in real form per |t| and order),
  *   - FP64 only: the staged passes in double-FP32 arithmetic (each value
  *     an unevaluated sum of two FP32 numbers, a 48-bit significand, on the
  *     FP32 pipe), from order 16 on, and the per-pair tiles in the same
@@ -359,33 +360,39 @@ FB_API fb_status fb_precond_use_graphs(fb_precond* pc, int enable);
  *   - mixed precision only: the stacked tensor-core GEMM of composed
  *     matrices (3xTF32).
  * Tiles are timed below order 60, the staged passes from order 24 on (the
- * measured crossover lies between); a level keeps at least one candidate.
- * times: FB_TUNE_TIMES*13 doubles or NULL, times[FB_TUNE_TIMES l + 0..11] =
+ * measured crossover lies between), with tensor-core rotations from order
+ * 12 on, in double-FP32 from order 16 on; a level keeps at least one
+ * candidate.
+ * times: FB_TUNE_TIMES*13 doubles or NULL, times[FB_TUNE_TIMES l + 0..13] =
  * M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles, M2M+L2L tensor, M2L RCR
  * staged, M2M+L2L RCR staged, M2L RCR staged with tensor-core rotations,
  * M2M+L2L RCR staged with tensor-core rotations, M2L RCR staged in
  * double-FP32, M2M+L2L RCR staged in double-FP32, M2L RCR tiles in
- * double-FP32, M2M+L2L RCR tiles in double-FP32, in ms (-1: not a
- * candidate); choice: 13 ints or NULL, bit 0 = M2L of level l on the tensor
+ * double-FP32, M2M+L2L RCR tiles in double-FP32, M2L RCR staged with
+ * rotations and coaxial step on the tensor cores, the same for M2M+L2L, in
+ * ms (-1: not a candidate); choice: 13 ints or NULL, bit 0 = M2L of level l on the tensor
  * cores, bit 1 = M2M/L2L into level l on the tensor cores, bit 2 = M2L of
  * level l by staged RCR, bit 3 = M2M/L2L into level l by staged RCR, bit 4 =
  * the staged M2L's rotations on the tensor cores (with bit 2), bit 5 = the
  * staged M2M/L2L's rotations on the tensor cores (with bit 3), bit 6 = the
  * staged M2L in double-FP32 (with bit 2), bit 7 = the staged M2M/L2L in
  * double-FP32 (with bit 3), bit 8 = the M2L tiles in double-FP32 (without
- * bit 2), bit 9 = the M2M/L2L tiles in double-FP32 (without bit 3).
+ * bit 2), bit 9 = the M2M/L2L tiles in double-FP32 (without bit 3), bit 10
+ * = the staged M2L's coaxial step on the tensor cores too (with bit 4),
+ * bit 11 = the same for M2M/L2L (with bit 5).
  * Rebuilds the operator's translation plans (synchronises the device).
  * Errors: FB_ERR_ARG. */
-#define FB_TUNE_TIMES 12
+#define FB_TUNE_TIMES 14
 FB_API fb_status fb_operator_autotune(fb_op* op, int nrhs, void* stream, double* times, int* choice);
 
 /* Installs a per-level choice in the format the autotuner returns (13 ints,
  * bits as above), so that a tuned configuration can be saved and restored
  * without timing.  Levels whose per-pair RCR working set does not fit one
  * CTA run staged whatever bit 2/3 says.  Tensor-core bits (0, 1, 4, 5) need
- * a mixed-precision operator, double-FP32 bits (6-9) an FP64 FMM operator;
- * bits 4 and 6 need bit 2, bits 5 and 7 need bit 3, bit 8 excludes bit 2
- * and bit 9 bit 3.  Errors: FB_ERR_ARG. */
+ * a mixed-precision operator (so do 10, 11), double-FP32 bits (6-9) an FP64
+ * FMM operator; bits 4 and 6 need bit 2, bits 5 and 7 need bit 3, bit 8
+ * excludes bit 2 and bit 9 bit 3, bit 10 needs bit 4 and bit 11 bit 5.
+ * Errors: FB_ERR_ARG. */
 FB_API fb_status fb_operator_set_forms(fb_op* op, const int* choice, void* stream);
 FB_API fb_status fb_operator_apply_multi(fb_op* op, const double* x, double* y, int nrhs, int memspace,
                                          void* stream);

@@ -352,7 +352,7 @@ def fb_operator_apply_noalloc(op, x, y, stream=None):
 
 
 FB_MAX_RHS = 64
-FB_TUNE_TIMES = 12   # autotuner timings per level
+FB_TUNE_TIMES = 14   # autotuner timings per level
 lib.fb_operator_apply_multi.restype = C.c_int
 lib.fb_operator_apply_multi.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
 lib.fb_fgmres_solve_multi.restype = C.c_int
@@ -404,10 +404,12 @@ def fb_operator_autotune(op, nrhs=1, stream=None):
     installs the fastest; returns {level: {"m2l_rcr", "m2l_tensor",
     "m2m_l2l_rcr", "m2m_l2l_tensor", "m2l_staged", "m2m_l2l_staged",
     "m2l_staged_tc", "m2m_l2l_staged_tc", "m2l_staged_df", "m2m_l2l_staged_df",
-    "m2l_tiles_df", "m2m_l2l_tiles_df" (ms, None if not a candidate),
+    "m2l_tiles_df", "m2m_l2l_tiles_df", "m2l_staged_tcc", "m2m_l2l_staged_tcc"
+    (ms, None if not a candidate),
     "m2l_on_tensor", "m2m_l2l_on_tensor", "m2l_staged_on", "m2m_l2l_staged_on",
     "m2l_staged_tc_on", "m2m_l2l_staged_tc_on", "m2l_staged_df_on",
-    "m2m_l2l_staged_df_on", "m2l_tiles_df_on", "m2m_l2l_tiles_df_on", "choice"}}."""
+    "m2m_l2l_staged_df_on", "m2l_tiles_df_on", "m2m_l2l_tiles_df_on",
+    "m2l_staged_tcc_on", "m2m_l2l_staged_tcc_on", "choice"}}."""
     nt = FB_TUNE_TIMES
     times = np.full(nt * 13, -1.0)
     choice = np.zeros(13, np.int32)
@@ -421,12 +423,14 @@ def fb_operator_autotune(op, nrhs=1, stream=None):
         out[l] = {"m2l_rcr": f(t[0]), "m2l_tensor": f(t[1]), "m2m_l2l_rcr": f(t[2]), "m2m_l2l_tensor": f(t[3]),
                   "m2l_staged": f(t[4]), "m2m_l2l_staged": f(t[5]), "m2l_staged_tc": f(t[6]),
                   "m2m_l2l_staged_tc": f(t[7]), "m2l_staged_df": f(t[8]), "m2m_l2l_staged_df": f(t[9]),
-                  "m2l_tiles_df": f(t[10]), "m2m_l2l_tiles_df": f(t[11]),
+                  "m2l_tiles_df": f(t[10]), "m2m_l2l_tiles_df": f(t[11]), "m2l_staged_tcc": f(t[12]),
+                  "m2m_l2l_staged_tcc": f(t[13]),
                   "m2l_on_tensor": bool(choice[l] & 1), "m2m_l2l_on_tensor": bool(choice[l] & 2),
                   "m2l_staged_on": bool(choice[l] & 4), "m2m_l2l_staged_on": bool(choice[l] & 8),
                   "m2l_staged_tc_on": bool(choice[l] & 16), "m2m_l2l_staged_tc_on": bool(choice[l] & 32),
                   "m2l_staged_df_on": bool(choice[l] & 64), "m2m_l2l_staged_df_on": bool(choice[l] & 128),
                   "m2l_tiles_df_on": bool(choice[l] & 256), "m2m_l2l_tiles_df_on": bool(choice[l] & 512),
+                  "m2l_staged_tcc_on": bool(choice[l] & 1024), "m2m_l2l_staged_tcc_on": bool(choice[l] & 2048),
                   "choice": int(choice[l])}
     return out
 
@@ -758,7 +762,7 @@ lib.fb_operator_staged_pass_times.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p
 
 def fb_operator_staged_pass_times(op, stream=None):
     """{level: {"prep", "rot", "coax", "back" (device ms of each staged M2L
-    pass alone), "form" ("cuda", "tensor_rot" or "df")}} for the operator's
+    pass alone), "form" ("cuda", "tensor_rot", "tensor_rot_coax" or "df")}} for the operator's
     staged levels; overwrites its expansion buffers."""
     ms = np.full(4 * 13, -1.0)
     tc = np.zeros(13, np.int32)
@@ -769,7 +773,7 @@ def fb_operator_staged_pass_times(op, stream=None):
         if np.all(t < 0):
             continue
         out[l] = {"prep": float(t[0]), "rot": float(t[1]), "coax": float(t[2]), "back": float(t[3]),
-                  "form": {1: "cuda", 2: "tensor_rot", 3: "df"}.get(int(tc[l]), "none")}
+                  "form": {1: "cuda", 2: "tensor_rot", 3: "df", 5: "tensor_rot_coax"}.get(int(tc[l]), "none")}
     return out
 
 

@@ -64,6 +64,9 @@ bool rcr_staged_candidate(int p, size_t csz) { return p >= 24 || !rcr_tile_candi
 // double-FP32 passes: their arithmetic runs several times faster than FP64,
 // which moves the crossover with the FP64 tiles to lower orders
 bool rcr_df_candidate(int p) { return p >= 16; }
+// staged passes with tensor-core rotations: their degree blocks pack into
+// one tile up to 256 columns, so low orders stay worth timing
+bool rcr_stc_candidate(int p) { return p >= 12; }
 
 }  // namespace
 
@@ -91,7 +94,7 @@ fb_status time_rcr(fb_op* op, const RcrPlan& base, Pick pick, int staged, void* 
     return st;
 }
 
-// times[12 * l + {0..11}] = M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles,
+// times[14 * l + {0..11}] = M2L RCR tiles, M2L tensor, M2M+L2L RCR tiles,
 // M2M+L2L tensor, M2L RCR staged, M2M+L2L RCR staged, M2L RCR staged with
 // tensor-core rotations, M2M+L2L RCR staged with tensor-core rotations, M2L
 // RCR staged in double-FP32, M2M+L2L RCR staged in double-FP32, M2L RCR
@@ -101,7 +104,9 @@ fb_status time_rcr(fb_op* op, const RcrPlan& base, Pick pick, int staged, void* 
 // bit 3 = M2M/L2L into level l by staged RCR, bit 4 = the staged M2L's
 // rotations on the tensor cores, bit 5 = the same for M2M/L2L, bit 6 = the
 // staged M2L in double-FP32, bit 7 = the same for M2M/L2L, bit 8 = the M2L
-// tiles in double-FP32, bit 9 = the same for M2M/L2L.
+// tiles in double-FP32, bit 9 = the same for M2M/L2L, bit 10 = the staged
+// M2L's coaxial step on the tensor cores too (with bit 4), bit 11 = the same
+// for M2M/L2L (with bit 5); times[14 l + 12, 13] time those forms.
 fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_out, int* choice) {
     const bool mixed = op->prec == FB_PREC_MIXED_FMM;
     double times_local[FB_TUNE_TIMES * (FB_MAXLEV + 1)];
@@ -139,15 +144,17 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 0, mp, loc, s, nrhs, cnt, reps, &tl[0]));
             if (!mixed) FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 4, mp, loc, s, nrhs, cnt, reps, &tl[10]));
         }
-        if (rcr_staged_candidate(op->p[l], csz)) {
+        if (rcr_staged_candidate(op->p[l], csz))
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 1, mp, loc, s, nrhs, cnt, reps, &tl[4]));
-            if (mixed) FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 2, mp, loc, s, nrhs, cnt, reps, &tl[6]));
+        if (mixed && rcr_stc_candidate(op->p[l])) {
+            FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 2, mp, loc, s, nrhs, cnt, reps, &tl[6]));
+            FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 5, mp, loc, s, nrhs, cnt, reps, &tl[12]));
         }
         if (!mixed && rcr_df_candidate(op->p[l]))
             FB_CHECK(time_rcr(op, op->m2l_rcr, at_level, 3, mp, loc, s, nrhs, cnt, reps, &tl[8]));
         double best = -1.0;
         if (tl[0] >= 0) best = tl[0];
-        for (int form = 1; form <= 4; ++form) {
+        for (int form = 1; form <= 5; ++form) {
             const double v = tl[2 + 2 * form];
             if (v >= 0 && (best < 0 || v < best)) {
                 best = v;
@@ -190,13 +197,13 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
         }
         if (stg_m2l[l] && !(ch & 1)) {
             const int f = stg_m2l[l];
-            ch |= f == 4 ? 256 : (f == 2 ? 4 | 16 : (f == 3 ? 4 | 64 : 4));
+            ch |= f == 4 ? 256 : (f == 5 ? 4 | 16 | 1024 : (f == 2 ? 4 | 16 : (f == 3 ? 4 | 64 : 4)));
         }
         // ---- M2M + L2L between levels l-1 and l
         if (l >= 3) {
             const int pm = std::max(op->p[l], op->p[l - 1]);
             auto all = [](const RcrTask&) { return true; };
-            double rt = -1.0, rs = -1.0, rc = -1.0, rd = -1.0, rtd = -1.0;
+            double rt = -1.0, rs = -1.0, rc = -1.0, rd = -1.0, rtd = -1.0, rcc = -1.0;
             if (rcr_tile_candidate(pm, csz)) {
                 double a = 0, b = 0;
                 FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 0, mp, mp, s, nrhs, cnt, reps, &a));
@@ -213,11 +220,15 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
                 FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 1, mp, mp, s, nrhs, cnt, reps, &a));
                 FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 1, loc, loc, s, nrhs, cnt, reps, &b));
                 rs = std::max(a, 0.0) + std::max(b, 0.0);
-                if (mixed) {
-                    FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 2, mp, mp, s, nrhs, cnt, reps, &a));
-                    FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 2, loc, loc, s, nrhs, cnt, reps, &b));
-                    rc = std::max(a, 0.0) + std::max(b, 0.0);
-                }
+            }
+            if (mixed && rcr_stc_candidate(pm)) {
+                double a = 0, b = 0;
+                FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 2, mp, mp, s, nrhs, cnt, reps, &a));
+                FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 2, loc, loc, s, nrhs, cnt, reps, &b));
+                rc = std::max(a, 0.0) + std::max(b, 0.0);
+                FB_CHECK(time_rcr(op, op->m2m_rcr[l], all, 5, mp, mp, s, nrhs, cnt, reps, &a));
+                FB_CHECK(time_rcr(op, op->l2l_rcr[l], all, 5, loc, loc, s, nrhs, cnt, reps, &b));
+                rcc = std::max(a, 0.0) + std::max(b, 0.0);
             }
             if (!mixed && rcr_df_candidate(pm)) {
                 double a = 0, b = 0;
@@ -230,12 +241,13 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             tl[7] = rc;
             tl[9] = rd;
             tl[11] = rtd;
+            tl[13] = rcc;
             double best2 = rt;
             if (rt < 0 || (rs >= 0 && rs < rt)) {
                 best2 = rs;
                 stg_pair[l] = 1;
             }
-            if (rc >= 0 && rc < best2) {
+            if (rc >= 0 && (best2 < 0 || rc < best2)) {
                 best2 = rc;
                 stg_pair[l] = 2;
             }
@@ -246,6 +258,10 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             if (rtd >= 0 && (best2 < 0 || rtd < best2)) {
                 best2 = rtd;
                 stg_pair[l] = 4;
+            }
+            if (rcc >= 0 && (best2 < 0 || rcc < best2)) {
+                best2 = rcc;
+                stg_pair[l] = 5;
             }
             std::vector<int> need;
             std::vector<TcGroup> up, down;
@@ -279,7 +295,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
             }
             if (stg_pair[l] && !(ch & 2)) {
                 const int f = stg_pair[l];
-                ch |= f == 4 ? 512 : (f == 2 ? 8 | 32 : (f == 3 ? 8 | 128 : 8));
+                ch |= f == 4 ? 512 : (f == 5 ? 8 | 32 | 2048 : (f == 2 ? 8 | 32 : (f == 3 ? 8 | 128 : 8)));
             }
         }
         if (choice) choice[l] = ch;
@@ -329,7 +345,7 @@ fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s) {
     int stg_m2l[FB_MAXLEV + 1] = {0}, stg_pair[FB_MAXLEV + 1] = {0};
     for (int l = 2; l <= L; ++l) {
         const int c = choice[l];
-        if (op->prec != FB_PREC_MIXED_FMM && (c & (1 | 2 | 16 | 32)))
+        if (op->prec != FB_PREC_MIXED_FMM && (c & (1 | 2 | 16 | 32 | 1024 | 2048)))
             return fb_fail(FB_ERR_ARG, "tensor-core forms apply to mixed operators");
         if (op->prec != FB_PREC_FP64_FMM && (c & (64 | 128 | 256 | 512)))
             return fb_fail(FB_ERR_ARG, "double-FP32 forms apply to FP64 operators");
@@ -337,8 +353,10 @@ fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s) {
             return fb_fail(FB_ERR_ARG, "bits 4-7 refine the staged bits 2/3");
         if (((c & 256) && (c & 4)) || ((c & 512) && (c & 8)))
             return fb_fail(FB_ERR_ARG, "bits 8/9 (tiles in double-FP32) exclude the staged bits 2/3");
-        stg_m2l[l] = (c & 4) ? ((c & 16) ? 2 : ((c & 64) ? 3 : 1)) : ((c & 256) ? 4 : 0);
-        stg_pair[l] = (c & 8) ? ((c & 32) ? 2 : ((c & 128) ? 3 : 1)) : ((c & 512) ? 4 : 0);
+        if (((c & 1024) && !(c & 16)) || ((c & 2048) && !(c & 32)))
+            return fb_fail(FB_ERR_ARG, "bits 10/11 (tensor-core coaxial step) refine bits 4/5");
+        stg_m2l[l] = (c & 4) ? ((c & 16) ? ((c & 1024) ? 5 : 2) : ((c & 64) ? 3 : 1)) : ((c & 256) ? 4 : 0);
+        stg_pair[l] = (c & 8) ? ((c & 32) ? ((c & 2048) ? 5 : 2) : ((c & 128) ? 3 : 1)) : ((c & 512) ? 4 : 0);
     }
     FB_CHECK(fb_rcr_restage(op, stg_m2l, stg_pair));
     if (op->prec != FB_PREC_MIXED_FMM) return FB_OK;

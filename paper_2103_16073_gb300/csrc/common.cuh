@@ -241,7 +241,8 @@ struct RcrTask {
     int32_t npairs, p_out, p_in, pc;
     int64_t src_base, dst_base;
     int32_t staged;      // 0: per-pair tiles, 1: staged GEMM passes, 2: staged with tensor-core
-                         // rotations, 3: staged in double-FP32, 4: per-pair tiles in double-FP32
+                         // rotations, 3: staged in double-FP32, 4: per-pair tiles in double-FP32,
+                         // 5: staged with tensor-core rotations and coaxial step
     int32_t pad;
 };
 struct RcrTile {
@@ -281,8 +282,8 @@ struct RcrPlan {
 };
 void fb_rcr_free(RcrPlan& p);
 bool fb_stg_staged(const RcrTask& tk);
-fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, int64_t per_dir, void** out,
-                       int64_t* elems);
+fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, int64_t per_dir, const cd* coax64,
+                       void** out, int64_t* elems);
 void fb_stg_free(void*& plan);
 // tables of the staged levels that run in double-FP32 arithmetic (FP64 operators)
 struct DfTabs {
@@ -307,7 +308,8 @@ fb_status fb_stg_run_d(void* plan, const double* rf, int64_t fper, const cd* rph
                        const DfTabs& dft, int only_level = -1, int pass_mask = 15);
 bool fb_stg_uses_df(const void* plan);
 int fb_stg_level_count(const void* plan);
-// form: 1 CUDA cores, 2 rotations on the tensor cores, 3 double-FP32 arithmetic
+// form: 1 CUDA cores, 2 rotations on the tensor cores, 3 double-FP32 arithmetic,
+// 5 rotations and coaxial step on the tensor cores
 void fb_stg_level_info(const void* plan, int li, int64_t* src_base, int64_t* dst_base, int* form);
 struct fb_op;
 fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* form);

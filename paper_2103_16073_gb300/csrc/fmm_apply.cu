@@ -630,7 +630,8 @@ static fb_status stg_run(void* plan, const RotArgs<double>& r, const cd* coax, c
 // of each pass of every staged M2L level of an operator, on its expansion
 // buffers: ms[4 l + {0..3}] = pre-pass, rotation, coaxial, back-rotation of
 // level l (-1: not staged); form[l] = 1 CUDA cores, 2 rotations on the
-// tensor cores, 3 double-FP32 arithmetic (0: not staged).
+// tensor cores, 3 double-FP32 arithmetic, 5 rotations and coaxial step on
+// the tensor cores (0: not staged).
 fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* tc) {
     for (int i = 0; i < 4 * (FB_MAXLEV + 1); ++i) ms[i] = -1.0;
     for (int l = 0; l <= FB_MAXLEV; ++l) tc[l] = 0;
@@ -748,7 +749,7 @@ fb_status fb_rcr_upload(fb_op* op, RcrPlan& pl, const int32_t* src, const int32_
     pl.dst_idx = dst;
     pl.csize = csize;
     for (const RcrTask& tk : pl.h_tasks) {
-        if (tk.staged == 2 && op->prec != FB_PREC_MIXED_FMM)
+        if ((tk.staged == 2 || tk.staged == 5) && op->prec != FB_PREC_MIXED_FMM)
             return fb_fail(FB_ERR_ARG, "tensor-core staged RCR applies to mixed operators");
         if ((tk.staged == 3 || tk.staged == 4) && op->prec != FB_PREC_FP64_FMM)
             return fb_fail(FB_ERR_ARG, "double-FP32 RCR applies to FP64 operators");
@@ -780,7 +781,7 @@ fb_status fb_rcr_upload(fb_op* op, RcrPlan& pl, const int32_t* src, const int32_
             FB_CUDA(cudaMemcpy(pl.df_tiles.tiles, h.data(), sizeof(RcrTile) * h.size(), cudaMemcpyHostToDevice));
         }
     }
-    FB_CHECK(fb_stg_build(pl, op->theta_slot, op->per_dir, &pl.stg, &pl.stg_elems));
+    FB_CHECK(fb_stg_build(pl, op->theta_slot, op->per_dir, op->coax64, &pl.stg, &pl.stg_elems));
     if (fb_stg_uses_tc(pl.stg)) FB_CHECK(fb_stc_tables(op, cudaStreamLegacy));
     if (fb_stg_uses_df(pl.stg)) FB_CHECK(fb_stg_df_tables(op, cudaStreamLegacy));
     if (pl.stg_elems > op->stg_elems) {

@@ -457,10 +457,16 @@ struct StgLevel {
     int nrt = 0, nct = 0, nbt = 0;
     // rotation passes on the tensor cores (rcr_staged_tc.cu) instead of rt / bt
     int tc = 0;
+    int tcc = 0;  // ... and the coaxial pass too
     int df = 0;   // passes in double-FP32 arithmetic (FP64 expansions)
     StcTile* rtc = nullptr;
     StcTile* btc = nullptr;
     int nrtc = 0, nbtc = 0;
+    // coaxial pass on the tensor cores (tc levels): tiles and the plan's
+    // pre-split coaxial blocks
+    StcCTile* ctc = nullptr;
+    int nctc = 0;
+    float* ctab = nullptr;
 };
 
 struct StgPlanImpl {
@@ -475,6 +481,8 @@ void free_level(StgLevel& lv) {
     dfree(lv.bt);
     dfree(lv.rtc);
     dfree(lv.btc);
+    dfree(lv.ctc);
+    dfree(lv.ctab);
 }
 
 template <class T>
@@ -487,7 +495,7 @@ fb_status upload(T** d, const std::vector<T>& h) {
 
 }  // namespace
 
-bool fb_stg_staged(const RcrTask& tk) { return tk.staged >= 1 && tk.staged <= 3; }
+bool fb_stg_staged(const RcrTask& tk) { return (tk.staged >= 1 && tk.staged <= 3) || tk.staged == 5; }
 
 bool fb_rcr_tile_fits(int p_in, int p_out, size_t csize) {
     const size_t per = (size_t)((int64_t)p_in * p_in + std::max<int64_t>((int64_t)p_in * p_in, (int64_t)p_out * p_out));
@@ -502,8 +510,8 @@ int fb_rcr_default_staged(int p_in, int p_out, size_t csize) {
 // the group's folded rotation tables).
 // *elems receives the complex coefficients one staging buffer needs (the
 // largest level: pairs x max(p_in, p_out)^2).
-fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, int64_t per_dir, void** out,
-                       int64_t* elems) {
+fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, int64_t per_dir, const cd* coax64,
+                       void** out, int64_t* elems) {
     *out = nullptr;
     *elems = 0;
     // tasks by level (same source and target level arrays and orders)
@@ -529,7 +537,8 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
         lv.p_in = p_in;
         lv.p_out = p_out;
         for (int t : ts) {
-            lv.tc = lv.tc || pl.h_tasks[t].staged == 2;
+            lv.tc = lv.tc || pl.h_tasks[t].staged == 2 || pl.h_tasks[t].staged == 5;
+            lv.tcc = lv.tcc || pl.h_tasks[t].staged == 5;
             lv.df = lv.df || pl.h_tasks[t].staged == 3;
         }
         lv.S = std::max(p_in * p_in, p_out * p_out);
@@ -599,12 +608,19 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
         }
         std::vector<int32_t> cidx;
         std::vector<StgCTile> ct;
+        std::vector<StcCTile> ctc;
+        std::vector<StcCBlock> cblocks;
+        int64_t ctab_floats = 0;
         const int q = std::min(p_in, p_out);
         for (auto& sv : sets) {
             const int c0 = (int)cidx.size();
             cidx.insert(cidx.end(), sv.second.begin(), sv.second.end());
             const int ns = (int)sv.second.size();
             const int pc = set_pc[sv.first];
+            if (lv.tcc && coax64) {
+                fb_stc_coax_set(c0, ns, sv.first, pc, p_in, p_out, ctc, cblocks, &ctab_floats);
+                continue;
+            }
             for (int am = 0; am < q; ++am) {
                 const int nvc = am == 0 ? ns : 2 * ns;
                 const int M = p_out - am, K = p_in - am;
@@ -635,14 +651,30 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
         };
         std::stable_sort(rtc.begin(), rtc.end(), heavier(0));
         std::stable_sort(btc.begin(), btc.end(), heavier(1));
+        std::stable_sort(ctc.begin(), ctc.end(), [](const StcCTile& x, const StcCTile& y) {
+            return (int64_t)x.K * x.nr > (int64_t)y.K * y.nr;
+        });
         lv.nrtc = (int)rtc.size();
         lv.nbtc = (int)btc.size();
+        lv.nctc = (int)ctc.size();
         fb_status st;
+        StcCBlock* d_blocks = nullptr;
         if ((st = upload(&lv.slots, slots)) || (st = upload(&lv.cidx, cidx)) || (st = upload(&lv.rt, rt)) ||
             (st = upload(&lv.ct, ct)) || (st = upload(&lv.bt, bt)) || (st = upload(&lv.rtc, rtc)) ||
-            (st = upload(&lv.btc, btc))) {
+            (st = upload(&lv.btc, btc)) || (st = upload(&lv.ctc, ctc)) || (st = upload(&d_blocks, cblocks)) ||
+            (ctab_floats > 0 && (st = dalloc(&lv.ctab, (size_t)ctab_floats))) ||
+            (st = fb_stc_coax_tables(d_blocks, (int)cblocks.size(), coax64, lv.ctab, cudaStreamLegacy))) {
+            dfree(d_blocks);
             free_level(lv);
             return fail(st);
+        }
+        if (d_blocks) {
+            const cudaError_t e = cudaStreamSynchronize(cudaStreamLegacy);
+            dfree(d_blocks);
+            if (e != cudaSuccess) {
+                free_level(lv);
+                return fail(fb_fail(FB_ERR_CUDA, std::string("coaxial tables: ") + cudaGetErrorString(e)));
+            }
         }
         *elems = std::max(*elems, (int64_t)lv.nslot * lv.S);
         P->levels.push_back(lv);
@@ -737,6 +769,15 @@ template <class X, class Y, class Ph>
 static fb_status stc_pass(const StgLevel&, int, const StcTabs*, const X*, Y*, const Ph*, int, cudaStream_t) {
     return fb_fail(FB_ERR_ARG, "tensor-core staged RCR applies to single precision");
 }
+// Tensor-core coaxial pass of a level (single precision only).
+static fb_status stc_coax(const StgLevel& lv, const StcTabs* tc, const cf* U, cf* V, cudaStream_t s) {
+    if (!tc) return fb_fail(FB_ERR_STATE, "staged RCR: tensor-core error flag missing");
+    return fb_stc_coax_run(lv.ctc, lv.nctc, lv.cidx, lv.ctab, U, V, lv.S, lv.p_out, tc->err, s);
+}
+template <class X>
+static fb_status stc_coax(const StgLevel&, const StcTabs*, const X*, X*, cudaStream_t) {
+    return fb_fail(FB_ERR_ARG, "tensor-core staged RCR applies to single precision");
+}
 
 
 // The four passes of one level and right-hand side: arithmetic in R
@@ -764,7 +805,9 @@ static fb_status stg_level(const StgLevel& lv, int pass_mask, const R* rf, int64
             fb_count_launch();
         }
     }
-    if ((pass_mask & 4) && lv.nct) {
+    if ((pass_mask & 4) && lv.nctc) {
+        FB_CHECK(stc_coax(lv, tc, U, V, s));
+    } else if ((pass_mask & 4) && lv.nct) {
         k_stg_coax<R><<<lv.nct, STHREADS, sm_c, s>>>(lv.ct, lv.cidx, coax, U, V, lv.S, lv.p_out);
         fb_count_launch();
     }
@@ -831,7 +874,7 @@ void fb_stg_level_info(const void* plan, int li, int64_t* src_base, int64_t* dst
     const StgLevel& lv = ((const StgPlanImpl*)plan)->levels[li];
     *src_base = lv.src_base;
     *dst_base = lv.dst_base;
-    *form = lv.tc ? 2 : (lv.df ? 3 : 1);
+    *form = lv.tcc ? 5 : (lv.tc ? 2 : (lv.df ? 3 : 1));
 }
 
 bool fb_stg_uses_df(const void* plan) {

@@ -58,8 +58,40 @@ __host__ __device__ __forceinline__ int stc_pad16(int v) { return (v + 15) & ~15
 int64_t fb_stc_layout(int P, std::vector<int64_t>& toff);
 
 // Appends the tiles of one polar-angle group (slots [g0, g1)) for degrees
-// [0, nmax) of a pass; kdeg(n) = K of degree n (0: no block).
+// [0, nmax) of pass 0 (rotation) or 1 (back-rotation; K limited by p_in).
 void fb_stc_group_tiles(int g, int g0, int g1, int nmax, int pass, int p_in, std::vector<StcTile>& out);
+
+// A tile of the tensor-core coaxial pass: virtual columns [vc0, vc0 + nvc)
+// (nvc <= 128; order 0: one slot each, order am > 0: slot (v / 2), even part
+// for even v and odd part for odd v) of one |t| set whose slots start at
+// cidx[c0], output degrees am + r0 .. am + r0 + nr - 1 (nr <= 128), summed
+// over the K = p_in - am input degrees; its pre-split coaxial block starts at
+// float toff of the plan's coaxial tables.
+struct StcCTile {
+    int64_t toff;
+    int32_t c0, vc0, nvc;
+    int32_t am, r0, nr, K;
+    int32_t pad;
+};
+// A pre-split coaxial block to build: C^{am}_{am + r0 + i, am + k} of the set
+// at coax offset cs_off (row stride pc), i < nr, k < K, at float toff.
+struct StcCBlock {
+    int64_t cs_off, toff;
+    int32_t pc, am, r0, nr, K, pad;
+};
+constexpr int STC_CROWS = 128;   // coaxial output rows (complex) per tile
+
+// Appends the coaxial tiles and table blocks of one |t| set (ns slots at
+// cidx[c0], coefficients at cs_off, stride pc) of a level; *tfloats grows by
+// the floats of the new table blocks.
+void fb_stc_coax_set(int c0, int ns, int64_t cs_off, int pc, int p_in, int p_out, std::vector<StcCTile>& tiles,
+                     std::vector<StcCBlock>& blocks, int64_t* tfloats);
+// Builds the pre-split coaxial blocks (3xTF32 real form of the complex
+// blocks) from the FP64 coaxial sets.
+fb_status fb_stc_coax_tables(const StcCBlock* blocks, int nblocks, const cd* coax64, float* out, cudaStream_t s);
+// Launches the coaxial tiles: U (degree-major folded) -> V (order-major).
+fb_status fb_stc_coax_run(const StcCTile* tiles, int ntiles, const int32_t* cidx, const float* tab, const cf* U,
+                          cf* V, int S, int p_out, int* err, cudaStream_t s);
 
 // Launches the rotation (pass 0) or back-rotation (pass 1) tiles.
 fb_status fb_stc_run(int pass, const StcTile* tiles, int ntiles, int npmax, const int64_t* toff, const float* tab,

@@ -357,6 +357,244 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stg_tc(const StcArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(STC_TMEM_COLS));
 }
 
+// ---------------------------------------------------------------------------
+// Coaxial pass (complex blocks): D[v][(i, re/im)] = sum_k u_v[k] C[i][k] in
+// the real form with interleaved K (u as stored, complex = (re, im) pairs):
+//   A[v][(k, c)] = u_v[k].c  (v: virtual column = slot x even/odd part),
+//   B[(i, 0)][(k, 0)] = Re C,  B[(i, 0)][(k, 1)] = -Im C,
+//   B[(i, 1)][(k, 0)] = Im C,  B[(i, 1)][(k, 1)] = Re C,
+// so D[v][(i, 0)] = Re(sum u C), D[v][(i, 1)] = Im(sum u C): no zero blocks,
+// and each accumulator lane holds one output vector, written contiguously
+// into the order-major v.
+struct StcCArgs {
+    const StcCTile* tiles;
+    const int32_t* cidx;
+    const float* tab;
+    const cf* U;
+    cf* V;
+    int* err;
+    long long wait_limit;
+    int S, p_out;
+    int stage_floats;
+    int nst;            // pipeline stages (<= STC_CSTAGES)
+    int inject_stall;
+};
+
+constexpr int STC_CSTAGES = 3;
+
+__global__ void __launch_bounds__(STC_THREADS, 2) k_stc_coax(const StcCArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[STC_CSTAGES];
+    __shared__ __align__(8) uint64_t b_bar[STC_CSTAGES];
+    __shared__ __align__(8) uint64_t empty_bar[STC_CSTAGES];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ __align__(8) uint64_t never_bar;
+    __shared__ uint32_t tmem_holder;
+    __shared__ int64_t s_row[STC_M];   // slot * S (-1: padding row)
+    __shared__ int32_t s_odd[STC_M];
+    __shared__ int s_fail;
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t pad = (1024 - (raw & 1023)) & 1023;
+    float* stage0 = (float*)(smem_raw + pad);
+
+    const StcCTile tl = a.tiles[blockIdx.x];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int am = tl.am;
+    if (tid < STC_M) {
+        const int v = tl.vc0 + tid;
+        const bool ok = tid < tl.nvc;
+        const int slot = ok ? (am == 0 ? a.cidx[tl.c0 + v] : a.cidx[tl.c0 + (v >> 1)]) : 0;
+        s_row[tid] = ok ? (int64_t)slot * a.S : -1;
+        s_odd[tid] = (ok && am != 0 && (v & 1)) ? 1 : 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
+                     "r"(STC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        s_fail = 0;
+        for (int s = 0; s < STC_CSTAGES; ++s) {
+            mbar_init(&full_bar[s], STC_NPROD);
+            mbar_init(&b_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        mbar_init(&done_bar, 1);
+        mbar_init(&never_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_holder;
+    const int nst = a.nst;
+    const int np = stc_pad16(2 * tl.nr);
+    const int nkc = (2 * tl.K + KC - 1) / KC;   // K chunks of 8 complex input degrees
+
+    if (warp < STC_PRODW) {
+        // ---------------- A producers: 2 (row, 2 complex K values) units each
+        auto load = [&](int kc, int unit, float (&v)[4]) {
+            const int r = unit >> 2, q = unit & 3;
+            const int64_t row = s_row[r];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int k = kc * (KC / 2) + 2 * q + i;
+                float2 x = make_float2(0.f, 0.f);
+                if (row >= 0 && k < tl.K) {
+                    const int n = am + k;
+                    x = __ldg(reinterpret_cast<const float2*>(a.U + row + (int64_t)n * n + (s_odd[r] ? n : 0) + am));
+                }
+                v[2 * i] = x.x;
+                v[2 * i + 1] = x.y;
+            }
+        };
+        float cur[2][4], nxt[2][4];
+        load(0, tid, cur[0]);
+        load(0, tid + STC_NPROD, cur[1]);
+        for (int c = 0; c < nkc; ++c) {
+            const bool more = c + 1 < nkc;
+            if (more) {
+                load(c + 1, tid, nxt[0]);
+                load(c + 1, tid + STC_NPROD, nxt[1]);
+            }
+            const int s = c % nst, u = c / nst;
+            if (u > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (u - 1) & 1, a.wait_limit)) {
+                atomicExch(&s_fail, 1);
+                break;
+            }
+            float* st = stage0 + (size_t)s * a.stage_floats;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int unit = tid + h * STC_NPROD;
+                const int r = unit >> 2, q = unit & 3;
+                float4 hi4, lo4;
+                float* ph = &hi4.x;
+                float* pl = &lo4.x;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float t = tf32_hi(cur[h][i]);
+                    ph[i] = t;
+                    pl[i] = cur[h][i] - t;
+                }
+                const int o = canon(r, 4 * q) >> 2;
+                *reinterpret_cast<float4*>(st + o) = hi4;
+                *reinterpret_cast<float4*>(st + A_PLANE + o) = lo4;
+            }
+            asm volatile("fence.proxy.async.shared::cta;");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&full_bar[s])));
+            if (!more) break;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+                for (int i = 0; i < 4; ++i) cur[h][i] = nxt[h][i];
+        }
+    } else if (warp == STC_PRODW) {
+        // ---------------- coaxial block chunks: one bulk copy per stage -----
+        if (lane == 0) {
+            int issued = 0;
+            const uint32_t bytes = (uint32_t)(2 * np * KC * sizeof(float));
+            for (int c = 0; c < nkc; ++c) {
+                const int s = c % nst, u = c / nst;
+                if (u > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (u - 1) & 1, a.wait_limit)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                const uint32_t bb = smem_u32(&b_bar[s]);
+                const uint32_t dB = smem_u32(stage0 + (size_t)s * a.stage_floats + 2 * A_PLANE);
+                const float* g = a.tab + tl.toff + (int64_t)c * 2 * np * KC;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bb), "r"(bytes));
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dB),
+                    "l"(g), "r"(bytes), "r"(bb));
+                ++issued;
+            }
+            for (int c = std::max(0, issued - nst); c < issued; ++c)
+                mbar_wait(smem_u32(&b_bar[c % nst]), (c / nst) & 1, DRAIN_LIMIT);
+        }
+        __syncwarp();
+    } else {
+        // ---------------- MMA issuer ----------------------------------------
+        if (lane == 0) {
+            const bool stalled = a.inject_stall && !mbar_wait(smem_u32(&never_bar), 0, a.wait_limit);
+            if (stalled) atomicExch(&s_fail, 1);
+            const uint32_t idesc = tcx::idesc_tf32(STC_M, np);
+            for (int c = 0; c < nkc && !stalled; ++c) {
+                const int s = c % nst, u = c / nst;
+                if (!mbar_wait(smem_u32(&full_bar[s]), u & 1, a.wait_limit) ||
+                    !mbar_wait(smem_u32(&b_bar[s]), u & 1, a.wait_limit)) {
+                    atomicExch(&s_fail, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const float* st = stage0 + (size_t)s * a.stage_floats;
+                const uint32_t aH = smem_u32(st), aL = smem_u32(st + A_PLANE);
+                const uint32_t bH = smem_u32(st + 2 * A_PLANE), bL = smem_u32(st + 2 * A_PLANE + np * KC);
+#pragma unroll
+                for (int ks = 0; ks < KC / 8; ++ks) {
+                    const uint32_t o = ks * 2 * LBO;
+                    const uint32_t first = (c == 0 && ks == 0) ? 0u : 1u;
+                    mma_tf32(tmem, umma_desc(aH + o), umma_desc(bH + o), idesc, first);
+                    mma_tf32(tmem, umma_desc(aH + o), umma_desc(bL + o), idesc, 1u);
+                    mma_tf32(tmem, umma_desc(aL + o), umma_desc(bH + o), idesc, 1u);
+                }
+                mma_commit(&empty_bar[s]);
+            }
+            mma_commit(&done_bar);
+        }
+        __syncwarp();
+    }
+
+    // ---------------- epilogue: v[slot][moff(+-am) + r0 + i] --------------------
+    const bool done = mbar_wait(smem_u32(&done_bar), 0, DRAIN_LIMIT);
+    __syncthreads();
+    const bool ok = done && s_fail == 0;
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok && warp < STC_PRODW) {
+        const int quad = warp & 3, half = warp >> 2;
+        const int r = quad * 32 + lane;
+        const bool valid = r < tl.nvc;
+        cf* vout = a.V + (valid ? s_row[r] : 0) + moff(s_odd[r] ? -am : am, a.p_out) + tl.r0;
+        for (int g16 = half; g16 < np / 16; g16 += 2) {
+            uint32_t v[16];
+            tcx::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g16 * 16), v);
+            if (!valid) continue;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const int i = g16 * 8 + t;
+                if (i < tl.nr)
+                    *reinterpret_cast<float2*>(vout + i) =
+                        make_float2(__uint_as_float(v[2 * t]), __uint_as_float(v[2 * t + 1]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(STC_TMEM_COLS));
+}
+
+// Pre-split real-form coaxial blocks (grid: one CTA per block).
+__global__ void k_stc_coax_tables(const StcCBlock* __restrict__ blocks, const cd* __restrict__ coax,
+                                  float* __restrict__ out) {
+    const StcCBlock b = blocks[blockIdx.x];
+    const int np = stc_pad16(2 * b.nr), kp = ((2 * b.K + KC - 1) / KC) * KC;
+    float* T = out + b.toff;
+    for (int e = threadIdx.x; e < np * kp; e += blockDim.x) {
+        const int j = e / kp, k2 = e % kp;   // row (i, c'), K index (k, c)
+        const int i = j >> 1, cp = j & 1, k = k2 >> 1, c = k2 & 1;
+        double v = 0.0;
+        if (i < b.nr && k < b.K) {
+            const cd C = coax[b.cs_off + ((int64_t)b.am * b.pc + b.am + b.r0 + i) * b.pc + b.am + k];
+            v = cp == 0 ? (c == 0 ? C.re : -C.im) : (c == 0 ? C.im : C.re);
+        }
+        const int64_t o = (int64_t)(k2 / KC) * 2 * np * KC + (canon(j, k2 % KC) >> 2);
+        const float h = tf32_hi((float)v);
+        T[o] = h;
+        T[o + (int64_t)np * KC] = (float)(v - (double)h);
+    }
+}
+
 // Pre-split canonical table blocks of every group (grid: degree n, group g)
 // from the FP64 real factors d^n of the group's representative direction:
 // the folded R and B tables of rcr_staged.cu, zero-padded to whole
@@ -438,6 +676,57 @@ void fb_stc_group_tiles(int g, int g0, int g1, int nmax, int pass, int p_in, std
         }
         flush(nmax);
     }
+}
+
+void fb_stc_coax_set(int c0, int ns, int64_t cs_off, int pc, int p_in, int p_out, std::vector<StcCTile>& tiles,
+                     std::vector<StcCBlock>& blocks, int64_t* tfloats) {
+    const int q = std::min(p_in, p_out);
+    for (int am = 0; am < q; ++am) {
+        const int M = p_out - am, K = p_in - am;
+        const int nvc = am == 0 ? ns : 2 * ns;
+        for (int r0 = 0; r0 < M; r0 += STC_CROWS) {
+            const int nr = std::min(STC_CROWS, M - r0);
+            const int np = stc_pad16(2 * nr), kp = ((2 * K + KC - 1) / KC) * KC;
+            blocks.push_back(StcCBlock{cs_off, *tfloats, pc, am, r0, nr, K, 0});
+            for (int v0 = 0; v0 < nvc; v0 += STC_M)
+                tiles.push_back(StcCTile{*tfloats, c0, v0, std::min(STC_M, nvc - v0), am, r0, nr, K, 0});
+            *tfloats += (int64_t)2 * np * kp;
+        }
+    }
+}
+
+fb_status fb_stc_coax_tables(const StcCBlock* blocks, int nblocks, const cd* coax64, float* out, cudaStream_t s) {
+    if (nblocks == 0) return FB_OK;
+    k_stc_coax_tables<<<(unsigned)nblocks, 256, 0, s>>>(blocks, coax64, out);
+    FB_LAUNCH_CHECK();
+    fb_count_launch();
+    return FB_OK;
+}
+
+fb_status fb_stc_coax_run(const StcCTile* tiles, int ntiles, const int32_t* cidx, const float* tab, const cf* U,
+                          cf* V, int S, int p_out, int* err, cudaStream_t s) {
+    if (ntiles == 0) return FB_OK;
+    const int npmax = stc_pad16(2 * std::min(STC_CROWS, p_out));
+    StcCArgs a;
+    a.tiles = tiles;
+    a.cidx = cidx;
+    a.tab = tab;
+    a.U = U;
+    a.V = V;
+    a.err = err;
+    a.wait_limit = fb_tc_wait_limit();
+    a.S = S;
+    a.p_out = p_out;
+    a.stage_floats = 2 * A_PLANE + 2 * npmax * KC;
+    // three stages while two CTAs still fit an SM, else two
+    a.nst = (size_t)STC_CSTAGES * a.stage_floats * sizeof(float) + 1024 <= 110 * 1024 ? STC_CSTAGES : 2;
+    a.inject_stall = fb_tc_inject_stall();
+    const size_t smem = std::max(STC_SMEM_MIN, (size_t)a.nst * a.stage_floats * sizeof(float) + 1024);
+    FB_CHECK(fb_smem_cap((const void*)k_stc_coax, smem));
+    k_stc_coax<<<(unsigned)ntiles, STC_THREADS, smem, s>>>(a);
+    FB_LAUNCH_CHECK();
+    fb_count_launch();
+    return FB_OK;
 }
 
 fb_status fb_stc_run(int pass, const StcTile* tiles, int ntiles, int npmax, const int64_t* toff, const float* tab,

@@ -66,7 +66,7 @@ def test_staged_tensor_rotation_wait_timeout():
     tree = fb.fb_tree_build(mesh, 64)
     A = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 30)
     try:
-        fb.fb_operator_set_forms(A, [4 | 8 | 16 | 32] * 13)
+        fb.fb_operator_set_forms(A, [4 | 8 | 16 | 32 | 1024 | 2048] * 13)   # rotations and coaxial step
         x = torch.tensor(seeded_vector(wl.n, 83), device="cuda")
         y0 = torch.empty_like(x)
         fb.fb_operator_apply(A, x, y0)
