@@ -23,13 +23,13 @@
 //      share a target).
 //
 // The rotations run folded (even / odd in m, see below: half the
-// multipliers).  u is kept per pair in degree-major order (degree n at n^2,
-// folded within the degree) and v in order-major order (the even part of
-// order m >= 0 at moff(m), the odd part at moff(-m), degrees |m|..p_out-1
-// contiguous), so each pass writes contiguous runs and the strided gathers
-// fall on reads only.  One CTA computes a 64 x 64 tile of
-// one GEMM (256 threads, 4 x 4 complex outputs each, K in chunks of 16,
-// double-buffered shared memory).
+// multipliers).  u and v are kept per pair in degree-major order (degree n
+// at n^2, folded within the degree: E_0..E_n, then O_1..O_n), so the
+// rotations read and write contiguous runs; the coaxial pass, which sums
+// over degrees at a fixed order, gathers its inputs and scatters its
+// outputs with a stride of one degree block.  One CTA computes a 64 x 64
+// tile of one GEMM (256 threads, 4 x 4 complex outputs each, K in chunks
+// of 16, three-stage cp.async pipeline).
 #include <algorithm>
 #include <map>
 #include <tuple>
@@ -313,8 +313,9 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_rot(const StgTile* __restri
 }
 
 // ------------------------------------------------------------- pass C ----
-// V[slot][moff(+am) + row] = sum_k C^{am}_{am+row, am+k} E^{am}_{am+k}   (even columns)
-// V[slot][moff(-am) + row] = sum_k C^{am}_{am+row, am+k} O^{am}_{am+k}   (odd columns, am > 0)
+// E^{am}_{n'} (V[slot][n'^2 + am])      = sum_k C^{am}_{n', am+k} E^{am}_{am+k}   (even columns)
+// O^{am}_{n'} (V[slot][n'^2 + n' + am]) = sum_k C^{am}_{n', am+k} O^{am}_{am+k}   (odd columns, am > 0)
+// for n' = am + row (degree-major folded, as u)
 // with E^{am}_n = U[slot][n^2 + am], O^{am}_n = U[slot][n^2 + n + am].
 template <class R>
 __global__ void __launch_bounds__(STHREADS, 2) k_stg_coax(const StgCTile* __restrict__ tiles,
@@ -356,18 +357,20 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_coax(const StgCTile* __rest
     for (int j = 0; j < 4; ++j) {
         const int c = tx + 16 * j;
         if (c >= tl.nvc) continue;
-        cx<R>* v = V + sm.col_off[c] + moff(sm.col_aux[c] ? -am : am, pout) + tl.row0;
+        cx<R>* v = V + sm.col_off[c] + am;
+        const int odd = sm.col_aux[c];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int r = ty * 4 + i;
-            if (r < M) v[r] = acc[i][j];
+            const int n1 = am + tl.row0 + r;
+            if (r < M) v[(int64_t)n1 * n1 + (odd ? n1 : 0)] = acc[i][j];
         }
     }
 }
 
 // ------------------------------------------------------------- pass B ----
-// part 0: Y+_{m'} (m' = 0..n) from E_mu = V[slot][moff(+mu) + n - mu], mu = 0..mmax;
-// part 1: Y-_{m'} (m' = 1..n) from O_mu = V[slot][moff(-mu) + n - mu], mu = 1..mmax;
+// part 0: Y+_{m'} (m' = 0..n) from E_mu = V[slot][n^2 + mu], mu = 0..mmax;
+// part 1: Y-_{m'} (m' = 1..n) from O_mu = V[slot][n^2 + n + mu], mu = 1..mmax;
 // mmax = min(n, p_in - 1).  dst[slot][n^2 + n +- m'] += e^{-+ i m' phi} (Y+ +- Y-)/2.
 template <class R>
 __device__ __forceinline__ void atomic_add_cx(cx<R>* d, const cx<R>& v);
@@ -417,7 +420,7 @@ __global__ void __launch_bounds__(STHREADS, 2) k_stg_back(const StgTile* __restr
     auto xptr = [&](int c, int k) -> const cx<R>* {
         if (c >= tl.ncol || k >= K) return nullptr;
         const int mu = lo + k;
-        return V + col_base + (int64_t)c * S + moff(part ? -mu : mu, pout) + (n - mu);
+        return V + col_base + (int64_t)c * S + (int64_t)n * n + (part ? n : 0) + mu;
     };
     cx<R> acc[4][4];
     stg_mainloop<R, false>(sm, K, aptr, xptr, (const void*)rf, acc);

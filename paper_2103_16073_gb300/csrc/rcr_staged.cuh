@@ -20,16 +20,6 @@ struct StgSlot {
 // start of degree n in the unfolded rotation factors of one direction
 __host__ __device__ __forceinline__ int64_t rot_off(int n) { return (int64_t)n * (2 * n - 1) * (2 * n + 1) / 3; }
 
-// start of order m in the order-major layout of an order-p expansion
-// (orders -(p-1) .. p-1, order m holding degrees |m| .. p-1)
-__host__ __device__ __forceinline__ int moff(int m, int p) {
-    if (m <= 0) {
-        int a = p + m;   // p - |m|
-        return (a - 1) * a / 2;
-    }
-    return (p - 1) * p / 2 + m * p - m * (m - 1) / 2;
-}
-
 // start of degree n in a folded rotation table (blocks (n+1)^2 + n^2)
 __host__ __device__ __forceinline__ int64_t fo(int n) {
     return (int64_t)(n - 1) * n * (2 * n - 1) / 3 + (int64_t)n * n;
@@ -89,7 +79,7 @@ void fb_stc_coax_set(int c0, int ns, int64_t cs_off, int pc, int p_in, int p_out
 // Builds the pre-split coaxial blocks (3xTF32 real form of the complex
 // blocks) from the FP64 coaxial sets.
 fb_status fb_stc_coax_tables(const StcCBlock* blocks, int nblocks, const cd* coax64, float* out, cudaStream_t s);
-// Launches the coaxial tiles: U (degree-major folded) -> V (order-major).
+// Launches the coaxial tiles: U -> V (both degree-major folded).
 fb_status fb_stc_coax_run(const StcCTile* tiles, int ntiles, const int32_t* cidx, const float* tab, const cf* U,
                           cf* V, int S, int p_out, int* err, cudaStream_t s);
 

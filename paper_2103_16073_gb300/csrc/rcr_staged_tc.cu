@@ -8,9 +8,10 @@
 // transposed, so that the short dimension of a degree block is the MMA's N:
 //     D[(slot, re/im)][row] = sum_k  x[slot][k].{re, im}  d[row][k]
 //   A = the slots' vectors: 64 slots per tile as 128 real rows (row 2j the
-//       real parts of slot j, row 2j + 1 the imaginary parts), gathered by
-//       producer warps with plain loads, split into TF32 hi + lo and stored
-//       in the canonical layout (the gather of pass B is strided);
+//       real parts of slot j, row 2j + 1 the imaginary parts), loaded by
+//       producer warps with plain loads (contiguous runs of the
+//       degree-major folded inputs), split into TF32 hi + lo and stored in
+//       the canonical layout;
 //   B = the table block, K-major as stored (row-major [row][k]), pre-split
 //       into hi + lo and laid out canonically per K chunk of 16 at setup, so
 //       that one bulk copy moves a chunk;
@@ -82,7 +83,7 @@ struct StcArgs {
     const float* tab;      // group g: R table at g * 2 tper, B table at g * 2 tper + tper
     int64_t tper;
     const StgSlot* slots;
-    const cf* X;           // R: folded phased inputs X0; B: order-major v
+    const cf* X;           // R: folded phased inputs X0; B: v (degree-major, folded)
     cf* out;               // R: u (degree-major, folded); B: target expansions
     const cf* rph;         // phases e^{i m phi} per direction
     int* err;
@@ -103,10 +104,9 @@ __device__ __forceinline__ void stc_load(const StcArgs& a, int64_t row, int n, i
         if (row >= 0 && k < K) {
             int64_t o;
             if (PASS == 0) {
-                o = row + (int64_t)n * n + (part ? n + 1 : 0) + k;
+                o = row + (int64_t)n * n + (part ? n + 1 : 0) + k;       // X0: s_k / t_{k+1}
             } else {
-                const int mu = part + k;
-                o = row + moff(part ? -mu : mu, a.p_out) + (n - mu);
+                o = row + (int64_t)n * n + (part ? n : 0) + part + k;    // v: E_mu / O_mu, mu = part + k
             }
             x = __ldg(reinterpret_cast<const float2*>(a.X + o));
         }
@@ -364,8 +364,8 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stg_tc(const StcArgs a) {
 //   B[(i, 0)][(k, 0)] = Re C,  B[(i, 0)][(k, 1)] = -Im C,
 //   B[(i, 1)][(k, 0)] = Im C,  B[(i, 1)][(k, 1)] = Re C,
 // so D[v][(i, 0)] = Re(sum u C), D[v][(i, 1)] = Im(sum u C): no zero blocks,
-// and each accumulator lane holds one output vector, written contiguously
-// into the order-major v.
+// and each accumulator lane holds one output vector (degrees n' at a fixed
+// order), scattered into the degree-major folded v.
 struct StcCArgs {
     const StcCTile* tiles;
     const int32_t* cidx;
@@ -544,7 +544,7 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stc_coax(const StcCArgs a) {
         __syncwarp();
     }
 
-    // ---------------- epilogue: v[slot][moff(+-am) + r0 + i] --------------------
+    // ---------------- epilogue: v[slot][n'^2 + (odd ? n' : 0) + am], n' = am + r0 + i
     const bool done = mbar_wait(smem_u32(&done_bar), 0, DRAIN_LIMIT);
     __syncthreads();
     const bool ok = done && s_fail == 0;
@@ -554,7 +554,8 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stc_coax(const StcCArgs a) {
         const int quad = warp & 3, half = warp >> 2;
         const int r = quad * 32 + lane;
         const bool valid = r < tl.nvc;
-        cf* vout = a.V + (valid ? s_row[r] : 0) + moff(s_odd[r] ? -am : am, a.p_out) + tl.r0;
+        cf* vout = a.V + (valid ? s_row[r] : 0) + am;
+        const int odd = s_odd[r];
         for (int g16 = half; g16 < np / 16; g16 += 2) {
             uint32_t v[16];
             tcx::tmem_ld16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(g16 * 16), v);
@@ -562,8 +563,9 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stc_coax(const StcCArgs a) {
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const int i = g16 * 8 + t;
+                const int n1 = am + tl.r0 + i;
                 if (i < tl.nr)
-                    *reinterpret_cast<float2*>(vout + i) =
+                    *reinterpret_cast<float2*>(vout + (int64_t)n1 * n1 + (odd ? n1 : 0)) =
                         make_float2(__uint_as_float(v[2 * t]), __uint_as_float(v[2 * t + 1]));
             }
         }
