@@ -306,8 +306,9 @@ FB_API fb_status fb_operator_status(fb_op* op, void* stream);
  * overwritten; apply the operator again before using its result).  Each
  * pass is launched alone between CUDA events on `stream`, once untimed and
  * three times timed (median).  ms: 4*13 doubles, ms[4l + 0..3] = pre-pass
- * (folded phased inputs), rotation, coaxial, back-rotation of level l (-1:
- * level not staged); form: 13 ints, 1 = passes on CUDA cores, 2 = rotation
+ * (folded phased inputs; -1 where the tensor-core rotation pass folds them
+ * itself), rotation, coaxial, back-rotation of level l (-1: level not
+ * staged); form: 13 ints, 1 = passes on CUDA cores, 2 = rotation
  * passes on the tensor cores, 3 = passes in double-FP32 arithmetic, 5 =
  * rotation and coaxial passes on the tensor cores (0: not staged).  Synchronises the device.
  * Errors: FB_ERR_ARG (NULL argument, dense or composite operator). */

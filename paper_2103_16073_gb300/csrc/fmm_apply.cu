@@ -652,6 +652,7 @@ fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* tc) {
         if (lev < 0 || sb != db) continue;
         tc[lev] = t;
         for (int pass = 0; pass < 4 && st == FB_OK; ++pass) {
+            if (pass == 0 && (t == 2 || t == 5)) continue;   // the tensor-core rotation pass folds its inputs
             auto run = [&]() {
                 return mixed ? fb_stg_run_f(pl.stg, (const float*)op->rotf, op->rotf_per, (const cf*)op->rph32,
                                             op->Prot, op->coax32, (const cf*)op->mp, (cf*)op->loc, (cf*)op->stg_u,

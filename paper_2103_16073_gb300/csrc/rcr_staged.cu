@@ -794,7 +794,7 @@ static fb_status stg_level(const StgLevel& lv, int pass_mask, const R* rf, int64
     FB_CHECK(fb_smem_cap((const void*)k_stg_rot<R>, sm_rc));
     FB_CHECK(fb_smem_cap((const void*)k_stg_coax<R>, sm_c));
     FB_CHECK(fb_smem_cap((const void*)k_stg_back<R, O>, sm_rc));
-    if (pass_mask & 1) {
+    if ((pass_mask & 1) && !lv.tc) {   // the tensor-core rotation pass folds its inputs itself
         const int64_t tot = (int64_t)lv.nslot * lv.p_in * lv.p_in;
         const int pb = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
         k_stg_prep<R, O><<<pb, 256, 0, s>>>(lv.slots, lv.nslot, sr, rph, prot, lv.p_in * lv.p_in, lv.S, V);
@@ -802,7 +802,7 @@ static fb_status stg_level(const StgLevel& lv, int pass_mask, const R* rf, int64
     }
     if (pass_mask & 2) {
         if (lv.tc) {
-            FB_CHECK(stc_pass(lv, 0, tc, V, U, rph, prot, s));
+            FB_CHECK(stc_pass(lv, 0, tc, sr, U, rph, prot, s));
         } else if (lv.nrt) {
             k_stg_rot<R><<<lv.nrt, STHREADS, sm_rc, s>>>(lv.rt, rf, fper, V, U, lv.S);
             fb_count_launch();

@@ -9,9 +9,9 @@
 //     D[(slot, re/im)][row] = sum_k  x[slot][k].{re, im}  d[row][k]
 //   A = the slots' vectors: 64 slots per tile as 128 real rows (row 2j the
 //       real parts of slot j, row 2j + 1 the imaginary parts), loaded by
-//       producer warps with plain loads (contiguous runs of the
-//       degree-major folded inputs), split into TF32 hi + lo and stored in
-//       the canonical layout;
+//       producer warps with plain loads (pass R folds and phases the source
+//       expansions on the fly; pass B reads contiguous runs of v), split
+//       into TF32 hi + lo and stored in the canonical layout;
 //   B = the table block, K-major as stored (row-major [row][k]), pre-split
 //       into hi + lo and laid out canonically per K chunk of 16 at setup, so
 //       that one bulk copy moves a chunk;
@@ -83,7 +83,7 @@ struct StcArgs {
     const float* tab;      // group g: R table at g * 2 tper, B table at g * 2 tper + tper
     int64_t tper;
     const StgSlot* slots;
-    const cf* X;           // R: folded phased inputs X0; B: v (degree-major, folded)
+    const cf* X;           // R: source expansions; B: v (degree-major, folded)
     cf* out;               // R: u (degree-major, folded); B: target expansions
     const cf* rph;         // phases e^{i m phi} per direction
     int* err;
@@ -93,22 +93,36 @@ struct StcArgs {
     int inject_stall;
 };
 
-// 4 consecutive K values (k0 .. k0 + 3) of one slot's vector of degree n
+// 4 consecutive K values (k0 .. k0 + 3) of one slot's vector of degree n.
+// Pass R folds and phases the source expansion on the fly (m = part + k):
+// s_0 = x_0, s_m = x_m e^{i m phi} + x_{-m} e^{-i m phi}, t_m = the
+// difference; pass B reads E_mu / O_mu (mu = part + k) of v.
 template <int PASS>
-__device__ __forceinline__ void stc_load(const StcArgs& a, int64_t row, int n, int part, int K, int k0,
+__device__ __forceinline__ void stc_load(const StcArgs& a, int64_t row, int dir, int n, int part, int K, int k0,
                                          float (&v)[8]) {
+    const cf* ph = a.rph + (int64_t)dir * (2 * a.prot - 1) + (a.prot - 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int k = k0 + i;
         float2 x = make_float2(0.f, 0.f);
         if (row >= 0 && k < K) {
-            int64_t o;
             if (PASS == 0) {
-                o = row + (int64_t)n * n + (part ? n + 1 : 0) + k;       // X0: s_k / t_{k+1}
+                const cf* xs = a.X + row + (int64_t)n * n + n;   // (n, 0)
+                const int m = part + k;
+                if (m == 0) {
+                    x = __ldg(reinterpret_cast<const float2*>(xs));
+                } else {
+                    const float2 xp = __ldg(reinterpret_cast<const float2*>(xs + m));
+                    const float2 xm = __ldg(reinterpret_cast<const float2*>(xs - m));
+                    const float2 pp = __ldg(reinterpret_cast<const float2*>(ph + m));
+                    const float2 pm = __ldg(reinterpret_cast<const float2*>(ph - m));
+                    const float ar = xp.x * pp.x - xp.y * pp.y, ai = xp.x * pp.y + xp.y * pp.x;
+                    const float br = xm.x * pm.x - xm.y * pm.y, bi = xm.x * pm.y + xm.y * pm.x;
+                    x = part ? make_float2(ar - br, ai - bi) : make_float2(ar + br, ai + bi);
+                }
             } else {
-                o = row + (int64_t)n * n + (part ? n : 0) + part + k;    // v: E_mu / O_mu, mu = part + k
+                x = __ldg(reinterpret_cast<const float2*>(a.X + row + (int64_t)n * n + (part ? n : 0) + part + k));
             }
-            x = __ldg(reinterpret_cast<const float2*>(a.X + o));
         }
         v[2 * i] = x.x;
         v[2 * i + 1] = x.y;
@@ -149,7 +163,7 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stg_tc(const StcArgs a) {
     __shared__ __align__(8) uint64_t never_bar;               // test hook: nothing arrives on it
     __shared__ uint32_t tmem_holder;
     __shared__ int64_t s_row[STC_SLOTS];   // slot * S (-1: padding row of zeros)
-    __shared__ int64_t s_dst[STC_SLOTS];   // pass B: target expansion of the slot
+    __shared__ int64_t s_dst[STC_SLOTS];   // pass R: the slot's row of u; pass B: its target expansion
     __shared__ int32_t s_dir[STC_SLOTS];   // pass B: direction (phases)
     __shared__ int s_fail;
     const uint32_t raw = smem_u32(smem_raw);
@@ -162,9 +176,10 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stg_tc(const StcArgs a) {
     if (tid < STC_SLOTS) {
         const bool ok = tid < tl.ns;
         const int sl = tl.s0 + tid;
-        s_row[tid] = ok ? (int64_t)sl * a.S : -1;
-        s_dst[tid] = (PASS == 1 && ok) ? a.slots[sl].dst_off : 0;
-        s_dir[tid] = (PASS == 1 && ok) ? a.slots[sl].dir : 0;
+        // pass R: the source expansion of the slot; pass B: its row of v
+        s_row[tid] = ok ? (PASS == 0 ? a.slots[sl].src_off : (int64_t)sl * a.S) : -1;
+        s_dst[tid] = ok ? (PASS == 0 ? (int64_t)sl * a.S : a.slots[sl].dst_off) : 0;
+        s_dir[tid] = ok ? a.slots[sl].dir : 0;
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_holder)),
@@ -192,10 +207,11 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stg_tc(const StcArgs a) {
         // ---------------- A producers ---------------------------------------
         const int j = tid >> 2, q = tid & 3;
         const int64_t row = s_row[j];
+        const int dir = s_dir[j];
         int n = tl.n0, kc = 0, N, K;
         stc_dims(PASS, n, part, a.p_in, N, K);
         float cur[8], nxt[8];
-        stc_load<PASS>(a, row, n, part, K, 4 * q, cur);
+        stc_load<PASS>(a, row, dir, n, part, K, 4 * q, cur);
         for (int c = 0;; ++c) {
             // the next chunk's loads go out before this one is stored
             int n2 = n, kc2 = kc + 1, K2 = K;
@@ -205,7 +221,7 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stg_tc(const StcArgs a) {
                 if (n2 < tl.n1) stc_dims(PASS, n2, part, a.p_in, N, K2);
             }
             const bool more = n2 < tl.n1;
-            if (more) stc_load<PASS>(a, row, n2, part, K2, kc2 * KC + 4 * q, nxt);
+            if (more) stc_load<PASS>(a, row, dir, n2, part, K2, kc2 * KC + 4 * q, nxt);
             const int s = c % STC_STAGES, u = c / STC_STAGES;
             if (u > 0 && !mbar_wait(smem_u32(&empty_bar[s]), (u - 1) & 1, a.wait_limit)) {
                 atomicExch(&s_fail, 1);
@@ -330,7 +346,7 @@ __global__ void __launch_bounds__(STC_THREADS, 2) k_stg_tc(const StcArgs a) {
                     const int i = g16 * 16 + 2 * qq + cpt;   // row of the degree block
                     if (!valid || i >= N) continue;
                     if (PASS == 0) {
-                        cf* u = a.out + s_row[j] + (int64_t)n * n + (part ? n : 0) + part + i;
+                        cf* u = a.out + s_dst[j] + (int64_t)n * n + (part ? n : 0) + part + i;
                         *reinterpret_cast<float2*>(u) = make_float2(re, im);
                     } else {
                         const int mp = part + i;

@@ -274,6 +274,15 @@ def test_staged_double_float_large_orders():
         assert rel(y_d, ref) < 1e-5
         passes = fb.fb_operator_staged_pass_times(op)
         assert passes[2]["form"] == "df" and all(passes[2][k] > 0 for k in ("prep", "rot", "coax", "back"))
+        A32 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 6.0, 12)
+        try:
+            fb.fb_operator_set_forms(A32, STAGED_TC)
+            apply(A32, xd)
+            p32 = fb.fb_operator_staged_pass_times(A32)
+            assert p32[2]["form"] == "tensor_rot" and p32[2]["prep"] < 0    # no separate pre-pass
+            assert all(p32[2][k] > 0 for k in ("rot", "coax", "back"))
+        finally:
+            fb.fb_operator_destroy(A32)
     finally:
         fb.fb_operator_destroy(op)
         fb.fb_tree_destroy(tree)
