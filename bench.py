@@ -209,8 +209,9 @@ def build_problem(fb, W, torch, wl, rank, forms="", forms_inner="", forms_fp64="
         tune["inner_fixed_forms"] = forms_inner
     else:
         tune["inner"] = fb.fb_operator_autotune(Alow, 1)
-    fb.fb_operator_use_graphs(Alow, True)
     pclow = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
+    fb.fb_operator_set_near_bf16(Alow, True)   # low-accuracy operator: 16-bit near-field entries
+    fb.fb_operator_use_graphs(Alow, True)
     inner = fb.fb_precond_create_inner(A32, Alow, pclow, INNER_ITERS)
     fb.fb_precond_use_graphs(inner, True)
     g = torch.empty(wl.n, dtype=torch.complex128, device="cuda")
@@ -495,6 +496,8 @@ def run_matvecs(args):
         fb.fb_operator_set_forms(op, [int(v) for v in args.forms.split(",")])
     else:
         tune = fb.fb_operator_autotune(op, 1)
+    if args.inner_operator:
+        fb.fb_operator_set_near_bf16(op, True)   # as the solve's inner operator
     stream = torch.cuda.current_stream()
     t, ph = matvec_rate(fb, torch, stream, op, wl.n, args.matvec_only)
     passes = fb.fb_operator_staged_pass_times(op)

@@ -300,6 +300,16 @@ FB_API fb_status fb_operator_apply_noalloc(fb_op* op, const double* x, double* y
  * Errors: FB_ERR_ARG (NULL operator, limit < 1). */
 FB_API fb_status fb_operator_status(fb_op* op, void* stream);
 
+/* Near-field entries (Sec. 3.3, the singular and near-singular part of a
+ * mixed FMM operator) stored as BF16 pairs instead of complex FP32: 8-bit
+ * significand, relative rounding of 2^-9 per entry, half the bytes the
+ * matvec's near-field pass reads (an HBM-bound pass).  Meant for the
+ * low-accuracy operator of an inner-outer preconditioner (Sec. 4), whose own
+ * truncation error is far larger; enable = 0 returns to the FP32 entries
+ * (both copies are kept).  Synchronises `stream` when it builds the copy.
+ * Errors: FB_ERR_ARG (NULL, dense, FP64 or composite operator). */
+FB_API fb_status fb_operator_set_near_bf16(fb_op* op, int enable, void* stream);
+
 /* Profiling: device time of each pass of the staged RCR M2L (Sec. 3.3) of
  * every staged level of an FMM operator, one right-hand side, on the
  * operator's own expansion and staging buffers (their contents are

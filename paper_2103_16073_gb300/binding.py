@@ -756,6 +756,16 @@ lib.fb_test_stall_device_waits.restype = C.c_int
 lib.fb_test_stall_device_waits.argtypes = [C.c_int]
 
 
+lib.fb_operator_set_near_bf16.restype = C.c_int
+lib.fb_operator_set_near_bf16.argtypes = [C.c_void_p, C.c_int, C.c_void_p]
+
+
+def fb_operator_set_near_bf16(op, enable=True, stream=None):
+    """Near-field entries of a mixed operator as BF16 pairs (for low-accuracy
+    inner operators) or back to FP32."""
+    _check(lib.fb_operator_set_near_bf16(op, 1 if enable else 0, _stream(stream)))
+
+
 lib.fb_operator_staged_pass_times.restype = C.c_int
 lib.fb_operator_staged_pass_times.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
 

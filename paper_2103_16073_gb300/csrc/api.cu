@@ -519,6 +519,12 @@ fb_status fb_operator_status(fb_op* op, void* stream) {
     return fb_op_wait_status(op);
 }
 
+fb_status fb_operator_set_near_bf16(fb_op* op, int enable, void* stream) {
+    if (!op) return fb_fail(FB_ERR_ARG, "NULL operator");
+    if (fb_is_composite(op)) return fb_fail(FB_ERR_ARG, "set the constituent operators instead");
+    return fb_near_bf16(op, enable, as_stream(stream));
+}
+
 fb_status fb_operator_staged_pass_times(fb_op* op, void* stream, double* ms, int* tc) {
     if (!op || !ms || !tc) return fb_fail(FB_ERR_ARG, "NULL argument");
     if (fb_is_composite(op) || op->prec == FB_PREC_FP64_DENSE)

@@ -66,6 +66,7 @@ void setup_job(const fb_batch_job& jb, const fb_batch_opts& o, cudaStream_t s, J
             FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_MIXED_FMM, o.inner_d0, o.inner_pmin, s,
                                         &js.Alow));
             FB_CHECK(fb_precond_create(js.Alow, FB_PC_BLOCK_JACOBI, s, &js.pclow));
+            FB_CHECK(fb_operator_set_near_bf16(js.Alow, 1, s));   // low-accuracy operator: 16-bit near field
             FB_CHECK(fb_precond_create_inner(js.A32, js.Alow, js.pclow, o.inner_iters, s, &js.inner));
             FB_CHECK(fb_operator_use_graphs(js.Alow, 1));
             FB_CHECK(fb_precond_use_graphs(js.inner, 1));

@@ -315,6 +315,7 @@ struct fb_op;
 fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* form);
 fb_status fb_stg_df_tables(fb_op* op, cudaStream_t s);
 fb_status fb_rcr_df_factors(fb_op* op, int P);
+fb_status fb_near_bf16(fb_op* op, int enable, cudaStream_t s);
 fb_status fb_stg_tables(fb_op* op, const double* rotd64, cudaStream_t s);
 
 // A group of box pairs sharing one composed translation matrix (job) on the
@@ -391,6 +392,8 @@ struct fb_op {
     int64_t stc_per = 0;                     // floats per group and table
     int stc_P = 0;
     int* stc_err = nullptr;                  // error flag of the tensor-core staged passes
+    uint32_t* nf16 = nullptr;                // near-field entries as BF16 pairs (re low, im high half)
+    int near16 = 0;                          // 1: the matvec reads nf16 instead of nf32
     df* rotf_df = nullptr;                   // FP64 operators: folded tables and coaxial sets in
     cx<df>* coax_df = nullptr;               // double-FP32 for the staged levels that use it
     df* rotd_df = nullptr;                   // ... and the real factors of degrees < rotd_df_P

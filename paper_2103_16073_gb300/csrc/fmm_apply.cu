@@ -124,11 +124,20 @@ __global__ void k_p2m(int P, const int32_t* __restrict__ leaf_start, const int32
 // for up to NB right-hand sides per CTA (blockIdx.y selects the chunk): each
 // near-field and L2P entry is read once and applied to every right-hand side
 // of the chunk.  x, y advance by xstride per rhs, loc by lstride.
-template <class R, int NB>
+// A near-field entry as stored: complex FP32 / FP64, or a BF16 pair (real
+// part in the low, imaginary part in the high 16 bits; BF16 is the upper
+// half of an FP32 word).
+__device__ __forceinline__ cf nf_entry(const cf& a) { return a; }
+__device__ __forceinline__ cd nf_entry(const cd& a) { return a; }
+__device__ __forceinline__ cf nf_entry(uint32_t a) {
+    return mk(__uint_as_float(a << 16), __uint_as_float(a & 0xFFFF0000u));
+}
+
+template <class R, int NB, class AS = cx<R>>
 __global__ void k_near_l2p(int P, const int32_t* __restrict__ leaf_start, const int32_t* __restrict__ perm,
                            const int32_t* __restrict__ ucnt, const int32_t* __restrict__ ulist,
                            const int64_t* __restrict__ nf_off, const int32_t* __restrict__ nf_ncol,
-                           const cx<R>* __restrict__ A, const cx<R>* __restrict__ V,
+                           const AS* __restrict__ A, const cx<R>* __restrict__ V,
                            const cx<R>* __restrict__ loc, const cd* __restrict__ x, cd* __restrict__ y,
                            int nrhs, int64_t xstride, int64_t lstride) {
     extern __shared__ unsigned char smem_raw[];
@@ -157,14 +166,16 @@ __global__ void k_near_l2p(int P, const int32_t* __restrict__ leaf_start, const 
     __syncthreads();
     int rb = leaf_start[t], nrow = leaf_start[t + 1] - rb;
     int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const cx<R>* At = A + nf_off[t];
+    const AS* At = A + nf_off[t];
     for (int r = warp; r < nrow; r += nw) {
         cx<R> acc[NB];
 #pragma unroll
         for (int j = 0; j < NB; ++j) acc[j] = mk<R>(0, 0);
-        const cx<R>* row = At + (int64_t)r * K;
+        const AS* row = At + (int64_t)r * K;
+        // unrolled: several independent row loads in flight per lane
+#pragma unroll 4
         for (int q = lane; q < K; q += 32) {
-            cx<R> a = row[q];
+            const cx<R> a = nf_entry(row[q]);
 #pragma unroll
             for (int j = 0; j < NB; ++j)
                 if (j < nr) cmac(acc[j], a, xs[j * K + q]);
@@ -895,21 +906,75 @@ static fb_status fmm_apply_t(fb_op* op, const cd* x, cd* y, cudaStream_t s, cons
     const cx<R>* locL = loc + op->lev_off[L];
     if (nrhs == 1) {
         size_t smem = sizeof(cx<R>) * (maxK + PL);
-        FB_CHECK(fb_smem_cap((const void*)k_near_l2p<R, 1>, smem));
-        k_near_l2p<R, 1><<<nleaf, 256, smem, s>>>(PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off,
-                                                  op->nf_ncol, A, V, locL, x, y, 1, n, cnt);
+        bool done16 = false;
+        if constexpr (sizeof(R) == 4) {
+            if (op->near16 && op->nf16) {   // 16-bit near-field entries
+                FB_CHECK(fb_smem_cap((const void*)k_near_l2p<R, 1, uint32_t>, smem));
+                k_near_l2p<R, 1, uint32_t><<<nleaf, 256, smem, s>>>(PL, t->leaf_start, t->perm, t->ucnt,
+                                                                    t->ulist, op->nf_off, op->nf_ncol, op->nf16, V,
+                                                                    locL, x, y, 1, n, cnt);
+                done16 = true;
+            }
+        }
+        if (!done16) {
+            FB_CHECK(fb_smem_cap((const void*)k_near_l2p<R, 1>, smem));
+            k_near_l2p<R, 1><<<nleaf, 256, smem, s>>>(PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off,
+                                                      op->nf_ncol, A, V, locL, x, y, 1, n, cnt);
+        }
     } else {
         constexpr int NB = 4;
         int nr = std::min(nrhs, NB);
         size_t smem = sizeof(cx<R>) * (size_t)nr * (maxK + PL);
         if (smem > 227 * 1024) return fb_fail(FB_ERR_ARG, "near-field tile exceeds shared memory");
-        FB_CHECK(fb_smem_cap((const void*)k_near_l2p<R, NB>, smem));
-        k_near_l2p<R, NB><<<dim3(nleaf, div_up(nrhs, NB)), 256, smem, s>>>(
-            PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off, op->nf_ncol, A, V, locL, x, y, nrhs, n, cnt);
+        bool done16 = false;
+        if constexpr (sizeof(R) == 4) {
+            if (op->near16 && op->nf16) {
+                FB_CHECK(fb_smem_cap((const void*)k_near_l2p<R, NB, uint32_t>, smem));
+                k_near_l2p<R, NB, uint32_t><<<dim3(nleaf, div_up(nrhs, NB)), 256, smem, s>>>(
+                    PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off, op->nf_ncol, op->nf16, V, locL, x,
+                    y, nrhs, n, cnt);
+                done16 = true;
+            }
+        }
+        if (!done16) {
+            FB_CHECK(fb_smem_cap((const void*)k_near_l2p<R, NB>, smem));
+            k_near_l2p<R, NB><<<dim3(nleaf, div_up(nrhs, NB)), 256, smem, s>>>(
+                PL, t->leaf_start, t->perm, t->ucnt, t->ulist, op->nf_off, op->nf_ncol, A, V, locL, x, y, nrhs, n,
+                cnt);
+        }
     }
     FB_LAUNCH_CHECK();
     fb_count_launch();
     mark(6);
+    return FB_OK;
+}
+
+// FP32 -> BF16 with round to nearest even (finite values)
+__device__ __forceinline__ uint32_t bf16_bits(float f) {
+    const uint32_t u = __float_as_uint(f);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+static __global__ void k_cf_to_bf16(const cf* __restrict__ in, int64_t n, uint32_t* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = bf16_bits(in[i].re) | (bf16_bits(in[i].im) << 16);
+}
+
+// Near-field entries of a mixed operator in BF16 (8-bit significand,
+// relative rounding 2^-9 per entry) for low-accuracy operators, whose
+// matvec then reads half the near-field bytes; enable = 0 returns to FP32.
+fb_status fb_near_bf16(fb_op* op, int enable, cudaStream_t s) {
+    if (op->prec != FB_PREC_MIXED_FMM || !op->nf32)
+        return fb_fail(FB_ERR_ARG, "BF16 near field applies to mixed FMM operators");
+    if (enable && !op->nf16) {
+        FB_CHECK(dalloc(&op->nf16, (size_t)op->nf_count));
+        k_cf_to_bf16<<<(unsigned)std::min<int64_t>(div_up(op->nf_count, 256), 8192), 256, 0, s>>>(
+            op->nf32, op->nf_count, op->nf16);
+        FB_LAUNCH_CHECK();
+        FB_CUDA(cudaStreamSynchronize(s));
+        fb_count_launch();
+    }
+    op->near16 = enable ? 1 : 0;
+    op->buf_gen++;   // captured graphs read the other entries
     return FB_OK;
 }
 
@@ -999,6 +1064,7 @@ void fb_fmm_destroy(fb_op* op) {
     dfree(op->nf_ncol);
     dfree(op->nf64);
     dfree(op->nf32);
+    dfree(op->nf16);
     dfree(op->self64);
     dfree(op->w64);
     dfree(op->w32);

@@ -206,6 +206,49 @@ def test_inner_outer_preconditioner(setup):
         fb.fb_tree_destroy(tree)
 
 
+def test_inner_operator_bf16_near_field(setup):
+    """The low-accuracy inner operator with its near-field entries in BF16:
+    its matvec moves from the FP32-entry one by the BF16 rounding only (well
+    under 1e-2, and not zero: the 16-bit path runs), the inner-outer solve
+    meets the FP64 true-residual tolerance in the same outer iterations
+    (+-1), and FP64 operators refuse the setting."""
+    wl, mesh, op = setup
+    A = op(fb.FB_PREC_MIXED_FMM)
+    A64 = op(fb.FB_PREC_FP64_FMM)
+    tree = fb.fb_tree_build(mesh, 64)
+    Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 0.5, 2)
+    bjl = fb.fb_precond_create(Alow, fb.FB_PC_BLOCK_JACOBI)
+    inner = fb.fb_precond_create_inner(A, Alow, bjl, 6)
+    try:
+        x = torch.tensor(seeded_vector(wl.n, 78), device="cuda")
+        y32, y16 = torch.empty_like(x), torch.empty_like(x)
+        fb.fb_operator_apply(Alow, x, y32)
+        b = torch.tensor(seeded_vector(wl.n, 79), device="cuda")
+        xs = torch.zeros_like(b)
+        it32 = fb.fb_fgmres_solve(A, b, xs, pc=inner, tol=1e-6, restart=30, true_op=A64)["iters"]
+        fb.fb_operator_set_near_bf16(Alow, True)
+        fb.fb_operator_apply(Alow, x, y16)
+        torch.cuda.synchronize()
+        d = rel(y16.cpu().numpy(), y32.cpu().numpy())
+        assert 1e-6 < d < 1e-2
+        xs = torch.zeros_like(b)
+        info = fb.fb_fgmres_solve(A, b, xs, pc=inner, tol=1e-6, restart=30, true_op=A64)
+        assert info["status"] == 0 and info["true_relres"] <= 1e-6
+        assert abs(info["iters"] - it32) <= 1
+        fb.fb_operator_set_near_bf16(Alow, False)
+        y = torch.empty_like(x)
+        fb.fb_operator_apply(Alow, x, y)
+        torch.cuda.synchronize()
+        assert rel(y.cpu().numpy(), y32.cpu().numpy()) < 1e-6   # FP32 atomics: summation order only
+        with pytest.raises(fb.FBError):
+            fb.fb_operator_set_near_bf16(A64, True)
+    finally:
+        fb.fb_precond_destroy(inner)
+        fb.fb_precond_destroy(bjl)
+        fb.fb_operator_destroy(Alow)
+        fb.fb_tree_destroy(tree)
+
+
 def test_inner_outer_several_rhs_and_graphs(setup):
     """The inner-outer preconditioner on several right-hand sides runs one
     lockstep inner GMRES (one multi-RHS matvec per inner step): in a batched
