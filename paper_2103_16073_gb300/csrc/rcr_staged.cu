@@ -624,14 +624,34 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
                 fb_stc_coax_set(c0, ns, sv.first, pc, p_in, p_out, ctc, cblocks, &ctab_floats);
                 continue;
             }
-            for (int am = 0; am < q; ++am) {
-                const int nvc = am == 0 ? ns : 2 * ns;
-                const int M = p_out - am, K = p_in - am;
-                const int64_t a_off = sv.first + ((int64_t)am * pc + am) * pc + am;
-                for (int r0 = 0; r0 < M; r0 += SBM)
-                    for (int v0 = 0; v0 < nvc; v0 += SBN)
-                        ct.push_back(StgCTile{a_off, c0, v0, std::min(SBN, nvc - v0), am, r0, pc, M, K});
+            if (pl.csize != sizeof(cf)) {
+                // FP64 / double-FP32 passes are bound by arithmetic: orders
+                // outermost, full column blocks, each coefficient block
+                // applied to every column block in turn
+                for (int am = 0; am < q; ++am) {
+                    const int nvc = am == 0 ? ns : 2 * ns;
+                    const int M = p_out - am, K = p_in - am;
+                    const int64_t a_off = sv.first + ((int64_t)am * pc + am) * pc + am;
+                    for (int r0 = 0; r0 < M; r0 += SBM)
+                        for (int v0 = 0; v0 < nvc; v0 += SBN)
+                            ct.push_back(StgCTile{a_off, c0, v0, std::min(SBN, nvc - v0), am, r0, pc, M, K});
+                }
+                continue;
             }
+            // FP32: slot blocks outermost, orders next: the tiles of
+            // consecutive orders of one slot block run together, so each
+            // 32-byte sector of u they gather from and of v they scatter to
+            // (four orders of one degree) is read and written while in L2
+            for (int sb = 0; sb < ns; sb += SBN / 2)
+                for (int am = 0; am < q; ++am) {
+                    const int M = p_out - am, K = p_in - am;
+                    const int64_t a_off = sv.first + ((int64_t)am * pc + am) * pc + am;
+                    // virtual columns: order 0 one per slot, else (slot, even / odd part)
+                    const int v0 = am == 0 ? sb : 2 * sb;
+                    const int nvc = am == 0 ? std::min(SBN / 2, ns - sb) : std::min(SBN, 2 * (ns - sb));
+                    for (int r0 = 0; r0 < M; r0 += SBM)
+                        ct.push_back(StgCTile{a_off, c0, v0, nvc, am, r0, pc, M, K});
+                }
         }
         lv.nslot = (int)slots.size();
         lv.nrt = (int)rt.size();
@@ -654,9 +674,6 @@ fb_status fb_stg_build(const RcrPlan& pl, const std::vector<int>& theta_slot, in
         };
         std::stable_sort(rtc.begin(), rtc.end(), heavier(0));
         std::stable_sort(btc.begin(), btc.end(), heavier(1));
-        std::stable_sort(ctc.begin(), ctc.end(), [](const StcCTile& x, const StcCTile& y) {
-            return (int64_t)x.K * x.nr > (int64_t)y.K * y.nr;
-        });
         lv.nrtc = (int)rtc.size();
         lv.nbtc = (int)btc.size();
         lv.nctc = (int)ctc.size();

@@ -699,18 +699,29 @@ void fb_stc_group_tiles(int g, int g0, int g1, int nmax, int pass, int p_in, std
 void fb_stc_coax_set(int c0, int ns, int64_t cs_off, int pc, int p_in, int p_out, std::vector<StcCTile>& tiles,
                      std::vector<StcCBlock>& blocks, int64_t* tfloats) {
     const int q = std::min(p_in, p_out);
+    // one pre-split block per (order, row block)
+    std::vector<std::vector<int64_t>> toff(q);
     for (int am = 0; am < q; ++am) {
         const int M = p_out - am, K = p_in - am;
-        const int nvc = am == 0 ? ns : 2 * ns;
         for (int r0 = 0; r0 < M; r0 += STC_CROWS) {
             const int nr = std::min(STC_CROWS, M - r0);
             const int np = stc_pad16(2 * nr), kp = ((2 * K + KC - 1) / KC) * KC;
             blocks.push_back(StcCBlock{cs_off, *tfloats, pc, am, r0, nr, K, 0});
-            for (int v0 = 0; v0 < nvc; v0 += STC_M)
-                tiles.push_back(StcCTile{*tfloats, c0, v0, std::min(STC_M, nvc - v0), am, r0, nr, K, 0});
+            toff[am].push_back(*tfloats);
             *tfloats += (int64_t)2 * np * kp;
         }
     }
+    // slot blocks outermost, orders next (sectors of u and v shared by
+    // consecutive orders are used while in L2)
+    for (int sb = 0; sb < ns; sb += STC_M / 2)
+        for (int am = 0; am < q; ++am) {
+            const int M = p_out - am, K = p_in - am;
+            const int v0 = am == 0 ? sb : 2 * sb;
+            const int nvc = am == 0 ? std::min(STC_M / 2, ns - sb) : std::min(STC_M, 2 * (ns - sb));
+            int b = 0;
+            for (int r0 = 0; r0 < M; r0 += STC_CROWS, ++b)
+                tiles.push_back(StcCTile{toff[am][b], c0, v0, nvc, am, r0, std::min(STC_CROWS, M - r0), K, 0});
+        }
 }
 
 fb_status fb_stc_coax_tables(const StcCBlock* blocks, int nblocks, const cd* coax64, float* out, cudaStream_t s) {
