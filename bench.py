@@ -164,8 +164,9 @@ def bench_config(name, wl, ws):
             "solver": "FGMRES(40), FP64 Arnoldi (CGS2), tol 1e-4 on the FP64 FMM true residual",
             "step": "one solve A x = b (Eq. dbem4), b = L gamma of a monopole",
             "precond": (f"inner-outer (Sec. 4): {INNER_ITERS} GMRES steps on a low-accuracy mixed FMM "
-                        f"(d0={INNER_D0:g}, p_min={INNER_PMIN}) with block Jacobi"),
-            "operator": "mixed: FP32 near field, P2M/L2P and translations",
+                        f"(d0={INNER_D0:g}, p_min={INNER_PMIN}, BF16 near-field entries) with block Jacobi"),
+            "operator": "mixed: FP32 near field, P2M/L2P and translations (3xTF32 tensor-core and FP32 forms, "
+                        "autotuned per level); FP64 judge: FP64 or double-FP32 translations, autotuned",
             "l2": "inputs larger than L2 (near-field entries and translation data of GB size)",
             "parallelism": f"replicas x{ws} (one (f, source) solve per GPU)"}
 
@@ -398,9 +399,14 @@ def roofline(fb, P, iters, true_mv, pk, fp32_peak, fp64_peak):
         return None, out
     dom = max(out, key=lambda k: out[k]["est_ms_per_step"])
     d = out[dom]
-    work = ("algorithmic bytes (16 B per complex coefficient read and written, 32 B in FP64) per box pair"
-            if d["unit"] == "TB/s" else
-            "algorithmic flops per box pair: rotations 8 x 2 sum_{n<p}(2n+1)^2, coaxial 8 x sum_m (p-|m|)^2")
+    if d["unit"] == "TB/s":
+        work = "algorithmic bytes per box pair: 16 B per complex coefficient read and written (32 B in FP64)"
+    elif dom in ("k_stg_tc", "k_stg_rot+back<float>"):
+        work = "algorithmic flops per box pair: rotations 8 x 2 sum_{n<p}(2n+1)^2 (unfolded count)"
+    elif dom in ("k_stc_coax", "k_stg_coax<float>"):
+        work = "algorithmic flops per box pair: coaxial step 8 x sum_m (p-|m|)^2"
+    else:
+        work = "algorithmic flops per box pair: rotations 8 x 2 sum_{n<p}(2n+1)^2 + coaxial 8 x sum_m (p-|m|)^2"
     rf = {"kernel": dom, "bound": d["bound"], "achieved": d["achieved"], "peak": d["peak"], "unit": d["unit"],
           "frac": d["frac"], "traffic": traffic_for(dom), "peak_kind": d["peak_kind"], "what": d["what"],
           "est_ms_per_step": d["est_ms_per_step"],
