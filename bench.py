@@ -181,8 +181,8 @@ def build_problem(fb, W, torch, wl, rank, forms="", forms_inner="", forms_fp64="
     mesh = fb.fb_mesh_create(wl.verts, wl.tris)
     fb.fb_mesh_set_admittance(mesh, wl.beta)
     tree = fb.fb_tree_build(mesh, 64)
-    A32 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, D0, PMIN)
     A64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, D0, PMIN)
+    A32 = fb.fb_operator_create_like(A64, fb.FB_PREC_MIXED_FMM, D0, PMIN)   # near-field entries copied
     L64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_L, fb.FB_PREC_FP64_FMM, D0, PMIN)
     pc32 = fb.fb_precond_create(A32, fb.FB_PC_BLOCK_JACOBI)
     pc64 = fb.fb_precond_create(A64, fb.FB_PC_BLOCK_JACOBI)
@@ -204,7 +204,7 @@ def build_problem(fb, W, torch, wl, rank, forms="", forms_inner="", forms_fp64="
         a64_forms = [tune["fp64"][l]["choice"] if l in tune["fp64"] else 0 for l in range(13)]
     for op in (A32, A64):
         fb.fb_operator_use_graphs(op, True)
-    Alow = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, INNER_D0, INNER_PMIN)
+    Alow = fb.fb_operator_create_like(A64, fb.FB_PREC_MIXED_FMM, INNER_D0, INNER_PMIN)
     if forms_inner:
         fb.fb_operator_set_forms(Alow, [int(v) for v in forms_inner.split(",")])
         tune["inner_fixed_forms"] = forms_inner

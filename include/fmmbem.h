@@ -193,6 +193,17 @@ FB_API void fb_tree_destroy(fb_tree* tree);
 FB_API fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k, int kind,
                              int precision, double d0, int pmin, void* stream, fb_op** out);
 
+/* An FMM operator of the donor's mesh, tree, wavenumber and kind, at another
+ * precision or order rule (d0, p_min): the near-field entries (Sec. 3.3),
+ * which depend on neither, are copied from the donor when it is an FP64 FMM
+ * operator (which keeps its FP64 entries) instead of being integrated
+ * again; otherwise they are computed as by fb_operator_create.  Meant for
+ * the FP64 judge, the mixed operator and the low-accuracy inner operator of
+ * one solve.  Errors: FB_ERR_ARG (NULL, dense or composite donor, dense
+ * precision). */
+FB_API fb_status fb_operator_create_like(const fb_op* donor, int precision, double d0, int pmin, void* stream,
+                                         fb_op** out);
+
 /* y = Op x.  x, y: N interleaved complex doubles in `memspace`; they must not
  * overlap.  Device memspace: enqueued on `stream`, no sync. */
 FB_API fb_status fb_operator_apply(fb_op* op, const double* x, double* y, int memspace, void* stream);

@@ -214,6 +214,19 @@ def fb_tree_destroy(tree):
     lib.fb_tree_destroy(tree)
 
 
+lib.fb_operator_create_like.restype = C.c_int
+lib.fb_operator_create_like.argtypes = [C.c_void_p, C.c_int, C.c_double, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
+
+
+def fb_operator_create_like(donor, precision, d0=6.0, pmin=12, stream=None):
+    """An FMM operator of the donor's mesh, tree, k and kind at another
+    precision / order rule; the near-field entries are copied from an FP64
+    FMM donor instead of being integrated again."""
+    out = C.c_void_p()
+    _check(lib.fb_operator_create_like(donor, int(precision), float(d0), int(pmin), _stream(stream), C.byref(out)))
+    return out
+
+
 def fb_operator_create(mesh, tree, k, kind, precision, d0=6.0, pmin=12, stream=None):
     out = C.c_void_p()
     _check(lib.fb_operator_create(mesh, tree, float(k), int(kind), int(precision), float(d0), int(pmin),

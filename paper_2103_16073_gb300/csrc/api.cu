@@ -208,7 +208,7 @@ void fb_tree_destroy(fb_tree* t) { fb_tree_free(t); }
 }  // extern "C"
 
 fb_status fb_operator_create_impl(const fb_mesh* mesh, const fb_tree* tree, double k, int kind, int precision,
-                                  double d0, int pmin, cudaStream_t s, fb_op** out) {
+                                  double d0, int pmin, cudaStream_t s, fb_op** out, const fb_op* donor) {
     if (!mesh || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
     *out = nullptr;
     if (!(k > 0.0)) return fb_fail(FB_ERR_ARG, "k must be > 0");
@@ -230,6 +230,7 @@ fb_status fb_operator_create_impl(const fb_mesh* mesh, const fb_tree* tree, doub
     op->d0 = d0;
     op->pmin = pmin;
     op->n = mesh->n;
+    op->near_donor = donor;
     fb_status st = kind == FB_OP_IBEM                  ? fb_ibem_create(op, s)
                    : kind == FB_OP_DBEM5             ? fb_dbem5_create(op, s)
                    : precision == FB_PREC_FP64_DENSE ? fb_dense_create(op, s)
@@ -238,6 +239,7 @@ fb_status fb_operator_create_impl(const fb_mesh* mesh, const fb_tree* tree, doub
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = fb_fail(FB_ERR_CUDA, std::string("operator setup: ") + cudaGetErrorString(e));
     }
+    op->near_donor = nullptr;
     if (st != FB_OK) {
         fb_operator_destroy(op);
         return st;
@@ -251,6 +253,17 @@ extern "C" {
 fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, double k, int kind, int precision,
                              double d0, int pmin, void* stream, fb_op** out) {
     return fb_operator_create_impl(mesh, tree, k, kind, precision, d0, pmin, as_stream(stream), out);
+}
+
+fb_status fb_operator_create_like(const fb_op* donor, int precision, double d0, int pmin, void* stream,
+                                  fb_op** out) {
+    if (!donor || !out) return fb_fail(FB_ERR_ARG, "NULL argument");
+    if (fb_is_composite(donor) || donor->prec == FB_PREC_FP64_DENSE)
+        return fb_fail(FB_ERR_ARG, "the donor must be an FMM operator");
+    if (precision != FB_PREC_FP64_FMM && precision != FB_PREC_MIXED_FMM)
+        return fb_fail(FB_ERR_ARG, "FMM precisions only");
+    return fb_operator_create_impl(donor->mesh, donor->tree, donor->k, donor->kind, precision, d0, pmin,
+                                   as_stream(stream), out, donor);
 }
 
 fb_status fb_mesh_set_admittance_plus(fb_mesh* m, const double* beta, int memspace, void* stream) {

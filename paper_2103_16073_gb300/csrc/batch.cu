@@ -55,16 +55,23 @@ void setup_job(const fb_batch_job& jb, const fb_batch_opts& o, cudaStream_t s, J
     cudaSetDevice(dev);   // the current device is per host thread
     double t0 = now_ms();
     auto run = [&]() -> fb_status {
-        FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_MIXED_FMM, o.d0, o.pmin, s, &js.A32));
-        FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_L, FB_PREC_FP64_FMM, o.d0, o.pmin, s, &js.L64));
-        if (o.fp64_judge)
+        // the FP64 judge first: the mixed operators copy its near-field entries
+        if (o.fp64_judge) {
             FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_FP64_FMM, o.d0, o.pmin, s, &js.A64));
+            FB_CHECK(fb_operator_create_like(js.A64, FB_PREC_MIXED_FMM, o.d0, o.pmin, s, &js.A32));
+        } else {
+            FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_MIXED_FMM, o.d0, o.pmin, s, &js.A32));
+        }
+        FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_L, FB_PREC_FP64_FMM, o.d0, o.pmin, s, &js.L64));
         FB_CHECK(fb_precond_create(js.A32, FB_PC_BLOCK_JACOBI, s, &js.pc));
         const int nrhs = std::max(1, std::min(jb.nsrc, o.max_rhs));
         if (o.autotune) FB_CHECK(fb_operator_autotune(js.A32, nrhs, s, nullptr, nullptr));
         if (o.inner_iters > 0) {
-            FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_MIXED_FMM, o.inner_d0, o.inner_pmin, s,
-                                        &js.Alow));
+            if (js.A64)
+                FB_CHECK(fb_operator_create_like(js.A64, FB_PREC_MIXED_FMM, o.inner_d0, o.inner_pmin, s, &js.Alow));
+            else
+                FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_MIXED_FMM, o.inner_d0,
+                                            o.inner_pmin, s, &js.Alow));
             FB_CHECK(fb_precond_create(js.Alow, FB_PC_BLOCK_JACOBI, s, &js.pclow));
             FB_CHECK(fb_operator_set_near_bf16(js.Alow, 1, s));   // low-accuracy operator: 16-bit near field
             FB_CHECK(fb_precond_create_inner(js.A32, js.Alow, js.pclow, o.inner_iters, s, &js.inner));

@@ -316,6 +316,10 @@ fb_status fb_stg_op_pass_times(fb_op* op, cudaStream_t s, double* ms, int* form)
 fb_status fb_stg_df_tables(fb_op* op, cudaStream_t s);
 fb_status fb_rcr_df_factors(fb_op* op, int P);
 fb_status fb_near_bf16(fb_op* op, int enable, cudaStream_t s);
+// Creates an operator; `donor` (an FP64 FMM operator of the same mesh, tree,
+// k and kind, or NULL) lends its near-field entries.
+fb_status fb_operator_create_impl(const fb_mesh* mesh, const fb_tree* tree, double k, int kind, int precision,
+                                  double d0, int pmin, cudaStream_t s, fb_op** out, const fb_op* donor = nullptr);
 fb_status fb_stg_tables(fb_op* op, const double* rotd64, cudaStream_t s);
 
 // A group of box pairs sharing one composed translation matrix (job) on the
@@ -392,6 +396,8 @@ struct fb_op {
     int64_t stc_per = 0;                     // floats per group and table
     int stc_P = 0;
     int* stc_err = nullptr;                  // error flag of the tensor-core staged passes
+    const fb_op* near_donor = nullptr;       // during creation: an FP64 FMM operator of the same
+                                             // mesh, tree, k and kind whose near-field entries are copied
     uint32_t* nf16 = nullptr;                // near-field entries as BF16 pairs (re low, im high half)
     int near16 = 0;                          // 1: the matvec reads nf16 instead of nf32
     df* rotf_df = nullptr;                   // FP64 operators: folded tables and coaxial sets in

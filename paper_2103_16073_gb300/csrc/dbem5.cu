@@ -47,8 +47,6 @@ __global__ void k_d5_psi(const cd* __restrict__ q, const cd* __restrict__ g, con
 
 }  // namespace
 
-fb_status fb_operator_create_impl(const fb_mesh* mesh, const fb_tree* tree, double k, int kind, int precision,
-                                  double d0, int pmin, cudaStream_t s, fb_op** out);
 
 fb_status fb_dbem5_create(fb_op* op, cudaStream_t s) {
     const int64_t n = op->mesh->n;

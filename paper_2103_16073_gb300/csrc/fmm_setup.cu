@@ -590,9 +590,16 @@ fb_status fb_fmm_create(fb_op* op, double d0, int pmin, cudaStream_t s) {
     FB_CHECK(dalloc(&op->nf64, op->nf_count));
     FB_CUDA(cudaMemcpyAsync(op->nf_off, op->h_nf_off.data(), sizeof(int64_t) * (nleaf + 1), cudaMemcpyHostToDevice, s));
     FB_CUDA(cudaMemcpyAsync(op->nf_ncol, op->h_nf_ncol.data(), sizeof(int32_t) * nleaf, cudaMemcpyHostToDevice, s));
-    k_near_fill<<<nleaf, 256, 0, s>>>(m->g, op->kind, k, m->rc, t->perm, t->leaf_start, t->ucnt, t->ulist,
-                                      op->nf_off, op->nf_ncol, op->nf64);
-    FB_LAUNCH_CHECK();
+    const fb_op* dn = op->near_donor;
+    if (dn && dn->nf64 && dn->kind == op->kind && dn->k == k && dn->mesh == m && dn->tree == t &&
+        dn->nf_count == op->nf_count) {
+        // the same entries: copy them instead of integrating again
+        FB_CUDA(cudaMemcpyAsync(op->nf64, dn->nf64, sizeof(cd) * op->nf_count, cudaMemcpyDeviceToDevice, s));
+    } else {
+        k_near_fill<<<nleaf, 256, 0, s>>>(m->g, op->kind, k, m->rc, t->perm, t->leaf_start, t->ucnt, t->ulist,
+                                          op->nf_off, op->nf_ncol, op->nf64);
+        FB_LAUNCH_CHECK();
+    }
     // ---- box centres of every level
     std::vector<double*> centers(L + 1, nullptr);
     auto free_centers = [&]() { for (auto& c : centers) dfree(c); };

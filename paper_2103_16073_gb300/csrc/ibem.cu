@@ -88,8 +88,6 @@ __global__ void k_ibem_field_dens(const cd* __restrict__ x, const cd* __restrict
 
 }  // namespace
 
-fb_status fb_operator_create_impl(const fb_mesh* mesh, const fb_tree* tree, double k, int kind, int precision,
-                                  double d0, int pmin, cudaStream_t s, fb_op** out);
 
 // Builds the four constituent operators and the work buffers.
 fb_status fb_ibem_create(fb_op* op, cudaStream_t s) {

@@ -206,6 +206,43 @@ def test_inner_outer_preconditioner(setup):
         fb.fb_tree_destroy(tree)
 
 
+def test_create_like_copies_near_field(setup):
+    """An operator made from an FP64 donor (fb_operator_create_like) copies
+    the donor's near-field entries: the same matvec as an operator created
+    from scratch, FP64 to round-off and mixed to FP32 summation order, and
+    at another order rule; dense donors and precisions are refused."""
+    wl, mesh, op = setup
+    A64 = op(fb.FB_PREC_FP64_FMM)
+    A32 = op(fb.FB_PREC_MIXED_FMM)
+    tree = fb.fb_tree_build(mesh, 64)
+    made = []
+    try:
+        x = torch.tensor(seeded_vector(wl.n, 84), device="cuda")
+
+        def mv(o):
+            y = torch.empty_like(x)
+            fb.fb_operator_apply(o, x, y)
+            torch.cuda.synchronize()
+            return y.cpu().numpy()
+        B64 = fb.fb_operator_create_like(A64, fb.FB_PREC_FP64_FMM, 6.0, 12)
+        made.append(B64)
+        assert rel(mv(B64), mv(A64)) < 1e-13
+        B32 = fb.fb_operator_create_like(A64, fb.FB_PREC_MIXED_FMM, 6.0, 12)
+        made.append(B32)
+        assert rel(mv(B32), mv(A32)) < 1e-6
+        Low = fb.fb_operator_create_like(A64, fb.FB_PREC_MIXED_FMM, 0.5, 2)
+        made.append(Low)
+        Ref = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_MIXED_FMM, 0.5, 2)
+        made.append(Ref)
+        assert rel(mv(Low), mv(Ref)) < 1e-6
+        with pytest.raises(fb.FBError):
+            fb.fb_operator_create_like(A64, fb.FB_PREC_FP64_DENSE, 6.0, 12)
+    finally:
+        for o in made:
+            fb.fb_operator_destroy(o)
+        fb.fb_tree_destroy(tree)
+
+
 def test_inner_operator_bf16_near_field(setup):
     """The low-accuracy inner operator with its near-field entries in BF16:
     its matvec moves from the FP32-entry one by the BF16 rounding only (well
