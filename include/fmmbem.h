@@ -637,7 +637,8 @@ typedef struct fb_batch_opts {
     int restart, maxit;       /* FGMRES; <= 0 selects 40 / 3000               */
     double d0;                /* order rule (<= 0: 6)                         */
     int pmin;                 /* order rule (<= 0: 12)                        */
-    int autotune;             /* 1: fb_operator_autotune per job              */
+    int autotune;             /* 1: autotune the mixed operator per job (one
+                                 timed run per candidate form)              */
     int max_rhs;              /* sources per batched solve (<= 0: 8)          */
     int fp64_judge;           /* 1: true residual by the FP64 FMM operator    */
     int lookahead;            /* 1: build job i+1 while job i solves          */

@@ -1,6 +1,7 @@
-// Autotuner of the translation passes.  For every level it times (median of
-// 3), on the device and for a given number of right-hand sides, the forms a
-// translation pass can take and keeps the fastest:
+// Autotuner of the translation passes.  For every level it times on the
+// device (median of 3 runs, or one run for the batch scheduler's quick
+// pass), for a given number of right-hand sides, the forms a translation
+// pass can take and keeps the fastest:
 //   * rotation - coaxial - rotation (RCR, Sec. 3.3) as per-pair tiles
 //     (where a pair's working set fits a CTA's shared memory),
 //   * RCR as staged batched GEMM passes (pairs grouped by polar angle and by
@@ -107,7 +108,7 @@ fb_status time_rcr(fb_op* op, const RcrPlan& base, Pick pick, int staged, void* 
 // tiles in double-FP32, bit 9 = the same for M2M/L2L, bit 10 = the staged
 // M2L's coaxial step on the tensor cores too (with bit 4), bit 11 = the same
 // for M2M/L2L (with bit 5); times[14 l + 12, 13] time those forms.
-fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_out, int* choice) {
+fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_out, int* choice, int reps) {
     const bool mixed = op->prec == FB_PREC_MIXED_FMM;
     double times_local[FB_TUNE_TIMES * (FB_MAXLEV + 1)];
     double* times = times_out ? times_out : times_local;   // callers may pass NULL
@@ -115,7 +116,7 @@ fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times_ou
     const int L = op->L;
     const int64_t cnt = op->lev_off[L + 1];
     const size_t csz = mixed ? sizeof(cf) : sizeof(cd);
-    const int reps = 3;
+    reps = std::max(1, reps);
     const double cap_bytes = 8.0e9;   // composed FP64 + packed TF32 tiles of one level
     // expansion buffers for nrhs sets (contents do not matter for timing)
     if (nrhs > op->exp_nrhs) {

@@ -65,7 +65,9 @@ void setup_job(const fb_batch_job& jb, const fb_batch_opts& o, cudaStream_t s, J
         FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_L, FB_PREC_FP64_FMM, o.d0, o.pmin, s, &js.L64));
         FB_CHECK(fb_precond_create(js.A32, FB_PC_BLOCK_JACOBI, s, &js.pc));
         const int nrhs = std::max(1, std::min(jb.nsrc, o.max_rhs));
-        if (o.autotune) FB_CHECK(fb_operator_autotune(js.A32, nrhs, s, nullptr, nullptr));
+        // one timed run per candidate: the setup of a sweep, not its solves,
+        // bounds a batch's throughput
+        if (o.autotune) FB_CHECK(fb_autotune_impl(js.A32, nrhs, s, nullptr, nullptr, 1));
         if (o.inner_iters > 0) {
             if (js.A64)
                 FB_CHECK(fb_operator_create_like(js.A64, FB_PREC_MIXED_FMM, o.inner_d0, o.inner_pmin, s, &js.Alow));

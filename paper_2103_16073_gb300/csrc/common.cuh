@@ -498,7 +498,8 @@ fb_status fb_rcr_run_op(fb_op* op, RcrPlan& pl, void* src, void* dst, cudaStream
 // per-pair working set does not fit a CTA are staged regardless) and
 // rebuilds the affected plans.
 fb_status fb_rcr_restage(fb_op* op, const int* m2l, const int* pair);
-fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times, int* choice);
+// reps: timed runs per candidate (median), after one untimed run
+fb_status fb_autotune_impl(fb_op* op, int nrhs, cudaStream_t s, double* times, int* choice, int reps = 3);
 fb_status fb_set_forms_impl(fb_op* op, const int* choice, cudaStream_t s);
 fb_status fb_compose_all(fb_op* op, cudaStream_t s);
 // Leaf self-blocks of the FP64 near-field entries (leaf t at d_off[t], nr x nr).
