@@ -18,7 +18,7 @@
 // multipoles written once per matvec by k_tc_split -> 16-byte cp.async
 // pieces into the canonical layout.
 //
-// Pipeline (8 warps, 4 shared-memory stages of 48 KB):
+// Pipeline (8 warps, 2 shared-memory stages of 48 KB, two CTAs per SM):
 //   warps 0-5  B producers (cp.async, completion tracked by the stage's
 //              "full" mbarrier), warp 6 lane 0 A producer (bulk copy with
 //              transaction count), warp 7 lane 0 MMA issuer (waits "full",
@@ -41,7 +41,7 @@ namespace {
 constexpr int TC_M = 128;       // real output rows per tile
 constexpr int TC_NMAX = 256;    // box pairs per tile
 constexpr int TC_KC = 16;       // real K per stage
-constexpr int TC_STAGES = 4;
+constexpr int TC_STAGES = 2;   // two 48 KB stages: two CTAs (and 2 x 256 TMEM columns) per SM
 constexpr int A_BLOCK = TC_M * TC_KC;       // floats per (hi or lo) A block
 constexpr int B_BLOCK = TC_NMAX * TC_KC;    // floats per (hi or lo) B block
 constexpr int STAGE_FLOATS = 2 * A_BLOCK + 2 * B_BLOCK;
@@ -126,7 +126,7 @@ __global__ void k_tc_split(const SplitLevel* __restrict__ lv, int nlev, const cf
     }
 }
 
-__global__ void __launch_bounds__(256, 1) k_trans_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
+__global__ void __launch_bounds__(256, 2) k_trans_tc(const TcTask* __restrict__ tasks, const TcTile* __restrict__ tiles,
                                                       const float* __restrict__ Abuf, const int32_t* __restrict__ src_idx,
                                                       const int32_t* __restrict__ dst_idx,
                                                       const float* __restrict__ plane_hi,
