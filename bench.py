@@ -166,7 +166,7 @@ def bench_config(name, wl, ws):
             "precond": (f"inner-outer (Sec. 4): {INNER_ITERS} GMRES steps on a low-accuracy mixed FMM "
                         f"(d0={INNER_D0:g}, p_min={INNER_PMIN}, BF16 near-field entries) with block Jacobi"),
             "operator": "mixed: FP32 near field, P2M/L2P and translations (3xTF32 tensor-core and FP32 forms, "
-                        "autotuned per level); FP64 judge: FP64 or double-FP32 translations, autotuned",
+                        "autotuned per level); FP64 true residual: FP64 or double-FP32 translations, autotuned",
             "l2": "inputs larger than L2 (near-field entries and translation data of GB size)",
             "parallelism": f"replicas x{ws} (one (f, source) solve per GPU)"}
 

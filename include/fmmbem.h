@@ -198,7 +198,7 @@ FB_API fb_status fb_operator_create(const fb_mesh* mesh, const fb_tree* tree, do
  * which depend on neither, are copied from the donor when it is an FP64 FMM
  * operator (which keeps its FP64 entries) instead of being integrated
  * again; otherwise they are computed as by fb_operator_create.  Meant for
- * the FP64 judge, the mixed operator and the low-accuracy inner operator of
+ * the FP64 true-residual operator, the mixed operator and the low-accuracy inner operator of
  * one solve.  Errors: FB_ERR_ARG (NULL, dense or composite donor, dense
  * precision). */
 FB_API fb_status fb_operator_create_like(const fb_op* donor, int precision, double d0, int pmin, void* stream,

@@ -55,7 +55,7 @@ void setup_job(const fb_batch_job& jb, const fb_batch_opts& o, cudaStream_t s, J
     cudaSetDevice(dev);   // the current device is per host thread
     double t0 = now_ms();
     auto run = [&]() -> fb_status {
-        // the FP64 judge first: the mixed operators copy its near-field entries
+        // the FP64 true-residual operator first: the mixed operators copy its near-field entries
         if (o.fp64_judge) {
             FB_CHECK(fb_operator_create(jb.mesh, jb.tree, jb.k, FB_OP_A, FB_PREC_FP64_FMM, o.d0, o.pmin, s, &js.A64));
             FB_CHECK(fb_operator_create_like(js.A64, FB_PREC_MIXED_FMM, o.d0, o.pmin, s, &js.A32));
