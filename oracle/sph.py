@@ -25,6 +25,11 @@ Rotation blocks are not given in the paper (Sec. 3.3 cites a separate
 chapter); the oracle uses their definition: for a rotation Q (x_new = Q x),
 D^n_{m'm} = int conj(Y_n^{m'}(y)) Y_n^m(Q^T y) dOmega(y), evaluated with a
 product Gauss-Legendre x trapezoid rule that is exact for the band limit.
+At the degrees of the largest orders, where that grid is too large,
+``rotation_factor`` gives the real factor of one degree from the generator
+of rotations about y; the two agree at low degree, and the generator form is
+pinned at high degree by the closed-form m = 0 column, Wigner's explicit sum
+in high precision and the quarter-turn identity the GPU setup uses.
 """
 from __future__ import annotations
 
@@ -325,6 +330,43 @@ def rotation_blocks(Q, p):
         s = slice(n * n, (n + 1) * (n + 1))
         out.append((np.conj(Y[s]) * W[None, :]) @ Y2[s].T)
     return out
+
+
+def _eps(m):
+    """(-1)^m for m > 0, else 1: Y_n^m of the Condon-Shortley convention
+    over Y_n^m of this one."""
+    m = np.asarray(m)
+    return np.where(m > 0, (-1.0) ** m, 1.0)
+
+
+def rotation_factor(n, theta):
+    """Real factor d^n(theta), [mu + n, m + n], of the rotation blocks at one
+    degree n: for the rotation Q = rotation_to_z(t) of a direction with polar
+    angle theta and azimuth phi, rotation_blocks gives
+    D^n_{mu,m} = d^n_{mu,m}(theta) e^{i m phi}.
+
+    Computed from the generator of rotations about y, not by projection (the
+    projection grid of rotation_blocks grows as p^2 points x p^2 harmonics and
+    stops near degree 40 here, far below the orders of Sec. 3.3's largest
+    boxes).  In the Condon-Shortley basis |n, m>, a rotation by beta about y
+    acts as exp(-i beta J_y), J_y = (J_+ - J_-) / (2i) with the ladder
+    elements <m+1|J_+|m> = <m|J_-|m+1> = sqrt(n(n+1) - m(m+1)).  Q turns by
+    -theta about y after a turn about z, and the harmonics here drop the
+    (-1)^m of positive orders, so
+        d^n_{mu,m}(theta) = eps_mu eps_m [exp(i theta J_y)]_{mu,m}.
+    J_y is Hermitian with eigenvalues exactly -n..n; the exponential is
+    formed from its eigenvectors with the eigenvalues rounded to those
+    integers."""
+    w = 2 * n + 1
+    m = np.arange(-n, n + 1)
+    lad = np.sqrt(n * (n + 1.0) - m[:-1] * (m[:-1] + 1.0))    # <m+1|J_+|m>
+    Jy = np.zeros((w, w), np.complex128)
+    Jy[np.arange(1, w), np.arange(w - 1)] = lad / 2j           # J_+ / (2i)
+    Jy[np.arange(w - 1), np.arange(1, w)] = -lad / 2j          # -J_- / (2i)
+    lam, V = np.linalg.eigh(Jy)
+    E = (V * np.exp(1j * theta * np.round(lam))[None, :]) @ V.conj().T
+    e = _eps(m)
+    return e[:, None] * E.real * e[None, :]
 
 
 def block_diag_rot(D, p):

@@ -401,7 +401,8 @@ __global__ void k_box_centers(const uint32_t* keys, int n, int level, double ox,
 // the rotation about y written as a rotation about z between two quarter
 // turns (the identity holds for the real factors of this harmonic
 // convention; checked against the projection of the definition to 1e-13 up
-// to degree 40).  Also writes the phase tables ph[m + P - 1] = e^{i m phi}
+// to degree 40, and against the exponential of the rotation generator J_y to
+// 1e-12 up to degree 318).  Also writes the phase tables ph[m + P - 1] = e^{i m phi}
 // and, for degrees n < Pc, the complex blocks D = d e^{i m phi} the
 // composed matrices use.  grid: (entry chunk, n, dir)
 __global__ void k_rot_delta(const cd* delta, const double* dirs, int ndir, int P, int Pc, double* d64, float* d32,

@@ -320,3 +320,108 @@ def test_ylm_unsold_identity_to_degree_158():
     for n in range(p):
         s = np.sum(np.abs(Y[n * n:(n + 1) ** 2]) ** 2, axis=0)
         assert np.max(np.abs(s - (2 * n + 1) / (4 * math.pi))) < 1e-11 * (2 * n + 1)
+
+
+# Degrees for the high-degree rotation pins: the largest room's orders reach
+# 159 (rotation degree 158), the GPU setup accepts orders to 256, and 318 is
+# twice the largest room's order.
+_HIGH_DEGREES = (0, 1, 2, 17, 40, 64, 101, 158, 159, 200, 255, 318)
+_THETAS = (1e-3, 0.4, math.pi / 2, 2.2, math.pi - 1e-3)
+
+
+def test_rotation_factor_generator_matches_projection():
+    """The generator form of the real factors against the projection of the
+    rotation definition (rotation_blocks) for general, axis-near and
+    lower-hemisphere directions, every degree below 40."""
+    p = 40
+    for t in ([1.0, -2.0, 0.7], [0.3, 0.1, 5.0], [-1.0, 2.0, -3.0], [2.0, 1.0, 0.0]):
+        t = np.asarray(t)
+        th = math.acos(t[2] / np.linalg.norm(t))
+        ph = math.atan2(t[1], t[0])
+        D = sph.rotation_blocks(sph.rotation_to_z(t), p)
+        for n in range(p):
+            m = np.arange(-n, n + 1)
+            assert np.max(np.abs(sph.rotation_factor(n, th) * np.exp(1j * m[None, :] * ph) - D[n])) < 1e-12
+
+
+def test_rotation_factor_column_closed_form_to_degree_318():
+    """Column m = 0 at high degree: with Q z at polar angle theta and azimuth
+    pi, D^n_{mu,0} = sqrt(4 pi / (2n+1)) conj(Y_n^mu(Q z)) (the addition
+    theorem), so d^n_{mu,0}(theta) = sqrt(4 pi / (2n+1)) (-1)^mu Q_n^|mu|(theta)
+    from the Legendre recursion of ylm, independent of the generator."""
+    p = 319
+    th = np.array(_THETAS)
+    Y = sph.ylm(p, th, np.full(th.size, math.pi))
+    for n in _HIGH_DEGREES:
+        col_ref = math.sqrt(4 * math.pi / (2 * n + 1)) * np.conj(Y[n * n:(n + 1) ** 2])
+        assert np.max(np.abs(col_ref.imag)) < 1e-12
+        for i, t in enumerate(_THETAS):
+            d = sph.rotation_factor(n, t)
+            assert np.max(np.abs(d[:, n] - col_ref[:, i].real)) < 1e-12, (n, t)
+
+
+def _wigner_sum(n, mu, m, beta, digits=300):
+    """d^n_{mu,m}(beta) of the Condon-Shortley convention by Wigner's
+    explicit finite sum, in `digits`-digit arithmetic (its terms reach about
+    4^n before they cancel)."""
+    mpmath = pytest.importorskip("mpmath")
+    with mpmath.workdps(digits):
+        f = [mpmath.factorial(i) for i in range(2 * n + 1)]
+        c, s = mpmath.cos(mpmath.mpf(beta) / 2), mpmath.sin(mpmath.mpf(beta) / 2)
+        pre = mpmath.sqrt(f[n + mu] * f[n - mu] * f[n + m] * f[n - m])
+        acc = mpmath.mpf(0)
+        for k in range(max(0, m - mu), min(n + m, n - mu) + 1):
+            term = pre / (f[n + m - k] * f[k] * f[mu - m + k] * f[n - mu - k])
+            term *= c ** (2 * n + m - mu - 2 * k) * s ** (mu - m + 2 * k)
+            acc += -term if (mu - m + k) % 2 else term
+        return float(acc)
+
+
+def test_rotation_factor_exact_sum_at_high_degree():
+    """Sampled entries (corners, centre, random) of d^n(theta) at degrees 158
+    and 318 against Wigner's explicit sum in 300-digit arithmetic:
+    d^n_{mu,m}(theta) = eps_mu eps_m d_CS^n_{mu,m}(-theta)."""
+    rng = np.random.default_rng(14)
+    for n in (158, 318):
+        for th in (0.4, 2.2):
+            d = sph.rotation_factor(n, th)
+            picks = [(n, n), (-n, -n), (n, -n), (0, 0), (1, -1), (n, 0)]
+            picks += [tuple(int(v) for v in rng.integers(-n, n + 1, 2)) for _ in range(6)]
+            for mu, m in picks:
+                eps = (-1.0) ** mu if mu > 0 else 1.0
+                eps *= (-1.0) ** m if m > 0 else 1.0
+                ref = eps * _wigner_sum(n, mu, m, -th)
+                assert abs(d[mu + n, m + n] - ref) < 1e-12, (n, th, mu, m)
+
+
+def test_rotation_factor_orthogonal_composes_symmetric_to_degree_318():
+    """d^n(theta) is orthogonal, d^n(0) = I, rotations about one axis compose
+    by adding angles, d^n(-theta) = d^n(theta)^T, and the folded kernels'
+    symmetry d^n_{-mu,-m} = d^n_{mu,m} holds, at every sampled degree."""
+    for n in _HIGH_DEGREES:
+        w = 2 * n + 1
+        I = np.eye(w)
+        assert np.max(np.abs(sph.rotation_factor(n, 0.0) - I)) < 1e-13
+        a, b = 0.7, 1.9
+        da, db, dab = sph.rotation_factor(n, a), sph.rotation_factor(n, b), sph.rotation_factor(n, a + b)
+        assert np.max(np.abs(da @ da.T - I)) < 1e-12
+        assert np.max(np.abs(da @ db - dab)) < 1e-12
+        assert np.max(np.abs(sph.rotation_factor(n, -a) - da.T)) < 1e-12
+        assert np.max(np.abs(da[::-1, ::-1] - da)) < 1e-12
+
+
+def test_quarter_turn_identity_to_degree_318():
+    """The identity the GPU setup builds every direction's factors from,
+    d^n_{mu,m}(theta) = sum_k Delta_{mu,k} Delta_{m,k} cos(k theta + (mu - m) pi/2)
+    with Delta = d^n(pi/2), at every sampled degree up to twice the largest
+    room's order (the GPU accepts orders to 256)."""
+    for n in _HIGH_DEGREES:
+        Dl = sph.rotation_factor(n, math.pi / 2)
+        k = np.arange(-n, n + 1)
+        j = (k[:, None] - k[None, :]) % 4          # (mu - m) mod 4
+        for th in _THETAS:
+            # cos(x + j pi/2) is cos x, -sin x, -cos x, sin x for j = 0..3
+            A = (Dl * np.cos(k * th)[None, :]) @ Dl.T
+            B = (Dl * np.sin(k * th)[None, :]) @ Dl.T
+            d = np.select([j == 0, j == 1, j == 2], [A, -B, -A], B)
+            assert np.max(np.abs(d - sph.rotation_factor(n, th))) < 1e-12, (n, th)
