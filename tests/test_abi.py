@@ -103,3 +103,48 @@ def test_input_generators_do_not_map_the_library():
             "assert 'libfmmbem' in open('/proc/self/maps').read()\n" % root)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_operator_entry_points_refuse_null_handles_on_the_host():
+    """The operator-level entry points (translation forms, autotuner, graphs,
+    timing, no-allocation matvec, BF16 near field, sibling operators) report
+    FB_ERR_ARG for a NULL handle or pointer before any device work."""
+    import ctypes as C
+    import numpy as np
+    lib = fb.lib
+    ms = np.zeros(64)
+    ch = np.zeros(16, np.int32)
+    out = C.c_void_p()
+    cnt = C.c_int64()
+    assert lib.fb_operator_create_like(None, fb.FB_PREC_MIXED_FMM, 6.0, 12, None, C.byref(out)) == 1
+    assert lib.fb_operator_apply_noalloc(None, ms.ctypes.data, ms.ctypes.data, None) == 1
+    assert lib.fb_operator_apply_timed(None, ms.ctypes.data, ms.ctypes.data, None, ms.ctypes.data) == 1
+    assert lib.fb_operator_set_near_bf16(None, 1, None) == 1
+    assert lib.fb_operator_staged_pass_times(None, None, ms.ctypes.data, ch.ctypes.data) == 1
+    assert lib.fb_operator_autotune(None, 1, None, None, None) == 1
+    assert lib.fb_operator_set_forms(None, ch.ctypes.data, None) == 1
+    assert lib.fb_operator_set_translation(None, 0) == 1
+    assert lib.fb_operator_use_graphs(None, 1) == 1
+    assert lib.fb_precond_use_graphs(None, 1) == 1
+    assert lib.fb_operator_status(None, None) == 1
+    assert lib.fb_operator_export(None, 7, 0, 0, None, C.byref(cnt)) == 1
+    assert lib.fb_operator_info(None, None, None, None) == 1
+
+
+def test_device_wait_limit_is_a_host_setting():
+    """fb_set_device_wait_limit refuses limits below 1 and returns the
+    previous limit (a host-side value the tensor-core launches read)."""
+    import ctypes as C
+    lib = fb.lib
+    prev = C.c_longlong()
+    assert lib.fb_set_device_wait_limit(0, C.byref(prev)) == 1
+    assert lib.fb_set_device_wait_limit(-5, None) == 1
+    assert lib.fb_set_device_wait_limit(12345, C.byref(prev)) == 0
+    old = prev.value
+    assert old >= 1
+    try:
+        back = C.c_longlong()
+        assert lib.fb_set_device_wait_limit(old, C.byref(back)) == 0
+        assert back.value == 12345
+    finally:
+        lib.fb_set_device_wait_limit(old, None)
