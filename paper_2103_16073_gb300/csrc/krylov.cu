@@ -280,9 +280,6 @@ struct InnerSolver {
     ~InnerSolver();
 };
 
-// The first k+1 Arnoldi vectors of the right-preconditioned Krylov space of
-// A for the start vector b (the inputs a preconditioner sees in the first k
-// iterations of a solve), written to V [(k+1) x N].
 // Workspace of fb_fgmres_solve on operator A with restart m, kept on A and
 // reused while (N, m) match and it holds the Z block a preconditioned solve
 // needs; otherwise it is replaced.  Every solve ends with a host read of a
@@ -306,6 +303,9 @@ static fb_status work_get(fb_op* A, int m, bool with_z, Work** out) {
     return FB_OK;
 }
 
+// The first k+1 Arnoldi vectors of the right-preconditioned Krylov space of
+// A for the start vector b (the inputs a preconditioner sees in the first k
+// iterations of a solve), written to V [(k+1) x N].
 fb_status fb_krylov_basis_impl(fb_op* A, const fb_precond* pc, const cd* b, int k, cd* V, cudaStream_t s) {
     Work W;
     FB_CHECK(work_alloc(W, A->n, k, pc != nullptr));

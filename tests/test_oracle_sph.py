@@ -1,5 +1,6 @@
 """Pins for the oracle's spherical basis, coaxial recursions (Sec. 3.3.1),
 rotations and composed RCR translations."""
+import functools
 import math
 
 import numpy as np
@@ -116,8 +117,9 @@ def test_printed_shft8_third_formula_fails_corrected_holds():
 
 def test_stabilized_scheme_stable_where_original_is_not():
     """Sec. 3.3.1: n-propagation (original step 3) is CFL-unstable for n' > n
-    at large k tau; the stabilized scheme is not.  Reference: the original
-    recursion run in 40-digit arithmetic."""
+    at large k tau; the stabilized scheme is not.  Reference: the stabilized
+    steps run in 40-digit arithmetic (their values are pinned independently
+    by the projection test at order 159)."""
     mpmath = pytest.importorskip("mpmath")
     mpmath.mp.dps = 40
     p, ktau = 100, 300.0
@@ -128,6 +130,66 @@ def test_stabilized_scheme_stable_where_original_is_not():
     e_stab = np.max(np.abs(sph.coaxial(p, ktau, "SR", "stabilized") - R)) / scale
     assert e_stab < 1e-13
     assert e_orig > 1e3 * e_stab
+
+
+@functools.lru_cache(maxsize=None)
+def _gauss_legendre(nodes):
+    return np.polynomial.legendre.leggauss(nodes)
+
+
+def _coax_by_projection(kind, m, n1, n, ktau, nodes=3000):
+    """(E|F)^m_{n'n}(tau) from its definition by projection, reduced to one
+    dimension: a coaxial shift keeps the azimuth of a u + tau z equal to
+    that of u, so with Y_n^m = P_n^m(theta) e^{i m phi} (scipy's normalised
+    P_n^m; its (-1)^m cancels in the product of two equal-m functions)
+        (E|F)^m_{n'n} j_n'(k a) = 2 pi int_{-1}^{1} P_n'^m(x) f_n(k rho) P_n^m(theta') dx,
+    rho = |a u + tau z|, cos theta' = (a x + tau) / rho, f = h (S|R) or j
+    (R|R); Gauss-Legendre in x.  k = 1 (only k tau matters).  The radius a
+    puts k a just past the first maximum of j_n' (so the division does not
+    amplify), below tau for S|R (where the expansion converges); returns the
+    value and the rounding floor eps sqrt(nodes) max|integrand| / |j_n'(k a)|."""
+    tau = ktau
+    a = n1 + 0.81 * n1 ** (1.0 / 3.0) + 1.0
+    if kind == "SR":
+        assert a < 0.9 * tau
+    elif abs(a - tau) < 0.05 * tau:
+        a = 1.1 * tau if a > tau else 0.9 * tau
+    x, w = _gauss_legendre(nodes)
+    rho = np.sqrt(a * a + tau * tau + 2 * a * tau * x)
+    th2 = np.arccos(np.clip((a * x + tau) / rho, -1.0, 1.0))
+    f = special.spherical_jn(n, rho).astype(np.complex128)
+    if kind == "SR":
+        f += 1j * special.spherical_yn(n, rho)
+    g = 2 * np.pi * special.sph_legendre_p(n1, m, np.arccos(x)) * f * special.sph_legendre_p(n, m, th2)
+    j1 = special.spherical_jn(n1, a)
+    return np.sum(w * g) / j1, 2.2e-16 * math.sqrt(nodes) * np.max(np.abs(g)) / abs(j1)
+
+
+@pytest.mark.parametrize("kind, ktau", [("SR", 300.0), ("SR", 773.0), ("RR", 64.0)])
+def test_coaxial_projection_at_order_159(kind, ktau):
+    """Coaxial coefficients at order 159 against their projection definition
+    (sampled entries: corners, sectorial, the high-degree corner at middle
+    orders, random): the 6.5 x 5.5 x 4.2 m room
+    at 5 kHz translates its level-2 M2L at k tau = 298..773 and its level-3
+    M2M / L2L at k tau = 64 with these orders.  Tolerance: 1e-12 of the
+    largest entry plus 50x the projection's own rounding floor (which is
+    loose only where n' + n exceeds k tau, for the reference's sake)."""
+    p = 159
+    X = sph.coaxial(p, ktau, kind)
+    scale = np.max(np.abs(X))
+    rng = np.random.default_rng(15)
+    picks = [(0, 0, 0), (0, p - 1, p - 1), (0, 0, p - 1), (0, p - 1, 0), (p - 1, p - 1, p - 1),
+             (100, 158, 120), (1, 2, 157)]
+    # the high-degree corner at middle orders, where an unstable recursion
+    # goes wrong first
+    picks += [(m, n1, n) for m in (20, 39, 59, 80, 120) for n1, n in ((157, 158), (158, 158), (158, 140))]
+    for _ in range(16):
+        m = int(rng.integers(0, p))
+        a, b = rng.integers(m, p, 2)
+        picks.append((m, int(a), int(b)))
+    for m, n1, n in picks:
+        ref, floor = _coax_by_projection(kind, m, n1, n, ktau)
+        assert abs(X[m, n1, n] - ref) <= 1e-12 * scale + 50 * floor, (m, n1, n)
 
 
 def _random_rotation(rng):
