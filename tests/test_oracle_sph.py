@@ -192,6 +192,68 @@ def test_coaxial_projection_at_order_159(kind, ktau):
         assert abs(X[m, n1, n] - ref) <= 1e-12 * scale + 50 * floor, (m, n1, n)
 
 
+def _rcr_apply(cin, t, k, p, kind):
+    """Rotation - coaxial - back-rotation (Sec. 3.3) applied to coefficient
+    vectors (columns of cin, flat index n^2 + n + m) degree by degree, as the
+    composed matrix of sph.translation would (which is p^2 x p^2 and too
+    large at order 159): u^n = D^n c^n, v = (E|F) u per order m,
+    out^n = D^n^H v^n, with D^n = d^n(theta) e^{i m phi} of t's direction."""
+    tau = float(np.linalg.norm(t))
+    th, ph = math.acos(t[2] / tau), math.atan2(t[1], t[0])
+    X = sph.coaxial(p, k * tau, kind)
+    D = []
+    u = np.zeros_like(cin)
+    for n in range(p):
+        m = np.arange(-n, n + 1)
+        D.append(sph.rotation_factor(n, th) * np.exp(1j * m * ph)[None, :])
+        u[n * n:(n + 1) ** 2] = D[n] @ cin[n * n:(n + 1) ** 2]
+    v = np.zeros_like(cin)
+    for mm in range(-(p - 1), p):
+        a = abs(mm)
+        rows = [sph.idx(n, mm) for n in range(a, p)]
+        v[rows] = X[a, a:p, a:p] @ u[rows]
+    out = np.zeros_like(cin)
+    for n in range(p):
+        out[n * n:(n + 1) ** 2] = D[n].conj().T @ v[n * n:(n + 1) ** 2]
+    return out
+
+
+@pytest.mark.parametrize("kind", ["SR", "RR"])
+def test_rcr_translation_addition_theorem_at_order_159(kind):
+    """The whole RCR chain at order 159 (generator-form rotations, stabilized
+    coaxial coefficients) against the Green's function of point sources:
+    S|R (M2L) at k tau = 300 along (2, -1, 2) with sources and receivers
+    within k r = 60 of the two centres; R|R (M2M, t = parent - child) at
+    k tau = 64 along (1, 1, -1) with sources within k r = 20 of the child
+    and receivers at k r = 200 from the parent (the 6.5 x 5.5 x 4.2 m room's
+    level-2 M2L and level-3 M2M at 5 kHz, with k = 1)."""
+    p, k = 159, 1.0
+    rng = np.random.default_rng(16)
+
+    def around(c, r, count):
+        v = rng.standard_normal((count, 3))
+        return c + r * v / np.linalg.norm(v, axis=1)[:, None]
+
+    neg = np.array([sph.idx(n, -m) for n in range(p) for m in range(-n, n + 1)])
+    c1 = np.zeros(3)
+    if kind == "SR":
+        t = np.array([2.0, -1.0, 2.0]) * 100.0
+        src, rcv = around(c1, 60.0, 3), around(c1 + t, 60.0, 3)
+    else:
+        t = np.array([1.0, 1.0, -1.0]) / math.sqrt(3.0) * 64.0
+        src, rcv = around(c1, 20.0, 3), around(c1 + t, 200.0, 3)
+    # multipole coefficients of each source about c1: G(x, y) = ik sum S_n^m(x - c) R_n^-m(y - c)
+    C = np.stack([1j * k * sph.regular(p, k, y - c1)[neg] for y in src], axis=1)
+    out = _rcr_apply(C, t, k, p, kind)
+    F = sph.regular if kind == "SR" else sph.singular
+    for x in rcv:
+        basis = F(p, k, x - (c1 + t))
+        for j, y in enumerate(src):
+            r = np.linalg.norm(x - y)
+            g = np.exp(1j * k * r) / (4 * math.pi * r)
+            assert abs(np.sum(out[:, j] * basis) - g) < 1e-12 * abs(g)
+
+
 def _random_rotation(rng):
     q = rng.standard_normal(4)
     q /= np.linalg.norm(q)
