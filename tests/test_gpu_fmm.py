@@ -105,6 +105,32 @@ def test_setup_stages_match_oracle(case, kind):
             assert maxrel(g.reshape(ref.shape), ref) < 1e-11, ("L2L", lev, o)
 
 
+def test_rotation_factor_export_matches_oracle(case):
+    """The device rotation data (every direction's real factors from the
+    quarter-turn identity) entry by entry against the oracle's factors from
+    the rotation generator, for M2L directions of the tree and degrees up
+    to the largest order: both give d^n(theta) of the direction, row mu,
+    column m."""
+    import math
+    from oracle import sph
+    op = case.op("A", fb.FB_PREC_FP64_FMM)
+    top = max(fb.fb_operator_info(op)[2]) - 1
+    found = 0
+    for d in ((2, 0, 0), (2, 2, 2), (3, -1, 2), (-2, 3, -3), (0, -2, 1), (-3, -3, -2)):
+        code = (d[0] + 3) * 49 + (d[1] + 3) * 7 + (d[2] + 3)
+        th = math.acos(d[2] / math.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2))
+        try:
+            fb.fb_operator_export(op, 8, 0, code)
+        except fb.FBError:
+            continue   # no M2L pair of this tree has that offset
+        found += 1
+        for n in sorted({0, 1, 2, 7, top // 2, top}):
+            w = 2 * n + 1
+            dn = fb.fb_operator_export(op, 8, n, code).real.reshape(w, w)
+            assert np.max(np.abs(dn - sph.rotation_factor(n, th))) < 1e-11, (d, n)
+    assert found >= 2
+
+
 @pytest.mark.parametrize("method", [fb.FB_TRANS_RCR, fb.FB_TRANS_COMPOSED])
 @pytest.mark.parametrize("kind", ["A", "L", "M", "LP"])
 def test_fp64_fmm_matvec(case, kind, method):
