@@ -46,3 +46,41 @@ def test_high_order_fmm_matches_dense():
             fb.fb_operator_destroy(op)
         fb.fb_tree_destroy(tree)
         fb.fb_mesh_destroy(mesh)
+
+
+def test_high_order_rotation_factors_match_oracle():
+    """The device's real rotation factors at degrees up to 115 (level 2 of
+    the same shoebox; quarter-turn identity on the device) entry by entry
+    against the oracle's factors from the rotation generator."""
+    import math
+    from oracle import sph
+    wl = workload("high_order")
+    mesh = fb.fb_mesh_create(wl.verts, wl.tris)
+    fb.fb_mesh_set_admittance(mesh, wl.beta)
+    tree = fb.fb_tree_build(mesh, 64)
+    A64 = None
+    try:
+        A64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, 12)
+        top = max(fb.fb_operator_info(A64)[2]) - 1
+        assert top >= 113
+        worst, found = 0.0, 0
+        for d in ((2, 0, 0), (2, 2, 2), (3, -1, 2), (-2, 3, -3), (0, -2, 1)):
+            code = (d[0] + 3) * 49 + (d[1] + 3) * 7 + (d[2] + 3)
+            try:
+                fb.fb_operator_export(A64, 8, 0, code)
+            except fb.FBError:
+                continue   # no M2L pair of this tree has that offset
+            found += 1
+            th = math.acos(d[2] / math.sqrt(d[0] ** 2 + d[1] ** 2 + d[2] ** 2))
+            for n in (0, 1, 40, 80, top):
+                w = 2 * n + 1
+                dn = fb.fb_operator_export(A64, 8, n, code).real.reshape(w, w)
+                worst = max(worst, float(np.max(np.abs(dn - sph.rotation_factor(n, th)))))
+        print(f"degree <= {top}, {found} directions: max |d_gpu - d_oracle| = {worst:.3e}")
+        assert found >= 2
+        assert worst < 1e-10
+    finally:
+        if A64 is not None:
+            fb.fb_operator_destroy(A64)
+        fb.fb_tree_destroy(tree)
+        fb.fb_mesh_destroy(mesh)
