@@ -148,3 +148,17 @@ def test_device_wait_limit_is_a_host_setting():
         assert back.value == 12345
     finally:
         lib.fb_set_device_wait_limit(old, None)
+
+
+def test_empty_and_degenerate_meshes_are_refused_on_the_host():
+    """No triangles, fewer than three vertices, or a negative vertex index:
+    FB_ERR_ARG before any allocation."""
+    import numpy as np
+    import pytest
+    v = np.array([[0.0, 0, 0], [1, 0, 0], [0, 1, 0]])
+    for verts, tris in ((v, np.zeros((0, 3), np.int32)),
+                        (v[:2], np.array([[0, 1, 1]])),
+                        (v, np.array([[0, -1, 2]]))):
+        with pytest.raises(fb.FBError) as e:
+            fb.fb_mesh_create(verts, tris)
+        assert e.value.code == 1
