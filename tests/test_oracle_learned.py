@@ -125,3 +125,77 @@ def test_approximate_adjoint_is_close():
     _, g_ex = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, lambda x: A.conj().T @ x, beta=BETA, k=K)
     _, g_ap = learned.loss_grad(theta, T, r, e, u, nrm, "residual", A, adj, beta=BETA, k=K)
     assert g_ap @ g_ex > 0.9 * np.linalg.norm(g_ap) * np.linalg.norm(g_ex)
+
+
+def test_trained_network_gain_on_held_out_sources():
+    """What the trained network gains, in FP64 on a dense operator (956
+    elements, 300 Hz, leaves of <= 32): trained with Adam on the residual
+    objective (exact adjoint) over the preconditioner inputs of block-Jacobi
+    FGMRES solves for 8 sources, it fits them (mean residual loss well below
+    block Jacobi's) and FGMRES, which admits the changing preconditioner,
+    still converges on 3 held-out sources within two iterations of block
+    Jacobi, and in all no more than block Jacobi.  Measured: residual loss
+    0.77 -> 0.35, iterations 25, 25, 24 -> 24, 24, 23 (at 700 Hz the same
+    recipe gives 56, 54, 58 -> 55-56, 53, 56-57): halving the mean residual
+    of the training inputs buys about one iteration."""
+    import math
+    from oracle.fgmres import fgmres
+    v, t, _ = W.shoebox_mesh(1.3, 1.1, 0.9, 11, 9, 7)
+    mesh = bem.Mesh(v, t)
+    n, k = mesh.n, 2 * math.pi * 300.0 / 343.0
+    beta = np.full(n, 0.05 + 0.0j)
+    Lm, Mm, _ = bem.dense_operators(mesh, k)
+    A = bem.system_matrix(Lm, Mm, k, beta)
+    el = mesh.el
+    T = learned.TreeInfo(Octree(np.concatenate([el.v0, el.v1, el.v2]), el.centroid, mesh.rc, 32))
+    blocks = []
+    for b in range(len(T.leaf_start) - 1):
+        idx = T.perm[T.leaf_start[b]:T.leaf_start[b + 1]]
+        blocks.append((idx, np.linalg.inv(A[np.ix_(idx, idx)])))
+
+    def bj(x):
+        u = np.zeros_like(x)
+        for idx, Bi in blocks:
+            u[idx] = Bi @ x[idx]
+        return u
+
+    rng = np.random.default_rng(5)
+    sources = [np.array([0.2, 0.2, 0.2]) + rng.uniform(0, 1, 3) * np.array([0.9, 0.7, 0.5]) for _ in range(11)]
+    rhs = [Lm @ bem.gamma_monopole(mesh, k, beta, xs) for xs in sources]
+
+    def solve(b, pc, log=None):
+        def p(x):
+            if log is not None:
+                log.append(x.copy())
+            return pc(x)
+        return fgmres(lambda x: A @ x, b, tol=1e-6, restart=40, precond=p)[1]["iters"]
+
+    inputs = []
+    for b in rhs[:8]:
+        solve(b, bj, inputs)
+    U = [bj(x) for x in inputs]
+    lay, total = learned.layout()
+    theta = rng.standard_normal(total) * 0.05
+    for name in ("Wo", "bo"):
+        o, nn = lay[name]
+        theta[o:o + nn] = 0.0
+    adj = lambda w: A.conj().T @ w
+    m1, m2 = np.zeros(total), np.zeros(total)
+    for it in range(1, 201):
+        g = np.zeros(total)
+        for q in rng.choice(len(inputs), 8, replace=False):
+            g += learned.loss_grad(theta, T, inputs[q], None, U[q], el.normal, "residual", A, adj, beta, k)[1] / 8
+        m1 = 0.9 * m1 + 0.1 * g
+        m2 = 0.999 * m2 + 0.001 * g * g
+        theta -= 1e-3 * (m1 / (1 - 0.9 ** it)) / (np.sqrt(m2 / (1 - 0.999 ** it)) + 1e-8)
+    loss_bj = np.mean([np.linalg.norm(A @ u - x) ** 2 / np.linalg.norm(x) ** 2 for x, u in zip(inputs, U)])
+    loss_net = np.mean([learned.loss_grad(theta, T, x, None, u, el.normal, "residual", A, adj, beta, k)[0]
+                        for x, u in zip(inputs, U)])
+    net = lambda x: learned.forward(theta, T, x, bj(x), el.normal, beta, k)[0]
+    it_bj = [solve(b, bj) for b in rhs[8:]]
+    it_net = [solve(b, net) for b in rhs[8:]]
+    print(f"residual loss: block Jacobi {loss_bj:.3f}, trained network {loss_net:.3f}; "
+          f"held-out FGMRES iterations: block Jacobi {it_bj}, network {it_net}")
+    assert loss_net < 0.7 * loss_bj
+    assert all(a <= b + 2 for a, b in zip(it_net, it_bj))
+    assert sum(it_net) <= sum(it_bj)
