@@ -48,13 +48,19 @@ def test_high_order_fmm_matches_dense():
         fb.fb_mesh_destroy(mesh)
 
 
-def test_high_order_rotation_factors_match_oracle():
-    """The device's real rotation factors at degrees up to 115 (level 2 of
-    the same shoebox; quarter-turn identity on the device) entry by entry
-    against the oracle's factors from the rotation generator."""
+@pytest.mark.parametrize("freq", [7500.0, 10800.0])
+def test_high_order_rotation_factors_match_oracle(freq):
+    """The device's real rotation factors (quarter-turn identity on the
+    device) entry by entry against the oracle's factors from the rotation
+    generator, on the same coarse shoebox at 7.5 kHz (orders 116 / 66) and
+    at 10.8 kHz (orders 159 / 89, the largest room's top two levels; the
+    mesh is too coarse for that frequency, which the rotation data do not
+    depend on)."""
     import math
     from oracle import sph
-    wl = workload("high_order")
+    from paper_2103_16073_gb300 import workloads as W
+    wl = W.shoebox_workload("shoebox-3.0x2.4x2.0-N3072", 3.0, 2.4, 2.0, (16, 16, 16), freq, 0.2,
+                            (0.7, 0.6, 0.5), 8, 0)
     mesh = fb.fb_mesh_create(wl.verts, wl.tris)
     fb.fb_mesh_set_admittance(mesh, wl.beta)
     tree = fb.fb_tree_build(mesh, 64)
@@ -62,7 +68,7 @@ def test_high_order_rotation_factors_match_oracle():
     try:
         A64 = fb.fb_operator_create(mesh, tree, wl.k, fb.FB_OP_A, fb.FB_PREC_FP64_FMM, 6.0, 12)
         top = max(fb.fb_operator_info(A64)[2]) - 1
-        assert top >= 113
+        assert top >= (158 if freq > 1e4 else 113)
         worst, found = 0.0, 0
         for d in ((2, 0, 0), (2, 2, 2), (3, -1, 2), (-2, 3, -3), (0, -2, 1)):
             code = (d[0] + 3) * 49 + (d[1] + 3) * 7 + (d[2] + 3)
