@@ -43,6 +43,8 @@ def expm1c(z):
 
 
 def green(x, y, k):
+    """Free-space Green's function G = e^{ikR} / (4 pi R), R = |x - y| (Sec. 2,
+    the kernel of the boundary integrals of Eq. dbem2)."""
     R = np.linalg.norm(x - y, axis=-1)
     return np.exp(1j * k * R) / (FOUR_PI * R)
 

@@ -30,6 +30,11 @@ from .octree import Octree
 
 
 def order_rule(k, delta, d0=6.0, pmin=9):
+    """Expansion order of a level with box side delta.  The paper gives no
+    truncation rule (it cites its FMM reference); this is that reference's
+    excess-bandwidth form p = ceil(k r + 1.8 d0^(2/3) (k r)^(1/3)), r = the
+    half-diagonal sqrt(3)/2 delta, d0 the number of accurate digits, and at
+    least pmin."""
     kr = k * math.sqrt(3.0) / 2.0 * delta
     p = math.ceil(kr + 1.8 * d0 ** (2.0 / 3.0) * kr ** (1.0 / 3.0))
     return max(int(pmin), int(p))
@@ -75,6 +80,10 @@ def l2p_operator(mesh, k, elems, c, p, kind):
 
 
 def near_entries(mesh, k, beta, rows, cols, kind):
+    """Near-field block of operator `kind` (L, M, LP or the system matrix A
+    of Eq. dbem4) for collocation rows at the elements `rows` and element
+    columns `cols`, with the singular and near-singular rules of the dense
+    operator (Sec. 3.3: near interactions are computed directly)."""
     L, M, LP = bem.operator_rows(mesh, k, mesh.el.centroid[rows], mesh.el.normal[rows],
                                  rows, cols)
     if kind == "L":
@@ -146,6 +155,9 @@ class FMM:
         return self._cache[key]
 
     def matvec(self, x):
+        """y = (operator) x by the passes of Sec. 3.3: near field per leaf,
+        P2M at the leaves, M2M upward, M2L over the interaction lists, L2L
+        downward, L2P at the leaves."""
         x = np.asarray(x, np.complex128)
         T, L = self.tree, self.L
         y = np.zeros(self.mesh.n, np.complex128)

@@ -19,6 +19,9 @@ import numpy as np
 
 
 def rule3():
+    """Symmetric 3-point rule on a triangle (barycentric points, weights
+    summing to 1), exact for polynomials of degree 2: the far-field rule of
+    the collocation (the paper leaves the quadrature to the implementer)."""
     bary = np.array([[2 / 3, 1 / 6, 1 / 6],
                      [1 / 6, 2 / 3, 1 / 6],
                      [1 / 6, 1 / 6, 2 / 3]])
@@ -27,6 +30,9 @@ def rule3():
 
 
 def rule7():
+    """Radon's 7-point rule on a triangle (barycentric points, weights
+    summing to 1), exact for polynomials of degree 5: the rule for the
+    smooth remainder of near and self entries."""
     s15 = math.sqrt(15.0)
     a = (6.0 - s15) / 21.0
     b = (6.0 + s15) / 21.0

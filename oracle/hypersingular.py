@@ -96,6 +96,8 @@ def mp_rows(mesh, k, rows, cols=None):
 
 
 def dense_mp(mesh, k, chunk=64):
+    """Dense hypersingular operator M' of Eq. ibem3 (all collocation rows,
+    built in row chunks by mp_rows)."""
     out = np.empty((mesh.n, mesh.n), np.complex128)
     for s in range(0, mesh.n, chunk):
         e = min(mesh.n, s + chunk)

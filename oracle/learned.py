@@ -35,6 +35,8 @@ HW, NF, DEPTH = 64, 11, 3
 
 
 def layout():
+    """Offsets of the named weight and bias blocks in the flat parameter
+    vector (the layout above) and its total length."""
     sizes = [("W0", NF * HW), ("b0", HW)]
     for k in range(DEPTH):
         sizes += [(f"Wu{k}", HW * HW), (f"bu{k}", HW)]
@@ -49,6 +51,7 @@ def layout():
 
 
 def unpack(theta):
+    """The flat parameter vector as named FP64 arrays (weights [in x out])."""
     lay, _ = layout()
     shapes = {"W0": (NF, HW), "Wh": (2 * HW, HW), "Wo": (HW, 2)}
     for k in range(DEPTH):
@@ -62,10 +65,12 @@ def unpack(theta):
 
 
 def silu(x):
+    """SiLU activation x / (1 + e^{-x})."""
     return x / (1.0 + np.exp(-x))
 
 
 def silu_grad(x):
+    """Derivative of SiLU: s (1 + x (1 - s)), s = 1 / (1 + e^{-x})."""
     s = 1.0 / (1.0 + np.exp(-x))
     return s * (1.0 + x * (1.0 - s))
 

@@ -24,6 +24,8 @@ import numpy as np
 
 
 def morton(ix, iy, iz, level):
+    """Morton key of integer box coordinates at `level`: bit b of x, y, z at
+    key bits 3b, 3b+1, 3b+2 (the box numbering of the octree of Sec. 3.3)."""
     key = np.zeros(np.shape(ix), dtype=np.int64)
     for b in range(level):
         key |= ((np.asarray(ix, np.int64) >> b) & 1) << (3 * b)
@@ -33,6 +35,7 @@ def morton(ix, iy, iz, level):
 
 
 def demorton(key, level):
+    """Inverse of morton: the integer box coordinates of a key."""
     key = np.asarray(key, np.int64)
     ix = np.zeros(key.shape, np.int64)
     iy = np.zeros(key.shape, np.int64)
@@ -45,6 +48,9 @@ def demorton(key, level):
 
 
 def bounding_cube(verts):
+    """Root box: the cube around the vertices' bounding box, its side the
+    largest extent times (1 + 1e-6) so that no vertex lies on the far face
+    (a reading: the paper does not fix the root box)."""
     v = np.asarray(verts, float)
     lo = v.min(axis=0)
     hi = v.max(axis=0)
@@ -54,6 +60,8 @@ def bounding_cube(verts):
 
 
 def box_coords(points, origin, side, level):
+    """Integer coordinates of the box containing each point at `level`
+    (clipped to the grid)."""
     nb = 1 << level
     delta = side / nb
     c = np.floor((np.asarray(points, float) - origin[None, :]) / delta).astype(np.int64)
@@ -61,6 +69,9 @@ def box_coords(points, origin, side, level):
 
 
 def choose_leaf_level(centroids, origin, side, rc, leaf_max, max_level=20):
+    """Leaf level (a reading: the paper gives no rule): the first level >= 2
+    where no box holds more than leaf_max centroids, but not deeper than the
+    last level whose box side still exceeds the near-field radius rc."""
     l_rc = 0
     while side / (1 << (l_rc + 1)) > rc and l_rc + 1 <= max_level:
         l_rc += 1
@@ -76,6 +87,10 @@ def choose_leaf_level(centroids, origin, side, rc, leaf_max, max_level=20):
 
 
 class Octree:
+    """Uniform-depth octree of the element centroids (Sec. 3.3): elements
+    sorted by leaf Morton key (perm), leaf ranges, and the occupied boxes of
+    every level."""
+
     def __init__(self, verts, centroids, rc, leaf_max=64, level=None):
         self.origin, self.side = bounding_cube(verts)
         cen = np.asarray(centroids, float)
@@ -92,9 +107,11 @@ class Octree:
             self.levels[lev] = np.unique(self.leaf_keys >> (3 * (L - lev)))
 
     def delta(self, lev):
+        """Box side at level lev."""
         return self.side / (1 << lev)
 
     def centers(self, lev):
+        """Centres of the occupied boxes of level lev, in key order."""
         ix, iy, iz = demorton(self.levels[lev], lev)
         d = self.delta(lev)
         return self.origin[None, :] + (np.stack([ix, iy, iz], 1) + 0.5) * d

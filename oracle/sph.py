@@ -40,6 +40,7 @@ from scipy import special
 
 
 def idx(n, m):
+    """Flat index n^2 + n + m of coefficient (n, m), |m| <= n."""
     return n * n + n + m
 
 
@@ -61,12 +62,15 @@ def b_coef(n, m):
 
 
 def sph_j(nmax, x):
+    """Spherical Bessel functions j_n(x), n = 0..nmax (the radial part of
+    R_n^m, Eq. shft0); shape [nmax+1, ...]."""
     n = np.arange(nmax + 1)
     x = np.asarray(x)
     return special.spherical_jn(n[:, None], x.ravel()[None, :]).reshape((nmax + 1,) + x.shape)
 
 
 def sph_jp(nmax, x):
+    """Derivatives j_n'(x), n = 0..nmax; shape [nmax+1, ...]."""
     n = np.arange(nmax + 1)
     x = np.asarray(x)
     return special.spherical_jn(n[:, None], x.ravel()[None, :], derivative=True).reshape(
@@ -74,6 +78,8 @@ def sph_jp(nmax, x):
 
 
 def sph_h(nmax, x):
+    """Spherical Hankel functions h_n(x) = j_n(x) + i y_n(x), n = 0..nmax (the
+    radial part of S_n^m, Eq. shft0); shape [nmax+1, ...]."""
     n = np.arange(nmax + 1)
     x = np.asarray(x)
     j = special.spherical_jn(n[:, None], x.ravel()[None, :])
@@ -370,6 +376,8 @@ def rotation_factor(n, theta):
 
 
 def block_diag_rot(D, p):
+    """The rotation blocks D^n, n < p, as one block-diagonal [p^2, p^2]
+    matrix acting on flat coefficient vectors."""
     Mx = np.zeros((p * p, p * p), np.complex128)
     for n in range(p):
         s = slice(n * n, (n + 1) * (n + 1))
