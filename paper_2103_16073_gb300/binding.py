@@ -511,15 +511,33 @@ lib.fb_operator_set_forms.restype = C.c_int
 lib.fb_operator_set_forms.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p]
 
 
-def fb_operator_set_forms(op, forms, stream=None):
-    """forms: {level: {"m2l_on_tensor": bool, "m2m_l2l_on_tensor": bool}} (as
-    fb_operator_autotune returns) or a sequence of 13 choice ints."""
+# form bits of a level's choice, in the order of the library's bit numbers 0..11
+_FORM_FLAGS = ("m2l_on_tensor", "m2m_l2l_on_tensor", "m2l_staged_on", "m2m_l2l_staged_on",
+               "m2l_staged_tc_on", "m2m_l2l_staged_tc_on", "m2l_staged_df_on", "m2m_l2l_staged_df_on",
+               "m2l_tiles_df_on", "m2m_l2l_tiles_df_on", "m2l_staged_tcc_on", "m2m_l2l_staged_tcc_on")
+
+
+def _forms_choice(forms):
+    """The 13 per-level choice ints of fb_operator_set_forms from a dict as
+    fb_operator_autotune returns (its "choice", else the "..._on" flags) or
+    from a sequence of ints."""
     ch = np.zeros(13, np.int32)
     if isinstance(forms, dict):
         for l, v in forms.items():
-            ch[int(l)] = (1 if v.get("m2l_on_tensor") else 0) | (2 if v.get("m2m_l2l_on_tensor") else 0)
+            if "choice" in v:
+                ch[int(l)] = int(v["choice"])
+            else:
+                ch[int(l)] = sum(1 << b for b, name in enumerate(_FORM_FLAGS) if v.get(name))
     else:
         ch[:len(forms)] = np.asarray(forms, np.int32)
+    return ch
+
+
+def fb_operator_set_forms(op, forms, stream=None):
+    """Installs per-level translation forms: forms is the dict
+    fb_operator_autotune returns (or one with the same "..._on" flags) or a
+    sequence of up to 13 choice ints (bits 0-11 as in include/fmmbem.h)."""
+    ch = _forms_choice(forms)
     _check(lib.fb_operator_set_forms(op, ch.ctypes.data, _stream(stream)))
 
 

@@ -162,3 +162,18 @@ def test_empty_and_degenerate_meshes_are_refused_on_the_host():
         with pytest.raises(fb.FBError) as e:
             fb.fb_mesh_create(verts, tris)
         assert e.value.code == 1
+
+
+def test_forms_dict_round_trips_every_form_bit():
+    """fb_operator_set_forms accepts the autotuner's dict: its "choice" ints,
+    or all twelve "..._on" flags when no "choice" is given, or a list."""
+    import numpy as np
+    from paper_2103_16073_gb300 import binding
+    tuned = {2: {"choice": 1044}, 5: {"choice": 3132}}
+    assert list(binding._forms_choice(tuned)[[2, 5]]) == [1044, 3132]
+    for bit, name in enumerate(binding._FORM_FLAGS):
+        assert binding._forms_choice({3: {name: True}})[3] == 1 << bit
+    flags = {4: {"m2l_staged_tc_on": True, "m2m_l2l_staged_tcc_on": True, "m2l_on_tensor": False}}
+    assert binding._forms_choice(flags)[4] == 16 | 2048
+    assert list(binding._forms_choice([0, 0, 20])[:4]) == [0, 0, 20, 0]
+    assert binding._forms_choice([]).shape == (13,) and not np.any(binding._forms_choice([]))
