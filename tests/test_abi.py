@@ -177,3 +177,24 @@ def test_forms_dict_round_trips_every_form_bit():
     assert binding._forms_choice(flags)[4] == 16 | 2048
     assert list(binding._forms_choice([0, 0, 20])[:4]) == [0, 0, 20, 0]
     assert binding._forms_choice([]).shape == (13,) and not np.any(binding._forms_choice([]))
+
+
+def test_binding_constants_match_the_header():
+    """Every FB_* integer constant the binding defines equals the header's
+    #define of the same name (operator kinds, precisions, memory spaces,
+    preconditioners, translation methods, limits, losses)."""
+    import re
+    from paper_2103_16073_gb300 import binding
+    text = open(HEADER).read()
+    defs = {}
+    for name, val, sh in re.findall(r"^#define\s+(FB_[A-Z0-9_]+)\s+\(?(\d+)u?\s*(?:<<\s*(\d+))?", text,
+                                    flags=re.M):
+        defs[name] = int(val) << (int(sh) if sh else 0)
+    checked = 0
+    for name in dir(binding):
+        if name.startswith("FB_") and isinstance(getattr(binding, name), int) and name in defs:
+            assert getattr(binding, name) == defs[name], name
+            checked += 1
+    assert checked >= 20
+    assert binding.NOALLOC_SCRATCH_BYTES == defs["FB_NOALLOC_SCRATCH_BYTES"]
+    assert "FB_MAX_RHS" in defs and "FB_TUNE_TIMES" in defs
