@@ -143,6 +143,15 @@ def _ptr(a, dtype=None):
     return C.c_void_p(arr.ctypes.data), FB_MEM_HOST, arr
 
 
+def _cuda_ptr(t, name):
+    """Device pointer of a contiguous CUDA tensor (the caller keeps it alive)."""
+    if not _is_cuda_tensor(t):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return C.c_void_p(t.data_ptr())
+
+
 def _same_space(*ms):
     if len(set(ms)) != 1:
         raise ValueError("all vector arguments must be host arrays or all device tensors")
@@ -335,11 +344,8 @@ PHASES = ("p2m", "m2m", "m2l_tc", "m2l", "l2l", "near_l2p", "total")
 
 def fb_operator_apply_timed(op, x, y, stream=None):
     """y = Op x on CUDA tensors; returns per-phase CUDA-event times (ms)."""
-    if not (_is_cuda_tensor(x) and _is_cuda_tensor(y)):
-        raise ValueError("fb_operator_apply_timed needs CUDA tensors")
     ms = np.zeros(7)
-    _check(lib.fb_operator_apply_timed(op, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
-                                       _stream(stream), ms.ctypes.data))
+    _check(lib.fb_operator_apply_timed(op, _cuda_ptr(x, "x"), _cuda_ptr(y, "y"), _stream(stream), ms.ctypes.data))
     return dict(zip(PHASES, ms.tolist()))
 
 
@@ -576,11 +582,9 @@ def fb_krylov_basis(A, pc, b, k, stream=None):
     """First k+1 Arnoldi vectors (CUDA complex128 [k+1, N]) of the right-
     preconditioned Krylov space of A from b (CUDA complex128 [N])."""
     import torch
-    if not _is_cuda_tensor(b):
-        raise ValueError("b must be a CUDA tensor")
+    pb = _cuda_ptr(b, "b")
     V = torch.empty((int(k) + 1, b.numel()), dtype=b.dtype, device=b.device)
-    _check(lib.fb_krylov_basis(A, pc, C.c_void_p(b.data_ptr()), int(k), C.c_void_p(V.data_ptr()),
-                               _stream(stream)))
+    _check(lib.fb_krylov_basis(A, pc, pb, int(k), C.c_void_p(V.data_ptr()), _stream(stream)))
     return V
 
 
@@ -632,23 +636,19 @@ def fb_learned_params(pc, new=None):
 
 def fb_learned_loss_and_grad(pc, R, E, stream=None):
     """R, E: CUDA complex128 tensors [npairs, N].  Returns (loss, grad)."""
-    if not (_is_cuda_tensor(R) and _is_cuda_tensor(E)):
-        raise ValueError("R and E must be CUDA tensors")
+    pr, pe = _cuda_ptr(R, "R"), _cuda_ptr(E, "E")
     cnt = C.c_int64(0)
     _check(lib.fb_learned_params(pc, None, None, C.byref(cnt)))
     grad = np.zeros(cnt.value, np.float32)
     loss = C.c_double()
-    _check(lib.fb_learned_loss_and_grad(pc, C.c_void_p(R.data_ptr()), C.c_void_p(E.data_ptr()), R.shape[0],
-                                        C.byref(loss), grad.ctypes.data, _stream(stream)))
+    _check(lib.fb_learned_loss_and_grad(pc, pr, pe, R.shape[0], C.byref(loss), grad.ctypes.data, _stream(stream)))
     return loss.value, grad
 
 
 def fb_learned_train_step(pc, R, E, lr, stream=None):
-    if not (_is_cuda_tensor(R) and _is_cuda_tensor(E)):
-        raise ValueError("R and E must be CUDA tensors")
+    pr, pe = _cuda_ptr(R, "R"), _cuda_ptr(E, "E")
     loss = C.c_double()
-    _check(lib.fb_learned_train_step(pc, C.c_void_p(R.data_ptr()), C.c_void_p(E.data_ptr()), R.shape[0],
-                                     float(lr), C.byref(loss), _stream(stream)))
+    _check(lib.fb_learned_train_step(pc, pr, pe, R.shape[0], float(lr), C.byref(loss), _stream(stream)))
     return loss.value
 
 
@@ -668,12 +668,6 @@ def fb_mesh_set_admittance_plus(mesh, beta, stream=None):
     indirect system FB_OP_IBEM."""
     p, ms, keep = _ptr(beta, np.complex128)
     _check(lib.fb_mesh_set_admittance_plus(mesh, p, ms, _stream(stream)))
-
-
-def _cuda_ptr(t, name):
-    if not _is_cuda_tensor(t):
-        raise ValueError(f"{name} must be a CUDA tensor")
-    return C.c_void_p(t.data_ptr())
 
 
 def fb_ibem_gammas_monopole(op, src, stream=None):

@@ -198,3 +198,31 @@ def test_binding_constants_match_the_header():
     assert checked >= 20
     assert binding.NOALLOC_SCRATCH_BYTES == defs["FB_NOALLOC_SCRATCH_BYTES"]
     assert "FB_MAX_RHS" in defs and "FB_TUNE_TIMES" in defs
+
+
+def test_device_pointer_marshalling_refuses_host_and_strided_tensors():
+    """Entry points that take device pointers refuse a host array and a
+    non-contiguous device tensor instead of passing a wrong layout."""
+    import numpy as np
+    import pytest
+    from paper_2103_16073_gb300 import binding
+
+    class FakeDevice:
+        is_cuda = True
+
+        def __init__(self, contiguous):
+            self._c = contiguous
+
+        def is_contiguous(self):
+            return self._c
+
+        def data_ptr(self):
+            return 4096
+
+    assert binding._cuda_ptr(FakeDevice(True), "x").value == 4096
+    with pytest.raises(ValueError, match="contiguous"):
+        binding._cuda_ptr(FakeDevice(False), "x")
+    with pytest.raises(ValueError, match="CUDA"):
+        binding._cuda_ptr(np.zeros(4, np.complex128), "x")
+    with pytest.raises(ValueError, match="contiguous"):
+        binding._ptr(FakeDevice(False))
