@@ -41,3 +41,20 @@ def test_free_field_pulse_arrives_at_r_over_c():
     t0 = R / c
     i_max, i_min = int(np.argmax(p)), int(np.argmin(p))
     assert abs(times[i_max] - (t0 + pulse_dt)) <= dt and abs(times[i_min] - (t0 - pulse_dt)) <= dt
+
+
+def test_wall_model_pairs_printed_in_the_paper():
+    """The oracle's reflection coefficient from the admittance reproduces the
+    (zeta, R, alpha) pairs the paper prints through Eq. (sp4) (golden file
+    with citations), including the sound-hard limit beta = 0."""
+    import json
+    import os
+    from oracle import images
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_wall_models.json")))
+    for c in g["cases"]:
+        R = complex(images.reflection_from_admittance(1.0 / c["zeta"]))
+        assert abs(R - c["R"]) < 1e-12, c
+        assert abs((1 - abs(R) ** 2) - c["alpha"]) < 1e-12, c
+    h = g["sound_hard"]
+    R = complex(images.reflection_from_admittance(h["beta"]))
+    assert abs(R - h["R"]) < 1e-15 and abs(1 - abs(R) ** 2 - h["alpha"]) < 1e-15
